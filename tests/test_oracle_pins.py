@@ -1,0 +1,308 @@
+"""Pins of the FP64 CPU oracle against what the mathematics and the paper fix.
+
+Each test targets a mistake that could hide in the oracle: a wrong quadrature
+or basis (exactness, partition of unity), a dropped or mis-signed term
+(patch test, conservation, free stream, symmetry and definiteness, upwind
+dissipation, the Riemann-jump closed form), a wrong derivative (complex step),
+and the convergence rates stated in Section 4.1 / Table 3.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_07824_b300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+SHEAR2 = np.array([[1.0, 0.3], [0.1, 0.9]])
+SHEAR3 = np.array([[1.0, 0.2, 0.1], [0.0, 0.9, 0.15], [0.05, 0.0, 1.1]])
+
+
+def _mesh(etype, n, **kw):
+    return {0: synth.tri_square, 1: synth.quad_box, 2: synth.hex_box}[etype](n, **kw)
+
+
+# ---------------------------------------------------------------- reference rules
+def test_gauss_and_gll_closed_forms():
+    o = oracle.Oracle(synth.quad_box(2), 2, oracle.POISSON, oracle.CASE_ZERO, nq1=3)
+    nodes, qx, qw, fs, fw = o.ref_rules()
+    # 3-point Gauss-Legendre: 0, +-sqrt(3/5); weights 8/9, 5/9
+    assert np.allclose(np.sort(fs[:, 0]), [-math.sqrt(0.6), 0, math.sqrt(0.6)], atol=1e-15)
+    assert np.allclose(fw[np.argsort(fs[:, 0])], [5 / 9, 8 / 9, 5 / 9], atol=1e-15)
+    # GLL with 3 points: -1, 0, 1
+    assert np.allclose(np.unique(nodes[:, 0]), [-1, 0, 1], atol=1e-15)
+    o = oracle.Oracle(synth.quad_box(2), 3, oracle.POISSON, oracle.CASE_ZERO)
+    assert np.allclose(np.unique(o.ref_rules()[0][:, 0]), [-1, -1 / math.sqrt(5), 1 / math.sqrt(5), 1],
+                       atol=1e-15)
+    o = oracle.Oracle(synth.quad_box(2), 4, oracle.POISSON, oracle.CASE_ZERO)
+    assert np.allclose(np.unique(o.ref_rules()[0][:, 0]),
+                       [-1, -math.sqrt(3 / 7), 0, math.sqrt(3 / 7), 1], atol=1e-15)
+
+
+def _tri_monomial_integral(a, b):
+    # integral of xi^a eta^b over the triangle (-1,-1),(1,-1),(-1,1): with xi = 2s-1,
+    # eta = 2t-1 on the unit triangle, and int s^m t^n = m! n! / (m+n+2)!
+    tot = 0.0
+    for m in range(a + 1):
+        for n in range(b + 1):
+            c = math.comb(a, m) * math.comb(b, n) * 2 ** (m + n) * (-1) ** (a - m + b - n)
+            tot += c * math.factorial(m) * math.factorial(n) / math.factorial(m + n + 2)
+    return 4 * tot
+
+
+@pytest.mark.parametrize("nq1", [2, 3, 4, 5])
+def test_triangle_rule_exactness(nq1):
+    o = oracle.Oracle(synth.tri_square(1), 1, oracle.POISSON, oracle.CASE_ZERO, nq1=nq1)
+    _, qx, qw, _, _ = o.ref_rules()
+    for a in range(2 * nq1 - 1):
+        for b in range(2 * nq1 - 1 - a):
+            got = np.sum(qw * qx[:, 0] ** a * qx[:, 1] ** b)
+            assert abs(got - _tri_monomial_integral(a, b)) < 1e-13, (a, b)
+
+
+@pytest.mark.parametrize("etype", [1, 2])
+def test_tensor_rule_exactness(etype):
+    nq1 = 3
+    o = oracle.Oracle(_mesh(etype, 1), 1, oracle.POISSON, oracle.CASE_ZERO, nq1=nq1)
+    _, qx, qw, _, _ = o.ref_rules()
+    nd = 2 if etype == 1 else 3
+
+    def exact1(a):
+        return 0.0 if a % 2 else 2.0 / (a + 1)
+    for a in range(2 * nq1):
+        for b in range(2 * nq1):
+            c = 1 if nd == 3 else 0
+            got = np.sum(qw * qx[:, 0] ** a * qx[:, 1] ** b * (qx[:, 2] ** c if nd == 3 else 1))
+            ref = exact1(a) * exact1(b) * (exact1(c) if nd == 3 else 1)
+            assert abs(got - ref) < 1e-13
+
+
+@pytest.mark.parametrize("etype,p", [(0, 1), (0, 2), (0, 3), (1, 1), (1, 3), (1, 5), (2, 2), (2, 4)])
+def test_basis_partition_and_kronecker(etype, p):
+    o = oracle.Oracle(_mesh(etype, 1), p, oracle.POISSON, oracle.CASE_ZERO)
+    nodes = o.ref_rules()[0]
+    phi, _ = o.basis(nodes)
+    assert np.allclose(phi, np.eye(o.npe), atol=1e-12)
+    rng = np.random.default_rng(0)
+    pts = rng.uniform(-1, 1, (20, 3))
+    if etype == 0:
+        pts[:, :2] = np.where((pts[:, 0] + pts[:, 1] > 0)[:, None], -pts[:, :2], pts[:, :2])
+    phi, dphi = o.basis(pts)
+    assert np.allclose(phi.sum(1), 1, atol=1e-12)
+    assert np.allclose(dphi.sum(1), 0, atol=1e-11)
+
+
+# ------------------------------------------------------------- discretisation
+@pytest.mark.parametrize("etype,p,model,case", [
+    (0, 1, oracle.POISSON, oracle.CASE_LINEAR), (0, 2, oracle.POISSON, oracle.CASE_POLY2),
+    (0, 3, oracle.CONVDIFF, oracle.CASE_POLY2), (1, 1, oracle.CONVDIFF, oracle.CASE_LINEAR),
+    (1, 2, oracle.POISSON, oracle.CASE_POLY2), (1, 3, oracle.CONVDIFF, oracle.CASE_POLY2),
+    (2, 2, oracle.CONVDIFF, oracle.CASE_POLY2), (2, 1, oracle.POISSON, oracle.CASE_LINEAR)])
+def test_patch_test(etype, p, model, case):
+    """Consistency + uniqueness of LDG: a polynomial of degree <= p (with q = -grad u
+    and the matching source/boundary data) has zero residual."""
+    aff = SHEAR3 if etype == 2 else SHEAR2
+    mesh = _mesh(etype, 3 if etype < 2 else 2, affine=aff)
+    mu = (0.7, 1.3) if model == oracle.POISSON else (0.05, 0.4, 1.0, -0.6, 0.3)
+    o = oracle.Oracle(mesh, p, model, case, mu)
+    u = o.interpolate()
+    r = o.residual(u)
+    assert np.abs(r).max() < 1e-12 * max(1.0, np.abs(o.residual(np.zeros_like(u))).max())
+
+
+@pytest.mark.parametrize("etype,model", [(0, oracle.POISSON), (1, oracle.CONVDIFF), (2, oracle.CONVDIFF),
+                                         (1, oracle.EULER)])
+def test_conservation_periodic(etype, model):
+    """Single-valued numerical fluxes and sum_i phi_i = 1: on a periodic mesh with no
+    source, the sum of all element residuals vanishes for any state."""
+    n = 3
+    nd = 3 if etype == 2 else 2
+    mesh = _mesh(etype, n, hi=(2.0,) * nd, periodic=(True,) * nd)
+    mu = {oracle.POISSON: (1.0, 1.0), oracle.CONVDIFF: (0.1, 0.2, 1.0, 0.5, 0.25), oracle.EULER: (1.4,)}[model]
+    o = oracle.Oracle(mesh, 2, model, oracle.CASE_ZERO if model != oracle.EULER else oracle.CASE_CONST, mu)
+    u = (synth.random_euler_state(mesh.n_elem, o.npe, 3) if model == oracle.EULER
+         else synth.random_vector(o.ndof, 3))
+    r = o.residual(u).reshape(mesh.n_elem, o.ncu, o.npe)
+    tot = r.sum(axis=(0, 2))
+    assert np.all(np.abs(tot) <= 1e-13 * np.abs(r).sum())
+
+
+def test_free_stream_euler():
+    mesh = synth.quad_box(4, hi=(10.0, 10.0), periodic=(True, True), affine=SHEAR2)
+    o = oracle.Oracle(mesh, 3, oracle.EULER, oracle.CASE_CONST, (1.4,))
+    assert np.abs(o.residual(o.interpolate())).max() < 1e-13
+
+
+def test_poisson_jacobian_symmetric_positive_definite():
+    o = oracle.Oracle(synth.tri_square(2, affine=SHEAR2), 2, oracle.POISSON, oracle.CASE_SINSIN, (1.0, 1.0))
+    J = o.jacobian_cs(np.zeros(o.ndof))
+    assert np.linalg.norm(J - J.T) <= 1e-13 * np.linalg.norm(J)
+    assert np.linalg.eigvalsh(0.5 * (J + J.T)).min() > 0
+
+
+def test_upwind_dissipation():
+    """Pure convection with the upwind flux on a periodic mesh: u^T R(u) =
+    1/2 sum_faces int |beta.n| [u]^2 > 0; a constant state gives zero."""
+    mesh = synth.quad_box(3, periodic=(True, True))
+    o = oracle.Oracle(mesh, 2, oracle.CONVDIFF, oracle.CASE_ZERO, (0.0, 0.0, 1.0, 0.5))
+    u = synth.random_vector(o.ndof, 5)
+    assert u @ o.residual(u) > 0
+    assert abs(np.ones(o.ndof) @ o.residual(np.ones(o.ndof))) < 1e-13
+
+
+def test_euler_riemann_jump_closed_form():
+    """Piecewise-constant Euler states U_L (x < 5) and U_R (x > 5) on the periodic
+    square: element residual sums reduce to the Rusanov flux jump on the interface,
+    sum_i R_{K,i} = |face| [ (F(U_R) - F(U_L)).n / 2 + lambda/2 (U_L - U_R) ],
+    lambda = max(|v_L.n| + c_L, |v_R.n| + c_R) (local Lax-Friedrichs)."""
+    g = 1.4
+
+    def prim2cons(r, vx, vy, p):
+        return np.array([r, r * vx, r * vy, p / (g - 1) + 0.5 * r * (vx * vx + vy * vy)])
+
+    def fx(U):
+        r, vx, vy = U[0], U[1] / U[0], U[2] / U[0]
+        p = (g - 1) * (U[3] - 0.5 * r * (vx * vx + vy * vy))
+        return np.array([r * vx, r * vx * vx + p, r * vx * vy, (U[3] + p) * vx]), abs(vx) + math.sqrt(g * p / r)
+    UL, UR = prim2cons(1.0, 0.3, -0.2, 1.0), prim2cons(0.6, -0.1, 0.4, 0.7)
+    n = 6
+    mesh = synth.quad_box(n, hi=(10.0, 10.0), periodic=(True, True))
+    o = oracle.Oracle(mesh, 2, oracle.EULER, oracle.CASE_CONST, (g,))
+    u = np.empty((mesh.n_elem, 4, o.npe))
+    for e in range(mesh.n_elem):
+        u[e] = (UL if (e % n) < n // 2 else UR)[:, None]
+    r = o.residual(u.ravel()).reshape(mesh.n_elem, 4, o.npe).sum(axis=2)
+    FL, sL = fx(UL)
+    FR, sR = fx(UR)
+    lam = max(sL, sR)
+    h = 10.0 / n
+    # element just left of x = 5 (normal +x): interface flux minus its own flux
+    exp_left = h * (0.5 * (FR - FL) + 0.5 * lam * (UL - UR))
+    # element just right of x = 0 seen from the seam at x = 0/10 (normal -x, neighbour U_R)
+    exp_seam = h * (-0.5 * (FR - FL) + 0.5 * lam * (UL - UR))
+    assert np.allclose(r[n // 2 - 1], exp_left, atol=1e-13)
+    assert np.allclose(r[0], exp_seam, atol=1e-13)
+    assert np.allclose(r[1], 0, atol=1e-13)          # no jump on any of its faces
+
+
+# ------------------------------------------------------------------- J.v pins
+@pytest.mark.parametrize("etype,model", [(0, oracle.POISSON), (2, oracle.CONVDIFF), (1, oracle.EULER)])
+def test_jvp_matches_complex_step_jacobian(etype, model):
+    if model == oracle.EULER:
+        mesh = synth.quad_box(3, hi=(10.0, 10.0), periodic=(True, True), affine=SHEAR2)
+        o = oracle.Oracle(mesh, 2, model, oracle.CASE_VORTEX, (1.4,))
+        u = synth.random_euler_state(mesh.n_elem, o.npe, 11)
+    else:
+        mesh = _mesh(etype, 2, affine=SHEAR3 if etype == 2 else SHEAR2)
+        o = oracle.Oracle(mesh, 1 if etype == 2 else 2, model, oracle.CASE_SINSIN,
+                          (1.0, 1.0) if model == oracle.POISSON else (0.1, 0.3, 1.0, 0.5, 0.25))
+        u = synth.random_vector(o.ndof, 11)
+    J = o.jacobian_cs(u)
+    v = synth.random_vector(o.ndof, 12)
+    jv = o.jvp(u, v)
+    assert np.linalg.norm(jv - J @ v) <= 1e-13 * np.linalg.norm(jv)
+    # finite differences agree to O(eps)
+    eps = 1e-7
+    fd = (o.residual(u + eps * v) - o.residual(u - eps * v)) / (2 * eps)
+    assert np.linalg.norm(fd - jv) <= 1e-6 * np.linalg.norm(jv)
+
+
+@pytest.mark.parametrize("etype", [0, 1, 2])
+def test_linear_jvp_is_residual_difference(etype):
+    o = oracle.Oracle(_mesh(etype, 2), 2, oracle.CONVDIFF, oracle.CASE_EXPSIN, (0.05, 0.2, 1.0, 0.5, 0.25))
+    u, v = synth.random_vector(o.ndof, 1), synth.random_vector(o.ndof, 2)
+    jv = o.jvp(u, v)
+    ref = o.residual(v) - o.residual(np.zeros(o.ndof))
+    assert np.linalg.norm(jv - ref) <= 1e-12 * np.linalg.norm(jv)
+
+
+def test_sampled_residual_matches_full():
+    o = oracle.Oracle(synth.hex_box(3), 2, oracle.CONVDIFF, oracle.CASE_EXPSIN, (0.01, 0.01, 1.0, 0.5, 0.25))
+    u, v = synth.random_vector(o.ndof, 3), synth.random_vector(o.ndof, 4)
+    el = np.array([0, 13, 26, 5])
+    full = o.residual(u).reshape(27, 1, -1)
+    assert np.array_equal(o.residual_some(u, el), full[el])
+    fullj = o.jvp(u, v).reshape(27, 1, -1)
+    assert np.array_equal(o.jvp_some(u, v, el), fullj[el])
+
+
+# ------------------------------------------------------------ solver pins
+def test_gmres_matches_dense_solve():
+    mesh = synth.quad_box(3, hi=(10.0, 10.0), periodic=(True, True))
+    o = oracle.Oracle(mesh, 2, oracle.EULER, oracle.CASE_VORTEX, (1.4,))
+    u = o.project(0.0)
+    un = u.copy()
+    o.set_time(1, 0.0, 0.5, un, un)
+    J = o.jacobian_cs(u)
+    b = synth.random_vector(o.ndof, 9)
+    x, its, rc, hist = o.gmres(u, b, m=20, rtol=1e-12, maxit=2000)
+    assert rc == 0
+    xd = np.linalg.solve(J, b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    assert np.all(np.diff(hist[: min(len(hist), 20)]) <= 1e-12 * hist[0])   # monotone within a cycle
+
+
+def test_newton_linear_one_step():
+    o = oracle.Oracle(synth.tri_square(4), 2, oracle.POISSON, oracle.CASE_SINSIN, (1.0, 1.0))
+    u, rc, st = o.newton(np.zeros(o.ndof), m=200, newton_rtol=1e-9, gmres_rtol=1e-11, max_newton=3)
+    assert rc == 0 and st["newton_iters"] == 1
+    assert st["rfinal"] <= 1e-9 * st["r0"]
+
+
+# ---------------------------------------------------------- convergence rates
+def _solve_linear(o):
+    u0 = np.zeros(o.ndof)
+    x, its, rc, _ = o.gmres(u0, o.residual(u0), m=300, rtol=1e-10, maxit=4000)
+    assert rc == 0
+    return -x
+
+
+@pytest.mark.parametrize("p,ns", [(1, (4, 8, 16)), (2, (4, 8, 16)), (3, (4, 8))])
+def test_simplex_convergence_rates_match_section_4_1(p, ns):
+    """On simplices the method converges at p+1 in u and p in q, as Section 4.1 and
+    Table 3 report for tetrahedra."""
+    gold = json.load(open(os.path.join(GOLD, "table3_rates.json")))
+    errs = []
+    for n in ns:
+        o = oracle.Oracle(synth.tri_square(n), p, oracle.POISSON, oracle.CASE_SINSIN, (1.0, 1.0))
+        errs.append(o.l2_error(_solve_linear(o)))
+    e = np.array(errs)
+    ru = np.log2(e[-2, 0] / e[-1, 0])
+    rq = np.log2(e[-2, 1] / e[-1, 1])
+    assert abs(ru - (p + 1)) < 0.3 and abs(rq - p) < 0.3, (ru, rq)
+    assert abs(ru - gold["u_rate_finest"][str(p)]) < 0.3
+    assert abs(rq - gold["q_rate_finest"][str(p)]) < 0.3
+
+
+@pytest.mark.parametrize("etype,p,ns", [(1, 1, (4, 8, 16)), (1, 2, (4, 8, 16)), (1, 3, (8, 16)), (2, 1, (2, 4, 8))])
+def test_tensor_convergence_rates(etype, p, ns):
+    """Uniform tensor meshes with central traces and an O(1) penalty: the LDG error
+    estimates for that penalty scaling give u at order p and q at order p - 1/2; odd p
+    shows rates close to those (even p is optimal, with q superconvergent)."""
+    errs = []
+    for n in ns:
+        o = oracle.Oracle(_mesh(etype, n), p, oracle.POISSON, oracle.CASE_SINSIN, (1.0, 1.0))
+        errs.append(o.l2_error(_solve_linear(o)))
+    e = np.array(errs)
+    ru = np.log2(e[-2, 0] / e[-1, 0])
+    rq = np.log2(e[-2, 1] / e[-1, 1])
+    assert ru > p and rq > p - 0.6, (ru, rq)
+
+
+def test_euler_vortex_consistency_rate():
+    """Truncation error of the spatial operator on the travelling vortex,
+    R(P u(t)) + M d/dt P u(t) -> 0 at order >= p in h."""
+    errs = []
+    p = 2
+    for n in (8, 16):
+        mesh = synth.quad_box(n, hi=(10.0, 10.0), periodic=(True, True))
+        o = oracle.Oracle(mesh, p, oracle.EULER, oracle.CASE_VORTEX, (1.4,))
+        d = 1e-4
+        dudt = (o.project(d) - o.project(-d)) / (2 * d)
+        res = o.residual(o.project(0.0)) + o.mass(dudt)
+        errs.append(np.linalg.norm(res) / np.linalg.norm(o.mass(dudt)))
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > p - 0.3, (errs, rate)
