@@ -1,0 +1,165 @@
+/* ldg.h — C-ABI of the B300 matrix-free LDG hot path.
+ *
+ * The library evaluates the local discontinuous Galerkin (LDG) discretisation of
+ * the first-order system q + grad u = 0, m du/dt + div f(u, q) = s (Section 2.1,
+ * Eq. 1a-1b), its exact Jacobian-vector product, and the matrix-free
+ * Newton-GMRES solve built on them (Section 3.3), with hand-written CUDA kernels
+ * for sm_103a.
+ *
+ * Conventions
+ *  - Every function returns an ldg_status (0 = LDG_OK, < 0 = error); no C++
+ *    exception crosses this boundary. On error, ldg_last_error(ctx) returns a
+ *    message that stays valid until the next call on that context.
+ *  - Vector arguments named *_dev are DEVICE pointers owned by the caller, at
+ *    least n_dof doubles (q: n_dof * dim), 8-byte aligned. Work is queued on
+ *    the context's CUDA stream; results are complete when that stream is.
+ *    Functions ending in _host take HOST pointers and return after the copy
+ *    back to host memory has finished.
+ *  - State layout is element-major: u[e][c][i] for element e, component c and
+ *    local node i (n_pe nodes); q[e][c][d][i] adds the space direction d.
+ *  - Host arrays passed to ldg_create are copied; the caller keeps ownership.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef LDG_H
+#define LDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ldg_ctx ldg_ctx;
+
+/* element shapes: triangles (equispaced Lagrange nodes), quadrilaterals and
+ * hexahedra (tensor Gauss-Lobatto-Legendre nodes); all elements affine */
+enum { LDG_TRI = 0, LDG_QUAD = 1, LDG_HEX = 2 };
+
+/* models of Table 1 (Section 2.1): Poisson and convection-diffusion are diffusion
+ * models (with q, Eq. 1a); 2-D Euler is a convection model (no q) */
+enum { LDG_POISSON = 0, LDG_CONVDIFF = 1, LDG_EULER = 2 };
+
+/* analytic data: Dirichlet/far-field boundary values, source terms and initial states */
+enum {
+  LDG_CASE_ZERO = 0,    /* u = 0, s = 0 */
+  LDG_CASE_SINSIN = 1,  /* u = prod_d sin(pi x_d) */
+  LDG_CASE_EXPSIN = 2,  /* u = exp(sum_d x_d) sin(pi prod_d x_d) */
+  LDG_CASE_POLY2 = 3,   /* a fixed quadratic polynomial (patch test) */
+  LDG_CASE_LINEAR = 4,  /* a fixed linear polynomial (patch test) */
+  LDG_CASE_VORTEX = 5,  /* isentropic vortex, strength 5, centre (5,5), velocity (1,1), period 10 */
+  LDG_CASE_CONST = 6    /* uniform Euler free stream rho = 1, v = (1,1), p = 1 */
+};
+
+typedef enum {
+  LDG_OK = 0,
+  LDG_ERR_ARG = -1,          /* invalid argument (null pointer, bad size or enum) */
+  LDG_ERR_CUDA = -2,         /* a CUDA call failed; the message names it */
+  LDG_ERR_UNSUPPORTED = -3,  /* no compiled kernel for this (element, p, quadrature, model) */
+  LDG_ERR_NONFINITE = -4,    /* NaN/Inf met in a residual or Krylov quantity */
+  LDG_ERR_MAXIT = -5,        /* iteration limit reached before the tolerance */
+  LDG_ERR_MESH = -6          /* mesh rejected: non-affine, inverted or non-conforming */
+} ldg_status;
+
+enum { LDG_STEADY = 0, LDG_BDF1 = 1, LDG_BDF2 = 2 };
+
+/* Mesh (Section 3.2): per-element vertex coordinates and topological vertex ids.
+ * xyz [n_elem][nv][dim] (host), vid [n_elem][nv] (host). Quadrilaterals and
+ * hexahedra list vertices in lexicographic order (x fastest), triangles
+ * counter-clockwise. Faces whose sorted vertex ids match are neighbours; a
+ * periodic mesh shares ids across the period while each element keeps its own
+ * (unwrapped) coordinates. Faces without a partner are boundary faces. */
+typedef struct {
+  int elem_type;
+  int64_t n_elem;
+  const double* xyz;
+  const int64_t* vid;
+} ldg_mesh_desc;
+
+/* Model and parameters mu (Section 2.1):
+ *   Poisson:   mu = {kappa, tau}
+ *   ConvDiff:  mu = {kappa, tau, beta_x, beta_y[, beta_z]}
+ *   Euler:     mu = {gamma}                                       */
+typedef struct {
+  int model;
+  int case_id;
+  int n_mu;
+  const double* mu;
+} ldg_model_desc;
+
+/* Solver options (Section 3.3). nq1 = Gauss points per direction (0 = default:
+ * p + 1 for linear models on quadrilaterals/hexahedra, p + 2 for triangles and Euler). */
+typedef struct {
+  int nq1;
+  int gmres_m;          /* Krylov dimension per restart cycle (default 30) */
+  int max_restarts;     /* restart cycles per linear solve (default 50) */
+  int max_newton;       /* Newton iterations (default 20) */
+  double newton_rtol;   /* stop when ||R(u_k)|| <= newton_rtol ||R(u_0)|| (default 1e-8) */
+  double gmres_rtol;    /* linear solve: ||b - J x|| <= gmres_rtol ||b|| (default 1e-3) */
+} ldg_options;
+
+typedef struct {
+  int newton_iters;
+  int gmres_iters;      /* Arnoldi steps over all linear solves */
+  int jv_calls;
+  int residual_calls;
+  double r0;            /* ||R(u_0)||_2 */
+  double rfinal;        /* ||R(u)||_2 at exit (recomputed in FP64) */
+  double lin_resid;     /* last linear solve: true relative residual */
+  double elapsed_ms;
+  int status;
+} ldg_solve_report;
+
+const char* ldg_version(void);
+
+/* Creates a context: builds the reference element, the affine geometry, the face
+ * connectivity and orientation tables on the host, uploads them, and allocates
+ * the work space. `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ * Returns LDG_ERR_UNSUPPORTED when no kernel is compiled for the combination. */
+int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_desc* model,
+               const ldg_options* opts, void* cuda_stream);
+int ldg_destroy(ldg_ctx* ctx);
+int ldg_set_stream(ldg_ctx* ctx, void* cuda_stream);
+
+/* n_dof = n_elem * n_cu * n_pe; dim = space dimension. */
+int ldg_sizes(const ldg_ctx* ctx, int64_t* n_dof, int* n_pe, int* n_cu, int* dim);
+
+/* Time scheme of the residual (Section 2.2): LDG_STEADY, or BDF1/BDF2 with step dt;
+ * R then gains M (a0 u + a1 u^n + a2 u^{n-1}) / dt. u_n_dev / u_nm1_dev are read
+ * once here (the history term is formed on the device); u_nm1_dev may be NULL for BDF1.
+ * t is the time at which boundary data are evaluated. */
+int ldg_set_time(ldg_ctx* ctx, int scheme, double t, double dt, const double* u_n_dev,
+                 const double* u_nm1_dev);
+
+/* Residual R(u) of Eq. 1b (with the q-stage of Eq. 1a for diffusion models). */
+int ldg_residual(ldg_ctx* ctx, const double* u_dev, double* r_dev);
+
+/* Exact J(u) v = dR/du(u) v (Section 3.3, the automatic-differentiation option):
+ * forward-mode dual numbers for nonlinear models, the homogeneous linear operator
+ * for linear ones. */
+int ldg_jvp(ldg_ctx* ctx, const double* u_dev, const double* v_dev, double* jv_dev);
+
+/* q of Eq. 1a for diffusion models: q_dev [n_elem][n_cu][dim][n_pe]. */
+int ldg_q(ldg_ctx* ctx, const double* u_dev, double* q_dev);
+
+/* Nodal interpolant of the context's analytic case at time t. */
+int ldg_interpolate(ldg_ctx* ctx, double t, double* u_dev);
+
+/* GMRES(m) on J(u) x = b from x = 0 (classical Gram-Schmidt with one
+ * re-orthogonalisation, Givens rotations, FP64), to gmres_rtol. */
+int ldg_gmres(ldg_ctx* ctx, const double* u_dev, const double* b_dev, double* x_dev, ldg_solve_report* rep);
+
+/* Newton-GMRES (Section 3.3): u <- u - delta with J(u) delta = R(u), until
+ * ||R(u)|| <= newton_rtol ||R(u_0)||. u_dev is the initial guess on entry and the
+ * solution on return. */
+int ldg_newton_gmres(ldg_ctx* ctx, double* u_dev, ldg_solve_report* rep);
+
+/* The same solve with u in HOST memory: copied to the device, solved, copied back. */
+int ldg_newton_gmres_host(ldg_ctx* ctx, double* u_host, ldg_solve_report* rep);
+
+const char* ldg_last_error(const ldg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LDG_H */

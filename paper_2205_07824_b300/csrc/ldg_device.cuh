@@ -1,0 +1,357 @@
+// Device building blocks of the LDG hot path (Section 2.2; Section 3.3):
+// forward-mode dual numbers for the exact J.v, element traits with their
+// reference operators (sum-factorised tensor elements, full-matrix triangles),
+// and the pointwise model functions of the first-order system of Eq. 1a-1b.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ldg {
+
+// ------------------------------------------------------------------ scalars
+template <class R> struct Dual {
+  R v, d;
+  __host__ __device__ Dual() {}
+  __host__ __device__ Dual(R a) : v(a), d(R(0)) {}
+  __host__ __device__ Dual(R a, R b) : v(a), d(b) {}
+};
+template <class R> __device__ __forceinline__ Dual<R> operator+(Dual<R> a, Dual<R> b) { return Dual<R>(a.v + b.v, a.d + b.d); }
+template <class R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a, Dual<R> b) { return Dual<R>(a.v - b.v, a.d - b.d); }
+template <class R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a) { return Dual<R>(-a.v, -a.d); }
+template <class R> __device__ __forceinline__ Dual<R> operator*(Dual<R> a, Dual<R> b) { return Dual<R>(a.v * b.v, a.d * b.v + a.v * b.d); }
+template <class R> __device__ __forceinline__ Dual<R> operator/(Dual<R> a, Dual<R> b) {
+  R inv = R(1) / b.v;
+  R q = a.v * inv;
+  return Dual<R>(q, (a.d - q * b.d) * inv);
+}
+template <class R> __device__ __forceinline__ Dual<R> operator+(Dual<R> a, R b) { return Dual<R>(a.v + b, a.d); }
+template <class R> __device__ __forceinline__ Dual<R> operator+(R a, Dual<R> b) { return Dual<R>(a + b.v, b.d); }
+template <class R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a, R b) { return Dual<R>(a.v - b, a.d); }
+template <class R> __device__ __forceinline__ Dual<R> operator-(R a, Dual<R> b) { return Dual<R>(a - b.v, -b.d); }
+template <class R> __device__ __forceinline__ Dual<R> operator*(Dual<R> a, R b) { return Dual<R>(a.v * b, a.d * b); }
+template <class R> __device__ __forceinline__ Dual<R> operator*(R a, Dual<R> b) { return Dual<R>(a * b.v, a * b.d); }
+template <class R> __device__ __forceinline__ Dual<R> operator/(Dual<R> a, R b) { R i = R(1) / b; return Dual<R>(a.v * i, a.d * i); }
+template <class R> __device__ __forceinline__ Dual<R> operator/(R a, Dual<R> b) {
+  R i = R(1) / b.v;
+  R q = a * i;
+  return Dual<R>(q, -q * b.d * i);
+}
+template <class R> __device__ __forceinline__ Dual<R>& operator+=(Dual<R>& a, Dual<R> b) { a.v += b.v; a.d += b.d; return a; }
+template <class R> __device__ __forceinline__ Dual<R>& operator-=(Dual<R>& a, Dual<R> b) { a.v -= b.v; a.d -= b.d; return a; }
+template <class R> __device__ __forceinline__ Dual<R> dsqrt(Dual<R> a) {
+  R s = sqrt(a.v);
+  return Dual<R>(s, a.d / (R(2) * s));
+}
+__device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
+
+template <class S> struct RealOf { typedef S type; };
+template <class R> struct RealOf<Dual<R>> { typedef R type; };
+
+__device__ __forceinline__ double val(double x) { return x; }
+__device__ __forceinline__ float val(float x) { return x; }
+template <class R> __device__ __forceinline__ R val(Dual<R> x) { return x.v; }
+// The part of a scalar a kernel writes out: the tangent for dual numbers, else the value.
+__device__ __forceinline__ double outp(double x) { return x; }
+__device__ __forceinline__ float outp(float x) { return x; }
+template <class R> __device__ __forceinline__ R outp(Dual<R> x) { return x.d; }
+
+// |x| with d|x| = 0 at x = 0; max(a, b) takes a on a tie (the element's own side).
+template <class S> __device__ __forceinline__ S sabs(S x) {
+  auto r = val(x);
+  return r > 0 ? x : (r < 0 ? -x : x * typename RealOf<S>::type(0));
+}
+template <class S> __device__ __forceinline__ S smax(S a, S b) { return val(a) >= val(b) ? a : b; }
+
+constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// ----------------------------------------------------------------- models
+enum { M_POISSON = 0, M_CONVDIFF = 1, M_EULER = 2 };
+enum { C_ZERO = 0, C_SINSIN = 1, C_EXPSIN = 2, C_POLY2 = 3, C_LINEAR = 4, C_VORTEX = 5, C_CONST = 6 };
+
+struct ModelParams {
+  double kappa, tau, beta[3], gamma;
+  int cas;
+};
+
+// Exact solution / boundary data and source of the manufactured and analytic cases.
+template <int DIM>
+__device__ void exact_state(const ModelParams& mp, int ncu, const double* x, double t, double* g) {
+  const double PI = 3.141592653589793238462643;
+  if (ncu == 4) {
+    if (mp.cas == C_VORTEX) {
+      // isentropic vortex of strength 5 centred at (5,5) + t (1,1) on the periodic [0,10]^2
+      double dx = x[0] - 5.0 - t, dy = x[1] - 5.0 - t;
+      dx -= 10.0 * floor(dx / 10.0 + 0.5);
+      dy -= 10.0 * floor(dy / 10.0 + 0.5);
+      double ex = exp(0.5 * (1.0 - dx * dx - dy * dy));
+      double k = 5.0 / (2.0 * PI) * ex;
+      double ux = 1.0 - k * dy, uy = 1.0 + k * dx;
+      double gm = mp.gamma;
+      double T = 1.0 - (gm - 1.0) * 25.0 / (8.0 * gm * PI * PI) * ex * ex;
+      double rho = pow(T, 1.0 / (gm - 1.0));
+      double p = pow(rho, gm);
+      g[0] = rho; g[1] = rho * ux; g[2] = rho * uy;
+      g[3] = p / (gm - 1.0) + 0.5 * rho * (ux * ux + uy * uy);
+    } else {
+      g[0] = 1.0; g[1] = 1.0; g[2] = 1.0; g[3] = 1.0 / (mp.gamma - 1.0) + 1.0;
+    }
+    return;
+  }
+  double u = 0.0;
+  switch (mp.cas) {
+    case C_SINSIN: { u = 1.0; for (int d = 0; d < DIM; ++d) u *= sin(PI * x[d]); break; }
+    case C_EXPSIN: {
+      double s = 0.0, pr = 1.0;
+      for (int d = 0; d < DIM; ++d) { s += x[d]; pr *= x[d]; }
+      u = exp(s) * sin(PI * pr);
+      break;
+    }
+    case C_POLY2: {
+      double X = x[0], Y = x[1];
+      u = 1.0 + 0.5 * X - 0.3 * Y + 0.7 * X * Y - 0.4 * X * X + 0.2 * Y * Y;
+      if (DIM == 3) { double Z = x[DIM - 1]; u += 0.25 * Z + 0.1 * X * Z - 0.35 * Z * Z; }
+      break;
+    }
+    case C_LINEAR: {
+      const double a[3] = {0.5, -0.3, 0.25};
+      u = 1.0;
+      for (int d = 0; d < DIM; ++d) u += a[d] * x[d];
+      break;
+    }
+    default: u = 0.0;
+  }
+  g[0] = u;
+}
+
+// Source s of Eq. 1b such that div(beta u - kappa grad u) = s for the scalar cases.
+template <int DIM>
+__device__ double source_term(const ModelParams& mp, bool conv, const double* x) {
+  const double PI = 3.141592653589793238462643;
+  double grad[3] = {0.0, 0.0, 0.0}, lap = 0.0;
+  switch (mp.cas) {
+    case C_SINSIN: {
+      double sn[3], cs[3];
+      for (int d = 0; d < DIM; ++d) { sn[d] = sin(PI * x[d]); cs[d] = cos(PI * x[d]); }
+      double u = 1.0;
+      for (int d = 0; d < DIM; ++d) u *= sn[d];
+      for (int k = 0; k < DIM; ++k) {
+        double g = PI * cs[k];
+        for (int d = 0; d < DIM; ++d) if (d != k) g *= sn[d];
+        grad[k] = g;
+      }
+      lap = -DIM * PI * PI * u;
+      break;
+    }
+    case C_EXPSIN: {
+      double s = 0.0, pr = 1.0;
+      for (int d = 0; d < DIM; ++d) { s += x[d]; pr *= x[d]; }
+      double E = exp(s), S = sin(PI * pr), C = cos(PI * pr);
+      for (int k = 0; k < DIM; ++k) {
+        double m = 1.0;
+        for (int d = 0; d < DIM; ++d) if (d != k) m *= x[d];
+        grad[k] = E * (S + PI * m * C);
+        lap += E * (S + 2.0 * PI * m * C - PI * PI * m * m * S);
+      }
+      break;
+    }
+    case C_POLY2: {
+      double X = x[0], Y = x[1];
+      grad[0] = 0.5 + 0.7 * Y - 0.8 * X;
+      grad[1] = -0.3 + 0.7 * X + 0.4 * Y;
+      lap = -0.4;
+      if (DIM == 3) {
+        double Z = x[DIM - 1];
+        grad[0] += 0.1 * Z;
+        grad[DIM - 1] = 0.25 + 0.1 * X - 0.7 * Z;
+        lap -= 0.7;
+      }
+      break;
+    }
+    case C_LINEAR: { grad[0] = 0.5; grad[1] = -0.3; if (DIM == 3) grad[DIM - 1] = 0.25; break; }
+    default: break;
+  }
+  double bg = 0.0;
+  if (conv) for (int d = 0; d < DIM; ++d) bg += mp.beta[d] * grad[d];
+  return bg - mp.kappa * lap;
+}
+
+// Scalar diffusion models: f = kappa q (Poisson) or beta u + kappa q (convection-diffusion).
+template <int DIM, bool CONV> struct ScalarModel {
+  static constexpr int NCU = 1;
+  static constexpr bool HASQ = true;
+  static constexpr bool LINEAR = true;
+  static constexpr int KIND = CONV ? M_CONVDIFF : M_POISSON;
+
+  template <class S> __device__ static void flux(const S* u, const S* q, S* f, const ModelParams& mp) {
+    for (int d = 0; d < DIM; ++d) {
+      S v = q[d] * mp.kappa;
+      if (CONV) v = v + u[0] * mp.beta[d];
+      f[d] = v;
+    }
+  }
+  // interior numerical flux: upwind convection, central diffusion plus tau jump
+  template <class S> __device__ static void fhat(const S* um, const S* up, const S* qm, const S* qp,
+                                                 const double* n, S* fh, const ModelParams& mp) {
+    S acc = (um[0] - up[0]) * mp.tau;
+    for (int d = 0; d < DIM; ++d) acc = acc + (qm[d] + qp[d]) * (0.5 * mp.kappa * n[d]);
+    if (CONV) {
+      double bn = 0.0;
+      for (int d = 0; d < DIM; ++d) bn += mp.beta[d] * n[d];
+      acc = acc + (bn >= 0.0 ? um[0] : up[0]) * bn;
+    }
+    fh[0] = acc;
+  }
+  // Dirichlet face: uhat = g; fhat = beta.n u_upwind + kappa q-.n + tau (u- - g)
+  template <class S> __device__ static void fhat_bnd(const S* um, const S* qm, const double* g,
+                                                     const double* n, S* fh, const ModelParams& mp) {
+    S acc = (um[0] - g[0]) * mp.tau;
+    for (int d = 0; d < DIM; ++d) acc = acc + qm[d] * (mp.kappa * n[d]);
+    if (CONV) {
+      double bn = 0.0;
+      for (int d = 0; d < DIM; ++d) bn += mp.beta[d] * n[d];
+      acc = acc + (bn >= 0.0 ? um[0] * bn : S(bn * g[0]));
+    }
+    fh[0] = acc;
+  }
+};
+
+// 2-D compressible Euler with the local Lax-Friedrichs (Rusanov) flux.
+struct EulerModel {
+  static constexpr int NCU = 4;
+  static constexpr bool HASQ = false;
+  static constexpr bool LINEAR = false;
+  static constexpr int KIND = M_EULER;
+
+  template <class S> __device__ static void flux(const S* u, const S*, S* f, const ModelParams& mp) {
+    typedef typename RealOf<S>::type R;
+    S ir = R(1) / u[0];
+    S vx = u[1] * ir, vy = u[2] * ir;
+    S p = (u[3] - (u[1] * vx + u[2] * vy) * R(0.5)) * R(mp.gamma - 1.0);
+    S h = u[3] + p;
+    f[0] = u[1];           f[1] = u[2];
+    f[2] = u[1] * vx + p;  f[3] = u[1] * vy;
+    f[4] = u[2] * vx;      f[5] = u[2] * vy + p;
+    f[6] = h * vx;         f[7] = h * vy;
+  }
+  template <class S> __device__ static S normal_flux(const S* u, const double* n, S* fn, const ModelParams& mp) {
+    typedef typename RealOf<S>::type R;
+    S ir = R(1) / u[0];
+    S vx = u[1] * ir, vy = u[2] * ir;
+    S p = (u[3] - (u[1] * vx + u[2] * vy) * R(0.5)) * R(mp.gamma - 1.0);
+    S vn = vx * R(n[0]) + vy * R(n[1]);
+    fn[0] = u[0] * vn;
+    fn[1] = u[1] * vn + p * R(n[0]);
+    fn[2] = u[2] * vn + p * R(n[1]);
+    fn[3] = (u[3] + p) * vn;
+    S c = dsqrt(p * ir * R(mp.gamma));
+    return sabs(vn) + c;
+  }
+  template <class S> __device__ static void fhat(const S* um, const S* up, const S*, const S*,
+                                                 const double* n, S* fh, const ModelParams& mp) {
+    typedef typename RealOf<S>::type R;
+    S fm[4], fp[4];
+    S lm = normal_flux(um, n, fm, mp);
+    S lp = normal_flux(up, n, fp, mp);
+    S lam = smax(lm, lp);
+    for (int c = 0; c < 4; ++c) fh[c] = (fm[c] + fp[c]) * R(0.5) + lam * R(0.5) * (um[c] - up[c]);
+  }
+  // far field: Rusanov flux against the exact state
+  template <class S> __device__ static void fhat_bnd(const S* um, const S* qm, const double* g,
+                                                     const double* n, S* fh, const ModelParams& mp) {
+    typedef typename RealOf<S>::type R;
+    S up[4] = {S(R(g[0])), S(R(g[1])), S(R(g[2])), S(R(g[3]))};
+    fhat(um, up, qm, qm, n, fh, mp);
+  }
+};
+
+// -------------------------------------------------------- element traits
+// Operator blob (FP64, row-major) shared by all elements of a context:
+//   tensor: B[NQ][N1], D[NQ][N1], W[NQ], XQ[NQ], Dn[N1][N1], Minv1[N1][N1], XN[N1]
+//   triangle: B[NQV][NPE], Dr[NQV][NPE], Ds[NQV][NPE], WV[NQV], XQV[NQV][2],
+//             Bf[NFQ][NFN], WF[NFQ], SF[NFQ], Dnr[NPE][NPE], Dns[NPE][NPE], Minv[NPE][NPE], XN[NPE][2]
+template <int DIM_, int P_, int NQ_> struct TensorEl {
+  static constexpr bool TENSOR = true;
+  static constexpr int DIM = DIM_, P = P_, N1 = P_ + 1, NQ = NQ_;
+  static constexpr int NPE = ipow(N1, DIM), NQV = ipow(NQ, DIM);
+  static constexpr int NF = 2 * DIM, NFN = ipow(N1, DIM - 1), NFQ = ipow(NQ, DIM - 1);
+  // blob offsets
+  static constexpr int OB = 0, OD = OB + NQ * N1, OW = OD + NQ * N1, OXQ = OW + NQ, ODN = OXQ + NQ,
+                       OMI = ODN + N1 * N1, OXN = OMI + N1 * N1, OPS = OXN + N1;
+  // local node of face-node j on face f = 2*axis + side (free axes ascending, first fastest)
+  __device__ static int face_node(int f, int j) {
+    int ax = f >> 1, side = f & 1;
+    int fix = side ? N1 - 1 : 0;
+    int idx[3], m = 0, jj = j;
+    for (int d = 0; d < DIM; ++d) {
+      if (d == ax) idx[d] = fix;
+      else { idx[d] = (m == 0) ? (jj % N1) : (jj / N1); ++m; }
+    }
+    int r = idx[0] + N1 * idx[1];
+    if (DIM == 3) r += N1 * N1 * idx[2];
+    return r;
+  }
+};
+
+template <int P_, int NQ_> struct TriEl {
+  static constexpr bool TENSOR = false;
+  static constexpr int DIM = 2, P = P_, NQ = NQ_, N1 = P_ + 1;
+  static constexpr int NPE = (P_ + 1) * (P_ + 2) / 2, NQV = NQ_ * NQ_;
+  static constexpr int NF = 3, NFN = P_ + 1, NFQ = NQ_;
+  static constexpr int OB = 0, ODR = OB + NQV * NPE, ODS = ODR + NQV * NPE, OWV = ODS + NQV * NPE,
+                       OXQ = OWV + NQV, OBF = OXQ + 2 * NQV, OWF = OBF + NFQ * NFN, OSF = OWF + NFQ,
+                       ODNR = OSF + NFQ, ODNS = ODNR + NPE * NPE, OMI = ODNS + NPE * NPE,
+                       OXN = OMI + NPE * NPE, OPS = OXN + 2 * NPE;
+  // node (i, j), i + j <= P, numbered row by row: j (P+1) - j (j-1)/2 + i
+  __device__ static int nidx(int i, int j) { return j * (P + 1) - j * (j - 1) / 2 + i; }
+  // edge nodes in the direction of the edge: f0 v0->v1, f1 v1->v2, f2 v2->v0
+  __device__ static int face_node(int f, int t) {
+    if (f == 0) return nidx(t, 0);
+    if (f == 1) return nidx(P - t, t);
+    return nidx(0, P - t);
+  }
+};
+
+// ---------------------------------------------------------- contractions
+// out[b][o] = sum_i M(o, i) in[b][i] along axis AX of a tensor of extents E0 x E1 x E2
+// (first fastest), with M(o, i) = Mat[o * NI + i] or, if TRANS, Mat[i * MOUT + o].
+// Every output is owned by one thread, so ACC (+=) is race-free.
+template <int AX, int E0, int E1, int E2, int MOUT, bool TRANS, bool ACC, class T, class TM>
+__device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict__ out,
+                                         const TM* __restrict__ Mat, int nbatch) {
+  constexpr int O0 = AX == 0 ? MOUT : E0, O1 = AX == 1 ? MOUT : E1, O2 = AX == 2 ? MOUT : E2;
+  constexpr int OSZ = O0 * O1 * O2, ISZ = E0 * E1 * E2;
+  constexpr int NI = AX == 0 ? E0 : (AX == 1 ? E1 : E2);
+  constexpr int STR = AX == 0 ? 1 : (AX == 1 ? E0 : E0 * E1);
+  const int total = nbatch * OSZ;
+  for (int it = threadIdx.x; it < total; it += blockDim.x) {
+    int b = it / OSZ, r = it - b * OSZ;
+    int o0 = r % O0, o1 = (r / O0) % O1, o2 = r / (O0 * O1);
+    int oa = AX == 0 ? o0 : (AX == 1 ? o1 : o2);
+    const T* src = in + b * ISZ + (AX == 0 ? o1 * E0 + o2 * E0 * E1 : (AX == 1 ? o0 + o2 * E0 * E1 : o0 + o1 * E0));
+    T acc = ACC ? out[it] : T(0);
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      TM m = TRANS ? Mat[i * MOUT + oa] : Mat[oa * NI + i];
+      acc += src[i * STR] * m;
+    }
+    out[it] = acc;
+  }
+}
+
+// out[b][o] = sum_i Mat[o][i] in[b][i] (full matrix, NO x NI), or transposed.
+template <int NO, int NI, bool TRANS, bool ACC, class T, class TM>
+__device__ __forceinline__ void matvec(const T* __restrict__ in, T* __restrict__ out,
+                                       const TM* __restrict__ Mat, int nbatch) {
+  const int total = nbatch * NO;
+  for (int it = threadIdx.x; it < total; it += blockDim.x) {
+    int b = it / NO, o = it - b * NO;
+    const T* src = in + b * NI;
+    T acc = ACC ? out[it] : T(0);
+#pragma unroll 4
+    for (int i = 0; i < NI; ++i) acc += src[i] * (TRANS ? Mat[i * NO + o] : Mat[o * NI + i]);
+    out[it] = acc;
+  }
+}
+
+}  // namespace ldg

@@ -1,0 +1,451 @@
+// Host-side preparation of the LDG operator (see ldg_host.h).
+//
+// Reference elements follow the readings of Section 2.2 used throughout the
+// library: tensor elements carry Gauss-Lobatto-Legendre nodes and Gauss-Legendre
+// quadrature with nq points per direction; triangles carry equispaced nodes
+// (Silvester's closed form of the Lagrange basis) and a collapsed Gauss rule.
+#include "ldg_host.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <unordered_map>
+
+namespace ldg {
+namespace {
+
+// Legendre P_n(x) and P_{n-1}(x) by the three-term recurrence.
+void leg_pair(int n, double x, double& pn, double& pn1) {
+  double a = 1.0, b = x;
+  if (n == 0) { pn = 1.0; pn1 = 0.0; return; }
+  for (int k = 2; k <= n; ++k) {
+    double c = ((2.0 * k - 1.0) * x * b - (k - 1.0) * a) / k;
+    a = b; b = c;
+  }
+  pn = b; pn1 = a;
+}
+
+// Gauss-Legendre: Newton on P_n with P_n' = n (x P_n - P_{n-1}) / (x^2 - 1).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n); w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (4.0 * i + 3.0) / (4.0 * n + 2.0));
+    double dp = 1.0;
+    for (int it = 0; it < 60; ++it) {
+      double pn, pn1;
+      leg_pair(n, z, pn, pn1);
+      dp = n * (z * pn - pn1) / (z * z - 1.0);
+      double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) <= 1e-17) break;
+    }
+    double pn, pn1;
+    leg_pair(n, z, pn, pn1);
+    dp = n * (z * pn - pn1) / (z * z - 1.0);
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Gauss-Lobatto-Legendre: endpoints and the zeros of P_N', by Newton with
+// P_N'' from Legendre's equation (1 - x^2) P'' = 2 x P' - N (N + 1) P.
+void gauss_lobatto(int n1, std::vector<double>& x) {
+  int N = n1 - 1;
+  x.assign(n1, 0.0);
+  x[0] = -1.0; x[N] = 1.0;
+  for (int i = 1; i < N; ++i) {
+    double z = -std::cos(M_PI * i / N);
+    for (int it = 0; it < 60; ++it) {
+      double pn, pn1;
+      leg_pair(N, z, pn, pn1);
+      double d1 = N * (z * pn - pn1) / (z * z - 1.0);
+      double d2 = (2.0 * z * d1 - N * (N + 1.0) * pn) / (1.0 - z * z);
+      double dz = d1 / d2;
+      z -= dz;
+      if (std::fabs(dz) <= 1e-17) break;
+    }
+    x[i] = z;
+  }
+}
+
+// Barycentric Lagrange interpolation on nodes X.
+struct Bary {
+  std::vector<double> X, lam;
+  explicit Bary(const std::vector<double>& nodes) : X(nodes), lam(nodes.size(), 1.0) {
+    for (size_t j = 0; j < X.size(); ++j)
+      for (size_t m = 0; m < X.size(); ++m)
+        if (m != j) lam[j] /= (X[j] - X[m]);
+  }
+  // values of all basis functions at x
+  void values(double x, double* l) const {
+    const size_t n = X.size();
+    for (size_t j = 0; j < n; ++j)
+      if (x == X[j]) { for (size_t m = 0; m < n; ++m) l[m] = (m == j) ? 1.0 : 0.0; return; }
+    double den = 0.0;
+    for (size_t j = 0; j < n; ++j) den += lam[j] / (x - X[j]);
+    for (size_t j = 0; j < n; ++j) l[j] = lam[j] / (x - X[j]) / den;
+  }
+  // differentiation matrix at the nodes: Dn[i][j] = l_j'(X_i)
+  std::vector<double> dmat() const {
+    const size_t n = X.size();
+    std::vector<double> D(n * n, 0.0);
+    for (size_t i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (size_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        D[i * n + j] = (lam[j] / lam[i]) / (X[i] - X[j]);
+        s += D[i * n + j];
+      }
+      D[i * n + i] = -s;
+    }
+    return D;
+  }
+};
+
+bool invert(std::vector<double> A, int n, std::vector<double>& inv) {
+  inv.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r) if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) return false;
+    for (int k = 0; k < n; ++k) { std::swap(A[c * n + k], A[piv * n + k]); std::swap(inv[c * n + k], inv[piv * n + k]); }
+    double d = 1.0 / A[c * n + c];
+    for (int k = 0; k < n; ++k) { A[c * n + k] *= d; inv[c * n + k] *= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = A[r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) { A[r * n + k] -= f * A[c * n + k]; inv[r * n + k] -= f * inv[c * n + k]; }
+    }
+  }
+  return true;
+}
+
+// Silvester's product form of the equispaced Lagrange basis on the triangle:
+// phi_{i,j,k} = R_k(l1) R_i(l2) R_j(l3), R_m(l) = prod_{a<m} (p l - a) / (a + 1),
+// barycentric l1 = -(xi + eta)/2, l2 = (1 + xi)/2, l3 = (1 + eta)/2.
+double silv(int m, int p, double l) {
+  double r = 1.0;
+  for (int a = 0; a < m; ++a) r *= (p * l - a) / (a + 1.0);
+  return r;
+}
+double dsilv(int m, int p, double l) {
+  double s = 0.0;
+  for (int b = 0; b < m; ++b) {
+    double t = p / (b + 1.0);
+    for (int a = 0; a < m; ++a) if (a != b) t *= (p * l - a) / (a + 1.0);
+    s += t;
+  }
+  return s;
+}
+void tri_basis(int p, double xi, double eta, double* phi, double* dr, double* ds) {
+  double l1 = -(xi + eta) / 2.0, l2 = (1.0 + xi) / 2.0, l3 = (1.0 + eta) / 2.0;
+  int n = 0;
+  for (int j = 0; j <= p; ++j)
+    for (int i = 0; i + j <= p; ++i, ++n) {
+      int k = p - i - j;
+      double a = silv(k, p, l1), b = silv(i, p, l2), c = silv(j, p, l3);
+      double da = dsilv(k, p, l1), db = dsilv(i, p, l2), dc = dsilv(j, p, l3);
+      phi[n] = a * b * c;
+      // d l1/d xi = d l1/d eta = -1/2, d l2/d xi = 1/2, d l3/d eta = 1/2
+      dr[n] = -0.5 * da * b * c + 0.5 * a * db * c;
+      ds[n] = -0.5 * da * b * c + 0.5 * a * b * dc;
+    }
+}
+
+}  // namespace
+
+bool build_ref_ops(int etype, int p, int nq, RefOps& R, std::string& err) {
+  if (p < 1 || p > 8 || nq < 1 || nq > 10) { err = "unsupported order or quadrature"; return false; }
+  R.etype = etype; R.p = p; R.nq = nq;
+  std::vector<double> gx, gw;
+  gauss_legendre(nq, gx, gw);
+  R.blob.clear();
+  auto put = [&](double v) { R.blob.push_back(v); };
+  if (etype == E_TRI) {
+    R.dim = 2; R.npe = (p + 1) * (p + 2) / 2; R.nqv = nq * nq; R.nf = 3; R.nfn = p + 1; R.nfq = nq;
+    const int npe = R.npe, nqv = R.nqv;
+    std::vector<double> qx(2 * nqv), qw(nqv);
+    for (int b = 0; b < nq; ++b)
+      for (int a = 0; a < nq; ++a) {
+        int q = a + nq * b;
+        qx[2 * q] = 0.5 * (1.0 + gx[a]) * (1.0 - gx[b]) - 1.0;
+        qx[2 * q + 1] = gx[b];
+        qw[q] = gw[a] * gw[b] * 0.5 * (1.0 - gx[b]);
+      }
+    std::vector<double> B(nqv * npe), Dr(nqv * npe), Ds(nqv * npe);
+    for (int q = 0; q < nqv; ++q) tri_basis(p, qx[2 * q], qx[2 * q + 1], &B[q * npe], &Dr[q * npe], &Ds[q * npe]);
+    std::vector<double> xn(2 * npe);
+    {
+      int n = 0;
+      for (int j = 0; j <= p; ++j)
+        for (int i = 0; i + j <= p; ++i, ++n) { xn[2 * n] = -1.0 + 2.0 * i / p; xn[2 * n + 1] = -1.0 + 2.0 * j / p; }
+    }
+    std::vector<double> Dnr(npe * npe), Dns(npe * npe), tmp(npe);
+    for (int i = 0; i < npe; ++i) tri_basis(p, xn[2 * i], xn[2 * i + 1], tmp.data(), &Dnr[i * npe], &Dns[i * npe]);
+    std::vector<double> M(npe * npe, 0.0), Mi;
+    for (int q = 0; q < nqv; ++q)
+      for (int i = 0; i < npe; ++i)
+        for (int j = 0; j < npe; ++j) M[i * npe + j] += qw[q] * B[q * npe + i] * B[q * npe + j];
+    if (!invert(M, npe, Mi)) { err = "singular reference mass matrix"; return false; }
+    std::vector<double> en(p + 1);
+    for (int t = 0; t <= p; ++t) en[t] = -1.0 + 2.0 * t / p;
+    Bary eb(en);
+    std::vector<double> Bf(nq * (p + 1));
+    for (int k = 0; k < nq; ++k) eb.values(gx[k], &Bf[k * (p + 1)]);
+    for (double v : B) put(v);
+    for (double v : Dr) put(v);
+    for (double v : Ds) put(v);
+    for (double v : qw) put(v);
+    for (double v : qx) put(v);
+    for (double v : Bf) put(v);
+    for (double v : gw) put(v);
+    for (double v : gx) put(v);
+    for (double v : Dnr) put(v);
+    for (double v : Dns) put(v);
+    for (double v : Mi) put(v);
+    for (double v : xn) put(v);
+    return true;
+  }
+  if (etype != E_QUAD && etype != E_HEX) { err = "unknown element type"; return false; }
+  R.dim = etype == E_QUAD ? 2 : 3;
+  const int n1 = p + 1;
+  R.npe = 1; R.nqv = 1; R.nfn = 1; R.nfq = 1;
+  for (int d = 0; d < R.dim; ++d) { R.npe *= n1; R.nqv *= nq; }
+  for (int d = 0; d < R.dim - 1; ++d) { R.nfn *= n1; R.nfq *= nq; }
+  R.nf = 2 * R.dim;
+  std::vector<double> xn;
+  gauss_lobatto(n1, xn);
+  Bary bl(xn);
+  std::vector<double> Dn = bl.dmat();
+  std::vector<double> B(nq * n1), D(nq * n1, 0.0);
+  for (int q = 0; q < nq; ++q) bl.values(gx[q], &B[q * n1]);
+  // l_j' is a polynomial of degree p: l_j'(x) = sum_i l_j'(X_i) l_i(x)
+  for (int q = 0; q < nq; ++q)
+    for (int j = 0; j < n1; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < n1; ++i) s += Dn[i * n1 + j] * B[q * n1 + i];
+      D[q * n1 + j] = s;
+    }
+  std::vector<double> M1(n1 * n1, 0.0), M1i;
+  for (int q = 0; q < nq; ++q)
+    for (int i = 0; i < n1; ++i)
+      for (int j = 0; j < n1; ++j) M1[i * n1 + j] += gw[q] * B[q * n1 + i] * B[q * n1 + j];
+  if (!invert(M1, n1, M1i)) { err = "singular 1-D mass matrix (nq < p + 1?)"; return false; }
+  for (double v : B) put(v);
+  for (double v : D) put(v);
+  for (double v : gw) put(v);
+  for (double v : gx) put(v);
+  for (double v : Dn) put(v);
+  for (double v : M1i) put(v);
+  for (double v : xn) put(v);
+  return true;
+}
+
+void ref_nodes(const RefOps& R, std::vector<double>& out) {
+  out.assign((size_t)R.npe * R.dim, 0.0);
+  if (R.etype == E_TRI) {
+    int n = 0;
+    for (int j = 0; j <= R.p; ++j)
+      for (int i = 0; i + j <= R.p; ++i, ++n) { out[2 * n] = -1.0 + 2.0 * i / R.p; out[2 * n + 1] = -1.0 + 2.0 * j / R.p; }
+    return;
+  }
+  const int n1 = R.p + 1;
+  const double* xn = R.blob.data() + 2 * R.nq * n1 + 2 * R.nq + 2 * n1 * n1;
+  for (int n = 0; n < R.npe; ++n) {
+    int id[3] = {n % n1, (n / n1) % n1, n / (n1 * n1)};
+    for (int d = 0; d < R.dim; ++d) out[n * R.dim + d] = xn[id[d]];
+  }
+}
+
+void ref_face_point(const RefOps& R, int f, int k, double* xi) {
+  std::vector<double> gx, gw;
+  gauss_legendre(R.nq, gx, gw);
+  if (R.etype == E_TRI) {
+    static const double V[3][2] = {{-1, -1}, {1, -1}, {-1, 1}};
+    int a = f, b = (f + 1) % 3;
+    double s = gx[k];
+    for (int d = 0; d < 2; ++d) xi[d] = 0.5 * (1 - s) * V[a][d] + 0.5 * (1 + s) * V[b][d];
+    return;
+  }
+  int ax = f >> 1, side = f & 1, m = 0;
+  int kk[2] = {k % R.nq, k / R.nq};
+  for (int d = 0; d < R.dim; ++d) xi[d] = (d == ax) ? (side ? 1.0 : -1.0) : gx[kk[m++]];
+}
+
+namespace {
+// local vertex ids of each face, ordered so that vertex 0 -> 1 follows the face parameter
+const std::vector<std::vector<int>>& face_vertices(int etype) {
+  static const std::vector<std::vector<int>> tri = {{0, 1}, {1, 2}, {2, 0}};
+  static const std::vector<std::vector<int>> quad = {{0, 2}, {1, 3}, {0, 1}, {2, 3}};
+  static const std::vector<std::vector<int>> hex = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5},
+                                                    {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
+  return etype == E_TRI ? tri : (etype == E_QUAD ? quad : hex);
+}
+}  // namespace
+
+bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* vid, MeshPrep& out, std::string& err) {
+  const int dim = R.dim, nf = R.nf;
+  const int nv = R.etype == E_TRI ? 3 : (1 << dim);
+  const int GEO = dim * dim + 1 + dim + dim * dim + nf * (dim + 1);
+  out.E = E;
+  out.geo.assign((size_t)E * GEO, 0.0);
+  out.nbr.assign((size_t)E * nf, -1);
+  out.nbf.assign((size_t)E * nf, 0);
+  const int axis_vert[3] = {1, 2, 4};
+  // Reference outward normals and the length factor |d xi / d s| of each face parameter.
+  auto ref_normal = [&](int f, double* N, double& ds) {
+    for (int d = 0; d < 3; ++d) N[d] = 0.0;
+    ds = 1.0;
+    if (R.etype == E_TRI) {
+      if (f == 0) N[1] = -1.0;
+      else if (f == 1) { N[0] = N[1] = 1.0 / std::sqrt(2.0); ds = std::sqrt(2.0); }
+      else N[0] = -1.0;
+    } else {
+      N[f >> 1] = (f & 1) ? 1.0 : -1.0;
+    }
+  };
+  std::vector<double> J(9), Ji(9);
+  for (int64_t e = 0; e < E; ++e) {
+    const double* X = xyz + (size_t)e * nv * dim;
+    // J[d][k] = (x_{axis vertex k} - x_0)_d / 2
+    for (int d = 0; d < dim; ++d)
+      for (int k = 0; k < dim; ++k) J[d * dim + k] = 0.5 * (X[axis_vert[k] * dim + d] - X[d]);
+    if (R.etype != E_TRI) {
+      for (int vtx = 0; vtx < nv; ++vtx)
+        for (int d = 0; d < dim; ++d) {
+          double pr = X[d];
+          for (int k = 0; k < dim; ++k) if ((vtx >> k) & 1) pr += 2.0 * J[d * dim + k];
+          if (std::fabs(pr - X[vtx * dim + d]) > 1e-10 * (1.0 + std::fabs(pr))) {
+            err = "element " + std::to_string(e) + " is not affine (parallelogram/parallelepiped)";
+            return false;
+          }
+        }
+    }
+    double det;
+    if (dim == 2) {
+      det = J[0] * J[3] - J[1] * J[2];
+      Ji[0] = J[3] / det; Ji[1] = -J[1] / det; Ji[2] = -J[2] / det; Ji[3] = J[0] / det;
+    } else {
+      det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
+      Ji[0] = (J[4] * J[8] - J[5] * J[7]) / det; Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det; Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+      Ji[3] = (J[5] * J[6] - J[3] * J[8]) / det; Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det; Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+      Ji[6] = (J[3] * J[7] - J[4] * J[6]) / det; Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det; Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+    }
+    if (!(det > 0.0)) { err = "element " + std::to_string(e) + " has non-positive Jacobian"; return false; }
+    double* g = &out.geo[(size_t)e * GEO];
+    for (int i = 0; i < dim * dim; ++i) g[i] = Ji[i];
+    g[dim * dim] = det;
+    // x(xi) = x_0 + J (xi + 1)  =>  x(0) = x_0 + J 1
+    for (int d = 0; d < dim; ++d) {
+      double s = X[d];
+      for (int k = 0; k < dim; ++k) s += J[d * dim + k];
+      g[dim * dim + 1 + d] = s;
+    }
+    for (int i = 0; i < dim * dim; ++i) g[dim * dim + 1 + dim + i] = J[i];
+    // Nanson: n dS = det J J^{-T} N dS_ref
+    for (int f = 0; f < nf; ++f) {
+      double N[3], ds;
+      ref_normal(f, N, ds);
+      double m[3] = {0, 0, 0}, len = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        for (int k = 0; k < dim; ++k) m[d] += Ji[k * dim + d] * N[k];
+        len += m[d] * m[d];
+      }
+      len = std::sqrt(len);
+      double* fr = g + 2 * dim * dim + 1 + dim + f * (dim + 1);
+      for (int d = 0; d < dim; ++d) fr[d] = m[d] / len;
+      fr[dim] = det * len * ds;
+    }
+  }
+  // connectivity by the sorted vertex ids of each face
+  const auto& FV = face_vertices(R.etype);
+  struct Key { int64_t v[4]; bool operator==(const Key& o) const { return v[0] == o.v[0] && v[1] == o.v[1] && v[2] == o.v[2] && v[3] == o.v[3]; } };
+  struct KH { size_t operator()(const Key& k) const { size_t h = 1469598103934665603ull; for (int i = 0; i < 4; ++i) { h ^= (size_t)k.v[i] + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2); } return h; } };
+  std::unordered_map<Key, int64_t, KH> open;
+  open.reserve((size_t)E * nf);
+  std::vector<int64_t> partner((size_t)E * nf, -1);
+  for (int64_t e = 0; e < E; ++e)
+    for (int f = 0; f < nf; ++f) {
+      Key k = {{-1, -1, -1, -1}};
+      for (size_t i = 0; i < FV[f].size(); ++i) k.v[i] = vid[e * nv + FV[f][i]];
+      std::sort(k.v, k.v + FV[f].size());
+      auto it = open.find(k);
+      if (it == open.end()) open.emplace(k, e * nf + f);
+      else {
+        if (it->second < 0) { err = "a face is shared by more than two elements"; return false; }
+        partner[e * nf + f] = it->second;
+        partner[it->second] = e * nf + f;
+        it->second = -2;
+      }
+    }
+  // face-point coordinates and orientation permutations
+  std::map<std::vector<unsigned char>, int> codes;
+  std::vector<double> xs(R.nfq * 3), xt(R.nfq * 3);
+  std::vector<double> fref((size_t)nf * R.nfq * 3, 0.0);   // reference face points, computed once
+  for (int f = 0; f < nf; ++f)
+    for (int k = 0; k < R.nfq; ++k) ref_face_point(R, f, k, &fref[((size_t)f * R.nfq + k) * 3]);
+  auto face_pts = [&](int64_t e, int f, double* P, const double* shift) {
+    const double* g = &out.geo[(size_t)e * GEO];
+    for (int k = 0; k < R.nfq; ++k) {
+      const double* xi = &fref[((size_t)f * R.nfq + k) * 3];
+      for (int d = 0; d < dim; ++d) {
+        double s = g[dim * dim + 1 + d];
+        for (int kk = 0; kk < dim; ++kk) s += g[dim * dim + 1 + dim + d * dim + kk] * xi[kk];
+        P[k * 3 + d] = s + (shift ? shift[d] : 0.0);
+      }
+    }
+  };
+  int nb_faces = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    const double* X = xyz + (size_t)e * nv * dim;
+    for (int f = 0; f < nf; ++f) {
+      int64_t pf = partner[e * nf + f];
+      if (pf < 0) { ++nb_faces; continue; }
+      int64_t e2 = pf / nf;
+      int f2 = (int)(pf % nf);
+      const double* X2 = xyz + (size_t)e2 * nv * dim;
+      // periodic shift: centroid of this face minus centroid of the partner face
+      double shift[3] = {0, 0, 0};
+      for (int d = 0; d < dim; ++d) {
+        double a = 0, b = 0;
+        for (int vv : FV[f]) a += X[vv * dim + d];
+        for (int vv : FV[f2]) b += X2[vv * dim + d];
+        shift[d] = (a - b) / FV[f].size();
+      }
+      face_pts(e, f, xs.data(), nullptr);
+      face_pts(e2, f2, xt.data(), shift);
+      std::vector<unsigned char> pm(R.nfq);
+      double hscale = 0.0;
+      for (int d = 0; d < dim; ++d) hscale = std::max(hscale, std::fabs(out.geo[(size_t)e * GEO + dim * dim + 1 + dim + d * dim]));
+      for (int k = 0; k < R.nfq; ++k) {
+        int best = -1;
+        double bd = 1e300;
+        for (int k2 = 0; k2 < R.nfq; ++k2) {
+          double dd = 0;
+          for (int d = 0; d < dim; ++d) dd += (xs[k * 3 + d] - xt[k2 * 3 + d]) * (xs[k * 3 + d] - xt[k2 * 3 + d]);
+          if (dd < bd) { bd = dd; best = k2; }
+        }
+        if (std::sqrt(bd) > 1e-8 * (1.0 + hscale)) { err = "non-conforming face points"; return false; }
+        pm[k] = (unsigned char)best;
+      }
+      auto it = codes.find(pm);
+      int code;
+      if (it == codes.end()) { code = (int)codes.size(); codes.emplace(pm, code); }
+      else code = it->second;
+      if (code > 31) { err = "too many face orientations"; return false; }
+      out.nbr[e * nf + f] = (int)e2;
+      out.nbf[e * nf + f] = (unsigned char)(f2 | (code << 3));
+    }
+  }
+  out.n_orient = (int)codes.size();
+  out.perm.assign((size_t)std::max(1, out.n_orient) * R.nfq, 0);
+  for (auto& kv : codes)
+    for (int k = 0; k < R.nfq; ++k) out.perm[kv.second * R.nfq + k] = kv.first[k];
+  out.n_boundary_faces = nb_faces;
+  return true;
+}
+
+}  // namespace ldg

@@ -1,0 +1,577 @@
+// Fused element-centric LDG stage kernels (Section 2.2, Eq. 1a-1b; Section 3.3).
+//
+// One CTA owns NE consecutive elements. Every stage is a loop of independent
+// items over the CTA's threads, separated by __syncthreads, on data staged in
+// shared memory. Each element evaluates both sides of its own faces (the
+// neighbour's face-node values are read from global memory, normally an L2 hit),
+// so no atomics are used and results are bitwise reproducible.
+//
+//   q-stage  : q_d = -d_d u_h + M^{-1} sum_f <(u- - uhat) n_d, phi>_f        (Eq. 1a)
+//              (the weak form integrated by parts once; exact because the
+//               quadrature integrates u d(phi) and the mass matrix exactly)
+//   residual : R = -(f(u,q), grad phi) + <fhat.n, phi> - (s, phi) + M (a0 u + h)
+//              with the BDF history h = (a1 u^n + a2 u^{n-1}) / dt          (Eq. 1b)
+//
+// MODE_R evaluates R(u); MODE_HOM the homogeneous linear part of a linear model
+// (R(v) - R(0): no source, zero boundary data), which is its exact J.v; MODE_JV
+// propagates dual numbers (u, v) through a nonlinear model and writes dR/du . v.
+#pragma once
+#include "ldg_device.cuh"
+
+namespace ldg {
+
+enum { MODE_R = 0, MODE_HOM = 1, MODE_JV = 2 };
+
+struct KArgs {
+  const void* u;              // [E][NCU][NPE]     state (R, JV) or direction (HOM)
+  const void* v;              // [E][NCU][NPE]     direction (JV)
+  const void* q;              // [E][NCU][DIM][NPE] q(u) (R) or q(v) (HOM), diffusion models
+  const void* hist;           // [E][NCU][NPE]     BDF history term, or null
+  void* out;                  // [E][NCU][NPE] residual / J.v, or [E][NCU][DIM][NPE] q
+  const double* geo;          // [E][GEO] per-element affine geometry
+  const int* nbr;             // [E][NF] neighbour element, -1 on the boundary
+  const unsigned char* nbf;   // [E][NF] neighbour's local face | (orientation code << 3)
+  const double* ops;          // reference operator blob (element traits)
+  const unsigned char* perm;  // [n_orient][NFQ] face-point permutations
+  double a0dt;                // a0 / dt of the BDF scheme, 0 when steady
+  double t;
+  ModelParams mp;
+  int E;
+};
+
+// Per-element geometry record: Jinv[k][d] = d xi_k / d x_d, detJ, x(0), J[d][k] = d x_d / d xi_k,
+// then for each face its unit outward normal and surface Jacobian.
+template <int DIM> struct Geo {
+  static constexpr int JINV = 0, DETJ = DIM * DIM, XM = DETJ + 1, JAC = XM + DIM, FACE = JAC + DIM * DIM;
+  static constexpr int size(int nf) { return FACE + nf * (DIM + 1); }
+};
+
+__host__ __device__ constexpr int al16(int b) { return (b + 15) & ~15; }
+
+// Calls fn(f, j) for every face f that contains local node n, with j the node's
+// index within that face. Written without dynamically indexed local arrays:
+// nvcc 13.0 at -O3 mis-assigned the face ids of an earlier array-based form
+// (correct at -G), so the enumeration is an unrolled loop of direct calls.
+template <class EL, class F> __device__ __forceinline__ void for_node_faces(int n, F&& fn) {
+  if constexpr (EL::TENSOR) {
+    constexpr int N1 = EL::N1;
+    const int i0 = n % N1, i1 = (n / N1) % N1, i2 = n / (N1 * N1);
+    // axis 0: free axes (1, 2); axis 1: (0, 2); axis 2: (0, 1)
+    if (i0 == 0) fn(0, i1 + N1 * i2);
+    if (i0 == N1 - 1) fn(1, i1 + N1 * i2);
+    if (i1 == 0) fn(2, i0 + N1 * i2);
+    if (i1 == N1 - 1) fn(3, i0 + N1 * i2);
+    if constexpr (EL::DIM == 3) {
+      if (i2 == 0) fn(4, i0 + N1 * i1);
+      if (i2 == N1 - 1) fn(5, i0 + N1 * i1);
+    }
+  } else {
+    constexpr int P = EL::P;
+    int j = 0, rem = n;
+    while (rem > P - j) { rem -= P + 1 - j; ++j; }
+    const int i = rem;
+    if (j == 0) fn(0, i);
+    if (i + j == P) fn(1, j);
+    if (i == 0) fn(2, P - j);
+  }
+}
+
+// Reference coordinates of face point k on face f.
+template <class EL> __device__ __forceinline__ void face_xi(const double* ops, int f, int k, double* xi) {
+  if constexpr (EL::TENSOR) {
+    const double* XQ = ops + EL::OXQ;
+    const int ax = f >> 1;
+    const double fix = (f & 1) ? 1.0 : -1.0;
+    if constexpr (EL::DIM == 2) {
+      xi[ax] = fix;
+      xi[1 - ax] = XQ[k];
+    } else {
+      // free axes in ascending order, the first one fastest
+      const double s0 = XQ[k % EL::NQ], s1 = XQ[k / EL::NQ];
+      if (ax == 0) { xi[0] = fix; xi[1] = s0; xi[2] = s1; }
+      else if (ax == 1) { xi[0] = s0; xi[1] = fix; xi[2] = s1; }
+      else { xi[0] = s0; xi[1] = s1; xi[2] = fix; }
+    }
+  } else {
+    const double V[3][2] = {{-1.0, -1.0}, {1.0, -1.0}, {-1.0, 1.0}};
+    int a = f, b = (f + 1) % 3;
+    double s = ops[EL::OSF + k];
+    xi[0] = 0.5 * (1.0 - s) * V[a][0] + 0.5 * (1.0 + s) * V[b][0];
+    xi[1] = 0.5 * (1.0 - s) * V[a][1] + 0.5 * (1.0 + s) * V[b][1];
+  }
+}
+template <class EL> __device__ __forceinline__ double face_w(const double* ops, int k) {
+  if constexpr (EL::TENSOR) {
+    const double* W = ops + EL::OW;
+    return EL::DIM == 2 ? W[k] : W[k % EL::NQ] * W[k / EL::NQ];
+  } else {
+    return ops[EL::OWF + k];
+  }
+}
+template <class EL> __device__ __forceinline__ void vol_xi(const double* ops, int q, double* xi, double& w) {
+  if constexpr (EL::TENSOR) {
+    const double* XQ = ops + EL::OXQ;
+    const double* W = ops + EL::OW;
+    int i0 = q % EL::NQ, i1 = (q / EL::NQ) % EL::NQ, i2 = q / (EL::NQ * EL::NQ);
+    xi[0] = XQ[i0]; xi[1] = XQ[i1];
+    w = W[i0] * W[i1];
+    if (EL::DIM == 3) { xi[2] = XQ[i2]; w *= W[i2]; }
+  } else {
+    xi[0] = ops[EL::OXQ + 2 * q];
+    xi[1] = ops[EL::OXQ + 2 * q + 1];
+    w = ops[EL::OWV + q];
+  }
+}
+
+template <int DIM> __device__ __forceinline__ void phys_x(const double* g, const double* xi, double* x) {
+  for (int d = 0; d < DIM; ++d) {
+    double s = g[Geo<DIM>::XM + d];
+    for (int k = 0; k < DIM; ++k) s += g[Geo<DIM>::JAC + d * DIM + k] * xi[k];
+    x[d] = s;
+  }
+}
+
+// ---------------------------------------------- reference operators on batches
+// face-node values [nb][NFN] -> face-point values [nb][NFQ]; tmp holds [nb][NQ*N1]
+template <class EL, class T> __device__ __forceinline__ void face_trace(const T* in, T* out, T* tmp, const double* ops, int nb) {
+  if constexpr (EL::TENSOR) {
+    const double* B = ops + EL::OB;
+    if constexpr (EL::DIM == 2) {
+      contract<0, EL::N1, 1, 1, EL::NQ, false, false>(in, out, B, nb);
+    } else {
+      contract<0, EL::N1, EL::N1, 1, EL::NQ, false, false>(in, tmp, B, nb);
+      __syncthreads();
+      contract<1, EL::NQ, EL::N1, 1, EL::NQ, false, false>(tmp, out, B, nb);
+    }
+  } else {
+    matvec<EL::NFQ, EL::NFN, false, false>(in, out, ops + EL::OBF, nb);
+  }
+}
+// face-point values [nb][NFQ] -> face-node moments [nb][NFN] (transpose of face_trace)
+template <class EL, class T> __device__ __forceinline__ void face_lift(const T* in, T* out, T* tmp, const double* ops, int nb) {
+  if constexpr (EL::TENSOR) {
+    const double* B = ops + EL::OB;
+    if constexpr (EL::DIM == 2) {
+      contract<0, EL::NQ, 1, 1, EL::N1, true, false>(in, out, B, nb);
+    } else {
+      contract<0, EL::NQ, EL::NQ, 1, EL::N1, true, false>(in, tmp, B, nb);
+      __syncthreads();
+      contract<1, EL::N1, EL::NQ, 1, EL::N1, true, false>(tmp, out, B, nb);
+    }
+  } else {
+    matvec<EL::NFN, EL::NFQ, true, false>(in, out, ops + EL::OBF, nb);
+  }
+}
+// nodal [nb][NPE] -> volume points [nb][NQV]; t1, t2 hold [nb][max(NQ,N1)^DIM]
+template <class EL, class T> __device__ __forceinline__ void vol_interp(const T* in, T* out, T* t1, const double* ops, int nb) {
+  if constexpr (EL::TENSOR) {
+    constexpr int N1 = EL::N1, NQ = EL::NQ;
+    const double* B = ops + EL::OB;
+    if constexpr (EL::DIM == 2) {
+      contract<0, N1, N1, 1, NQ, false, false>(in, t1, B, nb);
+      __syncthreads();
+      contract<1, NQ, N1, 1, NQ, false, false>(t1, out, B, nb);
+    } else {
+      contract<0, N1, N1, N1, NQ, false, false>(in, out, B, nb);
+      __syncthreads();
+      contract<1, NQ, N1, N1, NQ, false, false>(out, t1, B, nb);
+      __syncthreads();
+      contract<2, NQ, NQ, N1, NQ, false, false>(t1, out, B, nb);
+    }
+  } else {
+    matvec<EL::NQV, EL::NPE, false, false>(in, out, ops + EL::OB, nb);
+  }
+}
+// out[nb][NPE] (+)= sum over volume points of Op_k^T in_k: k < DIM uses the
+// reference derivative along axis k, k == DIM the plain basis (both transposed).
+template <class EL, bool ACC, class T>
+__device__ __forceinline__ void vol_integrate(int k, const T* in, T* out, T* t1, T* t2, const double* ops, int nb) {
+  if constexpr (EL::TENSOR) {
+    constexpr int N1 = EL::N1, NQ = EL::NQ;
+    const double* B = ops + EL::OB;
+    const double* D = ops + EL::OD;
+    if constexpr (EL::DIM == 2) {
+      contract<0, NQ, NQ, 1, N1, true, false>(in, t1, k == 0 ? D : B, nb);
+      __syncthreads();
+      contract<1, N1, NQ, 1, N1, true, ACC>(t1, out, k == 1 ? D : B, nb);
+    } else {
+      contract<0, NQ, NQ, NQ, N1, true, false>(in, t1, k == 0 ? D : B, nb);
+      __syncthreads();
+      contract<1, N1, NQ, NQ, N1, true, false>(t1, t2, k == 1 ? D : B, nb);
+      __syncthreads();
+      contract<2, N1, N1, NQ, N1, true, ACC>(t2, out, k == 2 ? D : B, nb);
+    }
+  } else {
+    const double* M = ops + (k == 0 ? EL::ODR : (k == 1 ? EL::ODS : EL::OB));
+    matvec<EL::NPE, EL::NQV, true, ACC>(in, out, M, nb);
+  }
+}
+// reference derivative along axis k at the nodes (collocation): [nb][NPE] -> [nb][NPE]
+template <class EL, class T> __device__ __forceinline__ void nodal_deriv(int k, const T* in, T* out, const double* ops, int nb) {
+  if constexpr (EL::TENSOR) {
+    constexpr int N1 = EL::N1;
+    const double* Dn = ops + EL::ODN;
+    if constexpr (EL::DIM == 2) {
+      if (k == 0) contract<0, N1, N1, 1, N1, false, false>(in, out, Dn, nb);
+      else contract<1, N1, N1, 1, N1, false, false>(in, out, Dn, nb);
+    } else {
+      if (k == 0) contract<0, N1, N1, N1, N1, false, false>(in, out, Dn, nb);
+      else if (k == 1) contract<1, N1, N1, N1, N1, false, false>(in, out, Dn, nb);
+      else contract<2, N1, N1, N1, N1, false, false>(in, out, Dn, nb);
+    }
+  } else {
+    matvec<EL::NPE, EL::NPE, false, false>(in, out, ops + (k == 0 ? EL::ODNR : EL::ODNS), nb);
+  }
+}
+// reference mass inverse: [nb][NPE] -> [nb][NPE] (in is overwritten for tensor elements)
+template <class EL, class T> __device__ __forceinline__ void mass_inv(T* in, T* out, const double* ops, int nb) {
+  if constexpr (EL::TENSOR) {
+    constexpr int N1 = EL::N1;
+    const double* Mi = ops + EL::OMI;
+    if constexpr (EL::DIM == 2) {
+      contract<0, N1, N1, 1, N1, false, false>(in, out, Mi, nb);
+      __syncthreads();
+      contract<1, N1, N1, 1, N1, false, false>(out, in, Mi, nb);
+      __syncthreads();
+      for (int i = threadIdx.x; i < nb * EL::NPE; i += blockDim.x) out[i] = in[i];
+    } else {
+      contract<0, N1, N1, N1, N1, false, false>(in, out, Mi, nb);
+      __syncthreads();
+      contract<1, N1, N1, N1, N1, false, false>(out, in, Mi, nb);
+      __syncthreads();
+      contract<2, N1, N1, N1, N1, false, false>(in, out, Mi, nb);
+    }
+  } else {
+    matvec<EL::NPE, EL::NPE, false, false>(in, out, ops + EL::OMI, nb);
+  }
+}
+
+template <class EL> struct Sizes {
+  static constexpr int M = (EL::TENSOR ? ipow(EL::NQ > EL::N1 ? EL::NQ : EL::N1, EL::DIM) : (EL::NQV > EL::NPE ? EL::NQV : EL::NPE));
+  static constexpr int MF = EL::TENSOR ? EL::NQ * EL::N1 : 1;
+};
+
+// ===================================================================== q-stage
+template <class EL, class MD, class R> struct QLayout {
+  static constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF;
+  static constexpr int GEO = Geo<DIM>::size(NF);
+  // bytes per element of each array
+  static constexpr int B_GEO = al16(GEO * 8), B_U = al16(NCU * EL::NPE * sizeof(R)),
+                       B_LF = al16(NF * NCU * EL::NFN * sizeof(R));
+  static constexpr int B_FN = al16(NF * NCU * EL::NFN * sizeof(R)), B_FT = al16(NF * NCU * Sizes<EL>::MF * sizeof(R)),
+                       B_TR = al16(NF * NCU * EL::NFQ * sizeof(R));
+  static constexpr int PHASE_F = 2 * B_FN + 2 * B_TR + 2 * B_FT;   // FNm, FNp, TRm(->Fq), TRp, tmp, tmpL
+  static constexpr int B_V = al16(NCU * DIM * EL::NPE * sizeof(R));
+  static constexpr int PHASE_V = 3 * B_V;                           // grad, b, scratch
+  static constexpr int PER_ELEM = B_GEO + B_U + B_LF + (PHASE_F > PHASE_V ? PHASE_F : PHASE_V);
+  static constexpr int NE_ = (96 * 1024) / PER_ELEM;
+  static constexpr int NE = NE_ < 1 ? 1 : (NE_ > 16 ? 16 : NE_);
+  static constexpr int SMEM = NE * PER_ELEM;
+};
+
+template <class EL, class MD, int MODE, class R>
+__global__ void __launch_bounds__(256) k_qstage(KArgs a) {
+  typedef QLayout<EL, MD, R> L;
+  constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ;
+  constexpr int NE = L::NE, GEO = L::GEO;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int e0 = blockIdx.x * NE;
+  const int ne = min(NE, a.E - e0);
+  double* Gs = (double*)smem;
+  R* Us = (R*)(smem + NE * L::B_GEO);
+  R* LF = (R*)(smem + NE * (L::B_GEO + L::B_U));
+  unsigned char* arena = smem + NE * (L::B_GEO + L::B_U + L::B_LF);
+  const R* u = (const R*)a.u;
+
+  for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = a.geo[(size_t)e0 * GEO + i];
+  for (int i = threadIdx.x; i < NE * NCU * NPE; i += blockDim.x)
+    Us[i] = i < ne * NCU * NPE ? u[(size_t)e0 * NCU * NPE + i] : R(0);
+  __syncthreads();
+
+  // ---- faces: traces of u on both sides, (u- - uhat) weighted, lifted to face nodes
+  R* FNm = (R*)arena;
+  R* FNp = (R*)(arena + NE * L::B_FN);
+  R* TRm = (R*)(arena + NE * 2 * L::B_FN);
+  R* TRp = (R*)(arena + NE * (2 * L::B_FN + L::B_TR));
+  R* TMP = (R*)(arena + NE * (2 * L::B_FN + 2 * L::B_TR));
+  for (int it = threadIdx.x; it < NE * NF * NCU * NFN; it += blockDim.x) {
+    int j = it % NFN, c = (it / NFN) % NCU, f = (it / (NFN * NCU)) % NF, e = it / (NFN * NCU * NF);
+    R vm = R(0), vp = R(0);
+    if (e < ne) {
+      vm = Us[(e * NCU + c) * NPE + EL::face_node(f, j)];
+      int nb = a.nbr[(size_t)(e0 + e) * NF + f];
+      if (nb >= 0) {
+        int nf = a.nbf[(size_t)(e0 + e) * NF + f] & 7;
+        vp = u[((size_t)nb * NCU + c) * NPE + EL::face_node(nf, j)];
+      }
+    }
+    FNm[it] = vm;
+    FNp[it] = vp;
+  }
+  __syncthreads();
+  face_trace<EL>(FNm, TRm, TMP, a.ops, NE * NF * NCU);
+  __syncthreads();
+  face_trace<EL>(FNp, TRp, TMP, a.ops, NE * NF * NCU);
+  __syncthreads();
+  for (int it = threadIdx.x; it < NE * NF * NFQ; it += blockDim.x) {
+    int k = it % NFQ, f = (it / NFQ) % NF, e = it / (NFQ * NF);
+    if (e >= ne) {
+      for (int c = 0; c < NCU; ++c) TRm[((e * NF + f) * NCU + c) * NFQ + k] = R(0);
+      continue;
+    }
+    const double* g = Gs + e * GEO;
+    double w = face_w<EL>(a.ops, k) * g[Geo<DIM>::FACE + f * (DIM + 1) + DIM];
+    int nb = a.nbr[(size_t)(e0 + e) * NF + f];
+    double gb[4] = {0.0, 0.0, 0.0, 0.0};
+    int kp = k;
+    if (nb >= 0) {
+      int code = a.nbf[(size_t)(e0 + e) * NF + f] >> 3;
+      kp = a.perm[code * NFQ + k];
+    } else if (MODE == MODE_R) {
+      double xi[3], x[3];
+      face_xi<EL>(a.ops, f, k, xi);
+      phys_x<DIM>(g, xi, x);
+      exact_state<DIM>(a.mp, NCU, x, a.t, gb);
+    }
+    for (int c = 0; c < NCU; ++c) {
+      int base = ((e * NF + f) * NCU + c) * NFQ;
+      R um = TRm[base + k];
+      R uh = nb >= 0 ? (um + TRp[base + kp]) * R(0.5) : R(gb[c]);
+      // TRm is overwritten in place: only this thread reads entry (e,f,c,k)
+      TRm[base + k] = (um - uh) * R(w);
+    }
+  }
+  __syncthreads();
+  face_lift<EL>(TRm, LF, TMP, a.ops, NE * NF * NCU);
+  __syncthreads();
+
+  // ---- volume: q_d = -sum_k Jinv[k][d] D_k u + (1/detJ) M^{-1} sum_f n_d lift_f
+  R* GR = (R*)arena;                          // [DIM][NE][NCU][NPE]
+  R* BV = (R*)(arena + NE * L::B_V);          // [NE][NCU][DIM][NPE]
+  R* SC = (R*)(arena + 2 * NE * L::B_V);
+  for (int k = 0; k < DIM; ++k) nodal_deriv<EL>(k, Us, GR + k * NE * NCU * NPE, a.ops, NE * NCU);
+  for (int it = threadIdx.x; it < NE * NCU * DIM * NPE; it += blockDim.x) {
+    int n = it % NPE, d = (it / NPE) % DIM, c = (it / (NPE * DIM)) % NCU, e = it / (NPE * DIM * NCU);
+    R s = R(0);
+    if (e < ne) {
+      const double* g = Gs + e * GEO;
+      for_node_faces<EL>(n, [&](int f, int j) {
+        s += LF[((e * NF + f) * NCU + c) * NFN + j] * R(g[Geo<DIM>::FACE + f * (DIM + 1) + d]);
+      });
+    }
+    BV[it] = s;
+  }
+  __syncthreads();
+  mass_inv<EL>(BV, SC, a.ops, NE * NCU * DIM);
+  __syncthreads();
+  R* qo = (R*)a.out;
+  for (int it = threadIdx.x; it < ne * NCU * DIM * NPE; it += blockDim.x) {
+    int n = it % NPE, d = (it / NPE) % DIM, c = (it / (NPE * DIM)) % NCU, e = it / (NPE * DIM * NCU);
+    const double* g = Gs + e * GEO;
+    R s = SC[it] * R(1.0 / g[Geo<DIM>::DETJ]);
+    for (int k = 0; k < DIM; ++k) s -= GR[(k * NE * NCU + e * NCU + c) * NPE + n] * R(g[Geo<DIM>::JINV + k * DIM + d]);
+    qo[(size_t)e0 * NCU * DIM * NPE + it] = s;
+  }
+}
+
+// ==================================================================== residual
+template <class EL, class MD, int MODE, class R> struct RLayout {
+  typedef typename std::conditional<MODE == MODE_JV, Dual<R>, R>::type S;
+  static constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF;
+  static constexpr int NCV = NCU * (1 + (MD::HASQ ? DIM : 0));      // u and q fields
+  static constexpr int GEO = Geo<DIM>::size(NF);
+  static constexpr int B_GEO = al16(GEO * 8), B_X = al16(NCV * EL::NPE * sizeof(S)),
+                       B_LF = al16(NF * NCU * EL::NFN * sizeof(R));
+  // face phase
+  static constexpr int B_FN = al16(NF * NCV * EL::NFN * sizeof(S)), B_FT = al16(NF * NCV * Sizes<EL>::MF * sizeof(S)),
+                       B_TR = al16(NF * NCV * EL::NFQ * sizeof(S)), B_FH = al16(NF * NCU * EL::NFQ * sizeof(R));
+  static constexpr int PHASE_F = 2 * B_FN + 2 * B_TR + B_FT + B_FH;
+  // volume phase
+  static constexpr int B_XQ = al16(NCV * Sizes<EL>::M * sizeof(S)), B_T1 = al16(NCV * Sizes<EL>::M * sizeof(S)),
+                       B_H = al16(NCU * Sizes<EL>::M * sizeof(R)), B_G = al16(NCU * Sizes<EL>::M * sizeof(R));
+  static constexpr int PHASE_V = B_XQ + B_T1 + 2 * B_H /*hist nodal + at points*/ + (DIM + 1) * B_G + 2 * B_G /*t1,t2*/ + B_G /*Rv*/;
+  static constexpr int PER_ELEM = B_GEO + B_X + B_LF + (PHASE_F > PHASE_V ? PHASE_F : PHASE_V);
+  static constexpr int NE_ = (100 * 1024) / PER_ELEM;
+  static constexpr int NE = NE_ < 1 ? 1 : (NE_ > 16 ? 16 : NE_);
+  static constexpr int SMEM = NE * PER_ELEM;
+};
+
+template <class EL, class MD, int MODE, class R>
+__global__ void __launch_bounds__(256) k_residual(KArgs a) {
+  typedef RLayout<EL, MD, MODE, R> L;
+  typedef typename L::S S;
+  constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ, NQV = EL::NQV;
+  constexpr int NE = L::NE, GEO = L::GEO, NCV = L::NCV, M = Sizes<EL>::M;
+  constexpr bool HASQ = MD::HASQ;
+  static_assert(!(MODE == MODE_JV && HASQ), "dual-number J.v is for models without q");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int e0 = blockIdx.x * NE;
+  const int ne = min(NE, a.E - e0);
+  double* Gs = (double*)smem;
+  S* X = (S*)(smem + NE * L::B_GEO);                       // [NE][NCV][NPE]
+  R* LF = (R*)(smem + NE * (L::B_GEO + L::B_X));           // [NE][NF][NCU][NFN]
+  unsigned char* arena = smem + NE * (L::B_GEO + L::B_X + L::B_LF);
+  const R* u = (const R*)a.u;
+  const R* v = (const R*)a.v;
+  const R* q = (const R*)a.q;
+
+  for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = a.geo[(size_t)e0 * GEO + i];
+  for (int i = threadIdx.x; i < NE * NCV * NPE; i += blockDim.x) {
+    int n = i % NPE, fld = (i / NPE) % NCV, e = i / (NPE * NCV);
+    S val = S(R(0));
+    if (e < ne) {
+      if (fld < NCU) {
+        size_t gi = ((size_t)(e0 + e) * NCU + fld) * NPE + n;
+        if constexpr (MODE == MODE_JV) val = S(u[gi], v[gi]);
+        else val = S(u[gi]);
+      } else {
+        if constexpr (HASQ) val = S(q[((size_t)(e0 + e) * NCU * DIM + (fld - NCU)) * NPE + n]);
+      }
+    }
+    X[i] = val;
+  }
+  __syncthreads();
+
+  // ------------------------------------------------------------- face phase
+  {
+    S* FNm = (S*)arena;
+    S* FNp = (S*)(arena + NE * L::B_FN);
+    S* TRm = (S*)(arena + NE * 2 * L::B_FN);
+    S* TRp = (S*)(arena + NE * (2 * L::B_FN + L::B_TR));
+    S* TMP = (S*)(arena + NE * (2 * L::B_FN + 2 * L::B_TR));
+    R* FH = (R*)(arena + NE * (2 * L::B_FN + 2 * L::B_TR + L::B_FT));
+    for (int it = threadIdx.x; it < NE * NF * NCV * NFN; it += blockDim.x) {
+      int j = it % NFN, fld = (it / NFN) % NCV, f = (it / (NFN * NCV)) % NF, e = it / (NFN * NCV * NF);
+      S vm = S(R(0)), vp = S(R(0));
+      if (e < ne) {
+        vm = X[(e * NCV + fld) * NPE + EL::face_node(f, j)];
+        int nb = a.nbr[(size_t)(e0 + e) * NF + f];
+        if (nb >= 0) {
+          int nfc = a.nbf[(size_t)(e0 + e) * NF + f] & 7;
+          int nn = EL::face_node(nfc, j);
+          if (fld < NCU) {
+            size_t gi = ((size_t)nb * NCU + fld) * NPE + nn;
+            if constexpr (MODE == MODE_JV) vp = S(u[gi], v[gi]);
+            else vp = S(u[gi]);
+          } else {
+            if constexpr (HASQ) vp = S(q[((size_t)nb * NCU * DIM + (fld - NCU)) * NPE + nn]);
+          }
+        }
+      }
+      FNm[it] = vm;
+      FNp[it] = vp;
+    }
+    __syncthreads();
+    face_trace<EL>(FNm, TRm, TMP, a.ops, NE * NF * NCV);
+    __syncthreads();
+    face_trace<EL>(FNp, TRp, TMP, a.ops, NE * NF * NCV);
+    __syncthreads();
+    for (int it = threadIdx.x; it < NE * NF * NFQ; it += blockDim.x) {
+      int k = it % NFQ, f = (it / NFQ) % NF, e = it / (NFQ * NF);
+      if (e >= ne) {
+        for (int c = 0; c < NCU; ++c) FH[((e * NF + f) * NCU + c) * NFQ + k] = R(0);
+        continue;
+      }
+      const double* g = Gs + e * GEO;
+      const double* nrm = g + Geo<DIM>::FACE + f * (DIM + 1);
+      double w = face_w<EL>(a.ops, k) * nrm[DIM];
+      int nb = a.nbr[(size_t)(e0 + e) * NF + f];
+      S um[NCU], qm[NCU * DIM + 1], fh[NCU];
+      for (int fld = 0; fld < NCV; ++fld) {
+        S val = TRm[((e * NF + f) * NCV + fld) * NFQ + k];
+        if (fld < NCU) um[fld] = val; else qm[fld - NCU] = val;
+      }
+      if (nb >= 0) {
+        int kp = a.perm[(a.nbf[(size_t)(e0 + e) * NF + f] >> 3) * NFQ + k];
+        S up[NCU], qp[NCU * DIM + 1];
+        for (int fld = 0; fld < NCV; ++fld) {
+          S val = TRp[((e * NF + f) * NCV + fld) * NFQ + kp];
+          if (fld < NCU) up[fld] = val; else qp[fld - NCU] = val;
+        }
+        MD::fhat(um, up, qm, qp, nrm, fh, a.mp);
+      } else {
+        double gb[4] = {0.0, 0.0, 0.0, 0.0};
+        if (MODE != MODE_HOM) {
+          double xi[3], x[3];
+          face_xi<EL>(a.ops, f, k, xi);
+          phys_x<DIM>(g, xi, x);
+          exact_state<DIM>(a.mp, NCU, x, a.t, gb);
+        }
+        MD::fhat_bnd(um, qm, gb, nrm, fh, a.mp);
+      }
+      for (int c = 0; c < NCU; ++c) FH[((e * NF + f) * NCU + c) * NFQ + k] = outp(fh[c]) * R(w);
+    }
+    __syncthreads();
+    face_lift<EL>(FH, LF, (R*)TMP, a.ops, NE * NF * NCU);
+    __syncthreads();
+  }
+
+  // ----------------------------------------------------------- volume phase
+  S* XQ = (S*)arena;                                                   // [NE][NCV][NQV]
+  S* T1 = (S*)(arena + NE * L::B_XQ);
+  R* HN = (R*)(arena + NE * (L::B_XQ + L::B_T1));                      // [NE][NCU][NPE]
+  R* HQ = (R*)(arena + NE * (L::B_XQ + L::B_T1 + L::B_H));             // [NE][NCU][NQV]
+  R* GK = (R*)(arena + NE * (L::B_XQ + L::B_T1 + 2 * L::B_H));         // [DIM+1][NE][NCU][NQV]
+  R* R1 = GK + (DIM + 1) * NE * (L::B_G / sizeof(R));
+  R* R2 = R1 + NE * (L::B_G / sizeof(R));
+  R* RV = R2 + NE * (L::B_G / sizeof(R));                              // [NE][NCU][NPE]
+  constexpr int GSTR = L::B_G / sizeof(R);                             // per-element stride of GK slabs
+  (void)GSTR;
+  vol_interp<EL>(X, XQ, T1, a.ops, NE * NCV);
+  const bool hist = (MODE == MODE_R) && a.hist != nullptr;
+  if (hist) {
+    const R* h = (const R*)a.hist;
+    for (int i = threadIdx.x; i < NE * NCU * NPE; i += blockDim.x)
+      HN[i] = i < ne * NCU * NPE ? h[(size_t)e0 * NCU * NPE + i] : R(0);
+    __syncthreads();
+    vol_interp<EL>(HN, HQ, (R*)T1 + 0, a.ops, NE * NCU);
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < NE * NQV; it += blockDim.x) {
+    int qp = it % NQV, e = it / NQV;
+    S uq[NCU], qq[NCU * DIM + 1], f[NCU * DIM];
+    for (int fld = 0; fld < NCV; ++fld) {
+      S val = XQ[(e * NCV + fld) * NQV + qp];
+      if (fld < NCU) uq[fld] = val; else qq[fld - NCU] = val;
+    }
+    double xi[3], w;
+    vol_xi<EL>(a.ops, qp, xi, w);
+    const double* g = Gs + e * GEO;
+    double wj = w * g[Geo<DIM>::DETJ];
+    double src = 0.0;
+    if (MODE == MODE_R && e < ne && MD::KIND != M_EULER) {
+      double x[3];
+      phys_x<DIM>(g, xi, x);
+      src = source_term<DIM>(a.mp, MD::KIND == M_CONVDIFF, x);
+    }
+    MD::flux(uq, qq, f, a.mp);
+    for (int c = 0; c < NCU; ++c) {
+      for (int k = 0; k < DIM; ++k) {
+        R s = R(0);
+        for (int d = 0; d < DIM; ++d) s += outp(f[c * DIM + d]) * R(g[Geo<DIM>::JINV + k * DIM + d]);
+        GK[((k + 1) * NE * NCU + e * NCU + c) * NQV + qp] = (e < ne) ? -s * R(wj) : R(0);
+      }
+      R tt = outp(uq[c]) * R(a.a0dt);
+      if (hist) tt += HQ[(e * NCU + c) * NQV + qp];
+      GK[(e * NCU + c) * NQV + qp] = (e < ne) ? (tt - R(src)) * R(wj) : R(0);
+    }
+  }
+  __syncthreads();
+  // slab 0: time/source term with the plain basis; slabs 1..DIM: flux with derivative along k
+  vol_integrate<EL, false>(DIM, GK, RV, R1, R2, a.ops, NE * NCU);
+  __syncthreads();
+  for (int k = 0; k < DIM; ++k) {
+    vol_integrate<EL, true>(k, GK + (k + 1) * NE * NCU * NQV, RV, R1, R2, a.ops, NE * NCU);
+    __syncthreads();
+  }
+  // ---- gather face moments and store
+  R* out = (R*)a.out;
+  for (int it = threadIdx.x; it < ne * NCU * NPE; it += blockDim.x) {
+    int n = it % NPE, c = (it / NPE) % NCU, e = it / (NPE * NCU);
+    R s = RV[it];
+    for_node_faces<EL>(n, [&](int f, int j) { s += LF[((e * NF + f) * NCU + c) * NFN + j]; });
+    out[(size_t)e0 * NCU * NPE + it] = s;
+  }
+}
+
+}  // namespace ldg

@@ -1,0 +1,196 @@
+"""Python binding of the C-ABI in ``include/ldg.h`` (argument marshalling only).
+
+Every computation runs in ``libldg.so``'s CUDA kernels; PyTorch only supplies
+device memory and the stream. There is no CPU fallback: constructing a context
+without the compiled library or without a CUDA device raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libldg.so")
+
+TRI, QUAD, HEX = 0, 1, 2
+POISSON, CONVDIFF, EULER = 0, 1, 2
+CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST = range(7)
+STEADY, BDF1, BDF2 = 0, 1, 2
+STATUS = {0: "LDG_OK", -1: "LDG_ERR_ARG", -2: "LDG_ERR_CUDA", -3: "LDG_ERR_UNSUPPORTED",
+          -4: "LDG_ERR_NONFINITE", -5: "LDG_ERR_MAXIT", -6: "LDG_ERR_MESH"}
+
+
+class LDGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("elem_type", ctypes.c_int), ("n_elem", ctypes.c_int64),
+                ("xyz", ctypes.POINTER(ctypes.c_double)), ("vid", ctypes.POINTER(ctypes.c_int64))]
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("case_id", ctypes.c_int), ("n_mu", ctypes.c_int),
+                ("mu", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("nq1", ctypes.c_int), ("gmres_m", ctypes.c_int), ("max_restarts", ctypes.c_int),
+                ("max_newton", ctypes.c_int), ("newton_rtol", ctypes.c_double), ("gmres_rtol", ctypes.c_double)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("gmres_iters", ctypes.c_int), ("jv_calls", ctypes.c_int),
+                ("residual_calls", ctypes.c_int), ("r0", ctypes.c_double), ("rfinal", ctypes.c_double),
+                ("lin_resid", ctypes.c_double), ("elapsed_ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Loads ``libldg.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2205_07824_b300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64p, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p
+        L.ldg_version.restype = ctypes.c_char_p
+        L.ldg_last_error.restype = ctypes.c_char_p
+        L.ldg_last_error.argtypes = [vp]
+        L.ldg_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Mesh), ctypes.c_int, ctypes.POINTER(_Model),
+                                 ctypes.POINTER(_Options), vp]
+        L.ldg_destroy.argtypes = [vp]
+        L.ldg_set_stream.argtypes = [vp, vp]
+        L.ldg_sizes.argtypes = [vp, i64p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int)]
+        L.ldg_set_time.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.ldg_residual.argtypes = [vp, dp, dp]
+        L.ldg_jvp.argtypes = [vp, dp, dp, dp]
+        L.ldg_q.argtypes = [vp, dp, dp]
+        L.ldg_interpolate.argtypes = [vp, ctypes.c_double, dp]
+        L.ldg_gmres.argtypes = [vp, dp, dp, dp, ctypes.POINTER(SolveReport)]
+        L.ldg_newton_gmres.argtypes = [vp, dp, ctypes.POINTER(SolveReport)]
+        L.ldg_newton_gmres_host.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveReport)]
+        _lib = L
+    return _lib
+
+
+def _ptr(t, n, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name}: expected a contiguous float64 CUDA tensor")
+    if t.numel() < n:
+        raise ValueError(f"{name}: needs {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class LDG:
+    """One LDG operator (mesh, order p, model) resident on the current CUDA device."""
+
+    def __init__(self, mesh, p: int, model: int, case: int, mu=(), nq1: int = 0, gmres_m: int = 30,
+                 max_restarts: int = 50, max_newton: int = 20, newton_rtol: float = 1e-8,
+                 gmres_rtol: float = 1e-3, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("LDG needs a CUDA device (no CPU fallback)")
+        L = lib()
+        self._xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+        self._vid = np.ascontiguousarray(mesh.vid, dtype=np.int64)
+        self._mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float64).reshape(-1))
+        md = _Mesh(mesh.etype, mesh.n_elem, self._xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                   self._vid.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+        mo = _Model(model, case, len(self._mu),
+                    self._mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(self._mu) else None)
+        op = _Options(nq1, gmres_m, max_restarts, max_newton, newton_rtol, gmres_rtol)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = L.ldg_create(ctypes.byref(h), ctypes.byref(md), p, ctypes.byref(mo), ctypes.byref(op),
+                          ctypes.c_void_p(stream.cuda_stream))
+        self._h = h
+        if rc != 0:
+            msg = L.ldg_last_error(h).decode() if h.value else "invalid arguments"
+            L.ldg_destroy(h)
+            self._h = None
+            raise LDGError(rc, msg)
+        n, npe, ncu, dim = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        L.ldg_sizes(h, ctypes.byref(n), ctypes.byref(npe), ctypes.byref(ncu), ctypes.byref(dim))
+        self.n_dof, self.n_pe, self.n_cu, self.dim = n.value, npe.value, ncu.value, dim.value
+        self.n_elem, self.p, self.model = mesh.n_elem, p, model
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ldg_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LDGError(rc, lib().ldg_last_error(self._h).decode())
+
+    def empty(self, n=None):
+        import torch
+        return torch.empty(self.n_dof if n is None else n, dtype=torch.float64, device="cuda")
+
+    def set_time(self, scheme: int, t: float, dt: float = 1.0, un=None, unm1=None):
+        n = self.n_dof
+        self._check(lib().ldg_set_time(self._h, scheme, t, dt, _ptr(un, n, "un") if un is not None else None,
+                                       _ptr(unm1, n, "unm1") if unm1 is not None else None))
+
+    def residual(self, u, out=None):
+        out = self.empty() if out is None else out
+        self._check(lib().ldg_residual(self._h, _ptr(u, self.n_dof, "u"), _ptr(out, self.n_dof, "out")))
+        return out
+
+    def jvp(self, u, v, out=None):
+        out = self.empty() if out is None else out
+        n = self.n_dof
+        self._check(lib().ldg_jvp(self._h, _ptr(u, n, "u"), _ptr(v, n, "v"), _ptr(out, n, "out")))
+        return out
+
+    def q(self, u, out=None):
+        out = self.empty(self.n_dof * self.dim) if out is None else out
+        self._check(lib().ldg_q(self._h, _ptr(u, self.n_dof, "u"), _ptr(out, self.n_dof * self.dim, "out")))
+        return out
+
+    def interpolate(self, t: float = 0.0, out=None):
+        out = self.empty() if out is None else out
+        self._check(lib().ldg_interpolate(self._h, t, _ptr(out, self.n_dof, "out")))
+        return out
+
+    def gmres(self, u, b, x=None):
+        x = self.empty() if x is None else x
+        rep = SolveReport()
+        n = self.n_dof
+        rc = lib().ldg_gmres(self._h, _ptr(u, n, "u"), _ptr(b, n, "b"), _ptr(x, n, "x"), ctypes.byref(rep))
+        self._check(rc)
+        return x, rep.as_dict()
+
+    def newton_gmres(self, u, check=True):
+        rep = SolveReport()
+        rc = lib().ldg_newton_gmres(self._h, _ptr(u, self.n_dof, "u"), ctypes.byref(rep))
+        if check:
+            self._check(rc)
+        return rep.as_dict()
+
+    def newton_gmres_host(self, u: np.ndarray, check=True):
+        if u.dtype != np.float64 or not u.flags.c_contiguous or u.size < self.n_dof:
+            raise TypeError("u: expected a contiguous float64 numpy array of n_dof elements")
+        rep = SolveReport()
+        rc = lib().ldg_newton_gmres_host(self._h, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         ctypes.byref(rep))
+        if check:
+            self._check(rc)
+        return rep.as_dict()

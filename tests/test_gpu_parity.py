@@ -1,0 +1,196 @@
+"""Parity of the CUDA LDG kernels with the FP64 CPU oracle (Section 2.2, Eq. 1a-1b;
+Section 3.3), element by element, on seeded inputs. Sizes span several CTA tiles
+with a ragged last tile; meshes are sheared so that every geometric factor is
+exercised."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_07824_b300 import synth
+from gpu_util import SHEAR2, SHEAR3, assert_parity, cuda, host, pair, state
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_r_jv(mesh, p, model, case, seed=1):
+    o, g = pair(mesh, p, model, case)
+    u = state(o, mesh, seed)
+    v = synth.random_vector(o.ndof, seed + 100)
+    r = host(g.residual(cuda(u)))
+    assert_parity(r, o.residual(u), what="R")
+    jv = host(g.jvp(cuda(u), cuda(v)))
+    assert_parity(jv, o.jvp(u, v), what="J.v")
+    return o, g
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("model,case", [(oracle.POISSON, oracle.CASE_SINSIN), (oracle.CONVDIFF, oracle.CASE_EXPSIN)])
+def test_triangles(p, model, case):
+    _run_r_jv(synth.tri_square(7, affine=SHEAR2), p, model, case)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("model,case", [(oracle.POISSON, oracle.CASE_SINSIN), (oracle.CONVDIFF, oracle.CASE_EXPSIN)])
+def test_quads_dirichlet(p, model, case):
+    _run_r_jv(synth.quad_box((7, 5), affine=SHEAR2), p, model, case)
+
+
+def test_quads_periodic_convdiff():
+    _run_r_jv(synth.quad_box((6, 5), hi=(2.0, 1.5), periodic=(True, True), affine=SHEAR2), 2,
+              oracle.CONVDIFF, oracle.CASE_ZERO)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_euler_periodic(p):
+    mesh = synth.quad_box((7, 6), hi=(10.0, 10.0), periodic=(True, True), affine=SHEAR2)
+    _run_r_jv(mesh, p, oracle.EULER, oracle.CASE_VORTEX)
+
+
+def test_euler_far_field_boundary():
+    mesh = synth.quad_box((5, 4), hi=(10.0, 10.0))
+    _run_r_jv(mesh, 2, oracle.EULER, oracle.CASE_VORTEX)
+
+
+@pytest.mark.parametrize("p,n", [(1, (3, 4, 5)), (2, (3, 4, 5)), (3, (3, 3, 4)), (4, (3, 3, 3)), (5, (2, 2, 3)),
+                                 (6, (2, 2, 2))])
+def test_hexes_convdiff(p, n):
+    _run_r_jv(synth.hex_box(n, affine=SHEAR3), p, oracle.CONVDIFF, oracle.CASE_EXPSIN)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_hexes_poisson(p):
+    _run_r_jv(synth.hex_box((3, 4, 3), affine=SHEAR3), p, oracle.POISSON, oracle.CASE_SINSIN)
+
+
+@pytest.mark.parametrize("etype,p", [(0, 2), (1, 3), (2, 2)])
+def test_q_stage(etype, p):
+    mesh = {0: synth.tri_square(5, affine=SHEAR2), 1: synth.quad_box((5, 4), affine=SHEAR2),
+            2: synth.hex_box((3, 3, 2), affine=SHEAR3)}[etype]
+    o, g = pair(mesh, p, oracle.POISSON, oracle.CASE_SINSIN)
+    u = synth.random_vector(o.ndof, 7)
+    assert_parity(host(g.q(cuda(u))), o.q(u), what="q")
+
+
+def test_interpolation_matches_oracle():
+    mesh = synth.quad_box((6, 6), hi=(10.0, 10.0), periodic=(True, True))
+    o, g = pair(mesh, 3, oracle.EULER, oracle.CASE_VORTEX)
+    assert_parity(host(g.interpolate(0.3)), o.interpolate(0.3), what="interp")
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_bdf_time_terms(scheme):
+    mesh = synth.quad_box((5, 6), hi=(10.0, 10.0), periodic=(True, True), affine=SHEAR2)
+    o, g = pair(mesh, 2, oracle.EULER, oracle.CASE_VORTEX)
+    u, un, unm1 = (synth.random_euler_state(mesh.n_elem, o.npe, s) for s in (1, 2, 3))
+    v = synth.random_vector(o.ndof, 4)
+    o.set_time(scheme, 0.1, 0.05, un, unm1)
+    g.set_time(scheme, 0.1, 0.05, cuda(un), cuda(unm1))
+    assert_parity(host(g.residual(cuda(u))), o.residual(u), what="R bdf")
+    assert_parity(host(g.jvp(cuda(u), cuda(v))), o.jvp(u, v), what="Jv bdf")
+    mesh = synth.hex_box((3, 2, 2), affine=SHEAR3)
+    o, g = pair(mesh, 2, oracle.CONVDIFF, oracle.CASE_EXPSIN)
+    u, un, unm1 = (synth.random_vector(o.ndof, s) for s in (1, 2, 3))
+    o.set_time(scheme, 0.0, 0.1, un, unm1)
+    g.set_time(scheme, 0.0, 0.1, cuda(un), cuda(unm1))
+    assert_parity(host(g.residual(cuda(u))), o.residual(u), what="R bdf cd")
+    assert_parity(host(g.jvp(cuda(u), cuda(v[: o.ndof]))), o.jvp(u, v[: o.ndof]), what="Jv bdf cd")
+
+
+def test_bitwise_reproducible():
+    mesh = synth.quad_box((9, 7), hi=(10.0, 10.0), periodic=(True, True), affine=SHEAR2)
+    o, g = pair(mesh, 3, oracle.EULER, oracle.CASE_VORTEX)
+    u = cuda(state(o, mesh, 5))
+    v = cuda(synth.random_vector(o.ndof, 6))
+    a = host(g.jvp(u, v))
+    b = host(g.jvp(u, v))
+    assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------ full workloads
+def test_full_c1_poisson_triangles():
+    """2-D Poisson, p = 2 on 16 x 16 squares split into 512 triangles."""
+    _run_r_jv(synth.tri_square(16), 2, oracle.POISSON, oracle.CASE_SINSIN)
+
+
+def test_full_c2_euler_vortex_64x64_p3():
+    """Isentropic vortex, periodic [0,10]^2, 64 x 64 quadrilaterals, p = 3, BDF2 step."""
+    mesh = synth.quad_box(64, hi=(10.0, 10.0), periodic=(True, True))
+    o, g = pair(mesh, 3, oracle.EULER, oracle.CASE_VORTEX)
+    un = o.interpolate(0.0)
+    unm1 = o.interpolate(-0.05)
+    o.set_time(2, 0.05, 0.05, un, unm1)
+    g.set_time(2, 0.05, 0.05, cuda(un), cuda(unm1))
+    # a perturbed state: at the interpolated exact solution R is a near-cancellation
+    u = o.interpolate(0.05) + 1e-2 * synth.random_vector(o.ndof, 4)
+    v = synth.random_vector(o.ndof, 3)
+    assert_parity(host(g.residual(cuda(u))), o.residual(u), what="R c2")
+    assert_parity(host(g.jvp(cuda(u), cuda(v))), o.jvp(u, v), what="Jv c2")
+
+
+def test_full_c3_hex48_p4_sampled():
+    """3-D convection-diffusion on 48^3 hexahedra, p = 4 (13.8 M DOF): the kernel runs
+    on the full mesh; the oracle evaluates a sample of elements (corners, faces, interior)."""
+    n = 48
+    mesh = synth.hex_box(n)
+    o, g = pair(mesh, 4, oracle.CONVDIFF, oracle.CASE_EXPSIN, mu=(1e-2, 1e-2, 1.0, 0.5, 0.25), gmres_m=2)
+    u = synth.random_vector(o.ndof, 0)
+    v = synth.random_vector(o.ndof, 1)
+    rng = np.random.default_rng(0)
+    el = np.unique(np.concatenate([[0, n - 1, n * n - 1, mesh.n_elem - 1, mesh.n_elem // 2],
+                                   rng.integers(0, mesh.n_elem, 40)]))
+    npe = o.npe
+    r = host(g.residual(cuda(u))).reshape(-1, 1, npe)[el]
+    assert_parity(r, o.residual_some(u, el), what="R c3")
+    jv = host(g.jvp(cuda(u), cuda(v))).reshape(-1, 1, npe)[el]
+    assert_parity(jv, o.jvp_some(u, v, el), what="Jv c3")
+
+
+# ------------------------------------------------------------------- solvers
+def test_gmres_matches_oracle_solve():
+    mesh = synth.quad_box((6, 6), hi=(10.0, 10.0), periodic=(True, True), affine=SHEAR2)
+    o, g = pair(mesh, 2, oracle.EULER, oracle.CASE_VORTEX, gmres_rtol=1e-11, gmres_m=30, max_restarts=200)
+    u = o.interpolate(0.0)
+    o.set_time(1, 0.0, 0.2, u, u)
+    g.set_time(1, 0.0, 0.2, cuda(u), cuda(u))
+    b = synth.random_vector(o.ndof, 2)
+    x, rep = g.gmres(cuda(u), cuda(b))
+    x = host(x)
+    xo, its, rc, _ = o.gmres(u, b, m=30, rtol=1e-12, maxit=5000)
+    assert rc == 0
+    assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo), rep
+    assert rep["lin_resid"] <= 1e-11 * 1.01
+
+
+def test_newton_c1_one_step():
+    """Config c1: one Newton step from u = 0 with unpreconditioned GMRES to 1e-10."""
+    mesh = synth.tri_square(16)
+    o, g = pair(mesh, 2, oracle.POISSON, oracle.CASE_SINSIN, gmres_m=30, gmres_rtol=1e-10,
+                max_restarts=400, newton_rtol=1e-9, max_newton=1)
+    u = cuda(np.zeros(o.ndof))
+    rep = g.newton_gmres(u)
+    uo, rc, st = o.newton(np.zeros(o.ndof), m=200, newton_rtol=1e-9, gmres_rtol=1e-11, max_newton=3)
+    assert rep["newton_iters"] == 1 and rep["rfinal"] <= 1e-9 * rep["r0"]
+    ug = host(u)
+    assert np.linalg.norm(ug - uo) <= 1e-8 * np.linalg.norm(uo)
+    eu, _ = o.l2_error(ug)
+    euo, _ = o.l2_error(uo)
+    assert abs(eu - euo) <= 1e-6 * euo
+
+
+def test_newton_c2_bdf2_step_small():
+    """One BDF2 step of the vortex by Newton-GMRES to 1e-8 on a 16 x 16 mesh, p = 3."""
+    mesh = synth.quad_box(16, hi=(10.0, 10.0), periodic=(True, True))
+    o, g = pair(mesh, 3, oracle.EULER, oracle.CASE_VORTEX, newton_rtol=1e-8, gmres_rtol=1e-4)
+    dt = 0.05
+    un, unm1 = o.interpolate(0.0), o.interpolate(-dt)
+    o.set_time(2, dt, dt, un, unm1)
+    g.set_time(2, dt, dt, cuda(un), cuda(unm1))
+    u = cuda(un)
+    rep = g.newton_gmres(u)
+    assert rep["rfinal"] <= 1e-8 * rep["r0"]
+    uo, rc, st = o.newton(un.copy(), m=30, newton_rtol=1e-10, gmres_rtol=1e-6)
+    assert rc == 0
+    ug = host(u)
+    # both satisfy ||R|| <= 1e-8 ||R0||; the solutions agree to the solve tolerance
+    assert np.linalg.norm(ug - uo) <= 1e-7 * np.linalg.norm(uo)
+    assert np.linalg.norm(o.residual(ug)) <= 1.5e-8 * st["r0"]
