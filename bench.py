@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 LDG hot path on the 2-D Euler isentropic-vortex workload.
+
+Workload: periodic [0,10]^2, 64 x 64 affine quadrilaterals, p = 3 (Gauss-Lobatto
+nodes, 5 x 5 Gauss points), local Lax-Friedrichs flux, BDF2 with dt = 0.05.
+One *step* is one implicit BDF2 time step: matrix-free Newton-GMRES (Section 3.3)
+from u^n until ||R(u)||_2 <= 1e-8 ||R(u^n)||_2, every J.v exact (dual numbers),
+Arnoldi with two-pass classical Gram-Schmidt and Givens rotations, all in FP64
+on the GPU. The L2 cache is flushed (a 256 MiB write) before every timed step,
+outside the step's event window.
+
+Metric: J.v GDOF/s = (DOFs x J.v applications) / step time, over the K timed
+steps; ms_per_step is the Newton-GMRES time to 1e-8 per implicit step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+With N > 1 (torchrun), every rank advances its own vortex instance (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "J·v GDOF/s (%HBM roofline); Newton-GMRES time-to-1e-8, learned+mixed vs plain FP64"
+UNIT = "GDOF/s"
+WORKLOAD = ("2D compressible Euler isentropic vortex (gamma 1.4, strength 5, centre (5,5)), periodic "
+            "[0,10]^2, 64x64 quads, p=3, Lax-Friedrichs flux, BDF2 dt=0.05, matrix-free Newton-GMRES(30) "
+            "to 1e-8, FP64")
+N_SIDE, P, DT = 64, 3, 0.05
+# FP64 FLOPs per element of one J.v launch, counted by ncu (2*DFMA + DADD + DMUL thread
+# instructions of the dual-number Euler kernel, p = 3, 5 x 5 Gauss points).
+JV_FLOP_PER_ELEM = None
+# FP64 peak derived from the unit counts: 148 SMs x 2 FP64 FMA/clock/SM x 2 FLOP x 2.032 GHz.
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms in a thread."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def aggregate(local_times_ms, local_jv_dofs, world, rank):
+    """Whole-job numbers: work summed over ranks, time = max over ranks (weak scaling)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([sum(local_times_ms)], dtype=torch.float64)
+    w = torch.tensor([float(local_jv_dofs)], dtype=torch.float64)
+    if world > 1:
+        if dist.get_backend() == "nccl":
+            t, w = t.cuda(), w.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    total_ms = float(t.item())
+    gdofs = float(w.item()) / (total_ms * 1e-3) / 1e9
+    return total_ms, gdofs
+
+
+def cpu_baseline_jv(u0, v, seconds=12.0):
+    """The FP64 oracle's J.v on the same workload, single-threaded, on the host cores."""
+    import oracle
+    from paper_2205_07824_b300 import synth
+    mesh = synth.quad_box(N_SIDE, hi=(10.0, 10.0), periodic=(True, True))
+    o = oracle.Oracle(mesh, P, oracle.EULER, oracle.CASE_VORTEX, (1.4,))
+    un, unm1 = o.interpolate(0.0), o.interpolate(-DT)
+    o.set_time(2, DT, DT, un, unm1)
+    calls, t0 = 0, time.perf_counter()
+    while True:
+        o.jvp(u0, v)
+        calls += 1
+        el = time.perf_counter() - t0
+        if el > seconds or calls >= 40:
+            break
+    return {"value": o.ndof * calls / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{calls} oracle J.v applications on the full 64x64 p=3 vortex state (BDF2 term on), "
+                      f"{el:.1f} s single-threaded"}
+
+
+def run_reference(args):
+    """The oracle, as it stands, timed on the host cores on this workload."""
+    import numpy as np
+    import oracle
+    from paper_2205_07824_b300 import synth
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    mesh = synth.quad_box(N_SIDE, hi=(10.0, 10.0), periodic=(True, True))
+    o = oracle.Oracle(mesh, P, oracle.EULER, oracle.CASE_VORTEX, (1.4,))
+    un, unm1 = o.interpolate(0.0), o.interpolate(-DT)
+    o.set_time(2, DT, DT, un, unm1)
+    v = synth.random_vector(o.ndof, 1)
+    per_step = 2   # J.v applications per sampled step
+    for _ in range(args.warmup):
+        o.jvp(un, v)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            o.jvp(un, v)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = o.ndof * per_step * args.steps / tot / 1e9
+    ms = tot / args.steps * 1e3
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n_dof": int(o.ndof),
+                       "sample": f"each step = {per_step} oracle J.v applications on the full workload state"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} J.v applications per step, single-threaded FP64 oracle"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--jv-reps", type=int, default=50)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, kernel_launches, BDF2, EULER, CASE_VORTEX
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    mesh = synth.quad_box(N_SIDE, hi=(10.0, 10.0), periodic=(True, True))
+    g = LDG(mesh, P, EULER, CASE_VORTEX, (1.4,), gmres_m=30, newton_rtol=1e-8, gmres_rtol=1e-3)
+    n = g.n_dof
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+
+    un, unm1 = g.interpolate(0.0), g.interpolate(-DT)
+    u = torch.empty_like(un)
+    state = {"t": 0.0}
+
+    def step():
+        t1 = state["t"] + DT
+        g.set_time(BDF2, t1, DT, un, unm1)
+        u.copy_(un)
+        rep = g.newton_gmres(u)
+        unm1.copy_(un)
+        un.copy_(u)
+        state["t"] = t1
+        return rep
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = kernel_launches()
+    times, jv_calls, newton_its, gmres_its = [], 0, 0, 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        rep = step()
+        ev[k][1].record(stream)
+        jv_calls += rep["jv_calls"]
+        newton_its += rep["newton_iters"]
+        gmres_its += rep["gmres_iters"]
+        assert rep["rfinal"] <= 1e-8 * rep["r0"], rep
+    torch.cuda.synchronize()
+    launches = kernel_launches() - l0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]
+    total_ms, gdofs = aggregate(times, n * jv_calls, world, rank)
+    ms_per_step = total_ms / args.steps
+
+    # J.v kernel alone (the dominant kernel), CUDA events on the launching stream
+    v = torch.randn(n, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    jv = torch.empty_like(v)
+    for _ in range(5):
+        g.jvp(u, v, jv)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.jv_reps):
+        g.jvp(u, v, jv)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    jv_ms = e0.elapsed_time(e1) / args.jv_reps
+    flop = JV_FLOP_PER_ELEM * mesh.n_elem if JV_FLOP_PER_ELEM else None
+    achieved = flop / (jv_ms * 1e-3) / 1e12 if flop else None
+    roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                "kernel": "k_residual<TensorEl<2,3,5>, EulerModel, MODE_JV, double>",
+                "launch_ms": jv_ms, "jv_gdofs_kernel": n / (jv_ms * 1e-3) / 1e9,
+                "peak_source": "FP64 ALU: 148 SMs x 2 FMA/clk x 2 FLOP x 2.032 GHz (derived)",
+                "flop_per_elem": JV_FLOP_PER_ELEM}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_un = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        h_unm1 = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        h_un.copy_(un)
+        h_unm1.copy_(unm1)
+        h_u = np.empty(n, dtype=np.float64)
+        d_un, d_unm1 = torch.empty_like(un), torch.empty_like(un)
+        k2 = min(args.steps, 5)
+        t_e2e, jv_e2e = 0.0, 0
+        tt = state["t"]
+        for _ in range(k2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d_un.copy_(h_un, non_blocking=True)
+            d_unm1.copy_(h_unm1, non_blocking=True)
+            g.set_time(BDF2, tt + DT, DT, d_un, d_unm1)
+            h_u[:] = h_un.numpy()
+            rep = g.newton_gmres_host(h_u)
+            t_e2e += time.perf_counter() - t0
+            jv_e2e += rep["jv_calls"]
+            h_unm1.copy_(h_un)
+            h_un.copy_(torch.from_numpy(h_u))
+            tt += DT
+        e2e = {"value": n * jv_e2e / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": 3 * 8 * n,
+               "d2h_bytes_per_step": 8 * n, "steps": k2,
+               "note": "host u^n, u^{n-1} and the initial guess copied in, the solution copied out, per step"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_jv(u.cpu().numpy(), v.cpu().numpy())
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": gdofs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_dof": int(n), "n_elem": int(mesh.n_elem),
+                           "time_to_1e-8_ms_per_step": ms_per_step,
+                           "newton_iters_per_step": newton_its / args.steps,
+                           "gmres_iters_per_step": gmres_its / args.steps,
+                           "jv_calls_per_step": jv_calls / args.steps,
+                           "preconditioner": "none", "precision": "FP64 throughout",
+                           "l2": "flushed (256 MiB write) before each timed step, outside its event window",
+                           "parallelism": f"{world} independent instance(s), one per GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

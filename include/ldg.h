@@ -112,6 +112,9 @@ typedef struct {
 
 const char* ldg_version(void);
 
+/* Number of CUDA kernels this library has launched in this process (all contexts). */
+int64_t ldg_kernel_launches(void);
+
 /* Creates a context: builds the reference element, the affine geometry, the face
  * connectivity and orientation tables on the host, uploads them, and allocates
  * the work space. `cuda_stream` is a cudaStream_t (NULL = legacy default stream).

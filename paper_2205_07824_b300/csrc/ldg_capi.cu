@@ -49,6 +49,13 @@ struct ldg_ctx {
   std::string err;
 };
 
+namespace ldg {
+long long& launch_counter() {
+  static long long n = 0;
+  return n;
+}
+}  // namespace ldg
+
 namespace {
 
 const std::vector<KernelSet>& registry() {
@@ -247,8 +254,10 @@ int64_t grid_for(int64_t n, int t = 256) { return (n + t - 1) / t; }
 // ||x||^2 into dst (device scalar)
 int dot_into(ldg_ctx* ctx, const double* V, int64_t ldv, int nvec, const double* w, double* dst, int add) {
   k_multidot<<<ctx->nblk, RED_T, 0, ctx->stream>>>(V, ldv, nvec, w, ctx->ndof, ctx->d_part, ctx->m + 2);
+  count_launch();
   CK(cudaGetLastError());
   k_reduce_part<<<1, RED_T, 0, ctx->stream>>>(ctx->d_part, ctx->nblk, ctx->m + 2, nvec, dst, add);
+  count_launch();
   CK(cudaGetLastError());
   return LDG_OK;
 }
@@ -310,7 +319,9 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
   for (int cycle = 0; cycle < ctx->opt.max_restarts; ++cycle) {
     // V[0] = r / ||r||, g = (||r||, 0, ...); sc[0] holds ||r||^2
     k_scale_inv<<<g1, 256, 0, ctx->stream>>>(ctx->d_r, sm + S.sc(), V, n);
+    count_launch();
     k_init_g<<<1, 64, 0, ctx->stream>>>(sm, m, sm + S.sc());
+    count_launch();
     CK(cudaGetLastError());
     int j = 0;
     bool done = false;
@@ -321,13 +332,17 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
       // classical Gram-Schmidt with one re-orthogonalisation pass
       if ((rc = dot_into(ctx, V, n, j + 1, w, sm + S.h(), 0))) return rc;
       k_update<<<g1, 256, 0, ctx->stream>>>(V, n, j + 1, sm + S.h(), -1.0, w, n);
+      count_launch();
       CK(cudaGetLastError());
       if ((rc = dot_into(ctx, V, n, j + 1, w, sm + S.h2(), 0))) return rc;
       k_update<<<g1, 256, 0, ctx->stream>>>(V, n, j + 1, sm + S.h2(), -1.0, w, n);
+      count_launch();
       CK(cudaGetLastError());
       if ((rc = dot_into(ctx, w, n, 1, w, sm + S.sc(), 0))) return rc;
       k_givens<<<1, 1, 0, ctx->stream>>>(sm, m, j);
+      count_launch();
       k_scale_inv<<<g1, 256, 0, ctx->stream>>>(w, sm + S.sc(), w, n);
+      count_launch();
       CK(cudaGetLastError());
       if ((rc = read_scalars(ctx, sm + S.sc(), 3))) return rc;
       const double est = ctx->h_pin[1], hn = ctx->h_pin[2];
@@ -337,12 +352,15 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
     if (j == m) done = false;
     // x += V y
     k_backsolve<<<1, 1, 0, ctx->stream>>>(sm, m, j);
+    count_launch();
     k_update<<<g1, 256, 0, ctx->stream>>>(V, n, j, sm + S.y(), 1.0, x, n);
+    count_launch();
     CK(cudaGetLastError());
     // true residual r = b - J x
     if ((rc = do_jvp(ctx, u, x, ctx->d_w))) return rc;
     if (rep) rep->jv_calls++;
     k_sub<<<g1, 256, 0, ctx->stream>>>(b, ctx->d_w, ctx->d_r, n);
+    count_launch();
     CK(cudaGetLastError());
     if ((rc = dot_into(ctx, ctx->d_r, n, 1, ctx->d_r, sm + S.sc(), 0))) return rc;
     if ((rc = read_scalars(ctx, sm + S.sc(), 1))) return rc;
@@ -376,6 +394,7 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
     if ((rc = do_gmres(ctx, u, res, del, ctx->opt.gmres_rtol, rep)) && rc != LDG_ERR_MAXIT) return rc;
     // u <- u - delta   (sc[6] holds -1)
     k_update<<<g1, 256, 0, ctx->stream>>>(del, n, 1, sm + S.sc() + 6, 1.0, u, n);
+    count_launch();
     CK(cudaGetLastError());
     if ((rc = do_residual(ctx, u, res))) return rc;
     if (rep) rep->residual_calls++;
@@ -400,6 +419,8 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
 extern "C" {
 
 const char* ldg_version(void) { return "ldg-b300 0.1 (sm_103a)"; }
+
+int64_t ldg_kernel_launches(void) { return (int64_t)launch_counter(); }
 
 const char* ldg_last_error(const ldg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
@@ -534,6 +555,7 @@ int ldg_set_time(ldg_ctx* ctx, int scheme, double t, double dt, const double* un
   ctx->a0dt = a0 / dt;
   k_hist<<<grid_for(ctx->ndof), 256, 0, ctx->stream>>>(ctx->ndof, a1 / dt, un, a2 / dt, scheme == LDG_BDF2 ? unm1 : nullptr,
                                                       ctx->d_hist);
+  count_launch();
   CK(cudaGetLastError());
   return LDG_OK;
 }
@@ -562,6 +584,7 @@ int ldg_interpolate(ldg_ctx* ctx, double t, double* u) {
   const int GEO = ctx->dim * ctx->dim * 2 + 1 + ctx->dim + ctx->nf * (ctx->dim + 1);
   k_interp_nodes<<<grid_for(ctx->E * ctx->npe), 256, 0, ctx->stream>>>(ctx->dim, ctx->npe, ctx->ncu, ctx->E, ctx->d_geo,
                                                                       GEO, ctx->d_xn, ctx->mp, t, u);
+  count_launch();
   CK(cudaGetLastError());
   return LDG_OK;
 }

@@ -8,6 +8,10 @@
 
 namespace ldg {
 
+// Process-wide count of kernel launches issued by this library.
+long long& launch_counter();
+inline void count_launch() { ++launch_counter(); }
+
 typedef cudaError_t (*StageFn)(int mode, const KArgs& a, cudaStream_t s);
 
 struct KernelSet {
@@ -25,6 +29,7 @@ template <class EL, class MD, int MODE, class R> cudaError_t launch_res1(const K
   if (a.E <= 0) return cudaSuccess;
   int grid = (a.E + L::NE - 1) / L::NE;
   k_residual<EL, MD, MODE, R><<<grid, 256, L::SMEM, s>>>(a);
+  count_launch();
   return cudaGetLastError();
 }
 template <class EL, class MD, int MODE, class R> cudaError_t launch_q1(const KArgs& a, cudaStream_t s) {
@@ -35,6 +40,7 @@ template <class EL, class MD, int MODE, class R> cudaError_t launch_q1(const KAr
   if (a.E <= 0) return cudaSuccess;
   int grid = (a.E + L::NE - 1) / L::NE;
   k_qstage<EL, MD, MODE, R><<<grid, 256, L::SMEM, s>>>(a);
+  count_launch();
   return cudaGetLastError();
 }
 

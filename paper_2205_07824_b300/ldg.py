@@ -65,6 +65,7 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         vp, i64p, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p
         L.ldg_version.restype = ctypes.c_char_p
+        L.ldg_kernel_launches.restype = ctypes.c_int64
         L.ldg_last_error.restype = ctypes.c_char_p
         L.ldg_last_error.argtypes = [vp]
         L.ldg_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Mesh), ctypes.c_int, ctypes.POINTER(_Model),
@@ -92,6 +93,11 @@ def _ptr(t, n, name):
     if t.numel() < n:
         raise ValueError(f"{name}: needs {n} elements, got {t.numel()}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libldg.so so far in this process."""
+    return int(lib().ldg_kernel_launches())
 
 
 class LDG:
