@@ -160,6 +160,34 @@ int ldg_newton_gmres(ldg_ctx* ctx, double* u_dev, ldg_solve_report* rep);
 /* The same solve with u in HOST memory: copied to the device, solved, copied back. */
 int ldg_newton_gmres_host(ldg_ctx* ctx, double* u_host, ldg_solve_report* rep);
 
+/* J(u) v without any device allocation (the paper has no counterpart; this is a
+ * service for callers that cannot allocate). It computes the same product as
+ * ldg_jvp, but the one piece of scratch that product needs (q of the direction v
+ * for Poisson and convection-diffusion, n_dof * dim doubles) lives in a static
+ * device array inside this library instead of the context's work space.
+ *
+ * Who needs it: code that must not call cudaMalloc at this point, for example a
+ * CUDA stream being captured into a graph in global capture mode (where
+ * allocation is not permitted), or an application whose device memory is held
+ * entirely by its own pool or caching allocator. The call itself performs no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Limits and behaviour:
+ *  - The static array holds LDG_NOALLOC_SCRATCH_DOUBLES doubles (32 MiB). Every
+ *    device that loads this library keeps it for the life of the process.
+ *    An operator needing more returns LDG_ERR_ARG with a message naming both sizes.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture begins.
+ *  - All calls, from every context on a device, share the one array and the
+ *    array keeps the last call's contents. The kernels overwrite every entry
+ *    they read, so nothing needs clearing; but calls whose work overlaps on the
+ *    GPU (different streams, or different host threads) race on the array and
+ *    must be serialised by the caller.
+ *  - Euler (no q) needs no scratch; the call then runs the dual-number kernel alone. */
+#define LDG_NOALLOC_SCRATCH_DOUBLES 4194304
+int ldg_jvp_noalloc(ldg_ctx* ctx, const double* u_dev, const double* v_dev, double* jv_dev);
+
 const char* ldg_last_error(const ldg_ctx* ctx);
 
 #ifdef __cplusplus

@@ -69,6 +69,14 @@ const std::vector<KernelSet>& registry() {
   return reg;
 }
 
+// Static scratch of ldg_jvp_noalloc: q of the direction v for diffusion models.
+// Host code must not use `noalloc_scratch` as an address; the device address is
+// looked up once per device with cudaGetSymbolAddress.
+constexpr size_t kNoAllocScratchDoubles = (size_t)LDG_NOALLOC_SCRATCH_DOUBLES;
+__device__ __align__(256) double noalloc_scratch[kNoAllocScratchDoubles];
+constexpr int kMaxDevices = 64;
+double* noalloc_addr[kMaxDevices] = {nullptr};
+
 int fail(ldg_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -609,6 +617,39 @@ int ldg_newton_gmres(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
   int rc = do_newton(ctx, u, rep);
   rep->status = rc;
   return rc;
+}
+
+int ldg_jvp_noalloc(ldg_ctx* ctx, const double* u, const double* v, double* jv) {
+  if (!ctx || !ctx->ks || !u || !v || !jv) return LDG_ERR_ARG;
+  if (!ctx->ks->qstage) {
+    // convection models need no scratch: the dual-number kernel reads u, v and writes jv only
+    KArgs a = base_args(ctx);
+    a.u = u; a.v = v; a.out = jv;
+    CK(ctx->ks->residual(MODE_JV, a, ctx->stream));
+    return LDG_OK;
+  }
+  const size_t need = (size_t)ctx->ndof * ctx->dim;
+  if (need > kNoAllocScratchDoubles)
+    return fail(ctx, LDG_ERR_ARG, "ldg_jvp_noalloc: this operator needs " + std::to_string(need) +
+                                      " doubles of scratch (n_dof * dim), more than the static maximum of " +
+                                      std::to_string(kNoAllocScratchDoubles));
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(ctx, LDG_ERR_ARG, "ldg_jvp_noalloc: device ordinal out of range");
+  if (!noalloc_addr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, noalloc_scratch));
+    noalloc_addr[dev] = (double*)p;
+  }
+  double* dq = noalloc_addr[dev];
+  // q(v) of the homogeneous operator overwrites every entry it later reads: nothing to clear
+  KArgs a = base_args(ctx);
+  a.u = v; a.out = dq;
+  CK(ctx->ks->qstage(MODE_HOM, a, ctx->stream));
+  a = base_args(ctx);
+  a.u = v; a.q = dq; a.out = jv;
+  CK(ctx->ks->residual(MODE_HOM, a, ctx->stream));
+  return LDG_OK;
 }
 
 int ldg_newton_gmres_host(ldg_ctx* ctx, double* u_host, ldg_solve_report* rep) {

@@ -77,6 +77,7 @@ def lib():
         L.ldg_set_time.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
         L.ldg_residual.argtypes = [vp, dp, dp]
         L.ldg_jvp.argtypes = [vp, dp, dp, dp]
+        L.ldg_jvp_noalloc.argtypes = [vp, dp, dp, dp]
         L.ldg_q.argtypes = [vp, dp, dp]
         L.ldg_interpolate.argtypes = [vp, ctypes.c_double, dp]
         L.ldg_gmres.argtypes = [vp, dp, dp, dp, ctypes.POINTER(SolveReport)]
@@ -164,6 +165,12 @@ class LDG:
         out = self.empty() if out is None else out
         n = self.n_dof
         self._check(lib().ldg_jvp(self._h, _ptr(u, n, "u"), _ptr(v, n, "v"), _ptr(out, n, "out")))
+        return out
+
+    def jvp_noalloc(self, u, v, out):
+        """J.v through ldg_jvp_noalloc (static device scratch; no allocation in the call)."""
+        n = self.n_dof
+        self._check(lib().ldg_jvp_noalloc(self._h, _ptr(u, n, "u"), _ptr(v, n, "v"), _ptr(out, n, "out")))
         return out
 
     def q(self, u, out=None):
