@@ -96,7 +96,16 @@ typedef struct {
   int max_newton;       /* Newton iterations (default 20) */
   double newton_rtol;   /* stop when ||R(u_k)|| <= newton_rtol ||R(u_0)|| (default 1e-8) */
   double gmres_rtol;    /* linear solve: ||b - J x|| <= gmres_rtol ||b|| (default 1e-3) */
+  int krylov_precision; /* LDG_FP64 (default) or LDG_FP32: arithmetic of the J.v inside GMRES
+                           and of the preconditioner. Newton residuals, Arnoldi, Givens and all
+                           vectors stay FP64. */
+  int precond;          /* LDG_PC_NONE (default) or LDG_PC_BJACOBI (flexible right preconditioning) */
+  int pc_refresh;       /* rebuild the preconditioner every pc_refresh Newton iterations
+                           (0 = once per ldg_newton_gmres call, at the initial guess) */
 } ldg_options;
+
+enum { LDG_FP64 = 0, LDG_FP32 = 1 };
+enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1 };
 
 typedef struct {
   int newton_iters;
@@ -108,6 +117,7 @@ typedef struct {
   double lin_resid;     /* last linear solve: true relative residual */
   double elapsed_ms;
   int status;
+  int pc_setups;        /* preconditioner builds during the call */
 } ldg_solve_report;
 
 const char* ldg_version(void);
@@ -141,6 +151,23 @@ int ldg_residual(ldg_ctx* ctx, const double* u_dev, double* r_dev);
  * forward-mode dual numbers for nonlinear models, the homogeneous linear operator
  * for linear ones. */
 int ldg_jvp(ldg_ctx* ctx, const double* u_dev, const double* v_dev, double* jv_dev);
+
+/* J.v in a chosen arithmetic: LDG_FP64 (same as ldg_jvp) or LDG_FP32 (inputs and
+ * output FP64 in memory; every operation of the operator in FP32). */
+int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u_dev, const double* v_dev, double* jv_dev);
+
+/* Exact element-diagonal blocks of J(u): blocks_dev [n_elem][n_loc][n_loc], column-major
+ * per element (column l at offset l * n_loc), n_loc = n_cu * n_pe. Convection models use
+ * dual numbers with a unit tangent on each element and none on its neighbours; diffusion
+ * models use coloured probing (no two elements of one colour within two faces). Needed by
+ * the block-Jacobi preconditioner that accelerates GMRES (the paper's own preconditioner,
+ * Section 3.3, is a reduced-basis one; this is the plain baseline). */
+int ldg_diag_blocks(ldg_ctx* ctx, int precision, const double* u_dev, double* blocks_dev);
+
+/* Builds the block-Jacobi preconditioner M = blockdiag(J(u)) at state u (inverses held by
+ * the context), and applies y = M^{-1} x (device vectors, n_dof doubles). */
+int ldg_precond_setup(ldg_ctx* ctx, const double* u_dev);
+int ldg_precond_apply(ldg_ctx* ctx, const double* x_dev, double* y_dev);
 
 /* q of Eq. 1a for diffusion models: q_dev [n_elem][n_cu][dim][n_pe]. */
 int ldg_q(ldg_ctx* ctx, const double* u_dev, double* q_dev);

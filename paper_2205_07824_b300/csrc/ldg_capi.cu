@@ -11,6 +11,8 @@
 
 #include "../../include/ldg.h"
 #include "ldg_host.h"
+#include "ldg_krylov.cuh"
+#include "ldg_precond.cuh"
 #include "ldg_launch.cuh"
 
 using namespace ldg;
@@ -24,6 +26,7 @@ struct ldg_ctx {
   const KernelSet* ks = nullptr;
   // device data
   double* d_ops = nullptr;
+  float* d_opsf = nullptr;
   double* d_geo = nullptr;
   int* d_nbr = nullptr;
   unsigned char* d_nbf = nullptr;
@@ -42,10 +45,27 @@ struct ldg_ctx {
   double* d_w = nullptr;       // [ndof]
   double* d_res = nullptr;     // [ndof] Newton residual
   double* d_x = nullptr;       // [ndof] Newton update
-  double* d_small = nullptr;   // H, cs, sn, g, y, h, scalars
-  double* d_part = nullptr;    // reduction partials [nblk][m+2]
+  double* d_small = nullptr;   // H, cs, sn, g, y, h1, h2, scalars (KrySmall)
+  double* d_part = nullptr;    // reduction partials [nblk][32]
+  int* d_flags = nullptr;      // done, columns, breakdown
+  unsigned int* d_ticket = nullptr;
   double* h_pin = nullptr;     // pinned host scalars
+  int* h_flags = nullptr;      // pinned copies of the flags, one slot per Arnoldi step
+  cudaEvent_t ev[64] = {};
   int nblk = 0;
+  // block-Jacobi preconditioner
+  int nloc = 0;
+  std::vector<int> h_nbr;      // host copy of the face neighbours (colouring)
+  int* d_colour = nullptr;
+  int ncolour = 0;
+  double* d_blocks = nullptr;  // [E][nloc][nloc] exact diagonal blocks, column-major
+  void* d_binv = nullptr;      // their inverses (float or double)
+  int binv_prec = -1;
+  double* d_Z = nullptr;       // [m][ndof] preconditioned Krylov vectors (flexible GMRES)
+  double* d_probe = nullptr;   // probing work vectors (linear models)
+  double* d_jp = nullptr;
+  int* d_status = nullptr;
+  bool pc_ready = false;
   std::string err;
 };
 
@@ -89,20 +109,6 @@ int fail(ldg_ctx* c, int code, const std::string& msg) {
       return fail(ctx, LDG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
   } while (0)
 
-// small-array offsets in d_small
-struct Small {
-  int m;
-  __host__ __device__ size_t H() const { return 0; }                              // (m+1) x m, column-major
-  __host__ __device__ size_t cs() const { return (size_t)(m + 1) * m; }
-  __host__ __device__ size_t sn() const { return cs() + m; }
-  __host__ __device__ size_t g() const { return sn() + m; }                       // m+1
-  __host__ __device__ size_t y() const { return g() + m + 1; }                    // m
-  __host__ __device__ size_t h() const { return y() + m; }                        // m+2: first Gram-Schmidt pass
-  __host__ __device__ size_t h2() const { return h() + m + 2; }                   // m+2: second pass
-  __host__ __device__ size_t sc() const { return h2() + m + 2; }                  // scalars: [0] ||w||^2, [1] |g_{j+1}|, [2] h_{j+1,j}
-  __host__ __device__ size_t total() const { return sc() + 8; }
-};
-
 // ---------------------------------------------------------------- aux kernels
 __global__ void k_interp_nodes(int dim, int npe, int ncu, int64_t E, const double* geo, int GEO, const double* xn,
                                ModelParams mp, double t, double* u) {
@@ -127,144 +133,30 @@ __global__ void k_hist(int64_t n, double c1, const double* a, double c2, const d
   if (i < n) out[i] = c1 * a[i] + (b ? c2 * b[i] : 0.0);
 }
 
-// Partial dot products of the nvec vectors V[k] (stride ldv) with w:
-// part[block][k] = sum over this block's slice of V[k][i] * w[i].
-constexpr int RED_T = 256;
-__global__ void __launch_bounds__(RED_T) k_multidot(const double* __restrict__ V, int64_t ldv, int nvec,
-                                                    const double* __restrict__ w, int64_t n, double* part, int ldp) {
-  double acc[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) acc[k] = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)RED_T + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_T) {
-    double wi = w[i];
-#pragma unroll
-    for (int k = 0; k < 32; ++k)
-      if (k < nvec) acc[k] += V[k * ldv + i] * wi;
-  }
-  __shared__ double red[RED_T / 32][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    if (k >= nvec) break;
-    double v = acc[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wid][k] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < nvec) {
-    double s = 0.0;
-    for (int q = 0; q < RED_T / 32; ++q) s += red[q][threadIdx.x];
-    part[blockIdx.x * (int64_t)ldp + threadIdx.x] = s;
-  }
-}
-// out[k] (=|+=) sum over blocks of part[b][k]; one block, deterministic order.
-__global__ void k_reduce_part(const double* part, int nblk, int ldp, int nvec, double* out, int add) {
-  __shared__ double red[RED_T];
-  for (int k = 0; k < nvec; ++k) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += RED_T) s += part[b * (int64_t)ldp + k];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = RED_T / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[k] = add ? out[k] + red[0] : red[0];
-    __syncthreads();
-  }
-}
-// w[i] += sgn * sum_k V[k][i] * h[k]
-__global__ void k_update(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ h,
-                         double sgn, double* __restrict__ w, int64_t n) {
-  __shared__ double hs[32];
-  if (threadIdx.x < nvec) hs[threadIdx.x] = sgn * h[threadIdx.x];
-  __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = w[i];
-    for (int k = 0; k < nvec; ++k) s += V[k * ldv + i] * hs[k];
-    w[i] = s;
-  }
-}
-// out = in / sqrt(*nrm2)   (nrm2 holds a squared norm; zero leaves out = 0)
-__global__ void k_scale_inv(const double* in, const double* nrm2, double* out, int64_t n) {
-  double s = sqrt(*nrm2);
-  double f = s > 0.0 ? 1.0 / s : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = in[i] * f;
-}
-// out = a - b
-__global__ void k_sub(const double* a, const double* b, double* out, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = a[i] - b[i];
-}
-// Arnoldi column j: H[:, j] = h[0..j], H[j+1][j] = ||w||; apply the previous rotations,
-// form the new one, rotate g, and record |g_{j+1}| in sc[1].
-__global__ void k_givens(double* small, int m, int j) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  Small S{m};
-  double* H = small + S.H();
-  double* cs = small + S.cs();
-  double* sn = small + S.sn();
-  double* g = small + S.g();
-  const double* h = small + S.h();
-  const double* h2 = small + S.h2();
-  double* sc = small + S.sc();
-  double* col = H + (size_t)j * (m + 1);
-  for (int i = 0; i <= j; ++i) col[i] = h[i] + h2[i];
-  double hn = sqrt(sc[0]);
-  col[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    double a = col[i], b = col[i + 1];
-    col[i] = cs[i] * a + sn[i] * b;
-    col[i + 1] = -sn[i] * a + cs[i] * b;
-  }
-  double a = col[j], b = col[j + 1];
-  double den = sqrt(a * a + b * b);
-  cs[j] = den > 0.0 ? a / den : 1.0;
-  sn[j] = den > 0.0 ? b / den : 0.0;
-  col[j] = den;
-  col[j + 1] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  sc[1] = fabs(g[j + 1]);
-  sc[2] = hn;
-}
-// y = H[0:k, 0:k]^{-1} g[0:k] (upper triangular)
-__global__ void k_backsolve(double* small, int m, int k) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  Small S{m};
-  const double* H = small + S.H();
-  const double* g = small + S.g();
-  double* y = small + S.y();
-  for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int l = i + 1; l < k; ++l) s -= H[(size_t)l * (m + 1) + i] * y[l];
-    y[i] = s / H[(size_t)i * (m + 1) + i];
-  }
-}
-__global__ void k_init_g(double* small, int m, const double* nrm2) {
-  Small S{m};
-  double* g = small + S.g();
-  for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = 0.0;
-  if (threadIdx.x == 0) g[0] = sqrt(*nrm2);
-}
-
 KArgs base_args(ldg_ctx* c) {
   KArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.geo = c->d_geo; a.nbr = c->d_nbr; a.nbf = c->d_nbf; a.ops = c->d_ops; a.perm = c->d_perm;
+  a.geo = c->d_geo; a.nbr = c->d_nbr; a.nbf = c->d_nbf; a.ops = c->d_ops; a.opsf = c->d_opsf; a.perm = c->d_perm;
   a.a0dt = c->a0dt; a.t = c->t; a.mp = c->mp; a.E = (int)c->E;
+  a.blk_col = -1;
   return a;
 }
 
 int64_t grid_for(int64_t n, int t = 256) { return (n + t - 1) / t; }
 
-// ||x||^2 into dst (device scalar)
-int dot_into(ldg_ctx* ctx, const double* V, int64_t ldv, int nvec, const double* w, double* dst, int add) {
-  k_multidot<<<ctx->nblk, RED_T, 0, ctx->stream>>>(V, ldv, nvec, w, ctx->ndof, ctx->d_part, ctx->m + 2);
-  count_launch();
-  CK(cudaGetLastError());
-  k_reduce_part<<<1, RED_T, 0, ctx->stream>>>(ctx->d_part, ctx->nblk, ctx->m + 2, nvec, dst, add);
+constexpr int LDP = 32;   // leading dimension of the reduction partials
+
+// out[k] = V[k] . w for k < nvec (device), optionally skipped when flags[0] is set
+int dots(ldg_ctx* ctx, const double* V, int64_t ldv, int nvec, const double* w, double* out, const int* flags) {
+  const int64_t n = ctx->ndof;
+  if (nvec <= 1)
+    k_dots<1><<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
+  else if (nvec <= 8)
+    k_dots<8><<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
+  else if (nvec <= 16)
+    k_dots<16><<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
+  else
+    k_dots<32><<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
   count_launch();
   CK(cudaGetLastError());
   return LDG_OK;
@@ -290,6 +182,26 @@ int do_residual(ldg_ctx* ctx, const double* u, double* r) {
   return LDG_OK;
 }
 
+int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv, int prec) {
+  const int* skip = a.skip;
+  const bool f32 = prec == LDG_FP32;
+  StageFn qs = f32 ? ctx->ks->qstage32 : ctx->ks->qstage;
+  StageFn rs = f32 ? ctx->ks->residual32 : ctx->ks->residual;
+  if (ctx->ks->qstage) {
+    // linear model: J v = R(v) - R(0), the homogeneous operator applied to v
+    a.u = v; a.out = ctx->d_dq;
+    CK(qs(MODE_HOM, a, ctx->stream));
+    a = base_args(ctx);
+    a.skip = skip;
+    a.u = v; a.q = ctx->d_dq; a.out = jv;
+    CK(rs(MODE_HOM, a, ctx->stream));
+  } else {
+    a.u = u; a.v = v; a.out = jv;
+    CK(rs(MODE_JV, a, ctx->stream));
+  }
+  return LDG_OK;
+}
+
 int do_jvp(ldg_ctx* ctx, const double* u, const double* v, double* jv) {
   KArgs a = base_args(ctx);
   if (ctx->ks->qstage) {
@@ -306,92 +218,240 @@ int do_jvp(ldg_ctx* ctx, const double* u, const double* v, double* jv) {
   return LDG_OK;
 }
 
+// ------------------------------------------------------- block-Jacobi
+// Greedy colouring such that no two elements of one colour are within `dist`
+// face steps (dist 2 for diffusion models: R_K depends on u up to two faces away
+// through q).
+void colour_mesh(ldg_ctx* ctx, int dist, std::vector<int>& col) {
+  const int64_t E = ctx->E;
+  const int nf = ctx->nf;
+  col.assign(E, -1);
+  std::vector<int> mark;
+  for (int64_t e = 0; e < E; ++e) {
+    std::vector<int64_t> near;
+    for (int f = 0; f < nf; ++f) {
+      int a = ctx->h_nbr[e * nf + f];
+      if (a < 0) continue;
+      near.push_back(a);
+      if (dist >= 2)
+        for (int g = 0; g < nf; ++g) {
+          int b = ctx->h_nbr[(int64_t)a * nf + g];
+          if (b >= 0 && b != e) near.push_back(b);
+        }
+    }
+    std::vector<char> used(near.size() + 1, 0);
+    for (int64_t x : near)
+      if (col[x] >= 0 && col[x] < (int)used.size()) used[col[x]] = 1;
+    int c = 0;
+    while (used[c]) ++c;   // at most near.size() colours are taken
+    col[e] = c;
+  }
+}
+
+int ensure_pc_storage(ldg_ctx* ctx) {
+  const int64_t E = ctx->E, n = ctx->nloc;
+  if (!ctx->d_blocks) CK(cudaMalloc(&ctx->d_blocks, (size_t)E * n * n * sizeof(double)));
+  if (!ctx->d_Z) CK(cudaMalloc(&ctx->d_Z, (size_t)ctx->m * ctx->ndof * sizeof(double)));
+  if (!ctx->d_status) {
+    CK(cudaMalloc(&ctx->d_status, sizeof(int)));
+    CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+  }
+  if (ctx->ks->qstage && !ctx->d_colour) {
+    std::vector<int> col;
+    colour_mesh(ctx, 2, col);
+    int nc = 0;
+    for (int c : col) nc = std::max(nc, c + 1);
+    ctx->ncolour = nc;
+    CK(cudaMalloc(&ctx->d_colour, col.size() * sizeof(int)));
+    CK(cudaMemcpy(ctx->d_colour, col.data(), col.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_probe, ctx->ndof * sizeof(double)));
+    CK(cudaMalloc(&ctx->d_jp, ctx->ndof * sizeof(double)));
+  }
+  return LDG_OK;
+}
+
+// Exact diagonal blocks dR_K/du_K at state u, computed in the given arithmetic.
+int do_blocks(ldg_ctx* ctx, const double* u, int prec, double* blocks) {
+  int rc;
+  if ((rc = ensure_pc_storage(ctx))) return rc;
+  if (!blocks) return fail(ctx, LDG_ERR_ARG, "block extraction: null output buffer");
+  const int nloc = ctx->nloc;
+  const int64_t E = ctx->E;
+  if (!ctx->ks->qstage) {
+    // dual numbers with a unit tangent on every element and none on its neighbours
+    StageFn rs = prec == LDG_FP32 ? ctx->ks->residual32 : ctx->ks->residual;
+    for (int l = 0; l < nloc; ++l) {
+      KArgs a = base_args(ctx);
+      a.u = u; a.v = u; a.out = nullptr;
+      a.blk_col = l;
+      a.blk_out = blocks;
+      CK(rs(MODE_JV, a, ctx->stream));
+    }
+    return LDG_OK;
+  }
+  // linear models: coloured probing, J applied to the sum of unit vectors of one colour
+  for (int c = 0; c < ctx->ncolour; ++c)
+    for (int l = 0; l < nloc; ++l) {
+      k_probe<<<grid_for(E * nloc), 256, 0, ctx->stream>>>(ctx->d_probe, ctx->d_colour, c, l, nloc, E);
+      count_launch();
+      if ((rc = jvp_args(ctx, base_args(ctx), u, ctx->d_probe, ctx->d_jp, prec))) return rc;
+      k_extract<<<grid_for(E * nloc), 256, 0, ctx->stream>>>(ctx->d_jp, ctx->d_colour, c, l, nloc, E, blocks);
+      count_launch();
+      CK(cudaGetLastError());
+    }
+  return LDG_OK;
+}
+
+// Build the block-Jacobi preconditioner at state u: blocks in the Krylov arithmetic,
+// inverses in FP32 when the Krylov J.v is FP32 (or the block is too large for an FP64
+// elimination in shared memory), else FP64.
+int do_pc_setup(ldg_ctx* ctx, const double* u) {
+  int rc;
+  const int prec = ctx->opt.krylov_precision;
+  // the block storage must exist before its address is handed to the extraction
+  if ((rc = ensure_pc_storage(ctx))) return rc;
+  if ((rc = do_blocks(ctx, u, prec, ctx->d_blocks))) return rc;
+  const int n = ctx->nloc;
+  const bool fp64 = prec == LDG_FP64 && (size_t)(2 * n * n + n) * sizeof(double) <= 200 * 1024;
+  const int want = fp64 ? LDG_FP64 : LDG_FP32;
+  if (ctx->binv_prec != want) {
+    cudaFree(ctx->d_binv);
+    ctx->d_binv = nullptr;
+    CK(cudaMalloc(&ctx->d_binv, (size_t)ctx->E * n * n * (fp64 ? sizeof(double) : sizeof(float))));
+    ctx->binv_prec = want;
+  }
+  const int threads = std::min(256, ((n + 31) / 32) * 32 * 2);
+  if (fp64) {
+    const size_t smem = (size_t)(2 * n * n + n) * sizeof(double);
+    CK(cudaFuncSetAttribute(k_block_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_block_inverse<double><<<(unsigned)ctx->E, threads, smem, ctx->stream>>>(ctx->d_blocks, (double*)ctx->d_binv, n,
+                                                                             ctx->d_status);
+  } else {
+    const size_t smem = (size_t)(2 * n * n + n) * sizeof(float);
+    CK(cudaFuncSetAttribute(k_block_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_block_inverse<float><<<(unsigned)ctx->E, threads, smem, ctx->stream>>>(ctx->d_blocks, (float*)ctx->d_binv, n,
+                                                                            ctx->d_status);
+  }
+  count_launch();
+  CK(cudaGetLastError());
+  ctx->pc_ready = true;
+  return LDG_OK;
+}
+
+int pc_apply(ldg_ctx* ctx, const double* x, double* y, const int* skip) {
+  const int n = ctx->nloc;
+  const int threads = std::min(256, ((n + 31) / 32) * 32);
+  if (ctx->binv_prec == LDG_FP64)
+    k_block_apply<double><<<(unsigned)ctx->E, threads, n * sizeof(double), ctx->stream>>>((const double*)ctx->d_binv, x,
+                                                                                         y, n, skip);
+  else
+    k_block_apply<float><<<(unsigned)ctx->E, threads, n * sizeof(float), ctx->stream>>>((const float*)ctx->d_binv, x, y,
+                                                                                       n, skip);
+  count_launch();
+  CK(cudaGetLastError());
+  return LDG_OK;
+}
+
 // GMRES(m) on J(u) x = b, x0 = 0, to ||b - J x|| <= rtol ||b||.
+// The host queues Arnoldi steps up to LAG steps ahead of the GPU; each step's
+// kernels return at once after the device-side convergence test has fired.
 int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double rtol, ldg_solve_report* rep) {
   const int m = ctx->m;
   const int64_t n = ctx->ndof;
-  Small S{m};
+  KrySmall S{m};
   double* sm = ctx->d_small;
+  double* sc = sm + S.sc();
   double* V = ctx->d_V;
+  int* flags = ctx->d_flags;
+  const int LAG = 2;
   int rc;
   CK(cudaMemsetAsync(x, 0, n * sizeof(double), ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-  if ((rc = dot_into(ctx, ctx->d_r, n, 1, ctx->d_r, sm + S.sc(), 0))) return rc;
-  if ((rc = read_scalars(ctx, sm + S.sc(), 1))) return rc;
+  if ((rc = dots(ctx, ctx->d_r, n, 1, ctx->d_r, sc + 4, nullptr))) return rc;
+  if ((rc = read_scalars(ctx, sc + 4, 1))) return rc;
   const double bnorm = std::sqrt(ctx->h_pin[0]);
   if (!std::isfinite(bnorm)) return fail(ctx, LDG_ERR_NONFINITE, "non-finite right-hand side");
   if (rep) rep->lin_resid = 0.0;
   if (bnorm == 0.0) return LDG_OK;
+  const double thr = rtol * bnorm;
+  CK(cudaMemcpyAsync(sc + 3, &thr, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  const bool pc = ctx->opt.precond == LDG_PC_BJACOBI && ctx->pc_ready;
   const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8);
-  double beta = bnorm;
   for (int cycle = 0; cycle < ctx->opt.max_restarts; ++cycle) {
-    // V[0] = r / ||r||, g = (||r||, 0, ...); sc[0] holds ||r||^2
-    k_scale_inv<<<g1, 256, 0, ctx->stream>>>(ctx->d_r, sm + S.sc(), V, n);
-    count_launch();
-    k_init_g<<<1, 64, 0, ctx->stream>>>(sm, m, sm + S.sc());
+    k_cycle_start<<<g1, 256, 0, ctx->stream>>>(ctx->d_r, V, n, sm, m, flags);
     count_launch();
     CK(cudaGetLastError());
-    int j = 0;
-    bool done = false;
-    for (; j < m; ++j) {
+    int queued = 0;
+    bool stop = false;
+    for (int j = 0; j < m && !stop; ++j) {
+      if (j >= LAG) {
+        CK(cudaEventSynchronize(ctx->ev[j - LAG]));
+        if (ctx->h_flags[(j - LAG) * 4]) { stop = true; break; }
+      }
       double* w = V + (size_t)(j + 1) * n;
-      if ((rc = do_jvp(ctx, u, V + (size_t)j * n, w))) return rc;
-      if (rep) { rep->jv_calls++; rep->gmres_iters++; }
-      // classical Gram-Schmidt with one re-orthogonalisation pass
-      if ((rc = dot_into(ctx, V, n, j + 1, w, sm + S.h(), 0))) return rc;
-      k_update<<<g1, 256, 0, ctx->stream>>>(V, n, j + 1, sm + S.h(), -1.0, w, n);
+      KArgs a = base_args(ctx);
+      a.skip = flags;
+      const double* dir = V + (size_t)j * n;
+      if (pc) {
+        // flexible right preconditioning: z_j = M^{-1} v_j, w = J z_j, x += Z y
+        double* z = ctx->d_Z + (size_t)j * n;
+        if ((rc = pc_apply(ctx, dir, z, flags))) return rc;
+        dir = z;
+      }
+      if ((rc = jvp_args(ctx, a, u, dir, w, ctx->opt.krylov_precision))) return rc;
+      if ((rc = dots(ctx, V, n, j + 1, w, sm + S.h1(), flags))) return rc;
+      k_orth_update<<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, n, j + 1, sm + S.h1(), w, n, ctx->d_part, LDP,
+                                                          ctx->d_ticket, sm, m, j, 0, flags);
+      count_launch();
+      if ((rc = dots(ctx, V, n, j + 1, w, sm + S.h2(), flags))) return rc;
+      k_orth_update<<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, n, j + 1, sm + S.h2(), w, n, ctx->d_part, LDP,
+                                                          ctx->d_ticket, sm, m, j, 1, flags);
+      count_launch();
+      k_scale_by_norm<<<g1, 256, 0, ctx->stream>>>(w, sc, w, n, flags);
       count_launch();
       CK(cudaGetLastError());
-      if ((rc = dot_into(ctx, V, n, j + 1, w, sm + S.h2(), 0))) return rc;
-      k_update<<<g1, 256, 0, ctx->stream>>>(V, n, j + 1, sm + S.h2(), -1.0, w, n);
-      count_launch();
-      CK(cudaGetLastError());
-      if ((rc = dot_into(ctx, w, n, 1, w, sm + S.sc(), 0))) return rc;
-      k_givens<<<1, 1, 0, ctx->stream>>>(sm, m, j);
-      count_launch();
-      k_scale_inv<<<g1, 256, 0, ctx->stream>>>(w, sm + S.sc(), w, n);
-      count_launch();
-      CK(cudaGetLastError());
-      if ((rc = read_scalars(ctx, sm + S.sc(), 3))) return rc;
-      const double est = ctx->h_pin[1], hn = ctx->h_pin[2];
-      if (!std::isfinite(est)) return fail(ctx, LDG_ERR_NONFINITE, "non-finite Arnoldi quantity");
-      if (est <= rtol * bnorm || hn == 0.0) { ++j; done = true; break; }
+      CK(cudaMemcpyAsync(ctx->h_flags + j * 4, flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaEventRecord(ctx->ev[j], ctx->stream));
+      queued = j + 1;
     }
-    if (j == m) done = false;
-    // x += V y
-    k_backsolve<<<1, 1, 0, ctx->stream>>>(sm, m, j);
+    (void)queued;
+    k_backsolve<<<1, 32, 0, ctx->stream>>>(sm, m, flags);
     count_launch();
-    k_update<<<g1, 256, 0, ctx->stream>>>(V, n, j, sm + S.y(), 1.0, x, n);
-    count_launch();
-    CK(cudaGetLastError());
-    // true residual r = b - J x
-    if ((rc = do_jvp(ctx, u, x, ctx->d_w))) return rc;
-    if (rep) rep->jv_calls++;
-    k_sub<<<g1, 256, 0, ctx->stream>>>(b, ctx->d_w, ctx->d_r, n);
+    k_solution_update<<<g1, 256, 0, ctx->stream>>>(pc ? ctx->d_Z : V, n, sm, m, flags, x, n);
     count_launch();
     CK(cudaGetLastError());
-    if ((rc = dot_into(ctx, ctx->d_r, n, 1, ctx->d_r, sm + S.sc(), 0))) return rc;
-    if ((rc = read_scalars(ctx, sm + S.sc(), 1))) return rc;
-    beta = std::sqrt(ctx->h_pin[0]);
+    // true residual r = b - J x (with the operator the Arnoldi process used)
+    if ((rc = jvp_args(ctx, base_args(ctx), u, x, ctx->d_w, ctx->opt.krylov_precision))) return rc;
+    k_sub_norm<<<ctx->nblk, KRY_T, 0, ctx->stream>>>(b, ctx->d_w, ctx->d_r, n, ctx->d_part, LDP, ctx->d_ticket, sc + 4);
+    count_launch();
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->h_pin, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_flags + 60 * 4, flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int cols = ctx->h_flags[60 * 4 + 1];
+    if (rep) { rep->gmres_iters += cols; rep->jv_calls += cols + 1; }
+    const double beta = std::sqrt(ctx->h_pin[4]);
     if (rep) rep->lin_resid = beta / bnorm;
     if (!std::isfinite(beta)) return fail(ctx, LDG_ERR_NONFINITE, "non-finite GMRES residual");
-    if (beta <= rtol * bnorm * (1.0 + 1e-6) || (done && beta <= rtol * bnorm * 10.0)) return LDG_OK;
+    const bool converged_est = ctx->h_flags[60 * 4] && !ctx->h_flags[60 * 4 + 2];
+    if (beta <= thr * (1.0 + 1e-6) || (converged_est && beta <= thr * 10.0)) return LDG_OK;
+    if (cols == 0) return fail(ctx, LDG_ERR_NONFINITE, "GMRES made no progress");
   }
   return fail(ctx, LDG_ERR_MAXIT, "GMRES did not reach its tolerance within max_restarts cycles");
 }
 
 int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
   const int64_t n = ctx->ndof;
-  Small S{ctx->m};
-  double* sm = ctx->d_small;
+  KrySmall S{ctx->m};
+  double* sc = ctx->d_small + S.sc();
   int rc;
   auto t0 = std::chrono::steady_clock::now();
   double* res = ctx->d_res;   // R(u_k), the right-hand side of each linear solve
   double* del = ctx->d_x;     // Newton update
   if ((rc = do_residual(ctx, u, res))) return rc;
   if (rep) rep->residual_calls++;
-  if ((rc = dot_into(ctx, res, n, 1, res, sm + S.sc() + 4, 0))) return rc;
-  if ((rc = read_scalars(ctx, sm + S.sc() + 4, 1))) return rc;
+  if ((rc = dots(ctx, res, n, 1, res, sc + 5, nullptr))) return rc;
+  if ((rc = read_scalars(ctx, sc + 5, 1))) return rc;
   const double r0 = std::sqrt(ctx->h_pin[0]);
   double rn = r0;
   if (rep) rep->r0 = r0;
@@ -399,15 +459,20 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
   int k = 0;
   const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8);
   while (rn > ctx->opt.newton_rtol * r0 && k < ctx->opt.max_newton) {
+    if (ctx->opt.precond == LDG_PC_BJACOBI &&
+        (k == 0 || (ctx->opt.pc_refresh > 0 && k % ctx->opt.pc_refresh == 0))) {
+      if ((rc = do_pc_setup(ctx, u))) return rc;
+      if (rep) rep->pc_setups++;
+    }
     if ((rc = do_gmres(ctx, u, res, del, ctx->opt.gmres_rtol, rep)) && rc != LDG_ERR_MAXIT) return rc;
     // u <- u - delta   (sc[6] holds -1)
-    k_update<<<g1, 256, 0, ctx->stream>>>(del, n, 1, sm + S.sc() + 6, 1.0, u, n);
+    k_axpy_dev<<<g1, 256, 0, ctx->stream>>>(del, sc + 6, u, n);
     count_launch();
     CK(cudaGetLastError());
     if ((rc = do_residual(ctx, u, res))) return rc;
     if (rep) rep->residual_calls++;
-    if ((rc = dot_into(ctx, res, n, 1, res, sm + S.sc() + 4, 0))) return rc;
-    if ((rc = read_scalars(ctx, sm + S.sc() + 4, 1))) return rc;
+    if ((rc = dots(ctx, res, n, 1, res, sc + 5, nullptr))) return rc;
+    if ((rc = read_scalars(ctx, sc + 5, 1))) return rc;
     rn = std::sqrt(ctx->h_pin[0]);
     if (!std::isfinite(rn)) return fail(ctx, LDG_ERR_NONFINITE, "non-finite residual after a Newton step");
     ++k;
@@ -434,10 +499,15 @@ const char* ldg_last_error(const ldg_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 int ldg_destroy(ldg_ctx* ctx) {
   if (!ctx) return LDG_OK;
-  cudaFree(ctx->d_ops); cudaFree(ctx->d_geo); cudaFree(ctx->d_nbr); cudaFree(ctx->d_nbf); cudaFree(ctx->d_perm);
+  cudaFree(ctx->d_ops); cudaFree(ctx->d_opsf); cudaFree(ctx->d_geo); cudaFree(ctx->d_nbr); cudaFree(ctx->d_nbf); cudaFree(ctx->d_perm);
   cudaFree(ctx->d_xn); cudaFree(ctx->d_q); cudaFree(ctx->d_dq); cudaFree(ctx->d_hist);
   cudaFree(ctx->d_V); cudaFree(ctx->d_r); cudaFree(ctx->d_w); cudaFree(ctx->d_res); cudaFree(ctx->d_x); cudaFree(ctx->d_small); cudaFree(ctx->d_part);
+  cudaFree(ctx->d_flags); cudaFree(ctx->d_ticket);
+  cudaFree(ctx->d_colour); cudaFree(ctx->d_blocks); cudaFree(ctx->d_binv); cudaFree(ctx->d_Z);
+  cudaFree(ctx->d_probe); cudaFree(ctx->d_jp); cudaFree(ctx->d_status);
   if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
+  if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+  for (int i = 0; i < 64; ++i) if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   delete ctx;
   return LDG_OK;
 }
@@ -466,6 +536,9 @@ int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if (o.max_newton <= 0) o.max_newton = 20;
   if (o.newton_rtol <= 0) o.newton_rtol = 1e-8;
   if (o.gmres_rtol <= 0) o.gmres_rtol = 1e-3;
+  if (o.krylov_precision != LDG_FP32) o.krylov_precision = LDG_FP64;
+  if (o.precond != LDG_PC_BJACOBI) o.precond = LDG_PC_NONE;
+  if (o.pc_refresh < 0) o.pc_refresh = 0;
   ctx->opt = o;
   ctx->p = p; ctx->nq = o.nq1;
   // model parameters
@@ -497,6 +570,8 @@ int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   ctx->E = mesh->n_elem;
   ctx->npe = ref.npe; ctx->nf = ref.nf; ctx->nfq = ref.nfq;
   ctx->ndof = ctx->E * ctx->npe * ctx->ncu;
+  ctx->nloc = ctx->npe * ctx->ncu;
+  ctx->h_nbr = mp_.nbr;
   ctx->m = o.gmres_m;
   std::vector<double> xn;
   ref_nodes(ref, xn);
@@ -509,6 +584,11 @@ int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   CK(cudaMalloc(&ctx->d_perm, mp_.perm.size()));
   CK(cudaMalloc(&ctx->d_xn, xn.size() * sizeof(double)));
   CK(cudaMemcpy(ctx->d_ops, ref.blob.data(), ref.blob.size() * sizeof(double), cudaMemcpyHostToDevice));
+  {
+    std::vector<float> bf(ref.blob.begin(), ref.blob.end());
+    CK(cudaMalloc(&ctx->d_opsf, bf.size() * sizeof(float)));
+    CK(cudaMemcpy(ctx->d_opsf, bf.data(), bf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   CK(cudaMemcpy(ctx->d_geo, mp_.geo.data(), mp_.geo.size() * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_nbr, mp_.nbr.data(), mp_.nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_nbf, mp_.nbf.data(), mp_.nbf.size(), cudaMemcpyHostToDevice));
@@ -524,12 +604,18 @@ int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   CK(cudaMalloc(&ctx->d_w, n * sizeof(double)));
   CK(cudaMalloc(&ctx->d_res, n * sizeof(double)));
   CK(cudaMalloc(&ctx->d_x, n * sizeof(double)));
-  Small S{ctx->m};
+  KrySmall S{ctx->m};
   CK(cudaMalloc(&ctx->d_small, S.total() * sizeof(double)));
   CK(cudaMemset(ctx->d_small, 0, S.total() * sizeof(double)));
-  ctx->nblk = 148 * 4;
-  CK(cudaMalloc(&ctx->d_part, (size_t)ctx->nblk * (ctx->m + 2) * sizeof(double)));
+  ctx->nblk = (int)std::min<int64_t>(148 * 2, std::max<int64_t>(1, (n + 2047) / 2048));
+  CK(cudaMalloc(&ctx->d_part, (size_t)ctx->nblk * LDP * sizeof(double)));
+  CK(cudaMalloc(&ctx->d_flags, 8 * sizeof(int)));
+  CK(cudaMemset(ctx->d_flags, 0, 8 * sizeof(int)));
+  CK(cudaMalloc(&ctx->d_ticket, 8 * sizeof(unsigned int)));
+  CK(cudaMemset(ctx->d_ticket, 0, 8 * sizeof(unsigned int)));
   CK(cudaMallocHost(&ctx->h_pin, 16 * sizeof(double)));
+  CK(cudaMallocHost(&ctx->h_flags, 64 * 4 * sizeof(int)));
+  for (int i = 0; i < 64; ++i) CK(cudaEventCreateWithFlags(&ctx->ev[i], cudaEventDisableTiming));
   // the Newton update uses sc[6] = -1 as its axpy coefficient
   double minus1 = -1.0;
   CK(cudaMemcpy(ctx->d_small + S.sc() + 6, &minus1, sizeof(double), cudaMemcpyHostToDevice));
@@ -576,6 +662,27 @@ int ldg_residual(ldg_ctx* ctx, const double* u, double* r) {
 int ldg_jvp(ldg_ctx* ctx, const double* u, const double* v, double* jv) {
   if (!ctx || !ctx->ks || !u || !v || !jv) return LDG_ERR_ARG;
   return do_jvp(ctx, u, v, jv);
+}
+
+int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u, const double* v, double* jv) {
+  if (!ctx || !ctx->ks || !u || !v || !jv || (precision != LDG_FP64 && precision != LDG_FP32)) return LDG_ERR_ARG;
+  return jvp_args(ctx, base_args(ctx), u, v, jv, precision);
+}
+
+int ldg_diag_blocks(ldg_ctx* ctx, int precision, const double* u, double* blocks) {
+  if (!ctx || !ctx->ks || !u || !blocks || (precision != LDG_FP64 && precision != LDG_FP32)) return LDG_ERR_ARG;
+  return do_blocks(ctx, u, precision, blocks);
+}
+
+int ldg_precond_setup(ldg_ctx* ctx, const double* u) {
+  if (!ctx || !ctx->ks || !u) return LDG_ERR_ARG;
+  return do_pc_setup(ctx, u);
+}
+
+int ldg_precond_apply(ldg_ctx* ctx, const double* x, double* y) {
+  if (!ctx || !ctx->ks || !x || !y) return LDG_ERR_ARG;
+  if (!ctx->pc_ready) return fail(ctx, LDG_ERR_ARG, "ldg_precond_apply: call ldg_precond_setup first");
+  return pc_apply(ctx, x, y, nullptr);
 }
 
 int ldg_q(ldg_ctx* ctx, const double* u, double* q) {

@@ -38,12 +38,13 @@ template <class R> __device__ __forceinline__ Dual<R> operator/(R a, Dual<R> b) 
 }
 template <class R> __device__ __forceinline__ Dual<R>& operator+=(Dual<R>& a, Dual<R> b) { a.v += b.v; a.d += b.d; return a; }
 template <class R> __device__ __forceinline__ Dual<R>& operator-=(Dual<R>& a, Dual<R> b) { a.v -= b.v; a.d -= b.d; return a; }
-template <class R> __device__ __forceinline__ Dual<R> dsqrt(Dual<R> a) {
-  R s = sqrt(a.v);
-  return Dual<R>(s, a.d / (R(2) * s));
-}
 __device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
+// (the real part goes through the overloads above, so an FP32 instance stays in FP32)
+template <class R> __device__ __forceinline__ Dual<R> dsqrt(Dual<R> a) {
+  R s = dsqrt(a.v);
+  return Dual<R>(s, a.d / (R(2) * s));
+}
 
 template <class S> struct RealOf { typedef S type; };
 template <class R> struct RealOf<Dual<R>> { typedef R type; };
@@ -176,6 +177,17 @@ __device__ double source_term(const ModelParams& mp, bool conv, const double* x)
   return bg - mp.kappa * lap;
 }
 
+// Model parameters in the kernel's compute precision.
+template <class R> struct MPar {
+  R kappa, tau, beta[3], gamma;
+};
+template <class R> __device__ __forceinline__ MPar<R> mpar(const ModelParams& mp) {
+  MPar<R> r;
+  r.kappa = R(mp.kappa); r.tau = R(mp.tau); r.gamma = R(mp.gamma);
+  for (int d = 0; d < 3; ++d) r.beta[d] = R(mp.beta[d]);
+  return r;
+}
+
 // Scalar diffusion models: f = kappa q (Poisson) or beta u + kappa q (convection-diffusion).
 template <int DIM, bool CONV> struct ScalarModel {
   static constexpr int NCU = 1;
@@ -183,7 +195,7 @@ template <int DIM, bool CONV> struct ScalarModel {
   static constexpr bool LINEAR = true;
   static constexpr int KIND = CONV ? M_CONVDIFF : M_POISSON;
 
-  template <class S> __device__ static void flux(const S* u, const S* q, S* f, const ModelParams& mp) {
+  template <class S, class R> __device__ static void flux(const S* u, const S* q, S* f, const MPar<R>& mp) {
     for (int d = 0; d < DIM; ++d) {
       S v = q[d] * mp.kappa;
       if (CONV) v = v + u[0] * mp.beta[d];
@@ -191,26 +203,26 @@ template <int DIM, bool CONV> struct ScalarModel {
     }
   }
   // interior numerical flux: upwind convection, central diffusion plus tau jump
-  template <class S> __device__ static void fhat(const S* um, const S* up, const S* qm, const S* qp,
-                                                 const double* n, S* fh, const ModelParams& mp) {
+  template <class S, class R> __device__ static void fhat(const S* um, const S* up, const S* qm, const S* qp,
+                                                          const R* n, S* fh, const MPar<R>& mp) {
     S acc = (um[0] - up[0]) * mp.tau;
-    for (int d = 0; d < DIM; ++d) acc = acc + (qm[d] + qp[d]) * (0.5 * mp.kappa * n[d]);
+    for (int d = 0; d < DIM; ++d) acc = acc + (qm[d] + qp[d]) * (R(0.5) * mp.kappa * n[d]);
     if (CONV) {
-      double bn = 0.0;
+      R bn = R(0);
       for (int d = 0; d < DIM; ++d) bn += mp.beta[d] * n[d];
-      acc = acc + (bn >= 0.0 ? um[0] : up[0]) * bn;
+      acc = acc + (bn >= R(0) ? um[0] : up[0]) * bn;
     }
     fh[0] = acc;
   }
   // Dirichlet face: uhat = g; fhat = beta.n u_upwind + kappa q-.n + tau (u- - g)
-  template <class S> __device__ static void fhat_bnd(const S* um, const S* qm, const double* g,
-                                                     const double* n, S* fh, const ModelParams& mp) {
+  template <class S, class R> __device__ static void fhat_bnd(const S* um, const S* qm, const R* g, const R* n,
+                                                              S* fh, const MPar<R>& mp) {
     S acc = (um[0] - g[0]) * mp.tau;
     for (int d = 0; d < DIM; ++d) acc = acc + qm[d] * (mp.kappa * n[d]);
     if (CONV) {
-      double bn = 0.0;
+      R bn = R(0);
       for (int d = 0; d < DIM; ++d) bn += mp.beta[d] * n[d];
-      acc = acc + (bn >= 0.0 ? um[0] * bn : S(bn * g[0]));
+      acc = acc + (bn >= R(0) ? um[0] * bn : S(bn * g[0]));
     }
     fh[0] = acc;
   }
@@ -223,33 +235,30 @@ struct EulerModel {
   static constexpr bool LINEAR = false;
   static constexpr int KIND = M_EULER;
 
-  template <class S> __device__ static void flux(const S* u, const S*, S* f, const ModelParams& mp) {
-    typedef typename RealOf<S>::type R;
+  template <class S, class R> __device__ static void flux(const S* u, const S*, S* f, const MPar<R>& mp) {
     S ir = R(1) / u[0];
     S vx = u[1] * ir, vy = u[2] * ir;
-    S p = (u[3] - (u[1] * vx + u[2] * vy) * R(0.5)) * R(mp.gamma - 1.0);
+    S p = (u[3] - (u[1] * vx + u[2] * vy) * R(0.5)) * (mp.gamma - R(1));
     S h = u[3] + p;
     f[0] = u[1];           f[1] = u[2];
     f[2] = u[1] * vx + p;  f[3] = u[1] * vy;
     f[4] = u[2] * vx;      f[5] = u[2] * vy + p;
     f[6] = h * vx;         f[7] = h * vy;
   }
-  template <class S> __device__ static S normal_flux(const S* u, const double* n, S* fn, const ModelParams& mp) {
-    typedef typename RealOf<S>::type R;
+  template <class S, class R> __device__ static S normal_flux(const S* u, const R* n, S* fn, const MPar<R>& mp) {
     S ir = R(1) / u[0];
     S vx = u[1] * ir, vy = u[2] * ir;
-    S p = (u[3] - (u[1] * vx + u[2] * vy) * R(0.5)) * R(mp.gamma - 1.0);
-    S vn = vx * R(n[0]) + vy * R(n[1]);
+    S p = (u[3] - (u[1] * vx + u[2] * vy) * R(0.5)) * (mp.gamma - R(1));
+    S vn = vx * n[0] + vy * n[1];
     fn[0] = u[0] * vn;
-    fn[1] = u[1] * vn + p * R(n[0]);
-    fn[2] = u[2] * vn + p * R(n[1]);
+    fn[1] = u[1] * vn + p * n[0];
+    fn[2] = u[2] * vn + p * n[1];
     fn[3] = (u[3] + p) * vn;
-    S c = dsqrt(p * ir * R(mp.gamma));
+    S c = dsqrt(p * ir * mp.gamma);
     return sabs(vn) + c;
   }
-  template <class S> __device__ static void fhat(const S* um, const S* up, const S*, const S*,
-                                                 const double* n, S* fh, const ModelParams& mp) {
-    typedef typename RealOf<S>::type R;
+  template <class S, class R> __device__ static void fhat(const S* um, const S* up, const S*, const S*,
+                                                          const R* n, S* fh, const MPar<R>& mp) {
     S fm[4], fp[4];
     S lm = normal_flux(um, n, fm, mp);
     S lp = normal_flux(up, n, fp, mp);
@@ -257,16 +266,15 @@ struct EulerModel {
     for (int c = 0; c < 4; ++c) fh[c] = (fm[c] + fp[c]) * R(0.5) + lam * R(0.5) * (um[c] - up[c]);
   }
   // far field: Rusanov flux against the exact state
-  template <class S> __device__ static void fhat_bnd(const S* um, const S* qm, const double* g,
-                                                     const double* n, S* fh, const ModelParams& mp) {
-    typedef typename RealOf<S>::type R;
-    S up[4] = {S(R(g[0])), S(R(g[1])), S(R(g[2])), S(R(g[3]))};
+  template <class S, class R> __device__ static void fhat_bnd(const S* um, const S* qm, const R* g, const R* n,
+                                                              S* fh, const MPar<R>& mp) {
+    S up[4] = {S(g[0]), S(g[1]), S(g[2]), S(g[3])};
     fhat(um, up, qm, qm, n, fh, mp);
   }
 };
 
 // -------------------------------------------------------- element traits
-// Operator blob (FP64, row-major) shared by all elements of a context:
+// Operator blob (row-major, one FP64 and one FP32 copy per context) shared by all elements:
 //   tensor: B[NQ][N1], D[NQ][N1], W[NQ], XQ[NQ], Dn[N1][N1], Minv1[N1][N1], XN[N1]
 //   triangle: B[NQV][NPE], Dr[NQV][NPE], Ds[NQV][NPE], WV[NQV], XQV[NQV][2],
 //             Bf[NFQ][NFN], WF[NFQ], SF[NFQ], Dnr[NPE][NPE], Dns[NPE][NPE], Minv[NPE][NPE], XN[NPE][2]

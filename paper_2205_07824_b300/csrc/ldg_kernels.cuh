@@ -15,6 +15,11 @@
 // MODE_R evaluates R(u); MODE_HOM the homogeneous linear part of a linear model
 // (R(v) - R(0): no source, zero boundary data), which is its exact J.v; MODE_JV
 // propagates dual numbers (u, v) through a nonlinear model and writes dR/du . v.
+//
+// Storage in HBM is always FP64. The compute type R is double (parity path) or
+// float (the mixed-precision Krylov path): an FP32 instance converts its inputs
+// on load, keeps operators, geometry and every intermediate in FP32, and widens
+// its result on the store.
 #pragma once
 #include "ldg_device.cuh"
 
@@ -31,8 +36,14 @@ struct KArgs {
   const double* geo;          // [E][GEO] per-element affine geometry
   const int* nbr;             // [E][NF] neighbour element, -1 on the boundary
   const unsigned char* nbf;   // [E][NF] neighbour's local face | (orientation code << 3)
-  const double* ops;          // reference operator blob (element traits)
+  const double* ops;          // reference operator blob (element traits), FP64
+  const float* opsf;          // the same blob in FP32 (for FP32-compute instances)
   const unsigned char* perm;  // [n_orient][NFQ] face-point permutations
+  const int* skip;            // optional: the kernel returns at once when *skip != 0
+  int blk_col;                // MODE_JV block extraction: -1 off; else the element's own tangent is
+                              // unit vector blk_col, neighbours' tangents are zero, and column blk_col
+                              // of each element's diagonal block dR_K/du_K is written to blk_out
+  double* blk_out;            // [E][NLOC][NLOC] column-major blocks (NLOC = NCU * NPE)
   double a0dt;                // a0 / dt of the BDF scheme, 0 when steady
   double t;
   ModelParams mp;
@@ -77,45 +88,45 @@ template <class EL, class F> __device__ __forceinline__ void for_node_faces(int 
 }
 
 // Reference coordinates of face point k on face f.
-template <class EL> __device__ __forceinline__ void face_xi(const double* ops, int f, int k, double* xi) {
+template <class EL, class R> __device__ __forceinline__ void face_xi(const R* ops, int f, int k, R* xi) {
   if constexpr (EL::TENSOR) {
-    const double* XQ = ops + EL::OXQ;
+    const R* XQ = ops + EL::OXQ;
     const int ax = f >> 1;
-    const double fix = (f & 1) ? 1.0 : -1.0;
+    const R fix = (f & 1) ? R(1) : R(-1);
     if constexpr (EL::DIM == 2) {
       xi[ax] = fix;
       xi[1 - ax] = XQ[k];
     } else {
       // free axes in ascending order, the first one fastest
-      const double s0 = XQ[k % EL::NQ], s1 = XQ[k / EL::NQ];
+      const R s0 = XQ[k % EL::NQ], s1 = XQ[k / EL::NQ];
       if (ax == 0) { xi[0] = fix; xi[1] = s0; xi[2] = s1; }
       else if (ax == 1) { xi[0] = s0; xi[1] = fix; xi[2] = s1; }
       else { xi[0] = s0; xi[1] = s1; xi[2] = fix; }
     }
   } else {
-    const double V[3][2] = {{-1.0, -1.0}, {1.0, -1.0}, {-1.0, 1.0}};
-    int a = f, b = (f + 1) % 3;
-    double s = ops[EL::OSF + k];
-    xi[0] = 0.5 * (1.0 - s) * V[a][0] + 0.5 * (1.0 + s) * V[b][0];
-    xi[1] = 0.5 * (1.0 - s) * V[a][1] + 0.5 * (1.0 + s) * V[b][1];
+    const R V[3][2] = {{R(-1), R(-1)}, {R(1), R(-1)}, {R(-1), R(1)}};
+    const int a = f, b = (f + 1) % 3;
+    const R s = ops[EL::OSF + k];
+    xi[0] = R(0.5) * (R(1) - s) * V[a][0] + R(0.5) * (R(1) + s) * V[b][0];
+    xi[1] = R(0.5) * (R(1) - s) * V[a][1] + R(0.5) * (R(1) + s) * V[b][1];
   }
 }
-template <class EL> __device__ __forceinline__ double face_w(const double* ops, int k) {
+template <class EL, class R> __device__ __forceinline__ R face_w(const R* ops, int k) {
   if constexpr (EL::TENSOR) {
-    const double* W = ops + EL::OW;
+    const R* W = ops + EL::OW;
     return EL::DIM == 2 ? W[k] : W[k % EL::NQ] * W[k / EL::NQ];
   } else {
     return ops[EL::OWF + k];
   }
 }
-template <class EL> __device__ __forceinline__ void vol_xi(const double* ops, int q, double* xi, double& w) {
+template <class EL, class R> __device__ __forceinline__ void vol_xi(const R* ops, int q, R* xi, R& w) {
   if constexpr (EL::TENSOR) {
-    const double* XQ = ops + EL::OXQ;
-    const double* W = ops + EL::OW;
-    int i0 = q % EL::NQ, i1 = (q / EL::NQ) % EL::NQ, i2 = q / (EL::NQ * EL::NQ);
+    const R* XQ = ops + EL::OXQ;
+    const R* W = ops + EL::OW;
+    const int i0 = q % EL::NQ, i1 = (q / EL::NQ) % EL::NQ, i2 = q / (EL::NQ * EL::NQ);
     xi[0] = XQ[i0]; xi[1] = XQ[i1];
     w = W[i0] * W[i1];
-    if (EL::DIM == 3) { xi[2] = XQ[i2]; w *= W[i2]; }
+    if constexpr (EL::DIM == 3) { xi[2] = XQ[i2]; w *= W[i2]; }
   } else {
     xi[0] = ops[EL::OXQ + 2 * q];
     xi[1] = ops[EL::OXQ + 2 * q + 1];
@@ -123,19 +134,19 @@ template <class EL> __device__ __forceinline__ void vol_xi(const double* ops, in
   }
 }
 
-template <int DIM> __device__ __forceinline__ void phys_x(const double* g, const double* xi, double* x) {
+template <int DIM, class R> __device__ __forceinline__ void phys_x(const R* g, const R* xi, double* x) {
   for (int d = 0; d < DIM; ++d) {
-    double s = g[Geo<DIM>::XM + d];
-    for (int k = 0; k < DIM; ++k) s += g[Geo<DIM>::JAC + d * DIM + k] * xi[k];
+    double s = (double)g[Geo<DIM>::XM + d];
+    for (int k = 0; k < DIM; ++k) s += (double)g[Geo<DIM>::JAC + d * DIM + k] * (double)xi[k];
     x[d] = s;
   }
 }
 
 // ---------------------------------------------- reference operators on batches
 // face-node values [nb][NFN] -> face-point values [nb][NFQ]; tmp holds [nb][NQ*N1]
-template <class EL, class T> __device__ __forceinline__ void face_trace(const T* in, T* out, T* tmp, const double* ops, int nb) {
+template <class EL, class T, class OT> __device__ __forceinline__ void face_trace(const T* in, T* out, T* tmp, const OT* ops, int nb) {
   if constexpr (EL::TENSOR) {
-    const double* B = ops + EL::OB;
+    const OT* B = ops + EL::OB;
     if constexpr (EL::DIM == 2) {
       contract<0, EL::N1, 1, 1, EL::NQ, false, false>(in, out, B, nb);
     } else {
@@ -148,9 +159,9 @@ template <class EL, class T> __device__ __forceinline__ void face_trace(const T*
   }
 }
 // face-point values [nb][NFQ] -> face-node moments [nb][NFN] (transpose of face_trace)
-template <class EL, class T> __device__ __forceinline__ void face_lift(const T* in, T* out, T* tmp, const double* ops, int nb) {
+template <class EL, class T, class OT> __device__ __forceinline__ void face_lift(const T* in, T* out, T* tmp, const OT* ops, int nb) {
   if constexpr (EL::TENSOR) {
-    const double* B = ops + EL::OB;
+    const OT* B = ops + EL::OB;
     if constexpr (EL::DIM == 2) {
       contract<0, EL::NQ, 1, 1, EL::N1, true, false>(in, out, B, nb);
     } else {
@@ -163,10 +174,10 @@ template <class EL, class T> __device__ __forceinline__ void face_lift(const T* 
   }
 }
 // nodal [nb][NPE] -> volume points [nb][NQV]; t1, t2 hold [nb][max(NQ,N1)^DIM]
-template <class EL, class T> __device__ __forceinline__ void vol_interp(const T* in, T* out, T* t1, const double* ops, int nb) {
+template <class EL, class T, class OT> __device__ __forceinline__ void vol_interp(const T* in, T* out, T* t1, const OT* ops, int nb) {
   if constexpr (EL::TENSOR) {
     constexpr int N1 = EL::N1, NQ = EL::NQ;
-    const double* B = ops + EL::OB;
+    const OT* B = ops + EL::OB;
     if constexpr (EL::DIM == 2) {
       contract<0, N1, N1, 1, NQ, false, false>(in, t1, B, nb);
       __syncthreads();
@@ -184,12 +195,12 @@ template <class EL, class T> __device__ __forceinline__ void vol_interp(const T*
 }
 // out[nb][NPE] (+)= sum over volume points of Op_k^T in_k: k < DIM uses the
 // reference derivative along axis k, k == DIM the plain basis (both transposed).
-template <class EL, bool ACC, class T>
-__device__ __forceinline__ void vol_integrate(int k, const T* in, T* out, T* t1, T* t2, const double* ops, int nb) {
+template <class EL, bool ACC, class T, class OT>
+__device__ __forceinline__ void vol_integrate(int k, const T* in, T* out, T* t1, T* t2, const OT* ops, int nb) {
   if constexpr (EL::TENSOR) {
     constexpr int N1 = EL::N1, NQ = EL::NQ;
-    const double* B = ops + EL::OB;
-    const double* D = ops + EL::OD;
+    const OT* B = ops + EL::OB;
+    const OT* D = ops + EL::OD;
     if constexpr (EL::DIM == 2) {
       contract<0, NQ, NQ, 1, N1, true, false>(in, t1, k == 0 ? D : B, nb);
       __syncthreads();
@@ -202,15 +213,15 @@ __device__ __forceinline__ void vol_integrate(int k, const T* in, T* out, T* t1,
       contract<2, N1, N1, NQ, N1, true, ACC>(t2, out, k == 2 ? D : B, nb);
     }
   } else {
-    const double* M = ops + (k == 0 ? EL::ODR : (k == 1 ? EL::ODS : EL::OB));
+    const OT* M = ops + (k == 0 ? EL::ODR : (k == 1 ? EL::ODS : EL::OB));
     matvec<EL::NPE, EL::NQV, true, ACC>(in, out, M, nb);
   }
 }
 // reference derivative along axis k at the nodes (collocation): [nb][NPE] -> [nb][NPE]
-template <class EL, class T> __device__ __forceinline__ void nodal_deriv(int k, const T* in, T* out, const double* ops, int nb) {
+template <class EL, class T, class OT> __device__ __forceinline__ void nodal_deriv(int k, const T* in, T* out, const OT* ops, int nb) {
   if constexpr (EL::TENSOR) {
     constexpr int N1 = EL::N1;
-    const double* Dn = ops + EL::ODN;
+    const OT* Dn = ops + EL::ODN;
     if constexpr (EL::DIM == 2) {
       if (k == 0) contract<0, N1, N1, 1, N1, false, false>(in, out, Dn, nb);
       else contract<1, N1, N1, 1, N1, false, false>(in, out, Dn, nb);
@@ -224,10 +235,10 @@ template <class EL, class T> __device__ __forceinline__ void nodal_deriv(int k, 
   }
 }
 // reference mass inverse: [nb][NPE] -> [nb][NPE] (in is overwritten for tensor elements)
-template <class EL, class T> __device__ __forceinline__ void mass_inv(T* in, T* out, const double* ops, int nb) {
+template <class EL, class T, class OT> __device__ __forceinline__ void mass_inv(T* in, T* out, const OT* ops, int nb) {
   if constexpr (EL::TENSOR) {
     constexpr int N1 = EL::N1;
-    const double* Mi = ops + EL::OMI;
+    const OT* Mi = ops + EL::OMI;
     if constexpr (EL::DIM == 2) {
       contract<0, N1, N1, 1, N1, false, false>(in, out, Mi, nb);
       __syncthreads();
@@ -251,16 +262,21 @@ template <class EL> struct Sizes {
   static constexpr int MF = EL::TENSOR ? EL::NQ * EL::N1 : 1;
 };
 
+template <class R> __device__ __forceinline__ const R* ops_of(const KArgs& a) {
+  if constexpr (sizeof(R) == 8) return (const R*)a.ops;
+  else return (const R*)a.opsf;
+}
+
 // ===================================================================== q-stage
 template <class EL, class MD, class R> struct QLayout {
   static constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF;
   static constexpr int GEO = Geo<DIM>::size(NF);
   // bytes per element of each array
-  static constexpr int B_GEO = al16(GEO * 8), B_U = al16(NCU * EL::NPE * sizeof(R)),
+  static constexpr int B_GEO = al16(GEO * sizeof(R)), B_U = al16(NCU * EL::NPE * sizeof(R)),
                        B_LF = al16(NF * NCU * EL::NFN * sizeof(R));
   static constexpr int B_FN = al16(NF * NCU * EL::NFN * sizeof(R)), B_FT = al16(NF * NCU * Sizes<EL>::MF * sizeof(R)),
                        B_TR = al16(NF * NCU * EL::NFQ * sizeof(R));
-  static constexpr int PHASE_F = 2 * B_FN + 2 * B_TR + 2 * B_FT;   // FNm, FNp, TRm(->Fq), TRp, tmp, tmpL
+  static constexpr int PHASE_F = 2 * B_FN + 2 * B_TR + 2 * B_FT;   // FNm, FNp, TRm, TRp, tmp
   static constexpr int B_V = al16(NCU * DIM * EL::NPE * sizeof(R));
   static constexpr int PHASE_V = 3 * B_V;                           // grad, b, scratch
   static constexpr int PER_ELEM = B_GEO + B_U + B_LF + (PHASE_F > PHASE_V ? PHASE_F : PHASE_V);
@@ -274,18 +290,20 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
   typedef QLayout<EL, MD, R> L;
   constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ;
   constexpr int NE = L::NE, GEO = L::GEO;
+  if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int e0 = blockIdx.x * NE;
   const int ne = min(NE, a.E - e0);
-  double* Gs = (double*)smem;
+  const R* OPS = ops_of<R>(a);
+  R* Gs = (R*)smem;
   R* Us = (R*)(smem + NE * L::B_GEO);
   R* LF = (R*)(smem + NE * (L::B_GEO + L::B_U));
   unsigned char* arena = smem + NE * (L::B_GEO + L::B_U + L::B_LF);
-  const R* u = (const R*)a.u;
+  const double* u = (const double*)a.u;
 
-  for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = a.geo[(size_t)e0 * GEO + i];
+  for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = R(a.geo[(size_t)e0 * GEO + i]);
   for (int i = threadIdx.x; i < NE * NCU * NPE; i += blockDim.x)
-    Us[i] = i < ne * NCU * NPE ? u[(size_t)e0 * NCU * NPE + i] : R(0);
+    Us[i] = i < ne * NCU * NPE ? R(u[(size_t)e0 * NCU * NPE + i]) : R(0);
   __syncthreads();
 
   // ---- faces: traces of u on both sides, (u- - uhat) weighted, lifted to face nodes
@@ -302,16 +320,16 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
       int nb = a.nbr[(size_t)(e0 + e) * NF + f];
       if (nb >= 0) {
         int nf = a.nbf[(size_t)(e0 + e) * NF + f] & 7;
-        vp = u[((size_t)nb * NCU + c) * NPE + EL::face_node(nf, j)];
+        vp = R(u[((size_t)nb * NCU + c) * NPE + EL::face_node(nf, j)]);
       }
     }
     FNm[it] = vm;
     FNp[it] = vp;
   }
   __syncthreads();
-  face_trace<EL>(FNm, TRm, TMP, a.ops, NE * NF * NCU);
+  face_trace<EL>(FNm, TRm, TMP, OPS, NE * NF * NCU);
   __syncthreads();
-  face_trace<EL>(FNp, TRp, TMP, a.ops, NE * NF * NCU);
+  face_trace<EL>(FNp, TRp, TMP, OPS, NE * NF * NCU);
   __syncthreads();
   for (int it = threadIdx.x; it < NE * NF * NFQ; it += blockDim.x) {
     int k = it % NFQ, f = (it / NFQ) % NF, e = it / (NFQ * NF);
@@ -319,8 +337,8 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
       for (int c = 0; c < NCU; ++c) TRm[((e * NF + f) * NCU + c) * NFQ + k] = R(0);
       continue;
     }
-    const double* g = Gs + e * GEO;
-    double w = face_w<EL>(a.ops, k) * g[Geo<DIM>::FACE + f * (DIM + 1) + DIM];
+    const R* g = Gs + e * GEO;
+    const R w = face_w<EL>(OPS, k) * g[Geo<DIM>::FACE + f * (DIM + 1) + DIM];
     int nb = a.nbr[(size_t)(e0 + e) * NF + f];
     double gb[4] = {0.0, 0.0, 0.0, 0.0};
     int kp = k;
@@ -328,8 +346,9 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
       int code = a.nbf[(size_t)(e0 + e) * NF + f] >> 3;
       kp = a.perm[code * NFQ + k];
     } else if (MODE == MODE_R) {
-      double xi[3], x[3];
-      face_xi<EL>(a.ops, f, k, xi);
+      R xi[3];
+      double x[3];
+      face_xi<EL>(OPS, f, k, xi);
       phys_x<DIM>(g, xi, x);
       exact_state<DIM>(a.mp, NCU, x, a.t, gb);
     }
@@ -338,39 +357,39 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
       R um = TRm[base + k];
       R uh = nb >= 0 ? (um + TRp[base + kp]) * R(0.5) : R(gb[c]);
       // TRm is overwritten in place: only this thread reads entry (e,f,c,k)
-      TRm[base + k] = (um - uh) * R(w);
+      TRm[base + k] = (um - uh) * w;
     }
   }
   __syncthreads();
-  face_lift<EL>(TRm, LF, TMP, a.ops, NE * NF * NCU);
+  face_lift<EL>(TRm, LF, TMP, OPS, NE * NF * NCU);
   __syncthreads();
 
   // ---- volume: q_d = -sum_k Jinv[k][d] D_k u + (1/detJ) M^{-1} sum_f n_d lift_f
   R* GR = (R*)arena;                          // [DIM][NE][NCU][NPE]
   R* BV = (R*)(arena + NE * L::B_V);          // [NE][NCU][DIM][NPE]
   R* SC = (R*)(arena + 2 * NE * L::B_V);
-  for (int k = 0; k < DIM; ++k) nodal_deriv<EL>(k, Us, GR + k * NE * NCU * NPE, a.ops, NE * NCU);
+  for (int k = 0; k < DIM; ++k) nodal_deriv<EL>(k, Us, GR + k * NE * NCU * NPE, OPS, NE * NCU);
   for (int it = threadIdx.x; it < NE * NCU * DIM * NPE; it += blockDim.x) {
     int n = it % NPE, d = (it / NPE) % DIM, c = (it / (NPE * DIM)) % NCU, e = it / (NPE * DIM * NCU);
     R s = R(0);
     if (e < ne) {
-      const double* g = Gs + e * GEO;
+      const R* g = Gs + e * GEO;
       for_node_faces<EL>(n, [&](int f, int j) {
-        s += LF[((e * NF + f) * NCU + c) * NFN + j] * R(g[Geo<DIM>::FACE + f * (DIM + 1) + d]);
+        s += LF[((e * NF + f) * NCU + c) * NFN + j] * g[Geo<DIM>::FACE + f * (DIM + 1) + d];
       });
     }
     BV[it] = s;
   }
   __syncthreads();
-  mass_inv<EL>(BV, SC, a.ops, NE * NCU * DIM);
+  mass_inv<EL>(BV, SC, OPS, NE * NCU * DIM);
   __syncthreads();
-  R* qo = (R*)a.out;
+  double* qo = (double*)a.out;
   for (int it = threadIdx.x; it < ne * NCU * DIM * NPE; it += blockDim.x) {
     int n = it % NPE, d = (it / NPE) % DIM, c = (it / (NPE * DIM)) % NCU, e = it / (NPE * DIM * NCU);
-    const double* g = Gs + e * GEO;
-    R s = SC[it] * R(1.0 / g[Geo<DIM>::DETJ]);
-    for (int k = 0; k < DIM; ++k) s -= GR[(k * NE * NCU + e * NCU + c) * NPE + n] * R(g[Geo<DIM>::JINV + k * DIM + d]);
-    qo[(size_t)e0 * NCU * DIM * NPE + it] = s;
+    const R* g = Gs + e * GEO;
+    R s = SC[it] / g[Geo<DIM>::DETJ];
+    for (int k = 0; k < DIM; ++k) s -= GR[(k * NE * NCU + e * NCU + c) * NPE + n] * g[Geo<DIM>::JINV + k * DIM + d];
+    qo[(size_t)e0 * NCU * DIM * NPE + it] = (double)s;
   }
 }
 
@@ -380,7 +399,7 @@ template <class EL, class MD, int MODE, class R> struct RLayout {
   static constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF;
   static constexpr int NCV = NCU * (1 + (MD::HASQ ? DIM : 0));      // u and q fields
   static constexpr int GEO = Geo<DIM>::size(NF);
-  static constexpr int B_GEO = al16(GEO * 8), B_X = al16(NCV * EL::NPE * sizeof(S)),
+  static constexpr int B_GEO = al16(GEO * sizeof(R)), B_X = al16(NCV * EL::NPE * sizeof(S)),
                        B_LF = al16(NF * NCU * EL::NFN * sizeof(R));
   // face phase
   static constexpr int B_FN = al16(NF * NCV * EL::NFN * sizeof(S)), B_FT = al16(NF * NCV * Sizes<EL>::MF * sizeof(S)),
@@ -401,31 +420,35 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
   typedef RLayout<EL, MD, MODE, R> L;
   typedef typename L::S S;
   constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ, NQV = EL::NQV;
-  constexpr int NE = L::NE, GEO = L::GEO, NCV = L::NCV, M = Sizes<EL>::M;
+  constexpr int NE = L::NE, GEO = L::GEO, NCV = L::NCV;
   constexpr bool HASQ = MD::HASQ;
   static_assert(!(MODE == MODE_JV && HASQ), "dual-number J.v is for models without q");
+  if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int e0 = blockIdx.x * NE;
   const int ne = min(NE, a.E - e0);
-  double* Gs = (double*)smem;
+  const R* OPS = ops_of<R>(a);
+  const MPar<R> mp = mpar<R>(a.mp);
+  R* Gs = (R*)smem;
   S* X = (S*)(smem + NE * L::B_GEO);                       // [NE][NCV][NPE]
   R* LF = (R*)(smem + NE * (L::B_GEO + L::B_X));           // [NE][NF][NCU][NFN]
   unsigned char* arena = smem + NE * (L::B_GEO + L::B_X + L::B_LF);
-  const R* u = (const R*)a.u;
-  const R* v = (const R*)a.v;
-  const R* q = (const R*)a.q;
+  const double* u = (const double*)a.u;
+  const double* v = (const double*)a.v;
+  const double* q = (const double*)a.q;
 
-  for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = a.geo[(size_t)e0 * GEO + i];
+  for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = R(a.geo[(size_t)e0 * GEO + i]);
   for (int i = threadIdx.x; i < NE * NCV * NPE; i += blockDim.x) {
     int n = i % NPE, fld = (i / NPE) % NCV, e = i / (NPE * NCV);
     S val = S(R(0));
     if (e < ne) {
       if (fld < NCU) {
         size_t gi = ((size_t)(e0 + e) * NCU + fld) * NPE + n;
-        if constexpr (MODE == MODE_JV) val = S(u[gi], v[gi]);
-        else val = S(u[gi]);
+        if constexpr (MODE == MODE_JV)
+          val = S(R(u[gi]), a.blk_col >= 0 ? R(fld * NPE + n == a.blk_col ? 1 : 0) : R(v[gi]));
+        else val = S(R(u[gi]));
       } else {
-        if constexpr (HASQ) val = S(q[((size_t)(e0 + e) * NCU * DIM + (fld - NCU)) * NPE + n]);
+        if constexpr (HASQ) val = S(R(q[((size_t)(e0 + e) * NCU * DIM + (fld - NCU)) * NPE + n]));
       }
     }
     X[i] = val;
@@ -451,10 +474,10 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
           int nn = EL::face_node(nfc, j);
           if (fld < NCU) {
             size_t gi = ((size_t)nb * NCU + fld) * NPE + nn;
-            if constexpr (MODE == MODE_JV) vp = S(u[gi], v[gi]);
-            else vp = S(u[gi]);
+            if constexpr (MODE == MODE_JV) vp = S(R(u[gi]), a.blk_col >= 0 ? R(0) : R(v[gi]));
+            else vp = S(R(u[gi]));
           } else {
-            if constexpr (HASQ) vp = S(q[((size_t)nb * NCU * DIM + (fld - NCU)) * NPE + nn]);
+            if constexpr (HASQ) vp = S(R(q[((size_t)nb * NCU * DIM + (fld - NCU)) * NPE + nn]));
           }
         }
       }
@@ -462,9 +485,9 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
       FNp[it] = vp;
     }
     __syncthreads();
-    face_trace<EL>(FNm, TRm, TMP, a.ops, NE * NF * NCV);
+    face_trace<EL>(FNm, TRm, TMP, OPS, NE * NF * NCV);
     __syncthreads();
-    face_trace<EL>(FNp, TRp, TMP, a.ops, NE * NF * NCV);
+    face_trace<EL>(FNp, TRp, TMP, OPS, NE * NF * NCV);
     __syncthreads();
     for (int it = threadIdx.x; it < NE * NF * NFQ; it += blockDim.x) {
       int k = it % NFQ, f = (it / NFQ) % NF, e = it / (NFQ * NF);
@@ -472,9 +495,9 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
         for (int c = 0; c < NCU; ++c) FH[((e * NF + f) * NCU + c) * NFQ + k] = R(0);
         continue;
       }
-      const double* g = Gs + e * GEO;
-      const double* nrm = g + Geo<DIM>::FACE + f * (DIM + 1);
-      double w = face_w<EL>(a.ops, k) * nrm[DIM];
+      const R* g = Gs + e * GEO;
+      const R* nrm = g + Geo<DIM>::FACE + f * (DIM + 1);
+      const R w = face_w<EL>(OPS, k) * nrm[DIM];
       int nb = a.nbr[(size_t)(e0 + e) * NF + f];
       S um[NCU], qm[NCU * DIM + 1], fh[NCU];
       for (int fld = 0; fld < NCV; ++fld) {
@@ -488,21 +511,23 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
           S val = TRp[((e * NF + f) * NCV + fld) * NFQ + kp];
           if (fld < NCU) up[fld] = val; else qp[fld - NCU] = val;
         }
-        MD::fhat(um, up, qm, qp, nrm, fh, a.mp);
+        MD::fhat(um, up, qm, qp, nrm, fh, mp);
       } else {
-        double gb[4] = {0.0, 0.0, 0.0, 0.0};
+        R gb[4] = {R(0), R(0), R(0), R(0)};
         if (MODE != MODE_HOM) {
-          double xi[3], x[3];
-          face_xi<EL>(a.ops, f, k, xi);
+          R xi[3];
+          double x[3], gd[4] = {0.0, 0.0, 0.0, 0.0};
+          face_xi<EL>(OPS, f, k, xi);
           phys_x<DIM>(g, xi, x);
-          exact_state<DIM>(a.mp, NCU, x, a.t, gb);
+          exact_state<DIM>(a.mp, NCU, x, a.t, gd);
+          for (int c = 0; c < 4; ++c) gb[c] = R(gd[c]);
         }
-        MD::fhat_bnd(um, qm, gb, nrm, fh, a.mp);
+        MD::fhat_bnd(um, qm, gb, nrm, fh, mp);
       }
-      for (int c = 0; c < NCU; ++c) FH[((e * NF + f) * NCU + c) * NFQ + k] = outp(fh[c]) * R(w);
+      for (int c = 0; c < NCU; ++c) FH[((e * NF + f) * NCU + c) * NFQ + k] = outp(fh[c]) * w;
     }
     __syncthreads();
-    face_lift<EL>(FH, LF, (R*)TMP, a.ops, NE * NF * NCU);
+    face_lift<EL>(FH, LF, (R*)TMP, OPS, NE * NF * NCU);
     __syncthreads();
   }
 
@@ -515,18 +540,17 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
   R* R1 = GK + (DIM + 1) * NE * (L::B_G / sizeof(R));
   R* R2 = R1 + NE * (L::B_G / sizeof(R));
   R* RV = R2 + NE * (L::B_G / sizeof(R));                              // [NE][NCU][NPE]
-  constexpr int GSTR = L::B_G / sizeof(R);                             // per-element stride of GK slabs
-  (void)GSTR;
-  vol_interp<EL>(X, XQ, T1, a.ops, NE * NCV);
+  vol_interp<EL>(X, XQ, T1, OPS, NE * NCV);
   const bool hist = (MODE == MODE_R) && a.hist != nullptr;
   if (hist) {
-    const R* h = (const R*)a.hist;
+    const double* h = (const double*)a.hist;
     for (int i = threadIdx.x; i < NE * NCU * NPE; i += blockDim.x)
-      HN[i] = i < ne * NCU * NPE ? h[(size_t)e0 * NCU * NPE + i] : R(0);
+      HN[i] = i < ne * NCU * NPE ? R(h[(size_t)e0 * NCU * NPE + i]) : R(0);
     __syncthreads();
-    vol_interp<EL>(HN, HQ, (R*)T1 + 0, a.ops, NE * NCU);
+    vol_interp<EL>(HN, HQ, (R*)T1, OPS, NE * NCU);
   }
   __syncthreads();
+  const R a0dt = R(a.a0dt);
   for (int it = threadIdx.x; it < NE * NQV; it += blockDim.x) {
     int qp = it % NQV, e = it / NQV;
     S uq[NCU], qq[NCU * DIM + 1], f[NCU * DIM];
@@ -534,43 +558,48 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
       S val = XQ[(e * NCV + fld) * NQV + qp];
       if (fld < NCU) uq[fld] = val; else qq[fld - NCU] = val;
     }
-    double xi[3], w;
-    vol_xi<EL>(a.ops, qp, xi, w);
-    const double* g = Gs + e * GEO;
-    double wj = w * g[Geo<DIM>::DETJ];
-    double src = 0.0;
+    R xi[3], w;
+    vol_xi<EL>(OPS, qp, xi, w);
+    const R* g = Gs + e * GEO;
+    const R wj = w * g[Geo<DIM>::DETJ];
+    R src = R(0);
     if (MODE == MODE_R && e < ne && MD::KIND != M_EULER) {
       double x[3];
       phys_x<DIM>(g, xi, x);
-      src = source_term<DIM>(a.mp, MD::KIND == M_CONVDIFF, x);
+      src = R(source_term<DIM>(a.mp, MD::KIND == M_CONVDIFF, x));
     }
-    MD::flux(uq, qq, f, a.mp);
+    MD::flux(uq, qq, f, mp);
     for (int c = 0; c < NCU; ++c) {
       for (int k = 0; k < DIM; ++k) {
         R s = R(0);
-        for (int d = 0; d < DIM; ++d) s += outp(f[c * DIM + d]) * R(g[Geo<DIM>::JINV + k * DIM + d]);
-        GK[((k + 1) * NE * NCU + e * NCU + c) * NQV + qp] = (e < ne) ? -s * R(wj) : R(0);
+        for (int d = 0; d < DIM; ++d) s += outp(f[c * DIM + d]) * g[Geo<DIM>::JINV + k * DIM + d];
+        GK[((k + 1) * NE * NCU + e * NCU + c) * NQV + qp] = (e < ne) ? -s * wj : R(0);
       }
-      R tt = outp(uq[c]) * R(a.a0dt);
+      R tt = outp(uq[c]) * a0dt;
       if (hist) tt += HQ[(e * NCU + c) * NQV + qp];
-      GK[(e * NCU + c) * NQV + qp] = (e < ne) ? (tt - R(src)) * R(wj) : R(0);
+      GK[(e * NCU + c) * NQV + qp] = (e < ne) ? (tt - src) * wj : R(0);
     }
   }
   __syncthreads();
   // slab 0: time/source term with the plain basis; slabs 1..DIM: flux with derivative along k
-  vol_integrate<EL, false>(DIM, GK, RV, R1, R2, a.ops, NE * NCU);
+  vol_integrate<EL, false>(DIM, GK, RV, R1, R2, OPS, NE * NCU);
   __syncthreads();
   for (int k = 0; k < DIM; ++k) {
-    vol_integrate<EL, true>(k, GK + (k + 1) * NE * NCU * NQV, RV, R1, R2, a.ops, NE * NCU);
+    vol_integrate<EL, true>(k, GK + (k + 1) * NE * NCU * NQV, RV, R1, R2, OPS, NE * NCU);
     __syncthreads();
   }
   // ---- gather face moments and store
-  R* out = (R*)a.out;
+  double* out = (double*)a.out;
   for (int it = threadIdx.x; it < ne * NCU * NPE; it += blockDim.x) {
     int n = it % NPE, c = (it / NPE) % NCU, e = it / (NPE * NCU);
     R s = RV[it];
     for_node_faces<EL>(n, [&](int f, int j) { s += LF[((e * NF + f) * NCU + c) * NFN + j]; });
-    out[(size_t)e0 * NCU * NPE + it] = s;
+    if (MODE == MODE_JV && a.blk_col >= 0) {
+      constexpr int NLOC = NCU * NPE;
+      a.blk_out[((size_t)(e0 + e) * NLOC + a.blk_col) * NLOC + (it - e * NLOC)] = (double)s;
+    } else {
+      out[(size_t)e0 * NCU * NPE + it] = (double)s;
+    }
   }
 }
 

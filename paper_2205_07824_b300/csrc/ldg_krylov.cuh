@@ -1,0 +1,228 @@
+// Device kernels of the restarted GMRES(m) solve (Section 3.3): FP64 dot
+// products, vector updates, Givens rotations and the triangular solve.
+//
+// Every grid-wide reduction is finished by the last block to arrive (threadfence
+// + atomic ticket), which sums the per-block partials in block order, so results
+// are deterministic and no separate reduction launch is needed. Each kernel
+// returns at once when the solve's `done` flag is set, so the host can queue
+// Arnoldi steps ahead of the GPU without waiting for the convergence test.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ldg {
+
+constexpr int KRY_T = 256;
+
+// Layout of the small FP64 work area of one GMRES(m) solve.
+struct KrySmall {
+  int m;
+  __host__ __device__ size_t H() const { return 0; }                      // (m+1) x m, column-major
+  __host__ __device__ size_t cs() const { return (size_t)(m + 1) * m; }
+  __host__ __device__ size_t sn() const { return cs() + m; }
+  __host__ __device__ size_t g() const { return sn() + m; }               // m+1
+  __host__ __device__ size_t y() const { return g() + m + 1; }            // m
+  __host__ __device__ size_t h1() const { return y() + m; }               // m+2
+  __host__ __device__ size_t h2() const { return h1() + m + 2; }          // m+2
+  __host__ __device__ size_t sc() const { return h2() + m + 2; }          // 16 scalars
+  __host__ __device__ size_t total() const { return sc() + 16; }
+};
+// scalars sc[]: 0 ||w||^2 (last norm), 1 |g_{j+1}|, 2 h_{j+1,j}, 3 convergence threshold,
+//               4 ||r||^2 (true residual), 5 spare, 6 -1.0 (axpy coefficient)
+// int flags[]: 0 done, 1 number of Arnoldi columns, 2 breakdown
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduce `NV` accumulators into part[blockIdx.x][k]; returns true in the
+// last block (after all partials are visible).
+template <int NV>
+__device__ __forceinline__ bool block_partials(double (&acc)[NV], int nvec, double* part, int ldp,
+                                               unsigned int* ticket) {
+  __shared__ double red[KRY_T / 32][NV];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double v = warp_sum(acc[k]);
+    if (lane == 0) red[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nvec) {
+    double s = 0.0;
+    for (int q = 0; q < KRY_T / 32; ++q) s += red[q][threadIdx.x];
+    part[(size_t)blockIdx.x * ldp + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return last;
+}
+
+// Sum of column k of the partials, in block order (called by the last block).
+__device__ __forceinline__ double sum_partials(const double* part, int ldp, int k) {
+  double s = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(part + (size_t)b * ldp + k);
+  return s;
+}
+
+// out[k] = sum_i V[k][i] w[i] for k < nvec (NV >= nvec).
+template <int NV>
+__global__ void __launch_bounds__(KRY_T) k_dots(const double* __restrict__ V, int64_t ldv, int nvec,
+                                               const double* __restrict__ w, int64_t n, double* part, int ldp,
+                                               unsigned int* ticket, double* out, const int* flags) {
+  if (flags && flags[0]) return;
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)KRY_T + threadIdx.x; i < n; i += (int64_t)gridDim.x * KRY_T) {
+    const double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+      if (k < nvec) acc[k] = fma(V[k * ldv + i], wi, acc[k]);
+  }
+  if (!block_partials<NV>(acc, nvec, part, ldp, ticket)) return;
+  if (threadIdx.x < nvec) out[threadIdx.x] = sum_partials(part, ldp, threadIdx.x);
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// w -= sum_k V[k] h[k]. With `givens`, also forms ||w||^2 and the last block
+// completes Arnoldi column j: H(:, j) = h1 + h2, H(j+1, j) = ||w||, applies the
+// previous rotations, forms rotation j, rotates g and sets the done flag when
+// |g_{j+1}| <= sc[3] or on breakdown.
+__global__ void __launch_bounds__(KRY_T) k_orth_update(const double* __restrict__ V, int64_t ldv, int nvec,
+                                                      const double* __restrict__ h, double* __restrict__ w,
+                                                      int64_t n, double* part, int ldp, unsigned int* ticket,
+                                                      double* small, int m, int j, int givens, int* flags) {
+  if (flags[0]) return;
+  __shared__ double hs[32];
+  if (threadIdx.x < nvec) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)KRY_T + threadIdx.x; i < n; i += (int64_t)gridDim.x * KRY_T) {
+    double s = w[i];
+    for (int k = 0; k < nvec; ++k) s = fma(-V[k * ldv + i], hs[k], s);
+    w[i] = s;
+    acc[0] = fma(s, s, acc[0]);
+  }
+  if (!givens) return;
+  if (!block_partials<1>(acc, 1, part, ldp, ticket)) return;
+  if (threadIdx.x != 0) return;
+  *ticket = 0u;
+  KrySmall S{m};
+  double* H = small + S.H();
+  double* cs = small + S.cs();
+  double* sn = small + S.sn();
+  double* g = small + S.g();
+  const double* h1 = small + S.h1();
+  const double* h2 = small + S.h2();
+  double* sc = small + S.sc();
+  const double nrm2 = sum_partials(part, ldp, 0);
+  const double hn = sqrt(nrm2);
+  sc[0] = nrm2;
+  double* col = H + (size_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = col[i], b = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * b;
+    col[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = col[j], b = col[j + 1];
+  const double den = sqrt(a * a + b * b);
+  cs[j] = den > 0.0 ? a / den : 1.0;
+  sn[j] = den > 0.0 ? b / den : 0.0;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  const double est = fabs(g[j + 1]);
+  sc[1] = est;
+  sc[2] = hn;
+  flags[1] = j + 1;
+  const bool breakdown = !(hn > 1e-14 * den);
+  if (!(est > sc[3]) || breakdown) flags[0] = 1;   // NaN also ends the cycle
+  if (breakdown) flags[2] = 1;
+}
+
+// out = in / sqrt(sc[0])
+__global__ void k_scale_by_norm(const double* in, const double* small_sc, double* out, int64_t n, const int* flags) {
+  if (flags && flags[0]) return;
+  const double s = sqrt(small_sc[0]);
+  const double f = s > 0.0 ? 1.0 / s : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i] * f;
+}
+
+// Cycle start: V0 = r / ||r|| (||r||^2 in sc[4]); g = (||r||, 0, ...); flags cleared.
+__global__ void k_cycle_start(const double* r, double* V0, int64_t n, double* small, int m, int* flags) {
+  KrySmall S{m};
+  const double* sc = small + S.sc();
+  const double s = sqrt(sc[4]);
+  const double f = s > 0.0 ? 1.0 / s : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    V0[i] = r[i] * f;
+  if (blockIdx.x == 0) {
+    double* g = small + S.g();
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = i == 0 ? s : 0.0;
+    if (threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; flags[2] = 0; }
+  }
+}
+
+// y = H(0:k, 0:k)^{-1} g(0:k), k = flags[1]
+__global__ void k_backsolve(double* small, int m, const int* flags) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  KrySmall S{m};
+  const double* H = small + S.H();
+  const double* g = small + S.g();
+  double* y = small + S.y();
+  const int k = flags[1];
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int l = i + 1; l < k; ++l) s -= H[(size_t)l * (m + 1) + i] * y[l];
+    y[i] = s / H[(size_t)i * (m + 1) + i];
+  }
+}
+
+// x += sum_{k < flags[1]} V[k] y[k]
+__global__ void k_solution_update(const double* __restrict__ V, int64_t ldv, const double* small, int m,
+                                  const int* flags, double* __restrict__ x, int64_t n) {
+  __shared__ double ys[32];
+  KrySmall S{m};
+  const int k = flags[1];
+  if (threadIdx.x < k) ys[threadIdx.x] = small[S.y() + threadIdx.x];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = x[i];
+    for (int l = 0; l < k; ++l) s = fma(V[l * ldv + i], ys[l], s);
+    x[i] = s;
+  }
+}
+
+// r = b - a and ||r||^2 -> *out
+__global__ void __launch_bounds__(KRY_T) k_sub_norm(const double* __restrict__ b, const double* __restrict__ a,
+                                                   double* __restrict__ r, int64_t n, double* part, int ldp,
+                                                   unsigned int* ticket, double* out) {
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)KRY_T + threadIdx.x; i < n; i += (int64_t)gridDim.x * KRY_T) {
+    const double s = b[i] - a[i];
+    r[i] = s;
+    acc[0] = fma(s, s, acc[0]);
+  }
+  if (!block_partials<1>(acc, 1, part, ldp, ticket)) return;
+  if (threadIdx.x == 0) {
+    *out = sum_partials(part, ldp, 0);
+    *ticket = 0u;
+  }
+}
+
+// x += alpha * y with alpha read from device memory
+__global__ void k_axpy_dev(const double* __restrict__ y, const double* alpha, double* __restrict__ x, int64_t n) {
+  const double a = *alpha;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = fma(a, y[i], x[i]);
+}
+
+}  // namespace ldg

@@ -19,6 +19,8 @@ TRI, QUAD, HEX = 0, 1, 2
 POISSON, CONVDIFF, EULER = 0, 1, 2
 CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST = range(7)
 STEADY, BDF1, BDF2 = 0, 1, 2
+FP64, FP32 = 0, 1
+PC_NONE, PC_BJACOBI = 0, 1
 STATUS = {0: "LDG_OK", -1: "LDG_ERR_ARG", -2: "LDG_ERR_CUDA", -3: "LDG_ERR_UNSUPPORTED",
           -4: "LDG_ERR_NONFINITE", -5: "LDG_ERR_MAXIT", -6: "LDG_ERR_MESH"}
 
@@ -41,13 +43,15 @@ class _Model(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("nq1", ctypes.c_int), ("gmres_m", ctypes.c_int), ("max_restarts", ctypes.c_int),
-                ("max_newton", ctypes.c_int), ("newton_rtol", ctypes.c_double), ("gmres_rtol", ctypes.c_double)]
+                ("max_newton", ctypes.c_int), ("newton_rtol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
+                ("krylov_precision", ctypes.c_int), ("precond", ctypes.c_int), ("pc_refresh", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("gmres_iters", ctypes.c_int), ("jv_calls", ctypes.c_int),
                 ("residual_calls", ctypes.c_int), ("r0", ctypes.c_double), ("rfinal", ctypes.c_double),
-                ("lin_resid", ctypes.c_double), ("elapsed_ms", ctypes.c_double), ("status", ctypes.c_int)]
+                ("lin_resid", ctypes.c_double), ("elapsed_ms", ctypes.c_double), ("status", ctypes.c_int),
+                ("pc_setups", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -78,6 +82,10 @@ def lib():
         L.ldg_residual.argtypes = [vp, dp, dp]
         L.ldg_jvp.argtypes = [vp, dp, dp, dp]
         L.ldg_jvp_noalloc.argtypes = [vp, dp, dp, dp]
+        L.ldg_jvp_prec.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+        L.ldg_diag_blocks.argtypes = [vp, ctypes.c_int, dp, dp]
+        L.ldg_precond_setup.argtypes = [vp, dp]
+        L.ldg_precond_apply.argtypes = [vp, dp, dp]
         L.ldg_q.argtypes = [vp, dp, dp]
         L.ldg_interpolate.argtypes = [vp, ctypes.c_double, dp]
         L.ldg_gmres.argtypes = [vp, dp, dp, dp, ctypes.POINTER(SolveReport)]
@@ -106,7 +114,8 @@ class LDG:
 
     def __init__(self, mesh, p: int, model: int, case: int, mu=(), nq1: int = 0, gmres_m: int = 30,
                  max_restarts: int = 50, max_newton: int = 20, newton_rtol: float = 1e-8,
-                 gmres_rtol: float = 1e-3, stream=None):
+                 gmres_rtol: float = 1e-3, krylov_precision: int = 0, precond: int = 0, pc_refresh: int = 0,
+                 stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("LDG needs a CUDA device (no CPU fallback)")
@@ -118,7 +127,8 @@ class LDG:
                    self._vid.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
         mo = _Model(model, case, len(self._mu),
                     self._mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(self._mu) else None)
-        op = _Options(nq1, gmres_m, max_restarts, max_newton, newton_rtol, gmres_rtol)
+        op = _Options(nq1, gmres_m, max_restarts, max_newton, newton_rtol, gmres_rtol, krylov_precision, precond,
+                      pc_refresh)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -165,6 +175,29 @@ class LDG:
         out = self.empty() if out is None else out
         n = self.n_dof
         self._check(lib().ldg_jvp(self._h, _ptr(u, n, "u"), _ptr(v, n, "v"), _ptr(out, n, "out")))
+        return out
+
+    def jvp_prec(self, precision: int, u, v, out=None):
+        """J.v in FP64 (precision 0) or FP32 arithmetic (precision 1); FP64 in memory."""
+        out = self.empty() if out is None else out
+        n = self.n_dof
+        self._check(lib().ldg_jvp_prec(self._h, precision, _ptr(u, n, "u"), _ptr(v, n, "v"), _ptr(out, n, "out")))
+        return out
+
+    def diag_blocks(self, u, precision: int = 0, out=None):
+        """Exact element-diagonal blocks of J(u), [n_elem][n_loc][n_loc] column-major per element."""
+        nloc = self.n_cu * self.n_pe
+        out = self.empty(self.n_elem * nloc * nloc) if out is None else out
+        self._check(lib().ldg_diag_blocks(self._h, precision, _ptr(u, self.n_dof, "u"),
+                                          _ptr(out, self.n_elem * nloc * nloc, "out")))
+        return out
+
+    def precond_setup(self, u):
+        self._check(lib().ldg_precond_setup(self._h, _ptr(u, self.n_dof, "u")))
+
+    def precond_apply(self, x, out=None):
+        out = self.empty() if out is None else out
+        self._check(lib().ldg_precond_apply(self._h, _ptr(x, self.n_dof, "x"), _ptr(out, self.n_dof, "out")))
         return out
 
     def jvp_noalloc(self, u, v, out):
