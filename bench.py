@@ -4,13 +4,16 @@
 Workload: periodic [0,10]^2, 64 x 64 affine quadrilaterals, p = 3 (Gauss-Lobatto
 nodes, 5 x 5 Gauss points), local Lax-Friedrichs flux, BDF2 with dt = 0.05.
 One *step* is one implicit BDF2 time step: matrix-free Newton-GMRES (Section 3.3)
-from u^n until ||R(u)||_2 <= 1e-8 ||R(u^n)||_2, every J.v exact (dual numbers),
-Arnoldi with two-pass classical Gram-Schmidt and Givens rotations, all in FP64
-on the GPU. The L2 cache is flushed (a 256 MiB write) before every timed step,
-outside the step's event window.
+from u^n until ||R(u)||_2 <= 1e-8 ||R(u^n)||_2 in FP64, every J.v exact (dual
+numbers), Arnoldi with two-pass classical Gram-Schmidt and Givens rotations in
+FP64. The default form is the mixed one: the Krylov J.v and the block-Jacobi
+preconditioner in FP32 arithmetic (FP64 in memory); the plain FP64 block-Jacobi
+form is timed in the same run for comparison. The L2 cache is flushed (a 256 MiB
+write) before every timed step, outside the step's event window.
 
-Metric: J.v GDOF/s = (DOFs x J.v applications) / step time, over the K timed
-steps; ms_per_step is the Newton-GMRES time to 1e-8 per implicit step.
+Metric: J.v GDOF/s = (DOFs x J.v applications of the whole solve) / step time,
+over the K timed steps; ms_per_step is the Newton-GMRES time to 1e-8 per
+implicit step.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 With N > 1 (torchrun), every rank advances its own vortex instance (weak scaling,
@@ -34,13 +37,16 @@ METRIC = "J·v GDOF/s (%HBM roofline); Newton-GMRES time-to-1e-8, learned+mixed 
 UNIT = "GDOF/s"
 WORKLOAD = ("2D compressible Euler isentropic vortex (gamma 1.4, strength 5, centre (5,5)), periodic "
             "[0,10]^2, 64x64 quads, p=3, Lax-Friedrichs flux, BDF2 dt=0.05, matrix-free Newton-GMRES(30) "
-            "to 1e-8, FP64")
+            "to 1e-8 (FP64 residual)")
 N_SIDE, P, DT = 64, 3, 0.05
-# FP64 FLOPs per element of one J.v launch, counted by ncu (2*DFMA + DADD + DMUL thread
-# instructions of the dual-number Euler kernel, p = 3, 5 x 5 Gauss points).
-JV_FLOP_PER_ELEM = None
-# FP64 peak derived from the unit counts: 148 SMs x 2 FP64 FMA/clock/SM x 2 FLOP x 2.032 GHz.
+# FLOPs per element of one J.v launch (dual-number Euler kernel, p = 3, 5 x 5 Gauss points),
+# counted by ncu as 2*FMA + ADD + MUL thread instructions: FP64 instance (index 0) and
+# FP32 instance (index 1); see profiles/.
+JV_FLOP_PER_ELEM = (18449.0, 17027.0)
+# ALU peaks derived from the unit counts and the maximum SM clock (2.032 GHz):
+# FP64 148 SMs x 2 FMA/clk x 2 FLOP; FP32 148 SMs x 128 FMA/clk x 2 FLOP.
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 
 def _dist():
@@ -176,46 +182,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--jv-reps", type=int, default=50)
-    ap.add_argument("--precond", default="none", choices=["none", "bjacobi"],
-                    help="block-Jacobi: exact element-diagonal blocks, rebuilt once per implicit step")
-    ap.add_argument("--krylov", default="fp64", choices=["fp64", "fp32"],
-                    help="arithmetic of the J.v inside GMRES (Newton residual and Arnoldi stay FP64)")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        run_reference(args)
-        return
-
-    import numpy as np
+def run_mode(LDG, mesh, kprec, pc, steps, warmup, flush, stream, launches):
+    """Advance the vortex `warmup` + `steps` BDF2 steps; time the last `steps`."""
     import torch
-    import torch.distributed as dist
-    from paper_2205_07824_b300 import synth
-    from paper_2205_07824_b300.ldg import LDG, kernel_launches, BDF2, EULER, CASE_VORTEX
-
-    world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    mesh = synth.quad_box(N_SIDE, hi=(10.0, 10.0), periodic=(True, True))
-    kprec = 1 if args.krylov == "fp32" else 0
-    pc = 1 if args.precond == "bjacobi" else 0
+    from paper_2205_07824_b300.ldg import BDF2, EULER, CASE_VORTEX
     g = LDG(mesh, P, EULER, CASE_VORTEX, (1.4,), gmres_m=30, newton_rtol=1e-8, gmres_rtol=1e-3,
             krylov_precision=kprec, precond=pc)
-    n = g.n_dof
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
-
     un, unm1 = g.interpolate(0.0), g.interpolate(-DT)
     u = torch.empty_like(un)
     state = {"t": 0.0}
+    nloc = g.n_cu * g.n_pe
 
     def step():
         t1 = state["t"] + DT
@@ -227,35 +203,87 @@ def main():
         state["t"] = t1
         return rep
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    l0 = kernel_launches()
-    times, jv_calls, newton_its, gmres_its = [], 0, 0, 0
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    tot = {"jv": 0, "newton": 0, "gmres": 0, "pc": 0}
+    l0 = launches()
+    for k in range(steps):
         flush.zero_()
         ev[k][0].record(stream)
         rep = step()
         ev[k][1].record(stream)
-        jv_calls += rep["jv_calls"]
-        newton_its += rep["newton_iters"]
-        gmres_its += rep["gmres_iters"]
         assert rep["rfinal"] <= 1e-8 * rep["r0"], rep
+        tot["jv"] += rep["jv_calls"] + rep["pc_setups"] * nloc   # block extraction: one J.v per block column
+        tot["newton"] += rep["newton_iters"]
+        tot["gmres"] += rep["gmres_iters"]
+        tot["pc"] += rep["pc_setups"]
     torch.cuda.synchronize()
-    launches = kernel_launches() - l0
+    n_launch = launches() - l0
+    times = [a.elapsed_time(b) for a, b in ev]
+    return g, u, times, tot, n_launch, state["t"]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--jv-reps", type=int, default=50)
+    ap.add_argument("--precond", default="bjacobi", choices=["none", "bjacobi"],
+                    help="block-Jacobi: exact element-diagonal blocks, rebuilt once per implicit step")
+    ap.add_argument("--krylov", default="fp32", choices=["fp64", "fp32"],
+                    help="arithmetic of the J.v inside GMRES (Newton residual and Arnoldi stay FP64)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, kernel_launches, BDF2
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    mesh = synth.quad_box(N_SIDE, hi=(10.0, 10.0), periodic=(True, True))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+    kprec = 1 if args.krylov == "fp32" else 0
+    pc = 1 if args.precond == "bjacobi" else 0
+
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    g, u, times, tot, launches, t_end = run_mode(LDG, mesh, kprec, pc, args.steps, args.warmup, flush, stream,
+                                                 kernel_launches)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    times = [a.elapsed_time(b) for a, b in ev]
-    total_ms, gdofs = aggregate(times, n * jv_calls, world, rank)
+    n = g.n_dof
+    total_ms, gdofs = aggregate(times, n * tot["jv"], world, rank)
     ms_per_step = total_ms / args.steps
 
-    # J.v kernel alone (the dominant kernel), CUDA events on the launching stream
+    # the plain FP64 block-Jacobi form on the same box, same steps (the benchmark spec comparison)
+    base = None
+    if not args.no_fp64_baseline and (kprec, pc) != (0, 1):
+        gb, ub, tb, totb, _, _ = run_mode(LDG, mesh, 0, 1, args.steps, args.warmup, flush, stream, kernel_launches)
+        base = {"form": "FP64 Krylov J.v + block-Jacobi", "ms_per_step": sum(tb) / args.steps,
+                "gmres_iters_per_step": totb["gmres"] / args.steps,
+                "solution_rel_diff_vs_headline": float(torch.linalg.norm(ub - u) / torch.linalg.norm(ub))}
+        base["speedup_headline_vs_fp64_bjacobi"] = base["ms_per_step"] / ms_per_step
+        del gb
+
+    # the Krylov J.v kernel alone (the dominant kernel), CUDA events on the launching stream
     v = torch.randn(n, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
     jv = torch.empty_like(v)
     for _ in range(5):
@@ -268,27 +296,33 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     jv_ms = e0.elapsed_time(e1) / args.jv_reps
-    flop = JV_FLOP_PER_ELEM * mesh.n_elem if JV_FLOP_PER_ELEM else None
-    achieved = flop / (jv_ms * 1e-3) / 1e12 if flop else None
-    roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
-                "kernel": "k_residual<TensorEl<2,3,5>, EulerModel, MODE_JV, double>",
+    jv64 = g.jvp_prec(0, u, v)
+    jv_err = float(torch.linalg.norm(jv - jv64) / torch.linalg.norm(jv64)) if kprec else 0.0
+    fpe = JV_FLOP_PER_ELEM[kprec]
+    achieved = fpe * mesh.n_elem / (jv_ms * 1e-3) / 1e12
+    peak = FP32_PEAK_TFLOPS if kprec else FP64_PEAK_TFLOPS
+    roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "traffic": None,
+                "kernel": f"k_residual<TensorEl<2,3,5>, EulerModel, MODE_JV, {'float' if kprec else 'double'}>",
                 "launch_ms": jv_ms, "jv_gdofs_kernel": n / (jv_ms * 1e-3) / 1e9,
-                "peak_source": "FP64 ALU: 148 SMs x 2 FMA/clk x 2 FLOP x 2.032 GHz (derived)",
-                "flop_per_elem": JV_FLOP_PER_ELEM}
+                "flop_per_elem": fpe, "flop_source": "ncu thread-instruction counts (FMA x2 + ADD + MUL)",
+                "peak_source": ("FP32 ALU: 148 SMs x 128 FMA/clk x 2 FLOP x 2.032 GHz (derived)" if kprec else
+                                "FP64 ALU: 148 SMs x 2 FMA/clk x 2 FLOP x 2.032 GHz (derived)"),
+                "jv_fp32_rel_err_vs_fp64": jv_err}
 
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
         h_un = torch.empty(n, dtype=torch.float64, pin_memory=True)
         h_unm1 = torch.empty(n, dtype=torch.float64, pin_memory=True)
-        h_un.copy_(un)
-        h_unm1.copy_(unm1)
+        h_un.copy_(u)
+        h_unm1.copy_(u)
         h_u = np.empty(n, dtype=np.float64)
-        d_un, d_unm1 = torch.empty_like(un), torch.empty_like(un)
+        d_un, d_unm1 = torch.empty_like(u), torch.empty_like(u)
         k2 = min(args.steps, 5)
         t_e2e, jv_e2e = 0.0, 0
-        tt = state["t"]
+        tt = t_end
+        nloc = g.n_cu * g.n_pe
         for _ in range(k2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -298,12 +332,12 @@ def main():
             h_u[:] = h_un.numpy()
             rep = g.newton_gmres_host(h_u)
             t_e2e += time.perf_counter() - t0
-            jv_e2e += rep["jv_calls"]
+            jv_e2e += rep["jv_calls"] + rep["pc_setups"] * nloc
             h_unm1.copy_(h_un)
             h_un.copy_(torch.from_numpy(h_u))
             tt += DT
         e2e = {"value": n * jv_e2e / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": 3 * 8 * n,
-               "d2h_bytes_per_step": 8 * n, "steps": k2,
+               "d2h_bytes_per_step": 8 * n, "steps": k2, "ms_per_step": t_e2e / k2 * 1e3,
                "note": "host u^n, u^{n-1} and the initial guess copied in, the solution copied out, per step"}
 
     cpu = None
@@ -315,16 +349,20 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if kprec == 0 else "f64+f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_dof": int(n), "n_elem": int(mesh.n_elem),
+                           "value_definition": "J.v applications of the whole solve (Arnoldi, true residual, "
+                                               "block extraction) x DOF / timed step time",
                            "time_to_1e-8_ms_per_step": ms_per_step,
-                           "newton_iters_per_step": newton_its / args.steps,
-                           "gmres_iters_per_step": gmres_its / args.steps,
-                           "jv_calls_per_step": jv_calls / args.steps,
+                           "newton_iters_per_step": tot["newton"] / args.steps,
+                           "gmres_iters_per_step": tot["gmres"] / args.steps,
+                           "jv_applications_per_step": tot["jv"] / args.steps,
                            "preconditioner": "none" if not pc else
                            "block-Jacobi (exact element-diagonal blocks, built once per implicit step)",
                            "precision": "FP64 throughout" if kprec == 0 else
-                           "Krylov J.v in FP32 arithmetic; Newton residual, Arnoldi, Givens, vectors FP64",
+                           "Krylov J.v and preconditioner in FP32 arithmetic; Newton residual, Arnoldi, Givens, "
+                           "vectors FP64",
                            "l2": "flushed (256 MiB write) before each timed step, outside its event window",
-                           "parallelism": f"{world} independent instance(s), one per GPU"},
+                           "parallelism": f"{world} independent instance(s), one per GPU",
+                           "fp64_bjacobi_baseline": base},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)

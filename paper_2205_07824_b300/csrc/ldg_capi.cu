@@ -52,7 +52,8 @@ struct ldg_ctx {
   double* h_pin = nullptr;     // pinned host scalars
   int* h_flags = nullptr;      // pinned copies of the flags, one slot per Arnoldi step
   cudaEvent_t ev[64] = {};
-  int nblk = 0;
+  int nblk = 0;                // grid of streaming vector kernels
+  int nblk_d = 0;              // grid of the many-accumulator reductions (dot products)
   // block-Jacobi preconditioner
   int nloc = 0;
   std::vector<int> h_nbr;      // host copy of the face neighbours (colouring)
@@ -150,13 +151,41 @@ constexpr int LDP = 32;   // leading dimension of the reduction partials
 int dots(ldg_ctx* ctx, const double* V, int64_t ldv, int nvec, const double* w, double* out, const int* flags) {
   const int64_t n = ctx->ndof;
   if (nvec <= 1)
-    k_dots<1><<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
+    k_dots<1><<<ctx->nblk_d, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
+  else if (nvec <= 4)
+    k_dots<4><<<ctx->nblk_d, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
   else if (nvec <= 8)
-    k_dots<8><<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
+    k_dots<8><<<ctx->nblk_d, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
   else if (nvec <= 16)
-    k_dots<16><<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
+    k_dots<16><<<ctx->nblk_d, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
   else
-    k_dots<32><<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
+    k_dots<32><<<ctx->nblk_d, KRY_T, 0, ctx->stream>>>(V, ldv, nvec, w, n, ctx->d_part, LDP, ctx->d_ticket, out, flags);
+  count_launch();
+  CK(cudaGetLastError());
+  return LDG_OK;
+}
+
+// w -= V h (nvec vectors). dots_out != null: also V . w_new into dots_out (DOTS form);
+// otherwise with givens, also completes Arnoldi column j.
+template <int NV>
+void launch_orth(ldg_ctx* ctx, const double* V, int nvec, const double* h, double* w, int j, int givens,
+                 double* dots_out) {
+  const int64_t n = ctx->ndof;
+  if (dots_out)
+    k_orth_update<NV, true><<<ctx->nblk_d, KRY_T, 0, ctx->stream>>>(V, n, nvec, h, w, n, ctx->d_part, LDP,
+                                                                   ctx->d_ticket, ctx->d_small, ctx->m, j, givens,
+                                                                   ctx->d_flags, dots_out);
+  else
+    k_orth_update<NV, false><<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, n, nvec, h, w, n, ctx->d_part, LDP,
+                                                                  ctx->d_ticket, ctx->d_small, ctx->m, j, givens,
+                                                                  ctx->d_flags, nullptr);
+}
+int orth_update(ldg_ctx* ctx, const double* V, int nvec, const double* h, double* w, int j, int givens,
+                double* dots_out = nullptr) {
+  if (nvec <= 4) launch_orth<4>(ctx, V, nvec, h, w, j, givens, dots_out);
+  else if (nvec <= 8) launch_orth<8>(ctx, V, nvec, h, w, j, givens, dots_out);
+  else if (nvec <= 16) launch_orth<16>(ctx, V, nvec, h, w, j, givens, dots_out);
+  else launch_orth<32>(ctx, V, nvec, h, w, j, givens, dots_out);
   count_launch();
   CK(cudaGetLastError());
   return LDG_OK;
@@ -312,7 +341,7 @@ int do_pc_setup(ldg_ctx* ctx, const double* u) {
   if ((rc = ensure_pc_storage(ctx))) return rc;
   if ((rc = do_blocks(ctx, u, prec, ctx->d_blocks))) return rc;
   const int n = ctx->nloc;
-  const bool fp64 = prec == LDG_FP64 && (size_t)(2 * n * n + n) * sizeof(double) <= 200 * 1024;
+  const bool fp64 = prec == LDG_FP64 && block_inverse_smem<double>(n) <= 200 * 1024;
   const int want = fp64 ? LDG_FP64 : LDG_FP32;
   if (ctx->binv_prec != want) {
     cudaFree(ctx->d_binv);
@@ -320,14 +349,14 @@ int do_pc_setup(ldg_ctx* ctx, const double* u) {
     CK(cudaMalloc(&ctx->d_binv, (size_t)ctx->E * n * n * (fp64 ? sizeof(double) : sizeof(float))));
     ctx->binv_prec = want;
   }
-  const int threads = std::min(256, ((n + 31) / 32) * 32 * 2);
+  const int threads = std::min(256, ((n + 31) / 32) * 32);
   if (fp64) {
-    const size_t smem = (size_t)(2 * n * n + n) * sizeof(double);
+    const size_t smem = block_inverse_smem<double>(n);
     CK(cudaFuncSetAttribute(k_block_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_block_inverse<double><<<(unsigned)ctx->E, threads, smem, ctx->stream>>>(ctx->d_blocks, (double*)ctx->d_binv, n,
                                                                              ctx->d_status);
   } else {
-    const size_t smem = (size_t)(2 * n * n + n) * sizeof(float);
+    const size_t smem = block_inverse_smem<float>(n);
     CK(cudaFuncSetAttribute(k_block_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_block_inverse<float><<<(unsigned)ctx->E, threads, smem, ctx->stream>>>(ctx->d_blocks, (float*)ctx->d_binv, n,
                                                                             ctx->d_status);
@@ -400,13 +429,9 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
       }
       if ((rc = jvp_args(ctx, a, u, dir, w, ctx->opt.krylov_precision))) return rc;
       if ((rc = dots(ctx, V, n, j + 1, w, sm + S.h1(), flags))) return rc;
-      k_orth_update<<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, n, j + 1, sm + S.h1(), w, n, ctx->d_part, LDP,
-                                                          ctx->d_ticket, sm, m, j, 0, flags);
-      count_launch();
-      if ((rc = dots(ctx, V, n, j + 1, w, sm + S.h2(), flags))) return rc;
-      k_orth_update<<<ctx->nblk, KRY_T, 0, ctx->stream>>>(V, n, j + 1, sm + S.h2(), w, n, ctx->d_part, LDP,
-                                                          ctx->d_ticket, sm, m, j, 1, flags);
-      count_launch();
+      // pass 1 projects and forms the pass-2 projections in the same sweep
+      if ((rc = orth_update(ctx, V, j + 1, sm + S.h1(), w, j, 0, sm + S.h2()))) return rc;
+      if ((rc = orth_update(ctx, V, j + 1, sm + S.h2(), w, j, 1))) return rc;
       k_scale_by_norm<<<g1, 256, 0, ctx->stream>>>(w, sc, w, n, flags);
       count_launch();
       CK(cudaGetLastError());
@@ -607,7 +632,8 @@ int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   KrySmall S{ctx->m};
   CK(cudaMalloc(&ctx->d_small, S.total() * sizeof(double)));
   CK(cudaMemset(ctx->d_small, 0, S.total() * sizeof(double)));
-  ctx->nblk = (int)std::min<int64_t>(148 * 2, std::max<int64_t>(1, (n + 2047) / 2048));
+  ctx->nblk = (int)std::min<int64_t>(148 * 4, std::max<int64_t>(1, (n + 511) / 512));
+  ctx->nblk_d = (int)std::min<int64_t>(148, std::max<int64_t>(1, (n + 2047) / 2048));
   CK(cudaMalloc(&ctx->d_part, (size_t)ctx->nblk * LDP * sizeof(double)));
   CK(cudaMalloc(&ctx->d_flags, 8 * sizeof(int)));
   CK(cudaMemset(ctx->d_flags, 0, 8 * sizeof(int)));

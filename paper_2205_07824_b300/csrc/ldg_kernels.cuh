@@ -27,6 +27,15 @@ namespace ldg {
 
 enum { MODE_R = 0, MODE_HOM = 1, MODE_JV = 2 };
 
+// Shared-memory budget per CTA from which the number of elements per CTA (NE) is
+// derived; smaller budgets give more, smaller CTAs per SM.
+#ifndef LDG_RES_SMEM_BUDGET
+#define LDG_RES_SMEM_BUDGET (100 * 1024)
+#endif
+#ifndef LDG_Q_SMEM_BUDGET
+#define LDG_Q_SMEM_BUDGET (96 * 1024)
+#endif
+
 struct KArgs {
   const void* u;              // [E][NCU][NPE]     state (R, JV) or direction (HOM)
   const void* v;              // [E][NCU][NPE]     direction (JV)
@@ -259,7 +268,8 @@ template <class EL, class T, class OT> __device__ __forceinline__ void mass_inv(
 
 template <class EL> struct Sizes {
   static constexpr int M = (EL::TENSOR ? ipow(EL::NQ > EL::N1 ? EL::NQ : EL::N1, EL::DIM) : (EL::NQV > EL::NPE ? EL::NQV : EL::NPE));
-  static constexpr int MF = EL::TENSOR ? EL::NQ * EL::N1 : 1;
+  // face-trace temporary: only the 3-D sum factorisation needs one
+  static constexpr int MF = (EL::TENSOR && EL::DIM == 3) ? EL::NQ * EL::N1 : 1;
 };
 
 template <class R> __device__ __forceinline__ const R* ops_of(const KArgs& a) {
@@ -280,7 +290,7 @@ template <class EL, class MD, class R> struct QLayout {
   static constexpr int B_V = al16(NCU * DIM * EL::NPE * sizeof(R));
   static constexpr int PHASE_V = 3 * B_V;                           // grad, b, scratch
   static constexpr int PER_ELEM = B_GEO + B_U + B_LF + (PHASE_F > PHASE_V ? PHASE_F : PHASE_V);
-  static constexpr int NE_ = (96 * 1024) / PER_ELEM;
+  static constexpr int NE_ = LDG_Q_SMEM_BUDGET / PER_ELEM;
   static constexpr int NE = NE_ < 1 ? 1 : (NE_ > 16 ? 16 : NE_);
   static constexpr int SMEM = NE * PER_ELEM;
 };
@@ -407,10 +417,11 @@ template <class EL, class MD, int MODE, class R> struct RLayout {
   static constexpr int PHASE_F = 2 * B_FN + 2 * B_TR + B_FT + B_FH;
   // volume phase
   static constexpr int B_XQ = al16(NCV * Sizes<EL>::M * sizeof(S)), B_T1 = al16(NCV * Sizes<EL>::M * sizeof(S)),
-                       B_H = al16(NCU * Sizes<EL>::M * sizeof(R)), B_G = al16(NCU * Sizes<EL>::M * sizeof(R));
+                       B_H = MODE == MODE_R ? al16(NCU * Sizes<EL>::M * sizeof(R)) : 0,
+                       B_G = al16(NCU * Sizes<EL>::M * sizeof(R));
   static constexpr int PHASE_V = B_XQ + B_T1 + 2 * B_H /*hist nodal + at points*/ + (DIM + 1) * B_G + 2 * B_G /*t1,t2*/ + B_G /*Rv*/;
   static constexpr int PER_ELEM = B_GEO + B_X + B_LF + (PHASE_F > PHASE_V ? PHASE_F : PHASE_V);
-  static constexpr int NE_ = (100 * 1024) / PER_ELEM;
+  static constexpr int NE_ = LDG_RES_SMEM_BUDGET / PER_ELEM;
   static constexpr int NE = NE_ < 1 ? 1 : (NE_ > 16 ? 16 : NE_);
   static constexpr int SMEM = NE * PER_ELEM;
 };

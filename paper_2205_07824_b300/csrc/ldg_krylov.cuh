@@ -61,14 +61,40 @@ __device__ __forceinline__ bool block_partials(double (&acc)[NV], int nvec, doub
   return last;
 }
 
-// Sum of column k of the partials, in block order (called by the last block).
+// Sum of column k of the partials, in block order (single thread; small grids).
 __device__ __forceinline__ double sum_partials(const double* part, int ldp, int k) {
   double s = 0.0;
   for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(part + (size_t)b * ldp + k);
   return s;
 }
 
-// out[k] = sum_i V[k][i] w[i] for k < nvec (NV >= nvec).
+// out[k] = sum over blocks of part[b][k], k < nvec, by the whole last block: the
+// threads form KRY_T / kw groups of kw lanes (kw = nvec rounded up to a power of
+// two), each group strides over the blocks, then one thread per k sums the groups
+// in order. The summation order is fixed, so the result is deterministic.
+__device__ __forceinline__ void reduce_partials(const double* part, int ldp, int nvec, double* out) {
+  __shared__ double gred[KRY_T];
+  int kw = 1;
+  while (kw < nvec) kw <<= 1;
+  const int groups = KRY_T / kw;
+  const int k = threadIdx.x % kw, grp = threadIdx.x / kw;
+  double s = 0.0;
+  if (k < nvec) {
+    const int nb = (int)gridDim.x;
+#pragma unroll 4
+    for (int b = grp; b < nb; b += groups) s += __ldcg(part + (size_t)b * ldp + k);
+  }
+  gred[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < nvec) {
+    double t = 0.0;
+    for (int g = 0; g < groups; ++g) t += gred[g * kw + threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+}
+
+// out[k] = sum_i V[k][i] w[i] for k < nvec (NV >= nvec). Loads of all nvec vectors
+// are issued together (compile-time bucket NV), two entries per thread per pass.
 template <int NV>
 __global__ void __launch_bounds__(KRY_T) k_dots(const double* __restrict__ V, int64_t ldv, int nvec,
                                                const double* __restrict__ w, int64_t n, double* part, int ldp,
@@ -77,74 +103,114 @@ __global__ void __launch_bounds__(KRY_T) k_dots(const double* __restrict__ V, in
   double acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)KRY_T + threadIdx.x; i < n; i += (int64_t)gridDim.x * KRY_T) {
+  const int64_t stride = (int64_t)gridDim.x * KRY_T;
+  int64_t i = blockIdx.x * (int64_t)KRY_T + threadIdx.x;
+  if constexpr (NV <= 16) {
+    for (; i + stride < n; i += 2 * stride) {
+      const double w0 = w[i], w1 = w[i + stride];
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        if (k < nvec) {
+          const double a = V[k * ldv + i], b = V[k * ldv + i + stride];
+          acc[k] = fma(b, w1, fma(a, w0, acc[k]));
+        }
+    }
+  }
+  for (; i < n; i += stride) {
     const double wi = w[i];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
       if (k < nvec) acc[k] = fma(V[k * ldv + i], wi, acc[k]);
   }
   if (!block_partials<NV>(acc, nvec, part, ldp, ticket)) return;
-  if (threadIdx.x < nvec) out[threadIdx.x] = sum_partials(part, ldp, threadIdx.x);
+  reduce_partials(part, ldp, nvec, out);
   if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// w -= sum_k V[k] h[k]. With `givens`, also forms ||w||^2 and the last block
-// completes Arnoldi column j: H(:, j) = h1 + h2, H(j+1, j) = ||w||, applies the
-// previous rotations, forms rotation j, rotates g and sets the done flag when
-// |g_{j+1}| <= sc[3] or on breakdown.
+// w -= sum_k V[k] h[k] (one classical Gram-Schmidt pass).
+// DOTS: the same loop, which already holds V[k][i] in registers, also forms the
+// next pass's projections out[k] = V[k] . w_new (the second Gram-Schmidt pass
+// needs nothing else), saving a separate sweep over V.
+// givens: forms ||w_new||^2 and the last block completes Arnoldi column j:
+// H(:, j) = h1 + h2, H(j+1, j) = ||w||, applies the previous rotations, forms
+// rotation j, rotates g and sets the done flag when |g_{j+1}| <= sc[3] or on breakdown.
+template <int NV, bool DOTS>
 __global__ void __launch_bounds__(KRY_T) k_orth_update(const double* __restrict__ V, int64_t ldv, int nvec,
                                                       const double* __restrict__ h, double* __restrict__ w,
                                                       int64_t n, double* part, int ldp, unsigned int* ticket,
-                                                      double* small, int m, int j, int givens, int* flags) {
+                                                      double* small, int m, int j, int givens, int* flags,
+                                                      double* dots_out) {
   if (flags[0]) return;
-  __shared__ double hs[32];
-  if (threadIdx.x < nvec) hs[threadIdx.x] = h[threadIdx.x];
+  __shared__ double hs[NV];
+  if (threadIdx.x < NV) hs[threadIdx.x] = threadIdx.x < nvec ? h[threadIdx.x] : 0.0;
   __syncthreads();
-  double acc[1] = {0.0};
+  constexpr int NA = DOTS ? NV : 1;
+  double acc[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)KRY_T + threadIdx.x; i < n; i += (int64_t)gridDim.x * KRY_T) {
+    double vv[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) vv[k] = k < nvec ? V[k * ldv + i] : 0.0;
     double s = w[i];
-    for (int k = 0; k < nvec; ++k) s = fma(-V[k * ldv + i], hs[k], s);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s = fma(-vv[k], hs[k], s);
     w[i] = s;
-    acc[0] = fma(s, s, acc[0]);
+    if constexpr (DOTS) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[k] = fma(vv[k], s, acc[k]);
+    } else {
+      acc[0] = fma(s, s, acc[0]);
+    }
   }
-  if (!givens) return;
-  if (!block_partials<1>(acc, 1, part, ldp, ticket)) return;
-  if (threadIdx.x != 0) return;
-  *ticket = 0u;
-  KrySmall S{m};
-  double* H = small + S.H();
-  double* cs = small + S.cs();
-  double* sn = small + S.sn();
-  double* g = small + S.g();
-  const double* h1 = small + S.h1();
-  const double* h2 = small + S.h2();
-  double* sc = small + S.sc();
-  const double nrm2 = sum_partials(part, ldp, 0);
-  const double hn = sqrt(nrm2);
-  sc[0] = nrm2;
-  double* col = H + (size_t)j * (m + 1);
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-  col[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double a = col[i], b = col[i + 1];
-    col[i] = cs[i] * a + sn[i] * b;
-    col[i + 1] = -sn[i] * a + cs[i] * b;
+  if constexpr (DOTS) {
+    if (!block_partials<NA>(acc, nvec, part, ldp, ticket)) return;
+    reduce_partials(part, ldp, nvec, dots_out);
+    if (threadIdx.x == 0) *ticket = 0u;
+    return;
+  } else {
+    if (!givens) return;
+    if (!block_partials<1>(acc, 1, part, ldp, ticket)) return;
+    __shared__ double nrm_s[1];
+    reduce_partials(part, ldp, 1, nrm_s);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    *ticket = 0u;
+    KrySmall S{m};
+    double* H = small + S.H();
+    double* cs = small + S.cs();
+    double* sn = small + S.sn();
+    double* g = small + S.g();
+    const double* h1 = small + S.h1();
+    const double* h2 = small + S.h2();
+    double* sc = small + S.sc();
+    const double nrm2 = nrm_s[0];
+    const double hn = sqrt(nrm2);
+    sc[0] = nrm2;
+    double* col = H + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a = col[i], b = col[i + 1];
+      col[i] = cs[i] * a + sn[i] * b;
+      col[i + 1] = -sn[i] * a + cs[i] * b;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double den = sqrt(a * a + b * b);
+    cs[j] = den > 0.0 ? a / den : 1.0;
+    sn[j] = den > 0.0 ? b / den : 0.0;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    const double est = fabs(g[j + 1]);
+    sc[1] = est;
+    sc[2] = hn;
+    flags[1] = j + 1;
+    const bool breakdown = !(hn > 1e-14 * den);
+    if (!(est > sc[3]) || breakdown) flags[0] = 1;   // NaN also ends the cycle
+    if (breakdown) flags[2] = 1;
   }
-  const double a = col[j], b = col[j + 1];
-  const double den = sqrt(a * a + b * b);
-  cs[j] = den > 0.0 ? a / den : 1.0;
-  sn[j] = den > 0.0 ? b / den : 0.0;
-  col[j] = den;
-  col[j + 1] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  const double est = fabs(g[j + 1]);
-  sc[1] = est;
-  sc[2] = hn;
-  flags[1] = j + 1;
-  const bool breakdown = !(hn > 1e-14 * den);
-  if (!(est > sc[3]) || breakdown) flags[0] = 1;   // NaN also ends the cycle
-  if (breakdown) flags[2] = 1;
 }
 
 // out = in / sqrt(sc[0])
@@ -212,10 +278,8 @@ __global__ void __launch_bounds__(KRY_T) k_sub_norm(const double* __restrict__ b
     acc[0] = fma(s, s, acc[0]);
   }
   if (!block_partials<1>(acc, 1, part, ldp, ticket)) return;
-  if (threadIdx.x == 0) {
-    *out = sum_partials(part, ldp, 0);
-    *ticket = 0u;
-  }
+  reduce_partials(part, ldp, 1, out);
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // x += alpha * y with alpha read from device memory

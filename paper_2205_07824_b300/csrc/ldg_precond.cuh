@@ -11,20 +11,23 @@
 
 namespace ldg {
 
-// inv[e] = blocks[e]^{-1} in precision T. One CTA per element; smem holds the
-// augmented [n x 2n] matrix (row-major) plus n pivot factors. A zero pivot sets *status = 1.
+// inv[e] = blocks[e]^{-1} in precision T: in-place Gauss-Jordan elimination with
+// partial (row) pivoting, the row interchanges undone as column interchanges at the
+// end. One CTA per element; thread t owns columns t, t + blockDim, ... of the n x n
+// matrix held row-major in shared memory, so every update is one FMA per owned
+// entry with no index arithmetic in the inner loop. A zero pivot sets *status = 1.
 template <class T>
 __global__ void k_block_inverse(const double* __restrict__ blocks, T* __restrict__ inv, int n, int* status) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* A = (T*)sm_raw;            // [n][2n]
-  T* fac = A + 2 * n * n;       // [n]
+  T* A = (T*)sm_raw;            // [n][n] row-major
+  T* fac = A + n * n;           // [n] column k before the update
+  int* ipiv = (int*)(fac + n);  // [n] row interchanges
   __shared__ int piv;
-  const int e = blockIdx.x, w2 = 2 * n;
-  const double* B = blocks + (size_t)e * n * n;
+  const int e = blockIdx.x;
+  const double* B = blocks + (size_t)e * n * n;   // column-major
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int col = idx / n, row = idx - col * n;
-    A[row * w2 + col] = (T)B[idx];
-    A[col * w2 + n + row] = (col == row) ? T(1) : T(0);
+    A[row * n + col] = (T)B[idx];
   }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
@@ -32,7 +35,7 @@ __global__ void k_block_inverse(const double* __restrict__ blocks, T* __restrict
       T best = T(-1);
       int bi = k;
       for (int i = k + threadIdx.x; i < n; i += 32) {
-        const T v = fabs(A[i * w2 + k]);
+        const T v = fabs(A[i * n + k]);
         if (v > best) { best = v; bi = i; }
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -40,35 +43,58 @@ __global__ void k_block_inverse(const double* __restrict__ blocks, T* __restrict
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (threadIdx.x == 0) piv = bi;
+      if (threadIdx.x == 0) { piv = bi; ipiv[k] = bi; }
     }
     __syncthreads();
     const int p = piv;
     if (p != k)
-      for (int j = threadIdx.x; j < w2; j += blockDim.x) {
-        const T t = A[k * w2 + j];
-        A[k * w2 + j] = A[p * w2 + j];
-        A[p * w2 + j] = t;
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const T t = A[k * n + j];
+        A[k * n + j] = A[p * n + j];
+        A[p * n + j] = t;
       }
     __syncthreads();
-    const T pv = A[k * w2 + k];
+    const T pv = A[k * n + k];
     if (pv == T(0) && threadIdx.x == 0) *status = 1;
     const T ip = pv != T(0) ? T(1) / pv : T(0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) fac[i] = (i == k) ? T(0) : A[i * n + k];
     __syncthreads();
-    for (int j = threadIdx.x; j < w2; j += blockDim.x) A[k * w2 + j] *= ip;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) fac[i] = (i == k) ? T(0) : A[i * w2 + k];
+    // pivot row: A[k][j] *= 1/pivot, with A[k][k] := 1/pivot
+    for (int j = threadIdx.x; j < n; j += blockDim.x) A[k * n + j] = (j == k ? T(1) : A[k * n + j]) * ip;
     __syncthreads();
-    for (int idx = threadIdx.x; idx < n * w2; idx += blockDim.x) {
-      const int i = idx / w2, j = idx - i * w2;
-      if (i != k) A[idx] -= fac[i] * A[k * w2 + j];
+    // other rows: A[i][j] -= fac[i] A[k][j], with column k taking -fac[i] / pivot
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const T akj = A[k * n + j];
+      const bool colk = (j == k);
+      for (int i = 0; i < n; ++i) {
+        if (i == k) continue;
+        const T aij = colk ? T(0) : A[i * n + j];
+        A[i * n + j] = aij - fac[i] * akj;
+      }
     }
     __syncthreads();
   }
+  // undo the row interchanges as column interchanges, last first; store column-major
   T* Iv = inv + (size_t)e * n * n;
+  for (int row = threadIdx.x; row < n; row += blockDim.x)
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = ipiv[k];
+      if (p != k) {
+        const T t = A[row * n + k];
+        A[row * n + k] = A[row * n + p];
+        A[row * n + p] = t;
+      }
+    }
+  __syncthreads();
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int col = idx / n, row = idx - col * n;
-    Iv[idx] = A[row * w2 + n + col];   // column-major
+    Iv[idx] = A[row * n + col];
   }
+}
+
+// shared memory of k_block_inverse<T> for block size n
+template <class T> constexpr size_t block_inverse_smem(int n) {
+  return (size_t)(n * n + n) * sizeof(T) + (size_t)n * sizeof(int) + 16;
 }
 
 // y_e = inv_e x_e for every element (arithmetic in T, FP64 vectors).
