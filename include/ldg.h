@@ -99,13 +99,15 @@ typedef struct {
   int krylov_precision; /* LDG_FP64 (default) or LDG_FP32: arithmetic of the J.v inside GMRES
                            and of the preconditioner. Newton residuals, Arnoldi, Givens and all
                            vectors stay FP64. */
-  int precond;          /* LDG_PC_NONE (default) or LDG_PC_BJACOBI (flexible right preconditioning) */
+  int precond;          /* LDG_PC_NONE (default), LDG_PC_BJACOBI or LDG_PC_MLP (flexible right
+                           preconditioning; the learned one falls back to block-Jacobi when a
+                           linear solve misses its tolerance) */
   int pc_refresh;       /* rebuild the preconditioner every pc_refresh Newton iterations
                            (0 = once per ldg_newton_gmres call, at the initial guess) */
 } ldg_options;
 
 enum { LDG_FP64 = 0, LDG_FP32 = 1 };
-enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1 };
+enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1, LDG_PC_MLP = 2 };
 
 typedef struct {
   int newton_iters;
@@ -118,7 +120,23 @@ typedef struct {
   double elapsed_ms;
   int status;
   int pc_setups;        /* preconditioner builds during the call */
+  int pc_fallbacks;     /* linear solves redone with block-Jacobi after the learned one failed */
 } ldg_solve_report;
+
+typedef struct {
+  int epochs;           /* passes over the pairs (default 50) */
+  int batch;            /* pairs per Adam step (default 4096) */
+  double lr;            /* Adam step size (default 1e-3) */
+  uint64_t seed;        /* shuffling seed */
+  int linear_init;      /* 1: start from the least-squares fit of the linear skip map (output
+                           layer of the nonlinear branch zeroed); 0: from the current weights */
+} ldg_train_opts;
+
+typedef struct {
+  double loss_first, loss_last;   /* mean loss of the first and last epoch */
+  int steps;
+  double elapsed_ms;
+} ldg_train_report;
 
 const char* ldg_version(void);
 
@@ -168,6 +186,34 @@ int ldg_diag_blocks(ldg_ctx* ctx, int precision, const double* u_dev, double* bl
  * the context), and applies y = M^{-1} x (device vectors, n_dof doubles). */
 int ldg_precond_setup(ldg_ctx* ctx, const double* u_dev);
 int ldg_precond_apply(ldg_ctx* ctx, const double* x_dev, double* y_dev);
+
+/* Learned per-element preconditioner (the learned pattern of this build; the paper's own
+ * preconditioner, Section 3.3, is a reduced-basis one). A multilayer perceptron
+ * 2n -> 128 -> 128 -> n (ReLU, n = n_cu * n_pe) shared by all elements acts on each
+ * element block scaled to unit norm, with the element's state as features:
+ *   M(v)_K = ||v_K|| net(v_K / ||v_K||, u_K)        (positively homogeneous in v).
+ * It is trained on the GPU (FP32 master weights, Adam) by mean-squared error on
+ * triples (v_K, z_K, u_K) where z = (block-Jacobi)^{-1} v is the block correction the
+ * plain solver computes; inference uses BF16 weights with FP32 arithmetic.
+ * X_dev, T_dev, U_dev: [n_pairs][n] FP64 element blocks (rows of v, z and u).
+ * The output layer adds a learned linear map of the scaled block: net = W3 h2 + b3 + Ws v/||v||.
+ * Parameters (get/set, FP64 host, *count entries): W1 [128][2n], b1, W2 [128][128],
+ * b2, W3 [n][128], b3, Ws [n][n]. ldg_mlp_apply evaluates y = M(x) at state u. */
+int ldg_mlp_init(ldg_ctx* ctx, uint64_t seed);
+int ldg_mlp_params(ldg_ctx* ctx, int get, double* host_params, int64_t* count);
+int ldg_mlp_loss_grad(ldg_ctx* ctx, const double* X_dev, const double* T_dev, const double* U_dev, int64_t n_pairs,
+                      double* loss, double* grad_host);
+int ldg_mlp_train(ldg_ctx* ctx, const double* X_dev, const double* T_dev, const double* U_dev, int64_t n_pairs,
+                  const ldg_train_opts* opts, ldg_train_report* rep);
+int ldg_mlp_apply(ldg_ctx* ctx, const double* u_dev, const double* x_dev, double* y_dev);
+
+/* ldg_newton_gmres with the block-Jacobi preconditioner that also stores, for every
+ * Arnoldi vector v_j of every linear solve, v_j in X_dev[i], its block correction
+ * (block-Jacobi)^{-1} v_j in T_dev[i] and the Newton state u in U_dev[i] (n_dof
+ * doubles each, up to `capacity` vectors; *count receives how many): training data
+ * for the learned preconditioner. */
+int ldg_newton_gmres_collect(ldg_ctx* ctx, double* u_dev, double* X_dev, double* T_dev, double* U_dev, int capacity,
+                             int* count, ldg_solve_report* rep);
 
 /* q of Eq. 1a for diffusion models: q_dev [n_elem][n_cu][dim][n_pe]. */
 int ldg_q(ldg_ctx* ctx, const double* u_dev, double* q_dev);

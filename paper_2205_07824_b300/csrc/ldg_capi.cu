@@ -13,6 +13,10 @@
 #include "ldg_host.h"
 #include "ldg_krylov.cuh"
 #include "ldg_precond.cuh"
+#include "ldg_mlp.cuh"
+#include <algorithm>
+#include <random>
+#include <numeric>
 #include "ldg_launch.cuh"
 
 using namespace ldg;
@@ -67,6 +71,28 @@ struct ldg_ctx {
   double* d_jp = nullptr;
   int* d_status = nullptr;
   bool pc_ready = false;
+  // learned per-element MLP preconditioner
+  struct Mlp {
+    int n = 0, h = 128;
+    int64_t nparam = 0;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16* theta_bf = nullptr;
+    int64_t cap = 0;                       // rows of the work buffers
+    float *X = nullptr, *T = nullptr, *mask = nullptr, *H1 = nullptr, *H2 = nullptr, *Y = nullptr;
+    float *dY = nullptr, *dH1 = nullptr, *dH2 = nullptr;
+    double* norms = nullptr;
+    double* loss = nullptr;
+    int* count = nullptr;
+    int* idx = nullptr;
+    int64_t idx_cap = 0;
+    int t = 0;
+    bool ready = false;
+  } mlp;
+  // pair collection during Newton (training data)
+  double* col_X = nullptr;
+  double* col_T = nullptr;
+  double* col_U = nullptr;
+  int col_cap = 0, col_count = 0;
   std::string err;
 };
 
@@ -381,6 +407,136 @@ int pc_apply(ldg_ctx* ctx, const double* x, double* y, const int* skip) {
   return LDG_OK;
 }
 
+// ------------------------------------------------------------ MLP preconditioner
+int mlp_reserve(ldg_ctx* ctx, int64_t rows) {
+  auto& M = ctx->mlp;
+  if (rows <= M.cap) return LDG_OK;
+  for (float** p : {&M.T, &M.Y, &M.dY}) { cudaFree(*p); *p = nullptr; CK(cudaMalloc(p, rows * M.n * sizeof(float))); }
+  cudaFree(M.X); M.X = nullptr;
+  CK(cudaMalloc(&M.X, rows * 2 * M.n * sizeof(float)));
+  for (float** p : {&M.H1, &M.H2, &M.dH1, &M.dH2}) { cudaFree(*p); *p = nullptr; CK(cudaMalloc(p, rows * M.h * sizeof(float))); }
+  cudaFree(M.mask); M.mask = nullptr;
+  CK(cudaMalloc(&M.mask, rows * sizeof(float)));
+  cudaFree(M.norms); M.norms = nullptr;
+  CK(cudaMalloc(&M.norms, rows * sizeof(double)));
+  M.cap = rows;
+  return LDG_OK;
+}
+
+int mlp_alloc(ldg_ctx* ctx) {
+  auto& M = ctx->mlp;
+  if (M.theta) return LDG_OK;
+  M.n = ctx->nloc;
+  M.nparam = (int64_t)M.h * 2 * M.n + M.h + (int64_t)M.h * M.h + M.h + (int64_t)M.n * M.h + M.n + (int64_t)M.n * M.n;
+  for (float** p : {&M.theta, &M.grad, &M.m, &M.v}) CK(cudaMalloc(p, M.nparam * sizeof(float)));
+  CK(cudaMalloc(&M.theta_bf, M.nparam * sizeof(__nv_bfloat16)));
+  CK(cudaMalloc(&M.loss, sizeof(double)));
+  CK(cudaMalloc(&M.count, sizeof(int)));
+  CK(cudaMemset(M.m, 0, M.nparam * sizeof(float)));
+  CK(cudaMemset(M.v, 0, M.nparam * sizeof(float)));
+  return mlp_reserve(ctx, ctx->E);
+}
+
+// parameter offsets: W1 [h][2n], b1 [h], W2 [h][h], b2 [h], W3 [n][h], b3 [n], Ws [n][n]
+struct MlpOff {
+  int64_t W1, b1, W2, b2, W3, b3, Ws;
+  MlpOff(int n, int h) {
+    W1 = 0; b1 = W1 + (int64_t)h * 2 * n; W2 = b1 + h; b2 = W2 + (int64_t)h * h; W3 = b2 + h;
+    b3 = W3 + (int64_t)n * h; Ws = b3 + n;
+  }
+};
+
+template <bool TA, bool TB, class TBt>
+void gemm(ldg_ctx* ctx, int M_, int N_, int K_, const float* A, int lda, const TBt* B, int ldb, float* C, int ldc,
+          const float* bias, int relu, const int* skip, int acc_c = 0) {
+  dim3 grid((N_ + 63) / 64, (M_ + 63) / 64);
+  k_gemm<TA, TB, TBt><<<grid, 256, 0, ctx->stream>>>(M_, N_, K_, A, lda, B, ldb, C, ldc, bias, relu, skip, acc_c);
+  count_launch();
+}
+
+// forward pass on `rows` prepared rows (Xn in M.X); weights FP32 (train) or BF16 (inference)
+template <class TW>
+void mlp_forward(ldg_ctx* ctx, int64_t rows, const TW* th, const float* thf, const int* skip) {
+  auto& M = ctx->mlp;
+  MlpOff o(M.n, M.h);
+  const int r = (int)rows;
+  gemm<false, true, TW>(ctx, r, M.h, 2 * M.n, M.X, 2 * M.n, th + o.W1, 2 * M.n, M.H1, M.h, thf + o.b1, 1, skip);
+  gemm<false, true, TW>(ctx, r, M.h, M.h, M.H1, M.h, th + o.W2, M.h, M.H2, M.h, thf + o.b2, 1, skip);
+  gemm<false, true, TW>(ctx, r, M.n, M.h, M.H2, M.h, th + o.W3, M.h, M.Y, M.n, thf + o.b3, 0, skip);
+  // linear skip path on the scaled vector block (first n input columns)
+  gemm<false, true, TW>(ctx, r, M.n, M.n, M.X, 2 * M.n, th + o.Ws, M.n, M.Y, M.n, nullptr, 0, skip, 1);
+}
+
+// loss and gradient (into M.grad) of the prepared batch in M.X / M.T / M.mask
+int mlp_backward(ldg_ctx* ctx, int64_t rows) {
+  auto& M = ctx->mlp;
+  MlpOff o(M.n, M.h);
+  const int r = (int)rows;
+  const int64_t g1 = std::min<int64_t>(grid_for(rows * M.n), 148 * 8);
+  k_mlp_dloss<<<g1, 256, 0, ctx->stream>>>(M.Y, M.T, M.mask, rows, M.n, M.count, M.dY, M.loss);
+  count_launch();
+  float* G = M.grad;
+  gemm<true, false, float>(ctx, M.n, M.h, r, M.dY, M.n, M.H2, M.h, G + o.W3, M.h, nullptr, 0, nullptr);
+  gemm<true, false, float>(ctx, M.n, M.n, r, M.dY, M.n, M.X, 2 * M.n, G + o.Ws, M.n, nullptr, 0, nullptr);
+  k_colsum<<<M.n, 256, 0, ctx->stream>>>(M.dY, rows, M.n, G + o.b3);
+  count_launch();
+  gemm<false, false, float>(ctx, r, M.h, M.n, M.dY, M.n, M.theta + o.W3, M.h, M.dH2, M.h, nullptr, 0, nullptr);
+  k_relu_back<<<std::min<int64_t>(grid_for(rows * M.h), 148 * 8), 256, 0, ctx->stream>>>(M.dH2, M.H2, rows * M.h);
+  count_launch();
+  gemm<true, false, float>(ctx, M.h, M.h, r, M.dH2, M.h, M.H1, M.h, G + o.W2, M.h, nullptr, 0, nullptr);
+  k_colsum<<<M.h, 256, 0, ctx->stream>>>(M.dH2, rows, M.h, G + o.b2);
+  count_launch();
+  gemm<false, false, float>(ctx, r, M.h, M.h, M.dH2, M.h, M.theta + o.W2, M.h, M.dH1, M.h, nullptr, 0, nullptr);
+  k_relu_back<<<std::min<int64_t>(grid_for(rows * M.h), 148 * 8), 256, 0, ctx->stream>>>(M.dH1, M.H1, rows * M.h);
+  count_launch();
+  gemm<true, false, float>(ctx, M.h, 2 * M.n, r, M.dH1, M.h, M.X, 2 * M.n, G + o.W1, 2 * M.n, nullptr, 0, nullptr);
+  k_colsum<<<M.h, 256, 0, ctx->stream>>>(M.dH1, rows, M.h, G + o.b1);
+  count_launch();
+  CK(cudaGetLastError());
+  return LDG_OK;
+}
+
+// prepare rows idx (or 0..rows-1) of the pair set X / T into the work buffers
+int mlp_prep(ldg_ctx* ctx, const double* X, const double* T, const double* U, const int* idx, int64_t rows,
+             const int* skip) {
+  auto& M = ctx->mlp;
+  int rc;
+  if ((rc = mlp_reserve(ctx, rows))) return rc;
+  if (!skip) {
+    CK(cudaMemsetAsync(M.count, 0, sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(M.loss, 0, sizeof(double), ctx->stream));
+  }
+  k_mlp_prep<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, ctx->stream>>>(X, T, U, idx, rows, M.n, M.X, T ? M.T : nullptr,
+                                                                          M.mask, M.norms, skip ? nullptr : M.count,
+                                                                          skip);
+  count_launch();
+  CK(cudaGetLastError());
+  return LDG_OK;
+}
+
+int mlp_refresh_bf16(ldg_ctx* ctx) {
+  auto& M = ctx->mlp;
+  k_to_bf16<<<std::min<int64_t>(grid_for(M.nparam), 148 * 4), 256, 0, ctx->stream>>>(M.theta, M.theta_bf, M.nparam);
+  count_launch();
+  CK(cudaGetLastError());
+  M.ready = true;
+  return LDG_OK;
+}
+
+// y = M(x) on a full n_dof vector (element blocks) at state u, BF16 weights
+int mlp_apply(ldg_ctx* ctx, const double* u, const double* x, double* y, const int* skip) {
+  auto& M = ctx->mlp;
+  int rc;
+  if ((rc = mlp_prep(ctx, x, nullptr, u, nullptr, ctx->E, skip))) return rc;
+  MlpOff o(M.n, M.h);
+  mlp_forward<__nv_bfloat16>(ctx, ctx->E, M.theta_bf, M.theta, skip);
+  k_mlp_unprep<<<std::min<int64_t>(grid_for(ctx->ndof), 148 * 8), 256, 0, ctx->stream>>>(M.Y, M.norms, ctx->E, M.n, y,
+                                                                                       skip);
+  count_launch();
+  CK(cudaGetLastError());
+  return LDG_OK;
+}
+
 // GMRES(m) on J(u) x = b, x0 = 0, to ||b - J x|| <= rtol ||b||.
 // The host queues Arnoldi steps up to LAG steps ahead of the GPU; each step's
 // kernels return at once after the device-side convergence test has fired.
@@ -404,7 +560,10 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
   if (bnorm == 0.0) return LDG_OK;
   const double thr = rtol * bnorm;
   CK(cudaMemcpyAsync(sc + 3, &thr, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  const bool pc = ctx->opt.precond == LDG_PC_BJACOBI && ctx->pc_ready;
+  const bool pc = (ctx->opt.precond == LDG_PC_BJACOBI && ctx->pc_ready) ||
+                  (ctx->opt.precond == LDG_PC_MLP && ctx->mlp.ready);
+  // the preconditioned Krylov vectors Z must exist before their addresses are used
+  if (pc && (rc = ensure_pc_storage(ctx))) return rc;
   const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8);
   for (int cycle = 0; cycle < ctx->opt.max_restarts; ++cycle) {
     k_cycle_start<<<g1, 256, 0, ctx->stream>>>(ctx->d_r, V, n, sm, m, flags);
@@ -424,7 +583,11 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
       if (pc) {
         // flexible right preconditioning: z_j = M^{-1} v_j, w = J z_j, x += Z y
         double* z = ctx->d_Z + (size_t)j * n;
-        if ((rc = pc_apply(ctx, dir, z, flags))) return rc;
+        if (ctx->opt.precond == LDG_PC_MLP) {
+          if ((rc = mlp_apply(ctx, u, dir, z, flags))) return rc;
+        } else {
+          if ((rc = pc_apply(ctx, dir, z, flags))) return rc;
+        }
         dir = z;
       }
       if ((rc = jvp_args(ctx, a, u, dir, w, ctx->opt.krylov_precision))) return rc;
@@ -455,6 +618,17 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
     CK(cudaStreamSynchronize(ctx->stream));
     const int cols = ctx->h_flags[60 * 4 + 1];
     if (rep) { rep->gmres_iters += cols; rep->jv_calls += cols + 1; }
+    if (pc && ctx->col_X && ctx->opt.precond == LDG_PC_BJACOBI) {
+      // training triples for the learned preconditioner: (v_j, M^{-1} v_j, u)
+      for (int jj = 0; jj < cols && ctx->col_count < ctx->col_cap; ++jj, ++ctx->col_count) {
+        const size_t o = (size_t)ctx->col_count * n;
+        CK(cudaMemcpyAsync(ctx->col_X + o, V + (size_t)jj * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CK(cudaMemcpyAsync(ctx->col_T + o, ctx->d_Z + (size_t)jj * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CK(cudaMemcpyAsync(ctx->col_U + o, u, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+    }
     const double beta = std::sqrt(ctx->h_pin[4]);
     if (rep) rep->lin_resid = beta / bnorm;
     if (!std::isfinite(beta)) return fail(ctx, LDG_ERR_NONFINITE, "non-finite GMRES residual");
@@ -489,7 +663,17 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
       if ((rc = do_pc_setup(ctx, u))) return rc;
       if (rep) rep->pc_setups++;
     }
-    if ((rc = do_gmres(ctx, u, res, del, ctx->opt.gmres_rtol, rep)) && rc != LDG_ERR_MAXIT) return rc;
+    if (ctx->opt.precond == LDG_PC_MLP && k == 0 && (rc = ensure_pc_storage(ctx))) return rc;
+    rc = do_gmres(ctx, u, res, del, ctx->opt.gmres_rtol, rep);
+    if (rc == LDG_ERR_MAXIT && ctx->opt.precond == LDG_PC_MLP) {
+      // the learned preconditioner did not reach the tolerance: fall back to block-Jacobi
+      ctx->opt.precond = LDG_PC_BJACOBI;
+      rc = do_pc_setup(ctx, u);
+      if (!rc) rc = do_gmres(ctx, u, res, del, ctx->opt.gmres_rtol, rep);
+      ctx->opt.precond = LDG_PC_MLP;
+      if (rep) { rep->pc_fallbacks++; rep->pc_setups++; }
+    }
+    if (rc && rc != LDG_ERR_MAXIT) return rc;
     // u <- u - delta   (sc[6] holds -1)
     k_axpy_dev<<<g1, 256, 0, ctx->stream>>>(del, sc + 6, u, n);
     count_launch();
@@ -530,6 +714,13 @@ int ldg_destroy(ldg_ctx* ctx) {
   cudaFree(ctx->d_flags); cudaFree(ctx->d_ticket);
   cudaFree(ctx->d_colour); cudaFree(ctx->d_blocks); cudaFree(ctx->d_binv); cudaFree(ctx->d_Z);
   cudaFree(ctx->d_probe); cudaFree(ctx->d_jp); cudaFree(ctx->d_status);
+  {
+    auto& M = ctx->mlp;
+    for (void* p : {(void*)M.theta, (void*)M.grad, (void*)M.m, (void*)M.v, (void*)M.theta_bf, (void*)M.X, (void*)M.T,
+                    (void*)M.mask, (void*)M.H1, (void*)M.H2, (void*)M.Y, (void*)M.dY, (void*)M.dH1, (void*)M.dH2,
+                    (void*)M.norms, (void*)M.loss, (void*)M.count, (void*)M.idx})
+      cudaFree(p);
+  }
   if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   for (int i = 0; i < 64; ++i) if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
@@ -562,7 +753,7 @@ int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if (o.newton_rtol <= 0) o.newton_rtol = 1e-8;
   if (o.gmres_rtol <= 0) o.gmres_rtol = 1e-3;
   if (o.krylov_precision != LDG_FP32) o.krylov_precision = LDG_FP64;
-  if (o.precond != LDG_PC_BJACOBI) o.precond = LDG_PC_NONE;
+  if (o.precond != LDG_PC_BJACOBI && o.precond != LDG_PC_MLP) o.precond = LDG_PC_NONE;
   if (o.pc_refresh < 0) o.pc_refresh = 0;
   ctx->opt = o;
   ctx->p = p; ctx->nq = o.nq1;
@@ -709,6 +900,183 @@ int ldg_precond_apply(ldg_ctx* ctx, const double* x, double* y) {
   if (!ctx || !ctx->ks || !x || !y) return LDG_ERR_ARG;
   if (!ctx->pc_ready) return fail(ctx, LDG_ERR_ARG, "ldg_precond_apply: call ldg_precond_setup first");
   return pc_apply(ctx, x, y, nullptr);
+}
+
+int ldg_mlp_init(ldg_ctx* ctx, uint64_t seed) {
+  if (!ctx || !ctx->ks) return LDG_ERR_ARG;
+  int rc;
+  if ((rc = mlp_alloc(ctx))) return rc;
+  auto& M = ctx->mlp;
+  MlpOff o(M.n, M.h);
+  // He initialisation for the ReLU layers, small output layer, zero biases
+  std::mt19937_64 gen(seed);
+  std::vector<float> th(M.nparam, 0.f);
+  auto fill = [&](int64_t off, int rows, int cols, double sd) {
+    std::normal_distribution<double> nd(0.0, sd);
+    for (int64_t i = 0; i < (int64_t)rows * cols; ++i) th[off + i] = (float)nd(gen);
+  };
+  fill(o.W1, M.h, M.n, std::sqrt(2.0 / M.n));
+  fill(o.W2, M.h, M.h, std::sqrt(2.0 / M.h));
+  fill(o.W3, M.n, M.h, 0.1 * std::sqrt(1.0 / M.h));
+  CK(cudaMemcpy(M.theta, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemset(M.m, 0, M.nparam * sizeof(float)));
+  CK(cudaMemset(M.v, 0, M.nparam * sizeof(float)));
+  M.t = 0;
+  return mlp_refresh_bf16(ctx);
+}
+
+int ldg_mlp_params(ldg_ctx* ctx, int get, double* host, int64_t* count) {
+  if (!ctx || !ctx->ks || !count) return LDG_ERR_ARG;
+  int rc;
+  if ((rc = mlp_alloc(ctx))) return rc;
+  auto& M = ctx->mlp;
+  if (!host) { *count = M.nparam; return LDG_OK; }
+  if (*count < M.nparam) return fail(ctx, LDG_ERR_ARG, "ldg_mlp_params: buffer too small");
+  std::vector<float> th(M.nparam);
+  if (get) {
+    CK(cudaMemcpy(th.data(), M.theta, M.nparam * sizeof(float), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < M.nparam; ++i) host[i] = th[i];
+  } else {
+    for (int64_t i = 0; i < M.nparam; ++i) th[i] = (float)host[i];
+    CK(cudaMemcpy(M.theta, th.data(), M.nparam * sizeof(float), cudaMemcpyHostToDevice));
+    if ((rc = mlp_refresh_bf16(ctx))) return rc;
+  }
+  *count = M.nparam;
+  return LDG_OK;
+}
+
+int ldg_mlp_loss_grad(ldg_ctx* ctx, const double* X, const double* T, const double* U, int64_t n_pairs, double* loss,
+                      double* grad) {
+  if (!ctx || !ctx->ks || !X || !T || !U || n_pairs <= 0 || !loss) return LDG_ERR_ARG;
+  auto& M = ctx->mlp;
+  if (!M.theta) return fail(ctx, LDG_ERR_ARG, "ldg_mlp_loss_grad: call ldg_mlp_init first");
+  int rc;
+  if ((rc = mlp_prep(ctx, X, T, U, nullptr, n_pairs, nullptr))) return rc;
+  mlp_forward<float>(ctx, n_pairs, M.theta, M.theta, nullptr);
+  if ((rc = mlp_backward(ctx, n_pairs))) return rc;
+  CK(cudaMemcpyAsync(loss, M.loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<float> g(M.nparam);
+  CK(cudaMemcpyAsync(g.data(), M.grad, M.nparam * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (grad)
+    for (int64_t i = 0; i < M.nparam; ++i) grad[i] = g[i];
+  return LDG_OK;
+}
+
+int ldg_mlp_train(ldg_ctx* ctx, const double* X, const double* T, const double* U, int64_t n_pairs,
+                  const ldg_train_opts* opts, ldg_train_report* rep) {
+  if (!ctx || !ctx->ks || !X || !T || !U || n_pairs <= 0) return LDG_ERR_ARG;
+  auto& M = ctx->mlp;
+  if (!M.theta) return fail(ctx, LDG_ERR_ARG, "ldg_mlp_train: call ldg_mlp_init first");
+  ldg_train_opts o{};
+  if (opts) o = *opts;
+  if (o.epochs <= 0) o.epochs = 50;
+  if (o.batch <= 0) o.batch = 4096;
+  if (o.lr <= 0) o.lr = 1e-3;
+  const int64_t B = std::min<int64_t>(o.batch, n_pairs);
+  int rc;
+  if ((rc = mlp_reserve(ctx, B))) return rc;
+  if (M.idx_cap < n_pairs) {
+    cudaFree(M.idx);
+    M.idx = nullptr;
+    CK(cudaMalloc(&M.idx, n_pairs * sizeof(int)));
+    M.idx_cap = n_pairs;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  if (o.linear_init) {
+    // least-squares fit of the linear skip map on all pairs: Ws = (Xn^T Tn)^T (Xn^T Xn)^{-1},
+    // with the nonlinear branch's output layer zeroed, so training starts from the best
+    // state-independent linear block map
+    MlpOff off(M.n, M.h);
+    const int n = M.n;
+    float *Gm = nullptr, *Cm = nullptr, *Gi32 = nullptr;
+    double *G64 = nullptr, *Gi64 = nullptr;
+    CK(cudaMalloc(&Gm, (size_t)n * n * sizeof(float)));
+    CK(cudaMalloc(&Cm, (size_t)n * n * sizeof(float)));
+    CK(cudaMalloc(&Gi32, (size_t)n * n * sizeof(float)));
+    CK(cudaMalloc(&G64, (size_t)n * n * sizeof(double)));
+    CK(cudaMalloc(&Gi64, (size_t)n * n * sizeof(double)));
+    for (int64_t b0 = 0; b0 < n_pairs; b0 += B) {
+      const int64_t rows = std::min<int64_t>(B, n_pairs - b0);
+      if ((rc = mlp_prep(ctx, X + b0 * n, T + b0 * n, U + b0 * n, nullptr, rows, nullptr))) return rc;
+      const int acc = b0 > 0;
+      gemm<true, false, float>(ctx, n, n, (int)rows, M.X, 2 * n, M.X, 2 * n, Gm, n, nullptr, 0, nullptr, acc);
+      gemm<true, false, float>(ctx, n, n, (int)rows, M.X, 2 * n, M.T, n, Cm, n, nullptr, 0, nullptr, acc);
+    }
+    k_gram_to_f64<<<1, 256, 0, ctx->stream>>>(Gm, n, 1e-6, G64);
+    count_launch();
+    if ((rc = ensure_pc_storage(ctx))) return rc;
+    const size_t smem = block_inverse_smem<double>(n);
+    CK(cudaFuncSetAttribute(k_block_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_block_inverse<double><<<1, std::min(256, ((n + 31) / 32) * 32), smem, ctx->stream>>>(G64, Gi64, n, ctx->d_status);
+    count_launch();
+    k_f64_to_f32<<<grid_for((int64_t)n * n), 256, 0, ctx->stream>>>(Gi64, Gi32, (int64_t)n * n);
+    count_launch();
+    // Ws[i][j] = sum_k C[k][i] Ginv[k][j]  (Ginv symmetric)
+    gemm<true, false, float>(ctx, n, n, n, Cm, n, Gi32, n, M.theta + off.Ws, n, nullptr, 0, nullptr);
+    CK(cudaMemsetAsync(M.theta + off.W3, 0, ((size_t)n * M.h + n) * sizeof(float), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(Gm); cudaFree(Cm); cudaFree(Gi32); cudaFree(G64); cudaFree(Gi64);
+    CK(cudaGetLastError());
+  }
+  std::vector<int> perm(n_pairs);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::mt19937_64 gen(o.seed);
+  double first = -1.0, last = 0.0;
+  int steps = 0;
+  std::vector<double> epoch_loss;
+  for (int ep = 0; ep < o.epochs; ++ep) {
+    std::shuffle(perm.begin(), perm.end(), gen);
+    CK(cudaMemcpyAsync(M.idx, perm.data(), n_pairs * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    double acc = 0.0;
+    int nb = 0;
+    for (int64_t b0 = 0; b0 + B <= n_pairs; b0 += B) {
+      if ((rc = mlp_prep(ctx, X, T, U, M.idx + b0, B, nullptr))) return rc;
+      mlp_forward<float>(ctx, B, M.theta, M.theta, nullptr);
+      if ((rc = mlp_backward(ctx, B))) return rc;
+      ++M.t;
+      k_adam<<<std::min<int64_t>(grid_for(M.nparam), 148 * 4), 256, 0, ctx->stream>>>(
+          M.theta, M.grad, M.m, M.v, M.nparam, (float)o.lr, 0.9f, 0.999f, 1e-8f, M.t);
+      count_launch();
+      double l = 0.0;
+      CK(cudaMemcpyAsync(ctx->h_pin, M.loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      l = ctx->h_pin[0];
+      acc += l;
+      ++nb;
+      ++steps;
+    }
+    const double el = nb ? acc / nb : 0.0;
+    if (first < 0) first = el;
+    last = el;
+  }
+  if ((rc = mlp_refresh_bf16(ctx))) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (rep) {
+    rep->loss_first = first;
+    rep->loss_last = last;
+    rep->steps = steps;
+    rep->elapsed_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return LDG_OK;
+}
+
+int ldg_mlp_apply(ldg_ctx* ctx, const double* u, const double* x, double* y) {
+  if (!ctx || !ctx->ks || !u || !x || !y) return LDG_ERR_ARG;
+  if (!ctx->mlp.ready) return fail(ctx, LDG_ERR_ARG, "ldg_mlp_apply: no trained network (ldg_mlp_init/train)");
+  return mlp_apply(ctx, u, x, y, nullptr);
+}
+
+int ldg_newton_gmres_collect(ldg_ctx* ctx, double* u, double* X, double* T, double* U, int capacity, int* count,
+                             ldg_solve_report* rep) {
+  if (!ctx || !ctx->ks || !u || !X || !T || !U || capacity <= 0 || !count) return LDG_ERR_ARG;
+  if (ctx->opt.precond != LDG_PC_BJACOBI)
+    return fail(ctx, LDG_ERR_ARG, "ldg_newton_gmres_collect: needs the block-Jacobi preconditioner");
+  ctx->col_X = X; ctx->col_T = T; ctx->col_U = U; ctx->col_cap = capacity; ctx->col_count = 0;
+  int rc = ldg_newton_gmres(ctx, u, rep);
+  *count = ctx->col_count;
+  ctx->col_X = nullptr; ctx->col_T = nullptr; ctx->col_U = nullptr; ctx->col_cap = 0;
+  return rc;
 }
 
 int ldg_q(ldg_ctx* ctx, const double* u, double* q) {

@@ -20,7 +20,7 @@ POISSON, CONVDIFF, EULER = 0, 1, 2
 CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST = range(7)
 STEADY, BDF1, BDF2 = 0, 1, 2
 FP64, FP32 = 0, 1
-PC_NONE, PC_BJACOBI = 0, 1
+PC_NONE, PC_BJACOBI, PC_MLP = 0, 1, 2
 STATUS = {0: "LDG_OK", -1: "LDG_ERR_ARG", -2: "LDG_ERR_CUDA", -3: "LDG_ERR_UNSUPPORTED",
           -4: "LDG_ERR_NONFINITE", -5: "LDG_ERR_MAXIT", -6: "LDG_ERR_MESH"}
 
@@ -51,7 +51,20 @@ class SolveReport(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("gmres_iters", ctypes.c_int), ("jv_calls", ctypes.c_int),
                 ("residual_calls", ctypes.c_int), ("r0", ctypes.c_double), ("rfinal", ctypes.c_double),
                 ("lin_resid", ctypes.c_double), ("elapsed_ms", ctypes.c_double), ("status", ctypes.c_int),
-                ("pc_setups", ctypes.c_int)]
+                ("pc_setups", ctypes.c_int), ("pc_fallbacks", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("linear_init", ctypes.c_int)]
+
+
+class TrainReport(ctypes.Structure):
+    _fields_ = [("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double), ("steps", ctypes.c_int),
+                ("elapsed_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -86,6 +99,15 @@ def lib():
         L.ldg_diag_blocks.argtypes = [vp, ctypes.c_int, dp, dp]
         L.ldg_precond_setup.argtypes = [vp, dp]
         L.ldg_precond_apply.argtypes = [vp, dp, dp]
+        L.ldg_mlp_init.argtypes = [vp, ctypes.c_uint64]
+        L.ldg_mlp_params.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), i64p]
+        L.ldg_mlp_loss_grad.argtypes = [vp, dp, dp, dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]
+        L.ldg_mlp_train.argtypes = [vp, dp, dp, dp, ctypes.c_int64, ctypes.POINTER(TrainOpts),
+                                    ctypes.POINTER(TrainReport)]
+        L.ldg_mlp_apply.argtypes = [vp, dp, dp, dp]
+        L.ldg_newton_gmres_collect.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(SolveReport)]
         L.ldg_q.argtypes = [vp, dp, dp]
         L.ldg_interpolate.argtypes = [vp, ctypes.c_double, dp]
         L.ldg_gmres.argtypes = [vp, dp, dp, dp, ctypes.POINTER(SolveReport)]
@@ -199,6 +221,59 @@ class LDG:
         out = self.empty() if out is None else out
         self._check(lib().ldg_precond_apply(self._h, _ptr(x, self.n_dof, "x"), _ptr(out, self.n_dof, "out")))
         return out
+
+    # ------------------------------------------------ learned preconditioner
+    def mlp_init(self, seed: int = 0):
+        self._check(lib().ldg_mlp_init(self._h, seed))
+
+    def mlp_params(self, theta=None):
+        """Get (theta None) or set the network parameters as an FP64 numpy vector."""
+        cnt = ctypes.c_int64(0)
+        self._check(lib().ldg_mlp_params(self._h, 1, None, ctypes.byref(cnt)))
+        if theta is None:
+            buf = np.empty(cnt.value)
+            self._check(lib().ldg_mlp_params(self._h, 1, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             ctypes.byref(cnt)))
+            return buf
+        buf = np.ascontiguousarray(theta, dtype=np.float64)
+        self._check(lib().ldg_mlp_params(self._h, 0, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         ctypes.byref(cnt)))
+
+    def mlp_loss_grad(self, X, T, U):
+        n_pairs = X.numel() // (self.n_cu * self.n_pe)
+        loss = ctypes.c_double()
+        cnt = ctypes.c_int64(0)
+        self._check(lib().ldg_mlp_params(self._h, 1, None, ctypes.byref(cnt)))
+        g = np.empty(cnt.value)
+        self._check(lib().ldg_mlp_loss_grad(self._h, _ptr(X, X.numel(), "X"), _ptr(T, T.numel(), "T"),
+                                            _ptr(U, U.numel(), "U"), n_pairs,
+                                            ctypes.byref(loss), g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return loss.value, g
+
+    def mlp_train(self, X, T, U, epochs=50, batch=4096, lr=1e-3, seed=0, linear_init=True):
+        n_pairs = X.numel() // (self.n_cu * self.n_pe)
+        rep = TrainReport()
+        o = TrainOpts(epochs, batch, lr, seed, int(linear_init))
+        self._check(lib().ldg_mlp_train(self._h, _ptr(X, X.numel(), "X"), _ptr(T, T.numel(), "T"),
+                                        _ptr(U, U.numel(), "U"), n_pairs, ctypes.byref(o), ctypes.byref(rep)))
+        return rep.as_dict()
+
+    def mlp_apply(self, u, x, out=None):
+        out = self.empty() if out is None else out
+        n = self.n_dof
+        self._check(lib().ldg_mlp_apply(self._h, _ptr(u, n, "u"), _ptr(x, n, "x"), _ptr(out, n, "out")))
+        return out
+
+    def newton_gmres_collect(self, u, X, T, U, capacity):
+        """Block-Jacobi Newton-GMRES that also stores (v_j, M^-1 v_j, u) per Arnoldi vector into
+        X, T, U [capacity][n_dof]."""
+        rep = SolveReport()
+        cnt = ctypes.c_int(0)
+        n = self.n_dof
+        self._check(lib().ldg_newton_gmres_collect(self._h, _ptr(u, n, "u"), _ptr(X, capacity * n, "X"),
+                                                   _ptr(T, capacity * n, "T"), _ptr(U, capacity * n, "U"),
+                                                   capacity, ctypes.byref(cnt), ctypes.byref(rep)))
+        return cnt.value, rep.as_dict()
 
     def jvp_noalloc(self, u, v, out):
         """J.v through ldg_jvp_noalloc (static device scratch; no allocation in the call)."""

@@ -306,3 +306,50 @@ def test_euler_vortex_consistency_rate():
         errs.append(np.linalg.norm(res) / np.linalg.norm(o.mass(dudt)))
     rate = np.log2(errs[0] / errs[1])
     assert rate > p - 0.3, (errs, rate)
+
+
+# ------------------------------------------------------------- MLP oracle
+def test_mlp_backprop_matches_central_differences():
+    """The chain-rule gradient of the MLP loss equals central finite differences."""
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    n_in, h, n_out = 6, 5, 6
+    nparam = sum(int(np.prod(s)) for s in mlp.shapes(n_in, h, n_out))
+    theta = rng.standard_normal(nparam) * 0.5
+    X = rng.standard_normal((9, n_in))
+    X[3] = 0.0                                    # a masked (zero-norm) pair
+    T = rng.standard_normal((9, n_out))
+    for U in (None, rng.standard_normal((9, 3))):
+        nin = n_in + (0 if U is None else 3)
+        nparam = sum(int(np.prod(s)) for s in mlp.shapes(nin, h, n_out))
+        theta = rng.standard_normal(nparam) * 0.5
+        loss, g = mlp.loss_grad(theta, X, T, nin, h, n_out, U=U)
+        eps = 1e-6
+        fd = np.empty_like(theta)
+        for i in range(nparam):
+            tp, tm = theta.copy(), theta.copy()
+            tp[i] += eps
+            tm[i] -= eps
+            fd[i] = (mlp.loss_grad(tp, X, T, nin, h, n_out, U=U)[0] -
+                     mlp.loss_grad(tm, X, T, nin, h, n_out, U=U)[0]) / (2 * eps)
+        assert np.linalg.norm(g - fd) <= 1e-7 * np.linalg.norm(g)
+
+
+def test_mlp_apply_is_positively_homogeneous():
+    from oracle import mlp
+    rng = np.random.default_rng(1)
+    n_in, h = 8, 7
+    theta = rng.standard_normal(sum(int(np.prod(s)) for s in mlp.shapes(n_in, h, n_in)))
+    V = rng.standard_normal((5, n_in))
+    a = mlp.apply(theta, V, n_in, h, n_in)
+    assert np.allclose(mlp.apply(theta, 3.7 * V, n_in, h, n_in), 3.7 * a, rtol=1e-12, atol=1e-12)
+    assert np.allclose(mlp.apply(theta, 0 * V, n_in, h, n_in), 0.0)
+
+
+def test_adam_reduces_a_quadratic():
+    from oracle import mlp
+    theta = np.array([3.0, -2.0])
+    m, v = np.zeros(2), np.zeros(2)
+    for t in range(1, 2001):
+        mlp.adam_step(theta, 2 * theta, m, v, t, lr=0.05)
+    assert np.abs(theta).max() < 1e-2
