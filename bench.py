@@ -183,27 +183,60 @@ def run_reference(args):
 
 
 def run_mode(LDG, mesh, kprec, pc, steps, warmup, flush, stream, launches):
-    """Advance the vortex `warmup` + `steps` BDF2 steps; time the last `steps`."""
+    """Advance the vortex `warmup` + `steps` BDF2 steps; time the last `steps`.
+
+    pc = 2 (learned): the warm-up steps run the block-Jacobi solver and collect its
+    (v, M^{-1} v, u) triples, the network is trained on them once (reported, not in
+    the timed steps), one more untimed step runs with the learned preconditioner,
+    then the timed steps."""
     import torch
     from paper_2205_07824_b300.ldg import BDF2, EULER, CASE_VORTEX
-    g = LDG(mesh, P, EULER, CASE_VORTEX, (1.4,), gmres_m=30, newton_rtol=1e-8, gmres_rtol=1e-3,
-            krylov_precision=kprec, precond=pc)
+    mk = lambda p: LDG(mesh, P, EULER, CASE_VORTEX, (1.4,), gmres_m=30, newton_rtol=1e-8, gmres_rtol=1e-3,
+                       krylov_precision=kprec, precond=p)
+    g = mk(1 if pc == 2 else pc)
     un, unm1 = g.interpolate(0.0), g.interpolate(-DT)
     u = torch.empty_like(un)
-    state = {"t": 0.0}
+    state = {"t": 0.0, "g": g}
     nloc = g.n_cu * g.n_pe
+    train = None
+    cap = 160 if pc == 2 else 0
+    if cap:
+        bufs = [torch.empty(cap * g.n_dof, dtype=torch.float64, device="cuda") for _ in range(3)]
+        state["used"] = 0
 
-    def step():
+    def step(collect=False):
+        gg = state["g"]
         t1 = state["t"] + DT
-        g.set_time(BDF2, t1, DT, un, unm1)
+        gg.set_time(BDF2, t1, DT, un, unm1)
         u.copy_(un)
-        rep = g.newton_gmres(u)
+        if collect and state["used"] < cap:
+            o = state["used"] * gg.n_dof
+            c, rep = gg.newton_gmres_collect(u, bufs[0][o:], bufs[1][o:], bufs[2][o:], cap - state["used"])
+            state["used"] += c
+        else:
+            rep = gg.newton_gmres(u)
         unm1.copy_(un)
         un.copy_(u)
         state["t"] = t1
         return rep
 
     for _ in range(warmup):
+        step(collect=bool(cap))
+    if cap:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nd = state["used"] * g.n_dof
+        g.mlp_init(seed=1)
+        rep_t = g.mlp_train(bufs[0][:nd], bufs[1][:nd], bufs[2][:nd], epochs=8, batch=4096, lr=1e-3)
+        torch.cuda.synchronize()
+        train = {"pairs": state["used"] * mesh.n_elem, "vectors": state["used"], "seconds": time.perf_counter() - t0,
+                 "adam_steps": rep_t["steps"], "loss_first": rep_t["loss_first"], "loss_last": rep_t["loss_last"],
+                 "data": "Arnoldi vectors of the block-Jacobi warm-up steps with their block corrections"}
+        gm = mk(2)
+        gm.mlp_init(seed=1)
+        gm.mlp_params(g.mlp_params())
+        state["g"] = gm
+        del bufs
         step()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -219,10 +252,12 @@ def run_mode(LDG, mesh, kprec, pc, steps, warmup, flush, stream, launches):
         tot["newton"] += rep["newton_iters"]
         tot["gmres"] += rep["gmres_iters"]
         tot["pc"] += rep["pc_setups"]
+        tot["pc_fallbacks"] = tot.get("pc_fallbacks", 0) + rep["pc_fallbacks"]
     torch.cuda.synchronize()
     n_launch = launches() - l0
     times = [a.elapsed_time(b) for a, b in ev]
-    return g, u, times, tot, n_launch, state["t"]
+    tot["pc_fallbacks"] = tot.get("pc_fallbacks", 0)
+    return state["g"], u, times, tot, n_launch, state["t"], train
 
 
 def main():
@@ -235,8 +270,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--jv-reps", type=int, default=50)
-    ap.add_argument("--precond", default="bjacobi", choices=["none", "bjacobi"],
-                    help="block-Jacobi: exact element-diagonal blocks, rebuilt once per implicit step")
+    ap.add_argument("--precond", default="bjacobi", choices=["none", "bjacobi", "mlp"],
+                    help="block-Jacobi: exact element-diagonal blocks, rebuilt once per implicit step; "
+                         "mlp: the learned per-element preconditioner trained on the warm-up steps")
     ap.add_argument("--krylov", default="fp32", choices=["fp64", "fp32"],
                     help="arithmetic of the J.v inside GMRES (Newton residual and Arnoldi stay FP64)")
     args = ap.parse_args()
@@ -258,14 +294,14 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
     kprec = 1 if args.krylov == "fp32" else 0
-    pc = 1 if args.precond == "bjacobi" else 0
+    pc = {"none": 0, "bjacobi": 1, "mlp": 2}[args.precond]
 
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    g, u, times, tot, launches, t_end = run_mode(LDG, mesh, kprec, pc, args.steps, args.warmup, flush, stream,
-                                                 kernel_launches)
+    g, u, times, tot, launches, t_end, train = run_mode(LDG, mesh, kprec, pc, args.steps, args.warmup, flush, stream,
+                                                        kernel_launches)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
@@ -276,7 +312,8 @@ def main():
     # the plain FP64 block-Jacobi form on the same box, same steps (the benchmark spec comparison)
     base = None
     if not args.no_fp64_baseline and (kprec, pc) != (0, 1):
-        gb, ub, tb, totb, _, _ = run_mode(LDG, mesh, 0, 1, args.steps, args.warmup, flush, stream, kernel_launches)
+        gb, ub, tb, totb, _, _, _ = run_mode(LDG, mesh, 0, 1, args.steps, args.warmup, flush, stream,
+                                             kernel_launches)
         base = {"form": "FP64 Krylov J.v + block-Jacobi", "ms_per_step": sum(tb) / args.steps,
                 "gmres_iters_per_step": totb["gmres"] / args.steps,
                 "solution_rel_diff_vs_headline": float(torch.linalg.norm(ub - u) / torch.linalg.norm(ub))}
@@ -355,8 +392,11 @@ def main():
                            "newton_iters_per_step": tot["newton"] / args.steps,
                            "gmres_iters_per_step": tot["gmres"] / args.steps,
                            "jv_applications_per_step": tot["jv"] / args.steps,
-                           "preconditioner": "none" if not pc else
-                           "block-Jacobi (exact element-diagonal blocks, built once per implicit step)",
+                           "preconditioner": {0: "none",
+                                              1: "block-Jacobi (exact element-diagonal blocks, built once per "
+                                                 "implicit step)",
+                                              2: "learned per-element MLP (BF16 weights), block-Jacobi fallback"}[pc],
+                           "pc_fallbacks": tot["pc_fallbacks"], "learned_pc_training": train,
                            "precision": "FP64 throughout" if kprec == 0 else
                            "Krylov J.v and preconditioner in FP32 arithmetic; Newton residual, Arnoldi, Givens, "
                            "vectors FP64",
