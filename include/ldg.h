@@ -263,6 +263,70 @@ int ldg_jvp_noalloc(ldg_ctx* ctx, const double* u_dev, const double* v_dev, doub
 
 const char* ldg_last_error(const ldg_ctx* ctx);
 
+/* ------------------------------------------------------------------ autotuning
+ * Every (element, p, quadrature, model) is compiled with several tile shapes (the
+ * elements each CTA owns and the shared-memory budget they are sized for; the
+ * paper's own code generator tunes its GPU kernels, Section 3.3). Tiles:
+ *   0: <= 16 elements in <= 100 KB (the default)   1: <= 8 elements in <= 48 KB
+ *   2: <= 32 elements in <= 100 KB                 3: <= 4 elements in <= 24 KB
+ * ldg_autotune times the J.v of every distinct tile (in the context's Krylov
+ * precision) on the context's own mesh, five timed calls after two warm-up calls
+ * with CUDA events, and keeps the fastest for all kernels of the context. The choice
+ * is cached per (element, p, quadrature, model, precision, element-count octave) in
+ * the process; force = 1 re-times. *best_ms = mean time of the chosen J.v (-1 when
+ * the cached choice was used). The call synchronises the context's stream and
+ * allocates three temporary vectors. ldg_set_tile forces a tile (LDG_ERR_UNSUPPORTED
+ * when none is compiled); ldg_get_tile reports the current tile and its elements per
+ * CTA for the q-stage, the residual and the J.v kernel. */
+int ldg_autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms);
+int ldg_set_tile(ldg_ctx* ctx, int tile);
+int ldg_get_tile(const ldg_ctx* ctx, int* tile, int* ne_q, int* ne_r, int* ne_j);
+
+/* ---------------------------------------------------- batched parametrised problems
+ * Many independent steady problems (one per instance: its own mesh, order p and model
+ * parameters mu, all of one model and element type) solved together by
+ * Newton-GMRES (Section 3.3) — a parameter sweep. Instances with the same
+ * (element, p, quadrature) form a group whose meshes are joined into one disjoint
+ * mesh, so each kernel launch covers every instance of a group; the model parameters
+ * are looked up per element.
+ *
+ * Batch vector: all instances' states in one device array of n_total doubles.
+ * Instance i occupies offsets[i] .. offsets[i] + n_dof[i] - 1 in its own element-major
+ * layout (the layout of a single context). Instances are stored group by group, so
+ * offsets need not increase with i.
+ *
+ * The solve runs Newton-GMRES per instance, all instances in lock step: classical
+ * Gram-Schmidt with re-orthogonalisation, Givens rotations, restarts, convergence
+ * tests and the Newton update are per instance (segmented reductions over the
+ * batch vector); an instance that has converged drops out of every kernel. With
+ * use_graph = 1 the whole solve is one CUDA graph launch: the Newton, restart and
+ * Arnoldi loops are graph WHILE nodes whose conditions the device sets, so the host
+ * neither waits nor decides anything until the batch is solved. use_graph = 0 runs
+ * the same kernels with host-driven loops (for testing).
+ * opts (shared by all instances): gmres_m, max_restarts, max_newton, newton_rtol,
+ * gmres_rtol, krylov_precision, precond (LDG_PC_NONE or LDG_PC_BJACOBI; the
+ * block-Jacobi blocks are built inside ldg_batch_solve at the initial guess);
+ * nq1 = 0 picks the default per order. Only steady problems (no time scheme).
+ * reps: n_inst reports (host), one per instance. *elapsed_ms: wall time of the whole
+ * batched solve, set-up included. */
+typedef struct ldg_batch ldg_batch;
+int ldg_batch_create(ldg_batch** out, int n_inst, const ldg_mesh_desc* meshes, const int* p,
+                     const ldg_model_desc* models, const ldg_options* opts, void* cuda_stream);
+int ldg_batch_destroy(ldg_batch* b);
+/* n_total doubles in the batch vector; offsets / n_dof: [n_inst] host arrays (may be NULL);
+ * n_groups: number of (element, p) groups. */
+int ldg_batch_sizes(const ldg_batch* b, int64_t* n_total, int64_t* offsets, int64_t* n_dof, int* n_groups);
+/* R(u) and J(u) v of every instance (batch vectors, device). */
+int ldg_batch_residual(ldg_batch* b, const double* u_dev, double* r_dev);
+int ldg_batch_jvp(ldg_batch* b, int precision, const double* u_dev, const double* v_dev, double* jv_dev);
+/* Autotunes each group (see ldg_autotune); tiles: [n_groups] chosen tiles (may be NULL). */
+int ldg_batch_autotune(ldg_batch* b, int force, int* tiles);
+int ldg_batch_solve(ldg_batch* b, double* u_dev, int use_graph, ldg_solve_report* reps, double* elapsed_ms);
+/* Kernel executions of the last ldg_batch_solve (inside the graph, counted from the
+ * loop trip counts the device recorded). */
+int64_t ldg_batch_kernel_executions(const ldg_batch* b);
+const char* ldg_batch_last_error(const ldg_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,466 @@
+// Device kernels of the batched Newton-GMRES solve (Section 3.3 applied to many
+// independent parametrised problems at once).
+//
+// The batch vector holds every instance's state; instance s is the contiguous
+// segment [off_s, off_s + n_s). Streaming kernels run one CTA per chunk (a
+// contiguous piece of one segment, at most KB_CHUNK entries). Per-instance
+// reductions (dot products, norms) are finished by the last chunk of the segment
+// to arrive (threadfence + per-segment atomic ticket), which sums the segment's
+// chunk partials in chunk order, so every result is deterministic.
+//
+// All instances advance in lock step through the same Newton iteration, restart
+// cycle and Arnoldi step; each keeps its own Hessenberg matrix, Givens rotations
+// and convergence state, and an instance that has converged is skipped by every
+// kernel (skip arrays indexed by instance). The loop control kernels run in one
+// CTA, decide the next trip of each loop from the per-instance state, and, inside
+// a CUDA graph, set the WHILE node's condition with cudaGraphSetConditional. The
+// Arnoldi step index lives in device memory (BatchCtl::j), so one captured body
+// serves every step.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ldg_krylov.cuh"
+
+namespace ldg {
+
+constexpr int KB_CHUNK = 4096;   // entries per chunk (16 per thread)
+constexpr int KB_LDP = 32;       // leading dimension of the chunk partials
+constexpr int KB_NV = 32;        // Gram-Schmidt bucket: up to 32 basis vectors (m <= 30)
+
+struct SegView {
+  const int* chunk_seg;     // [n_chunk] segment of each chunk
+  const int64_t* chunk_lo;  // [n_chunk] first entry
+  const int64_t* chunk_hi;  // [n_chunk] one past the last entry
+  const int* seg_c0;        // [n_seg] first chunk of the segment
+  const int* seg_nc;        // [n_seg] number of chunks
+  double* part;             // [n_chunk][KB_LDP] reduction partials
+  unsigned int* tick;       // [n_seg] arrival tickets (zero between kernels)
+  double* small;            // [n_seg][ks] per-instance KrySmall areas
+  int64_t ks;               // KrySmall{m}.total()
+  int m;
+  int* sflags;              // [n_seg][4]: 0 Arnoldi done, 1 columns, 2 breakdown
+  int nseg;
+};
+
+// Per-instance Newton state.
+struct SegState {
+  double r0, rn, bnorm, lin_resid;
+  int newton_done, gmres_active, status, newton_iters, gmres_iters, jv_calls, residual_calls, cycles;
+};
+
+// Loop state of the batched solve (one record).
+struct BatchCtl {
+  int k;          // Newton iteration
+  int restart;    // restart cycle within the current linear solve
+  int j;          // Arnoldi step within the current cycle
+  int cond_a, cond_b, cond_c;        // last decision of each loop (read by the host-driven form)
+  int n_newton, n_gmres, n_arn;      // instances active in each loop
+  int max_newton, max_restarts, m;
+  double newton_rtol, gmres_rtol;
+  long long trips_a, trips_b, trips_c;   // loop bodies executed
+};
+
+// Block-reduce NV accumulators of chunk c into part[c][:]; true in the last chunk of
+// segment s to arrive (after every partial of the segment is visible).
+template <int NV>
+__device__ __forceinline__ bool seg_partials(double (&acc)[NV], int nvec, const SegView& sv, int c, int s) {
+  __shared__ double red[KRY_T / 32][NV];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) red[wid][k] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nvec) {
+    double t = 0.0;
+    for (int q = 0; q < KRY_T / 32; ++q) t += red[q][threadIdx.x];
+    sv.part[(size_t)c * KB_LDP + threadIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(sv.tick + s, 1u) == (unsigned)(sv.seg_nc[s] - 1);
+  __syncthreads();
+  return last;
+}
+
+// out[k] = sum over the segment's chunks of part[c][k] in chunk order (whole CTA).
+__device__ __forceinline__ void seg_reduce(const SegView& sv, int s, int nvec, double* out) {
+  __shared__ double gred[KRY_T];
+  int kw = 1;
+  while (kw < nvec) kw <<= 1;
+  const int groups = KRY_T / kw;
+  const int k = threadIdx.x % kw, grp = threadIdx.x / kw;
+  const int c0 = sv.seg_c0[s], nc = sv.seg_nc[s];
+  double t = 0.0;
+  if (k < nvec)
+    for (int b = grp; b < nc; b += groups) t += __ldcg(sv.part + (size_t)(c0 + b) * KB_LDP + k);
+  gred[threadIdx.x] = t;
+  __syncthreads();
+  if ((int)threadIdx.x < nvec) {
+    double r = 0.0;
+    for (int g = 0; g < groups; ++g) r += gred[g * kw + threadIdx.x];
+    out[threadIdx.x] = r;
+  }
+}
+
+// small_s[out_off] = ||x_s||^2 for every segment not skipped.
+__global__ void __launch_bounds__(KRY_T) kb_norm2(SegView sv, const double* __restrict__ x, int out_off,
+                                                 const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip && skip[s]) return;
+  double acc[1] = {0.0};
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += KRY_T) acc[0] = fma(x[i], x[i], acc[0]);
+  if (!seg_partials<1>(acc, 1, sv, c, s)) return;
+  seg_reduce(sv, s, 1, sv.small + (size_t)s * sv.ks + out_off);
+  if (threadIdx.x == 0) sv.tick[s] = 0u;
+}
+
+// Pass 1 of Gram-Schmidt at step j = ctl->j: h1_s = V[0..j]_s . w_s. With zsrc, the
+// same sweep stores Z[j] = zsrc (the preconditioned direction of flexible GMRES).
+__global__ void __launch_bounds__(KRY_T) kb_dots(SegView sv, const BatchCtl* ctl, const double* __restrict__ V,
+                                                int64_t ldv, const double* __restrict__ w,
+                                                const double* __restrict__ zsrc, double* __restrict__ Z,
+                                                const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  const int j = ctl->j, nvec = j + 1;
+  double acc[KB_NV];
+#pragma unroll
+  for (int k = 0; k < KB_NV; ++k) acc[k] = 0.0;
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += KRY_T) {
+    const double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < KB_NV; ++k)
+      if (k < nvec) acc[k] = fma(V[k * ldv + i], wi, acc[k]);
+    if (zsrc) Z[j * ldv + i] = zsrc[i];
+  }
+  if (!seg_partials<KB_NV>(acc, nvec, sv, c, s)) return;
+  KrySmall S{sv.m};
+  seg_reduce(sv, s, nvec, sv.small + (size_t)s * sv.ks + S.h1());
+  if (threadIdx.x == 0) sv.tick[s] = 0u;
+}
+
+// w_s -= V[0..j]_s h_s. DOTS: the sweep also forms h2_s = V . w_new (the second pass's
+// projections). Otherwise it forms ||w_new||^2 and the last chunk completes Arnoldi
+// column j of the instance; an instance that converges or breaks down sets skip[s].
+template <bool DOTS>
+__global__ void __launch_bounds__(KRY_T) kb_orth(SegView sv, const BatchCtl* ctl, const double* __restrict__ V,
+                                                int64_t ldv, double* __restrict__ w, int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  const int j = ctl->j, nvec = j + 1;
+  KrySmall S{sv.m};
+  double* sm = sv.small + (size_t)s * sv.ks;
+  __shared__ double hs[KB_NV];
+  if (threadIdx.x < KB_NV) hs[threadIdx.x] = (int)threadIdx.x < nvec ? sm[(DOTS ? S.h1() : S.h2()) + threadIdx.x] : 0.0;
+  __syncthreads();
+  constexpr int NA = DOTS ? KB_NV : 1;
+  double acc[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += KRY_T) {
+    double vv[KB_NV];
+#pragma unroll
+    for (int k = 0; k < KB_NV; ++k) vv[k] = k < nvec ? V[k * ldv + i] : 0.0;
+    double t = w[i];
+#pragma unroll
+    for (int k = 0; k < KB_NV; ++k) t = fma(-vv[k], hs[k], t);
+    w[i] = t;
+    if constexpr (DOTS) {
+#pragma unroll
+      for (int k = 0; k < KB_NV; ++k) acc[k] = fma(vv[k], t, acc[k]);
+    } else {
+      acc[0] = fma(t, t, acc[0]);
+    }
+  }
+  if constexpr (DOTS) {
+    if (!seg_partials<NA>(acc, nvec, sv, c, s)) return;
+    seg_reduce(sv, s, nvec, sm + S.h2());
+    if (threadIdx.x == 0) sv.tick[s] = 0u;
+  } else {
+    if (!seg_partials<1>(acc, 1, sv, c, s)) return;
+    __shared__ double nrm_s[1];
+    seg_reduce(sv, s, 1, nrm_s);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    sv.tick[s] = 0u;
+    int* fl = sv.sflags + 4 * s;
+    arnoldi_column(sm, sv.m, j, nrm_s[0], fl);
+    if (fl[0]) skip[s] = 1;
+  }
+}
+
+// V[j+1]_s = vcur_s = w_s / ||w_s|| (j = ctl->j)
+__global__ void kb_scale(SegView sv, const BatchCtl* ctl, const double* __restrict__ w, double* __restrict__ V,
+                         int64_t ldv, double* __restrict__ vcur, const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  KrySmall S{sv.m};
+  const double nr = sqrt(sv.small[(size_t)s * sv.ks + S.sc()]);
+  const double f = nr > 0.0 ? 1.0 / nr : 0.0;
+  double* out = V + (size_t)(ctl->j + 1) * ldv;
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) {
+    const double t = w[i] * f;
+    out[i] = t;
+    vcur[i] = t;
+  }
+}
+
+// Cycle start: V[0]_s = vcur_s = r_s / ||r_s|| (||r_s||^2 in sc[4]).
+__global__ void kb_cycle_start(SegView sv, const double* __restrict__ r, double* __restrict__ V0,
+                               double* __restrict__ vcur, const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  KrySmall S{sv.m};
+  const double nr = sqrt(sv.small[(size_t)s * sv.ks + S.sc() + 4]);
+  const double f = nr > 0.0 ? 1.0 / nr : 0.0;
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) {
+    const double t = r[i] * f;
+    V0[i] = t;
+    vcur[i] = t;
+  }
+}
+
+// y_s = H_s(0:k, 0:k)^{-1} g_s(0:k), k = columns of the instance (one thread per instance)
+__global__ void kb_backsolve(SegView sv, const int* skip) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= sv.nseg || skip[s]) return;
+  KrySmall S{sv.m};
+  double* sm = sv.small + (size_t)s * sv.ks;
+  const double* H = sm + S.H();
+  const double* g = sm + S.g();
+  double* y = sm + S.y();
+  const int m = sv.m, k = sv.sflags[4 * s + 1];
+  for (int i = k - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int l = i + 1; l < k; ++l) t -= H[(size_t)l * (m + 1) + i] * y[l];
+    y[i] = t / H[(size_t)i * (m + 1) + i];
+  }
+}
+
+// x_s += sum_{l < k_s} B[l]_s y_s[l]  (B = V, or Z for flexible preconditioning)
+__global__ void kb_solution_update(SegView sv, const double* __restrict__ B, int64_t ldb, double* __restrict__ x,
+                                   const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  __shared__ double ys[KB_NV];
+  KrySmall S{sv.m};
+  const int k = sv.sflags[4 * s + 1];
+  if ((int)threadIdx.x < k) ys[threadIdx.x] = sv.small[(size_t)s * sv.ks + S.y() + threadIdx.x];
+  __syncthreads();
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) {
+    double t = x[i];
+    for (int l = 0; l < k; ++l) t = fma(B[l * ldb + i], ys[l], t);
+    x[i] = t;
+  }
+}
+
+// r_s = b_s - a_s and ||r_s||^2 -> sc[4]
+__global__ void __launch_bounds__(KRY_T) kb_sub_norm(SegView sv, const double* __restrict__ b,
+                                                    const double* __restrict__ a, double* __restrict__ r,
+                                                    const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  double acc[1] = {0.0};
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += KRY_T) {
+    const double t = b[i] - a[i];
+    r[i] = t;
+    acc[0] = fma(t, t, acc[0]);
+  }
+  if (!seg_partials<1>(acc, 1, sv, c, s)) return;
+  KrySmall S{sv.m};
+  seg_reduce(sv, s, 1, sv.small + (size_t)s * sv.ks + S.sc() + 4);
+  if (threadIdx.x == 0) sv.tick[s] = 0u;
+}
+
+// Start of a linear solve: r_s = res_s, x_s = 0
+__global__ void kb_prep_linear(SegView sv, const double* __restrict__ res, double* __restrict__ r,
+                               double* __restrict__ x, const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) {
+    r[i] = res[i];
+    x[i] = 0.0;
+  }
+}
+
+// Newton update u_s -= x_s
+__global__ void kb_newton_update(SegView sv, const double* __restrict__ x, double* __restrict__ u, const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) u[i] -= x[i];
+}
+
+// ------------------------------------------------------------ loop control (one CTA)
+__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, unsigned v) {
+  if (use) cudaGraphSetConditional(h, v);
+}
+
+// Solve start: every instance active, counters cleared.
+__global__ void kb_init(BatchCtl* ctl, SegState* st, int nseg, int* skip_newt, int* skip_gm, int* skip_arn) {
+  for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+    SegState z;
+    z.r0 = z.rn = z.bnorm = z.lin_resid = 0.0;
+    z.newton_done = 0; z.gmres_active = 0; z.status = 0; z.newton_iters = 0; z.gmres_iters = 0;
+    z.jv_calls = 0; z.residual_calls = 0; z.cycles = 0;
+    st[s] = z;
+    skip_newt[s] = 0; skip_gm[s] = 1; skip_arn[s] = 1;
+  }
+  if (threadIdx.x == 0) {
+    ctl->k = 0; ctl->restart = 0; ctl->j = 0;
+    ctl->cond_a = 1; ctl->cond_b = 0; ctl->cond_c = 0;
+    ctl->n_newton = nseg; ctl->n_gmres = 0; ctl->n_arn = 0;
+    ctl->trips_a = 0; ctl->trips_b = 0; ctl->trips_c = 0;
+  }
+}
+
+// After R(u_k) and ||R_s||^2 (sc[5]): Newton convergence test per instance; the ones
+// still active start a linear solve J delta = R with threshold gmres_rtol ||R_s||.
+__global__ void kb_newton_check(BatchCtl* ctl, SegView sv, SegState* st, int* skip_newt, int* skip_gm,
+                                cudaGraphConditionalHandle hb, int use_cond) {
+  const int k = ctl->k;
+  KrySmall S{sv.m};
+  int active = 0;
+  for (int s = threadIdx.x; s < sv.nseg; s += blockDim.x) {
+    SegState& q = st[s];
+    skip_gm[s] = 1;
+    if (q.newton_done) continue;
+    double* sc = sv.small + (size_t)s * sv.ks + S.sc();
+    const double rn = sqrt(sc[5]);
+    q.residual_calls++;
+    if (k == 0) q.r0 = rn;
+    q.rn = rn;
+    int done = 0;
+    if (!isfinite(rn)) { q.status = -4; done = 1; }                 // LDG_ERR_NONFINITE
+    else if (rn <= ctl->newton_rtol * q.r0) { q.status = 0; done = 1; }
+    else if (k >= ctl->max_newton) { q.status = -5; done = 1; }     // LDG_ERR_MAXIT
+    if (done) { q.newton_done = 1; skip_newt[s] = 1; continue; }
+    q.gmres_active = 1;
+    q.bnorm = rn;
+    q.newton_iters++;
+    sc[3] = ctl->gmres_rtol * rn;
+    sc[4] = rn * rn;
+    skip_gm[s] = 0;
+    ++active;
+  }
+  const int cnt = __syncthreads_count(active > 0) > 0 ? 1 : 0;
+  __shared__ int tot;
+  if (threadIdx.x == 0) tot = 0;
+  __syncthreads();
+  if (active) atomicAdd(&tot, active);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->n_newton = tot;
+    ctl->restart = 0;
+    ctl->trips_a++;
+    ctl->cond_b = cnt;
+    set_cond(hb, use_cond, (unsigned)cnt);
+  }
+}
+
+// Restart cycle start: g_s = (||r_s||, 0, ...), flags cleared, Arnoldi active for the
+// instances whose linear solve continues.
+__global__ void kb_cycle_init(BatchCtl* ctl, SegView sv, const int* skip_gm, int* skip_arn,
+                              cudaGraphConditionalHandle hc, int use_cond) {
+  KrySmall S{sv.m};
+  int active = 0;
+  for (int s = threadIdx.x; s < sv.nseg; s += blockDim.x) {
+    if (skip_gm[s]) { skip_arn[s] = 1; continue; }
+    double* sm = sv.small + (size_t)s * sv.ks;
+    double* g = sm + S.g();
+    g[0] = sqrt(sm[S.sc() + 4]);
+    for (int i = 1; i <= sv.m; ++i) g[i] = 0.0;
+    int* fl = sv.sflags + 4 * s;
+    fl[0] = 0; fl[1] = 0; fl[2] = 0;
+    skip_arn[s] = 0;
+    ++active;
+  }
+  const int any = __syncthreads_count(active > 0) > 0 ? 1 : 0;
+  if (threadIdx.x == 0) {
+    ctl->j = 0;
+    ctl->n_arn = any;
+    ctl->trips_b++;
+    ctl->cond_c = any;
+    set_cond(hc, use_cond, (unsigned)any);
+  }
+}
+
+// End of an Arnoldi step: j += 1; continue while j < m and an instance is active.
+__global__ void kb_arnoldi_end(BatchCtl* ctl, const int* skip_arn, int nseg, cudaGraphConditionalHandle hc,
+                               int use_cond) {
+  int active = 0;
+  for (int s = threadIdx.x; s < nseg; s += blockDim.x) active += skip_arn[s] ? 0 : 1;
+  const int any = __syncthreads_count(active > 0) > 0 ? 1 : 0;
+  if (threadIdx.x == 0) {
+    const int j = ctl->j + 1;
+    ctl->j = j;
+    ctl->trips_c++;
+    const int go = (j < ctl->m && any) ? 1 : 0;
+    ctl->cond_c = go;
+    set_cond(hc, use_cond, (unsigned)go);
+  }
+}
+
+// End of a restart cycle (true residual ||b - J x||^2 in sc[4]): an instance has
+// converged when the true residual meets its threshold (or the Arnoldi estimate did
+// and the true residual is within 10x of it); a cycle without columns or a
+// non-finite residual ends its solve. Continue while some instance is unconverged
+// and fewer than max_restarts cycles ran.
+__global__ void kb_cycle_end(BatchCtl* ctl, SegView sv, SegState* st, int* skip_gm, int* skip_newt,
+                             cudaGraphConditionalHandle hb, int use_cond) {
+  KrySmall S{sv.m};
+  const int restart = ctl->restart + 1;
+  const bool last_cycle = restart >= ctl->max_restarts;
+  int active = 0;
+  for (int s = threadIdx.x; s < sv.nseg; s += blockDim.x) {
+    if (skip_gm[s]) continue;
+    SegState& q = st[s];
+    const double* sc = sv.small + (size_t)s * sv.ks + S.sc();
+    const int* fl = sv.sflags + 4 * s;
+    const int cols = fl[1];
+    const double beta = sqrt(sc[4]), thr = sc[3];
+    q.gmres_iters += cols;
+    q.jv_calls += cols + 1;
+    q.cycles++;
+    q.lin_resid = q.bnorm > 0.0 ? beta / q.bnorm : 0.0;
+    const bool est = fl[0] && !fl[2];
+    bool stop = false;
+    if (!isfinite(beta)) {
+      q.status = -4; q.newton_done = 1; skip_newt[s] = 1; stop = true;
+    } else if (beta <= thr * (1.0 + 1e-6) || (est && beta <= thr * 10.0)) {
+      stop = true;
+    } else if (cols == 0 || last_cycle) {
+      stop = true;   // no progress or out of cycles: Newton continues with this update
+    }
+    if (stop) { q.gmres_active = 0; skip_gm[s] = 1; }
+    else ++active;
+  }
+  const int any = __syncthreads_count(active > 0) > 0 ? 1 : 0;
+  if (threadIdx.x == 0) {
+    ctl->restart = restart;
+    ctl->n_gmres = any;
+    const int go = (any && !last_cycle) ? 1 : 0;
+    ctl->cond_b = go;
+    set_cond(hb, use_cond, (unsigned)go);
+  }
+}
+
+// End of a Newton iteration: k += 1; continue while an instance is unconverged
+// (bounded by max_newton + 2 iterations).
+__global__ void kb_newton_end(BatchCtl* ctl, const int* skip_newt, int nseg, cudaGraphConditionalHandle ha,
+                              int use_cond) {
+  int active = 0;
+  for (int s = threadIdx.x; s < nseg; s += blockDim.x) active += skip_newt[s] ? 0 : 1;
+  const int any = __syncthreads_count(active > 0) > 0 ? 1 : 0;
+  if (threadIdx.x == 0) {
+    const int k = ctl->k + 1;
+    ctl->k = k;
+    const int go = (any && k <= ctl->max_newton + 1) ? 1 : 0;
+    ctl->cond_a = go;
+    set_cond(ha, use_cond, (unsigned)go);
+  }
+}
+
+}  // namespace ldg

@@ -16,101 +16,36 @@
 #include "ldg_mlp.cuh"
 #include <algorithm>
 #include <random>
+#include <map>
 #include <numeric>
+#include <tuple>
 #include "ldg_launch.cuh"
+#include "ldg_ctx.h"
 
 using namespace ldg;
 
-struct ldg_ctx {
-  int etype = 0, p = 0, nq = 0, dim = 0, npe = 0, ncu = 0, nf = 0, nfq = 0, model = 0;
-  int64_t E = 0, ndof = 0;
-  ModelParams mp{};
-  ldg_options opt{};
-  cudaStream_t stream = nullptr;
-  const KernelSet* ks = nullptr;
-  // device data
-  double* d_ops = nullptr;
-  float* d_opsf = nullptr;
-  double* d_geo = nullptr;
-  int* d_nbr = nullptr;
-  unsigned char* d_nbf = nullptr;
-  unsigned char* d_perm = nullptr;
-  double* d_xn = nullptr;      // reference node coordinates [npe][dim]
-  double* d_q = nullptr;       // q(u) scratch [E][ncu][dim][npe]
-  double* d_dq = nullptr;      // q(v) scratch
-  double* d_hist = nullptr;    // BDF history term
-  // time scheme
-  int scheme = LDG_STEADY;
-  double t = 0.0, dt = 1.0, a0dt = 0.0;
-  // Krylov work space
-  int m = 0;
-  double* d_V = nullptr;       // [(m+1)][ndof]
-  double* d_r = nullptr;       // [ndof]
-  double* d_w = nullptr;       // [ndof]
-  double* d_res = nullptr;     // [ndof] Newton residual
-  double* d_x = nullptr;       // [ndof] Newton update
-  double* d_small = nullptr;   // H, cs, sn, g, y, h1, h2, scalars (KrySmall)
-  double* d_part = nullptr;    // reduction partials [nblk][32]
-  int* d_flags = nullptr;      // done, columns, breakdown
-  unsigned int* d_ticket = nullptr;
-  double* h_pin = nullptr;     // pinned host scalars
-  int* h_flags = nullptr;      // pinned copies of the flags, one slot per Arnoldi step
-  cudaEvent_t ev[64] = {};
-  int nblk = 0;                // grid of streaming vector kernels
-  int nblk_d = 0;              // grid of the many-accumulator reductions (dot products)
-  // block-Jacobi preconditioner
-  int nloc = 0;
-  std::vector<int> h_nbr;      // host copy of the face neighbours (colouring)
-  int* d_colour = nullptr;
-  int ncolour = 0;
-  double* d_blocks = nullptr;  // [E][nloc][nloc] exact diagonal blocks, column-major
-  void* d_binv = nullptr;      // their inverses (float or double)
-  int binv_prec = -1;
-  double* d_Z = nullptr;       // [m][ndof] preconditioned Krylov vectors (flexible GMRES)
-  double* d_probe = nullptr;   // probing work vectors (linear models)
-  double* d_jp = nullptr;
-  int* d_status = nullptr;
-  bool pc_ready = false;
-  // learned per-element MLP preconditioner
-  struct Mlp {
-    int n = 0, h = 128;
-    int64_t nparam = 0;
-    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
-    __nv_bfloat16* theta_bf = nullptr;
-    int64_t cap = 0;                       // rows of the work buffers
-    float *X = nullptr, *T = nullptr, *mask = nullptr, *H1 = nullptr, *H2 = nullptr, *Y = nullptr;
-    float *dY = nullptr, *dH1 = nullptr, *dH2 = nullptr;
-    double* norms = nullptr;
-    double* loss = nullptr;
-    int* count = nullptr;
-    int* idx = nullptr;
-    int64_t idx_cap = 0;
-    int t = 0;
-    bool ready = false;
-  } mlp;
-  // pair collection during Newton (training data)
-  double* col_X = nullptr;
-  double* col_T = nullptr;
-  double* col_U = nullptr;
-  int col_cap = 0, col_count = 0;
-  std::string err;
-};
 
 namespace ldg {
+void register_all(std::vector<KernelSet>& reg) {
+  // Tile0 first: the default instance of every (element, order, model)
+  register_tri_t<Tile0>(reg); register_quad_t<Tile0>(reg); register_hex_t<Tile0>(reg);
+  register_tri_t<Tile1>(reg); register_quad_t<Tile1>(reg); register_hex_t<Tile1>(reg);
+  register_tri_t<Tile2>(reg); register_quad_t<Tile2>(reg); register_hex_t<Tile2>(reg);
+  register_tri_t<Tile3>(reg); register_quad_t<Tile3>(reg); register_hex_t<Tile3>(reg);
+}
 long long& launch_counter() {
   static long long n = 0;
   return n;
 }
 }  // namespace ldg
 
-namespace {
+namespace ldg {
+namespace impl {
 
 const std::vector<KernelSet>& registry() {
   static std::vector<KernelSet> reg = [] {
     std::vector<KernelSet> r;
-    register_tri(r);
-    register_quad(r);
-    register_hex(r);
+    register_all(r);
     return r;
   }();
   return reg;
@@ -165,11 +100,12 @@ KArgs base_args(ldg_ctx* c) {
   std::memset(&a, 0, sizeof(a));
   a.geo = c->d_geo; a.nbr = c->d_nbr; a.nbf = c->d_nbf; a.ops = c->d_ops; a.opsf = c->d_opsf; a.perm = c->d_perm;
   a.a0dt = c->a0dt; a.t = c->t; a.mp = c->mp; a.E = (int)c->E;
+  a.inst = c->ext_inst; a.mtab = c->ext_mtab;
   a.blk_col = -1;
   return a;
 }
 
-int64_t grid_for(int64_t n, int t = 256) { return (n + t - 1) / t; }
+int64_t grid_for(int64_t n, int t) { return (n + t - 1) / t; }
 
 constexpr int LDP = 32;   // leading dimension of the reduction partials
 
@@ -239,6 +175,7 @@ int do_residual(ldg_ctx* ctx, const double* u, double* r) {
 
 int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv, int prec) {
   const int* skip = a.skip;
+  const int* inst_skip = a.inst_skip;
   const bool f32 = prec == LDG_FP32;
   StageFn qs = f32 ? ctx->ks->qstage32 : ctx->ks->qstage;
   StageFn rs = f32 ? ctx->ks->residual32 : ctx->ks->residual;
@@ -248,6 +185,7 @@ int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv
     CK(qs(MODE_HOM, a, ctx->stream));
     a = base_args(ctx);
     a.skip = skip;
+    a.inst_skip = inst_skip;
     a.u = v; a.q = ctx->d_dq; a.out = jv;
     CK(rs(MODE_HOM, a, ctx->stream));
   } else {
@@ -306,7 +244,7 @@ void colour_mesh(ldg_ctx* ctx, int dist, std::vector<int>& col) {
 int ensure_pc_storage(ldg_ctx* ctx) {
   const int64_t E = ctx->E, n = ctx->nloc;
   if (!ctx->d_blocks) CK(cudaMalloc(&ctx->d_blocks, (size_t)E * n * n * sizeof(double)));
-  if (!ctx->d_Z) CK(cudaMalloc(&ctx->d_Z, (size_t)ctx->m * ctx->ndof * sizeof(double)));
+  if (!ctx->d_Z && !ctx->lean) CK(cudaMalloc(&ctx->d_Z, (size_t)ctx->m * ctx->ndof * sizeof(double)));
   if (!ctx->d_status) {
     CK(cudaMalloc(&ctx->d_status, sizeof(int)));
     CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
@@ -393,15 +331,17 @@ int do_pc_setup(ldg_ctx* ctx, const double* u) {
   return LDG_OK;
 }
 
-int pc_apply(ldg_ctx* ctx, const double* x, double* y, const int* skip) {
+int pc_apply(ldg_ctx* ctx, const double* x, double* y, const int* skip, const int* inst_skip) {
   const int n = ctx->nloc;
   const int threads = std::min(256, ((n + 31) / 32) * 32);
+  const int* inst = inst_skip ? ctx->ext_inst : nullptr;
+  if (inst_skip && !inst) return fail(ctx, LDG_ERR_ARG, "per-instance skip on a context without instances");
   if (ctx->binv_prec == LDG_FP64)
     k_block_apply<double><<<(unsigned)ctx->E, threads, n * sizeof(double), ctx->stream>>>((const double*)ctx->d_binv, x,
-                                                                                         y, n, skip);
+                                                                                         y, n, skip, inst, inst_skip);
   else
     k_block_apply<float><<<(unsigned)ctx->E, threads, n * sizeof(float), ctx->stream>>>((const float*)ctx->d_binv, x, y,
-                                                                                       n, skip);
+                                                                                       n, skip, inst, inst_skip);
   count_launch();
   CK(cudaGetLastError());
   return LDG_OK;
@@ -695,7 +635,111 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
   return LDG_OK;
 }
 
-}  // namespace
+// Model parameters from the ABI description (defaults: kappa = tau = 1, beta = 0, gamma = 1.4).
+ModelParams make_params(const ldg_model_desc* model) {
+  ModelParams mp{};
+  mp.kappa = 1.0; mp.tau = 1.0; mp.gamma = 1.4; mp.cas = model->case_id;
+  const double* mu = model->mu;
+  const int nmu = mu ? model->n_mu : 0;
+  if (model->model == LDG_EULER) { if (nmu > 0) mp.gamma = mu[0]; }
+  else {
+    if (nmu > 0) mp.kappa = mu[0];
+    if (nmu > 1) mp.tau = mu[1];
+    for (int d = 0; d < 3; ++d) if (nmu > 2 + d) mp.beta[d] = mu[2 + d];
+  }
+  return mp;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Deterministic direction for timing: v_i = sin(0.37 i + 0.5).
+__global__ void k_tune_pattern(double* v, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) v[i] = sin(0.37 * (double)i + 0.5);
+}
+
+const KernelSet* find_set(const ldg_ctx* ctx, int tile) {
+  for (const KernelSet& k : registry())
+    if (k.etype == ctx->etype && k.p == ctx->p && k.nq == ctx->nq && k.model == ctx->model && k.tile == tile) return &k;
+  return nullptr;
+}
+
+int autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms) {
+  static std::map<std::tuple<int, int, int, int, int, int>, int> cache;
+  const int prec = ctx->opt.krylov_precision;
+  int eb = 0;
+  while ((int64_t(1) << eb) < ctx->E) ++eb;
+  const auto key = std::make_tuple(ctx->etype, ctx->p, ctx->nq, ctx->model, prec, eb);
+  if (best_ms) *best_ms = -1.0;
+  if (!force) {
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      if (const KernelSet* k = find_set(ctx, it->second)) {
+        ctx->ks = k;
+        if (tile) *tile = k->tile;
+        return LDG_OK;
+      }
+    }
+  }
+  // candidates: the compiled tiles with distinct elements-per-CTA counts
+  std::vector<const KernelSet*> cand;
+  for (const KernelSet& k : registry()) {
+    if (k.etype != ctx->etype || k.p != ctx->p || k.nq != ctx->nq || k.model != ctx->model) continue;
+    bool dup = false;
+    for (const KernelSet* c : cand) dup |= (c->ne_q == k.ne_q && c->ne_j == k.ne_j && c->ne_r == k.ne_r);
+    if (!dup) cand.push_back(&k);
+  }
+  if (cand.empty()) return fail(ctx, LDG_ERR_UNSUPPORTED, "autotune: no compiled kernels");
+  const int64_t n = ctx->ndof;
+  double *u = nullptr, *v = nullptr, *jv = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto release = [&]() {
+    cudaFree(u); cudaFree(v); cudaFree(jv);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  int rc = LDG_OK;
+  double best = 1e300;
+  const KernelSet* pick = cand[0];
+  do {
+    cudaError_t ce;
+    if ((ce = cudaMalloc(&u, n * sizeof(double))) || (ce = cudaMalloc(&v, n * sizeof(double))) ||
+        (ce = cudaMalloc(&jv, n * sizeof(double))) || (ce = cudaEventCreate(&e0)) || (ce = cudaEventCreate(&e1))) {
+      rc = fail(ctx, LDG_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+      break;
+    }
+    const int GEO = ctx->dim == 2 ? Geo<2>::size(ctx->nf) : Geo<3>::size(ctx->nf);
+    k_interp_nodes<<<grid_for(ctx->E * ctx->npe), 256, 0, ctx->stream>>>(ctx->dim, ctx->npe, ctx->ncu, ctx->E, ctx->d_geo,
+                                                                        GEO, ctx->d_xn, ctx->mp, ctx->t, u);
+    k_tune_pattern<<<grid_for(n), 256, 0, ctx->stream>>>(v, n);
+    count_launch();
+    count_launch();
+    for (const KernelSet* k : cand) {
+      ctx->ks = k;
+      const int reps = 5;
+      for (int w = 0; w < 2 && !rc; ++w) rc = jvp_args(ctx, base_args(ctx), u, v, jv, prec);
+      if (!rc && (ce = cudaEventRecord(e0, ctx->stream))) rc = fail(ctx, LDG_ERR_CUDA, cudaGetErrorString(ce));
+      for (int r = 0; r < reps && !rc; ++r) rc = jvp_args(ctx, base_args(ctx), u, v, jv, prec);
+      if (!rc && (ce = cudaEventRecord(e1, ctx->stream))) rc = fail(ctx, LDG_ERR_CUDA, cudaGetErrorString(ce));
+      if (!rc && (ce = cudaEventSynchronize(e1))) rc = fail(ctx, LDG_ERR_CUDA, cudaGetErrorString(ce));
+      if (rc) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / reps < best) { best = ms / reps; pick = k; }
+    }
+  } while (false);
+  release();
+  ctx->ks = pick;
+  if (rc) return rc;
+  cache[key] = pick->tile;
+  if (tile) *tile = pick->tile;
+  if (best_ms) *best_ms = best;
+  return LDG_OK;
+}
+
+}  // namespace impl
+}  // namespace ldg
+
+using namespace ldg::impl;
 
 // ===================================================================== C ABI
 extern "C" {
@@ -730,9 +774,19 @@ int ldg_destroy(ldg_ctx* ctx) {
 
 int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_desc* model, const ldg_options* opts,
                void* cuda_stream) {
+  return create_ctx(out, mesh, p, model, opts, cuda_stream, false);
+}
+
+}  // extern "C"
+
+namespace ldg {
+namespace impl {
+int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_desc* model, const ldg_options* opts,
+               void* cuda_stream, bool lean) {
   if (!out || !mesh || !model || !mesh->xyz || !mesh->vid || mesh->n_elem <= 0) return LDG_ERR_ARG;
   *out = nullptr;
   ldg_ctx* ctx = new ldg_ctx();
+  ctx->lean = lean;
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->etype = mesh->elem_type;
   ctx->model = model->model;
@@ -757,20 +811,9 @@ int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if (o.pc_refresh < 0) o.pc_refresh = 0;
   ctx->opt = o;
   ctx->p = p; ctx->nq = o.nq1;
-  // model parameters
-  ModelParams mp{};
-  mp.kappa = 1.0; mp.tau = 1.0; mp.gamma = 1.4; mp.cas = model->case_id;
-  const double* mu = model->mu;
-  int nmu = mu ? model->n_mu : 0;
-  if (ctx->model == LDG_EULER) { if (nmu > 0) mp.gamma = mu[0]; }
-  else {
-    if (nmu > 0) mp.kappa = mu[0];
-    if (nmu > 1) mp.tau = mu[1];
-    for (int d = 0; d < 3; ++d) if (nmu > 2 + d) mp.beta[d] = mu[2 + d];
-  }
-  ctx->mp = mp;
+  ctx->mp = make_params(model);
   for (const KernelSet& k : registry())
-    if (k.etype == ctx->etype && k.p == p && k.nq == o.nq1 && k.model == ctx->model) ctx->ks = &k;
+    if (!ctx->ks && k.etype == ctx->etype && k.p == p && k.nq == o.nq1 && k.model == ctx->model) ctx->ks = &k;
   if (!ctx->ks) {
     ctx->err = "no compiled kernel for element " + std::to_string(ctx->etype) + ", p " + std::to_string(p) +
                ", nq1 " + std::to_string(o.nq1) + ", model " + std::to_string(ctx->model);
@@ -815,7 +858,7 @@ int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
     CK(cudaMalloc(&ctx->d_dq, n * ctx->dim * sizeof(double)));
   }
   CK(cudaMalloc(&ctx->d_hist, n * sizeof(double)));
-  CK(cudaMalloc(&ctx->d_V, (size_t)(ctx->m + 1) * n * sizeof(double)));
+  if (!lean) CK(cudaMalloc(&ctx->d_V, (size_t)(ctx->m + 1) * n * sizeof(double)));
   CK(cudaMalloc(&ctx->d_r, n * sizeof(double)));
   CK(cudaMalloc(&ctx->d_w, n * sizeof(double)));
   CK(cudaMalloc(&ctx->d_res, n * sizeof(double)));
@@ -836,6 +879,32 @@ int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   // the Newton update uses sc[6] = -1 as its axpy coefficient
   double minus1 = -1.0;
   CK(cudaMemcpy(ctx->d_small + S.sc() + 6, &minus1, sizeof(double), cudaMemcpyHostToDevice));
+  return LDG_OK;
+}
+}  // namespace impl
+}  // namespace ldg
+
+extern "C" {
+
+int ldg_autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms) {
+  if (!ctx || !ctx->ks) return LDG_ERR_ARG;
+  return autotune(ctx, force, tile, best_ms);
+}
+
+int ldg_set_tile(ldg_ctx* ctx, int tile) {
+  if (!ctx || !ctx->ks) return LDG_ERR_ARG;
+  const KernelSet* k = find_set(ctx, tile);
+  if (!k) return fail(ctx, LDG_ERR_UNSUPPORTED, "no compiled kernel with tile " + std::to_string(tile));
+  ctx->ks = k;
+  return LDG_OK;
+}
+
+int ldg_get_tile(const ldg_ctx* ctx, int* tile, int* ne_q, int* ne_r, int* ne_j) {
+  if (!ctx || !ctx->ks) return LDG_ERR_ARG;
+  if (tile) *tile = ctx->ks->tile;
+  if (ne_q) *ne_q = ctx->ks->ne_q;
+  if (ne_r) *ne_r = ctx->ks->ne_r;
+  if (ne_j) *ne_j = ctx->ks->ne_j;
   return LDG_OK;
 }
 

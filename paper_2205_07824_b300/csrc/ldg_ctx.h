@@ -1,0 +1,114 @@
+// Internal interface shared by the single-problem C-ABI and the batched solver:
+// the context record and the helpers both use. Not part of the public ABI.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ldg.h"
+#include "ldg_launch.cuh"
+
+struct ldg_ctx {
+  int etype = 0, p = 0, nq = 0, dim = 0, npe = 0, ncu = 0, nf = 0, nfq = 0, model = 0;
+  int64_t E = 0, ndof = 0;
+  ldg::ModelParams mp{};
+  ldg_options opt{};
+  cudaStream_t stream = nullptr;
+  const ldg::KernelSet* ks = nullptr;
+  // device data
+  double* d_ops = nullptr;
+  float* d_opsf = nullptr;
+  double* d_geo = nullptr;
+  int* d_nbr = nullptr;
+  unsigned char* d_nbf = nullptr;
+  unsigned char* d_perm = nullptr;
+  double* d_xn = nullptr;      // reference node coordinates [npe][dim]
+  double* d_q = nullptr;       // q(u) scratch [E][ncu][dim][npe]
+  double* d_dq = nullptr;      // q(v) scratch
+  double* d_hist = nullptr;    // BDF history term
+  // time scheme
+  int scheme = LDG_STEADY;
+  double t = 0.0, dt = 1.0, a0dt = 0.0;
+  // Krylov work space
+  int m = 0;
+  double* d_V = nullptr;       // [(m+1)][ndof]
+  double* d_r = nullptr;       // [ndof]
+  double* d_w = nullptr;       // [ndof]
+  double* d_res = nullptr;     // [ndof] Newton residual
+  double* d_x = nullptr;       // [ndof] Newton update
+  double* d_small = nullptr;   // H, cs, sn, g, y, h1, h2, scalars (KrySmall)
+  double* d_part = nullptr;    // reduction partials [nblk][32]
+  int* d_flags = nullptr;      // done, columns, breakdown
+  unsigned int* d_ticket = nullptr;
+  double* h_pin = nullptr;     // pinned host scalars
+  int* h_flags = nullptr;      // pinned copies of the flags, one slot per Arnoldi step
+  cudaEvent_t ev[64] = {};
+  int nblk = 0;                // grid of streaming vector kernels
+  int nblk_d = 0;              // grid of the many-accumulator reductions (dot products)
+  // block-Jacobi preconditioner
+  int nloc = 0;
+  std::vector<int> h_nbr;      // host copy of the face neighbours (colouring)
+  int* d_colour = nullptr;
+  int ncolour = 0;
+  double* d_blocks = nullptr;  // [E][nloc][nloc] exact diagonal blocks, column-major
+  void* d_binv = nullptr;      // their inverses (float or double)
+  int binv_prec = -1;
+  double* d_Z = nullptr;       // [m][ndof] preconditioned Krylov vectors (flexible GMRES)
+  double* d_probe = nullptr;   // probing work vectors (linear models)
+  double* d_jp = nullptr;
+  int* d_status = nullptr;
+  bool pc_ready = false;
+  // learned per-element MLP preconditioner
+  struct Mlp {
+    int n = 0, h = 128;
+    int64_t nparam = 0;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16* theta_bf = nullptr;
+    int64_t cap = 0;                       // rows of the work buffers
+    float *X = nullptr, *T = nullptr, *mask = nullptr, *H1 = nullptr, *H2 = nullptr, *Y = nullptr;
+    float *dY = nullptr, *dH1 = nullptr, *dH2 = nullptr;
+    double* norms = nullptr;
+    double* loss = nullptr;
+    int* count = nullptr;
+    int* idx = nullptr;
+    int64_t idx_cap = 0;
+    int t = 0;
+    bool ready = false;
+  } mlp;
+  // pair collection during Newton (training data)
+  double* col_X = nullptr;
+  double* col_T = nullptr;
+  double* col_U = nullptr;
+  int col_cap = 0, col_count = 0;
+  // batched contexts: per-element instance ids and the per-instance parameter table
+  // (owned by the batch, not by this context)
+  const int* ext_inst = nullptr;
+  const ldg::ModelParams* ext_mtab = nullptr;
+  bool lean = false;           // no Krylov basis or preconditioned vectors (batch groups)
+  std::string err;
+};
+
+
+namespace ldg {
+namespace impl {
+const std::vector<KernelSet>& registry();
+int fail(ldg_ctx* c, int code, const std::string& msg);
+KArgs base_args(ldg_ctx* c);
+int64_t grid_for(int64_t n, int t = 256);
+int do_residual(ldg_ctx* ctx, const double* u, double* r);
+int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv, int prec);
+int ensure_pc_storage(ldg_ctx* ctx);
+int do_pc_setup(ldg_ctx* ctx, const double* u);
+int pc_apply(ldg_ctx* ctx, const double* x, double* y, const int* skip, const int* inst_skip = nullptr);
+// ldg_create with `lean` contexts (no Krylov work space) for batch groups
+int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_desc* model, const ldg_options* opts,
+               void* cuda_stream, bool lean);
+// Times every compiled tile of the context's (element, order, model) on its mesh and
+// selects the fastest J.v in the Krylov precision; force = 0 reuses a cached choice.
+int autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms);
+ModelParams make_params(const ldg_model_desc* model);
+}  // namespace impl
+}  // namespace ldg

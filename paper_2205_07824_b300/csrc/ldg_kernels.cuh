@@ -27,14 +27,18 @@ namespace ldg {
 
 enum { MODE_R = 0, MODE_HOM = 1, MODE_JV = 2 };
 
-// Shared-memory budget per CTA from which the number of elements per CTA (NE) is
-// derived; smaller budgets give more, smaller CTAs per SM.
-#ifndef LDG_RES_SMEM_BUDGET
-#define LDG_RES_SMEM_BUDGET (100 * 1024)
-#endif
-#ifndef LDG_Q_SMEM_BUDGET
-#define LDG_Q_SMEM_BUDGET (96 * 1024)
-#endif
+// Tile shape of a kernel instance: the number of elements per CTA is the largest
+// count whose shared-memory arrays fit the budget (bytes per CTA), at most NE_MAX.
+// Smaller budgets give more, smaller CTAs per SM. Several tiles are compiled per
+// (element, order, model) and the autotuner picks one per context.
+template <int NEMAX, int BUDGET_R_, int BUDGET_Q_> struct Tile {
+  static constexpr int NE_MAX = NEMAX, BUDGET_R = BUDGET_R_, BUDGET_Q = BUDGET_Q_;
+};
+typedef Tile<16, 100 * 1024, 96 * 1024> Tile0;   // default
+typedef Tile<8, 48 * 1024, 48 * 1024> Tile1;
+typedef Tile<32, 100 * 1024, 100 * 1024> Tile2;
+typedef Tile<4, 24 * 1024, 24 * 1024> Tile3;
+constexpr int N_TILES = 4;
 
 struct KArgs {
   const void* u;              // [E][NCU][NPE]     state (R, JV) or direction (HOM)
@@ -55,9 +59,24 @@ struct KArgs {
   double* blk_out;            // [E][NLOC][NLOC] column-major blocks (NLOC = NCU * NPE)
   double a0dt;                // a0 / dt of the BDF scheme, 0 when steady
   double t;
-  ModelParams mp;
+  ModelParams mp;             // model parameters (all elements, unless inst is set)
+  const int* inst;            // optional [E]: instance of each element (batched contexts) ...
+  const ModelParams* mtab;    // ... indexing this per-instance parameter table
+  const int* inst_skip;       // optional [n_inst]: a CTA whose elements all belong to instances
+                              // with inst_skip != 0 returns at once (outputs left unchanged)
   int E;
 };
+
+// Model parameters of element e.
+__device__ __forceinline__ ModelParams elem_mp(const KArgs& a, int e) { return a.inst ? a.mtab[a.inst[e]] : a.mp; }
+
+// True when the CTA has at least one element of an instance that is not skipped
+// (call from all threads; ne <= blockDim.x).
+__device__ __forceinline__ bool cta_active(const KArgs& a, int e0, int ne) {
+  if (!a.inst_skip) return true;
+  const int act = (int)threadIdx.x < ne && !a.inst_skip[a.inst[e0 + threadIdx.x]];
+  return __syncthreads_or(act) != 0;
+}
 
 // Per-element geometry record: Jinv[k][d] = d xi_k / d x_d, detJ, x(0), J[d][k] = d x_d / d xi_k,
 // then for each face its unit outward normal and surface Jacobian.
@@ -278,7 +297,7 @@ template <class R> __device__ __forceinline__ const R* ops_of(const KArgs& a) {
 }
 
 // ===================================================================== q-stage
-template <class EL, class MD, class R> struct QLayout {
+template <class EL, class MD, class R, class TL> struct QLayout {
   static constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF;
   static constexpr int GEO = Geo<DIM>::size(NF);
   // bytes per element of each array
@@ -290,20 +309,21 @@ template <class EL, class MD, class R> struct QLayout {
   static constexpr int B_V = al16(NCU * DIM * EL::NPE * sizeof(R));
   static constexpr int PHASE_V = 3 * B_V;                           // grad, b, scratch
   static constexpr int PER_ELEM = B_GEO + B_U + B_LF + (PHASE_F > PHASE_V ? PHASE_F : PHASE_V);
-  static constexpr int NE_ = LDG_Q_SMEM_BUDGET / PER_ELEM;
-  static constexpr int NE = NE_ < 1 ? 1 : (NE_ > 16 ? 16 : NE_);
+  static constexpr int NE_ = TL::BUDGET_Q / PER_ELEM;
+  static constexpr int NE = NE_ < 1 ? 1 : (NE_ > TL::NE_MAX ? TL::NE_MAX : NE_);
   static constexpr int SMEM = NE * PER_ELEM;
 };
 
-template <class EL, class MD, int MODE, class R>
+template <class EL, class MD, int MODE, class R, class TL>
 __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
-  typedef QLayout<EL, MD, R> L;
+  typedef QLayout<EL, MD, R, TL> L;
   constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ;
   constexpr int NE = L::NE, GEO = L::GEO;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int e0 = blockIdx.x * NE;
   const int ne = min(NE, a.E - e0);
+  if (!cta_active(a, e0, ne)) return;
   const R* OPS = ops_of<R>(a);
   R* Gs = (R*)smem;
   R* Us = (R*)(smem + NE * L::B_GEO);
@@ -360,7 +380,7 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
       double x[3];
       face_xi<EL>(OPS, f, k, xi);
       phys_x<DIM>(g, xi, x);
-      exact_state<DIM>(a.mp, NCU, x, a.t, gb);
+      exact_state<DIM>(elem_mp(a, e0 + e), NCU, x, a.t, gb);
     }
     for (int c = 0; c < NCU; ++c) {
       int base = ((e * NF + f) * NCU + c) * NFQ;
@@ -404,7 +424,7 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
 }
 
 // ==================================================================== residual
-template <class EL, class MD, int MODE, class R> struct RLayout {
+template <class EL, class MD, int MODE, class R, class TL> struct RLayout {
   typedef typename std::conditional<MODE == MODE_JV, Dual<R>, R>::type S;
   static constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF;
   static constexpr int NCV = NCU * (1 + (MD::HASQ ? DIM : 0));      // u and q fields
@@ -421,14 +441,14 @@ template <class EL, class MD, int MODE, class R> struct RLayout {
                        B_G = al16(NCU * Sizes<EL>::M * sizeof(R));
   static constexpr int PHASE_V = B_XQ + B_T1 + 2 * B_H /*hist nodal + at points*/ + (DIM + 1) * B_G + 2 * B_G /*t1,t2*/ + B_G /*Rv*/;
   static constexpr int PER_ELEM = B_GEO + B_X + B_LF + (PHASE_F > PHASE_V ? PHASE_F : PHASE_V);
-  static constexpr int NE_ = LDG_RES_SMEM_BUDGET / PER_ELEM;
-  static constexpr int NE = NE_ < 1 ? 1 : (NE_ > 16 ? 16 : NE_);
+  static constexpr int NE_ = TL::BUDGET_R / PER_ELEM;
+  static constexpr int NE = NE_ < 1 ? 1 : (NE_ > TL::NE_MAX ? TL::NE_MAX : NE_);
   static constexpr int SMEM = NE * PER_ELEM;
 };
 
-template <class EL, class MD, int MODE, class R>
+template <class EL, class MD, int MODE, class R, class TL>
 __global__ void __launch_bounds__(256) k_residual(KArgs a) {
-  typedef RLayout<EL, MD, MODE, R> L;
+  typedef RLayout<EL, MD, MODE, R, TL> L;
   typedef typename L::S S;
   constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ, NQV = EL::NQV;
   constexpr int NE = L::NE, GEO = L::GEO, NCV = L::NCV;
@@ -438,8 +458,10 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int e0 = blockIdx.x * NE;
   const int ne = min(NE, a.E - e0);
+  if (!cta_active(a, e0, ne)) return;
   const R* OPS = ops_of<R>(a);
-  const MPar<R> mp = mpar<R>(a.mp);
+  __shared__ MPar<R> MPs[NE];   // per-element model parameters (padding elements: a.mp)
+  for (int e = threadIdx.x; e < NE; e += blockDim.x) MPs[e] = mpar<R>(e < ne ? elem_mp(a, e0 + e) : a.mp);
   R* Gs = (R*)smem;
   S* X = (S*)(smem + NE * L::B_GEO);                       // [NE][NCV][NPE]
   R* LF = (R*)(smem + NE * (L::B_GEO + L::B_X));           // [NE][NF][NCU][NFN]
@@ -522,7 +544,7 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
           S val = TRp[((e * NF + f) * NCV + fld) * NFQ + kp];
           if (fld < NCU) up[fld] = val; else qp[fld - NCU] = val;
         }
-        MD::fhat(um, up, qm, qp, nrm, fh, mp);
+        MD::fhat(um, up, qm, qp, nrm, fh, MPs[e]);
       } else {
         R gb[4] = {R(0), R(0), R(0), R(0)};
         if (MODE != MODE_HOM) {
@@ -530,10 +552,10 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
           double x[3], gd[4] = {0.0, 0.0, 0.0, 0.0};
           face_xi<EL>(OPS, f, k, xi);
           phys_x<DIM>(g, xi, x);
-          exact_state<DIM>(a.mp, NCU, x, a.t, gd);
+          exact_state<DIM>(elem_mp(a, e0 + e), NCU, x, a.t, gd);
           for (int c = 0; c < 4; ++c) gb[c] = R(gd[c]);
         }
-        MD::fhat_bnd(um, qm, gb, nrm, fh, mp);
+        MD::fhat_bnd(um, qm, gb, nrm, fh, MPs[e]);
       }
       for (int c = 0; c < NCU; ++c) FH[((e * NF + f) * NCU + c) * NFQ + k] = outp(fh[c]) * w;
     }
@@ -577,9 +599,9 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
     if (MODE == MODE_R && e < ne && MD::KIND != M_EULER) {
       double x[3];
       phys_x<DIM>(g, xi, x);
-      src = R(source_term<DIM>(a.mp, MD::KIND == M_CONVDIFF, x));
+      src = R(source_term<DIM>(elem_mp(a, e0 + e), MD::KIND == M_CONVDIFF, x));
     }
-    MD::flux(uq, qq, f, mp);
+    MD::flux(uq, qq, f, MPs[e]);
     for (int c = 0; c < NCU; ++c) {
       for (int k = 0; k < DIM; ++k) {
         R s = R(0);

@@ -93,6 +93,46 @@ __device__ __forceinline__ void reduce_partials(const double* part, int ldp, int
   }
 }
 
+// Completes Arnoldi column j from the two Gram-Schmidt passes' projections h1 + h2 and
+// ||w||^2 (single thread): H(:, j) = h1 + h2, H(j+1, j) = ||w||, applies the previous
+// Givens rotations, forms rotation j, rotates g, and sets flags[0] (done) when
+// |g_{j+1}| <= sc[3] or on breakdown (flags[2]); flags[1] = j + 1 columns.
+__device__ __forceinline__ void arnoldi_column(double* small, int m, int j, double nrm2, int* flags) {
+  KrySmall S{m};
+  double* H = small + S.H();
+  double* cs = small + S.cs();
+  double* sn = small + S.sn();
+  double* g = small + S.g();
+  const double* h1 = small + S.h1();
+  const double* h2 = small + S.h2();
+  double* sc = small + S.sc();
+  const double hn = sqrt(nrm2);
+  sc[0] = nrm2;
+  double* col = H + (size_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = col[i], b = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * b;
+    col[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = col[j], b = col[j + 1];
+  const double den = sqrt(a * a + b * b);
+  cs[j] = den > 0.0 ? a / den : 1.0;
+  sn[j] = den > 0.0 ? b / den : 0.0;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  const double est = fabs(g[j + 1]);
+  sc[1] = est;
+  sc[2] = hn;
+  flags[1] = j + 1;
+  const bool breakdown = !(hn > 1e-14 * den);
+  if (!(est > sc[3]) || breakdown) flags[0] = 1;   // NaN also ends the cycle
+  if (breakdown) flags[2] = 1;
+}
+
 // out[k] = sum_i V[k][i] w[i] for k < nvec (NV >= nvec). Loads of all nvec vectors
 // are issued together (compile-time bucket NV), two entries per thread per pass.
 template <int NV>
@@ -176,45 +216,12 @@ __global__ void __launch_bounds__(KRY_T) k_orth_update(const double* __restrict_
     __syncthreads();
     if (threadIdx.x != 0) return;
     *ticket = 0u;
-    KrySmall S{m};
-    double* H = small + S.H();
-    double* cs = small + S.cs();
-    double* sn = small + S.sn();
-    double* g = small + S.g();
-    const double* h1 = small + S.h1();
-    const double* h2 = small + S.h2();
-    double* sc = small + S.sc();
-    const double nrm2 = nrm_s[0];
-    const double hn = sqrt(nrm2);
-    sc[0] = nrm2;
-    double* col = H + (size_t)j * (m + 1);
-    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-    col[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-      const double a = col[i], b = col[i + 1];
-      col[i] = cs[i] * a + sn[i] * b;
-      col[i + 1] = -sn[i] * a + cs[i] * b;
-    }
-    const double a = col[j], b = col[j + 1];
-    const double den = sqrt(a * a + b * b);
-    cs[j] = den > 0.0 ? a / den : 1.0;
-    sn[j] = den > 0.0 ? b / den : 0.0;
-    col[j] = den;
-    col[j + 1] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    const double est = fabs(g[j + 1]);
-    sc[1] = est;
-    sc[2] = hn;
-    flags[1] = j + 1;
-    const bool breakdown = !(hn > 1e-14 * den);
-    if (!(est > sc[3]) || breakdown) flags[0] = 1;   // NaN also ends the cycle
-    if (breakdown) flags[2] = 1;
+    arnoldi_column(small, m, j, nrm_s[0], flags);
   }
 }
 
 // out = in / sqrt(sc[0])
-__global__ void k_scale_by_norm(const double* in, const double* small_sc, double* out, int64_t n, const int* flags) {
+static __global__ void k_scale_by_norm(const double* in, const double* small_sc, double* out, int64_t n, const int* flags) {
   if (flags && flags[0]) return;
   const double s = sqrt(small_sc[0]);
   const double f = s > 0.0 ? 1.0 / s : 0.0;
@@ -223,7 +230,7 @@ __global__ void k_scale_by_norm(const double* in, const double* small_sc, double
 }
 
 // Cycle start: V0 = r / ||r|| (||r||^2 in sc[4]); g = (||r||, 0, ...); flags cleared.
-__global__ void k_cycle_start(const double* r, double* V0, int64_t n, double* small, int m, int* flags) {
+static __global__ void k_cycle_start(const double* r, double* V0, int64_t n, double* small, int m, int* flags) {
   KrySmall S{m};
   const double* sc = small + S.sc();
   const double s = sqrt(sc[4]);
@@ -238,7 +245,7 @@ __global__ void k_cycle_start(const double* r, double* V0, int64_t n, double* sm
 }
 
 // y = H(0:k, 0:k)^{-1} g(0:k), k = flags[1]
-__global__ void k_backsolve(double* small, int m, const int* flags) {
+static __global__ void k_backsolve(double* small, int m, const int* flags) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   KrySmall S{m};
   const double* H = small + S.H();
@@ -253,7 +260,7 @@ __global__ void k_backsolve(double* small, int m, const int* flags) {
 }
 
 // x += sum_{k < flags[1]} V[k] y[k]
-__global__ void k_solution_update(const double* __restrict__ V, int64_t ldv, const double* small, int m,
+static __global__ void k_solution_update(const double* __restrict__ V, int64_t ldv, const double* small, int m,
                                   const int* flags, double* __restrict__ x, int64_t n) {
   __shared__ double ys[32];
   KrySmall S{m};
@@ -268,7 +275,7 @@ __global__ void k_solution_update(const double* __restrict__ V, int64_t ldv, con
 }
 
 // r = b - a and ||r||^2 -> *out
-__global__ void __launch_bounds__(KRY_T) k_sub_norm(const double* __restrict__ b, const double* __restrict__ a,
+static __global__ void __launch_bounds__(KRY_T) k_sub_norm(const double* __restrict__ b, const double* __restrict__ a,
                                                    double* __restrict__ r, int64_t n, double* part, int ldp,
                                                    unsigned int* ticket, double* out) {
   double acc[1] = {0.0};
@@ -283,7 +290,7 @@ __global__ void __launch_bounds__(KRY_T) k_sub_norm(const double* __restrict__ b
 }
 
 // x += alpha * y with alpha read from device memory
-__global__ void k_axpy_dev(const double* __restrict__ y, const double* alpha, double* __restrict__ x, int64_t n) {
+static __global__ void k_axpy_dev(const double* __restrict__ y, const double* alpha, double* __restrict__ x, int64_t n) {
   const double a = *alpha;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = fma(a, y[i], x[i]);

@@ -16,6 +16,7 @@ typedef cudaError_t (*StageFn)(int mode, const KArgs& a, cudaStream_t s);
 
 struct KernelSet {
   int etype, p, nq, model;
+  int tile;           // tile variant (Tile0 .. Tile3)
   StageFn qstage;     // FP64 compute. Diffusion models: MODE_R / MODE_HOM; null otherwise
   StageFn residual;   // FP64 compute. MODE_R / MODE_HOM (linear models) / MODE_JV (nonlinear models)
   StageFn qstage32;   // FP32 compute, MODE_HOM (diffusion models); null otherwise
@@ -23,85 +24,92 @@ struct KernelSet {
   int ne_q, ne_r, ne_j, smem_q, smem_r, smem_j;
 };
 
-template <class EL, class MD, int MODE, class R> cudaError_t launch_res1(const KArgs& a, cudaStream_t s) {
-  typedef RLayout<EL, MD, MODE, R> L;
-  static const cudaError_t attr = cudaFuncSetAttribute(k_residual<EL, MD, MODE, R>,
+template <class EL, class MD, int MODE, class R, class TL> cudaError_t launch_res1(const KArgs& a, cudaStream_t s) {
+  typedef RLayout<EL, MD, MODE, R, TL> L;
+  static const cudaError_t attr = cudaFuncSetAttribute(k_residual<EL, MD, MODE, R, TL>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
   if (attr != cudaSuccess) return attr;
   if (a.E <= 0) return cudaSuccess;
   int grid = (a.E + L::NE - 1) / L::NE;
-  k_residual<EL, MD, MODE, R><<<grid, 256, L::SMEM, s>>>(a);
+  k_residual<EL, MD, MODE, R, TL><<<grid, 256, L::SMEM, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }
-template <class EL, class MD, int MODE, class R> cudaError_t launch_q1(const KArgs& a, cudaStream_t s) {
-  typedef QLayout<EL, MD, R> L;
-  static const cudaError_t attr = cudaFuncSetAttribute(k_qstage<EL, MD, MODE, R>,
+template <class EL, class MD, int MODE, class R, class TL> cudaError_t launch_q1(const KArgs& a, cudaStream_t s) {
+  typedef QLayout<EL, MD, R, TL> L;
+  static const cudaError_t attr = cudaFuncSetAttribute(k_qstage<EL, MD, MODE, R, TL>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
   if (attr != cudaSuccess) return attr;
   if (a.E <= 0) return cudaSuccess;
   int grid = (a.E + L::NE - 1) / L::NE;
-  k_qstage<EL, MD, MODE, R><<<grid, 256, L::SMEM, s>>>(a);
+  k_qstage<EL, MD, MODE, R, TL><<<grid, 256, L::SMEM, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }
 
-template <class EL, class MD, class R> cudaError_t stage_res(int mode, const KArgs& a, cudaStream_t s) {
+template <class EL, class MD, class R, class TL> cudaError_t stage_res(int mode, const KArgs& a, cudaStream_t s) {
   if constexpr (MD::LINEAR) {
-    if (mode == MODE_R) return launch_res1<EL, MD, MODE_R, R>(a, s);
-    if (mode == MODE_HOM) return launch_res1<EL, MD, MODE_HOM, R>(a, s);
+    if (mode == MODE_R) return launch_res1<EL, MD, MODE_R, R, TL>(a, s);
+    if (mode == MODE_HOM) return launch_res1<EL, MD, MODE_HOM, R, TL>(a, s);
   } else {
-    if (mode == MODE_R) return launch_res1<EL, MD, MODE_R, R>(a, s);
-    if (mode == MODE_JV) return launch_res1<EL, MD, MODE_JV, R>(a, s);
+    if (mode == MODE_R) return launch_res1<EL, MD, MODE_R, R, TL>(a, s);
+    if (mode == MODE_JV) return launch_res1<EL, MD, MODE_JV, R, TL>(a, s);
   }
   return cudaErrorInvalidValue;
 }
 // FP32-compute stages: only the J.v modes are instantiated (the Newton residual stays FP64)
-template <class EL, class MD> cudaError_t stage_res32(int mode, const KArgs& a, cudaStream_t s) {
+template <class EL, class MD, class TL> cudaError_t stage_res32(int mode, const KArgs& a, cudaStream_t s) {
   if constexpr (MD::LINEAR) {
-    if (mode == MODE_HOM) return launch_res1<EL, MD, MODE_HOM, float>(a, s);
+    if (mode == MODE_HOM) return launch_res1<EL, MD, MODE_HOM, float, TL>(a, s);
   } else {
-    if (mode == MODE_JV) return launch_res1<EL, MD, MODE_JV, float>(a, s);
+    if (mode == MODE_JV) return launch_res1<EL, MD, MODE_JV, float, TL>(a, s);
   }
   return cudaErrorInvalidValue;
 }
-template <class EL, class MD> cudaError_t stage_q32(int mode, const KArgs& a, cudaStream_t s) {
-  if (mode == MODE_HOM) return launch_q1<EL, MD, MODE_HOM, float>(a, s);
+template <class EL, class MD, class TL> cudaError_t stage_q32(int mode, const KArgs& a, cudaStream_t s) {
+  if (mode == MODE_HOM) return launch_q1<EL, MD, MODE_HOM, float, TL>(a, s);
   return cudaErrorInvalidValue;
 }
 
-template <class EL, class MD, class R> cudaError_t stage_q(int mode, const KArgs& a, cudaStream_t s) {
-  if (mode == MODE_R) return launch_q1<EL, MD, MODE_R, R>(a, s);
-  if (mode == MODE_HOM) return launch_q1<EL, MD, MODE_HOM, R>(a, s);
+template <class EL, class MD, class R, class TL> cudaError_t stage_q(int mode, const KArgs& a, cudaStream_t s) {
+  if (mode == MODE_R) return launch_q1<EL, MD, MODE_R, R, TL>(a, s);
+  if (mode == MODE_HOM) return launch_q1<EL, MD, MODE_HOM, R, TL>(a, s);
   return cudaErrorInvalidValue;
 }
 
-template <class EL, class MD> void add_set(std::vector<KernelSet>& reg, int etype) {
+template <class TL> constexpr int tile_id() {
+  return std::is_same<TL, Tile0>::value ? 0 : std::is_same<TL, Tile1>::value ? 1 : std::is_same<TL, Tile2>::value ? 2 : 3;
+}
+
+template <class EL, class MD, class TL = Tile0> void add_set(std::vector<KernelSet>& reg, int etype) {
   KernelSet k;
   k.etype = etype; k.p = EL::P; k.nq = EL::NQ; k.model = MD::KIND;
-  k.residual = &stage_res<EL, MD, double>;
-  k.residual32 = &stage_res32<EL, MD>;
-  k.ne_r = RLayout<EL, MD, MODE_R, double>::NE;
-  k.smem_r = RLayout<EL, MD, MODE_R, double>::SMEM;
+  k.tile = tile_id<TL>();
+  k.residual = &stage_res<EL, MD, double, TL>;
+  k.residual32 = &stage_res32<EL, MD, TL>;
+  k.ne_r = RLayout<EL, MD, MODE_R, double, TL>::NE;
+  k.smem_r = RLayout<EL, MD, MODE_R, double, TL>::SMEM;
   if constexpr (MD::HASQ) {
-    k.qstage = &stage_q<EL, MD, double>;
-    k.qstage32 = &stage_q32<EL, MD>;
-    k.ne_q = QLayout<EL, MD, double>::NE;
-    k.smem_q = QLayout<EL, MD, double>::SMEM;
-    k.ne_j = RLayout<EL, MD, MODE_HOM, double>::NE;
-    k.smem_j = RLayout<EL, MD, MODE_HOM, double>::SMEM;
+    k.qstage = &stage_q<EL, MD, double, TL>;
+    k.qstage32 = &stage_q32<EL, MD, TL>;
+    k.ne_q = QLayout<EL, MD, double, TL>::NE;
+    k.smem_q = QLayout<EL, MD, double, TL>::SMEM;
+    k.ne_j = RLayout<EL, MD, MODE_HOM, double, TL>::NE;
+    k.smem_j = RLayout<EL, MD, MODE_HOM, double, TL>::SMEM;
   } else {
     k.qstage = nullptr;
     k.qstage32 = nullptr;
     k.ne_q = 0; k.smem_q = 0;
-    k.ne_j = RLayout<EL, MD, MODE_JV, double>::NE;
-    k.smem_j = RLayout<EL, MD, MODE_JV, double>::SMEM;
+    k.ne_j = RLayout<EL, MD, MODE_JV, double, TL>::NE;
+    k.smem_j = RLayout<EL, MD, MODE_JV, double, TL>::SMEM;
   }
   reg.push_back(k);
 }
 
-void register_tri(std::vector<KernelSet>& reg);
-void register_quad(std::vector<KernelSet>& reg);
-void register_hex(std::vector<KernelSet>& reg);
+// Registration of the compiled instances, one function per element family and tile.
+template <class TL> void register_tri_t(std::vector<KernelSet>& reg);
+template <class TL> void register_quad_t(std::vector<KernelSet>& reg);
+template <class TL> void register_hex_t(std::vector<KernelSet>& reg);
+void register_all(std::vector<KernelSet>& reg);
 
 }  // namespace ldg

@@ -97,14 +97,16 @@ template <class T> constexpr size_t block_inverse_smem(int n) {
   return (size_t)(n * n + n) * sizeof(T) + (size_t)n * sizeof(int) + 16;
 }
 
-// y_e = inv_e x_e for every element (arithmetic in T, FP64 vectors).
+// y_e = inv_e x_e for every element (arithmetic in T, FP64 vectors). Optional skips:
+// the whole launch (*skip != 0), or element e when inst_skip[inst[e]] != 0.
 template <class T>
 __global__ void k_block_apply(const T* __restrict__ inv, const double* __restrict__ x, double* __restrict__ y,
-                              int n, const int* skip) {
+                              int n, const int* skip, const int* inst, const int* inst_skip) {
   if (skip && *skip) return;
+  const int e = blockIdx.x;
+  if (inst_skip && inst_skip[inst[e]]) return;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* xs = (T*)sm_raw;
-  const int e = blockIdx.x;
   const double* xe = x + (size_t)e * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = (T)xe[i];
   __syncthreads();

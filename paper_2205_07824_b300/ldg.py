@@ -113,6 +113,22 @@ def lib():
         L.ldg_gmres.argtypes = [vp, dp, dp, dp, ctypes.POINTER(SolveReport)]
         L.ldg_newton_gmres.argtypes = [vp, dp, ctypes.POINTER(SolveReport)]
         L.ldg_newton_gmres_host.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveReport)]
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.ldg_autotune.argtypes = [vp, ctypes.c_int, ip, ctypes.POINTER(ctypes.c_double)]
+        L.ldg_set_tile.argtypes = [vp, ctypes.c_int]
+        L.ldg_get_tile.argtypes = [vp, ip, ip, ip, ip]
+        L.ldg_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(_Mesh), ip,
+                                       ctypes.POINTER(_Model), ctypes.POINTER(_Options), vp]
+        L.ldg_batch_destroy.argtypes = [vp]
+        L.ldg_batch_sizes.argtypes = [vp, i64p, i64p, i64p, ip]
+        L.ldg_batch_residual.argtypes = [vp, dp, dp]
+        L.ldg_batch_jvp.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+        L.ldg_batch_autotune.argtypes = [vp, ctypes.c_int, ip]
+        L.ldg_batch_solve.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(SolveReport), ctypes.POINTER(ctypes.c_double)]
+        L.ldg_batch_kernel_executions.restype = ctypes.c_int64
+        L.ldg_batch_kernel_executions.argtypes = [vp]
+        L.ldg_batch_last_error.restype = ctypes.c_char_p
+        L.ldg_batch_last_error.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -178,6 +194,22 @@ class LDG:
     def _check(self, rc):
         if rc != 0:
             raise LDGError(rc, lib().ldg_last_error(self._h).decode())
+
+    # ------------------------------------------------------------- tiles
+    def autotune(self, force: bool = False):
+        """Times the compiled tiles on this mesh and keeps the fastest J.v; returns (tile, ms)."""
+        t, ms = ctypes.c_int(), ctypes.c_double()
+        self._check(lib().ldg_autotune(self._h, int(force), ctypes.byref(t), ctypes.byref(ms)))
+        return t.value, ms.value
+
+    def set_tile(self, tile: int):
+        self._check(lib().ldg_set_tile(self._h, tile))
+
+    def get_tile(self):
+        """(tile, elements per CTA of the q-stage, residual and J.v kernels)."""
+        v = [ctypes.c_int() for _ in range(4)]
+        self._check(lib().ldg_get_tile(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def empty(self, n=None):
         import torch
@@ -315,3 +347,103 @@ class LDG:
         if check:
             self._check(rc)
         return rep.as_dict()
+
+
+class Batch:
+    """Many independent steady problems (per-instance mesh, order p and parameters mu)
+    solved together; see the batched section of ``include/ldg.h``.
+
+    meshes: list of synth.Mesh; ps: orders; mus: per-instance parameter sequences;
+    cases: per-instance analytic case (int or list). The batch vector is one float64
+    CUDA tensor of ``n_total`` entries; instance i is ``u[offsets[i]:offsets[i] + n_dof[i]]``.
+    """
+
+    def __init__(self, meshes, ps, model: int, cases, mus, nq1: int = 0, gmres_m: int = 30,
+                 max_restarts: int = 50, max_newton: int = 20, newton_rtol: float = 1e-8,
+                 gmres_rtol: float = 1e-3, krylov_precision: int = 0, precond: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Batch needs a CUDA device (no CPU fallback)")
+        L = lib()
+        n = len(meshes)
+        if isinstance(cases, int):
+            cases = [cases] * n
+        self._keep = []
+        md = (_Mesh * n)()
+        mo = (_Model * n)()
+        for i, m in enumerate(meshes):
+            xyz = np.ascontiguousarray(m.xyz, dtype=np.float64)
+            vid = np.ascontiguousarray(m.vid, dtype=np.int64)
+            mu = np.ascontiguousarray(np.asarray(mus[i], dtype=np.float64).reshape(-1))
+            self._keep += [xyz, vid, mu]
+            md[i] = _Mesh(m.etype, m.n_elem, xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          vid.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+            mo[i] = _Model(model, int(cases[i]), len(mu),
+                           mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(mu) else None)
+        pa = (ctypes.c_int * n)(*[int(p) for p in ps])
+        op = _Options(nq1, gmres_m, max_restarts, max_newton, newton_rtol, gmres_rtol, krylov_precision, precond, 0)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = L.ldg_batch_create(ctypes.byref(h), n, md, pa, mo, ctypes.byref(op), ctypes.c_void_p(stream.cuda_stream))
+        self._h = h
+        if rc != 0:
+            msg = L.ldg_batch_last_error(h).decode() if h.value else "invalid arguments"
+            L.ldg_batch_destroy(h)
+            self._h = None
+            raise LDGError(rc, msg)
+        tot = ctypes.c_int64()
+        off = (ctypes.c_int64 * n)()
+        nd = (ctypes.c_int64 * n)()
+        ng = ctypes.c_int()
+        L.ldg_batch_sizes(h, ctypes.byref(tot), off, nd, ctypes.byref(ng))
+        self.n_inst, self.n_total, self.n_groups = n, tot.value, ng.value
+        self.offsets, self.n_dof = list(off), list(nd)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ldg_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LDGError(rc, lib().ldg_batch_last_error(self._h).decode())
+
+    def empty(self):
+        import torch
+        return torch.empty(self.n_total, dtype=torch.float64, device="cuda")
+
+    def slice(self, u, i):
+        return u[self.offsets[i]:self.offsets[i] + self.n_dof[i]]
+
+    def residual(self, u, out=None):
+        out = self.empty() if out is None else out
+        n = self.n_total
+        self._check(lib().ldg_batch_residual(self._h, _ptr(u, n, "u"), _ptr(out, n, "out")))
+        return out
+
+    def jvp(self, u, v, precision: int = 0, out=None):
+        out = self.empty() if out is None else out
+        n = self.n_total
+        self._check(lib().ldg_batch_jvp(self._h, precision, _ptr(u, n, "u"), _ptr(v, n, "v"), _ptr(out, n, "out")))
+        return out
+
+    def autotune(self, force: bool = False):
+        tiles = (ctypes.c_int * self.n_groups)()
+        self._check(lib().ldg_batch_autotune(self._h, int(force), tiles))
+        return list(tiles)
+
+    def solve(self, u, use_graph: bool = True, check: bool = True):
+        """Newton-GMRES of every instance in place; returns (reports, elapsed_ms)."""
+        reps = (SolveReport * self.n_inst)()
+        ms = ctypes.c_double()
+        rc = lib().ldg_batch_solve(self._h, _ptr(u, self.n_total, "u"), int(use_graph), reps, ctypes.byref(ms))
+        if check:
+            self._check(rc)
+        return [r.as_dict() for r in reps], ms.value
+
+    def kernel_executions(self) -> int:
+        return int(lib().ldg_batch_kernel_executions(self._h))
