@@ -199,13 +199,17 @@ int emit_arnoldi(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle hc, in
     dir = b->d_zcur;
   }
   if ((rc = emit_jv(b, s, b->d_u, dir, b->d_w, b->opt.krylov_precision, b->d_skip_arn))) return rc;
-  kb_dots<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, b->pc ? b->d_zcur : nullptr, b->d_Z,
+  // classical Gram-Schmidt, two passes: h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2 (+ Givens)
+  KrySmall S{b->m};
+  kb_mdot<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, (int)S.h1(),
+                                      b->pc ? b->d_zcur : nullptr, b->d_Z, b->d_skip_arn);
+  kb_update<false><<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, (int)S.h1(), b->d_w, b->d_skip_arn);
+  kb_mdot<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, (int)S.h2(), nullptr, nullptr,
                                       b->d_skip_arn);
-  kb_orth<true><<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, b->d_skip_arn);
-  kb_orth<false><<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, b->d_skip_arn);
+  kb_update<true><<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, (int)S.h2(), b->d_w, b->d_skip_arn);
   kb_scale<<<b->nchunk, 256, 0, s>>>(sv, b->d_ctl, b->d_w, b->d_V, b->ntot, b->d_vcur, b->d_skip_arn);
   kb_arnoldi_end<<<1, 256, 0, s>>>(b->d_ctl, b->d_skip_arn, b->nseg, hc, use);
-  for (int i = 0; i < 5; ++i) count_launch();
+  for (int i = 0; i < 6; ++i) count_launch();
   BK(cudaGetLastError());
   return LDG_OK;
 }

@@ -117,70 +117,111 @@ __global__ void __launch_bounds__(KRY_T) kb_norm2(SegView sv, const double* __re
   if (threadIdx.x == 0) sv.tick[s] = 0u;
 }
 
-// Pass 1 of Gram-Schmidt at step j = ctl->j: h1_s = V[0..j]_s . w_s. With zsrc, the
-// same sweep stores Z[j] = zsrc (the preconditioned direction of flexible GMRES).
-__global__ void __launch_bounds__(KRY_T) kb_dots(SegView sv, const BatchCtl* ctl, const double* __restrict__ V,
-                                                int64_t ldv, const double* __restrict__ w,
+// Marks chunk c of segment s as done (its partials written); true in the last chunk
+// of the segment to arrive, after every partial of the segment is visible.
+__device__ __forceinline__ bool seg_arrive(const SegView& sv, int c, int s) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(sv.tick + s, 1u) == (unsigned)(sv.seg_nc[s] - 1);
+  __syncthreads();
+  return last;
+}
+
+constexpr int KB_RB = 512;   // rows of one multi-dot work unit (16 per lane)
+
+// Gram-Schmidt projections at step j = ctl->j: out_s = V[0..j]_s^T w_s, into
+// small_s + out_off. The chunk of w is staged in shared memory; the work units
+// (column k, 512-row block) are spread over the warps, each lane keeping 16
+// independent loads in flight, so a step with few columns still fills the memory
+// pipeline. With zsrc, the staging also stores Z[j] = zsrc (flexible GMRES).
+__global__ void __launch_bounds__(KRY_T) kb_mdot(SegView sv, const BatchCtl* ctl, const double* __restrict__ V,
+                                                int64_t ldv, const double* __restrict__ w, int out_off,
                                                 const double* __restrict__ zsrc, double* __restrict__ Z,
                                                 const int* skip) {
   const int c = blockIdx.x, s = sv.chunk_seg[c];
   if (skip[s]) return;
+  __shared__ double ws[KB_CHUNK];
+  __shared__ double red[KB_NV][KB_CHUNK / KB_RB];
   const int j = ctl->j, nvec = j + 1;
-  double acc[KB_NV];
-#pragma unroll
-  for (int k = 0; k < KB_NV; ++k) acc[k] = 0.0;
-  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += KRY_T) {
-    const double wi = w[i];
-#pragma unroll
-    for (int k = 0; k < KB_NV; ++k)
-      if (k < nvec) acc[k] = fma(V[k * ldv + i], wi, acc[k]);
-    if (zsrc) Z[j * ldv + i] = zsrc[i];
+  const int64_t lo = sv.chunk_lo[c];
+  const int len = (int)(sv.chunk_hi[c] - lo);
+  for (int t = threadIdx.x; t < len; t += KRY_T) {
+    ws[t] = w[lo + t];
+    if (zsrc) Z[j * ldv + lo + t] = zsrc[lo + t];
   }
-  if (!seg_partials<KB_NV>(acc, nvec, sv, c, s)) return;
-  KrySmall S{sv.m};
-  seg_reduce(sv, s, nvec, sv.small + (size_t)s * sv.ks + S.h1());
+  __syncthreads();
+  const int nb = (len + KB_RB - 1) / KB_RB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int u = warp; u < nvec * nb; u += KRY_T / 32) {
+    const int k = u / nb, b = u - k * nb;
+    const int r0 = b * KB_RB + lane;
+    const double* col = V + k * ldv + lo;
+    double a = 0.0;
+#pragma unroll
+    for (int t = 0; t < KB_RB / 32; ++t) {
+      const int r = r0 + 32 * t;
+      if (r < len) a = fma(col[r], ws[r], a);
+    }
+    a = warp_sum(a);
+    if (lane == 0) red[k][b] = a;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nvec) {
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += red[threadIdx.x][b];
+    sv.part[(size_t)c * KB_LDP + threadIdx.x] = t;
+  }
+  if (!seg_arrive(sv, c, s)) return;
+  seg_reduce(sv, s, nvec, sv.small + (size_t)s * sv.ks + out_off);
   if (threadIdx.x == 0) sv.tick[s] = 0u;
 }
 
-// w_s -= V[0..j]_s h_s. DOTS: the sweep also forms h2_s = V . w_new (the second pass's
-// projections). Otherwise it forms ||w_new||^2 and the last chunk completes Arnoldi
-// column j of the instance; an instance that converges or breaks down sets skip[s].
-template <bool DOTS>
-__global__ void __launch_bounds__(KRY_T) kb_orth(SegView sv, const BatchCtl* ctl, const double* __restrict__ V,
-                                                int64_t ldv, double* __restrict__ w, int* skip) {
+// w_s -= V[0..j]_s h_s with h_s at small_s + h_off (4 rows per thread per pass, the
+// column loop unrolled so 16 loads are in flight). NORM: also ||w_new||^2, and the
+// last chunk of the segment completes Arnoldi column j of the instance; an instance
+// that converges or breaks down sets skip[s].
+template <bool NORM>
+__global__ void __launch_bounds__(KRY_T) kb_update(SegView sv, const BatchCtl* ctl, const double* __restrict__ V,
+                                                  int64_t ldv, int h_off, double* __restrict__ w, int* skip) {
   const int c = blockIdx.x, s = sv.chunk_seg[c];
   if (skip[s]) return;
   const int j = ctl->j, nvec = j + 1;
-  KrySmall S{sv.m};
   double* sm = sv.small + (size_t)s * sv.ks;
   __shared__ double hs[KB_NV];
-  if (threadIdx.x < KB_NV) hs[threadIdx.x] = (int)threadIdx.x < nvec ? sm[(DOTS ? S.h1() : S.h2()) + threadIdx.x] : 0.0;
+  if ((int)threadIdx.x < KB_NV) hs[threadIdx.x] = (int)threadIdx.x < nvec ? sm[h_off + threadIdx.x] : 0.0;
   __syncthreads();
-  constexpr int NA = DOTS ? KB_NV : 1;
-  double acc[NA];
+  const int64_t lo = sv.chunk_lo[c], hi = sv.chunk_hi[c];
+  double acc = 0.0;
+  for (int64_t base = lo + threadIdx.x; base < hi; base += 4 * KRY_T) {
+    double t[4];
 #pragma unroll
-  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
-  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += KRY_T) {
-    double vv[KB_NV];
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = base + q * KRY_T;
+      t[q] = i < hi ? w[i] : 0.0;
+    }
+#pragma unroll 4
+    for (int k = 0; k < nvec; ++k) {
+      const double hk = hs[k];
+      const double* col = V + k * ldv;
 #pragma unroll
-    for (int k = 0; k < KB_NV; ++k) vv[k] = k < nvec ? V[k * ldv + i] : 0.0;
-    double t = w[i];
+      for (int q = 0; q < 4; ++q) {
+        const int64_t i = base + q * KRY_T;
+        if (i < hi) t[q] = fma(-col[i], hk, t[q]);
+      }
+    }
 #pragma unroll
-    for (int k = 0; k < KB_NV; ++k) t = fma(-vv[k], hs[k], t);
-    w[i] = t;
-    if constexpr (DOTS) {
-#pragma unroll
-      for (int k = 0; k < KB_NV; ++k) acc[k] = fma(vv[k], t, acc[k]);
-    } else {
-      acc[0] = fma(t, t, acc[0]);
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = base + q * KRY_T;
+      if (i < hi) {
+        w[i] = t[q];
+        acc = fma(t[q], t[q], acc);
+      }
     }
   }
-  if constexpr (DOTS) {
-    if (!seg_partials<NA>(acc, nvec, sv, c, s)) return;
-    seg_reduce(sv, s, nvec, sm + S.h2());
-    if (threadIdx.x == 0) sv.tick[s] = 0u;
-  } else {
-    if (!seg_partials<1>(acc, 1, sv, c, s)) return;
+  if constexpr (NORM) {
+    double a1[1] = {acc};
+    if (!seg_partials<1>(a1, 1, sv, c, s)) return;
     __shared__ double nrm_s[1];
     seg_reduce(sv, s, 1, nrm_s);
     __syncthreads();

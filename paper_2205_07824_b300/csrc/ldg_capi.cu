@@ -336,12 +336,26 @@ int pc_apply(ldg_ctx* ctx, const double* x, double* y, const int* skip, const in
   const int threads = std::min(256, ((n + 31) / 32) * 32);
   const int* inst = inst_skip ? ctx->ext_inst : nullptr;
   if (inst_skip && !inst) return fail(ctx, LDG_ERR_ARG, "per-instance skip on a context without instances");
-  if (ctx->binv_prec == LDG_FP64)
-    k_block_apply<double><<<(unsigned)ctx->E, threads, n * sizeof(double), ctx->stream>>>((const double*)ctx->d_binv, x,
-                                                                                         y, n, skip, inst, inst_skip);
-  else
-    k_block_apply<float><<<(unsigned)ctx->E, threads, n * sizeof(float), ctx->stream>>>((const float*)ctx->d_binv, x, y,
-                                                                                       n, skip, inst, inst_skip);
+  const int64_t E = ctx->E;
+  const unsigned gw = (unsigned)((E + 7) / 8);
+  const bool f64 = ctx->binv_prec == LDG_FP64;
+  const double* bd = (const double*)ctx->d_binv;
+  const float* bf = (const float*)ctx->d_binv;
+  // one warp per element up to 128 rows; one CTA per element beyond
+  if (n <= 32) {
+    if (f64) k_block_apply_warp<double, 1><<<gw, 256, 0, ctx->stream>>>(bd, x, y, n, E, skip, inst, inst_skip);
+    else k_block_apply_warp<float, 1><<<gw, 256, 0, ctx->stream>>>(bf, x, y, n, E, skip, inst, inst_skip);
+  } else if (n <= 64) {
+    if (f64) k_block_apply_warp<double, 2><<<gw, 256, 0, ctx->stream>>>(bd, x, y, n, E, skip, inst, inst_skip);
+    else k_block_apply_warp<float, 2><<<gw, 256, 0, ctx->stream>>>(bf, x, y, n, E, skip, inst, inst_skip);
+  } else if (n <= 128) {
+    if (f64) k_block_apply_warp<double, 4><<<gw, 256, 0, ctx->stream>>>(bd, x, y, n, E, skip, inst, inst_skip);
+    else k_block_apply_warp<float, 4><<<gw, 256, 0, ctx->stream>>>(bf, x, y, n, E, skip, inst, inst_skip);
+  } else if (f64) {
+    k_block_apply<double><<<(unsigned)E, threads, n * sizeof(double), ctx->stream>>>(bd, x, y, n, skip, inst, inst_skip);
+  } else {
+    k_block_apply<float><<<(unsigned)E, threads, n * sizeof(float), ctx->stream>>>(bf, x, y, n, skip, inst, inst_skip);
+  }
   count_launch();
   CK(cudaGetLastError());
   return LDG_OK;

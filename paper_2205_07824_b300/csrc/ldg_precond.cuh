@@ -118,6 +118,49 @@ __global__ void k_block_apply(const T* __restrict__ inv, const double* __restric
   }
 }
 
+// y_e = inv_e x_e with one warp per element (n <= 32 RW): lane r holds x_e rows
+// r, r + 32, ... and computes the same output rows; column c of the block is read as
+// one coalesced run of n values while x_e[c] is broadcast by a warp shuffle. Skips
+// as k_block_apply. 8 elements per CTA.
+template <class T, int RW>
+__global__ void __launch_bounds__(256) k_block_apply_warp(const T* __restrict__ inv, const double* __restrict__ x,
+                                                         double* __restrict__ y, int n, int64_t E, const int* skip,
+                                                         const int* inst, const int* inst_skip) {
+  if (skip && *skip) return;
+  const int64_t e = blockIdx.x * (int64_t)8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= E) return;
+  if (inst_skip && inst_skip[inst[e]]) return;
+  const double* xe = x + e * n;
+  T xr[RW], acc[RW];
+#pragma unroll
+  for (int t = 0; t < RW; ++t) {
+    const int r = lane + 32 * t;
+    xr[t] = r < n ? (T)xe[r] : T(0);
+    acc[t] = T(0);
+  }
+  const T* Iv = inv + e * n * n;
+#pragma unroll
+  for (int tb = 0; tb < RW; ++tb) {
+    const int cn = min(32, n - 32 * tb);
+#pragma unroll 4
+    for (int cc = 0; cc < cn; ++cc) {
+      const T xc = __shfl_sync(0xffffffffu, xr[tb], cc);
+      const T* col = Iv + (size_t)(32 * tb + cc) * n;
+#pragma unroll
+      for (int t = 0; t < RW; ++t) {
+        const int r = lane + 32 * t;
+        if (r < n) acc[t] = fma(col[r], xc, acc[t]);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < RW; ++t) {
+    const int r = lane + 32 * t;
+    if (r < n) y[e * n + r] = (double)acc[t];
+  }
+}
+
 // probe[e][l'] = 1 where colour[e] == colour and l' == l, else 0
 __global__ void k_probe(double* probe, const int* colour, int c, int l, int nloc, int64_t E) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
