@@ -306,7 +306,8 @@ int ldg_get_tile(const ldg_ctx* ctx, int* tile, int* ne_q, int* ne_r, int* ne_j)
  * opts (shared by all instances): gmres_m, max_restarts, max_newton, newton_rtol,
  * gmres_rtol, krylov_precision, precond (LDG_PC_NONE or LDG_PC_BJACOBI; the
  * block-Jacobi blocks are built inside ldg_batch_solve at the initial guess);
- * nq1 = 0 picks the default per order. Only steady problems (no time scheme).
+ * nq1 = 0 picks the default per order. Time schemes: ldg_batch_set_time (as ldg_set_time,
+ * with batch vectors); the default is steady.
  * reps: n_inst reports (host), one per instance. *elapsed_ms: wall time of the whole
  * batched solve, set-up included. */
 typedef struct ldg_batch ldg_batch;
@@ -316,6 +317,11 @@ int ldg_batch_destroy(ldg_batch* b);
 /* n_total doubles in the batch vector; offsets / n_dof: [n_inst] host arrays (may be NULL);
  * n_groups: number of (element, p) groups. */
 int ldg_batch_sizes(const ldg_batch* b, int64_t* n_total, int64_t* offsets, int64_t* n_dof, int* n_groups);
+/* Time scheme of every instance (see ldg_set_time; u_n_dev / u_nm1_dev are batch vectors).
+ * The boundary-data time is kept in device memory, so a captured solve graph stays valid
+ * from step to step; a change of scheme or dt re-captures it at the next solve. */
+int ldg_batch_set_time(ldg_batch* b, int scheme, double t, double dt, const double* u_n_dev,
+                       const double* u_nm1_dev);
 /* R(u) and J(u) v of every instance (batch vectors, device). */
 int ldg_batch_residual(ldg_batch* b, const double* u_dev, double* r_dev);
 int ldg_batch_jvp(ldg_batch* b, int precision, const double* u_dev, const double* v_dev, double* jv_dev);

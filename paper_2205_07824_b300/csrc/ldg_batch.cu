@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -59,6 +60,8 @@ struct ldg_batch {
   double *d_u = nullptr, *d_res = nullptr, *d_r = nullptr, *d_x = nullptr, *d_w = nullptr;
   double *d_vcur = nullptr, *d_zcur = nullptr, *d_V = nullptr, *d_Z = nullptr;
   bool pc = false;
+  unsigned int* d_bar = nullptr;   // grid barrier of the fused Arnoldi step: count, generation, error
+  int coop_grid = 0;               // CTAs of the fused (cooperative) Arnoldi step; 0 = split kernels
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long k_pre = 0, k_a = 0, k_b = 0, k_c = 0;   // kernels per graph part (captured)
@@ -89,7 +92,7 @@ SegView seg_view(const ldg_batch* b) {
   v.seg_c0 = b->d_seg_c0; v.seg_nc = b->d_seg_nc;
   v.part = b->d_part; v.tick = b->d_tick;
   v.small = b->d_small; v.ks = (int64_t)KrySmall{b->m}.total(); v.m = b->m;
-  v.sflags = b->d_sflags; v.nseg = b->nseg;
+  v.sflags = b->d_sflags; v.nseg = b->nseg; v.nchunk = b->nchunk;
   return v;
 }
 
@@ -110,6 +113,7 @@ int emit_residual(ldg_batch* b, cudaStream_t s, const double* u, double* r, cons
       a.q = g.ctx->d_q;
     }
     a.u = u + g.off; a.out = r + g.off;
+    a.hist = g.ctx->scheme != LDG_STEADY ? g.ctx->d_hist : nullptr;
     BK(g.ctx->ks->residual(MODE_R, a, s));
   }
   return LDG_OK;
@@ -199,6 +203,27 @@ int emit_arnoldi(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle hc, in
     dir = b->d_zcur;
   }
   if ((rc = emit_jv(b, s, b->d_u, dir, b->d_w, b->opt.krylov_precision, b->d_skip_arn))) return rc;
+  if (b->coop_grid > 0) {
+    // the whole classical Gram-Schmidt step (two passes, Givens, v_{j+1}) in one cooperative launch
+    double* V = b->d_V;
+    int64_t ldv = b->ntot;
+    double* w = b->d_w;
+    const double* zsrc = b->pc ? b->d_zcur : nullptr;
+    double* Z = b->d_Z;
+    double* vcur = b->d_vcur;
+    double* part = b->d_part;
+    int* skip = b->d_skip_arn;
+    GridBar gb{b->d_bar, b->d_bar + 1, (int*)(b->d_bar + 2)};
+    const BatchCtl* ctl = b->d_ctl;
+    SegView svv = sv;
+    void* args[] = {&svv, &ctl, &V, &ldv, &w, &zsrc, &Z, &vcur, &part, &skip, &gb};
+    BK(cudaLaunchCooperativeKernel((const void*)kb_arnoldi_fused, dim3(b->coop_grid), dim3(KRY_T), args, 0, s));
+    kb_arnoldi_end<<<1, 256, 0, s>>>(b->d_ctl, b->d_skip_arn, b->nseg, hc, use);
+    count_launch();
+    count_launch();
+    BK(cudaGetLastError());
+    return LDG_OK;
+  }
   // classical Gram-Schmidt, two passes: h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2 (+ Givens)
   KrySmall S{b->m};
   kb_mdot<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, (int)S.h1(),
@@ -359,7 +384,7 @@ void free_batch(ldg_batch* b) {
                   (void*)b->d_chunk_lo, (void*)b->d_chunk_hi, (void*)b->d_part, (void*)b->d_tick, (void*)b->d_small,
                   (void*)b->d_sflags, (void*)b->d_st, (void*)b->d_ctl, (void*)b->d_skip_newt, (void*)b->d_skip_gm,
                   (void*)b->d_skip_arn, (void*)b->d_u, (void*)b->d_res, (void*)b->d_r, (void*)b->d_x, (void*)b->d_w,
-                  (void*)b->d_vcur, (void*)b->d_zcur, (void*)b->d_V, (void*)b->d_Z})
+                  (void*)b->d_vcur, (void*)b->d_zcur, (void*)b->d_V, (void*)b->d_Z, (void*)b->d_bar})
     cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
@@ -466,14 +491,18 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
   if ((rc = upload(b, &b->d_mtab, mtab))) return rc;
   for (BGroup& g : b->groups) g.ctx->ext_mtab = b->d_mtab;
   // chunk tables
+  // chunk size: a power of two in [512, KB_CHUNK] giving about two chunks per SM, so
+  // small batches still spread over the whole GPU
+  int64_t ch = 512;
+  while (ch < KB_CHUNK && ch * 148 * 2 < b->ntot) ch *= 2;
   std::vector<int> cseg, c0(b->nseg), nc(b->nseg);
   std::vector<int64_t> clo, chi;
   for (int s = 0; s < b->nseg; ++s) {
     c0[s] = (int)cseg.size();
-    for (int64_t lo = seg_off[s]; lo < seg_off[s] + seg_n[s]; lo += KB_CHUNK) {
+    for (int64_t lo = seg_off[s]; lo < seg_off[s] + seg_n[s]; lo += ch) {
       cseg.push_back(s);
       clo.push_back(lo);
-      chi.push_back(std::min(lo + KB_CHUNK, seg_off[s] + seg_n[s]));
+      chi.push_back(std::min(lo + ch, seg_off[s] + seg_n[s]));
     }
     nc[s] = (int)cseg.size() - c0[s];
   }
@@ -482,7 +511,23 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
       (rc = upload(b, &b->d_chunk_hi, chi)) || (rc = upload(b, &b->d_seg_c0, c0)) || (rc = upload(b, &b->d_seg_nc, nc)))
     return rc;
   const size_t ks = KrySmall{b->m}.total();
-  BK(cudaMalloc(&b->d_part, (size_t)b->nchunk * KB_LDP * sizeof(double)));
+  BK(cudaMalloc(&b->d_part, (size_t)3 * b->nchunk * KB_LDP * sizeof(double)));
+  BK(cudaMalloc(&b->d_bar, 4 * sizeof(unsigned int)));
+  BK(cudaMemset(b->d_bar, 0, 4 * sizeof(unsigned int)));
+  {
+    // fused Arnoldi step: as many co-resident CTAs as the chunks need, at most what fits
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    BK(cudaGetDevice(&dev));
+    BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_arnoldi_fused, KRY_T, 0));
+    // the split kernels measured faster on both the single vortex and the 256-instance
+    // batch (graph launches hide the per-kernel latency better than grid barriers do);
+    // LDG_BATCH_FUSED_GS=1 selects the fused form
+    const char* fused = getenv("LDG_BATCH_FUSED_GS");
+    if (coop && per_sm > 0 && fused && fused[0] == '1')
+      b->coop_grid = (int)std::min<int64_t>(b->nchunk, (int64_t)std::min(per_sm, 2) * sms);
+  }
   BK(cudaMalloc(&b->d_tick, b->nseg * sizeof(unsigned int)));
   BK(cudaMemset(b->d_tick, 0, b->nseg * sizeof(unsigned int)));
   BK(cudaMalloc(&b->d_small, (size_t)b->nseg * ks * sizeof(double)));
@@ -541,6 +586,25 @@ int ldg_batch_sizes(const ldg_batch* b, int64_t* n_total, int64_t* offsets, int6
     if (n_dof) n_dof[i] = b->user_n[i];
   }
   if (n_groups) *n_groups = (int)b->groups.size();
+  return LDG_OK;
+}
+
+int ldg_batch_set_time(ldg_batch* b, int scheme, double t, double dt, const double* un, const double* unm1) {
+  if (!b || b->groups.empty()) return LDG_ERR_ARG;
+  if (scheme != LDG_STEADY && (!un || (scheme == LDG_BDF2 && !unm1))) return bfail(b, LDG_ERR_ARG, "missing history");
+  bool changed = false;
+  for (BGroup& g : b->groups) {
+    g.ctx->stream = b->stream;
+    const double a0_before = g.ctx->a0dt;
+    const int rc = ldg_set_time(g.ctx, scheme, t, dt, un ? un + g.off : nullptr, unm1 ? unm1 + g.off : nullptr);
+    if (rc) return gfail(b, g, rc);
+    changed |= g.ctx->a0dt != a0_before;
+  }
+  // the captured kernels hold a0/dt by value; the time itself is read from device memory
+  if (changed) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  }
   return LDG_OK;
 }
 
@@ -604,7 +668,10 @@ int ldg_batch_solve(ldg_batch* b, double* u_dev, int use_graph, ldg_solve_report
   BatchCtl ctl;
   BK(cudaMemcpyAsync(st.data(), b->d_st, st.size() * sizeof(SegState), cudaMemcpyDeviceToHost, s));
   BK(cudaMemcpyAsync(&ctl, b->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, s));
+  unsigned int bar[4] = {0, 0, 0, 0};
+  BK(cudaMemcpyAsync(bar, b->d_bar, sizeof(bar), cudaMemcpyDeviceToHost, s));
   BK(cudaStreamSynchronize(s));
+  if (bar[2]) return bfail(b, LDG_ERR_CUDA, "fused Arnoldi step: a grid barrier timed out");
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (use_graph) {
     b->last_exec = b->k_pre + ctl.trips_a * b->k_a + ctl.trips_b * b->k_b + ctl.trips_c * b->k_c;

@@ -40,6 +40,7 @@ struct SegView {
   int m;
   int* sflags;              // [n_seg][4]: 0 Arnoldi done, 1 columns, 2 breakdown
   int nseg;
+  int nchunk;
 };
 
 // Per-instance Newton state.
@@ -225,11 +226,224 @@ __global__ void __launch_bounds__(KRY_T) kb_update(SegView sv, const BatchCtl* c
     __shared__ double nrm_s[1];
     seg_reduce(sv, s, 1, nrm_s);
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    sv.tick[s] = 0u;
-    int* fl = sv.sflags + 4 * s;
-    arnoldi_column(sm, sv.m, j, nrm_s[0], fl);
-    if (fl[0]) skip[s] = 1;
+    if (threadIdx.x == 0) sv.tick[s] = 0u;
+    const int done = arnoldi_column_block(sm, sv.m, j, nrm_s[0], sv.sflags + 4 * s);
+    if (threadIdx.x == 0 && done) skip[s] = 1;
+  }
+}
+
+// ------------------------------------------------ fused Arnoldi step (cooperative)
+// Grid barrier of a cooperative launch (all CTAs co-resident). Sense by generation
+// counter; the wait gives up after about one second of SM clock (2^31 cycles),
+// records the failure in *err and continues, so a broken launch ends instead of
+// hanging.
+struct GridBar {
+  unsigned int* count;
+  unsigned int* gen;
+  int* err;
+};
+
+__device__ __forceinline__ void grid_sync(const GridBar& gb) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* genp = gb.gen;
+    const unsigned int g = *genp;
+    __threadfence();
+    if (atomicAdd(gb.count, 1u) == gridDim.x - 1) {
+      *gb.count = 0u;
+      __threadfence();
+      atomicAdd(gb.gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*genp == g) {
+        if (clock64() - t0 > (1ll << 31)) {
+          atomicExch(gb.err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// out[k] (shared memory) = sum over the chunks of segment s of part[c][k], in chunk
+// order (whole CTA; every CTA computes the same bits).
+__device__ __forceinline__ void seg_sum(const SegView& sv, const double* part, int s, int nvec, double* out) {
+  __shared__ double gred[KRY_T];
+  int kw = 1;
+  while (kw < nvec) kw <<= 1;
+  const int groups = KRY_T / kw;
+  const int k = threadIdx.x % kw, grp = threadIdx.x / kw;
+  const int c0 = sv.seg_c0[s], nc = sv.seg_nc[s];
+  double t = 0.0;
+  if (k < nvec)
+    for (int b = grp; b < nc; b += groups) t += __ldcg(part + (size_t)(c0 + b) * KB_LDP + k);
+  gred[threadIdx.x] = t;
+  __syncthreads();
+  if ((int)threadIdx.x < nvec) {
+    double r = 0.0;
+    for (int g = 0; g < groups; ++g) r += gred[g * kw + threadIdx.x];
+    out[threadIdx.x] = r;
+  }
+  __syncthreads();
+}
+
+// Chunk c: part[c][k] = V[k] . w over the chunk (w staged in ws), k < nvec.
+__device__ __forceinline__ void chunk_mdot(const SegView& sv, int c, int nvec, const double* __restrict__ V,
+                                           int64_t ldv, const double* w, double* ws, double (*red)[KB_CHUNK / KB_RB],
+                                           double* part) {
+  const int64_t lo = sv.chunk_lo[c];
+  const int len = (int)(sv.chunk_hi[c] - lo);
+  for (int t = threadIdx.x; t < len; t += KRY_T) ws[t] = __ldcg(w + lo + t);
+  __syncthreads();
+  const int nb = (len + KB_RB - 1) / KB_RB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int u = warp; u < nvec * nb; u += KRY_T / 32) {
+    const int k = u / nb, b = u - k * nb;
+    const int r0 = b * KB_RB + lane;
+    const double* col = V + k * ldv + lo;
+    double a = 0.0;
+#pragma unroll
+    for (int t = 0; t < KB_RB / 32; ++t) {
+      const int r = r0 + 32 * t;
+      if (r < len) a = fma(col[r], ws[r], a);
+    }
+    a = warp_sum(a);
+    if (lane == 0) red[k][b] = a;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nvec) {
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += red[threadIdx.x][b];
+    part[(size_t)c * KB_LDP + threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// Chunk c: w -= V[0..nvec) h (h in shared memory); returns this thread's share of
+// ||w_new||^2.
+__device__ __forceinline__ double chunk_update(const SegView& sv, int c, int nvec, const double* __restrict__ V,
+                                               int64_t ldv, const double* hs, double* w) {
+  const int64_t lo = sv.chunk_lo[c], hi = sv.chunk_hi[c];
+  double acc = 0.0;
+  for (int64_t base = lo + threadIdx.x; base < hi; base += 4 * KRY_T) {
+    double t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = base + q * KRY_T;
+      t[q] = i < hi ? __ldcg(w + i) : 0.0;
+    }
+#pragma unroll 4
+    for (int k = 0; k < nvec; ++k) {
+      const double hk = hs[k];
+      const double* col = V + k * ldv;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t i = base + q * KRY_T;
+        if (i < hi) t[q] = fma(-col[i], hk, t[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = base + q * KRY_T;
+      if (i < hi) {
+        w[i] = t[q];
+        acc = fma(t[q], t[q], acc);
+      }
+    }
+  }
+  return acc;
+}
+
+// One Arnoldi step j = ctl->j of every active instance, as one cooperative launch:
+//   phase 1  h1 = V^T w                    (and Z[j] = zsrc for flexible GMRES)
+//   phase 2  w -= V h1, h2 = V^T w
+//   phase 3  w -= V h2, ||w||^2
+//   phase 4  v_{j+1} = vcur = w / ||w||; the CTA owning the instance's first chunk
+//            forms Arnoldi column j (h1 + h2, ||w||), its Givens rotation and the
+//            convergence test, and sets skip[s] when the instance is done.
+// Grid barriers separate the phases; every CTA sums its instance's partials itself in
+// chunk order, so no ticket is needed and the result is deterministic.
+__global__ void __launch_bounds__(KRY_T) kb_arnoldi_fused(SegView sv, const BatchCtl* ctl, double* V, int64_t ldv,
+                                                         double* w, const double* zsrc, double* Z, double* vcur,
+                                                         double* part, int* skip, GridBar gb) {
+  __shared__ double ws[KB_CHUNK];
+  __shared__ double red[KB_NV][KB_CHUNK / KB_RB];
+  __shared__ double hs[KB_NV], hs2[KB_NV];
+  const int j = ctl->j, nvec = j + 1;
+  const int nchunk = sv.nchunk;
+  double* part1 = part;
+  double* part2 = part + (size_t)nchunk * KB_LDP;
+  double* part3 = part + (size_t)2 * nchunk * KB_LDP;
+  // phase 1
+  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    const int s = sv.chunk_seg[c];
+    if (skip[s]) continue;
+    if (zsrc) {
+      const int64_t lo = sv.chunk_lo[c], hi = sv.chunk_hi[c];
+      for (int64_t i = lo + threadIdx.x; i < hi; i += KRY_T) Z[j * ldv + i] = zsrc[i];
+    }
+    chunk_mdot(sv, c, nvec, V, ldv, w, ws, red, part1);
+  }
+  grid_sync(gb);
+  // phase 2
+  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    const int s = sv.chunk_seg[c];
+    if (skip[s]) continue;
+    seg_sum(sv, part1, s, nvec, hs);
+    chunk_update(sv, c, nvec, V, ldv, hs, w);
+    __syncthreads();
+    chunk_mdot(sv, c, nvec, V, ldv, w, ws, red, part2);
+  }
+  grid_sync(gb);
+  // phase 3
+  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    const int s = sv.chunk_seg[c];
+    if (skip[s]) continue;
+    seg_sum(sv, part2, s, nvec, hs);
+    double a1[1] = {chunk_update(sv, c, nvec, V, ldv, hs, w)};
+    // block sum of ||w||^2 into part3[c][0]
+    const double v = warp_sum(a1[0]);
+    if ((threadIdx.x & 31) == 0) red[0][threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < KRY_T / 32; ++q) t += red[0][q];
+      part3[(size_t)c * KB_LDP] = t;
+    }
+    __syncthreads();
+  }
+  grid_sync(gb);
+  // phase 4
+  KrySmall S{sv.m};
+  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    const int s = sv.chunk_seg[c];
+    if (skip[s]) continue;
+    seg_sum(sv, part3, s, 1, hs);
+    const double nrm2 = hs[0];
+    const double hn = sqrt(nrm2);
+    const double f = hn > 0.0 ? 1.0 / hn : 0.0;
+    const int64_t lo = sv.chunk_lo[c], hi = sv.chunk_hi[c];
+    double* out = V + (size_t)(j + 1) * ldv;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += KRY_T) {
+      const double t = __ldcg(w + i) * f;
+      out[i] = t;
+      vcur[i] = t;
+    }
+    if (c != sv.seg_c0[s]) continue;
+    // Arnoldi column j and its Givens rotation
+    double* sm = sv.small + (size_t)s * sv.ks;
+    seg_sum(sv, part1, s, nvec, hs);
+    seg_sum(sv, part2, s, nvec, hs2);
+    if ((int)threadIdx.x < nvec) {
+      sm[S.h1() + threadIdx.x] = hs[threadIdx.x];
+      sm[S.h2() + threadIdx.x] = hs2[threadIdx.x];
+    }
+    __syncthreads();
+    const int done = arnoldi_column_block(sm, sv.m, j, nrm2, sv.sflags + 4 * s);
+    if (threadIdx.x == 0 && done) skip[s] = 1;
+    __syncthreads();
   }
 }
 

@@ -90,6 +90,8 @@ __global__ void k_interp_nodes(int dim, int npe, int ncu, int64_t E, const doubl
   for (int c = 0; c < ncu; ++c) u[(e * ncu + c) * npe + n] = st[c];
 }
 
+__global__ void k_set_scalar(double* dst, double v) { *dst = v; }
+
 __global__ void k_hist(int64_t n, double c1, const double* a, double c2, const double* b, double* out) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = c1 * a[i] + (b ? c2 * b[i] : 0.0);
@@ -100,7 +102,7 @@ KArgs base_args(ldg_ctx* c) {
   std::memset(&a, 0, sizeof(a));
   a.geo = c->d_geo; a.nbr = c->d_nbr; a.nbf = c->d_nbf; a.ops = c->d_ops; a.opsf = c->d_opsf; a.perm = c->d_perm;
   a.a0dt = c->a0dt; a.t = c->t; a.mp = c->mp; a.E = (int)c->E;
-  a.inst = c->ext_inst; a.mtab = c->ext_mtab;
+  a.inst = c->ext_inst; a.mtab = c->ext_mtab; a.t_dev = c->d_t;
   a.blk_col = -1;
   return a;
 }
@@ -769,7 +771,7 @@ int ldg_destroy(ldg_ctx* ctx) {
   cudaFree(ctx->d_ops); cudaFree(ctx->d_opsf); cudaFree(ctx->d_geo); cudaFree(ctx->d_nbr); cudaFree(ctx->d_nbf); cudaFree(ctx->d_perm);
   cudaFree(ctx->d_xn); cudaFree(ctx->d_q); cudaFree(ctx->d_dq); cudaFree(ctx->d_hist);
   cudaFree(ctx->d_V); cudaFree(ctx->d_r); cudaFree(ctx->d_w); cudaFree(ctx->d_res); cudaFree(ctx->d_x); cudaFree(ctx->d_small); cudaFree(ctx->d_part);
-  cudaFree(ctx->d_flags); cudaFree(ctx->d_ticket);
+  cudaFree(ctx->d_flags); cudaFree(ctx->d_ticket); cudaFree(ctx->d_t);
   cudaFree(ctx->d_colour); cudaFree(ctx->d_blocks); cudaFree(ctx->d_binv); cudaFree(ctx->d_Z);
   cudaFree(ctx->d_probe); cudaFree(ctx->d_jp); cudaFree(ctx->d_status);
   {
@@ -873,6 +875,10 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   }
   CK(cudaMalloc(&ctx->d_hist, n * sizeof(double)));
   if (!lean) CK(cudaMalloc(&ctx->d_V, (size_t)(ctx->m + 1) * n * sizeof(double)));
+  if (lean) {
+    CK(cudaMalloc(&ctx->d_t, sizeof(double)));
+    CK(cudaMemset(ctx->d_t, 0, sizeof(double)));
+  }
   CK(cudaMalloc(&ctx->d_r, n * sizeof(double)));
   CK(cudaMalloc(&ctx->d_w, n * sizeof(double)));
   CK(cudaMalloc(&ctx->d_res, n * sizeof(double)));
@@ -940,6 +946,11 @@ int ldg_sizes(const ldg_ctx* ctx, int64_t* n_dof, int* n_pe, int* n_cu, int* dim
 int ldg_set_time(ldg_ctx* ctx, int scheme, double t, double dt, const double* un, const double* unm1) {
   if (!ctx || !ctx->ks) return LDG_ERR_ARG;
   ctx->t = t;
+  if (ctx->d_t) {
+    k_set_scalar<<<1, 1, 0, ctx->stream>>>(ctx->d_t, t);
+    count_launch();
+    CK(cudaGetLastError());
+  }
   if (scheme == LDG_STEADY) { ctx->scheme = scheme; ctx->a0dt = 0.0; return LDG_OK; }
   if ((scheme != LDG_BDF1 && scheme != LDG_BDF2) || !(dt > 0) || !un || (scheme == LDG_BDF2 && !unm1))
     return fail(ctx, LDG_ERR_ARG, "ldg_set_time: bad scheme, step or history");

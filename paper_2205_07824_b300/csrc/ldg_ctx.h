@@ -88,6 +88,7 @@ struct ldg_ctx {
   const int* ext_inst = nullptr;
   const ldg::ModelParams* ext_mtab = nullptr;
   bool lean = false;           // no Krylov basis or preconditioned vectors (batch groups)
+  double* d_t = nullptr;       // lean contexts: boundary-data time in device memory
   std::string err;
 };
 

@@ -58,7 +58,8 @@ struct KArgs {
                               // of each element's diagonal block dR_K/du_K is written to blk_out
   double* blk_out;            // [E][NLOC][NLOC] column-major blocks (NLOC = NCU * NPE)
   double a0dt;                // a0 / dt of the BDF scheme, 0 when steady
-  double t;
+  double t;                   // time of the boundary data ...
+  const double* t_dev;        // ... or, when set, read from device memory (graph replays)
   ModelParams mp;             // model parameters (all elements, unless inst is set)
   const int* inst;            // optional [E]: instance of each element (batched contexts) ...
   const ModelParams* mtab;    // ... indexing this per-instance parameter table
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
       double x[3];
       face_xi<EL>(OPS, f, k, xi);
       phys_x<DIM>(g, xi, x);
-      exact_state<DIM>(elem_mp(a, e0 + e), NCU, x, a.t, gb);
+      exact_state<DIM>(elem_mp(a, e0 + e), NCU, x, a.t_dev ? *a.t_dev : a.t, gb);
     }
     for (int c = 0; c < NCU; ++c) {
       int base = ((e * NF + f) * NCU + c) * NFQ;
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
           double x[3], gd[4] = {0.0, 0.0, 0.0, 0.0};
           face_xi<EL>(OPS, f, k, xi);
           phys_x<DIM>(g, xi, x);
-          exact_state<DIM>(elem_mp(a, e0 + e), NCU, x, a.t, gd);
+          exact_state<DIM>(elem_mp(a, e0 + e), NCU, x, a.t_dev ? *a.t_dev : a.t, gd);
           for (int c = 0; c < 4; ++c) gb[c] = R(gd[c]);
         }
         MD::fhat_bnd(um, qm, gb, nrm, fh, MPs[e]);

@@ -94,43 +94,55 @@ __device__ __forceinline__ void reduce_partials(const double* part, int ldp, int
 }
 
 // Completes Arnoldi column j from the two Gram-Schmidt passes' projections h1 + h2 and
-// ||w||^2 (single thread): H(:, j) = h1 + h2, H(j+1, j) = ||w||, applies the previous
-// Givens rotations, forms rotation j, rotates g, and sets flags[0] (done) when
-// |g_{j+1}| <= sc[3] or on breakdown (flags[2]); flags[1] = j + 1 columns.
-__device__ __forceinline__ void arnoldi_column(double* small, int m, int j, double nrm2, int* flags) {
+// ||w||^2: H(:, j) = h1 + h2, H(j+1, j) = ||w||, applies the previous Givens rotations,
+// forms rotation j, rotates g, and sets flags[0] (done) when |g_{j+1}| <= sc[3] or on
+// breakdown (flags[2]); flags[1] = j + 1 columns. The previous rotations and h1 + h2 are
+// staged in shared memory by the whole CTA, so the one-thread rotation loop reads no
+// global memory. Call from all threads of the CTA; returns flags[0] in every thread.
+__device__ __forceinline__ int arnoldi_column_block(double* small, int m, int j, double nrm2, int* flags) {
+  __shared__ double cs_s[32], sn_s[32], col_s[34];
+  __shared__ int done_s;
   KrySmall S{m};
-  double* H = small + S.H();
-  double* cs = small + S.cs();
-  double* sn = small + S.sn();
-  double* g = small + S.g();
-  const double* h1 = small + S.h1();
-  const double* h2 = small + S.h2();
-  double* sc = small + S.sc();
-  const double hn = sqrt(nrm2);
-  sc[0] = nrm2;
-  double* col = H + (size_t)j * (m + 1);
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-  col[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double a = col[i], b = col[i + 1];
-    col[i] = cs[i] * a + sn[i] * b;
-    col[i + 1] = -sn[i] * a + cs[i] * b;
+  const int t = threadIdx.x;
+  if (t < j) {
+    cs_s[t] = small[S.cs() + t];
+    sn_s[t] = small[S.sn() + t];
   }
-  const double a = col[j], b = col[j + 1];
-  const double den = sqrt(a * a + b * b);
-  cs[j] = den > 0.0 ? a / den : 1.0;
-  sn[j] = den > 0.0 ? b / den : 0.0;
-  col[j] = den;
-  col[j + 1] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  const double est = fabs(g[j + 1]);
-  sc[1] = est;
-  sc[2] = hn;
-  flags[1] = j + 1;
-  const bool breakdown = !(hn > 1e-14 * den);
-  if (!(est > sc[3]) || breakdown) flags[0] = 1;   // NaN also ends the cycle
-  if (breakdown) flags[2] = 1;
+  if (t <= j) col_s[t] = small[S.h1() + t] + small[S.h2() + t];
+  __syncthreads();
+  if (t == 0) {
+    double* sc = small + S.sc();
+    double* g = small + S.g();
+    const double hn = sqrt(nrm2);
+    sc[0] = nrm2;
+    col_s[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a = col_s[i], b = col_s[i + 1];
+      col_s[i] = cs_s[i] * a + sn_s[i] * b;
+      col_s[i + 1] = -sn_s[i] * a + cs_s[i] * b;
+    }
+    const double a = col_s[j], b = col_s[j + 1];
+    const double den = sqrt(a * a + b * b);
+    const double cj = den > 0.0 ? a / den : 1.0, sj = den > 0.0 ? b / den : 0.0;
+    small[S.cs() + j] = cj;
+    small[S.sn() + j] = sj;
+    col_s[j] = den;
+    col_s[j + 1] = 0.0;
+    const double gj = g[j];
+    g[j + 1] = -sj * gj;
+    g[j] = cj * gj;
+    const double est = fabs(g[j + 1]);
+    sc[1] = est;
+    sc[2] = hn;
+    flags[1] = j + 1;
+    const bool breakdown = !(hn > 1e-14 * den);
+    if (!(est > sc[3]) || breakdown) flags[0] = 1;   // NaN also ends the cycle
+    if (breakdown) flags[2] = 1;
+    done_s = flags[0];
+  }
+  __syncthreads();
+  if (t <= j + 1) small[S.H() + (size_t)j * (m + 1) + t] = col_s[t];
+  return done_s;
 }
 
 // out[k] = sum_i V[k][i] w[i] for k < nvec (NV >= nvec). Loads of all nvec vectors
@@ -214,9 +226,8 @@ __global__ void __launch_bounds__(KRY_T) k_orth_update(const double* __restrict_
     __shared__ double nrm_s[1];
     reduce_partials(part, ldp, 1, nrm_s);
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    *ticket = 0u;
-    arnoldi_column(small, m, j, nrm_s[0], flags);
+    if (threadIdx.x == 0) *ticket = 0u;
+    arnoldi_column_block(small, m, j, nrm_s[0], flags);
   }
 }
 

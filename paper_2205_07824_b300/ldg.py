@@ -122,6 +122,7 @@ def lib():
         L.ldg_batch_destroy.argtypes = [vp]
         L.ldg_batch_sizes.argtypes = [vp, i64p, i64p, i64p, ip]
         L.ldg_batch_residual.argtypes = [vp, dp, dp]
+        L.ldg_batch_set_time.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
         L.ldg_batch_jvp.argtypes = [vp, ctypes.c_int, dp, dp, dp]
         L.ldg_batch_autotune.argtypes = [vp, ctypes.c_int, ip]
         L.ldg_batch_solve.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(SolveReport), ctypes.POINTER(ctypes.c_double)]
@@ -418,6 +419,12 @@ class Batch:
 
     def slice(self, u, i):
         return u[self.offsets[i]:self.offsets[i] + self.n_dof[i]]
+
+    def set_time(self, scheme: int, t: float, dt: float = 1.0, un=None, unm1=None):
+        n = self.n_total
+        self._check(lib().ldg_batch_set_time(self._h, scheme, t, dt,
+                                             _ptr(un, n, "un") if un is not None else None,
+                                             _ptr(unm1, n, "unm1") if unm1 is not None else None))
 
     def residual(self, u, out=None):
         out = self.empty() if out is None else out

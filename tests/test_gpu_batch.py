@@ -179,3 +179,36 @@ def test_batch_fp32_krylov_reaches_fp64_tolerance():
     u = cuda(np.zeros(b.n_total))
     reps, _ = b.solve(u)
     _check_solution(b, spec, host(u), reps, 1e-8)
+
+
+def test_batch_bdf2_euler_matches_single_context():
+    """Time-dependent batch: two BDF2 steps of the vortex (one instance, and the same
+    vortex twice) against the single-context solver."""
+    from paper_2205_07824_b300.ldg import LDG, Batch, BDF2
+    mesh = synth.quad_box(8, hi=(10.0, 10.0), periodic=(True, True))
+    dt = 0.05
+    for n_inst in (1, 2):
+        b = Batch([mesh] * n_inst, [3] * n_inst, oracle.EULER, oracle.CASE_VORTEX, [(1.4,)] * n_inst, gmres_m=20,
+                  precond=1, krylov_precision=1)
+        g = LDG(mesh, 3, oracle.EULER, oracle.CASE_VORTEX, (1.4,), gmres_m=20, precond=1, krylov_precision=1)
+        un, unm1 = g.interpolate(0.0), g.interpolate(-dt)
+        bun = cuda(np.tile(host(un), n_inst))
+        bunm1 = cuda(np.tile(host(unm1), n_inst))
+        for k in range(2):
+            t1 = (k + 1) * dt
+            g.set_time(BDF2, t1, dt, un, unm1)
+            u = un.clone()
+            rep = g.newton_gmres(u)
+            unm1.copy_(un)
+            un.copy_(u)
+            b.set_time(BDF2, t1, dt, bun, bunm1)
+            bu = bun.clone()
+            reps, _ = b.solve(bu)
+            bunm1.copy_(bun)
+            bun.copy_(bu)
+            ref = host(un)
+            for i in range(n_inst):
+                got = host(b.slice(bun, i))
+                assert np.linalg.norm(got - ref) <= 1e-7 * np.linalg.norm(ref), (n_inst, k, i)
+                assert reps[i]["status"] == 0 and reps[i]["rfinal"] <= 1e-8 * reps[i]["r0"]
+                assert reps[i]["newton_iters"] == rep["newton_iters"]
