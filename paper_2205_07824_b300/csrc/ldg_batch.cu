@@ -60,6 +60,10 @@ struct ldg_batch {
   double *d_u = nullptr, *d_res = nullptr, *d_r = nullptr, *d_x = nullptr, *d_w = nullptr;
   double *d_vcur = nullptr, *d_zcur = nullptr, *d_V = nullptr, *d_Z = nullptr;
   bool pc = false;
+  bool borrowed = false;           // one instance whose context belongs to the caller
+  std::vector<const KernelSet*> cap_ks;   // per group: kernels, time scheme and a0/dt the graph holds
+  std::vector<int> cap_scheme;
+  std::vector<double> cap_a0dt;
   unsigned int* d_bar = nullptr;   // grid barrier of the fused Arnoldi step: count, generation, error
   int coop_grid = 0;               // CTAs of the fused (cooperative) Arnoldi step; 0 = split kernels
   cudaGraph_t graph = nullptr;
@@ -103,13 +107,15 @@ int verts_per_elem(int etype) { return etype == LDG_TRI ? 3 : etype == LDG_QUAD 
 int emit_residual(ldg_batch* b, cudaStream_t s, const double* u, double* r, const int* skip) {
   for (BGroup& g : b->groups) {
     g.ctx->stream = s;
+    // per-instance skipping needs the element -> instance map (absent for one borrowed context)
+    const int* sk = g.ctx->ext_inst ? skip : nullptr;
     KArgs a = base_args(g.ctx);
-    a.inst_skip = skip;
+    a.inst_skip = sk;
     if (g.ctx->ks->qstage) {
       a.u = u + g.off; a.out = g.ctx->d_q;
       BK(g.ctx->ks->qstage(MODE_R, a, s));
       a = base_args(g.ctx);
-      a.inst_skip = skip;
+      a.inst_skip = sk;
       a.q = g.ctx->d_q;
     }
     a.u = u + g.off; a.out = r + g.off;
@@ -123,7 +129,7 @@ int emit_jv(ldg_batch* b, cudaStream_t s, const double* u, const double* v, doub
   for (BGroup& g : b->groups) {
     g.ctx->stream = s;
     KArgs a = base_args(g.ctx);
-    a.inst_skip = skip;
+    a.inst_skip = g.ctx->ext_inst ? skip : nullptr;
     int rc = jvp_args(g.ctx, a, u + g.off, v + g.off, jv + g.off, prec);
     if (rc) return gfail(b, g, rc);
   }
@@ -133,7 +139,7 @@ int emit_jv(ldg_batch* b, cudaStream_t s, const double* u, const double* v, doub
 int emit_pc(ldg_batch* b, cudaStream_t s, const double* x, double* y, const int* skip) {
   for (BGroup& g : b->groups) {
     g.ctx->stream = s;
-    int rc = pc_apply(g.ctx, x + g.off, y + g.off, nullptr, skip);
+    int rc = pc_apply(g.ctx, x + g.off, y + g.off, nullptr, g.ctx->ext_inst ? skip : nullptr);
     if (rc) return gfail(b, g, rc);
   }
   return LDG_OK;
@@ -377,7 +383,7 @@ void free_batch(ldg_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (BGroup& g : b->groups) {
-    if (g.ctx) ldg_destroy(g.ctx);
+    if (g.ctx && !b->borrowed) ldg_destroy(g.ctx);
     cudaFree(g.d_inst);
   }
   for (void* p : {(void*)b->d_mtab, (void*)b->d_chunk_seg, (void*)b->d_seg_c0, (void*)b->d_seg_nc,
@@ -395,6 +401,8 @@ template <class T> int upload(ldg_batch* b, T** dst, const std::vector<T>& src) 
   if (!src.empty()) BK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
   return LDG_OK;
 }
+
+int finish_build(ldg_batch* b, const std::vector<int64_t>& seg_off, const std::vector<int64_t>& seg_n);
 
 int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int* p, const ldg_model_desc* models,
                 const ldg_options* opts) {
@@ -490,6 +498,14 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
   b->nseg = (int)b->seg_user.size();
   if ((rc = upload(b, &b->d_mtab, mtab))) return rc;
   for (BGroup& g : b->groups) g.ctx->ext_mtab = b->d_mtab;
+  return finish_build(b, seg_off, seg_n);
+}
+
+// Chunk tables, per-instance state and the Krylov work space of a batch whose groups
+// and instance segments are set.
+int finish_build(ldg_batch* b, const std::vector<int64_t>& seg_off, const std::vector<int64_t>& seg_n) {
+  const ldg_options& o = b->opt;
+  int rc;
   // chunk tables
   // chunk size: a power of two in [512, KB_CHUNK] giving about two chunks per SM, so
   // small batches still spread over the whole GPU
@@ -646,6 +662,20 @@ int ldg_batch_solve(ldg_batch* b, double* u_dev, int use_graph, ldg_solve_report
       if ((rc = do_pc_setup(g.ctx, b->d_u + g.off))) return gfail(b, g, rc);
     }
   long long before = launch_counter();
+  if (b->exec) {
+    // the captured kernels hold the tile, the time scheme and a0/dt of every group
+    bool stale = false;
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+      const ldg_ctx* c = b->groups[i].ctx;
+      stale |= c->ks != b->cap_ks[i] || c->scheme != b->cap_scheme[i] || c->a0dt != b->cap_a0dt[i];
+    }
+    if (stale) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+      cudaGraphDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
   if (use_graph) {
     if (!b->exec) {
       // every kernel instance runs once outside the capture (function attributes are set then)
@@ -658,6 +688,12 @@ int ldg_batch_solve(ldg_batch* b, double* u_dev, int use_graph, ldg_solve_report
       rc = build_graph(b);
       for (BGroup& g : b->groups) g.ctx->stream = s;
       if (rc) return rc;
+      b->cap_ks.clear(); b->cap_scheme.clear(); b->cap_a0dt.clear();
+      for (const BGroup& g : b->groups) {
+        b->cap_ks.push_back(g.ctx->ks);
+        b->cap_scheme.push_back(g.ctx->scheme);
+        b->cap_a0dt.push_back(g.ctx->a0dt);
+      }
     }
     BK(cudaGraphLaunch(b->exec, s));
   } else {
@@ -707,3 +743,57 @@ int64_t ldg_batch_kernel_executions(const ldg_batch* b) { return b ? b->last_exe
 const char* ldg_batch_last_error(const ldg_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
 }  // extern "C"
+
+namespace ldg {
+namespace impl {
+
+int batch_wrap(ldg_ctx* ctx, ldg_batch** out) {
+  *out = nullptr;
+  ldg_batch* b = new ldg_batch();
+  b->borrowed = true;
+  b->stream = ctx->stream;
+  b->opt = ctx->opt;
+  b->m = ctx->opt.gmres_m;
+  b->pc = ctx->opt.precond == LDG_PC_BJACOBI;
+  b->n_inst = 1;
+  BGroup g;
+  g.ctx = ctx;
+  g.off = 0;
+  g.ndof = ctx->ndof;
+  g.etype = ctx->etype; g.p = ctx->p; g.nq = ctx->nq; g.model = ctx->model;
+  b->groups.push_back(g);
+  b->seg_user = {0};
+  b->user_off = {0};
+  b->user_n = {ctx->ndof};
+  b->ntot = ctx->ndof;
+  b->nseg = 1;
+  const int rc = finish_build(b, {0}, {ctx->ndof});
+  if (rc) {
+    ctx->err = b->err;
+    free_batch(b);
+    return rc;
+  }
+  *out = b;
+  return LDG_OK;
+}
+
+int batch_solve_one(ldg_batch* b, double* u, ldg_solve_report* rep) {
+  b->stream = b->groups[0].ctx->stream;
+  ldg_solve_report r{};
+  double ms = 0.0;
+  const int rc = ldg_batch_solve(b, u, 1, &r, &ms);
+  if (rep) {
+    *rep = r;
+    rep->elapsed_ms = ms;
+  }
+  return rc;
+}
+
+void batch_free(ldg_batch* b) {
+  if (b) free_batch(b);
+}
+
+const char* batch_error(const ldg_batch* b) { return b ? b->err.c_str() : "no solver"; }
+
+}  // namespace impl
+}  // namespace ldg

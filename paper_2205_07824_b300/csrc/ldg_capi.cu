@@ -768,6 +768,7 @@ const char* ldg_last_error(const ldg_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 int ldg_destroy(ldg_ctx* ctx) {
   if (!ctx) return LDG_OK;
+  if (ctx->engine) batch_free(ctx->engine);
   cudaFree(ctx->d_ops); cudaFree(ctx->d_opsf); cudaFree(ctx->d_geo); cudaFree(ctx->d_nbr); cudaFree(ctx->d_nbf); cudaFree(ctx->d_perm);
   cudaFree(ctx->d_xn); cudaFree(ctx->d_q); cudaFree(ctx->d_dq); cudaFree(ctx->d_hist);
   cudaFree(ctx->d_V); cudaFree(ctx->d_r); cudaFree(ctx->d_w); cudaFree(ctx->d_res); cudaFree(ctx->d_x); cudaFree(ctx->d_small); cudaFree(ctx->d_part);
@@ -875,10 +876,8 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   }
   CK(cudaMalloc(&ctx->d_hist, n * sizeof(double)));
   if (!lean) CK(cudaMalloc(&ctx->d_V, (size_t)(ctx->m + 1) * n * sizeof(double)));
-  if (lean) {
-    CK(cudaMalloc(&ctx->d_t, sizeof(double)));
-    CK(cudaMemset(ctx->d_t, 0, sizeof(double)));
-  }
+  CK(cudaMalloc(&ctx->d_t, sizeof(double)));
+  CK(cudaMemset(ctx->d_t, 0, sizeof(double)));
   CK(cudaMalloc(&ctx->d_r, n * sizeof(double)));
   CK(cudaMalloc(&ctx->d_w, n * sizeof(double)));
   CK(cudaMalloc(&ctx->d_res, n * sizeof(double)));
@@ -1209,7 +1208,19 @@ int ldg_newton_gmres(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
   ldg_solve_report local{};
   if (!rep) rep = &local;
   std::memset(rep, 0, sizeof(*rep));
-  int rc = do_newton(ctx, u, rep);
+  int rc;
+  // block-Jacobi built once per call, or no preconditioner: the graph-driven solver
+  // (the whole Newton-GMRES one CUDA graph launch); otherwise the host-driven loop
+  if (ctx->opt.precond != LDG_PC_MLP && ctx->opt.pc_refresh == 0 && !ctx->col_X) {
+    if (!ctx->engine && (rc = batch_wrap(ctx, &ctx->engine))) {
+      rep->status = rc;
+      return rc;
+    }
+    rc = batch_solve_one(ctx->engine, u, rep);
+    if (rc) ctx->err = batch_error(ctx->engine);
+  } else {
+    rc = do_newton(ctx, u, rep);
+  }
   rep->status = rc;
   return rc;
 }

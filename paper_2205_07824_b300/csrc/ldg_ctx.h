@@ -88,7 +88,8 @@ struct ldg_ctx {
   const int* ext_inst = nullptr;
   const ldg::ModelParams* ext_mtab = nullptr;
   bool lean = false;           // no Krylov basis or preconditioned vectors (batch groups)
-  double* d_t = nullptr;       // lean contexts: boundary-data time in device memory
+  double* d_t = nullptr;       // boundary-data time in device memory (read by captured graphs)
+  ldg_batch* engine = nullptr; // graph-driven Newton-GMRES over this context (created on first use)
   std::string err;
 };
 
@@ -111,5 +112,10 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
 // selects the fastest J.v in the Krylov precision; force = 0 reuses a cached choice.
 int autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms);
 ModelParams make_params(const ldg_model_desc* model);
+// The graph-driven batched solver with one borrowed context as its only instance.
+int batch_wrap(ldg_ctx* ctx, ldg_batch** out);
+int batch_solve_one(ldg_batch* b, double* u, ldg_solve_report* rep);
+void batch_free(ldg_batch* b);
+const char* batch_error(const ldg_batch* b);
 }  // namespace impl
 }  // namespace ldg
