@@ -43,13 +43,26 @@ def normalise(X, T, tiny=1e-30, U=None):
     return Xn, T * s[:, None], mask
 
 
-def forward(theta, Xn, n_in, hidden, n_out):
+def round_bf16(x):
+    """Nearest BF16 value (8-bit significand, ties to even) of each entry, via its FP32
+    bit pattern, returned as FP64."""
+    f = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    f = (f + 0x7FFF + ((f >> 16) & 1)) & 0xFFFF0000
+    return f.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(theta, Xn, n_in, hidden, n_out, act_round=None):
+    """act_round (optional) is applied to the network input and to both hidden
+    activations before they enter the next layer (storage precision of a kernel)."""
     W1, b1, W2, b2, W3, b3, Ws = unflatten(theta, n_in, hidden, n_out)
-    Z1 = Xn @ W1.T + b1
+    r = act_round if act_round is not None else (lambda a: a)
+    Xr = r(Xn)
+    Z1 = Xr @ W1.T + b1
     H1 = np.maximum(Z1, 0.0)
-    Z2 = H1 @ W2.T + b2
+    H1r = r(H1)
+    Z2 = H1r @ W2.T + b2
     H2 = np.maximum(Z2, 0.0)
-    Y = H2 @ W3.T + b3 + Xn[:, :n_out] @ Ws.T
+    Y = r(H2) @ W3.T + b3 + Xr[:, :n_out] @ Ws.T
     return Y, (Z1, H1, Z2, H2)
 
 
@@ -75,14 +88,14 @@ def loss_grad(theta, X, T, n_in, hidden, n_out, U=None):
     return loss, g
 
 
-def apply(theta, v_blocks, n_in, hidden, n_out, U=None):
+def apply(theta, v_blocks, n_in, hidden, n_out, U=None, act_round=None):
     """M(v)_K = ||v_K|| net(v_K / ||v_K||[, u_K]) for blocks v [E][n]."""
     nrm = np.linalg.norm(v_blocks, axis=1)
     safe = np.where(nrm > 0, nrm, 1.0)
     x = v_blocks / safe[:, None]
     if U is not None:
         x = np.hstack([x, U])
-    Y, _ = forward(theta, x, n_in, hidden, n_out)
+    Y, _ = forward(theta, x, n_in, hidden, n_out, act_round)
     return Y * nrm[:, None]
 
 

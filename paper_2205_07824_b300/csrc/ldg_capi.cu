@@ -14,6 +14,8 @@
 #include "ldg_krylov.cuh"
 #include "ldg_precond.cuh"
 #include "ldg_mlp.cuh"
+#include "ldg_tc.cuh"
+#include <cudaTypedefs.h>
 #include <algorithm>
 #include <random>
 #include <map>
@@ -470,22 +472,127 @@ int mlp_prep(ldg_ctx* ctx, const double* X, const double* T, const double* U, co
   return LDG_OK;
 }
 
+// ------------------------------------------------- tensor-core inference (tcgen05)
+// BF16 row-major [rows][cols] with row stride ld elements, as a TMA map with
+// 64 x box_rows boxes and 128-byte swizzle.
+int tc_map(ldg_ctx* ctx, CUtensorMap* map, const void* base, int64_t rows, int cols, int ld, int box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !encode) return fail(ctx, LDG_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, LDG_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return LDG_OK;
+}
+
+// Buffers and TMA maps of the tensor-core inference over the context's E elements.
+int mlp_tc_setup(ldg_ctx* ctx) {
+  auto& M = ctx->mlp;
+  const char* simt = getenv("LDG_MLP_SIMT");
+  M.tc = M.n % 64 == 0 && M.n <= 128 && M.h % 64 == 0 && M.h <= 256 && !(simt && simt[0] == '1');
+  if (!M.tc || M.tc_rows == ctx->E) return LDG_OK;
+  const int n = M.n, h = M.h;
+  const int64_t E = ctx->E;
+  for (__nv_bfloat16** p : {&M.Xbf, &M.H1bf, &M.H2bf, &M.wtc}) { cudaFree(*p); *p = nullptr; }
+  CK(cudaMalloc(&M.Xbf, (size_t)E * 2 * n * sizeof(__nv_bfloat16)));
+  CK(cudaMalloc(&M.H1bf, (size_t)E * h * sizeof(__nv_bfloat16)));
+  CK(cudaMalloc(&M.H2bf, (size_t)E * h * sizeof(__nv_bfloat16)));
+  // W1 [h][2n], W2 [h][h], W3 [n][h], Ws [n][n], each at a 256-byte boundary
+  const int64_t w1 = 0, w2 = w1 + (((int64_t)h * 2 * n + 127) & ~127), w3 = w2 + (((int64_t)h * h + 127) & ~127),
+                ws = w3 + (((int64_t)n * h + 127) & ~127), wend = ws + (((int64_t)n * n + 127) & ~127);
+  CK(cudaMalloc(&M.wtc, wend * sizeof(__nv_bfloat16)));
+  if (!M.d_err) {
+    CK(cudaMalloc(&M.d_err, sizeof(int)));
+    CK(cudaMemset(M.d_err, 0, sizeof(int)));
+  }
+  int rc;
+  if ((rc = tc_map(ctx, &M.maps[0], M.Xbf, E, 2 * n, 2 * n, TC_BM)) ||
+      (rc = tc_map(ctx, &M.maps[1], M.Xbf, E, n, 2 * n, TC_BM)) ||
+      (rc = tc_map(ctx, &M.maps[2], M.H1bf, E, h, h, TC_BM)) ||
+      (rc = tc_map(ctx, &M.maps[3], M.H2bf, E, h, h, TC_BM)) ||
+      (rc = tc_map(ctx, &M.maps[4], M.wtc + w1, h, 2 * n, 2 * n, h)) ||
+      (rc = tc_map(ctx, &M.maps[5], M.wtc + w2, h, h, h, h)) ||
+      (rc = tc_map(ctx, &M.maps[6], M.wtc + w3, n, h, h, n)) ||
+      (rc = tc_map(ctx, &M.maps[7], M.wtc + ws, n, n, n, n)))
+    return rc;
+  M.tc_rows = E;
+  return LDG_OK;
+}
+
 int mlp_refresh_bf16(ldg_ctx* ctx) {
   auto& M = ctx->mlp;
   k_to_bf16<<<std::min<int64_t>(grid_for(M.nparam), 148 * 4), 256, 0, ctx->stream>>>(M.theta, M.theta_bf, M.nparam);
   count_launch();
   CK(cudaGetLastError());
+  int rc;
+  if ((rc = mlp_tc_setup(ctx))) return rc;
+  if (M.tc) {
+    const int n = M.n, h = M.h;
+    MlpOff o(n, h);
+    const int64_t w1 = 0, w2 = w1 + (((int64_t)h * 2 * n + 127) & ~127), w3 = w2 + (((int64_t)h * h + 127) & ~127),
+                  ws = w3 + (((int64_t)n * h + 127) & ~127);
+    const struct { int64_t src, dst; int rows, cols; } part[4] = {
+        {o.W1, w1, h, 2 * n}, {o.W2, w2, h, h}, {o.W3, w3, n, h}, {o.Ws, ws, n, n}};
+    for (const auto& q : part) {
+      k_to_bf16_2d<<<148, 256, 0, ctx->stream>>>(M.theta + q.src, q.cols, M.wtc + q.dst, q.cols, q.rows, q.cols,
+                                                 nullptr);
+      count_launch();
+    }
+    CK(cudaGetLastError());
+  }
   M.ready = true;
   return LDG_OK;
 }
 
-// y = M(x) on a full n_dof vector (element blocks) at state u, BF16 weights
+// One tcgen05 GEMM launch: C = act(A1 B1^T [+ A2 B2^T] + bias), maps by index.
+int tc_gemm(ldg_ctx* ctx, int a1, int b1, int a2, int b2, int N, int K1, int K2, const float* bias, int relu,
+            void* C, int ldc, int out_bf16, const int* skip) {
+  auto& M = ctx->mlp;
+  TcGemmArgs g;
+  g.M = (int)ctx->E; g.N = N; g.K1 = K1; g.K2 = K2; g.bias = bias; g.relu = relu; g.C = C; g.ldc = ldc;
+  g.out_bf16 = out_bf16; g.err = M.d_err; g.skip = skip;
+  const size_t smem = tc_gemm_smem(N, K1, K2);
+  static int smem_set = 0;
+  if (smem_set < (int)smem) {
+    CK(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    smem_set = 200 * 1024;
+  }
+  if (smem > 200 * 1024) return fail(ctx, LDG_ERR_UNSUPPORTED, "tensor-core GEMM tile too large");
+  const unsigned grid = (unsigned)((ctx->E + TC_BM - 1) / TC_BM);
+  k_tc_gemm<<<grid, 128, smem, ctx->stream>>>(M.maps[a1], M.maps[b1], M.maps[a2 >= 0 ? a2 : a1],
+                                              M.maps[b2 >= 0 ? b2 : b1], g);
+  count_launch();
+  CK(cudaGetLastError());
+  return LDG_OK;
+}
+
+// y = M(x) on a full n_dof vector (element blocks) at state u, BF16 weights. With the
+// tensor-core path the input and hidden activations are stored in BF16 as well, and
+// the output layer accumulates W3 h2 and the skip map Ws x_v in one TMEM accumulator.
 int mlp_apply(ldg_ctx* ctx, const double* u, const double* x, double* y, const int* skip) {
   auto& M = ctx->mlp;
   int rc;
   if ((rc = mlp_prep(ctx, x, nullptr, u, nullptr, ctx->E, skip))) return rc;
   MlpOff o(M.n, M.h);
-  mlp_forward<__nv_bfloat16>(ctx, ctx->E, M.theta_bf, M.theta, skip);
+  if (M.tc && M.tc_rows == ctx->E) {
+    const int n = M.n, h = M.h;
+    k_to_bf16_2d<<<std::min<int64_t>(grid_for(ctx->E * 2 * n), 148 * 8), 256, 0, ctx->stream>>>(
+        M.X, 2 * n, M.Xbf, 2 * n, ctx->E, 2 * n, skip);
+    count_launch();
+    if ((rc = tc_gemm(ctx, 0, 4, -1, -1, h, 2 * n, 0, M.theta + o.b1, 1, M.H1bf, h, 1, skip))) return rc;
+    if ((rc = tc_gemm(ctx, 2, 5, -1, -1, h, h, 0, M.theta + o.b2, 1, M.H2bf, h, 1, skip))) return rc;
+    if ((rc = tc_gemm(ctx, 3, 6, 1, 7, n, h, n, M.theta + o.b3, 0, M.Y, n, 0, skip))) return rc;
+  } else {
+    mlp_forward<__nv_bfloat16>(ctx, ctx->E, M.theta_bf, M.theta, skip);
+  }
   k_mlp_unprep<<<std::min<int64_t>(grid_for(ctx->ndof), 148 * 8), 256, 0, ctx->stream>>>(M.Y, M.norms, ctx->E, M.n, y,
                                                                                        skip);
   count_launch();
@@ -777,6 +884,8 @@ int ldg_destroy(ldg_ctx* ctx) {
   cudaFree(ctx->d_probe); cudaFree(ctx->d_jp); cudaFree(ctx->d_status);
   {
     auto& M = ctx->mlp;
+    for (void* p : {(void*)M.Xbf, (void*)M.H1bf, (void*)M.H2bf, (void*)M.wtc, (void*)M.d_err})
+      cudaFree(p);
     for (void* p : {(void*)M.theta, (void*)M.grad, (void*)M.m, (void*)M.v, (void*)M.theta_bf, (void*)M.X, (void*)M.T,
                     (void*)M.mask, (void*)M.H1, (void*)M.H2, (void*)M.Y, (void*)M.dY, (void*)M.dH1, (void*)M.dH2,
                     (void*)M.norms, (void*)M.loss, (void*)M.count, (void*)M.idx})
@@ -1157,7 +1266,13 @@ int ldg_mlp_train(ldg_ctx* ctx, const double* X, const double* T, const double* 
 int ldg_mlp_apply(ldg_ctx* ctx, const double* u, const double* x, double* y) {
   if (!ctx || !ctx->ks || !u || !x || !y) return LDG_ERR_ARG;
   if (!ctx->mlp.ready) return fail(ctx, LDG_ERR_ARG, "ldg_mlp_apply: no trained network (ldg_mlp_init/train)");
-  return mlp_apply(ctx, u, x, y, nullptr);
+  int rc = mlp_apply(ctx, u, x, y, nullptr);
+  if (rc || !ctx->mlp.d_err) return rc;
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, ctx->mlp.d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (err) return fail(ctx, LDG_ERR_CUDA, "tensor-core GEMM: a TMA or MMA wait timed out");
+  return LDG_OK;
 }
 
 int ldg_newton_gmres_collect(ldg_ctx* ctx, double* u, double* X, double* T, double* U, int capacity, int* count,

@@ -1,6 +1,7 @@
 // Internal interface shared by the single-problem C-ABI and the batched solver:
 // the context record and the helpers both use. Not part of the public ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -77,6 +78,12 @@ struct ldg_ctx {
     int64_t idx_cap = 0;
     int t = 0;
     bool ready = false;
+    // tensor-core inference: BF16 activations, aligned BF16 weight copies, TMA maps
+    bool tc = false;                       // shapes suit the tcgen05 GEMM (n, 2n, h multiples of 64)
+    __nv_bfloat16 *Xbf = nullptr, *H1bf = nullptr, *H2bf = nullptr, *wtc = nullptr;
+    int64_t tc_rows = 0;
+    CUtensorMap maps[8];                   // A: X, X[:, :n], H1, H2; B: W1, W2, W3, Ws
+    int* d_err = nullptr;
   } mlp;
   // pair collection during Newton (training data)
   double* col_X = nullptr;

@@ -1,0 +1,241 @@
+// Tensor-core GEMM for the learned preconditioner (5th-generation tensor cores):
+//   C[M][N] = act( A1[M][K1] B1[N][K1]^T + A2[M][K2] B2[N][K2]^T + bias )
+// with BF16 operands, FP32 accumulation in tensor memory (TMEM) and FP32 or BF16
+// output. One CTA of 128 threads owns a 128-row tile and the whole N (<= 256):
+//   thread 0 loads every K-slab of A and B with TMA (cp.async.bulk.tensor, 128-byte
+//   swizzle) onto one mbarrier, issues the tcgen05.mma chain into TMEM and commits
+//   it to a second mbarrier; the four warps then read their 32 TMEM lanes back
+//   (tcgen05.ld), add the bias, apply ReLU and store their rows.
+// Operands are K-major: rows of 64 BF16 (128 bytes) per K-slab, 8-row groups 1024
+// bytes apart (the canonical 128-byte-swizzle layout). K1, K2 are multiples of 64.
+// Every mbarrier wait is bounded (about a second of SM clock); on timeout the CTA
+// records *err, skips the rest of its work, frees its TMEM and returns.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ldg {
+
+constexpr int TC_BM = 128;        // rows per CTA (MMA M)
+constexpr int TC_BK = 64;         // K elements per slab (128 bytes of BF16)
+constexpr int TC_SLAB_A = TC_BM * TC_BK * 2;   // bytes of one A slab
+
+struct TcGemmArgs {
+  int M, N, K1, K2;         // K2 = 0: one operand pair
+  const float* bias;        // [N] or null
+  int relu;
+  void* C;                  // [M][ldc] FP32 or BF16
+  int ldc;
+  int out_bf16;
+  int* err;                 // set to 1 when a wait times out
+  const int* skip;          // optional: return at once when *skip != 0
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// true when the barrier completed phase `parity`; false after ~2^31 cycles
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(const void* p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = (addr & 0x3FFFFull) >> 4;      // start address
+  d |= (uint64_t)1 << 16;                      // leading byte offset (16 B; unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, both K-major, M x N.
+__host__ __device__ constexpr uint32_t bf16_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap ta1,
+                                                    const __grid_constant__ CUtensorMap tb1,
+                                                    const __grid_constant__ CUtensorMap ta2,
+                                                    const __grid_constant__ CUtensorMap tb2, TcGemmArgs g) {
+  if (g.skip && *g.skip) return;
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  // the 128-byte swizzle is a function of the shared-memory address: align that to 1024
+  unsigned char* smem = tc_smem_raw + ((1024u - (smem_u32(tc_smem_raw) & 1023u)) & 1023u);
+  __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int ok_s;
+  const int nk1 = g.K1 / TC_BK, nk2 = g.K2 / TC_BK, nk = nk1 + nk2;
+  const int N = g.N;
+  const int slab_b = N * TC_BK * 2;
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + (size_t)nk * TC_SLAB_A;
+  const uint32_t ncols = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TC_BM;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(&bar_tma, 1);
+    mbar_init(&bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    ok_s = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar_tma, (uint32_t)(nk * (TC_SLAB_A + slab_b)));
+    for (int kb = 0; kb < nk1; ++kb) {
+      tma_load_2d(sA + (size_t)kb * TC_SLAB_A, &ta1, kb * TC_BK, m0, &bar_tma);
+      tma_load_2d(sB + (size_t)kb * slab_b, &tb1, kb * TC_BK, 0, &bar_tma);
+    }
+    for (int kb = 0; kb < nk2; ++kb) {
+      tma_load_2d(sA + (size_t)(nk1 + kb) * TC_SLAB_A, &ta2, kb * TC_BK, m0, &bar_tma);
+      tma_load_2d(sB + (size_t)(nk1 + kb) * slab_b, &tb2, kb * TC_BK, 0, &bar_tma);
+    }
+    if (mbar_wait(&bar_tma, 0)) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t idesc = bf16_idesc(TC_BM, N);
+      for (int kb = 0; kb < nk; ++kb)
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          const uint64_t ad = sw128_desc(sA + (size_t)kb * TC_SLAB_A + kk * 32);
+          const uint64_t bd = sw128_desc(sB + (size_t)kb * slab_b + kk * 32);
+          tc_mma(tmem, ad, bd, idesc, (kb | kk) != 0);
+        }
+      tc_commit(&bar_mma);
+    } else {
+      ok_s = 0;
+      atomicExch(g.err, 1);
+    }
+  }
+  __syncthreads();
+  if (ok_s) {
+    if (!mbar_wait(&bar_mma, 0)) {
+      atomicExch(g.err, 1);
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = m0 + warp * 32 + lane;
+      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tc_ld16(lane_addr + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          float x = v[i];
+          if (g.bias) x += g.bias[c0 + i];
+          if (g.relu) x = fmaxf(x, 0.f);
+          v[i] = x;
+        }
+        // 16-byte vector stores of the thread's 16 consecutive outputs (row strides and c0
+        // are multiples of 16 bytes)
+        if (row < g.M) {
+          if (g.out_bf16) {
+            uint32_t pk[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+              pk[i] = *reinterpret_cast<uint32_t*>(&b2);
+            }
+            uint4* out = reinterpret_cast<uint4*>((__nv_bfloat16*)g.C + (size_t)row * g.ldc + c0);
+            out[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            out[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          } else {
+            float4* out = reinterpret_cast<float4*>((float*)g.C + (size_t)row * g.ldc + c0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) out[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// dynamic shared memory of k_tc_gemm (+1 KB for the 1024-byte alignment)
+inline size_t tc_gemm_smem(int N, int K1, int K2) {
+  const int nk = (K1 + K2) / TC_BK;
+  return (size_t)nk * (TC_SLAB_A + (size_t)N * TC_BK * 2) + 1024;
+}
+
+// FP32 -> BF16, row-major with independent strides (rows x cols)
+__global__ void k_to_bf16_2d(const float* __restrict__ src, int lds, __nv_bfloat16* __restrict__ dst, int ldd,
+                             int64_t rows, int cols, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t total = rows * cols;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / cols;
+    const int c = (int)(i - r * cols);
+    dst[r * ldd + c] = __float2bfloat16(src[r * lds + c]);
+  }
+}
+
+}  // namespace ldg

@@ -353,3 +353,17 @@ def test_adam_reduces_a_quadratic():
     for t in range(1, 2001):
         mlp.adam_step(theta, 2 * theta, m, v, t, lr=0.05)
     assert np.abs(theta).max() < 1e-2
+
+
+def test_bf16_rounding_matches_torch_and_ties_to_even():
+    """The oracle's BF16 rounding (storage precision of the tensor-core inference
+    path) against torch's float32 -> bfloat16 conversion, plus the tie cases."""
+    import torch
+    from oracle import mlp as omlp
+    x = np.random.default_rng(3).standard_normal(10000) * np.exp(np.random.default_rng(4).uniform(-20, 20, 10000))
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(omlp.round_bf16(x), ref)
+    ulp = 2.0 ** -7
+    assert omlp.round_bf16(1.0 + ulp / 2) == 1.0                  # tie -> even (1.0)
+    assert omlp.round_bf16(1.0 + 3 * ulp / 2) == 1.0 + 2 * ulp    # tie -> even (1 + 2 ulp)
+    assert omlp.round_bf16(1.0 + 0.6 * ulp) == 1.0 + ulp
