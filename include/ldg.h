@@ -270,7 +270,7 @@ const char* ldg_last_error(const ldg_ctx* ctx);
  *   0: <= 16 elements in <= 100 KB (the default)   1: <= 8 elements in <= 48 KB
  *   2: <= 32 elements in <= 100 KB                 3: <= 4 elements in <= 24 KB
  * ldg_autotune times the J.v of every distinct tile (in the context's Krylov
- * precision) on the context's own mesh, five timed calls after two warm-up calls
+ * precision) on the context's own mesh, ten timed calls after three warm-up calls
  * with CUDA events, and keeps the fastest for all kernels of the context. The choice
  * is cached per (element, p, quadrature, model, precision, element-count octave) in
  * the process; force = 1 re-times. *best_ms = mean time of the chosen J.v (-1 when

@@ -13,7 +13,6 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
-#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -64,8 +63,6 @@ struct ldg_batch {
   std::vector<const KernelSet*> cap_ks;   // per group: kernels, time scheme and a0/dt the graph holds
   std::vector<int> cap_scheme;
   std::vector<double> cap_a0dt;
-  unsigned int* d_bar = nullptr;   // grid barrier of the fused Arnoldi step: count, generation, error
-  int coop_grid = 0;               // CTAs of the fused (cooperative) Arnoldi step; 0 = split kernels
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long k_pre = 0, k_a = 0, k_b = 0, k_c = 0;   // kernels per graph part (captured)
@@ -209,36 +206,21 @@ int emit_arnoldi(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle hc, in
     dir = b->d_zcur;
   }
   if ((rc = emit_jv(b, s, b->d_u, dir, b->d_w, b->opt.krylov_precision, b->d_skip_arn))) return rc;
-  if (b->coop_grid > 0) {
-    // the whole classical Gram-Schmidt step (two passes, Givens, v_{j+1}) in one cooperative launch
-    double* V = b->d_V;
-    int64_t ldv = b->ntot;
-    double* w = b->d_w;
-    const double* zsrc = b->pc ? b->d_zcur : nullptr;
-    double* Z = b->d_Z;
-    double* vcur = b->d_vcur;
-    double* part = b->d_part;
-    int* skip = b->d_skip_arn;
-    GridBar gb{b->d_bar, b->d_bar + 1, (int*)(b->d_bar + 2)};
-    const BatchCtl* ctl = b->d_ctl;
-    SegView svv = sv;
-    void* args[] = {&svv, &ctl, &V, &ldv, &w, &zsrc, &Z, &vcur, &part, &skip, &gb};
-    BK(cudaLaunchCooperativeKernel((const void*)kb_arnoldi_fused, dim3(b->coop_grid), dim3(KRY_T), args, 0, s));
-    kb_arnoldi_end<<<1, 256, 0, s>>>(b->d_ctl, b->d_skip_arn, b->nseg, hc, use);
-    count_launch();
-    count_launch();
-    BK(cudaGetLastError());
-    return LDG_OK;
-  }
-  // classical Gram-Schmidt, two passes: h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2 (+ Givens)
+  // classical Gram-Schmidt, two passes: h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2,
+  // then v_{j+1} = w / ||w|| and the Givens column
+  double* part1 = b->d_part;
+  double* part2 = b->d_part + (size_t)b->nchunk * KB_LDP;
+  double* part3 = b->d_part + (size_t)2 * b->nchunk * KB_LDP;
   KrySmall S{b->m};
-  kb_mdot<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, (int)S.h1(),
-                                      b->pc ? b->d_zcur : nullptr, b->d_Z, b->d_skip_arn);
-  kb_update<false><<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, (int)S.h1(), b->d_w, b->d_skip_arn);
-  kb_mdot<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, (int)S.h2(), nullptr, nullptr,
-                                      b->d_skip_arn);
-  kb_update<true><<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, (int)S.h2(), b->d_w, b->d_skip_arn);
-  kb_scale<<<b->nchunk, 256, 0, s>>>(sv, b->d_ctl, b->d_w, b->d_V, b->ntot, b->d_vcur, b->d_skip_arn);
+  kb_mdot<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, part1, b->pc ? b->d_zcur : nullptr,
+                                      b->d_Z, b->d_skip_arn);
+  kb_update<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, part1, (int)S.h1(), b->d_w, nullptr,
+                                        b->d_skip_arn);
+  kb_mdot<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, part2, nullptr, nullptr, b->d_skip_arn);
+  kb_update<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, part2, (int)S.h2(), b->d_w, part3,
+                                        b->d_skip_arn);
+  kb_scale<<<b->nseg + b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_w, part3, b->d_V, b->ntot, b->d_vcur,
+                                                 b->d_skip_arn);
   kb_arnoldi_end<<<1, 256, 0, s>>>(b->d_ctl, b->d_skip_arn, b->nseg, hc, use);
   for (int i = 0; i < 6; ++i) count_launch();
   BK(cudaGetLastError());
@@ -390,7 +372,7 @@ void free_batch(ldg_batch* b) {
                   (void*)b->d_chunk_lo, (void*)b->d_chunk_hi, (void*)b->d_part, (void*)b->d_tick, (void*)b->d_small,
                   (void*)b->d_sflags, (void*)b->d_st, (void*)b->d_ctl, (void*)b->d_skip_newt, (void*)b->d_skip_gm,
                   (void*)b->d_skip_arn, (void*)b->d_u, (void*)b->d_res, (void*)b->d_r, (void*)b->d_x, (void*)b->d_w,
-                  (void*)b->d_vcur, (void*)b->d_zcur, (void*)b->d_V, (void*)b->d_Z, (void*)b->d_bar})
+                  (void*)b->d_vcur, (void*)b->d_zcur, (void*)b->d_V, (void*)b->d_Z})
     cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
@@ -528,22 +510,6 @@ int finish_build(ldg_batch* b, const std::vector<int64_t>& seg_off, const std::v
     return rc;
   const size_t ks = KrySmall{b->m}.total();
   BK(cudaMalloc(&b->d_part, (size_t)3 * b->nchunk * KB_LDP * sizeof(double)));
-  BK(cudaMalloc(&b->d_bar, 4 * sizeof(unsigned int)));
-  BK(cudaMemset(b->d_bar, 0, 4 * sizeof(unsigned int)));
-  {
-    // fused Arnoldi step: as many co-resident CTAs as the chunks need, at most what fits
-    int dev = 0, sms = 0, per_sm = 0, coop = 0;
-    BK(cudaGetDevice(&dev));
-    BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    BK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-    BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_arnoldi_fused, KRY_T, 0));
-    // the split kernels measured faster on both the single vortex and the 256-instance
-    // batch (graph launches hide the per-kernel latency better than grid barriers do);
-    // LDG_BATCH_FUSED_GS=1 selects the fused form
-    const char* fused = getenv("LDG_BATCH_FUSED_GS");
-    if (coop && per_sm > 0 && fused && fused[0] == '1')
-      b->coop_grid = (int)std::min<int64_t>(b->nchunk, (int64_t)std::min(per_sm, 2) * sms);
-  }
   BK(cudaMalloc(&b->d_tick, b->nseg * sizeof(unsigned int)));
   BK(cudaMemset(b->d_tick, 0, b->nseg * sizeof(unsigned int)));
   BK(cudaMalloc(&b->d_small, (size_t)b->nseg * ks * sizeof(double)));
@@ -704,10 +670,7 @@ int ldg_batch_solve(ldg_batch* b, double* u_dev, int use_graph, ldg_solve_report
   BatchCtl ctl;
   BK(cudaMemcpyAsync(st.data(), b->d_st, st.size() * sizeof(SegState), cudaMemcpyDeviceToHost, s));
   BK(cudaMemcpyAsync(&ctl, b->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, s));
-  unsigned int bar[4] = {0, 0, 0, 0};
-  BK(cudaMemcpyAsync(bar, b->d_bar, sizeof(bar), cudaMemcpyDeviceToHost, s));
   BK(cudaStreamSynchronize(s));
-  if (bar[2]) return bfail(b, LDG_ERR_CUDA, "fused Arnoldi step: a grid barrier timed out");
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (use_graph) {
     b->last_exec = b->k_pre + ctl.trips_a * b->k_a + ctl.trips_b * b->k_b + ctl.trips_c * b->k_c;

@@ -99,11 +99,12 @@ __device__ __forceinline__ void seg_reduce(const SegView& sv, int s, int nvec, d
     for (int b = grp; b < nc; b += groups) t += __ldcg(sv.part + (size_t)(c0 + b) * KB_LDP + k);
   gred[threadIdx.x] = t;
   __syncthreads();
-  if ((int)threadIdx.x < nvec) {
-    double r = 0.0;
-    for (int g = 0; g < groups; ++g) r += gred[g * kw + threadIdx.x];
-    out[threadIdx.x] = r;
+  // fixed-shape tree over the groups (groups is a power of two)
+  for (int st = groups >> 1; st > 0; st >>= 1) {
+    if (grp < st) gred[threadIdx.x] += gred[threadIdx.x + st * kw];
+    __syncthreads();
   }
+  if ((int)threadIdx.x < nvec) out[threadIdx.x] = gred[threadIdx.x];
 }
 
 // small_s[out_off] = ||x_s||^2 for every segment not skipped.
@@ -118,26 +119,48 @@ __global__ void __launch_bounds__(KRY_T) kb_norm2(SegView sv, const double* __re
   if (threadIdx.x == 0) sv.tick[s] = 0u;
 }
 
-// Marks chunk c of segment s as done (its partials written); true in the last chunk
-// of the segment to arrive, after every partial of the segment is visible.
-__device__ __forceinline__ bool seg_arrive(const SegView& sv, int c, int s) {
-  __shared__ bool last;
-  __threadfence();
+// ------------------------------------------------------------ Arnoldi step
+// One classical Gram-Schmidt step with re-orthogonalisation is five launches:
+//   kb_mdot(part1)  kb_update(h1 <- part1; w -= V h1)  kb_mdot(part2)
+//   kb_update(h2 <- part2; w -= V h2; ||w||^2 -> part3)  kb_scale(||w|| <- part3; v_{j+1})
+// A kernel only writes per-chunk partials; the next kernel's CTAs each sum the
+// partials of their own instance in chunk order (every CTA gets the same bits), so
+// no atomics, tickets or serial last-block tails are needed. The CTA owning an
+// instance's first chunk also keeps h1, h2 in the instance's small area, and in
+// kb_scale completes the Arnoldi column and its Givens rotation.
+
+// out[k] (shared memory) = sum over the chunks of segment s of part[c][k], in chunk
+// order (whole CTA; every CTA computes the same bits).
+__device__ __forceinline__ void seg_sum(const SegView& sv, const double* part, int s, int nvec, double* out) {
+  __shared__ double gred[KRY_T];
+  int kw = 1;
+  while (kw < nvec) kw <<= 1;
+  const int groups = KRY_T / kw;
+  const int k = threadIdx.x % kw, grp = threadIdx.x / kw;
+  const int c0 = sv.seg_c0[s], nc = sv.seg_nc[s];
+  double t = 0.0;
+  if (k < nvec)
+    for (int b = grp; b < nc; b += groups) t += part[(size_t)(c0 + b) * KB_LDP + k];
+  gred[threadIdx.x] = t;
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(sv.tick + s, 1u) == (unsigned)(sv.seg_nc[s] - 1);
+  // fixed-shape tree over the groups (groups is a power of two)
+  for (int st = groups >> 1; st > 0; st >>= 1) {
+    if (grp < st) gred[threadIdx.x] += gred[threadIdx.x + st * kw];
+    __syncthreads();
+  }
+  if ((int)threadIdx.x < nvec) out[threadIdx.x] = gred[threadIdx.x];
   __syncthreads();
-  return last;
 }
 
 constexpr int KB_RB = 512;   // rows of one multi-dot work unit (16 per lane)
 
-// Gram-Schmidt projections at step j = ctl->j: out_s = V[0..j]_s^T w_s, into
-// small_s + out_off. The chunk of w is staged in shared memory; the work units
-// (column k, 512-row block) are spread over the warps, each lane keeping 16
-// independent loads in flight, so a step with few columns still fills the memory
-// pipeline. With zsrc, the staging also stores Z[j] = zsrc (flexible GMRES).
+// part[c][k] = V[k] . w over chunk c, k <= j = ctl->j. The chunk of w is staged in
+// shared memory; the work units (column k, 512-row block) are spread over the warps,
+// each lane keeping 16 independent loads in flight, so a step with few columns still
+// fills the memory pipeline. With zsrc, the staging also stores Z[j] = zsrc (flexible
+// GMRES).
 __global__ void __launch_bounds__(KRY_T) kb_mdot(SegView sv, const BatchCtl* ctl, const double* __restrict__ V,
-                                                int64_t ldv, const double* __restrict__ w, int out_off,
+                                                int64_t ldv, const double* __restrict__ w, double* __restrict__ part,
                                                 const double* __restrict__ zsrc, double* __restrict__ Z,
                                                 const int* skip) {
   const int c = blockIdx.x, s = sv.chunk_seg[c];
@@ -171,27 +194,24 @@ __global__ void __launch_bounds__(KRY_T) kb_mdot(SegView sv, const BatchCtl* ctl
   if ((int)threadIdx.x < nvec) {
     double t = 0.0;
     for (int b = 0; b < nb; ++b) t += red[threadIdx.x][b];
-    sv.part[(size_t)c * KB_LDP + threadIdx.x] = t;
+    part[(size_t)c * KB_LDP + threadIdx.x] = t;
   }
-  if (!seg_arrive(sv, c, s)) return;
-  seg_reduce(sv, s, nvec, sv.small + (size_t)s * sv.ks + out_off);
-  if (threadIdx.x == 0) sv.tick[s] = 0u;
 }
 
-// w_s -= V[0..j]_s h_s with h_s at small_s + h_off (4 rows per thread per pass, the
-// column loop unrolled so 16 loads are in flight). NORM: also ||w_new||^2, and the
-// last chunk of the segment completes Arnoldi column j of the instance; an instance
-// that converges or breaks down sets skip[s].
-template <bool NORM>
+// h_s = sum of part_in over the instance's chunks (kept at small_s + h_off by the
+// instance's first chunk), then w_s -= V[0..j]_s h_s (4 rows per thread per pass, the
+// column loop unrolled so 16 loads are in flight). With part_norm, the chunk's share
+// of ||w_new||^2 goes to part_norm[c][0].
 __global__ void __launch_bounds__(KRY_T) kb_update(SegView sv, const BatchCtl* ctl, const double* __restrict__ V,
-                                                  int64_t ldv, int h_off, double* __restrict__ w, int* skip) {
+                                                  int64_t ldv, const double* __restrict__ part_in, int h_off,
+                                                  double* __restrict__ w, double* __restrict__ part_norm,
+                                                  const int* skip) {
   const int c = blockIdx.x, s = sv.chunk_seg[c];
   if (skip[s]) return;
   const int j = ctl->j, nvec = j + 1;
-  double* sm = sv.small + (size_t)s * sv.ks;
   __shared__ double hs[KB_NV];
-  if ((int)threadIdx.x < KB_NV) hs[threadIdx.x] = (int)threadIdx.x < nvec ? sm[h_off + threadIdx.x] : 0.0;
-  __syncthreads();
+  seg_sum(sv, part_in, s, nvec, hs);
+  if (c == sv.seg_c0[s] && (int)threadIdx.x < nvec) sv.small[(size_t)s * sv.ks + h_off + threadIdx.x] = hs[threadIdx.x];
   const int64_t lo = sv.chunk_lo[c], hi = sv.chunk_hi[c];
   double acc = 0.0;
   for (int64_t base = lo + threadIdx.x; base < hi; base += 4 * KRY_T) {
@@ -220,243 +240,46 @@ __global__ void __launch_bounds__(KRY_T) kb_update(SegView sv, const BatchCtl* c
       }
     }
   }
-  if constexpr (NORM) {
-    double a1[1] = {acc};
-    if (!seg_partials<1>(a1, 1, sv, c, s)) return;
-    __shared__ double nrm_s[1];
-    seg_reduce(sv, s, 1, nrm_s);
-    __syncthreads();
-    if (threadIdx.x == 0) sv.tick[s] = 0u;
-    const int done = arnoldi_column_block(sm, sv.m, j, nrm_s[0], sv.sflags + 4 * s);
-    if (threadIdx.x == 0 && done) skip[s] = 1;
-  }
-}
-
-// ------------------------------------------------ fused Arnoldi step (cooperative)
-// Grid barrier of a cooperative launch (all CTAs co-resident). Sense by generation
-// counter; the wait gives up after about one second of SM clock (2^31 cycles),
-// records the failure in *err and continues, so a broken launch ends instead of
-// hanging.
-struct GridBar {
-  unsigned int* count;
-  unsigned int* gen;
-  int* err;
-};
-
-__device__ __forceinline__ void grid_sync(const GridBar& gb) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* genp = gb.gen;
-    const unsigned int g = *genp;
-    __threadfence();
-    if (atomicAdd(gb.count, 1u) == gridDim.x - 1) {
-      *gb.count = 0u;
-      __threadfence();
-      atomicAdd(gb.gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*genp == g) {
-        if (clock64() - t0 > (1ll << 31)) {
-          atomicExch(gb.err, 1);
-          break;
-        }
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-}
-
-// out[k] (shared memory) = sum over the chunks of segment s of part[c][k], in chunk
-// order (whole CTA; every CTA computes the same bits).
-__device__ __forceinline__ void seg_sum(const SegView& sv, const double* part, int s, int nvec, double* out) {
-  __shared__ double gred[KRY_T];
-  int kw = 1;
-  while (kw < nvec) kw <<= 1;
-  const int groups = KRY_T / kw;
-  const int k = threadIdx.x % kw, grp = threadIdx.x / kw;
-  const int c0 = sv.seg_c0[s], nc = sv.seg_nc[s];
-  double t = 0.0;
-  if (k < nvec)
-    for (int b = grp; b < nc; b += groups) t += __ldcg(part + (size_t)(c0 + b) * KB_LDP + k);
-  gred[threadIdx.x] = t;
-  __syncthreads();
-  if ((int)threadIdx.x < nvec) {
-    double r = 0.0;
-    for (int g = 0; g < groups; ++g) r += gred[g * kw + threadIdx.x];
-    out[threadIdx.x] = r;
-  }
-  __syncthreads();
-}
-
-// Chunk c: part[c][k] = V[k] . w over the chunk (w staged in ws), k < nvec.
-__device__ __forceinline__ void chunk_mdot(const SegView& sv, int c, int nvec, const double* __restrict__ V,
-                                           int64_t ldv, const double* w, double* ws, double (*red)[KB_CHUNK / KB_RB],
-                                           double* part) {
-  const int64_t lo = sv.chunk_lo[c];
-  const int len = (int)(sv.chunk_hi[c] - lo);
-  for (int t = threadIdx.x; t < len; t += KRY_T) ws[t] = __ldcg(w + lo + t);
-  __syncthreads();
-  const int nb = (len + KB_RB - 1) / KB_RB;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int u = warp; u < nvec * nb; u += KRY_T / 32) {
-    const int k = u / nb, b = u - k * nb;
-    const int r0 = b * KB_RB + lane;
-    const double* col = V + k * ldv + lo;
-    double a = 0.0;
-#pragma unroll
-    for (int t = 0; t < KB_RB / 32; ++t) {
-      const int r = r0 + 32 * t;
-      if (r < len) a = fma(col[r], ws[r], a);
-    }
-    a = warp_sum(a);
-    if (lane == 0) red[k][b] = a;
-  }
-  __syncthreads();
-  if ((int)threadIdx.x < nvec) {
-    double t = 0.0;
-    for (int b = 0; b < nb; ++b) t += red[threadIdx.x][b];
-    part[(size_t)c * KB_LDP + threadIdx.x] = t;
-  }
-  __syncthreads();
-}
-
-// Chunk c: w -= V[0..nvec) h (h in shared memory); returns this thread's share of
-// ||w_new||^2.
-__device__ __forceinline__ double chunk_update(const SegView& sv, int c, int nvec, const double* __restrict__ V,
-                                               int64_t ldv, const double* hs, double* w) {
-  const int64_t lo = sv.chunk_lo[c], hi = sv.chunk_hi[c];
-  double acc = 0.0;
-  for (int64_t base = lo + threadIdx.x; base < hi; base += 4 * KRY_T) {
-    double t[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t i = base + q * KRY_T;
-      t[q] = i < hi ? __ldcg(w + i) : 0.0;
-    }
-#pragma unroll 4
-    for (int k = 0; k < nvec; ++k) {
-      const double hk = hs[k];
-      const double* col = V + k * ldv;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t i = base + q * KRY_T;
-        if (i < hi) t[q] = fma(-col[i], hk, t[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t i = base + q * KRY_T;
-      if (i < hi) {
-        w[i] = t[q];
-        acc = fma(t[q], t[q], acc);
-      }
-    }
-  }
-  return acc;
-}
-
-// One Arnoldi step j = ctl->j of every active instance, as one cooperative launch:
-//   phase 1  h1 = V^T w                    (and Z[j] = zsrc for flexible GMRES)
-//   phase 2  w -= V h1, h2 = V^T w
-//   phase 3  w -= V h2, ||w||^2
-//   phase 4  v_{j+1} = vcur = w / ||w||; the CTA owning the instance's first chunk
-//            forms Arnoldi column j (h1 + h2, ||w||), its Givens rotation and the
-//            convergence test, and sets skip[s] when the instance is done.
-// Grid barriers separate the phases; every CTA sums its instance's partials itself in
-// chunk order, so no ticket is needed and the result is deterministic.
-__global__ void __launch_bounds__(KRY_T) kb_arnoldi_fused(SegView sv, const BatchCtl* ctl, double* V, int64_t ldv,
-                                                         double* w, const double* zsrc, double* Z, double* vcur,
-                                                         double* part, int* skip, GridBar gb) {
-  __shared__ double ws[KB_CHUNK];
-  __shared__ double red[KB_NV][KB_CHUNK / KB_RB];
-  __shared__ double hs[KB_NV], hs2[KB_NV];
-  const int j = ctl->j, nvec = j + 1;
-  const int nchunk = sv.nchunk;
-  double* part1 = part;
-  double* part2 = part + (size_t)nchunk * KB_LDP;
-  double* part3 = part + (size_t)2 * nchunk * KB_LDP;
-  // phase 1
-  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
-    const int s = sv.chunk_seg[c];
-    if (skip[s]) continue;
-    if (zsrc) {
-      const int64_t lo = sv.chunk_lo[c], hi = sv.chunk_hi[c];
-      for (int64_t i = lo + threadIdx.x; i < hi; i += KRY_T) Z[j * ldv + i] = zsrc[i];
-    }
-    chunk_mdot(sv, c, nvec, V, ldv, w, ws, red, part1);
-  }
-  grid_sync(gb);
-  // phase 2
-  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
-    const int s = sv.chunk_seg[c];
-    if (skip[s]) continue;
-    seg_sum(sv, part1, s, nvec, hs);
-    chunk_update(sv, c, nvec, V, ldv, hs, w);
-    __syncthreads();
-    chunk_mdot(sv, c, nvec, V, ldv, w, ws, red, part2);
-  }
-  grid_sync(gb);
-  // phase 3
-  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
-    const int s = sv.chunk_seg[c];
-    if (skip[s]) continue;
-    seg_sum(sv, part2, s, nvec, hs);
-    double a1[1] = {chunk_update(sv, c, nvec, V, ldv, hs, w)};
-    // block sum of ||w||^2 into part3[c][0]
-    const double v = warp_sum(a1[0]);
-    if ((threadIdx.x & 31) == 0) red[0][threadIdx.x >> 5] = v;
+  if (part_norm) {
+    __shared__ double red[KRY_T / 32];
+    const double v = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
-      for (int q = 0; q < KRY_T / 32; ++q) t += red[0][q];
-      part3[(size_t)c * KB_LDP] = t;
+      for (int q = 0; q < KRY_T / 32; ++q) t += red[q];
+      part_norm[(size_t)c * KB_LDP] = t;
     }
-    __syncthreads();
-  }
-  grid_sync(gb);
-  // phase 4
-  KrySmall S{sv.m};
-  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
-    const int s = sv.chunk_seg[c];
-    if (skip[s]) continue;
-    seg_sum(sv, part3, s, 1, hs);
-    const double nrm2 = hs[0];
-    const double hn = sqrt(nrm2);
-    const double f = hn > 0.0 ? 1.0 / hn : 0.0;
-    const int64_t lo = sv.chunk_lo[c], hi = sv.chunk_hi[c];
-    double* out = V + (size_t)(j + 1) * ldv;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += KRY_T) {
-      const double t = __ldcg(w + i) * f;
-      out[i] = t;
-      vcur[i] = t;
-    }
-    if (c != sv.seg_c0[s]) continue;
-    // Arnoldi column j and its Givens rotation
-    double* sm = sv.small + (size_t)s * sv.ks;
-    seg_sum(sv, part1, s, nvec, hs);
-    seg_sum(sv, part2, s, nvec, hs2);
-    if ((int)threadIdx.x < nvec) {
-      sm[S.h1() + threadIdx.x] = hs[threadIdx.x];
-      sm[S.h2() + threadIdx.x] = hs2[threadIdx.x];
-    }
-    __syncthreads();
-    const int done = arnoldi_column_block(sm, sv.m, j, nrm2, sv.sflags + 4 * s);
-    if (threadIdx.x == 0 && done) skip[s] = 1;
-    __syncthreads();
   }
 }
 
-// V[j+1]_s = vcur_s = w_s / ||w_s|| (j = ctl->j)
-__global__ void kb_scale(SegView sv, const BatchCtl* ctl, const double* __restrict__ w, double* __restrict__ V,
-                         int64_t ldv, double* __restrict__ vcur, const int* skip) {
-  const int c = blockIdx.x, s = sv.chunk_seg[c];
+// ||w_s||^2 = sum of part_norm over the instance's chunks; V[j+1]_s = vcur_s = w_s /
+// ||w_s||. CTAs 0 .. nseg-1 (scheduled first) complete Arnoldi column j of one instance
+// each (from h1, h2 in its small area), its Givens rotation and the convergence test,
+// and set skip[s] when the instance is done; the other CTAs scale one chunk each
+// (a chunk of an instance that is done at this step may be left unscaled: its v_{j+1}
+// is never used).
+__global__ void __launch_bounds__(KRY_T) kb_scale(SegView sv, const BatchCtl* ctl, const double* __restrict__ w,
+                                                 const double* __restrict__ part_norm, double* __restrict__ V,
+                                                 int64_t ldv, double* __restrict__ vcur, int* skip) {
+  const int b = blockIdx.x;
+  const bool givens = b < sv.nseg;
+  const int c = givens ? -1 : b - sv.nseg;
+  const int s = givens ? b : sv.chunk_seg[c];
   if (skip[s]) return;
-  KrySmall S{sv.m};
-  const double nr = sqrt(sv.small[(size_t)s * sv.ks + S.sc()]);
+  __shared__ double nrm_s[1];
+  seg_sum(sv, part_norm, s, 1, nrm_s);
+  const double nrm2 = nrm_s[0];
+  const int j = ctl->j;
+  if (givens) {
+    const int done = arnoldi_column_block(sv.small + (size_t)s * sv.ks, sv.m, j, nrm2, sv.sflags + 4 * s);
+    if (threadIdx.x == 0 && done) skip[s] = 1;
+    return;
+  }
+  const double nr = sqrt(nrm2);
   const double f = nr > 0.0 ? 1.0 / nr : 0.0;
-  double* out = V + (size_t)(ctl->j + 1) * ldv;
-  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) {
+  double* out = V + (size_t)(j + 1) * ldv;
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += KRY_T) {
     const double t = w[i] * f;
     out[i] = t;
     vcur[i] = t;

@@ -21,6 +21,7 @@
 #include <map>
 #include <numeric>
 #include <tuple>
+#include <type_traits>
 #include "ldg_launch.cuh"
 #include "ldg_ctx.h"
 
@@ -317,7 +318,25 @@ int do_pc_setup(ldg_ctx* ctx, const double* u) {
     CK(cudaMalloc(&ctx->d_binv, (size_t)ctx->E * n * n * (fp64 ? sizeof(double) : sizeof(float))));
     ctx->binv_prec = want;
   }
-  const int threads = std::min(256, ((n + 31) / 32) * 32);
+  const int threads = n >= 16 ? 256 : ((n + 31) / 32) * 32;
+  // compile-time block sizes of the common element blocks (quadrilateral Euler p = 1..4,
+  // scalar models p = 3)
+  auto fixed = [&](auto tag, auto nconst) -> int {
+    typedef decltype(tag) T;
+    constexpr int NN = decltype(nconst)::value;
+    const size_t smem = block_inverse_smem<T>(NN);
+    CK(cudaFuncSetAttribute(k_block_inverse_n<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_block_inverse_n<T, NN><<<(unsigned)ctx->E, 256, smem, ctx->stream>>>(ctx->d_blocks, (T*)ctx->d_binv,
+                                                                           ctx->d_status);
+    count_launch();
+    CK(cudaGetLastError());
+    ctx->pc_ready = true;
+    return LDG_OK;
+  };
+  if (n == 16) return fp64 ? fixed(0.0, std::integral_constant<int, 16>()) : fixed(0.f, std::integral_constant<int, 16>());
+  if (n == 36) return fp64 ? fixed(0.0, std::integral_constant<int, 36>()) : fixed(0.f, std::integral_constant<int, 36>());
+  if (n == 64) return fp64 ? fixed(0.0, std::integral_constant<int, 64>()) : fixed(0.f, std::integral_constant<int, 64>());
+  if (n == 100 && !fp64) return fixed(0.f, std::integral_constant<int, 100>());
   if (fp64) {
     const size_t smem = block_inverse_smem<double>(n);
     CK(cudaFuncSetAttribute(k_block_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -345,8 +364,11 @@ int pc_apply(ldg_ctx* ctx, const double* x, double* y, const int* skip, const in
   const bool f64 = ctx->binv_prec == LDG_FP64;
   const double* bd = (const double*)ctx->d_binv;
   const float* bf = (const float*)ctx->d_binv;
-  // one warp per element up to 128 rows; one CTA per element beyond
-  if (n <= 32) {
+  // FP32 blocks whose size divides 128: flat 16-byte loads; otherwise one warp per
+  // element up to 128 rows, one CTA per element beyond
+  if (!f64 && n >= 16 && 128 % n == 0) {
+    k_block_apply_vec<<<gw, 256, 0, ctx->stream>>>(bf, x, y, n, E, skip, inst, inst_skip);
+  } else if (n <= 32) {
     if (f64) k_block_apply_warp<double, 1><<<gw, 256, 0, ctx->stream>>>(bd, x, y, n, E, skip, inst, inst_skip);
     else k_block_apply_warp<float, 1><<<gw, 256, 0, ctx->stream>>>(bf, x, y, n, E, skip, inst, inst_skip);
   } else if (n <= 64) {
@@ -838,8 +860,8 @@ int autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms) {
     count_launch();
     for (const KernelSet* k : cand) {
       ctx->ks = k;
-      const int reps = 5;
-      for (int w = 0; w < 2 && !rc; ++w) rc = jvp_args(ctx, base_args(ctx), u, v, jv, prec);
+      const int reps = 10;
+      for (int w = 0; w < 3 && !rc; ++w) rc = jvp_args(ctx, base_args(ctx), u, v, jv, prec);
       if (!rc && (ce = cudaEventRecord(e0, ctx->stream))) rc = fail(ctx, LDG_ERR_CUDA, cudaGetErrorString(ce));
       for (int r = 0; r < reps && !rc; ++r) rc = jvp_args(ctx, base_args(ctx), u, v, jv, prec);
       if (!rc && (ce = cudaEventRecord(e1, ctx->stream))) rc = fail(ctx, LDG_ERR_CUDA, cudaGetErrorString(ce));

@@ -70,8 +70,8 @@ __device__ __forceinline__ double sum_partials(const double* part, int ldp, int 
 
 // out[k] = sum over blocks of part[b][k], k < nvec, by the whole last block: the
 // threads form KRY_T / kw groups of kw lanes (kw = nvec rounded up to a power of
-// two), each group strides over the blocks, then one thread per k sums the groups
-// in order. The summation order is fixed, so the result is deterministic.
+// two), each group strides over the blocks, then a fixed-shape tree sums the groups.
+// The summation order is fixed, so the result is deterministic.
 __device__ __forceinline__ void reduce_partials(const double* part, int ldp, int nvec, double* out) {
   __shared__ double gred[KRY_T];
   int kw = 1;
@@ -86,11 +86,12 @@ __device__ __forceinline__ void reduce_partials(const double* part, int ldp, int
   }
   gred[threadIdx.x] = s;
   __syncthreads();
-  if (threadIdx.x < nvec) {
-    double t = 0.0;
-    for (int g = 0; g < groups; ++g) t += gred[g * kw + threadIdx.x];
-    out[threadIdx.x] = t;
+  // fixed-shape tree over the groups (groups is a power of two)
+  for (int st = groups >> 1; st > 0; st >>= 1) {
+    if (grp < st) gred[threadIdx.x] += gred[threadIdx.x + st * kw];
+    __syncthreads();
   }
+  if (threadIdx.x < nvec) out[threadIdx.x] = gred[threadIdx.x];
 }
 
 // Completes Arnoldi column j from the two Gram-Schmidt passes' projections h1 + h2 and

@@ -13,9 +13,9 @@ namespace ldg {
 
 // inv[e] = blocks[e]^{-1} in precision T: in-place Gauss-Jordan elimination with
 // partial (row) pivoting, the row interchanges undone as column interchanges at the
-// end. One CTA per element; thread t owns columns t, t + blockDim, ... of the n x n
-// matrix held row-major in shared memory, so every update is one FMA per owned
-// entry with no index arithmetic in the inner loop. A zero pivot sets *status = 1.
+// end. One CTA per element, the n x n matrix row-major in shared memory; in each
+// elimination step thread t updates column t mod n in every (blockDim / n)-th row,
+// consecutive threads on consecutive columns. A zero pivot sets *status = 1.
 template <class T>
 __global__ void k_block_inverse(const double* __restrict__ blocks, T* __restrict__ inv, int n, int* status) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -25,6 +25,10 @@ __global__ void k_block_inverse(const double* __restrict__ blocks, T* __restrict
   __shared__ int piv;
   const int e = blockIdx.x;
   const double* B = blocks + (size_t)e * n * n;   // column-major
+  // elimination mapping: thread t updates column jc = t mod n in rows rg, rg + ng, ...
+  const int ng = max(1, (int)blockDim.x / n);
+  const int jc = n <= (int)blockDim.x ? ((int)threadIdx.x < ng * n ? (int)threadIdx.x % n : n) : (int)threadIdx.x;
+  const int rg = n <= (int)blockDim.x ? (int)threadIdx.x / n : 0;
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int col = idx / n, row = idx - col * n;
     A[row * n + col] = (T)B[idx];
@@ -63,10 +67,12 @@ __global__ void k_block_inverse(const double* __restrict__ blocks, T* __restrict
     for (int j = threadIdx.x; j < n; j += blockDim.x) A[k * n + j] = (j == k ? T(1) : A[k * n + j]) * ip;
     __syncthreads();
     // other rows: A[i][j] -= fac[i] A[k][j], with column k taking -fac[i] / pivot
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    // (row k is not written here, so its entries are read unchanged)
+    // (blocks wider than the CTA: each thread takes columns t, t + blockDim, ... in all rows)
+    for (int j = jc; j < n; j += (n <= (int)blockDim.x ? n : (int)blockDim.x)) {
       const T akj = A[k * n + j];
       const bool colk = (j == k);
-      for (int i = 0; i < n; ++i) {
+      for (int i = rg; i < n; i += ng) {
         if (i == k) continue;
         const T aij = colk ? T(0) : A[i * n + j];
         A[i * n + j] = aij - fac[i] * akj;
@@ -89,6 +95,106 @@ __global__ void k_block_inverse(const double* __restrict__ blocks, T* __restrict
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int col = idx / n, row = idx - col * n;
     Iv[idx] = A[row * n + col];
+  }
+}
+
+template <class T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 type; };
+template <> struct Vec4<double> { typedef double4 type; };
+
+// The same Gauss-Jordan inversion for a compile-time block size N (a multiple of 4,
+// N <= 128, 256 threads): the elimination gives each thread 4 adjacent columns (one
+// 16- or 32-byte shared-memory access per row) in N / (256 / (N/4)) rows, all loops
+// unrolled, so the update issues about two instructions per FMA instead of ten.
+template <class T, int N>
+__global__ void __launch_bounds__(256) k_block_inverse_n(const double* __restrict__ blocks, T* __restrict__ inv,
+                                                         int* status) {
+  static_assert(N % 4 == 0 && N <= 128, "block size");
+  typedef typename Vec4<T>::type V4;
+  constexpr int CG = N / 4;                       // column groups of 4
+  constexpr int NG = (256 / CG) < N ? (256 / CG) : N;   // row groups
+  constexpr int RPT = (N + NG - 1) / NG;          // rows per thread
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* A = (T*)sm_raw;             // [N][N] row-major
+  T* fac = A + N * N;            // [N]
+  int* ipiv = (int*)(fac + N);   // [N]
+  __shared__ int piv;
+  const int e = blockIdx.x;
+  const double* B = blocks + (size_t)e * N * N;   // column-major
+  for (int idx = threadIdx.x; idx < N * N; idx += 256) {
+    const int col = idx / N, row = idx - col * N;
+    A[row * N + col] = (T)B[idx];
+  }
+  const int cg = threadIdx.x % CG, rg = threadIdx.x / CG;
+  const bool elim = rg < NG;
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    if (threadIdx.x < 32) {
+      T best = T(-1);
+      int bi = k;
+      for (int i = k + threadIdx.x; i < N; i += 32) {
+        const T v = fabs(A[i * N + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (threadIdx.x == 0) { piv = bi; ipiv[k] = bi; }
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != k && threadIdx.x < N) {
+      const T t = A[k * N + threadIdx.x];
+      A[k * N + threadIdx.x] = A[p * N + threadIdx.x];
+      A[p * N + threadIdx.x] = t;
+    }
+    __syncthreads();
+    const T pv = A[k * N + k];
+    if (pv == T(0) && threadIdx.x == 0) *status = 1;
+    const T ip = pv != T(0) ? T(1) / pv : T(0);
+    if (threadIdx.x < N) fac[threadIdx.x] = ((int)threadIdx.x == k) ? T(0) : A[threadIdx.x * N + k];
+    __syncthreads();
+    if (threadIdx.x < N) A[k * N + threadIdx.x] = ((int)threadIdx.x == k ? T(1) : A[k * N + threadIdx.x]) * ip;
+    __syncthreads();
+    if (elim) {
+      const V4 pk = reinterpret_cast<const V4*>(A + k * N)[cg];
+      const int kc = k - 4 * cg;                  // column k's position in this group, if 0..3
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int i = rg + NG * r;
+        if (i >= N || i == k) continue;
+        V4* ap = reinterpret_cast<V4*>(A + i * N) + cg;
+        V4 a = *ap;
+        if (kc == 0) a.x = T(0);
+        if (kc == 1) a.y = T(0);
+        if (kc == 2) a.z = T(0);
+        if (kc == 3) a.w = T(0);
+        const T f = fac[i];
+        a.x -= f * pk.x;
+        a.y -= f * pk.y;
+        a.z -= f * pk.z;
+        a.w -= f * pk.w;
+        *ap = a;
+      }
+    }
+    __syncthreads();
+  }
+  T* Iv = inv + (size_t)e * N * N;
+  for (int row = threadIdx.x; row < N; row += 256)
+    for (int k = N - 1; k >= 0; --k) {
+      const int p = ipiv[k];
+      if (p != k) {
+        const T t = A[row * N + k];
+        A[row * N + k] = A[row * N + p];
+        A[row * N + p] = t;
+      }
+    }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < N * N; idx += 256) {
+    const int col = idx / N, row = idx - col * N;
+    Iv[idx] = A[row * N + col];
   }
 }
 
@@ -158,6 +264,53 @@ __global__ void __launch_bounds__(256) k_block_apply_warp(const T* __restrict__ 
   for (int t = 0; t < RW; ++t) {
     const int r = lane + 32 * t;
     if (r < n) y[e * n + r] = (double)acc[t];
+  }
+}
+
+// y_e = inv_e x_e (FP32 blocks) for block sizes n that divide 128 (n >= 16): one warp per
+// element reads the column-major block as a flat array with 16-byte loads, 128
+// consecutive values (128 / n columns) per warp instruction, so every lane keeps the
+// same 4 rows r = 4 lane mod n throughout; lanes holding the same rows are summed by
+// shuffles at the end. x_e is staged in shared memory. 8 elements per CTA.
+__global__ void __launch_bounds__(256) k_block_apply_vec(const float* __restrict__ inv, const double* __restrict__ x,
+                                                        double* __restrict__ y, int n, int64_t E, const int* skip,
+                                                        const int* inst, const int* inst_skip) {
+  if (skip && *skip) return;
+  __shared__ float xs[8][128];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = blockIdx.x * (int64_t)8 + wid;
+  const bool live = e < E && !(inst_skip && inst_skip[inst[e]]);
+  if (live)
+    for (int i = lane; i < n; i += 32) xs[wid][i] = (float)x[e * n + i];
+  __syncwarp();
+  if (!live) return;
+  const float4* blk = reinterpret_cast<const float4*>(inv + e * n * n);
+  const int per = n * n / 128;                 // float4 loads per lane
+  const int cpi = 128 / n;                     // columns per warp instruction
+  const int c_lane = (4 * lane) / n;           // the lane's column within the instruction
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+  for (int k = 0; k < per; ++k) {
+    const float4 b = __ldg(blk + k * 32 + lane);
+    const float xc = xs[wid][k * cpi + c_lane];
+    acc.x = fmaf(b.x, xc, acc.x);
+    acc.y = fmaf(b.y, xc, acc.y);
+    acc.z = fmaf(b.z, xc, acc.z);
+    acc.w = fmaf(b.w, xc, acc.w);
+  }
+  // lanes l and l + n/4, l + 2n/4, ... hold partial sums of the same rows
+  for (int off = n / 4; off < 32; off <<= 1) {
+    acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+    acc.z += __shfl_down_sync(0xffffffffu, acc.z, off);
+    acc.w += __shfl_down_sync(0xffffffffu, acc.w, off);
+  }
+  if (lane < n / 4) {
+    double* ye = y + e * n + 4 * lane;
+    ye[0] = (double)acc.x;
+    ye[1] = (double)acc.y;
+    ye[2] = (double)acc.z;
+    ye[3] = (double)acc.w;
   }
 }
 

@@ -36,10 +36,12 @@ def test_diag_blocks_match_complex_step_jacobian(mesh, p, model, case):
     assert_parity(blk.transpose(0, 2, 1), ref, what="diag blocks")
 
 
-def test_block_inverse_applies():
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_block_inverse_applies(p):
+    """Block sizes 16, 36, 64, 100 (the compile-time-size inversion), FP64 and FP32."""
     mesh = synth.quad_box((5, 4), hi=(10.0, 10.0), periodic=(True, True))
     for prec, tol in ((0, 1e-11), (1, 1e-4)):
-        o, g = pair(mesh, 3, oracle.EULER, oracle.CASE_VORTEX, krylov_precision=prec, precond=1)
+        o, g = pair(mesh, p, oracle.EULER, oracle.CASE_VORTEX, krylov_precision=prec, precond=1)
         u = o.interpolate(0.0)
         g.set_time(2, 0.05, 0.05, cuda(u), cuda(u))
         g.precond_setup(cuda(u))
