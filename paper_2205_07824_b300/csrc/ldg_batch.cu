@@ -214,10 +214,10 @@ int emit_arnoldi(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle hc, in
   KrySmall S{b->m};
   kb_mdot<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, part1, b->pc ? b->d_zcur : nullptr,
                                       b->d_Z, b->d_skip_arn);
-  kb_update<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, part1, (int)S.h1(), b->d_w, nullptr,
+  kb_update<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, part1, (int)S.h1(), b->d_w, nullptr, nullptr,
                                         b->d_skip_arn);
   kb_mdot<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, part2, nullptr, nullptr, b->d_skip_arn);
-  kb_update<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, part2, (int)S.h2(), b->d_w, part3,
+  kb_update<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, part2, (int)S.h2(), b->d_w, part3, nullptr,
                                         b->d_skip_arn);
   kb_scale<<<b->nseg + b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_w, part3, b->d_V, b->ntot, b->d_vcur,
                                                  b->d_skip_arn);

@@ -123,6 +123,8 @@ __global__ void __launch_bounds__(KRY_T) kb_norm2(SegView sv, const double* __re
 // One classical Gram-Schmidt step with re-orthogonalisation is five launches:
 //   kb_mdot(part1)  kb_update(h1 <- part1; w -= V h1)  kb_mdot(part2)
 //   kb_update(h2 <- part2; w -= V h2; ||w||^2 -> part3)  kb_scale(||w|| <- part3; v_{j+1})
+// (kb_update can also form the next projections in its own sweep, part_dots; the
+// per-column warp sums inside the row loop measured slower than the separate kb_mdot.)
 // A kernel only writes per-chunk partials; the next kernel's CTAs each sum the
 // partials of their own instance in chunk order (every CTA gets the same bits), so
 // no atomics, tickets or serial last-block tails are needed. The CTA owning an
@@ -201,11 +203,13 @@ __global__ void __launch_bounds__(KRY_T) kb_mdot(SegView sv, const BatchCtl* ctl
 // h_s = sum of part_in over the instance's chunks (kept at small_s + h_off by the
 // instance's first chunk), then w_s -= V[0..j]_s h_s (4 rows per thread per pass, the
 // column loop unrolled so 16 loads are in flight). With part_norm, the chunk's share
-// of ||w_new||^2 goes to part_norm[c][0].
+// of ||w_new||^2 goes to part_norm[c][0]. With part_dots, the same sweep also forms
+// the next pass's projections V[k] . w_new over the chunk (the rows of V it just read,
+// read again from L1) into part_dots[c][k].
 __global__ void __launch_bounds__(KRY_T) kb_update(SegView sv, const BatchCtl* ctl, const double* __restrict__ V,
                                                   int64_t ldv, const double* __restrict__ part_in, int h_off,
                                                   double* __restrict__ w, double* __restrict__ part_norm,
-                                                  const int* skip) {
+                                                  double* __restrict__ part_dots, const int* skip) {
   const int c = blockIdx.x, s = sv.chunk_seg[c];
   if (skip[s]) return;
   const int j = ctl->j, nvec = j + 1;
@@ -213,8 +217,15 @@ __global__ void __launch_bounds__(KRY_T) kb_update(SegView sv, const BatchCtl* c
   seg_sum(sv, part_in, s, nvec, hs);
   if (c == sv.seg_c0[s] && (int)threadIdx.x < nvec) sv.small[(size_t)s * sv.ks + h_off + threadIdx.x] = hs[threadIdx.x];
   const int64_t lo = sv.chunk_lo[c], hi = sv.chunk_hi[c];
+  __shared__ double dred[KB_NV][KRY_T / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (part_dots && lane < KB_NV) dred[lane][warp] = 0.0;
+  __syncwarp();
   double acc = 0.0;
-  for (int64_t base = lo + threadIdx.x; base < hi; base += 4 * KRY_T) {
+  // the trip count depends on the warp's first row only, so every lane of a warp takes
+  // part in the shuffles below (rows past the chunk end are masked per lane)
+  for (int64_t base0 = lo + (threadIdx.x - lane); base0 < hi; base0 += 4 * KRY_T) {
+    const int64_t base = base0 + lane;
     double t[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -238,6 +249,28 @@ __global__ void __launch_bounds__(KRY_T) kb_update(SegView sv, const BatchCtl* c
         w[i] = t[q];
         acc = fma(t[q], t[q], acc);
       }
+    }
+    if (part_dots) {
+      // warp sums per column, accumulated per warp in a fixed order
+      for (int k = 0; k < nvec; ++k) {
+        const double* col = V + k * ldv;
+        double d = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t i = base + q * KRY_T;
+          if (i < hi) d = fma(col[i], t[q], d);
+        }
+        d = warp_sum(d);
+        if (lane == 0) dred[k][warp] += d;
+      }
+    }
+  }
+  if (part_dots) {
+    __syncthreads();
+    if ((int)threadIdx.x < nvec) {
+      double t = 0.0;
+      for (int q = 0; q < KRY_T / 32; ++q) t += dred[threadIdx.x][q];
+      part_dots[(size_t)c * KB_LDP + threadIdx.x] = t;
     }
   }
   if (part_norm) {

@@ -268,6 +268,8 @@ int ensure_pc_storage(ldg_ctx* ctx) {
   return LDG_OK;
 }
 
+const KernelSet* find_set(const ldg_ctx* ctx, int tile);
+
 // Exact diagonal blocks dR_K/du_K at state u, computed in the given arithmetic.
 int do_blocks(ldg_ctx* ctx, const double* u, int prec, double* blocks) {
   int rc;
@@ -276,14 +278,26 @@ int do_blocks(ldg_ctx* ctx, const double* u, int prec, double* blocks) {
   const int nloc = ctx->nloc;
   const int64_t E = ctx->E;
   if (!ctx->ks->qstage) {
-    // dual numbers with a unit tangent on every element and none on its neighbours
-    StageFn rs = prec == LDG_FP32 ? ctx->ks->residual32 : ctx->ks->residual;
-    for (int l = 0; l < nloc; ++l) {
-      KArgs a = base_args(ctx);
-      a.u = u; a.v = u; a.out = nullptr;
-      a.blk_col = l;
-      a.blk_out = blocks;
-      CK(rs(MODE_JV, a, ctx->stream));
+    if (prec == LDG_FP32) {
+      // dual numbers with BLK_KT unit tangents on every element and none on its neighbours;
+      // the default tile (the J.v's tuned tile suits one tangent, not eight)
+      const KernelSet* k0 = find_set(ctx, 0);
+      for (int l = 0; l < nloc; l += BLK_KT) {
+        KArgs a = base_args(ctx);
+        a.u = u; a.v = u; a.out = nullptr;
+        a.blk_out = blocks;
+        CK(k0->blocks32(l, a, ctx->stream));
+      }
+    } else {
+      // FP64: one unit tangent per launch (the FP64 multi-tangent kernel needs one
+      // element per CTA at over 200 registers per thread, and measured slower)
+      for (int l = 0; l < nloc; ++l) {
+        KArgs a = base_args(ctx);
+        a.u = u; a.v = u; a.out = nullptr;
+        a.blk_col = l;
+        a.blk_out = blocks;
+        CK(ctx->ks->residual(MODE_JV, a, ctx->stream));
+      }
     }
     return LDG_OK;
   }

@@ -46,12 +46,89 @@ template <class R> __device__ __forceinline__ Dual<R> dsqrt(Dual<R> a) {
   return Dual<R>(s, a.d / (R(2) * s));
 }
 
+// Dual numbers with K tangents: the derivative along K directions in one evaluation
+// (the element-diagonal block extraction seeds K unit columns at once).
+template <class R, int K> struct DualK {
+  R v, d[K];
+  __host__ __device__ DualK() {}
+  __host__ __device__ DualK(R a) : v(a) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) d[i] = R(0);
+  }
+};
+#define LDG_DK template <class R, int K> __device__ __forceinline__ DualK<R, K>
+LDG_DK operator+(DualK<R, K> a, DualK<R, K> b) {
+  a.v += b.v;
+#pragma unroll
+  for (int i = 0; i < K; ++i) a.d[i] += b.d[i];
+  return a;
+}
+LDG_DK operator-(DualK<R, K> a, DualK<R, K> b) {
+  a.v -= b.v;
+#pragma unroll
+  for (int i = 0; i < K; ++i) a.d[i] -= b.d[i];
+  return a;
+}
+LDG_DK operator-(DualK<R, K> a) {
+  a.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < K; ++i) a.d[i] = -a.d[i];
+  return a;
+}
+LDG_DK operator*(DualK<R, K> a, DualK<R, K> b) {
+  DualK<R, K> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+LDG_DK operator/(DualK<R, K> a, DualK<R, K> b) {
+  const R inv = R(1) / b.v;
+  DualK<R, K> r;
+  r.v = a.v * inv;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * inv;
+  return r;
+}
+LDG_DK operator+(DualK<R, K> a, R b) { a.v += b; return a; }
+LDG_DK operator+(R a, DualK<R, K> b) { b.v += a; return b; }
+LDG_DK operator-(DualK<R, K> a, R b) { a.v -= b; return a; }
+LDG_DK operator-(R a, DualK<R, K> b) { return DualK<R, K>(a) - b; }
+LDG_DK operator*(DualK<R, K> a, R b) {
+  a.v *= b;
+#pragma unroll
+  for (int i = 0; i < K; ++i) a.d[i] *= b;
+  return a;
+}
+LDG_DK operator*(R a, DualK<R, K> b) { return b * a; }
+LDG_DK operator/(DualK<R, K> a, R b) { return a * (R(1) / b); }
+LDG_DK operator/(R a, DualK<R, K> b) { return DualK<R, K>(a) / b; }
+template <class R, int K> __device__ __forceinline__ DualK<R, K>& operator+=(DualK<R, K>& a, DualK<R, K> b) {
+  a = a + b;
+  return a;
+}
+template <class R, int K> __device__ __forceinline__ DualK<R, K>& operator-=(DualK<R, K>& a, DualK<R, K> b) {
+  a = a - b;
+  return a;
+}
+LDG_DK dsqrt(DualK<R, K> a) {
+  DualK<R, K> r;
+  r.v = dsqrt(a.v);
+  const R h = R(1) / (R(2) * r.v);
+#pragma unroll
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * h;
+  return r;
+}
+#undef LDG_DK
+
 template <class S> struct RealOf { typedef S type; };
 template <class R> struct RealOf<Dual<R>> { typedef R type; };
+template <class R, int K> struct RealOf<DualK<R, K>> { typedef R type; };
 
 __device__ __forceinline__ double val(double x) { return x; }
 __device__ __forceinline__ float val(float x) { return x; }
 template <class R> __device__ __forceinline__ R val(Dual<R> x) { return x.v; }
+template <class R, int K> __device__ __forceinline__ R val(const DualK<R, K>& x) { return x.v; }
 // The part of a scalar a kernel writes out: the tangent for dual numbers, else the value.
 __device__ __forceinline__ double outp(double x) { return x; }
 __device__ __forceinline__ float outp(float x) { return x; }

@@ -637,4 +637,177 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
   }
 }
 
+// ============================================================ block columns
+// Columns col0 .. col0 + KT - 1 of every element's diagonal block dR_K/du_K for a
+// model without q (Euler): the same stages as k_residual in MODE_JV, with a dual
+// number of KT tangents seeded with the unit columns on the element's own state and
+// no tangent on its neighbours. The linear stages after the flux evaluation (face
+// lift, volume integration) treat the KT tangents as KT extra components.
+template <class EL, class MD, class R, class TL, int KT> struct BLayout {
+  typedef DualK<R, KT> S;
+  static constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NCO = NCU * KT;
+  static constexpr int GEO = Geo<DIM>::size(NF);
+  static constexpr int B_GEO = al16(GEO * sizeof(R)), B_X = al16(NCU * EL::NPE * sizeof(S)),
+                       B_LF = al16(NF * NCO * EL::NFN * sizeof(R));
+  static constexpr int B_FNM = al16(NF * NCU * EL::NFN * sizeof(S)), B_FNP = al16(NF * NCU * EL::NFN * sizeof(R)),
+                       B_TRM = al16(NF * NCU * EL::NFQ * sizeof(S)), B_TRP = al16(NF * NCU * EL::NFQ * sizeof(R)),
+                       B_FT = al16(NF * NCU * Sizes<EL>::MF * sizeof(S) > NF * NCO * Sizes<EL>::MF * sizeof(R)
+                                       ? NF * NCU * Sizes<EL>::MF * sizeof(S)
+                                       : NF * NCO * Sizes<EL>::MF * sizeof(R)),
+                       B_FH = al16(NF * NCO * EL::NFQ * sizeof(R));
+  static constexpr int PHASE_F = B_FNM + B_FNP + B_TRM + B_TRP + B_FT + B_FH;
+  static constexpr int B_XQ = al16(NCU * Sizes<EL>::M * sizeof(S)), B_G = al16(NCO * Sizes<EL>::M * sizeof(R));
+  static constexpr int PHASE_V = 2 * B_XQ + (DIM + 1) * B_G + 2 * B_G + B_G;
+  static constexpr int PER_ELEM = B_GEO + B_X + B_LF + (PHASE_F > PHASE_V ? PHASE_F : PHASE_V);
+  static constexpr int NE_ = TL::BUDGET_R / PER_ELEM;
+  static constexpr int NE = NE_ < 1 ? 1 : (NE_ > TL::NE_MAX ? TL::NE_MAX : NE_);
+  static constexpr int SMEM = NE * PER_ELEM;
+};
+
+template <class EL, class MD, class R, class TL, int KT>
+__global__ void __launch_bounds__(256) k_block_columns(KArgs a, int col0) {
+  typedef BLayout<EL, MD, R, TL, KT> L;
+  typedef typename L::S S;
+  constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ, NQV = EL::NQV;
+  constexpr int NE = L::NE, GEO = L::GEO, NCO = L::NCO, NLOC = NCU * NPE;
+  static_assert(!MD::HASQ, "block columns by dual numbers are for models without q");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int e0 = blockIdx.x * NE;
+  const int ne = min(NE, a.E - e0);
+  if (!cta_active(a, e0, ne)) return;
+  const R* OPS = ops_of<R>(a);
+  __shared__ MPar<R> MPs[NE];
+  for (int e = threadIdx.x; e < NE; e += blockDim.x) MPs[e] = mpar<R>(e < ne ? elem_mp(a, e0 + e) : a.mp);
+  R* Gs = (R*)smem;
+  S* X = (S*)(smem + NE * L::B_GEO);                        // [NE][NCU][NPE]
+  R* LF = (R*)(smem + NE * (L::B_GEO + L::B_X));            // [NE][NF][NCO][NFN]
+  unsigned char* arena = smem + NE * (L::B_GEO + L::B_X + L::B_LF);
+  const double* u = (const double*)a.u;
+
+  for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = R(a.geo[(size_t)e0 * GEO + i]);
+  for (int i = threadIdx.x; i < NE * NCU * NPE; i += blockDim.x) {
+    const int loc = i % NLOC, e = i / NLOC;
+    S val = S(R(0));
+    if (e < ne) {
+      val = S(R(u[(size_t)e0 * NLOC + i]));
+#pragma unroll
+      for (int t = 0; t < KT; ++t) val.d[t] = (loc == col0 + t) ? R(1) : R(0);
+    }
+    X[i] = val;
+  }
+  __syncthreads();
+
+  // ------------------------------------------------------------- face phase
+  {
+    S* FNm = (S*)arena;
+    R* FNp = (R*)(arena + NE * L::B_FNM);
+    S* TRm = (S*)(arena + NE * (L::B_FNM + L::B_FNP));
+    R* TRp = (R*)(arena + NE * (L::B_FNM + L::B_FNP + L::B_TRM));
+    unsigned char* TMP = arena + NE * (L::B_FNM + L::B_FNP + L::B_TRM + L::B_TRP);
+    R* FH = (R*)(arena + NE * (L::B_FNM + L::B_FNP + L::B_TRM + L::B_TRP + L::B_FT));
+    for (int it = threadIdx.x; it < NE * NF * NCU * NFN; it += blockDim.x) {
+      const int j = it % NFN, c = (it / NFN) % NCU, f = (it / (NFN * NCU)) % NF, e = it / (NFN * NCU * NF);
+      S vm = S(R(0));
+      R vp = R(0);
+      if (e < ne) {
+        vm = X[(e * NCU + c) * NPE + EL::face_node(f, j)];
+        const int nb = a.nbr[(size_t)(e0 + e) * NF + f];
+        if (nb >= 0) {
+          const int nfc = a.nbf[(size_t)(e0 + e) * NF + f] & 7;
+          vp = R(u[((size_t)nb * NCU + c) * NPE + EL::face_node(nfc, j)]);
+        }
+      }
+      FNm[it] = vm;
+      FNp[it] = vp;
+    }
+    __syncthreads();
+    face_trace<EL>(FNm, TRm, (S*)TMP, OPS, NE * NF * NCU);
+    __syncthreads();
+    face_trace<EL>(FNp, TRp, (R*)TMP, OPS, NE * NF * NCU);
+    __syncthreads();
+    for (int it = threadIdx.x; it < NE * NF * NFQ; it += blockDim.x) {
+      const int k = it % NFQ, f = (it / NFQ) % NF, e = it / (NFQ * NF);
+      if (e >= ne) {
+        for (int co = 0; co < NCO; ++co) FH[((e * NF + f) * NCO + co) * NFQ + k] = R(0);
+        continue;
+      }
+      const R* g = Gs + e * GEO;
+      const R* nrm = g + Geo<DIM>::FACE + f * (DIM + 1);
+      const R w = face_w<EL>(OPS, k) * nrm[DIM];
+      const int nb = a.nbr[(size_t)(e0 + e) * NF + f];
+      S um[NCU], qm[1], fh[NCU];
+      for (int c = 0; c < NCU; ++c) um[c] = TRm[((e * NF + f) * NCU + c) * NFQ + k];
+      if (nb >= 0) {
+        const int kp = a.perm[(a.nbf[(size_t)(e0 + e) * NF + f] >> 3) * NFQ + k];
+        S up[NCU], qp[1];
+        for (int c = 0; c < NCU; ++c) up[c] = S(TRp[((e * NF + f) * NCU + c) * NFQ + kp]);
+        MD::fhat(um, up, qm, qp, nrm, fh, MPs[e]);
+      } else {
+        R gb[4] = {R(0), R(0), R(0), R(0)};
+        R xi[3];
+        double x[3], gd[4] = {0.0, 0.0, 0.0, 0.0};
+        face_xi<EL>(OPS, f, k, xi);
+        phys_x<DIM>(g, xi, x);
+        exact_state<DIM>(elem_mp(a, e0 + e), NCU, x, a.t_dev ? *a.t_dev : a.t, gd);
+        for (int c = 0; c < 4; ++c) gb[c] = R(gd[c]);
+        MD::fhat_bnd(um, qm, gb, nrm, fh, MPs[e]);
+      }
+      for (int c = 0; c < NCU; ++c)
+#pragma unroll
+        for (int t = 0; t < KT; ++t) FH[((e * NF + f) * NCO + c * KT + t) * NFQ + k] = fh[c].d[t] * w;
+    }
+    __syncthreads();
+    face_lift<EL>(FH, LF, (R*)TMP, OPS, NE * NF * NCO);
+    __syncthreads();
+  }
+
+  // ----------------------------------------------------------- volume phase
+  S* XQ = (S*)arena;                                                   // [NE][NCU][NQV]
+  S* T1 = (S*)(arena + NE * L::B_XQ);
+  R* GK = (R*)(arena + NE * 2 * L::B_XQ);                              // [DIM+1][NE][NCO][NQV]
+  R* R1 = GK + (DIM + 1) * NE * (L::B_G / sizeof(R));
+  R* R2 = R1 + NE * (L::B_G / sizeof(R));
+  R* RV = R2 + NE * (L::B_G / sizeof(R));                              // [NE][NCO][NPE]
+  vol_interp<EL>(X, XQ, T1, OPS, NE * NCU);
+  __syncthreads();
+  const R a0dt = R(a.a0dt);
+  for (int it = threadIdx.x; it < NE * NQV; it += blockDim.x) {
+    const int qp = it % NQV, e = it / NQV;
+    S uq[NCU], qq[1], f[NCU * DIM];
+    for (int c = 0; c < NCU; ++c) uq[c] = XQ[(e * NCU + c) * NQV + qp];
+    R xi[3], w;
+    vol_xi<EL>(OPS, qp, xi, w);
+    const R* g = Gs + e * GEO;
+    const R wj = w * g[Geo<DIM>::DETJ];
+    MD::flux(uq, qq, f, MPs[e]);
+    for (int c = 0; c < NCU; ++c)
+#pragma unroll
+      for (int t = 0; t < KT; ++t) {
+        const int co = c * KT + t;
+        for (int k = 0; k < DIM; ++k) {
+          R sk = R(0);
+          for (int d = 0; d < DIM; ++d) sk += f[c * DIM + d].d[t] * g[Geo<DIM>::JINV + k * DIM + d];
+          GK[((k + 1) * NE * NCO + e * NCO + co) * NQV + qp] = (e < ne) ? -sk * wj : R(0);
+        }
+        GK[(e * NCO + co) * NQV + qp] = (e < ne) ? uq[c].d[t] * a0dt * wj : R(0);
+      }
+  }
+  __syncthreads();
+  vol_integrate<EL, false>(DIM, GK, RV, R1, R2, OPS, NE * NCO);
+  __syncthreads();
+  for (int k = 0; k < DIM; ++k) {
+    vol_integrate<EL, true>(k, GK + (k + 1) * NE * NCO * NQV, RV, R1, R2, OPS, NE * NCO);
+    __syncthreads();
+  }
+  // ---- gather face moments and store columns col0 + t of the blocks
+  for (int it = threadIdx.x; it < ne * NCO * NPE; it += blockDim.x) {
+    const int n = it % NPE, co = (it / NPE) % NCO, e = it / (NPE * NCO);
+    const int c = co / KT, t = co - c * KT;
+    if (col0 + t >= NLOC) continue;
+    R sacc = RV[it];
+    for_node_faces<EL>(n, [&](int f, int j) { sacc += LF[((e * NF + f) * NCO + co) * NFN + j]; });
+    a.blk_out[((size_t)(e0 + e) * NLOC + col0 + t) * NLOC + c * NPE + n] = (double)sacc;
+  }
+}
+
 }  // namespace ldg

@@ -13,6 +13,9 @@ long long& launch_counter();
 inline void count_launch() { ++launch_counter(); }
 
 typedef cudaError_t (*StageFn)(int mode, const KArgs& a, cudaStream_t s);
+// columns col0 .. col0 + BLK_KT - 1 of the element-diagonal blocks (models without q)
+typedef cudaError_t (*BlockFn)(int col0, const KArgs& a, cudaStream_t s);
+constexpr int BLK_KT = 8;
 
 struct KernelSet {
   int etype, p, nq, model;
@@ -21,8 +24,22 @@ struct KernelSet {
   StageFn residual;   // FP64 compute. MODE_R / MODE_HOM (linear models) / MODE_JV (nonlinear models)
   StageFn qstage32;   // FP32 compute, MODE_HOM (diffusion models); null otherwise
   StageFn residual32; // FP32 compute, MODE_HOM (linear) / MODE_JV (nonlinear): the Krylov J.v
+  BlockFn blocks;     // (unused: FP64 blocks take one tangent per launch)
+  BlockFn blocks32;   // FP32 block columns by BLK_KT-tangent dual numbers (models without q)
   int ne_q, ne_r, ne_j, smem_q, smem_r, smem_j;
 };
+
+template <class EL, class MD, class R, class TL> cudaError_t launch_blk(int col0, const KArgs& a, cudaStream_t s) {
+  typedef BLayout<EL, MD, R, TL, BLK_KT> L;
+  static const cudaError_t attr = cudaFuncSetAttribute(k_block_columns<EL, MD, R, TL, BLK_KT>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+  if (attr != cudaSuccess) return attr;
+  if (a.E <= 0) return cudaSuccess;
+  int grid = (a.E + L::NE - 1) / L::NE;
+  k_block_columns<EL, MD, R, TL, BLK_KT><<<grid, 256, L::SMEM, s>>>(a, col0);
+  count_launch();
+  return cudaGetLastError();
+}
 
 template <class EL, class MD, int MODE, class R, class TL> cudaError_t launch_res1(const KArgs& a, cudaStream_t s) {
   typedef RLayout<EL, MD, MODE, R, TL> L;
@@ -96,9 +113,13 @@ template <class EL, class MD, class TL = Tile0> void add_set(std::vector<KernelS
     k.smem_q = QLayout<EL, MD, double, TL>::SMEM;
     k.ne_j = RLayout<EL, MD, MODE_HOM, double, TL>::NE;
     k.smem_j = RLayout<EL, MD, MODE_HOM, double, TL>::SMEM;
+    k.blocks = nullptr;
+    k.blocks32 = nullptr;
   } else {
     k.qstage = nullptr;
     k.qstage32 = nullptr;
+    k.blocks = nullptr;
+    k.blocks32 = &launch_blk<EL, MD, float, TL>;
     k.ne_q = 0; k.smem_q = 0;
     k.ne_j = RLayout<EL, MD, MODE_JV, double, TL>::NE;
     k.smem_j = RLayout<EL, MD, MODE_JV, double, TL>::SMEM;

@@ -176,7 +176,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   }
   __syncthreads();
   if (ok_s) {
-    if (!mbar_wait(&bar_mma, 0)) {
+    // every lane of a warp takes the same branch (tcgen05.ld is warp-collective)
+    const bool mma_done = __all_sync(0xffffffffu, mbar_wait(&bar_mma, 0));
+    if (!mma_done) {
       atomicExch(g.err, 1);
     } else {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

@@ -85,3 +85,15 @@ def test_block_jacobi_c1_poisson():
     assert rep["rfinal"] <= 1e-9 * rep["r0"]
     uo, rc, st = o.newton(np.zeros(o.ndof), m=200, newton_rtol=1e-10, gmres_rtol=1e-12, max_newton=2)
     assert np.linalg.norm(host(u) - uo) <= 1e-8 * np.linalg.norm(uo)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_diag_blocks_fp32_match_fp64(p):
+    """The FP32 block columns (eight tangents per launch) against the FP64 ones."""
+    mesh = synth.quad_box((4, 5), hi=(10.0, 10.0), periodic=(True, True))
+    o, g = pair(mesh, p, oracle.EULER, oracle.CASE_VORTEX)
+    u = synth.random_euler_state(mesh.n_elem, o.npe, 11)
+    g.set_time(2, 0.1, 0.05, cuda(u), cuda(u))
+    b64 = host(g.diag_blocks(cuda(u), precision=0))
+    b32 = host(g.diag_blocks(cuda(u), precision=1))
+    assert np.linalg.norm(b32 - b64) <= 2e-6 * np.linalg.norm(b64)
