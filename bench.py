@@ -300,14 +300,14 @@ def run_batch(args):
         u = b.empty()
         for _ in range(warmup):
             u.zero_()
-            b.solve(u, use_graph=use_graph)
+            b.solve(u, use_graph=use_graph and not args.host_loops)
         times, reps = [], None
         for _ in range(steps):
             u.zero_()
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            reps, _ = b.solve(u, use_graph=use_graph)
+            reps, _ = b.solve(u, use_graph=use_graph and not args.host_loops)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -381,7 +381,7 @@ def run_batch(args):
     for _ in range(k2):
         h_u.zero_()
         d_u.copy_(h_u, non_blocking=True)
-        r_e, _ = b.solve(d_u)
+        r_e, _ = b.solve(d_u, use_graph=not args.host_loops)
         h_u.copy_(d_u)
         jv_e2e += sum(b.n_dof[i] * r_e[i]["jv_calls"] for i in range(b.n_inst))
     t_e2e = time.perf_counter() - t0
@@ -434,6 +434,84 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+HEX_WORKLOAD = ("3D steady convection-diffusion on [0,1]^3, 48^3 affine hexahedra, beta = (1, 0.5, 0.25), "
+                "kappa = 1e-2, manufactured u = exp(x+y+z) sin(pi xyz); J.v throughput sweep p = 1..6 in FP64 and "
+                "FP32 arithmetic (FP64 storage)")
+# Algorithmic HBM bytes per DOF of the 3-D linear J.v: v read twice (8 + 8), q(v) written
+# and read (2 x 24), J.v written (8).
+HEX_JV_BYTES_PER_DOF = 72.0
+
+
+def run_hex(args):
+    """J.v throughput of the 3-D convection-diffusion operator, p = 1..6 (p = 4 is the headline)."""
+    import torch
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, CONVDIFF, CASE_EXPSIN, kernel_launches
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    mesh = synth.hex_box(48)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    sweep = []
+    head = None
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = kernel_launches()
+    for p in range(1, 7):
+        row = {"p": p}
+        for prec in (0, 1):
+            g = LDG(mesh, p, CONVDIFF, CASE_EXPSIN, (1e-2, 1.0, 1.0, 0.5, 0.25), krylov_precision=prec)
+            tile, _ = g.autotune()
+            u = g.interpolate(0.0)
+            v = torch.randn(g.n_dof, dtype=torch.float64, device="cuda",
+                            generator=torch.Generator("cuda").manual_seed(p))
+            out = torch.empty_like(v)
+            for _ in range(args.warmup):
+                g.jvp_prec(prec, u, v, out)
+            times = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.jvp_prec(prec, u, v, out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = sorted(times)[len(times) // 2]
+            key = "fp64" if prec == 0 else "fp32"
+            row[key] = {"ms": ms, "gdofs": g.n_dof / (ms * 1e-3) / 1e9, "tile": tile,
+                        "hbm_frac": HEX_JV_BYTES_PER_DOF * g.n_dof / (ms * 1e-3) / 1e9 / hbm}
+            row["n_dof"] = g.n_dof
+            if p == 4 and prec == 1:
+                head = (g.n_dof, ms, tile)
+            del g, u, v, out
+            torch.cuda.empty_cache()
+        sweep.append(row)
+    launches = kernel_launches() - l0
+    clk = clocks.stop()
+    n, ms, tile = head
+    achieved = HEX_JV_BYTES_PER_DOF * n / (ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": n / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": HEX_WORKLOAD, "n_dof_p4": n, "step": "one J.v application (median of the timed ones)",
+                       "headline": "p = 4, FP32 arithmetic", "sweep": sweep,
+                       "l2": "flushed (256 MiB write) before each timed J.v"},
+            "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": hbm, "frac": achieved / hbm,
+                         "traffic": None, "bytes_per_dof": HEX_JV_BYTES_PER_DOF,
+                         "kernel": "k_qstage + k_residual (MODE_HOM, float), hex p = 4",
+                         "peak_source": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,15 +527,23 @@ def main():
                          "mlp: the learned per-element preconditioner trained on the warm-up steps")
     ap.add_argument("--krylov", default="fp32", choices=["fp64", "fp32"],
                     help="arithmetic of the J.v inside GMRES (Newton residual and Arnoldi stay FP64)")
-    ap.add_argument("--workload", default="vortex", choices=["vortex", "batch"],
+    ap.add_argument("--host-loops", action="store_true",
+                    help="run the solver's Newton / restart / Arnoldi loops from the host instead of the CUDA "
+                         "graph's WHILE nodes (same kernels; for profilers that do not follow graph nodes)")
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "batch", "hex"],
                     help="vortex: the 64x64 p=3 Euler BDF2 step; batch: 256 parametrised convection-diffusion "
-                         "solves in one graph launch")
+                         "solves in one graph launch; hex: the 48^3 convection-diffusion J.v sweep p=1..6")
     args = ap.parse_args()
+    if args.host_loops:
+        os.environ["LDG_SOLVER_HOST_LOOPS"] = "1"
     if args.impl == "reference":
         run_reference(args)
         return
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "hex":
+        run_hex(args)
         return
 
     import numpy as np

@@ -227,7 +227,10 @@ int ldg_gmres(ldg_ctx* ctx, const double* u_dev, const double* b_dev, double* x_
 
 /* Newton-GMRES (Section 3.3): u <- u - delta with J(u) delta = R(u), until
  * ||R(u)|| <= newton_rtol ||R(u_0)||. u_dev is the initial guess on entry and the
- * solution on return. */
+ * solution on return. Without the learned preconditioner (and with pc_refresh = 0)
+ * the solve runs as the batched solver's single instance: one CUDA graph launch
+ * (see ldg_batch_solve); the environment variable LDG_SOLVER_HOST_LOOPS=1 runs the
+ * same kernels from host-driven loops instead (for profilers). */
 int ldg_newton_gmres(ldg_ctx* ctx, double* u_dev, ldg_solve_report* rep);
 
 /* The same solve with u in HOST memory: copied to the device, solved, copied back. */

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -744,7 +745,10 @@ int batch_solve_one(ldg_batch* b, double* u, ldg_solve_report* rep) {
   b->stream = b->groups[0].ctx->stream;
   ldg_solve_report r{};
   double ms = 0.0;
-  const int rc = ldg_batch_solve(b, u, 1, &r, &ms);
+  // LDG_SOLVER_HOST_LOOPS=1: the same kernels driven by host loops instead of the
+  // graph's WHILE nodes (profilers that do not follow conditional graph nodes)
+  const char* host = getenv("LDG_SOLVER_HOST_LOOPS");
+  const int rc = ldg_batch_solve(b, u, (host && host[0] == '1') ? 0 : 1, &r, &ms);
   if (rep) {
     *rep = r;
     rep->elapsed_ms = ms;
