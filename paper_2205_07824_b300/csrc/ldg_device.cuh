@@ -400,27 +400,68 @@ template <int P_, int NQ_> struct TriEl {
 // ---------------------------------------------------------- contractions
 // out[b][o] = sum_i M(o, i) in[b][i] along axis AX of a tensor of extents E0 x E1 x E2
 // (first fastest), with M(o, i) = Mat[o * NI + i] or, if TRANS, Mat[i * MOUT + o].
-// Every output is owned by one thread, so ACC (+=) is race-free.
+// Every output (line) is owned by one thread, so ACC (+=) is race-free. Both forms sum
+// over i in the same order, so they give the same bits.
 template <int AX, int E0, int E1, int E2, int MOUT, bool TRANS, bool ACC, class T, class TM>
 __device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict__ out,
                                          const TM* __restrict__ Mat, int nbatch) {
   constexpr int O0 = AX == 0 ? MOUT : E0, O1 = AX == 1 ? MOUT : E1, O2 = AX == 2 ? MOUT : E2;
   constexpr int OSZ = O0 * O1 * O2, ISZ = E0 * E1 * E2;
   constexpr int NI = AX == 0 ? E0 : (AX == 1 ? E1 : E2);
-  constexpr int STR = AX == 0 ? 1 : (AX == 1 ? E0 : E0 * E1);
-  const int total = nbatch * OSZ;
-  for (int it = threadIdx.x; it < total; it += blockDim.x) {
-    int b = it / OSZ, r = it - b * OSZ;
-    int o0 = r % O0, o1 = (r / O0) % O1, o2 = r / (O0 * O1);
-    int oa = AX == 0 ? o0 : (AX == 1 ? o1 : o2);
-    const T* src = in + b * ISZ + (AX == 0 ? o1 * E0 + o2 * E0 * E1 : (AX == 1 ? o0 + o2 * E0 * E1 : o0 + o1 * E0));
-    T acc = ACC ? out[it] : T(0);
+  constexpr int STR = AX == 0 ? 1 : (AX == 1 ? E0 : E0 * E1);       // input stride along AX
+  constexpr int OSTR = AX == 0 ? 1 : (AX == 1 ? O0 : O0 * O1);      // output stride along AX
+  if constexpr (sizeof(TM) == 8 && MOUT * NI > 16) {
+    // FP64 operators beyond 4 x 4: one thread per output point (the line form's
+    // register-held operator measured slower here)
+    const int total = nbatch * OSZ;
+    for (int it = threadIdx.x; it < total; it += blockDim.x) {
+      const int b = it / OSZ, r = it - b * OSZ;
+      const int o0 = r % O0, o1 = (r / O0) % O1, o2 = r / (O0 * O1);
+      const int oa = AX == 0 ? o0 : (AX == 1 ? o1 : o2);
+      const T* src = in + b * ISZ + (AX == 0 ? o1 * E0 + o2 * E0 * E1 : (AX == 1 ? o0 + o2 * E0 * E1 : o0 + o1 * E0));
+      T acc = ACC ? out[it] : T(0);
 #pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      TM m = TRANS ? Mat[i * MOUT + oa] : Mat[oa * NI + i];
-      acc += src[i * STR] * m;
+      for (int i = 0; i < NI; ++i) acc += src[i * STR] * (TRANS ? Mat[i * MOUT + oa] : Mat[oa * NI + i]);
+      out[it] = acc;
     }
-    out[it] = acc;
+    return;
+  }
+  // one thread per line along AX: the line's NI inputs are loaded once, the MOUT x NI
+  // operator is held in registers, and all MOUT outputs of the line are produced
+  constexpr int LPB = ISZ / NI;                                      // lines per batch item
+  TM m[MOUT][NI];
+#pragma unroll
+  for (int o = 0; o < MOUT; ++o)
+#pragma unroll
+    for (int i = 0; i < NI; ++i) m[o][i] = TRANS ? Mat[i * MOUT + o] : Mat[o * NI + i];
+  const int total = nbatch * LPB;
+  for (int it = threadIdx.x; it < total; it += blockDim.x) {
+    const int b = it / LPB, r = it - b * LPB;
+    // r enumerates the line's indices along the two other axes, the fastest first
+    int ioff, ooff;
+    if constexpr (AX == 0) {          // r = i1 + E1 i2
+      ioff = r * E0;
+      ooff = r * O0;
+    } else if constexpr (AX == 1) {   // r = i0 + E0 i2
+      const int i0 = r % E0, i2 = r / E0;
+      ioff = i0 + i2 * E0 * E1;
+      ooff = i0 + i2 * O0 * O1;
+    } else {                          // r = i0 + E0 i1
+      ioff = r;
+      ooff = r;
+    }
+    const T* src = in + b * ISZ + ioff;
+    T* dst = out + b * OSZ + ooff;
+    T x[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) x[i] = src[i * STR];
+#pragma unroll
+    for (int o = 0; o < MOUT; ++o) {
+      T acc = ACC ? dst[o * OSTR] : T(0);
+#pragma unroll
+      for (int i = 0; i < NI; ++i) acc += x[i] * m[o][i];
+      dst[o * OSTR] = acc;
+    }
   }
 }
 
