@@ -338,10 +338,11 @@ int do_pc_setup(ldg_ctx* ctx, const double* u) {
   auto fixed = [&](auto tag, auto nconst) -> int {
     typedef decltype(tag) T;
     constexpr int NN = decltype(nconst)::value;
-    const size_t smem = block_inverse_smem<T>(NN);
-    CK(cudaFuncSetAttribute(k_block_inverse_n<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_block_inverse_n<T, NN><<<(unsigned)ctx->E, 256, smem, ctx->stream>>>(ctx->d_blocks, (T*)ctx->d_binv,
-                                                                           ctx->d_status);
+    constexpr int NT = 256;   // 64 threads per block (168 registers each) measured slower
+    const size_t smem = BInvN<T, NN, NT>::SMEM;
+    CK(cudaFuncSetAttribute(k_block_inverse_n<T, NN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_block_inverse_n<T, NN, NT><<<(unsigned)ctx->E, NT, smem, ctx->stream>>>(ctx->d_blocks, (T*)ctx->d_binv,
+                                                                               ctx->d_status);
     count_launch();
     CK(cudaGetLastError());
     ctx->pc_ready = true;

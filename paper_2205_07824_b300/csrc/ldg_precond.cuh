@@ -98,42 +98,67 @@ __global__ void k_block_inverse(const double* __restrict__ blocks, T* __restrict
   }
 }
 
-template <class T> struct Vec4;
-template <> struct Vec4<float> { typedef float4 type; };
-template <> struct Vec4<double> { typedef double4 type; };
-
 // The same Gauss-Jordan inversion for a compile-time block size N (a multiple of 4,
-// N <= 128, 256 threads): the elimination gives each thread 4 adjacent columns (one
-// 16- or 32-byte shared-memory access per row) in N / (256 / (N/4)) rows, all loops
-// unrolled, so the update issues about two instructions per FMA instead of ten.
-template <class T, int N>
-__global__ void __launch_bounds__(256) k_block_inverse_n(const double* __restrict__ blocks, T* __restrict__ inv,
-                                                         int* status) {
-  static_assert(N % 4 == 0 && N <= 128, "block size");
-  typedef typename Vec4<T>::type V4;
-  constexpr int CG = N / 4;                       // column groups of 4
-  constexpr int NG = (256 / CG) < N ? (256 / CG) : N;   // row groups
-  constexpr int RPT = (N + NG - 1) / NG;          // rows per thread
+// N <= 128, NT threads) with the matrix held in registers: thread t owns columns
+// 4 (t mod N/4) .. +3 in rows rg, rg + NG, ... (rg = t div N/4, NG row groups), so the
+// elimination reads only the pivot column, the scaled pivot row and the old row k from
+// shared memory (double-buffered by the parity of k, three barriers per step). The
+// block is staged through a padded [N][N+1] shared tile on the way in and out, where
+// the row interchanges are undone as one column permutation.
+template <class T, int N, int NT> struct BInvN {
+  static constexpr int CG = N / 4;                               // column groups of 4
+  static constexpr int NG = (NT / CG) < N ? (NT / CG) : N;       // row groups
+  static constexpr int RPT = (N + NG - 1) / NG;                  // rows per thread
+  static constexpr size_t SMEM = (size_t)N * (N + 1) * sizeof(T) + 6 * N * sizeof(T) + N * sizeof(int) + 64;
+};
+
+template <class T, int N, int NT>
+__global__ void __launch_bounds__(NT) k_block_inverse_n(const double* __restrict__ blocks, T* __restrict__ inv,
+                                                        int* status) {
+  static_assert(N % 4 == 0 && N <= 128 && NT % 32 == 0 && NT / (N / 4) >= 1, "block size");
+  typedef BInvN<T, N, NT> L;
+  constexpr int CG = L::CG, NG = L::NG, RPT = L::RPT, LD = N + 1;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* A = (T*)sm_raw;             // [N][N] row-major
-  T* fac = A + N * N;            // [N]
-  int* ipiv = (int*)(fac + N);   // [N]
+  T* S = (T*)sm_raw;                   // [N][N+1] staging tile
+  T* colbuf = S + N * LD;              // [2][N] pivot column of step k
+  T* prow = colbuf + 2 * N;            // [2][N] scaled pivot row
+  T* rowk = prow + 2 * N;              // [2][N] old row k
+  int* srcc = (int*)(rowk + 2 * N);    // [N] final column permutation
   __shared__ int piv;
   const int e = blockIdx.x;
   const double* B = blocks + (size_t)e * N * N;   // column-major
-  for (int idx = threadIdx.x; idx < N * N; idx += 256) {
+  for (int idx = threadIdx.x; idx < N * N; idx += NT) {
     const int col = idx / N, row = idx - col * N;
-    A[row * N + col] = (T)B[idx];
+    S[row * LD + col] = (T)B[idx];
   }
   const int cg = threadIdx.x % CG, rg = threadIdx.x / CG;
-  const bool elim = rg < NG;
+  const bool act = rg < NG;
   __syncthreads();
+  T a[RPT][4];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int i = rg + NG * r;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a[r][c] = (act && i < N) ? S[i * LD + 4 * cg + c] : T(0);
+  }
   for (int k = 0; k < N; ++k) {
+    const int par = (k & 1) * N;
+    const int kq = k >> 2, kc = k & 3;
+    // (1) the owners of column k publish it
+    if (act && cg == kq) {
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int i = rg + NG * r;
+        if (i < N) colbuf[par + i] = kc == 0 ? a[r][0] : kc == 1 ? a[r][1] : kc == 2 ? a[r][2] : a[r][3];
+      }
+    }
+    __syncthreads();
+    // (2) pivot row: largest |A(i, k)|, i >= k (ties to the smaller index)
     if (threadIdx.x < 32) {
       T best = T(-1);
       int bi = k;
       for (int i = k + threadIdx.x; i < N; i += 32) {
-        const T v = fabs(A[i * N + k]);
+        const T v = fabs(colbuf[par + i]);
         if (v > best) { best = v; bi = i; }
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -141,60 +166,81 @@ __global__ void __launch_bounds__(256) k_block_inverse_n(const double* __restric
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (threadIdx.x == 0) { piv = bi; ipiv[k] = bi; }
+      if (threadIdx.x == 0) { piv = bi; srcc[k] = bi; }
     }
     __syncthreads();
     const int p = piv;
-    if (p != k && threadIdx.x < N) {
-      const T t = A[k * N + threadIdx.x];
-      A[k * N + threadIdx.x] = A[p * N + threadIdx.x];
-      A[p * N + threadIdx.x] = t;
-    }
-    __syncthreads();
-    const T pv = A[k * N + k];
+    const T pv = colbuf[par + p];
     if (pv == T(0) && threadIdx.x == 0) *status = 1;
     const T ip = pv != T(0) ? T(1) / pv : T(0);
-    if (threadIdx.x < N) fac[threadIdx.x] = ((int)threadIdx.x == k) ? T(0) : A[threadIdx.x * N + k];
-    __syncthreads();
-    if (threadIdx.x < N) A[k * N + threadIdx.x] = ((int)threadIdx.x == k ? T(1) : A[k * N + threadIdx.x]) * ip;
-    __syncthreads();
-    if (elim) {
-      const V4 pk = reinterpret_cast<const V4*>(A + k * N)[cg];
-      const int kc = k - 4 * cg;                  // column k's position in this group, if 0..3
+    // (3) the owners of row p publish it scaled, the owners of row k publish the old row k
+    if (act) {
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
         const int i = rg + NG * r;
-        if (i >= N || i == k) continue;
-        V4* ap = reinterpret_cast<V4*>(A + i * N) + cg;
-        V4 a = *ap;
-        if (kc == 0) a.x = T(0);
-        if (kc == 1) a.y = T(0);
-        if (kc == 2) a.z = T(0);
-        if (kc == 3) a.w = T(0);
-        const T f = fac[i];
-        a.x -= f * pk.x;
-        a.y -= f * pk.y;
-        a.z -= f * pk.z;
-        a.w -= f * pk.w;
-        *ap = a;
+        if (i == p)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) prow[par + 4 * cg + c] = (4 * cg + c == k ? T(1) : a[r][c]) * ip;
+        if (i == k)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) rowk[par + 4 * cg + c] = a[r][c];
       }
     }
     __syncthreads();
-  }
-  T* Iv = inv + (size_t)e * N * N;
-  for (int row = threadIdx.x; row < N; row += 256)
-    for (int k = N - 1; k >= 0; --k) {
-      const int p = ipiv[k];
-      if (p != k) {
-        const T t = A[row * N + k];
-        A[row * N + k] = A[row * N + p];
-        A[row * N + p] = t;
+    // (4) elimination in registers; the interchange of rows k and p is part of it
+    if (act) {
+      T pk[4], ok[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        pk[c] = prow[par + 4 * cg + c];
+        ok[c] = rowk[par + 4 * cg + c];
+      }
+      const T fk = colbuf[par + k];                    // old A(k, k): multiplier of the new row p
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int i = rg + NG * r;
+        if (i >= N) continue;
+        if (i == k) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) a[r][c] = pk[c];
+          continue;
+        }
+        const bool isp = (i == p);
+        const T f = isp ? fk : colbuf[par + i];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const T src = isp ? ok[c] : a[r][c];
+          a[r][c] = (4 * cg + c == k ? T(0) : src) - f * pk[c];
+        }
       }
     }
+  }
+  // undo the row interchanges as column interchanges (last first): column c of the
+  // inverse is column srcc[c] of the eliminated matrix
   __syncthreads();
-  for (int idx = threadIdx.x; idx < N * N; idx += 256) {
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int i = rg + NG * r;
+    if (act && i < N)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) S[i * LD + 4 * cg + c] = a[r][c];
+  }
+  if (threadIdx.x == 0) {
+    int perm[N];
+    for (int c = 0; c < N; ++c) perm[c] = c;
+    for (int k = N - 1; k >= 0; --k) {
+      const int q = srcc[k];
+      const int t = perm[k];
+      perm[k] = perm[q];
+      perm[q] = t;
+    }
+    for (int c = 0; c < N; ++c) srcc[c] = perm[c];
+  }
+  __syncthreads();
+  T* Iv = inv + (size_t)e * N * N;
+  for (int idx = threadIdx.x; idx < N * N; idx += NT) {
     const int col = idx / N, row = idx - col * N;
-    Iv[idx] = A[row * N + col];
+    Iv[idx] = S[row * LD + srcc[col]];
   }
 }
 
