@@ -16,8 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ldg_oracle.cpp")
 _LIB = os.path.join(_HERE, "libldg_oracle.so")
 
-POISSON, CONVDIFF, EULER = 0, 1, 2
-CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST = range(7)
+POISSON, CONVDIFF, EULER, NS = 0, 1, 2, 3
+CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST, CASE_ROTATION = range(8)
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.POINTER(ctypes.c_int64)
@@ -87,7 +87,7 @@ class Oracle:
 
     def __init__(self, mesh, p: int, model: int, case: int, mu=(), nq1: int | None = None):
         if nq1 is None:
-            nq1 = p + 2 if (model == EULER or mesh.etype == 0) else p + 1
+            nq1 = p + 2 if (model in (EULER, NS) or mesh.etype == 0) else p + 1
         self.mesh, self.p, self.nq1, self.model, self.case = mesh, p, nq1, model, case
         xyz = _c(mesh.xyz)
         vid = _c(mesh.vid, np.int64)

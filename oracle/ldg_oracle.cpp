@@ -24,6 +24,13 @@
 //   Dirichlet faces: uhat = g; fhat.n = beta.n u_up + kappa q-.n + tau (u- - g),
 //     u_up = u- when beta.n >= 0 else g. Euler far field: Rusanov against the
 //     exact state.
+//   Navier-Stokes (2-D, conservative u = (rho, rho v, rho E), q = -grad u):
+//     f = F(u) - Fv(u, grad u) with the Euler flux F, the Newtonian stress
+//     tau_ij = mu (d_j v_i + d_i v_j) - 2/3 mu (div v) delta_ij, mu = 1/Re, and the
+//     energy flux v.tau + (mu gamma / Pr) grad e (e = E - |v|^2 / 2, the internal
+//     energy per unit mass); velocity and energy gradients follow from grad u by the
+//     chain rule. Interior: Rusanov on F, central on Fv, penalty tau (u- - u+),
+//     tau = 1/Re; far field: the same against the exact state, with Fv(u-, q-).
 //   Non-differentiable points: d|x| at 0 is 0; max(a,b) with a == b is a.
 //
 // The residual is templated on the scalar type: double (R), Dual (exact
@@ -322,17 +329,17 @@ struct Ref {
 };
 
 // ------------------------------------------------------------------ models
-enum { POISSON = 0, CONVDIFF = 1, EULER = 2 };
+enum { POISSON = 0, CONVDIFF = 1, EULER = 2, NS = 3 };
 enum { CASE_ZERO = 0, CASE_SINSIN = 1, CASE_EXPSIN = 2, CASE_POLY2 = 3, CASE_LINEAR = 4,
-       CASE_VORTEX = 5, CASE_CONST = 6 };
+       CASE_VORTEX = 5, CASE_CONST = 6, CASE_ROTATION = 7 };
 
 struct Model {
   int kind, cas, nd, ncu;
-  double kappa = 1, tau = 1, beta[3] = {0, 0, 0}, gamma = 1.4;
+  double kappa = 1, tau = 1, beta[3] = {0, 0, 0}, gamma = 1.4, pr = 0.72;   // NS: kappa = mu = 1/Re
 
   // exact solution u(x, t) for the manufactured / analytic cases
   void exact(const double* x, double t, double* u) const {
-    if (kind == EULER) {
+    if (kind == EULER || kind == NS) {
       if (cas == CASE_VORTEX) {
         // isentropic vortex: strength 5, centre (5,5), free stream rho = p = 1,
         // velocity (1,1), convected on the periodic square [0,10]^2.
@@ -349,6 +356,11 @@ struct Model {
         double pr = std::pow(rho, gamma);
         u[0] = rho; u[1] = rho * vx; u[2] = rho * vy;
         u[3] = pr / (gamma - 1) + 0.5 * rho * (vx * vx + vy * vy);
+      } else if (cas == CASE_ROTATION) {
+        // rigid rotation v = 0.5 (-y, x) with density 1 + 0.1 x + 0.05 y and uniform
+        // internal energy e = 2: a cubic state with zero strain rate and zero grad e
+        const double rho = 1.0 + 0.1 * x[0] + 0.05 * x[1], vx = -0.5 * x[1], vy = 0.5 * x[0];
+        u[0] = rho; u[1] = rho * vx; u[2] = rho * vy; u[3] = rho * (2.0 + 0.5 * (vx * vx + vy * vy));
       } else {
         u[0] = 1; u[1] = 1; u[2] = 1; u[3] = 1.0 / (gamma - 1) + 1.0;
       }
@@ -414,7 +426,7 @@ struct Model {
   }
   // source s(x) of Eq. 1b for the manufactured scalar cases: div f = s
   void source(const double* x, double* s) const {
-    if (kind == EULER) { for (int c = 0; c < ncu; ++c) s[c] = 0; return; }
+    if (kind == EULER || kind == NS) { for (int c = 0; c < ncu; ++c) s[c] = 0; return; }
     double u, g[3], L;
     scalar_exact(x, u, g, &L);
     double bg = 0;
@@ -422,15 +434,50 @@ struct Model {
     s[0] = bg - kappa * L;
   }
 
-  // physical flux f[c*nd + d](u, q): f = beta u + kappa q (q = -grad u), or Euler
+  // Euler flux F[c*2 + d](u)
+  template <class S> void euler_flux(const S* u, S* f) const {
+    S rho = u[0], vx = u[1] / rho, vy = u[2] / rho;
+    S p = (gamma - 1) * (u[3] - 0.5 * (u[1] * vx + u[2] * vy));
+    f[0] = u[1];          f[1] = u[2];
+    f[2] = u[1] * vx + p; f[3] = u[1] * vy;
+    f[4] = u[2] * vx;      f[5] = u[2] * vy + p;
+    f[6] = (u[3] + p) * vx; f[7] = (u[3] + p) * vy;
+  }
+
+  // Navier-Stokes viscous flux Fv[c*2 + d](u, grad u) with grad u = -q
+  template <class S> void viscous_flux(const S* u, const S* q, S* fv) const {
+    const double mu = kappa;
+    S rho = u[0], vx = u[1] / rho, vy = u[2] / rho, E = u[3] / rho;
+    S g[4][2];
+    for (int c = 0; c < 4; ++c)
+      for (int d = 0; d < 2; ++d) g[c][d] = -q[c * 2 + d];
+    // d v_i / d x_d = (d m_i / d x_d - v_i d rho / d x_d) / rho
+    S vxx = (g[1][0] - vx * g[0][0]) / rho, vxy = (g[1][1] - vx * g[0][1]) / rho;
+    S vyx = (g[2][0] - vy * g[0][0]) / rho, vyy = (g[2][1] - vy * g[0][1]) / rho;
+    S dv = vxx + vyy;
+    S txx = mu * (2.0 * vxx - (2.0 / 3.0) * dv);
+    S tyy = mu * (2.0 * vyy - (2.0 / 3.0) * dv);
+    S txy = mu * (vxy + vyx);
+    // d e / d x_d = (d(rho E)/d x_d - E d rho / d x_d) / rho - v . d v / d x_d
+    S ex = (g[3][0] - E * g[0][0]) / rho - (vx * vxx + vy * vyx);
+    S ey = (g[3][1] - E * g[0][1]) / rho - (vx * vxy + vy * vyy);
+    const double kt = mu * gamma / pr;
+    fv[0] = 0.0; fv[1] = 0.0;
+    fv[2] = txx; fv[3] = txy;
+    fv[4] = txy; fv[5] = tyy;
+    fv[6] = vx * txx + vy * txy + kt * ex;
+    fv[7] = vx * txy + vy * tyy + kt * ey;
+  }
+
+  // physical flux f[c*nd + d](u, q): f = beta u + kappa q (q = -grad u), Euler, or
+  // Navier-Stokes F(u) - Fv(u, grad u)
   template <class S> void flux(const S* u, const S* q, S* f) const {
-    if (kind == EULER) {
-      S rho = u[0], vx = u[1] / rho, vy = u[2] / rho;
-      S pr = (gamma - 1) * (u[3] - 0.5 * (u[1] * vx + u[2] * vy));
-      f[0] = u[1];          f[1] = u[2];
-      f[2] = u[1] * vx + pr; f[3] = u[1] * vy;
-      f[4] = u[2] * vx;      f[5] = u[2] * vy + pr;
-      f[6] = (u[3] + pr) * vx; f[7] = (u[3] + pr) * vy;
+    if (kind == EULER) { euler_flux(u, f); return; }
+    if (kind == NS) {
+      S fv[8];
+      euler_flux(u, f);
+      viscous_flux(u, q, fv);
+      for (int i = 0; i < 8; ++i) f[i] = f[i] - fv[i];
       return;
     }
     for (int d = 0; d < nd; ++d) f[d] = kappa * q[d] + (kind == CONVDIFF ? beta[d] * u[0] : S(0.0));
@@ -446,13 +493,20 @@ struct Model {
 
   template <class S> void fhat_interior(const S* um, const S* up, const S* qm, const S* qp,
                                         const double* n, S* fh) const {
-    if (kind == EULER) {
+    if (kind == EULER || kind == NS) {
       S fm[8], fp[8];
-      flux(um, qm, fm); flux(up, qp, fp);
+      euler_flux(um, fm); euler_flux(up, fp);
       S lam = maxS(wave_speed(um, n), wave_speed(up, n));
       for (int c = 0; c < 4; ++c)
         fh[c] = 0.5 * ((fm[2 * c] + fp[2 * c]) * n[0] + (fm[2 * c + 1] + fp[2 * c + 1]) * n[1]) +
                 0.5 * lam * (um[c] - up[c]);
+      if (kind == NS) {
+        S vm[8], vp[8];
+        viscous_flux(um, qm, vm); viscous_flux(up, qp, vp);
+        for (int c = 0; c < 4; ++c)
+          fh[c] = fh[c] - 0.5 * ((vm[2 * c] + vp[2 * c]) * n[0] + (vm[2 * c + 1] + vp[2 * c + 1]) * n[1]) +
+                  tau * (um[c] - up[c]);
+      }
       return;
     }
     double bn = 0;
@@ -467,10 +521,20 @@ struct Model {
                                         const double* n, S* fh) const {
     double g[4];
     exact(x, t, g);
-    if (kind == EULER) {
+    if (kind == EULER || kind == NS) {
       S up[4] = {g[0], g[1], g[2], g[3]};
-      S qz[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-      fhat_interior(um, up, qz, qz, n, fh);
+      S fm[8], fp[8];
+      euler_flux(um, fm); euler_flux(up, fp);
+      S lam = maxS(wave_speed(um, n), wave_speed(up, n));
+      for (int c = 0; c < 4; ++c)
+        fh[c] = 0.5 * ((fm[2 * c] + fp[2 * c]) * n[0] + (fm[2 * c + 1] + fp[2 * c + 1]) * n[1]) +
+                0.5 * lam * (um[c] - up[c]);
+      if (kind == NS) {
+        S vm[8];
+        viscous_flux(um, qm, vm);
+        for (int c = 0; c < 4; ++c)
+          fh[c] = fh[c] - (vm[2 * c] * n[0] + vm[2 * c + 1] * n[1]) + tau * (um[c] - up[c]);
+      }
       return;
     }
     double bn = 0;
@@ -917,7 +981,7 @@ void* orc_create(int etype, int p, int nq1, int64_t E, const double* xyz, const 
   P->model.cas = cas;
   int nd = etype == HEX ? 3 : 2;
   P->model.nd = nd;
-  P->model.ncu = model == EULER ? 4 : 1;
+  P->model.ncu = (model == EULER || model == NS) ? 4 : 1;
   if (model == POISSON) { if (nmu > 0) P->model.kappa = mu[0]; if (nmu > 1) P->model.tau = mu[1]; }
   if (model == CONVDIFF) {
     if (nmu > 0) P->model.kappa = mu[0];
@@ -925,6 +989,14 @@ void* orc_create(int etype, int p, int nq1, int64_t E, const double* xyz, const 
     for (int d = 0; d < 3; ++d) if (nmu > 2 + d) P->model.beta[d] = mu[2 + d];
   }
   if (model == EULER && nmu > 0) P->model.gamma = mu[0];
+  if (model == NS) {
+    // mu = {gamma, Re, Pr, tau}; defaults 1.4, 100, 0.72 and tau = 1/Re
+    const double re = nmu > 1 ? mu[1] : 100.0;
+    if (nmu > 0) P->model.gamma = mu[0];
+    P->model.kappa = 1.0 / re;
+    if (nmu > 2) P->model.pr = mu[2];
+    P->model.tau = nmu > 3 ? mu[3] : 1.0 / re;
+  }
   if (!setup(*P, etype, p, nq1, E, xyz, vid)) { delete P; return nullptr; }
   return P;
 }

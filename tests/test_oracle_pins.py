@@ -113,18 +113,22 @@ def test_patch_test(etype, p, model, case):
     assert np.abs(r).max() < 1e-12 * max(1.0, np.abs(o.residual(np.zeros_like(u))).max())
 
 
+NS_MU = (1.4, 10.0, 0.72)          # gamma, Re, Pr (penalty tau = 1/Re)
+
+
 @pytest.mark.parametrize("etype,model", [(0, oracle.POISSON), (1, oracle.CONVDIFF), (2, oracle.CONVDIFF),
-                                         (1, oracle.EULER)])
+                                         (1, oracle.EULER), (1, oracle.NS)])
 def test_conservation_periodic(etype, model):
     """Single-valued numerical fluxes and sum_i phi_i = 1: on a periodic mesh with no
     source, the sum of all element residuals vanishes for any state."""
     n = 3
     nd = 3 if etype == 2 else 2
     mesh = _mesh(etype, n, hi=(2.0,) * nd, periodic=(True,) * nd)
-    mu = {oracle.POISSON: (1.0, 1.0), oracle.CONVDIFF: (0.1, 0.2, 1.0, 0.5, 0.25), oracle.EULER: (1.4,)}[model]
-    o = oracle.Oracle(mesh, 2, model, oracle.CASE_ZERO if model != oracle.EULER else oracle.CASE_CONST, mu)
-    u = (synth.random_euler_state(mesh.n_elem, o.npe, 3) if model == oracle.EULER
-         else synth.random_vector(o.ndof, 3))
+    mu = {oracle.POISSON: (1.0, 1.0), oracle.CONVDIFF: (0.1, 0.2, 1.0, 0.5, 0.25), oracle.EULER: (1.4,),
+          oracle.NS: NS_MU}[model]
+    gas = model in (oracle.EULER, oracle.NS)
+    o = oracle.Oracle(mesh, 2, model, oracle.CASE_CONST if gas else oracle.CASE_ZERO, mu)
+    u = synth.random_euler_state(mesh.n_elem, o.npe, 3) if gas else synth.random_vector(o.ndof, 3)
     r = o.residual(u).reshape(mesh.n_elem, o.ncu, o.npe)
     tot = r.sum(axis=(0, 2))
     assert np.all(np.abs(tot) <= 1e-13 * np.abs(r).sum())
@@ -134,6 +138,44 @@ def test_free_stream_euler():
     mesh = synth.quad_box(4, hi=(10.0, 10.0), periodic=(True, True), affine=SHEAR2)
     o = oracle.Oracle(mesh, 3, oracle.EULER, oracle.CASE_CONST, (1.4,))
     assert np.abs(o.residual(o.interpolate())).max() < 1e-13
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_free_stream_navier_stokes(periodic):
+    """A uniform state is an exact solution: R = 0, also against far-field boundaries."""
+    mesh = synth.quad_box(4, hi=(10.0, 10.0), periodic=(periodic, periodic), affine=SHEAR2)
+    o = oracle.Oracle(mesh, 3, oracle.NS, oracle.CASE_CONST, NS_MU)
+    assert np.abs(o.residual(o.interpolate())).max() < 1e-13
+
+
+def test_navier_stokes_inviscid_limit_is_euler():
+    """With zero viscosity and zero penalty the NS residual is the Euler residual."""
+    mesh = synth.quad_box(3, hi=(10.0, 10.0), periodic=(True, True), affine=SHEAR2)
+    oe = oracle.Oracle(mesh, 2, oracle.EULER, oracle.CASE_VORTEX, (1.4,))
+    on = oracle.Oracle(mesh, 2, oracle.NS, oracle.CASE_VORTEX, (1.4, 1e300, 0.72, 0.0))
+    u = synth.random_euler_state(mesh.n_elem, oe.npe, 5)
+    re, rn = oe.residual(u), on.residual(u)
+    assert np.linalg.norm(rn - re) <= 1e-14 * np.linalg.norm(re)
+
+
+def test_navier_stokes_viscous_terms_vanish_for_rigid_rotation():
+    """A rigid rotation (zero strain rate) with variable density and uniform internal
+    energy carries no viscous stress and no heat flux. Its state is cubic, so on Q3
+    elements u_h and the LDG gradient are exact, and the NS residual must equal the
+    Euler residual (viscous volume, face and penalty terms all zero). A missing
+    transpose in the stress, or a heat flux built on grad E instead of grad e, would
+    not vanish here; with a shear flow (the vortex) the two residuals do differ."""
+    mesh = synth.quad_box(3, affine=SHEAR2)
+    oe = oracle.Oracle(mesh, 3, oracle.EULER, oracle.CASE_ROTATION, (1.4,))
+    on = oracle.Oracle(mesh, 3, oracle.NS, oracle.CASE_ROTATION, (1.4, 2.0, 0.72))
+    u = on.interpolate()
+    re, rn = oe.residual(u), on.residual(u)
+    # the viscous terms cancel out of O(mu |grad v|) ~ 0.25 entries: rounding ~ 1e-12 relative
+    assert np.linalg.norm(rn - re) <= 1e-10 * np.linalg.norm(re)
+    oe2 = oracle.Oracle(mesh, 3, oracle.EULER, oracle.CASE_VORTEX, (1.4,))
+    on2 = oracle.Oracle(mesh, 3, oracle.NS, oracle.CASE_VORTEX, (1.4, 2.0, 0.72))
+    u2 = on2.interpolate()
+    assert np.linalg.norm(on2.residual(u2) - oe2.residual(u2)) > 1e-3 * np.linalg.norm(oe2.residual(u2))
 
 
 def test_poisson_jacobian_symmetric_positive_definite():
@@ -189,11 +231,12 @@ def test_euler_riemann_jump_closed_form():
 
 
 # ------------------------------------------------------------------- J.v pins
-@pytest.mark.parametrize("etype,model", [(0, oracle.POISSON), (2, oracle.CONVDIFF), (1, oracle.EULER)])
+@pytest.mark.parametrize("etype,model", [(0, oracle.POISSON), (2, oracle.CONVDIFF), (1, oracle.EULER),
+                                         (1, oracle.NS)])
 def test_jvp_matches_complex_step_jacobian(etype, model):
-    if model == oracle.EULER:
+    if model in (oracle.EULER, oracle.NS):
         mesh = synth.quad_box(3, hi=(10.0, 10.0), periodic=(True, True), affine=SHEAR2)
-        o = oracle.Oracle(mesh, 2, model, oracle.CASE_VORTEX, (1.4,))
+        o = oracle.Oracle(mesh, 2, model, oracle.CASE_VORTEX, (1.4,) if model == oracle.EULER else NS_MU)
         u = synth.random_euler_state(mesh.n_elem, o.npe, 11)
     else:
         mesh = _mesh(etype, 2, affine=SHEAR3 if etype == 2 else SHEAR2)
