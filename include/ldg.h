@@ -37,8 +37,9 @@ typedef struct ldg_ctx ldg_ctx;
 enum { LDG_TRI = 0, LDG_QUAD = 1, LDG_HEX = 2 };
 
 /* models of Table 1 (Section 2.1): Poisson and convection-diffusion are diffusion
- * models (with q, Eq. 1a); 2-D Euler is a convection model (no q) */
-enum { LDG_POISSON = 0, LDG_CONVDIFF = 1, LDG_EULER = 2 };
+ * models (with q, Eq. 1a); 2-D Euler is a convection model (no q); 2-D compressible
+ * Navier-Stokes is nonlinear with q (its viscous flux takes grad u = -q) */
+enum { LDG_POISSON = 0, LDG_CONVDIFF = 1, LDG_EULER = 2, LDG_NS = 3 };
 
 /* analytic data: Dirichlet/far-field boundary values, source terms and initial states */
 enum {
@@ -48,7 +49,8 @@ enum {
   LDG_CASE_POLY2 = 3,   /* a fixed quadratic polynomial (patch test) */
   LDG_CASE_LINEAR = 4,  /* a fixed linear polynomial (patch test) */
   LDG_CASE_VORTEX = 5,  /* isentropic vortex, strength 5, centre (5,5), velocity (1,1), period 10 */
-  LDG_CASE_CONST = 6    /* uniform Euler free stream rho = 1, v = (1,1), p = 1 */
+  LDG_CASE_CONST = 6,   /* uniform Euler free stream rho = 1, v = (1,1), p = 1 */
+  LDG_CASE_ROTATION = 7 /* rigid rotation v = (-y, x)/2, rho = 1 + x/10 + y/20, internal energy 2 */
 };
 
 typedef enum {
@@ -79,7 +81,10 @@ typedef struct {
 /* Model and parameters mu (Section 2.1):
  *   Poisson:   mu = {kappa, tau}
  *   ConvDiff:  mu = {kappa, tau, beta_x, beta_y[, beta_z]}
- *   Euler:     mu = {gamma}                                       */
+ *   Euler:     mu = {gamma}
+ *   NS:        mu = {gamma, Re, Pr[, tau]}: viscosity 1/Re, heat conductivity
+ *              gamma / (Re Pr) on the internal energy, jump penalty tau
+ *              (default 1/Re); defaults 1.4, 100, 0.72; quadrilaterals only  */
 typedef struct {
   int model;
   int case_id;
@@ -88,7 +93,8 @@ typedef struct {
 } ldg_model_desc;
 
 /* Solver options (Section 3.3). nq1 = Gauss points per direction (0 = default:
- * p + 1 for linear models on quadrilaterals/hexahedra, p + 2 for triangles and Euler). */
+ * p + 1 for linear models on quadrilaterals/hexahedra, p + 2 for triangles, Euler and
+ * Navier-Stokes). */
 typedef struct {
   int nq1;
   int gmres_m;          /* Krylov dimension per restart cycle (default 30) */
@@ -238,9 +244,10 @@ int ldg_newton_gmres_host(ldg_ctx* ctx, double* u_host, ldg_solve_report* rep);
 
 /* J(u) v without any device allocation (the paper has no counterpart; this is a
  * service for callers that cannot allocate). It computes the same product as
- * ldg_jvp, but the one piece of scratch that product needs (q of the direction v
- * for Poisson and convection-diffusion, n_dof * dim doubles) lives in a static
- * device array inside this library instead of the context's work space.
+ * ldg_jvp, but the scratch that product needs (q of the direction v for Poisson
+ * and convection-diffusion, n_dof * dim doubles; q(u) and q of v for Navier-Stokes,
+ * twice that) lives in a static device array inside this library instead of the
+ * context's work space.
  *
  * Who needs it: code that must not call cudaMalloc at this point, for example a
  * CUDA stream being captured into a graph in global capture mode (where

@@ -98,7 +98,9 @@ SegView seg_view(const ldg_batch* b) {
   return v;
 }
 
-int default_nq(int etype, int model, int p) { return (model == LDG_EULER || etype == LDG_TRI) ? p + 2 : p + 1; }
+int default_nq(int etype, int model, int p) {
+  return (model == LDG_EULER || model == LDG_NS || etype == LDG_TRI) ? p + 2 : p + 1;
+}
 int verts_per_elem(int etype) { return etype == LDG_TRI ? 3 : etype == LDG_QUAD ? 4 : 8; }
 
 // ------------------------------------------------------------ stage emission
@@ -123,12 +125,14 @@ int emit_residual(ldg_batch* b, cudaStream_t s, const double* u, double* r, cons
   return LDG_OK;
 }
 
-int emit_jv(ldg_batch* b, cudaStream_t s, const double* u, const double* v, double* jv, int prec, const int* skip) {
+// q_ready: the last residual was evaluated at u (its q-stage left q(u) in each group)
+int emit_jv(ldg_batch* b, cudaStream_t s, const double* u, const double* v, double* jv, int prec, const int* skip,
+            bool q_ready) {
   for (BGroup& g : b->groups) {
     g.ctx->stream = s;
     KArgs a = base_args(g.ctx);
     a.inst_skip = g.ctx->ext_inst ? skip : nullptr;
-    int rc = jvp_args(g.ctx, a, u + g.off, v + g.off, jv + g.off, prec);
+    int rc = jvp_args(g.ctx, a, u + g.off, v + g.off, jv + g.off, prec, q_ready);
     if (rc) return gfail(b, g, rc);
   }
   return LDG_OK;
@@ -188,7 +192,7 @@ int emit_cycle_tail(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle hb,
   count_launch();
   count_launch();
   BK(cudaGetLastError());
-  if ((rc = emit_jv(b, s, b->d_u, b->d_x, b->d_w, b->opt.krylov_precision, b->d_skip_gm))) return rc;
+  if ((rc = emit_jv(b, s, b->d_u, b->d_x, b->d_w, b->opt.krylov_precision, b->d_skip_gm, true))) return rc;
   kb_sub_norm<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_res, b->d_w, b->d_r, b->d_skip_gm);
   kb_cycle_end<<<1, 256, 0, s>>>(b->d_ctl, sv, b->d_st, b->d_skip_gm, b->d_skip_newt, hb, use);
   count_launch();
@@ -206,7 +210,7 @@ int emit_arnoldi(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle hc, in
     if ((rc = emit_pc(b, s, b->d_vcur, b->d_zcur, b->d_skip_arn))) return rc;
     dir = b->d_zcur;
   }
-  if ((rc = emit_jv(b, s, b->d_u, dir, b->d_w, b->opt.krylov_precision, b->d_skip_arn))) return rc;
+  if ((rc = emit_jv(b, s, b->d_u, dir, b->d_w, b->opt.krylov_precision, b->d_skip_arn, true))) return rc;
   // classical Gram-Schmidt, two passes: h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2,
   // then v_{j+1} = w / ||w|| and the Givens column
   double* part1 = b->d_part;
@@ -410,7 +414,7 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
     const ldg_mesh_desc& M = meshes[i];
     if (!M.xyz || !M.vid || M.n_elem <= 0 || M.elem_type < 0 || M.elem_type > 2)
       return bfail(b, LDG_ERR_ARG, "instance " + std::to_string(i) + ": bad mesh");
-    if (models[i].model < 0 || models[i].model > 2)
+    if (models[i].model < 0 || models[i].model > 3)
       return bfail(b, LDG_ERR_ARG, "instance " + std::to_string(i) + ": bad model");
     const int nq = opts && opts->nq1 > 0 ? opts->nq1 : default_nq(M.elem_type, models[i].model, p[i]);
     keyed[std::make_tuple(M.elem_type, p[i], nq, models[i].model)].push_back(i);
@@ -598,7 +602,7 @@ int ldg_batch_residual(ldg_batch* b, const double* u, double* r) {
 
 int ldg_batch_jvp(ldg_batch* b, int precision, const double* u, const double* v, double* jv) {
   if (!b || b->groups.empty() || !u || !v || !jv) return LDG_ERR_ARG;
-  return emit_jv(b, b->stream, u, v, jv, precision == LDG_FP32 ? LDG_FP32 : LDG_FP64, nullptr);
+  return emit_jv(b, b->stream, u, v, jv, precision == LDG_FP32 ? LDG_FP32 : LDG_FP64, nullptr, false);
 }
 
 int ldg_batch_autotune(ldg_batch* b, int force, int* tiles) {
@@ -648,7 +652,7 @@ int ldg_batch_solve(ldg_batch* b, double* u_dev, int use_graph, ldg_solve_report
       // every kernel instance runs once outside the capture (function attributes are set then)
       BK(cudaStreamSynchronize(s));
       if ((rc = emit_residual(b, s, b->d_u, b->d_res, nullptr))) return rc;
-      if ((rc = emit_jv(b, s, b->d_u, b->d_res, b->d_w, b->opt.krylov_precision, nullptr))) return rc;
+      if ((rc = emit_jv(b, s, b->d_u, b->d_res, b->d_w, b->opt.krylov_precision, nullptr, true))) return rc;
       if (b->pc && (rc = emit_pc(b, s, b->d_res, b->d_w, nullptr))) return rc;
       BK(cudaStreamSynchronize(s));
       before = launch_counter();

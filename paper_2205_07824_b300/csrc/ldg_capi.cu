@@ -31,10 +31,10 @@ using namespace ldg;
 namespace ldg {
 void register_all(std::vector<KernelSet>& reg) {
   // Tile0 first: the default instance of every (element, order, model)
-  register_tri_t<Tile0>(reg); register_quad_t<Tile0>(reg); register_hex_t<Tile0>(reg);
-  register_tri_t<Tile1>(reg); register_quad_t<Tile1>(reg); register_hex_t<Tile1>(reg);
-  register_tri_t<Tile2>(reg); register_quad_t<Tile2>(reg); register_hex_t<Tile2>(reg);
-  register_tri_t<Tile3>(reg); register_quad_t<Tile3>(reg); register_hex_t<Tile3>(reg);
+  register_tri_t<Tile0>(reg); register_quad_t<Tile0>(reg); register_hex_t<Tile0>(reg); register_ns_t<Tile0>(reg);
+  register_tri_t<Tile1>(reg); register_quad_t<Tile1>(reg); register_hex_t<Tile1>(reg); register_ns_t<Tile1>(reg);
+  register_tri_t<Tile2>(reg); register_quad_t<Tile2>(reg); register_hex_t<Tile2>(reg); register_ns_t<Tile2>(reg);
+  register_tri_t<Tile3>(reg); register_quad_t<Tile3>(reg); register_hex_t<Tile3>(reg); register_ns_t<Tile3>(reg);
 }
 long long& launch_counter() {
   static long long n = 0;
@@ -178,40 +178,34 @@ int do_residual(ldg_ctx* ctx, const double* u, double* r) {
   return LDG_OK;
 }
 
-int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv, int prec) {
-  const int* skip = a.skip;
-  const int* inst_skip = a.inst_skip;
+int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv, int prec, bool q_ready) {
   const bool f32 = prec == LDG_FP32;
   StageFn qs = f32 ? ctx->ks->qstage32 : ctx->ks->qstage;
   StageFn rs = f32 ? ctx->ks->residual32 : ctx->ks->residual;
-  if (ctx->ks->qstage) {
+  KArgs b = a;   // skip flags, instance map and model data of the caller
+  if (ctx->ks->linear && ctx->ks->qstage) {
     // linear model: J v = R(v) - R(0), the homogeneous operator applied to v
-    a.u = v; a.out = ctx->d_dq;
-    CK(qs(MODE_HOM, a, ctx->stream));
-    a = base_args(ctx);
-    a.skip = skip;
-    a.inst_skip = inst_skip;
-    a.u = v; a.q = ctx->d_dq; a.out = jv;
-    CK(rs(MODE_HOM, a, ctx->stream));
+    b.u = v; b.out = ctx->d_dq;
+    CK(qs(MODE_HOM, b, ctx->stream));
+    b = a;
+    b.u = v; b.q = ctx->d_dq; b.out = jv;
+    CK(rs(MODE_HOM, b, ctx->stream));
+  } else if (ctx->ks->qstage) {
+    // nonlinear model with q: dual numbers (u, v) and (q(u), Q v). q(u) is the FP64
+    // q-stage of the residual (reused when the caller has just evaluated R(u))
+    if (!q_ready) {
+      b.u = u; b.out = ctx->d_q;
+      CK(ctx->ks->qstage(MODE_R, b, ctx->stream));
+      b = a;
+    }
+    b.u = v; b.out = ctx->d_dq;
+    CK(qs(MODE_HOM, b, ctx->stream));
+    b = a;
+    b.u = u; b.v = v; b.q = ctx->d_q; b.dq = ctx->d_dq; b.out = jv;
+    CK(rs(MODE_JV, b, ctx->stream));
   } else {
-    a.u = u; a.v = v; a.out = jv;
-    CK(rs(MODE_JV, a, ctx->stream));
-  }
-  return LDG_OK;
-}
-
-int do_jvp(ldg_ctx* ctx, const double* u, const double* v, double* jv) {
-  KArgs a = base_args(ctx);
-  if (ctx->ks->qstage) {
-    // linear model: J v = R(v) - R(0), the homogeneous operator applied to v
-    a.u = v; a.out = ctx->d_dq;
-    CK(ctx->ks->qstage(MODE_HOM, a, ctx->stream));
-    a = base_args(ctx);
-    a.u = v; a.q = ctx->d_dq; a.out = jv;
-    CK(ctx->ks->residual(MODE_HOM, a, ctx->stream));
-  } else {
-    a.u = u; a.v = v; a.out = jv;
-    CK(ctx->ks->residual(MODE_JV, a, ctx->stream));
+    b.u = u; b.v = v; b.out = jv;
+    CK(rs(MODE_JV, b, ctx->stream));
   }
   return LDG_OK;
 }
@@ -801,8 +795,16 @@ ModelParams make_params(const ldg_model_desc* model) {
   mp.kappa = 1.0; mp.tau = 1.0; mp.gamma = 1.4; mp.cas = model->case_id;
   const double* mu = model->mu;
   const int nmu = mu ? model->n_mu : 0;
+  mp.pr = 0.72;
   if (model->model == LDG_EULER) { if (nmu > 0) mp.gamma = mu[0]; }
-  else {
+  else if (model->model == LDG_NS) {
+    // mu = {gamma, Re, Pr, tau}: viscosity 1/Re, penalty tau = 1/Re unless given
+    const double re = nmu > 1 ? mu[1] : 100.0;
+    if (nmu > 0) mp.gamma = mu[0];
+    mp.kappa = 1.0 / re;
+    if (nmu > 2) mp.pr = mu[2];
+    mp.tau = nmu > 3 ? mu[3] : 1.0 / re;
+  } else {
     if (nmu > 0) mp.kappa = mu[0];
     if (nmu > 1) mp.tau = mu[1];
     for (int d = 0; d < 3; ++d) if (nmu > 2 + d) mp.beta[d] = mu[2 + d];
@@ -953,16 +955,17 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->etype = mesh->elem_type;
   ctx->model = model->model;
-  if (ctx->etype < 0 || ctx->etype > 2 || ctx->model < 0 || ctx->model > 2) {
+  if (ctx->etype < 0 || ctx->etype > 2 || ctx->model < 0 || ctx->model > 3) {
     ldg_destroy(ctx);
     return LDG_ERR_ARG;
   }
   ctx->dim = ctx->etype == LDG_HEX ? 3 : 2;
-  if (ctx->model == LDG_EULER && ctx->dim != 2) { ldg_destroy(ctx); return LDG_ERR_UNSUPPORTED; }
-  ctx->ncu = ctx->model == LDG_EULER ? 4 : 1;
+  const bool gas = ctx->model == LDG_EULER || ctx->model == LDG_NS;
+  if (gas && ctx->dim != 2) { ldg_destroy(ctx); return LDG_ERR_UNSUPPORTED; }
+  ctx->ncu = gas ? 4 : 1;
   ldg_options o{};
   if (opts) o = *opts;
-  if (o.nq1 <= 0) o.nq1 = (ctx->model == LDG_EULER || ctx->etype == LDG_TRI) ? p + 2 : p + 1;
+  if (o.nq1 <= 0) o.nq1 = (gas || ctx->etype == LDG_TRI) ? p + 2 : p + 1;
   if (o.gmres_m <= 0) o.gmres_m = 30;
   if (o.gmres_m > 30) o.gmres_m = 30;
   if (o.max_restarts <= 0) o.max_restarts = 50;
@@ -1117,7 +1120,7 @@ int ldg_residual(ldg_ctx* ctx, const double* u, double* r) {
 
 int ldg_jvp(ldg_ctx* ctx, const double* u, const double* v, double* jv) {
   if (!ctx || !ctx->ks || !u || !v || !jv) return LDG_ERR_ARG;
-  return do_jvp(ctx, u, v, jv);
+  return jvp_args(ctx, base_args(ctx), u, v, jv, LDG_FP64);
 }
 
 int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u, const double* v, double* jv) {
@@ -1386,10 +1389,12 @@ int ldg_jvp_noalloc(ldg_ctx* ctx, const double* u, const double* v, double* jv) 
     CK(ctx->ks->residual(MODE_JV, a, ctx->stream));
     return LDG_OK;
   }
-  const size_t need = (size_t)ctx->ndof * ctx->dim;
+  // linear models: Q v; nonlinear models with q: q(u) and Q v
+  const size_t nq = (size_t)ctx->ndof * ctx->dim;
+  const size_t need = ctx->ks->linear ? nq : 2 * nq;
   if (need > kNoAllocScratchDoubles)
     return fail(ctx, LDG_ERR_ARG, "ldg_jvp_noalloc: this operator needs " + std::to_string(need) +
-                                      " doubles of scratch (n_dof * dim), more than the static maximum of " +
+                                      " doubles of scratch (n_dof * dim per q field), more than the static maximum of " +
                                       std::to_string(kNoAllocScratchDoubles));
   int dev = 0;
   CK(cudaGetDevice(&dev));
@@ -1400,13 +1405,23 @@ int ldg_jvp_noalloc(ldg_ctx* ctx, const double* u, const double* v, double* jv) 
     noalloc_addr[dev] = (double*)p;
   }
   double* dq = noalloc_addr[dev];
-  // q(v) of the homogeneous operator overwrites every entry it later reads: nothing to clear
+  // each q-stage overwrites every entry that is later read: nothing to clear
   KArgs a = base_args(ctx);
   a.u = v; a.out = dq;
   CK(ctx->ks->qstage(MODE_HOM, a, ctx->stream));
+  if (ctx->ks->linear) {
+    a = base_args(ctx);
+    a.u = v; a.q = dq; a.out = jv;
+    CK(ctx->ks->residual(MODE_HOM, a, ctx->stream));
+    return LDG_OK;
+  }
+  double* qu = dq + nq;
   a = base_args(ctx);
-  a.u = v; a.q = dq; a.out = jv;
-  CK(ctx->ks->residual(MODE_HOM, a, ctx->stream));
+  a.u = u; a.out = qu;
+  CK(ctx->ks->qstage(MODE_R, a, ctx->stream));
+  a = base_args(ctx);
+  a.u = u; a.v = v; a.q = qu; a.dq = dq; a.out = jv;
+  CK(ctx->ks->residual(MODE_JV, a, ctx->stream));
   return LDG_OK;
 }
 

@@ -108,7 +108,9 @@ int fail(ldg_ctx* c, int code, const std::string& msg);
 KArgs base_args(ldg_ctx* c);
 int64_t grid_for(int64_t n, int t = 256);
 int do_residual(ldg_ctx* ctx, const double* u, double* r);
-int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv, int prec);
+// J.v in the given arithmetic; q_ready: ctx->d_q already holds q(u) (nonlinear models
+// with q, after a residual evaluation at the same u)
+int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv, int prec, bool q_ready = false);
 int ensure_pc_storage(ldg_ctx* ctx);
 int do_pc_setup(ldg_ctx* ctx, const double* u);
 int pc_apply(ldg_ctx* ctx, const double* x, double* y, const int* skip, const int* inst_skip = nullptr);

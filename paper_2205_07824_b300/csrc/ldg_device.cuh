@@ -144,11 +144,14 @@ template <class S> __device__ __forceinline__ S smax(S a, S b) { return val(a) >
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
 // ----------------------------------------------------------------- models
-enum { M_POISSON = 0, M_CONVDIFF = 1, M_EULER = 2 };
-enum { C_ZERO = 0, C_SINSIN = 1, C_EXPSIN = 2, C_POLY2 = 3, C_LINEAR = 4, C_VORTEX = 5, C_CONST = 6 };
+enum { M_POISSON = 0, M_CONVDIFF = 1, M_EULER = 2, M_NS = 3 };
+enum { C_ZERO = 0, C_SINSIN = 1, C_EXPSIN = 2, C_POLY2 = 3, C_LINEAR = 4, C_VORTEX = 5, C_CONST = 6,
+       C_ROTATION = 7 };
 
+// kappa: diffusivity, or the dynamic viscosity 1/Re of Navier-Stokes; tau: the
+// LDG jump penalty; pr: the Prandtl number (Navier-Stokes)
 struct ModelParams {
-  double kappa, tau, beta[3], gamma;
+  double kappa, tau, beta[3], gamma, pr;
   int cas;
 };
 
@@ -171,6 +174,11 @@ __device__ void exact_state(const ModelParams& mp, int ncu, const double* x, dou
       double p = pow(rho, gm);
       g[0] = rho; g[1] = rho * ux; g[2] = rho * uy;
       g[3] = p / (gm - 1.0) + 0.5 * rho * (ux * ux + uy * uy);
+    } else if (mp.cas == C_ROTATION) {
+      // rigid rotation v = (-y, x) / 2, density 1 + x / 10 + y / 20, internal energy 2:
+      // zero strain rate and zero temperature gradient, so no viscous stress or heat flux
+      const double rho = 1.0 + 0.1 * x[0] + 0.05 * x[1], ux = -0.5 * x[1], uy = 0.5 * x[0];
+      g[0] = rho; g[1] = rho * ux; g[2] = rho * uy; g[3] = rho * (2.0 + 0.5 * (ux * ux + uy * uy));
     } else {
       g[0] = 1.0; g[1] = 1.0; g[2] = 1.0; g[3] = 1.0 / (mp.gamma - 1.0) + 1.0;
     }
@@ -256,11 +264,11 @@ __device__ double source_term(const ModelParams& mp, bool conv, const double* x)
 
 // Model parameters in the kernel's compute precision.
 template <class R> struct MPar {
-  R kappa, tau, beta[3], gamma;
+  R kappa, tau, beta[3], gamma, pr;
 };
 template <class R> __device__ __forceinline__ MPar<R> mpar(const ModelParams& mp) {
   MPar<R> r;
-  r.kappa = R(mp.kappa); r.tau = R(mp.tau); r.gamma = R(mp.gamma);
+  r.kappa = R(mp.kappa); r.tau = R(mp.tau); r.gamma = R(mp.gamma); r.pr = R(mp.pr);
   for (int d = 0; d < 3; ++d) r.beta[d] = R(mp.beta[d]);
   return r;
 }
@@ -270,6 +278,7 @@ template <int DIM, bool CONV> struct ScalarModel {
   static constexpr int NCU = 1;
   static constexpr bool HASQ = true;
   static constexpr bool LINEAR = true;
+  static constexpr bool SOURCE = true;   // manufactured source s of Eq. 1b
   static constexpr int KIND = CONV ? M_CONVDIFF : M_POISSON;
 
   template <class S, class R> __device__ static void flux(const S* u, const S* q, S* f, const MPar<R>& mp) {
@@ -310,6 +319,7 @@ struct EulerModel {
   static constexpr int NCU = 4;
   static constexpr bool HASQ = false;
   static constexpr bool LINEAR = false;
+  static constexpr bool SOURCE = false;
   static constexpr int KIND = M_EULER;
 
   template <class S, class R> __device__ static void flux(const S* u, const S*, S* f, const MPar<R>& mp) {
@@ -347,6 +357,67 @@ struct EulerModel {
                                                               S* fh, const MPar<R>& mp) {
     S up[4] = {S(g[0]), S(g[1]), S(g[2]), S(g[3])};
     fhat(um, up, qm, qm, n, fh, mp);
+  }
+};
+
+// 2-D compressible Navier-Stokes (Section 2.1): f = F(u) - F_v(u, grad u), the
+// viscous flux taken from q = -grad u of Eq. 1a (LDG). Interior faces: the Euler
+// Rusanov flux, minus the central average of F_v.n, plus the jump penalty
+// tau (u- - u+); far-field faces: the same against the exact state with the
+// one-sided F_v(u-, q-).n and tau (u- - g).
+struct NSModel {
+  static constexpr int NCU = 4;
+  static constexpr bool HASQ = true;
+  static constexpr bool LINEAR = false;
+  static constexpr bool SOURCE = false;
+  static constexpr int KIND = M_NS;
+
+  // F_v[c * 2 + d] with grad u = -q: Stokes stress with bulk viscosity -2/3 mu and
+  // Fourier heat flux mu gamma / Pr grad e, e = E / rho - |v|^2 / 2 the internal energy
+  // (temperature in units of c_v); velocity and energy gradients by the chain rule.
+  template <class S, class R> __device__ static void viscous(const S* u, const S* q, S* fv, const MPar<R>& mp) {
+    const S ir = R(1) / u[0];
+    const S vx = u[1] * ir, vy = u[2] * ir, E = u[3] * ir;
+    const S vxx = (vx * q[0] - q[2]) * ir, vxy = (vx * q[1] - q[3]) * ir;   // d v_x / d x_d
+    const S vyx = (vy * q[0] - q[4]) * ir, vyy = (vy * q[1] - q[5]) * ir;   // d v_y / d x_d
+    const S dv = vxx + vyy;
+    const S txx = (vxx * R(2) - dv * R(2.0 / 3.0)) * mp.kappa;
+    const S tyy = (vyy * R(2) - dv * R(2.0 / 3.0)) * mp.kappa;
+    const S txy = (vxy + vyx) * mp.kappa;
+    const S ex = (E * q[0] - q[6]) * ir - (vx * vxx + vy * vyx);
+    const S ey = (E * q[1] - q[7]) * ir - (vx * vxy + vy * vyy);
+    const R kt = mp.kappa * mp.gamma / mp.pr;
+    fv[0] = S(R(0)); fv[1] = S(R(0));
+    fv[2] = txx;     fv[3] = txy;
+    fv[4] = txy;     fv[5] = tyy;
+    fv[6] = vx * txx + vy * txy + ex * kt;
+    fv[7] = vx * txy + vy * tyy + ey * kt;
+  }
+  template <class S, class R> __device__ static void flux(const S* u, const S* q, S* f, const MPar<R>& mp) {
+    S fv[8];
+    EulerModel::flux(u, q, f, mp);
+    viscous(u, q, fv, mp);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) f[i] = f[i] - fv[i];
+  }
+  template <class S, class R> __device__ static void fhat(const S* um, const S* up, const S* qm, const S* qp,
+                                                          const R* n, S* fh, const MPar<R>& mp) {
+    S vm[8], vp[8];
+    EulerModel::fhat(um, up, qm, qp, n, fh, mp);
+    viscous(um, qm, vm, mp);
+    viscous(up, qp, vp, mp);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      fh[c] = fh[c] - ((vm[2 * c] + vp[2 * c]) * n[0] + (vm[2 * c + 1] + vp[2 * c + 1]) * n[1]) * R(0.5) +
+              (um[c] - up[c]) * mp.tau;
+  }
+  template <class S, class R> __device__ static void fhat_bnd(const S* um, const S* qm, const R* g, const R* n,
+                                                              S* fh, const MPar<R>& mp) {
+    S vm[8];
+    EulerModel::fhat_bnd(um, qm, g, n, fh, mp);
+    viscous(um, qm, vm, mp);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) fh[c] = fh[c] - (vm[2 * c] * n[0] + vm[2 * c + 1] * n[1]) + (um[c] - g[c]) * mp.tau;
   }
 };
 

@@ -15,6 +15,9 @@
 // MODE_R evaluates R(u); MODE_HOM the homogeneous linear part of a linear model
 // (R(v) - R(0): no source, zero boundary data), which is its exact J.v; MODE_JV
 // propagates dual numbers (u, v) through a nonlinear model and writes dR/du . v.
+// A nonlinear model with q (Navier-Stokes) carries the dual pair (q(u), Q v) too:
+// the q-stage is affine in u, so its derivative along v is the homogeneous q-stage
+// Q v (zero boundary data), computed by the q-stage in MODE_HOM.
 //
 // Storage in HBM is always FP64. The compute type R is double (parity path) or
 // float (the mixed-precision Krylov path): an FP32 instance converts its inputs
@@ -43,7 +46,8 @@ constexpr int N_TILES = 4;
 struct KArgs {
   const void* u;              // [E][NCU][NPE]     state (R, JV) or direction (HOM)
   const void* v;              // [E][NCU][NPE]     direction (JV)
-  const void* q;              // [E][NCU][DIM][NPE] q(u) (R) or q(v) (HOM), diffusion models
+  const void* q;              // [E][NCU][DIM][NPE] q(u) (R, JV) or q(v) (HOM), models with q
+  const void* dq;             // [E][NCU][DIM][NPE] Q v, the tangent of q (JV, nonlinear models with q)
   const void* hist;           // [E][NCU][NPE]     BDF history term, or null
   void* out;                  // [E][NCU][NPE] residual / J.v, or [E][NCU][DIM][NPE] q
   const double* geo;          // [E][GEO] per-element affine geometry
@@ -53,7 +57,7 @@ struct KArgs {
   const float* opsf;          // the same blob in FP32 (for FP32-compute instances)
   const unsigned char* perm;  // [n_orient][NFQ] face-point permutations
   const int* skip;            // optional: the kernel returns at once when *skip != 0
-  int blk_col;                // MODE_JV block extraction: -1 off; else the element's own tangent is
+  int blk_col;                // MODE_JV block extraction (models without q): -1 off; else the element's own tangent is
                               // unit vector blk_col, neighbours' tangents are zero, and column blk_col
                               // of each element's diagonal block dR_K/du_K is written to blk_out
   double* blk_out;            // [E][NLOC][NLOC] column-major blocks (NLOC = NCU * NPE)
@@ -454,7 +458,7 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
   constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ, NQV = EL::NQV;
   constexpr int NE = L::NE, GEO = L::GEO, NCV = L::NCV;
   constexpr bool HASQ = MD::HASQ;
-  static_assert(!(MODE == MODE_JV && HASQ), "dual-number J.v is for models without q");
+  static_assert(!(MODE == MODE_JV && HASQ && MD::LINEAR), "linear models take MODE_HOM for J.v");
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int e0 = blockIdx.x * NE;
@@ -470,6 +474,7 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
   const double* u = (const double*)a.u;
   const double* v = (const double*)a.v;
   const double* q = (const double*)a.q;
+  const double* dq = (const double*)a.dq;
 
   for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = R(a.geo[(size_t)e0 * GEO + i]);
   for (int i = threadIdx.x; i < NE * NCV * NPE; i += blockDim.x) {
@@ -481,8 +486,10 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
         if constexpr (MODE == MODE_JV)
           val = S(R(u[gi]), a.blk_col >= 0 ? R(fld * NPE + n == a.blk_col ? 1 : 0) : R(v[gi]));
         else val = S(R(u[gi]));
-      } else {
-        if constexpr (HASQ) val = S(R(q[((size_t)(e0 + e) * NCU * DIM + (fld - NCU)) * NPE + n]));
+      } else if constexpr (HASQ) {
+        const size_t gi = ((size_t)(e0 + e) * NCU * DIM + (fld - NCU)) * NPE + n;
+        if constexpr (MODE == MODE_JV) val = S(R(q[gi]), R(dq[gi]));
+        else val = S(R(q[gi]));
       }
     }
     X[i] = val;
@@ -510,8 +517,10 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
             size_t gi = ((size_t)nb * NCU + fld) * NPE + nn;
             if constexpr (MODE == MODE_JV) vp = S(R(u[gi]), a.blk_col >= 0 ? R(0) : R(v[gi]));
             else vp = S(R(u[gi]));
-          } else {
-            if constexpr (HASQ) vp = S(R(q[((size_t)nb * NCU * DIM + (fld - NCU)) * NPE + nn]));
+          } else if constexpr (HASQ) {
+            const size_t gi = ((size_t)nb * NCU * DIM + (fld - NCU)) * NPE + nn;
+            if constexpr (MODE == MODE_JV) vp = S(R(q[gi]), R(dq[gi]));
+            else vp = S(R(q[gi]));
           }
         }
       }
@@ -597,7 +606,7 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
     const R* g = Gs + e * GEO;
     const R wj = w * g[Geo<DIM>::DETJ];
     R src = R(0);
-    if (MODE == MODE_R && e < ne && MD::KIND != M_EULER) {
+    if (MODE == MODE_R && e < ne && MD::SOURCE) {
       double x[3];
       phys_x<DIM>(g, xi, x);
       src = R(source_term<DIM>(elem_mp(a, e0 + e), MD::KIND == M_CONVDIFF, x));

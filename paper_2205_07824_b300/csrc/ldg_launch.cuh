@@ -20,9 +20,10 @@ constexpr int BLK_KT = 8;
 struct KernelSet {
   int etype, p, nq, model;
   int tile;           // tile variant (Tile0 .. Tile3)
-  StageFn qstage;     // FP64 compute. Diffusion models: MODE_R / MODE_HOM; null otherwise
+  bool linear;        // linear model: J.v is the homogeneous operator (MODE_HOM)
+  StageFn qstage;     // FP64 compute. Models with q: MODE_R / MODE_HOM; null otherwise
   StageFn residual;   // FP64 compute. MODE_R / MODE_HOM (linear models) / MODE_JV (nonlinear models)
-  StageFn qstage32;   // FP32 compute, MODE_HOM (diffusion models); null otherwise
+  StageFn qstage32;   // FP32 compute, MODE_HOM (models with q); null otherwise
   StageFn residual32; // FP32 compute, MODE_HOM (linear) / MODE_JV (nonlinear): the Krylov J.v
   BlockFn blocks;     // (unused: FP64 blocks take one tangent per launch)
   BlockFn blocks32;   // FP32 block columns by BLK_KT-tangent dual numbers (models without q)
@@ -102,6 +103,7 @@ template <class EL, class MD, class TL = Tile0> void add_set(std::vector<KernelS
   KernelSet k;
   k.etype = etype; k.p = EL::P; k.nq = EL::NQ; k.model = MD::KIND;
   k.tile = tile_id<TL>();
+  k.linear = MD::LINEAR;
   k.residual = &stage_res<EL, MD, double, TL>;
   k.residual32 = &stage_res32<EL, MD, TL>;
   k.ne_r = RLayout<EL, MD, MODE_R, double, TL>::NE;
@@ -111,8 +113,9 @@ template <class EL, class MD, class TL = Tile0> void add_set(std::vector<KernelS
     k.qstage32 = &stage_q32<EL, MD, TL>;
     k.ne_q = QLayout<EL, MD, double, TL>::NE;
     k.smem_q = QLayout<EL, MD, double, TL>::SMEM;
-    k.ne_j = RLayout<EL, MD, MODE_HOM, double, TL>::NE;
-    k.smem_j = RLayout<EL, MD, MODE_HOM, double, TL>::SMEM;
+    constexpr int JM = MD::LINEAR ? MODE_HOM : MODE_JV;
+    k.ne_j = RLayout<EL, MD, JM, double, TL>::NE;
+    k.smem_j = RLayout<EL, MD, JM, double, TL>::SMEM;
     k.blocks = nullptr;
     k.blocks32 = nullptr;
   } else {
@@ -131,6 +134,7 @@ template <class EL, class MD, class TL = Tile0> void add_set(std::vector<KernelS
 template <class TL> void register_tri_t(std::vector<KernelSet>& reg);
 template <class TL> void register_quad_t(std::vector<KernelSet>& reg);
 template <class TL> void register_hex_t(std::vector<KernelSet>& reg);
+template <class TL> void register_ns_t(std::vector<KernelSet>& reg);
 void register_all(std::vector<KernelSet>& reg);
 
 }  // namespace ldg

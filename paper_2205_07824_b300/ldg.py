@@ -16,8 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libldg.so")
 
 TRI, QUAD, HEX = 0, 1, 2
-POISSON, CONVDIFF, EULER = 0, 1, 2
-CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST = range(7)
+POISSON, CONVDIFF, EULER, NS = 0, 1, 2, 3
+CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST, CASE_ROTATION = range(8)
 STEADY, BDF1, BDF2 = 0, 1, 2
 FP64, FP32 = 0, 1
 PC_NONE, PC_BJACOBI, PC_MLP = 0, 1, 2

@@ -29,6 +29,8 @@ def mu_for(model, nd):
         return (1.0, 1.0)
     if model == oracle.CONVDIFF:
         return (0.05, 0.3, 1.0, 0.5, 0.25)[: 2 + nd]
+    if model == oracle.NS:
+        return (1.4, 10.0, 0.72)       # gamma, Re, Pr: Re = 10 makes the viscous terms large
     return (1.4,)
 
 
@@ -43,7 +45,7 @@ def pair(mesh, p, model, case, mu=None, **kw):
 
 
 def state(o, mesh, seed):
-    if o.model == oracle.EULER:
+    if o.model in (oracle.EULER, oracle.NS):
         return synth.random_euler_state(mesh.n_elem, o.npe, seed)
     return synth.random_vector(o.ndof, seed)
 
