@@ -17,7 +17,8 @@ _SRC = os.path.join(_HERE, "ldg_oracle.cpp")
 _LIB = os.path.join(_HERE, "libldg_oracle.so")
 
 POISSON, CONVDIFF, EULER, NS = 0, 1, 2, 3
-CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST, CASE_ROTATION = range(8)
+(CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST, CASE_ROTATION,
+ CASE_CYLINDER, CASE_REST) = range(10)
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.POINTER(ctypes.c_int64)
@@ -41,6 +42,10 @@ def lib():
         L.orc_create.restype = ctypes.c_void_p
         L.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _D, _I64,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.orc_create_curved.restype = ctypes.c_void_p
+        L.orc_create_curved.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _D, _I64,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _D,
+                                        ctypes.c_void_p]
         L.orc_destroy.argtypes = [ctypes.c_void_p]
         L.orc_ndof.restype = ctypes.c_int64
         L.orc_ndof.argtypes = [ctypes.c_void_p]
@@ -92,8 +97,17 @@ class Oracle:
         xyz = _c(mesh.xyz)
         vid = _c(mesh.vid, np.int64)
         mu = _c(np.asarray(mu, dtype=np.float64).reshape(-1))
-        self._h = lib().orc_create(mesh.etype, p, nq1, mesh.n_elem, _p(xyz), vid.ctypes.data_as(_I64),
-                                   model, case, len(mu), _p(mu) if len(mu) else None)
+        pg = int(getattr(mesh, "pg", 0) or 0)
+        if pg > 0:
+            xgeo = _c(mesh.xgeo)
+            bc = None if mesh.bc is None else np.ascontiguousarray(mesh.bc, dtype=np.uint8)
+            self._keep = (xgeo, bc)
+            self._h = lib().orc_create_curved(mesh.etype, p, nq1, mesh.n_elem, _p(xyz), vid.ctypes.data_as(_I64),
+                                              model, case, len(mu), _p(mu) if len(mu) else None, pg, _p(xgeo),
+                                              None if bc is None else bc.ctypes.data)
+        else:
+            self._h = lib().orc_create(mesh.etype, p, nq1, mesh.n_elem, _p(xyz), vid.ctypes.data_as(_I64),
+                                       model, case, len(mu), _p(mu) if len(mu) else None)
         if not self._h:
             raise ValueError("oracle rejected the mesh")
         a = [ctypes.c_int() for _ in range(5)]

@@ -331,7 +331,7 @@ struct Ref {
 // ------------------------------------------------------------------ models
 enum { POISSON = 0, CONVDIFF = 1, EULER = 2, NS = 3 };
 enum { CASE_ZERO = 0, CASE_SINSIN = 1, CASE_EXPSIN = 2, CASE_POLY2 = 3, CASE_LINEAR = 4,
-       CASE_VORTEX = 5, CASE_CONST = 6, CASE_ROTATION = 7 };
+       CASE_VORTEX = 5, CASE_CONST = 6, CASE_ROTATION = 7, CASE_CYLINDER = 8, CASE_REST = 9 };
 
 struct Model {
   int kind, cas, nd, ncu;
@@ -361,6 +361,13 @@ struct Model {
         // internal energy e = 2: a cubic state with zero strain rate and zero grad e
         const double rho = 1.0 + 0.1 * x[0] + 0.05 * x[1], vx = -0.5 * x[1], vy = 0.5 * x[0];
         u[0] = rho; u[1] = rho * vx; u[2] = rho * vy; u[3] = rho * (2.0 + 0.5 * (vx * vx + vy * vy));
+      } else if (cas == CASE_CYLINDER) {
+        // free stream of the cylinder flow: rho = 1, v = (1, 0), Mach 0.2: p = 1 / (gamma 0.2^2)
+        const double pr = 1.0 / (gamma * 0.04);
+        u[0] = 1; u[1] = 1; u[2] = 0; u[3] = pr / (gamma - 1) + 0.5;
+      } else if (cas == CASE_REST) {
+        // gas at rest: rho = 1, v = 0, p = 1
+        u[0] = 1; u[1] = 0; u[2] = 0; u[3] = 1.0 / (gamma - 1);
       } else {
         u[0] = 1; u[1] = 1; u[2] = 1; u[3] = 1.0 / (gamma - 1) + 1.0;
       }
@@ -517,6 +524,21 @@ struct Model {
             tau * (um[0] - up[0]);
   }
 
+  // No-slip adiabatic wall (gas models): boundary state ub = (rho-, 0, 0, (rho E)-);
+  // fhat.n = F(ub).n (pressure only) - F_v(ub, q-).n without its energy component
+  // (zero velocity, zero heat flux) + tau (u- - ub) for Navier-Stokes.
+  template <class S> void fhat_wall(const S* um, const S* qm, const double* n, S* fh) const {
+    S ub[4] = {um[0], S(0.0), S(0.0), um[3]};
+    S f[8];
+    euler_flux(ub, f);
+    for (int c = 0; c < 4; ++c) fh[c] = f[2 * c] * n[0] + f[2 * c + 1] * n[1];
+    if (kind == NS) {
+      S fv[8];
+      viscous_flux(ub, qm, fv);
+      for (int c = 0; c < 3; ++c) fh[c] = fh[c] - (fv[2 * c] * n[0] + fv[2 * c + 1] * n[1]) + tau * (um[c] - ub[c]);
+    }
+  }
+
   template <class S> void fhat_boundary(const S* um, const S* qm, const double* x, double t,
                                         const double* n, S* fh) const {
     double g[4];
@@ -567,17 +589,96 @@ struct Problem {
   std::vector<double> un, unm1;
   std::string msg;
 
+  // Curved quadrilaterals: x(xi) = sum_a xgeo[K][a] l_a(xi), the degree-pg Lagrange
+  // interpolant through (pg+1)^2 equispaced reference points (first axis fastest).
+  int pg = 0;
+  std::vector<double> xgeo;           // [E][(pg+1)^2][2]
+  std::vector<unsigned char> bc;      // [E][nf]: 1 marks a wall face, 0 a data face
+  bool curved() const { return pg > 0; }
+  bool wall(int64_t K, int f) const {
+    return !bc.empty() && bc[K * ref.nf + f] == 1 && (model.kind == EULER || model.kind == NS);
+  }
+
   int nd() const { return ref.nd; }
   int ncu() const { return model.ncu; }
   int64_t nloc() const { return (int64_t)ref.npe * model.ncu; }
   int64_t ndof() const { return E * nloc(); }
 
+  // 1-D Lagrange basis on the pg+1 equispaced points of [-1, 1] and its derivative
+  void lagr(double t, double* l, double* dl) const {
+    const int m = pg;
+    for (int a = 0; a <= m; ++a) {
+      const double ta = -1.0 + 2.0 * a / m;
+      double den = 1, num = 1, der = 0;
+      for (int b = 0; b <= m; ++b) {
+        if (b == a) continue;
+        const double tb = -1.0 + 2.0 * b / m;
+        den *= ta - tb;
+        // product rule: d/dt prod (t - t_b) = sum_c prod_{b != c} (t - t_b)
+        der = der * (t - tb) + num;
+        num *= t - tb;
+      }
+      l[a] = num / den;
+      dl[a] = der / den;
+    }
+  }
+  // curved map: x and J[d][k] = d x_d / d xi_k at xi
+  void curved_map(int64_t K, const double* xi, double* x, double J[2][2]) const {
+    double l0[16], d0[16], l1[16], d1[16];
+    lagr(xi[0], l0, d0);
+    lagr(xi[1], l1, d1);
+    const int n1 = pg + 1;
+    x[0] = x[1] = 0;
+    J[0][0] = J[0][1] = J[1][0] = J[1][1] = 0;
+    for (int b = 0; b < n1; ++b)
+      for (int a = 0; a < n1; ++a) {
+        const double* X = &xgeo[((size_t)K * n1 * n1 + a + n1 * b) * 2];
+        for (int d = 0; d < 2; ++d) {
+          x[d] += X[d] * l0[a] * l1[b];
+          J[d][0] += X[d] * d0[a] * l1[b];
+          J[d][1] += X[d] * l0[a] * d1[b];
+        }
+      }
+  }
+
   void map(int64_t K, const double* xi, double* x) const {
+    if (curved()) { double J[2][2]; curved_map(K, xi, x, J); return; }
     int d_ = nd();
     for (int d = 0; d < d_; ++d) {
       x[d] = v0[K * 3 + d];
       for (int k = 0; k < d_; ++k) x[d] += A[K * 9 + d * 3 + k] * 0.5 * (xi[k] + 1);
     }
+  }
+  // Ji[k*3 + d] = d xi_k / d x_d and det J at reference point xi
+  void jac(int64_t K, const double* xi, double* Ji, double& det) const {
+    if (!curved()) {
+      for (int i = 0; i < 9; ++i) Ji[i] = Jinv[K * 9 + i];
+      det = detJ[K];
+      return;
+    }
+    double x[2], J[2][2];
+    curved_map(K, xi, x, J);
+    det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    for (int i = 0; i < 9; ++i) Ji[i] = 0;
+    Ji[0] = J[1][1] / det; Ji[1] = -J[0][1] / det;
+    Ji[3] = -J[1][0] / det; Ji[4] = J[0][0] / det;
+  }
+  // outward unit normal n and surface Jacobian sJ of face f at the reference point xi on it
+  void face_frame(int64_t K, int f, const double* xi, double* n, double& sJ) const {
+    if (!curved()) {
+      const Face& F = faces[K * ref.nf + f];
+      for (int d = 0; d < 3; ++d) n[d] = F.n[d];
+      sJ = F.sJ;
+      return;
+    }
+    // n sJ = +-det J J^{-T} e_axis (Nanson), + on the face xi_axis = +1
+    double Ji[9], det;
+    jac(K, xi, Ji, det);
+    const int ax = f / 2;
+    const double sg = (f % 2) ? 1.0 : -1.0;
+    double m[2] = {sg * det * Ji[ax * 3 + 0], sg * det * Ji[ax * 3 + 1]};
+    sJ = std::sqrt(m[0] * m[0] + m[1] * m[1]);
+    n[0] = m[0] / sJ; n[1] = m[1] / sJ; n[2] = 0;
   }
   void invmap(int64_t K, const double* x, double* xi) const {
     int d_ = nd();
@@ -586,13 +687,55 @@ struct Problem {
       for (int d = 0; d < d_; ++d) s += Ainv[K * 9 + k * 3 + d] * (x[d] - v0[K * 3 + d]);
       xi[k] = 2 * s - 1;
     }
+    if (!curved()) return;
+    // Damped Newton iteration on x(xi) = x (step halved while the misfit grows), from
+    // the corner-based affine guess, then from the reference centre and the face
+    // centres; the first root found inside the reference square is taken.
+    const double starts[6][2] = {{xi[0], xi[1]}, {0, 0}, {-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    for (int st = 0; st < 6; ++st) {
+      double z[2] = {starts[st][0], starts[st][1]};
+      double y[2], J[2][2];
+      curved_map(K, z, y, J);
+      double res = std::hypot(y[0] - x[0], y[1] - x[1]);
+      for (int it = 0; it < 100 && res > 0; ++it) {
+        const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const double r0 = y[0] - x[0], r1 = y[1] - x[1];
+        const double d0 = (J[1][1] * r0 - J[0][1] * r1) / det, d1 = (-J[1][0] * r0 + J[0][0] * r1) / det;
+        double a = 1.0, zn[2], yn[2], Jn[2][2], rn = 0;
+        for (int h = 0; h < 40; ++h, a *= 0.5) {
+          zn[0] = z[0] - a * d0; zn[1] = z[1] - a * d1;
+          curved_map(K, zn, yn, Jn);
+          rn = std::hypot(yn[0] - x[0], yn[1] - x[1]);
+          if (rn < res) break;
+        }
+        if (!(rn < res)) break;
+        const double step = a * (std::fabs(d0) + std::fabs(d1));
+        z[0] = zn[0]; z[1] = zn[1]; y[0] = yn[0]; y[1] = yn[1];
+        J[0][0] = Jn[0][0]; J[0][1] = Jn[0][1]; J[1][0] = Jn[1][0]; J[1][1] = Jn[1][1];
+        res = rn;
+        if (step < 1e-15) break;
+      }
+      if (std::fabs(z[0]) <= 1 + 1e-9 && std::fabs(z[1]) <= 1 + 1e-9 &&
+          res <= 1e-12 * (1 + std::fabs(x[0]) + std::fabs(x[1]))) {
+        xi[0] = z[0]; xi[1] = z[1];
+        return;
+      }
+    }
+    xi[0] = xi[1] = std::nan("");   // no preimage: the mesh does not conform
   }
 };
 
-bool setup(Problem& P, int etype, int p, int nq1, int64_t E, const double* xyz, const int64_t* vid) {
+bool setup(Problem& P, int etype, int p, int nq1, int64_t E, const double* xyz, const int64_t* vid,
+           int pg = 0, const double* xgeo = nullptr, const unsigned char* bc = nullptr) {
   P.ref.init(etype, p, nq1);
   P.err.init(etype, p, p + 3);
   P.E = E;
+  if (pg > 0) {
+    if (etype != QUAD || !xgeo || pg > 15) { P.msg = "oracle: curved elements are quadrilaterals of degree <= 15"; return false; }
+    P.pg = pg;
+    P.xgeo.assign(xgeo, xgeo + (size_t)E * (pg + 1) * (pg + 1) * 2);
+  }
+  if (bc) P.bc.assign(bc, bc + (size_t)E * P.ref.nf);
   const int nd = P.ref.nd, nv = P.ref.nv, nf = P.ref.nf;
   P.v0.assign(E * 3, 0); P.A.assign(E * 9, 0); P.Ainv.assign(E * 9, 0);
   P.Jinv.assign(E * 9, 0); P.detJ.assign(E, 0);
@@ -604,7 +747,7 @@ bool setup(Problem& P, int etype, int p, int nq1, int64_t E, const double* xyz, 
     for (int k = 0; k < nd; ++k)
       for (int d = 0; d < nd; ++d) M[d][k] = X[P.ref.axisv[k] * nd + d] - X[d];
     // affine elements only: every vertex must be the affine image of its reference vertex
-    if (etype != TRI)
+    if (etype != TRI && !P.curved())
       for (int v = 0; v < nv; ++v)
         for (int d = 0; d < nd; ++d) {
           double e = X[d];
@@ -617,7 +760,7 @@ bool setup(Problem& P, int etype, int p, int nq1, int64_t E, const double* xyz, 
     double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
                  M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
                  M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
-    if (!(det > 0)) { P.msg = "oracle: element with non-positive orientation"; return false; }
+    if (!(det > 0) && !P.curved()) { P.msg = "oracle: element with non-positive orientation"; return false; }
     double inv[3][3];
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) {
@@ -690,6 +833,24 @@ bool setup(Problem& P, int etype, int p, int nq1, int64_t E, const double* xyz, 
       }
     }
   }
+  if (P.curved()) {
+    // the element maps must be positively oriented wherever they are evaluated
+    std::vector<std::array<double, 3>> pts(P.ref.qx);
+    pts.insert(pts.end(), P.err.qx.begin(), P.err.qx.end());
+    pts.insert(pts.end(), P.ref.node.begin(), P.ref.node.end());
+    for (int f = 0; f < nf; ++f)
+      for (size_t k = 0; k < P.ref.fs.size(); ++k) {
+        std::array<double, 3> xi = {0, 0, 0};
+        P.ref.face_xi(f, P.ref.fs[k].data(), xi.data());
+        pts.push_back(xi);
+      }
+    for (int64_t K = 0; K < E; ++K)
+      for (const auto& xi : pts) {
+        double Ji[9], det;
+        P.jac(K, xi.data(), Ji, det);
+        if (!(det > 0)) { P.msg = "oracle: curved element with non-positive Jacobian"; return false; }
+      }
+  }
   return true;
 }
 
@@ -712,11 +873,12 @@ void q_stage(const Problem& P, const S* u, int64_t K, S* q) {
   const int npe = R.npe, nd = R.nd, ncu = P.ncu();
   std::vector<S> rhs(ncu * nd * npe, S(0.0));
   std::vector<double> M(npe * npe, 0.0), phi(npe), dphi(npe * nd), gphi(npe * nd);
-  const double* Ji = &P.Jinv[K * 9];
   S uq[8];
   for (size_t qp = 0; qp < R.qx.size(); ++qp) {
     R.basis(R.qx[qp].data(), phi.data(), dphi.data());
-    double w = R.qw[qp] * P.detJ[K];
+    double Ji[9], dj;
+    P.jac(K, R.qx[qp].data(), Ji, dj);
+    double w = R.qw[qp] * dj;
     for (int i = 0; i < npe; ++i)
       for (int d = 0; d < nd; ++d) {
         double g = 0;
@@ -735,11 +897,12 @@ void q_stage(const Problem& P, const S* u, int64_t K, S* q) {
   for (int f = 0; f < R.nf; ++f) {
     const Face& F = P.faces[K * R.nf + f];
     for (int k = 0; k < R.nfq; ++k) {
-      double xi[3], x[3];
+      double xi[3], x[3], nrm[3], sJ;
       R.face_xi(f, R.fs[k].data(), xi);
       P.map(K, xi, x);
+      P.face_frame(K, f, xi, nrm, sJ);
       R.basis(xi, phi.data(), dphi.data());
-      double w = R.fw[k] * F.sJ;
+      double w = R.fw[k] * sJ;
       S um[8], uh[8];
       eval_u(P, u, K, phi.data(), um);
       if (F.nbr >= 0) {
@@ -750,6 +913,9 @@ void q_stage(const Problem& P, const S* u, int64_t K, S* q) {
         S up[8];
         eval_u(P, u, F.nbr, phin.data(), up);
         for (int c = 0; c < ncu; ++c) uh[c] = 0.5 * (um[c] + up[c]);
+      } else if (P.wall(K, f)) {
+        // no-slip adiabatic wall: trace (rho-, 0, 0, (rho E)-)
+        uh[0] = um[0]; uh[1] = 0.0; uh[2] = 0.0; uh[3] = um[3];
       } else {
         double g[8];
         P.model.exact(x, P.t, g);
@@ -758,7 +924,7 @@ void q_stage(const Problem& P, const S* u, int64_t K, S* q) {
       for (int c = 0; c < ncu; ++c)
         for (int d = 0; d < nd; ++d)
           for (int i = 0; i < npe; ++i)
-            rhs[(c * nd + d) * npe + i] = rhs[(c * nd + d) * npe + i] - w * uh[c] * F.n[d] * phi[i];
+            rhs[(c * nd + d) * npe + i] = rhs[(c * nd + d) * npe + i] - w * uh[c] * nrm[d] * phi[i];
     }
   }
   std::vector<int> piv;
@@ -790,14 +956,15 @@ void residual_elem(const Problem& P, const S* u, int64_t K, QOF qof, S* r) {
   const bool hasq = Mo.kind != EULER;
   for (int i = 0; i < ncu * npe; ++i) r[i] = 0.0;
   std::vector<double> phi(npe), dphi(npe * nd), gphi(npe * nd), phin(npe), dphin(npe * nd);
-  const double* Ji = &P.Jinv[K * 9];
   const S* qK = hasq ? qof(K) : nullptr;
   double a0 = 0, a1 = 0, a2 = 0;
   if (P.scheme == 1) { a0 = 1; a1 = -1; }
   if (P.scheme == 2) { a0 = 1.5; a1 = -2; a2 = 0.5; }
   for (size_t qp = 0; qp < R.qx.size(); ++qp) {
     R.basis(R.qx[qp].data(), phi.data(), dphi.data());
-    double w = R.qw[qp] * P.detJ[K];
+    double Ji[9], dj;
+    P.jac(K, R.qx[qp].data(), Ji, dj);
+    double w = R.qw[qp] * dj;
     for (int i = 0; i < npe; ++i)
       for (int d = 0; d < nd; ++d) {
         double g = 0;
@@ -831,11 +998,12 @@ void residual_elem(const Problem& P, const S* u, int64_t K, QOF qof, S* r) {
   for (int f = 0; f < R.nf; ++f) {
     const Face& F = P.faces[K * R.nf + f];
     for (int k = 0; k < R.nfq; ++k) {
-      double xi[3], x[3];
+      double xi[3], x[3], nrm[3], sJ;
       R.face_xi(f, R.fs[k].data(), xi);
       P.map(K, xi, x);
+      P.face_frame(K, f, xi, nrm, sJ);
       R.basis(xi, phi.data(), dphi.data());
-      double w = R.fw[k] * F.sJ;
+      double w = R.fw[k] * sJ;
       S um[8], qm[24], fh[8];
       eval_u(P, u, K, phi.data(), um);
       if (hasq) eval_q(P, qK, phi.data(), qm);
@@ -847,9 +1015,11 @@ void residual_elem(const Problem& P, const S* u, int64_t K, QOF qof, S* r) {
         S up[8], qp[24];
         eval_u(P, u, F.nbr, phin.data(), up);
         if (hasq) eval_q(P, qof(F.nbr), phin.data(), qp);
-        Mo.fhat_interior(um, up, qm, qp, F.n, fh);
+        Mo.fhat_interior(um, up, qm, qp, nrm, fh);
+      } else if (P.wall(K, f)) {
+        Mo.fhat_wall(um, qm, nrm, fh);
       } else {
-        Mo.fhat_boundary(um, qm, x, P.t, F.n, fh);
+        Mo.fhat_boundary(um, qm, x, P.t, nrm, fh);
       }
       for (int c = 0; c < ncu; ++c)
         for (int i = 0; i < npe; ++i) r[c * npe + i] = r[c * npe + i] + w * fh[c] * phi[i];
@@ -974,8 +1144,20 @@ struct orc_stats {
   double r0, rfinal;
 };
 
+void* orc_create_curved(int etype, int p, int nq1, int64_t E, const double* xyz, const int64_t* vid,
+                        int model, int cas, int nmu, const double* mu, int pg, const double* xgeo,
+                        const unsigned char* bc);
+
 void* orc_create(int etype, int p, int nq1, int64_t E, const double* xyz, const int64_t* vid,
                  int model, int cas, int nmu, const double* mu) {
+  return orc_create_curved(etype, p, nq1, E, xyz, vid, model, cas, nmu, mu, 0, nullptr, nullptr);
+}
+
+// pg > 0: curved quadrilaterals with map points xgeo [E][(pg+1)^2][2]; bc [E][nf]
+// (optional) marks wall faces with 1.
+void* orc_create_curved(int etype, int p, int nq1, int64_t E, const double* xyz, const int64_t* vid,
+                        int model, int cas, int nmu, const double* mu, int pg, const double* xgeo,
+                        const unsigned char* bc) {
   Problem* P = new Problem();
   P->model.kind = model;
   P->model.cas = cas;
@@ -997,7 +1179,7 @@ void* orc_create(int etype, int p, int nq1, int64_t E, const double* xyz, const 
     if (nmu > 2) P->model.pr = mu[2];
     P->model.tau = nmu > 3 ? mu[3] : 1.0 / re;
   }
-  if (!setup(*P, etype, p, nq1, E, xyz, vid)) { delete P; return nullptr; }
+  if (!setup(*P, etype, p, nq1, E, xyz, vid, pg, xgeo, bc)) { delete P; return nullptr; }
   return P;
 }
 
@@ -1083,7 +1265,9 @@ void orc_project(void* h, double t, double* u) {
     std::vector<double> M(npe * npe, 0.0), b(ncu * npe, 0.0);
     for (size_t qp = 0; qp < Q.qx.size(); ++qp) {
       R.basis(Q.qx[qp].data(), phi.data(), dphi.data());
-      double x[3], g[8], w = Q.qw[qp] * P->detJ[K];
+      double x[3], g[8], Ji[9], dj;
+      P->jac(K, Q.qx[qp].data(), Ji, dj);
+      const double w = Q.qw[qp] * dj;
       P->map(K, Q.qx[qp].data(), x);
       P->model.exact(x, t, g);
       for (int i = 0; i < npe; ++i) {
@@ -1127,7 +1311,9 @@ void orc_l2_error(void* h, const double* u, double t, double* eu, double* eq) {
     if (hasq) q_stage(*P, u, K, qK.data());
     for (size_t qp = 0; qp < Q.qx.size(); ++qp) {
       R.basis(Q.qx[qp].data(), phi.data(), dphi.data());
-      double x[3], g[8], w = Q.qw[qp] * P->detJ[K];
+      double x[3], g[8], Ji[9], dj;
+      P->jac(K, Q.qx[qp].data(), Ji, dj);
+      const double w = Q.qw[qp] * dj;
       P->map(K, Q.qx[qp].data(), x);
       P->model.exact(x, t, g);
       double uh[8];
@@ -1230,7 +1416,9 @@ void orc_mass(void* h, const double* u, double* Mu) {
   for (int64_t K = 0; K < P->E; ++K)
     for (size_t qp = 0; qp < R.qx.size(); ++qp) {
       R.basis(R.qx[qp].data(), phi.data(), dphi.data());
-      double w = R.qw[qp] * P->detJ[K], uq[8];
+      double Ji[9], dj, uq[8];
+      P->jac(K, R.qx[qp].data(), Ji, dj);
+      const double w = R.qw[qp] * dj;
       eval_u(*P, u, K, phi.data(), uq);
       for (int c = 0; c < ncu; ++c)
         for (int i = 0; i < npe; ++i) Mu[(K * ncu + c) * npe + i] += w * uq[c] * phi[i];

@@ -14,6 +14,15 @@ Mesh convention
   neighbours across the seam are found.
 * Vertex order: quadrilaterals and hexahedra list their vertices in
   lexicographic (tensor) order, x fastest; triangles counter-clockwise.
+
+Curved quadrilaterals additionally carry
+* ``pg``   the degree of the element map, and
+* ``xgeo`` float64 ``[E][(pg+1)^2][2]``: the physical positions of the
+  (pg+1)^2 equispaced reference points (-1 + 2a/pg, -1 + 2b/pg), a fastest;
+  the element map is their degree-pg Lagrange interpolant. Shared edges are
+  images of the same points, so neighbouring maps agree along them.
+* ``bc``   uint8 ``[E][4]``: kind of each boundary face, 1 = solid wall,
+  0 = data (Dirichlet or far field); ignored on interior faces.
 """
 from __future__ import annotations
 
@@ -32,6 +41,9 @@ class Mesh:
     xyz: np.ndarray      # [E][nv][nd] float64
     vid: np.ndarray      # [E][nv] int64
     name: str = ""
+    pg: int = 0                       # curved quadrilaterals: degree of the element map
+    xgeo: np.ndarray | None = None    # [E][(pg+1)^2][2] map points
+    bc: np.ndarray | None = None      # [E][4] uint8 boundary kinds
 
     @property
     def n_elem(self) -> int:
@@ -130,6 +142,136 @@ def tri_square(n: int, lo=(0.0, 0.0), hi=(1.0, 1.0), periodic=(False, False),
     if affine is not None:
         xyz = xyz @ np.asarray(affine, dtype=np.float64).T
     return Mesh(TRI, xyz, ids, f"tri{n}x{n}")
+
+
+def _curved_quads(params, node_id, n0, n1, G, pg, bc_of, name):
+    """Quadrilaterals of a structured n0 x n1 grid of parameter points: element (i, j)
+    (i fastest) has corners params[i..i+1, j..j+1]; its map sends reference point
+    (xi, eta) to G of the bilinear blend of its corner parameters, sampled at the
+    equispaced points of degree pg."""
+    t = np.linspace(-1.0, 1.0, pg + 1)
+    a = np.tile(t, pg + 1)                  # first reference coordinate, fastest
+    b = np.repeat(t, pg + 1)
+    w = np.stack([(1 - a) * (1 - b), (1 + a) * (1 - b), (1 - a) * (1 + b), (1 + a) * (1 + b)], 1) / 4
+    E = n0 * n1
+    xyz = np.empty((E, 4, 2))
+    ids = np.empty((E, 4), dtype=np.int64)
+    xgeo = np.empty((E, (pg + 1) ** 2, 2))
+    bc = np.zeros((E, 4), dtype=np.uint8)
+    e = 0
+    for j in range(n1):
+        for i in range(n0):
+            cor = [(i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1)]
+            P = np.array([params[c] for c in cor])            # [4][2] parameters
+            xyz[e] = G(P)
+            ids[e] = [node_id(*c) for c in cor]
+            xgeo[e] = G(w @ P)
+            bc[e] = bc_of(i, j)
+            e += 1
+    return Mesh(QUAD, xyz, ids, name, pg=pg, xgeo=xgeo, bc=bc)
+
+
+def warped_box(n: int | tuple, pg: int, lo=(0.0, 0.0), hi=(1.0, 1.0), periodic=(False, False),
+               amp: float = 0.1) -> Mesh:
+    """n[0] x n[1] curved quadrilaterals of the box [lo, hi]: the uniform grid moved by
+    the smooth displacement amp L / (2 pi) sin(2 pi X) sin(2 pi Y) in each direction
+    (X, Y the box coordinates scaled to [0, 1]). The displacement vanishes on the box
+    boundary and is periodic, so periodic meshes stay periodic."""
+    nx, ny = (n, n) if np.isscalar(n) else n
+    L = np.array(hi, dtype=np.float64) - np.array(lo, dtype=np.float64)
+    params = {(i, j): (lo[0] + i * L[0] / nx, lo[1] + j * L[1] / ny) for j in range(ny + 1) for i in range(nx + 1)}
+
+    def G(P):
+        P = np.atleast_2d(P)
+        X = (P[:, 0] - lo[0]) / L[0]
+        Y = (P[:, 1] - lo[1]) / L[1]
+        s = amp / (2 * np.pi) * np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y)
+        return np.stack([P[:, 0] + L[0] * s, P[:, 1] + L[1] * s], 1)
+    vid = _grid_ids((nx, ny), periodic)
+    return _curved_quads(params, vid, nx, ny, G, pg, lambda i, j: (0, 0, 0, 0), f"warped{nx}x{ny}")
+
+
+def o_grid(n_r: int, n_theta: int, pg: int, r0: float = 0.5, outer=("rect", (-10.0, 30.0, -10.0, 10.0)),
+           first: float | None = None, jitter: float = 0.0, seed: int = 7, wall: bool = True,
+           outer_wall: bool = False) -> Mesh:
+    """Curved quadrilaterals between the circle of radius r0 about the origin and an
+    outer boundary: ("circle", R) or ("rect", (x0, x1, y0, y1)) around the origin.
+
+    Parameter grid: s_j in [0, 1] across the layer (j = 0 on the circle) and the angle
+    theta_i = 2 pi i / n_theta. A point (s, theta) lies on the ray at angle theta,
+    a fraction s of the way from the circle to the outer boundary. With ``first`` the
+    s-spacing grows geometrically from a first layer of that physical thickness
+    (advancing layers); otherwise it is uniform. ``jitter`` moves every parameter
+    point off both boundaries by up to +- jitter/2 of the local spacing in each
+    direction (seeded, numpy PCG64). The first reference axis runs across the layer
+    (outward), the second along theta, so every element is positively oriented.
+    Faces on the circle are walls when ``wall`` is set; outer faces carry data unless
+    ``outer_wall`` is set."""
+    kind, spec = outer
+
+    def radius(th):
+        c, s = np.cos(th), np.sin(th)
+        if kind == "circle":
+            return np.full_like(th, float(spec))
+        x0, x1, y0, y1 = spec
+        with np.errstate(divide="ignore", invalid="ignore"):
+            tx = np.where(c > 0, x1 / c, np.where(c < 0, x0 / c, np.inf))
+            ty = np.where(s > 0, y1 / s, np.where(s < 0, y0 / s, np.inf))
+        return np.minimum(tx, ty)
+
+    if first is None:
+        sj = np.linspace(0.0, 1.0, n_r + 1)
+    else:
+        # thickness of the layer along the ray with the smallest span sets the growth
+        span = float(radius(np.linspace(0, 2 * np.pi, 721)).min() - r0)
+        h0 = first / span
+        lo_g, hi_g = 1.0 + 1e-12, 2.0
+        for _ in range(200):   # bisection for the ratio g with h0 (g^n - 1) / (g - 1) = 1
+            g = 0.5 * (lo_g + hi_g)
+            if h0 * (g ** n_r - 1) / (g - 1) > 1.0:
+                hi_g = g
+            else:
+                lo_g = g
+        sj = np.concatenate([[0.0], np.cumsum(h0 * g ** np.arange(n_r))])
+        sj /= sj[-1]
+    rng = np.random.default_rng(seed)
+    params = {}
+    for j in range(n_r + 1):
+        ds = (sj[min(j + 1, n_r)] - sj[max(j - 1, 0)]) / 2
+        for i in range(n_theta):
+            s, th = sj[j], 2 * np.pi * i / n_theta
+            if jitter and 0 < j < n_r:
+                s += jitter * ds * (rng.uniform() - 0.5)
+                th += jitter * (2 * np.pi / n_theta) * (rng.uniform() - 0.5)
+            params[(j, i)] = (s, th)
+    for j in range(n_r + 1):      # the seam: the same points one turn on
+        s, th = params[(j, 0)]
+        params[(j, n_theta)] = (s, th + 2 * np.pi)
+
+    def G(P):
+        P = np.atleast_2d(P)
+        s, th = P[:, 0], P[:, 1]
+        r = r0 + s * (radius(th) - r0)
+        return np.stack([r * np.cos(th), r * np.sin(th)], 1)
+
+    def node_id(j, i):
+        return (i % n_theta) + n_theta * j
+    # element (j, i): first reference axis across the layer (j), second along theta (i)
+    par = {(j, i): params[(j, i)] for j in range(n_r + 1) for i in range(n_theta + 1)}
+    m = _curved_quads(par, node_id, n_r, n_theta, G, pg,
+                      lambda j, i: (1 if (wall and j == 0) else 0, 1 if (outer_wall and j == n_r - 1) else 0, 0, 0),
+                      f"ogrid{n_r}x{n_theta}")
+    # elements ordered with theta fastest for locality along the layers
+    order = np.arange(n_r * n_theta).reshape(n_theta, n_r).T.ravel()
+    return Mesh(QUAD, m.xyz[order], m.vid[order], m.name, pg=pg, xgeo=m.xgeo[order], bc=m.bc[order])
+
+
+def cylinder_mesh(n_r: int = 100, n_theta: int = 400, pg: int = 3, seed: int = 7) -> Mesh:
+    """Flow past a cylinder: radius 0.5 about the origin in [-10, 30] x [-10, 10],
+    n_r x n_theta curved quadrilaterals (40,000 by default) in advancing layers from a
+    first layer of thickness 0.01, interior nodes jittered by +- 10% of the spacing."""
+    return o_grid(n_r, n_theta, pg, 0.5, ("rect", (-10.0, 30.0, -10.0, 10.0)), first=0.01, jitter=0.2,
+                  seed=seed)
 
 
 def random_vector(n: int, seed: int, scale: float = 1.0) -> np.ndarray:

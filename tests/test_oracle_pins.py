@@ -410,3 +410,129 @@ def test_bf16_rounding_matches_torch_and_ties_to_even():
     assert omlp.round_bf16(1.0 + ulp / 2) == 1.0                  # tie -> even (1.0)
     assert omlp.round_bf16(1.0 + 3 * ulp / 2) == 1.0 + 2 * ulp    # tie -> even (1 + 2 ulp)
     assert omlp.round_bf16(1.0 + 0.6 * ulp) == 1.0 + ulp
+
+
+# ------------------------------------------------------- curved quadrilaterals
+def _as_curved(mesh, pg):
+    """The same affine mesh described by degree-pg map points (equispaced, a fastest)."""
+    t = np.linspace(-1.0, 1.0, pg + 1)
+    a, b = np.tile(t, pg + 1), np.repeat(t, pg + 1)
+    w = np.stack([(1 - a) * (1 - b), (1 + a) * (1 - b), (1 - a) * (1 + b), (1 + a) * (1 + b)], 1) / 4
+    return synth.Mesh(mesh.etype, mesh.xyz, mesh.vid, mesh.name, pg=pg, xgeo=np.einsum("pv,evd->epd", w, mesh.xyz))
+
+
+@pytest.mark.parametrize("model,pg", [(oracle.CONVDIFF, 1), (oracle.NS, 3)])
+def test_curved_path_on_affine_elements_equals_affine_path(model, pg):
+    """Map points placed by the affine map: per-point Jacobians, normals and the
+    Newton inverse map give the affine path's residual."""
+    mesh = synth.quad_box((4, 3), hi=(10.0, 10.0), periodic=(True, False), affine=SHEAR2)
+    mu = (0.1, 0.2, 1.0, 0.5) if model == oracle.CONVDIFF else NS_MU
+    case = oracle.CASE_SINSIN if model == oracle.CONVDIFF else oracle.CASE_VORTEX
+    oa = oracle.Oracle(mesh, 2, model, case, mu)
+    oc = oracle.Oracle(_as_curved(mesh, pg), 2, model, case, mu)
+    u = (synth.random_euler_state(mesh.n_elem, oa.npe, 4) if model == oracle.NS
+         else synth.random_vector(oa.ndof, 4))
+    ra = oa.residual(u)
+    assert np.linalg.norm(oc.residual(u) - ra) <= 1e-13 * np.linalg.norm(ra)
+
+
+@pytest.mark.parametrize("pg", [1, 2, 3])
+def test_curved_mass_integrates_the_area(pg):
+    """sum_ij M_ij = integral of det J: the warped elements tile the box exactly (the
+    displacement vanishes on its boundary and shared edges conform), so the total is
+    the box area; per element it is positive."""
+    mesh = synth.warped_box((5, 4), pg, hi=(3.0, 2.0), amp=0.15)
+    o = oracle.Oracle(mesh, 3, oracle.POISSON, oracle.CASE_ZERO)
+    m = o.mass(np.ones(o.ndof)).reshape(mesh.n_elem, o.npe)
+    assert abs(m.sum() - 6.0) < 1e-12
+    assert (m.sum(1) > 0).all()
+
+
+@pytest.mark.parametrize("model", [oracle.EULER, oracle.NS])
+@pytest.mark.parametrize("which", ["warped_periodic", "warped_farfield", "ogrid_farfield"])
+def test_curved_free_stream(model, which):
+    """A uniform state is preserved on curved isoparametric quadrilaterals: in 2-D the
+    metric terms det J J^-1 have the map's degree, so the chosen quadrature integrates
+    the discrete divergence theorem exactly."""
+    if which == "ogrid_farfield":
+        mesh = synth.o_grid(3, 12, 3, outer=("circle", 2.0), jitter=0.3, wall=False)
+    else:
+        mesh = synth.warped_box(4, 3, hi=(10.0, 10.0), periodic=(which == "warped_periodic",) * 2, amp=0.2)
+    mu = (1.4,) if model == oracle.EULER else NS_MU
+    o = oracle.Oracle(mesh, 3, model, oracle.CASE_CONST, mu)
+    u = o.interpolate()
+    assert np.abs(o.residual(u)).max() < 1e-12
+
+
+def test_curved_conservation_periodic():
+    mesh = synth.warped_box(3, 2, hi=(2.0, 2.0), periodic=(True, True), amp=0.2)
+    for model, mu, case in ((oracle.CONVDIFF, (0.1, 0.2, 1.0, 0.5), oracle.CASE_ZERO),
+                            (oracle.NS, NS_MU, oracle.CASE_CONST)):
+        o = oracle.Oracle(mesh, 2, model, case, mu)
+        u = (synth.random_euler_state(mesh.n_elem, o.npe, 3) if model == oracle.NS
+             else synth.random_vector(o.ndof, 3))
+        r = o.residual(u).reshape(mesh.n_elem, o.ncu, o.npe)
+        assert np.all(np.abs(r.sum(axis=(0, 2))) <= 1e-13 * np.abs(r).sum())
+
+
+@pytest.mark.parametrize("model", [oracle.EULER, oracle.NS])
+def test_wall_gas_at_rest(model):
+    """Gas at rest between two circular walls is an exact steady solution: the wall
+    flux carries only the pressure, and the viscous and penalty terms vanish."""
+    mesh = synth.o_grid(3, 12, 3, outer=("circle", 2.0), jitter=0.3, outer_wall=True)
+    o = oracle.Oracle(mesh, 3, model, oracle.CASE_REST, (1.4,) if model == oracle.EULER else NS_MU)
+    assert np.abs(o.residual(o.interpolate())).max() < 1e-12
+
+
+def test_walls_conserve_mass_and_energy():
+    """With walls all round, no mass or energy crosses the boundary: the density and
+    energy residuals sum to zero for any state (momentum feels the wall pressure)."""
+    mesh = synth.o_grid(3, 12, 2, outer=("circle", 2.0), jitter=0.3, outer_wall=True)
+    o = oracle.Oracle(mesh, 2, oracle.NS, oracle.CASE_REST, NS_MU)
+    u = synth.random_euler_state(mesh.n_elem, o.npe, 8)
+    r = o.residual(u).reshape(mesh.n_elem, 4, o.npe)
+    tot = r.sum(axis=(0, 2))
+    scale = np.abs(r).sum(axis=(0, 2))
+    assert abs(tot[0]) <= 1e-13 * scale[0] and abs(tot[3]) <= 1e-13 * scale[3]
+    assert abs(tot[1]) > 1e-6 * scale[1]
+
+
+def test_curved_wall_jvp_matches_complex_step():
+    """J.v through curved geometry, the wall trace and the wall flux."""
+    mesh = synth.o_grid(2, 8, 3, outer=("circle", 2.0), jitter=0.3)
+    o = oracle.Oracle(mesh, 2, oracle.NS, oracle.CASE_CYLINDER, NS_MU)
+    u = synth.random_euler_state(mesh.n_elem, o.npe, 12)
+    u = u.reshape(mesh.n_elem, 4, o.npe)
+    u[:, 3] += 15.0                                 # pressure of the Mach 0.2 free stream
+    u = u.ravel()
+    v = synth.random_vector(o.ndof, 13)
+    J = o.jacobian_cs(u)
+    jv = o.jvp(u, v)
+    assert np.linalg.norm(jv - J @ v) <= 1e-13 * np.linalg.norm(J @ v)
+
+
+def test_curved_annulus_convergence():
+    """Poisson on the annulus 0.5 < r < 1 with curved maps of degree p = 2: u converges
+    at order p + 1 (even p; a wrong metric term would stall it)."""
+    errs = []
+    for n in (4, 8, 16):
+        mesh = synth.o_grid(n, 4 * n, 2, outer=("circle", 1.0), wall=False)
+        o = oracle.Oracle(mesh, 2, oracle.POISSON, oracle.CASE_SINSIN, (1.0, 1.0))
+        errs.append(o.l2_error(_solve_linear(o)))
+    e = np.array(errs)
+    assert np.log2(e[-2, 0] / e[-1, 0]) > 2.7, e
+
+
+def test_curved_annulus_area():
+    """sum_ij M_ij on the annulus 0.5 < r < 2: straight-sided maps give exactly the area
+    between the two inscribed regular polygons, (n/2) sin(2 pi / n) (R^2 - r0^2); cubic
+    maps approach pi (R^2 - r0^2) at order >= 4 in the angular spacing."""
+    def area(pg, n):
+        mesh = synth.o_grid(2, n, pg, outer=("circle", 2.0), wall=False)
+        o = oracle.Oracle(mesh, 3, oracle.POISSON, oracle.CASE_ZERO)
+        return o.mass(np.ones(o.ndof)).sum()
+    for n in (8, 12):
+        assert abs(area(1, n) - n / 2 * np.sin(2 * np.pi / n) * 3.75) < 1e-12
+    exact = np.pi * 3.75
+    e1, e2 = abs(area(3, 8) - exact), abs(area(3, 16) - exact)
+    assert e2 < e1 and np.log2(e1 / e2) > 3.8, (e1, e2)
