@@ -50,7 +50,9 @@ enum {
   LDG_CASE_LINEAR = 4,  /* a fixed linear polynomial (patch test) */
   LDG_CASE_VORTEX = 5,  /* isentropic vortex, strength 5, centre (5,5), velocity (1,1), period 10 */
   LDG_CASE_CONST = 6,   /* uniform Euler free stream rho = 1, v = (1,1), p = 1 */
-  LDG_CASE_ROTATION = 7 /* rigid rotation v = (-y, x)/2, rho = 1 + x/10 + y/20, internal energy 2 */
+  LDG_CASE_ROTATION = 7, /* rigid rotation v = (-y, x)/2, rho = 1 + x/10 + y/20, internal energy 2 */
+  LDG_CASE_CYLINDER = 8, /* cylinder free stream rho = 1, v = (1, 0), Mach 0.2 (p = 1 / (gamma 0.04)) */
+  LDG_CASE_REST = 9      /* gas at rest rho = 1, v = 0, p = 1 */
 };
 
 typedef enum {
@@ -60,7 +62,7 @@ typedef enum {
   LDG_ERR_UNSUPPORTED = -3,  /* no compiled kernel for this (element, p, quadrature, model) */
   LDG_ERR_NONFINITE = -4,    /* NaN/Inf met in a residual or Krylov quantity */
   LDG_ERR_MAXIT = -5,        /* iteration limit reached before the tolerance */
-  LDG_ERR_MESH = -6          /* mesh rejected: non-affine, inverted or non-conforming */
+  LDG_ERR_MESH = -6          /* mesh rejected: non-affine without a curved map, inverted or non-conforming */
 } ldg_status;
 
 enum { LDG_STEADY = 0, LDG_BDF1 = 1, LDG_BDF2 = 2 };
@@ -70,12 +72,28 @@ enum { LDG_STEADY = 0, LDG_BDF1 = 1, LDG_BDF2 = 2 };
  * hexahedra list vertices in lexicographic order (x fastest), triangles
  * counter-clockwise. Faces whose sorted vertex ids match are neighbours; a
  * periodic mesh shares ids across the period while each element keeps its own
- * (unwrapped) coordinates. Faces without a partner are boundary faces. */
+ * (unwrapped) coordinates. Faces without a partner are boundary faces.
+ *
+ * Curved quadrilaterals (geom_order = pg > 0): element K's map is the degree-pg
+ * Lagrange interpolant of the points xgeo [n_elem][(pg+1)^2][2] (host) placed at
+ * the equispaced reference points (-1 + 2a/pg, -1 + 2b/pg), a fastest; its corner
+ * points must equal xyz, and neighbouring maps must agree along shared edges
+ * (checked at the face quadrature points: LDG_ERR_MESH otherwise). The geometry
+ * is sampled at the quadrature points once, at creation (metrics, normals and
+ * the element mass matrices, whose inverses the q-stage applies). geom_order = 0
+ * (xgeo null): affine elements.
+ * bc [n_elem][n_faces] (host, optional): 1 marks a boundary face as a no-slip
+ * adiabatic wall for Euler / Navier-Stokes (trace (rho, 0, 0, rho E) from inside,
+ * pressure flux, viscous momentum flux and penalty); other boundary faces take the
+ * case's data (Dirichlet or far field). Faces are numbered 2 * axis + side. */
 typedef struct {
   int elem_type;
   int64_t n_elem;
   const double* xyz;
   const int64_t* vid;
+  int geom_order;
+  const double* xgeo;
+  const unsigned char* bc;
 } ldg_mesh_desc;
 
 /* Model and parameters mu (Section 2.1):

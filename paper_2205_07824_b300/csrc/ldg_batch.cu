@@ -408,8 +408,9 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
   b->m = o.gmres_m;
   b->pc = o.precond == LDG_PC_BJACOBI;
   b->n_inst = n_inst;
-  // groups keyed by (element, p, quadrature, model), instances in caller order within a group
-  std::map<std::tuple<int, int, int, int>, std::vector<int>> keyed;
+  // groups keyed by (element, p, quadrature, model, curved-map degree), instances in
+  // caller order within a group
+  std::map<std::tuple<int, int, int, int, int>, std::vector<int>> keyed;
   for (int i = 0; i < n_inst; ++i) {
     const ldg_mesh_desc& M = meshes[i];
     if (!M.xyz || !M.vid || M.n_elem <= 0 || M.elem_type < 0 || M.elem_type > 2)
@@ -417,7 +418,9 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
     if (models[i].model < 0 || models[i].model > 3)
       return bfail(b, LDG_ERR_ARG, "instance " + std::to_string(i) + ": bad model");
     const int nq = opts && opts->nq1 > 0 ? opts->nq1 : default_nq(M.elem_type, models[i].model, p[i]);
-    keyed[std::make_tuple(M.elem_type, p[i], nq, models[i].model)].push_back(i);
+    if (M.geom_order > 0 && !M.xgeo)
+      return bfail(b, LDG_ERR_ARG, "instance " + std::to_string(i) + ": curved mesh without map points");
+    keyed[std::make_tuple(M.elem_type, p[i], nq, models[i].model, std::max(0, M.geom_order))].push_back(i);
   }
   b->user_off.assign(n_inst, 0);
   b->user_n.assign(n_inst, 0);
@@ -426,7 +429,8 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
   int64_t off = 0;
   for (auto& kv : keyed) {
     BGroup g;
-    std::tie(g.etype, g.p, g.nq, g.model) = kv.first;
+    int pg = 0;
+    std::tie(g.etype, g.p, g.nq, g.model, pg) = kv.first;
     const std::vector<int>& ids = kv.second;
     const int nv = verts_per_elem(g.etype), dim = g.etype == LDG_HEX ? 3 : 2;
     int64_t E = 0;
@@ -435,6 +439,11 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
     std::vector<double> xyz;
     std::vector<int64_t> vid;
     std::vector<int> inst;
+    std::vector<double> xgeo;            // curved groups: map points, concatenated
+    std::vector<unsigned char> bc;       // wall marks (0 where an instance gives none)
+    const int nfc = 2 * dim + (g.etype == LDG_TRI ? -1 : 0);
+    bool any_bc = false;
+    for (int i : ids) any_bc |= meshes[i].bc != nullptr;
     xyz.reserve((size_t)E * nv * dim);
     vid.reserve((size_t)E * nv);
     inst.reserve(E);
@@ -451,10 +460,16 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
       }
       vshift += vmax + 1;
       inst.insert(inst.end(), (size_t)M.n_elem, seg);
+      if (pg > 0) xgeo.insert(xgeo.end(), M.xgeo, M.xgeo + (size_t)M.n_elem * (pg + 1) * (pg + 1) * 2);
+      if (any_bc) {
+        if (M.bc) bc.insert(bc.end(), M.bc, M.bc + (size_t)M.n_elem * nfc);
+        else bc.insert(bc.end(), (size_t)M.n_elem * nfc, (unsigned char)0);
+      }
       b->seg_user.push_back(i);
       mtab.push_back(make_params(&models[i]));
     }
-    ldg_mesh_desc um{g.etype, E, xyz.data(), vid.data()};
+    ldg_mesh_desc um{g.etype, E, xyz.data(), vid.data(), pg, pg > 0 ? xgeo.data() : nullptr,
+                     any_bc ? bc.data() : nullptr};
     ldg_model_desc gm = models[ids[0]];
     ldg_options go = o;
     go.nq1 = g.nq;

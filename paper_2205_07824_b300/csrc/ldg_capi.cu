@@ -35,6 +35,9 @@ void register_all(std::vector<KernelSet>& reg) {
   register_tri_t<Tile1>(reg); register_quad_t<Tile1>(reg); register_hex_t<Tile1>(reg); register_ns_t<Tile1>(reg);
   register_tri_t<Tile2>(reg); register_quad_t<Tile2>(reg); register_hex_t<Tile2>(reg); register_ns_t<Tile2>(reg);
   register_tri_t<Tile3>(reg); register_quad_t<Tile3>(reg); register_hex_t<Tile3>(reg); register_ns_t<Tile3>(reg);
+  // curved quadrilaterals: two tile shapes
+  register_curved_scalar_t<Tile0>(reg); register_curved_gas_t<Tile0>(reg);
+  register_curved_scalar_t<Tile1>(reg); register_curved_gas_t<Tile1>(reg);
 }
 long long& launch_counter() {
   static long long n = 0;
@@ -75,8 +78,9 @@ int fail(ldg_ctx* c, int code, const std::string& msg) {
   } while (0)
 
 // ---------------------------------------------------------------- aux kernels
+// xnode (curved elements): physical node coordinates [E][npe][dim]; else the affine map
 __global__ void k_interp_nodes(int dim, int npe, int ncu, int64_t E, const double* geo, int GEO, const double* xn,
-                               ModelParams mp, double t, double* u) {
+                               ModelParams mp, double t, double* u, const double* xnode) {
   int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (it >= E * npe) return;
   int64_t e = it / npe;
@@ -86,7 +90,7 @@ __global__ void k_interp_nodes(int dim, int npe, int ncu, int64_t E, const doubl
   for (int d = 0; d < dim; ++d) {
     double s = g[dim * dim + 1 + d];
     for (int k = 0; k < dim; ++k) s += g[dim * dim + 1 + dim + d * dim + k] * xn[n * dim + k];
-    x[d] = s;
+    x[d] = xnode ? xnode[it * dim + d] : s;
   }
   if (dim == 2) exact_state<2>(mp, ncu, x, t, st);
   else exact_state<3>(mp, ncu, x, t, st);
@@ -106,6 +110,7 @@ KArgs base_args(ldg_ctx* c) {
   a.geo = c->d_geo; a.nbr = c->d_nbr; a.nbf = c->d_nbf; a.ops = c->d_ops; a.opsf = c->d_opsf; a.perm = c->d_perm;
   a.a0dt = c->a0dt; a.t = c->t; a.mp = c->mp; a.E = (int)c->E;
   a.inst = c->ext_inst; a.mtab = c->ext_mtab; a.t_dev = c->d_t;
+  a.cgeo = c->d_cgeo; a.cgeof = c->d_cgeof; a.cx = c->d_cx; a.minv = c->d_minv; a.minvf = c->d_minvf;
   a.blk_col = -1;
   return a;
 }
@@ -272,7 +277,16 @@ int do_blocks(ldg_ctx* ctx, const double* u, int prec, double* blocks) {
   const int nloc = ctx->nloc;
   const int64_t E = ctx->E;
   if (!ctx->ks->qstage) {
-    if (prec == LDG_FP32) {
+    if (prec == LDG_FP32 && !ctx->ks->blocks32) {
+      // curved elements: one unit tangent per launch in FP32 arithmetic
+      for (int l = 0; l < nloc; ++l) {
+        KArgs a = base_args(ctx);
+        a.u = u; a.v = u; a.out = nullptr;
+        a.blk_col = l;
+        a.blk_out = blocks;
+        CK(ctx->ks->residual32(MODE_JV, a, ctx->stream));
+      }
+    } else if (prec == LDG_FP32) {
       // dual numbers with BLK_KT unit tangents on every element and none on its neighbours;
       // the default tile (the J.v's tuned tile suits one tangent, not eight)
       const KernelSet* k0 = find_set(ctx, 0);
@@ -821,7 +835,9 @@ __global__ void k_tune_pattern(double* v, int64_t n) {
 
 const KernelSet* find_set(const ldg_ctx* ctx, int tile) {
   for (const KernelSet& k : registry())
-    if (k.etype == ctx->etype && k.p == ctx->p && k.nq == ctx->nq && k.model == ctx->model && k.tile == tile) return &k;
+    if (k.etype == ctx->etype && k.p == ctx->p && k.nq == ctx->nq && k.model == ctx->model && k.tile == tile &&
+        k.curved == (ctx->pg > 0))
+      return &k;
   return nullptr;
 }
 
@@ -830,7 +846,8 @@ int autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms) {
   const int prec = ctx->opt.krylov_precision;
   int eb = 0;
   while ((int64_t(1) << eb) < ctx->E) ++eb;
-  const auto key = std::make_tuple(ctx->etype, ctx->p, ctx->nq, ctx->model, prec, eb);
+  // (curved elements are keyed apart as element type 3)
+  const auto key = std::make_tuple(ctx->pg > 0 ? 3 : ctx->etype, ctx->p, ctx->nq, ctx->model, prec, eb);
   if (best_ms) *best_ms = -1.0;
   if (!force) {
     auto it = cache.find(key);
@@ -845,7 +862,9 @@ int autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms) {
   // candidates: the compiled tiles with distinct elements-per-CTA counts
   std::vector<const KernelSet*> cand;
   for (const KernelSet& k : registry()) {
-    if (k.etype != ctx->etype || k.p != ctx->p || k.nq != ctx->nq || k.model != ctx->model) continue;
+    if (k.etype != ctx->etype || k.p != ctx->p || k.nq != ctx->nq || k.model != ctx->model ||
+        k.curved != (ctx->pg > 0))
+      continue;
     bool dup = false;
     for (const KernelSet* c : cand) dup |= (c->ne_q == k.ne_q && c->ne_j == k.ne_j && c->ne_r == k.ne_r);
     if (!dup) cand.push_back(&k);
@@ -871,7 +890,8 @@ int autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms) {
     }
     const int GEO = ctx->dim == 2 ? Geo<2>::size(ctx->nf) : Geo<3>::size(ctx->nf);
     k_interp_nodes<<<grid_for(ctx->E * ctx->npe), 256, 0, ctx->stream>>>(ctx->dim, ctx->npe, ctx->ncu, ctx->E, ctx->d_geo,
-                                                                        GEO, ctx->d_xn, ctx->mp, ctx->t, u);
+                                                                        GEO, ctx->d_xn, ctx->mp, ctx->t, u,
+                                                                        ctx->d_xnode);
     k_tune_pattern<<<grid_for(n), 256, 0, ctx->stream>>>(v, n);
     count_launch();
     count_launch();
@@ -917,6 +937,8 @@ int ldg_destroy(ldg_ctx* ctx) {
   if (ctx->engine) batch_free(ctx->engine);
   cudaFree(ctx->d_ops); cudaFree(ctx->d_opsf); cudaFree(ctx->d_geo); cudaFree(ctx->d_nbr); cudaFree(ctx->d_nbf); cudaFree(ctx->d_perm);
   cudaFree(ctx->d_xn); cudaFree(ctx->d_q); cudaFree(ctx->d_dq); cudaFree(ctx->d_hist);
+  cudaFree(ctx->d_cgeo); cudaFree(ctx->d_cgeof); cudaFree(ctx->d_cx); cudaFree(ctx->d_minv); cudaFree(ctx->d_minvf);
+  cudaFree(ctx->d_xnode);
   cudaFree(ctx->d_V); cudaFree(ctx->d_r); cudaFree(ctx->d_w); cudaFree(ctx->d_res); cudaFree(ctx->d_x); cudaFree(ctx->d_small); cudaFree(ctx->d_part);
   cudaFree(ctx->d_flags); cudaFree(ctx->d_ticket); cudaFree(ctx->d_t);
   cudaFree(ctx->d_colour); cudaFree(ctx->d_blocks); cudaFree(ctx->d_binv); cudaFree(ctx->d_Z);
@@ -962,6 +984,8 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   ctx->dim = ctx->etype == LDG_HEX ? 3 : 2;
   const bool gas = ctx->model == LDG_EULER || ctx->model == LDG_NS;
   if (gas && ctx->dim != 2) { ldg_destroy(ctx); return LDG_ERR_UNSUPPORTED; }
+  ctx->pg = mesh->geom_order > 0 ? mesh->geom_order : 0;
+  if (ctx->pg > 0 && (ctx->etype != LDG_QUAD || !mesh->xgeo)) { ldg_destroy(ctx); return LDG_ERR_UNSUPPORTED; }
   ctx->ncu = gas ? 4 : 1;
   ldg_options o{};
   if (opts) o = *opts;
@@ -979,7 +1003,9 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   ctx->p = p; ctx->nq = o.nq1;
   ctx->mp = make_params(model);
   for (const KernelSet& k : registry())
-    if (!ctx->ks && k.etype == ctx->etype && k.p == p && k.nq == o.nq1 && k.model == ctx->model) ctx->ks = &k;
+    if (!ctx->ks && k.etype == ctx->etype && k.p == p && k.nq == o.nq1 && k.model == ctx->model &&
+        k.curved == (ctx->pg > 0))
+      ctx->ks = &k;
   if (!ctx->ks) {
     ctx->err = "no compiled kernel for element " + std::to_string(ctx->etype) + ", p " + std::to_string(p) +
                ", nq1 " + std::to_string(o.nq1) + ", model " + std::to_string(ctx->model);
@@ -990,7 +1016,21 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   MeshPrep mp_;
   std::string err;
   if (!build_ref_ops(ctx->etype, p, o.nq1, ref, err)) { ctx->err = err; *out = ctx; return LDG_ERR_ARG; }
-  if (!prepare_mesh(ref, mesh->n_elem, mesh->xyz, mesh->vid, mp_, err)) { ctx->err = err; *out = ctx; return LDG_ERR_MESH; }
+  if (!prepare_mesh(ref, mesh->n_elem, mesh->xyz, mesh->vid, mp_, err, ctx->pg, mesh->xgeo)) {
+    ctx->err = err;
+    *out = ctx;
+    return LDG_ERR_MESH;
+  }
+  CurvedPrep cp;
+  if (ctx->pg > 0 && !prepare_curved(ref, mesh->n_elem, ctx->pg, mesh->xgeo, cp, err)) {
+    ctx->err = err;
+    *out = ctx;
+    return LDG_ERR_MESH;
+  }
+  // wall faces (gas models): boundary faces marked 1 in mesh->bc become neighbour -2
+  if (mesh->bc && gas)
+    for (size_t i = 0; i < mp_.nbr.size(); ++i)
+      if (mp_.nbr[i] < 0 && mesh->bc[i] == 1) mp_.nbr[i] = -2;
   if (mesh->n_elem > (int64_t)0x7fffffff) { ctx->err = "too many elements"; *out = ctx; return LDG_ERR_ARG; }
   ctx->E = mesh->n_elem;
   ctx->npe = ref.npe; ctx->nf = ref.nf; ctx->nfq = ref.nfq;
@@ -1019,6 +1059,23 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   CK(cudaMemcpy(ctx->d_nbf, mp_.nbf.data(), mp_.nbf.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_perm, mp_.perm.data(), mp_.perm.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_xn, xn.data(), xn.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (ctx->pg > 0) {
+    auto up64 = [&](double** dst, const std::vector<double>& v) -> cudaError_t {
+      cudaError_t e = cudaMalloc(dst, v.size() * sizeof(double));
+      return e ? e : cudaMemcpy(*dst, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+    };
+    auto up32 = [&](float** dst, const std::vector<double>& v) -> cudaError_t {
+      std::vector<float> f(v.begin(), v.end());
+      cudaError_t e = cudaMalloc(dst, f.size() * sizeof(float));
+      return e ? e : cudaMemcpy(*dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
+    };
+    CK(up64(&ctx->d_cgeo, cp.geo));
+    CK(up32(&ctx->d_cgeof, cp.geo));
+    CK(up64(&ctx->d_cx, cp.x));
+    CK(up64(&ctx->d_minv, cp.minv));
+    CK(up32(&ctx->d_minvf, cp.minv));
+    CK(up64(&ctx->d_xnode, cp.xnode));
+  }
   if (ctx->ks->qstage) {
     CK(cudaMalloc(&ctx->d_q, n * ctx->dim * sizeof(double)));
     CK(cudaMalloc(&ctx->d_dq, n * ctx->dim * sizeof(double)));
@@ -1340,7 +1397,7 @@ int ldg_interpolate(ldg_ctx* ctx, double t, double* u) {
   if (!ctx || !ctx->ks || !u) return LDG_ERR_ARG;
   const int GEO = ctx->dim * ctx->dim * 2 + 1 + ctx->dim + ctx->nf * (ctx->dim + 1);
   k_interp_nodes<<<grid_for(ctx->E * ctx->npe), 256, 0, ctx->stream>>>(ctx->dim, ctx->npe, ctx->ncu, ctx->E, ctx->d_geo,
-                                                                      GEO, ctx->d_xn, ctx->mp, t, u);
+                                                                      GEO, ctx->d_xn, ctx->mp, t, u, ctx->d_xnode);
   count_launch();
   CK(cudaGetLastError());
   return LDG_OK;

@@ -27,6 +27,14 @@ struct ldg_ctx {
   unsigned char* d_nbf = nullptr;
   unsigned char* d_perm = nullptr;
   double* d_xn = nullptr;      // reference node coordinates [npe][dim]
+  // curved quadrilaterals (pg > 0): per-point geometry records (see CurvedPrep)
+  int pg = 0;
+  double* d_cgeo = nullptr;
+  float* d_cgeof = nullptr;
+  double* d_cx = nullptr;
+  double* d_minv = nullptr;
+  float* d_minvf = nullptr;
+  double* d_xnode = nullptr;   // [E][npe][dim] physical node coordinates
   double* d_q = nullptr;       // q(u) scratch [E][ncu][dim][npe]
   double* d_dq = nullptr;      // q(v) scratch
   double* d_hist = nullptr;    // BDF history term

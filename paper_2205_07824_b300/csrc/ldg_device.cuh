@@ -146,7 +146,7 @@ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 // ----------------------------------------------------------------- models
 enum { M_POISSON = 0, M_CONVDIFF = 1, M_EULER = 2, M_NS = 3 };
 enum { C_ZERO = 0, C_SINSIN = 1, C_EXPSIN = 2, C_POLY2 = 3, C_LINEAR = 4, C_VORTEX = 5, C_CONST = 6,
-       C_ROTATION = 7 };
+       C_ROTATION = 7, C_CYLINDER = 8, C_REST = 9 };
 
 // kappa: diffusivity, or the dynamic viscosity 1/Re of Navier-Stokes; tau: the
 // LDG jump penalty; pr: the Prandtl number (Navier-Stokes)
@@ -179,6 +179,12 @@ __device__ void exact_state(const ModelParams& mp, int ncu, const double* x, dou
       // zero strain rate and zero temperature gradient, so no viscous stress or heat flux
       const double rho = 1.0 + 0.1 * x[0] + 0.05 * x[1], ux = -0.5 * x[1], uy = 0.5 * x[0];
       g[0] = rho; g[1] = rho * ux; g[2] = rho * uy; g[3] = rho * (2.0 + 0.5 * (ux * ux + uy * uy));
+    } else if (mp.cas == C_CYLINDER) {
+      // cylinder free stream: rho = 1, v = (1, 0), Mach 0.2
+      const double p = 1.0 / (mp.gamma * 0.04);
+      g[0] = 1.0; g[1] = 1.0; g[2] = 0.0; g[3] = p / (mp.gamma - 1.0) + 0.5;
+    } else if (mp.cas == C_REST) {
+      g[0] = 1.0; g[1] = 0.0; g[2] = 0.0; g[3] = 1.0 / (mp.gamma - 1.0);
     } else {
       g[0] = 1.0; g[1] = 1.0; g[2] = 1.0; g[3] = 1.0 / (mp.gamma - 1.0) + 1.0;
     }
@@ -358,6 +364,16 @@ struct EulerModel {
     S up[4] = {S(g[0]), S(g[1]), S(g[2]), S(g[3])};
     fhat(um, up, qm, qm, n, fh, mp);
   }
+  // solid wall: the physical flux of the wall state (rho-, 0, 0, (rho E)-), i.e. the
+  // pressure (gamma - 1) (rho E)- on the momentum components only
+  template <class S, class R> __device__ static void fhat_wall(const S* um, const S*, const R* n, S* fh,
+                                                               const MPar<R>& mp) {
+    const S p = um[3] * (mp.gamma - R(1));
+    fh[0] = um[0] * R(0);
+    fh[1] = p * n[0];
+    fh[2] = p * n[1];
+    fh[3] = um[3] * R(0);
+  }
 };
 
 // 2-D compressible Navier-Stokes (Section 2.1): f = F(u) - F_v(u, grad u), the
@@ -419,6 +435,18 @@ struct NSModel {
 #pragma unroll
     for (int c = 0; c < 4; ++c) fh[c] = fh[c] - (vm[2 * c] * n[0] + vm[2 * c + 1] * n[1]) + (um[c] - g[c]) * mp.tau;
   }
+  // no-slip adiabatic wall: wall state ub = (rho-, 0, 0, (rho E)-); pressure flux,
+  // minus the viscous momentum flux F_v(ub, q-).n (no energy flux: zero velocity and
+  // zero heat flux), plus the penalty tau (u- - ub) on the momentum
+  template <class S, class R> __device__ static void fhat_wall(const S* um, const S* qm, const R* n, S* fh,
+                                                               const MPar<R>& mp) {
+    const S z = um[0] * R(0);
+    S ub[4] = {um[0], z, z, um[3]}, vb[8];
+    EulerModel::fhat_wall(um, qm, n, fh, mp);
+    viscous(ub, qm, vb, mp);
+#pragma unroll
+    for (int c = 1; c < 3; ++c) fh[c] = fh[c] - (vb[2 * c] * n[0] + vb[2 * c + 1] * n[1]) + um[c] * mp.tau;
+  }
 };
 
 // -------------------------------------------------------- element traits
@@ -428,6 +456,7 @@ struct NSModel {
 //             Bf[NFQ][NFN], WF[NFQ], SF[NFQ], Dnr[NPE][NPE], Dns[NPE][NPE], Minv[NPE][NPE], XN[NPE][2]
 template <int DIM_, int P_, int NQ_> struct TensorEl {
   static constexpr bool TENSOR = true;
+  static constexpr bool CURVED = false;   // affine (parallelogram / parallelepiped) geometry
   static constexpr int DIM = DIM_, P = P_, N1 = P_ + 1, NQ = NQ_;
   static constexpr int NPE = ipow(N1, DIM), NQV = ipow(NQ, DIM);
   static constexpr int NF = 2 * DIM, NFN = ipow(N1, DIM - 1), NFQ = ipow(NQ, DIM - 1);
@@ -449,8 +478,16 @@ template <int DIM_, int P_, int NQ_> struct TensorEl {
   }
 };
 
+// Curved quadrilateral: the tensor element's reference operators with per-point
+// geometry (the element map has its own degree; its metrics are sampled at the
+// quadrature points on the host).
+template <int P_, int NQ_> struct CurvedQuadEl : TensorEl<2, P_, NQ_> {
+  static constexpr bool CURVED = true;
+};
+
 template <int P_, int NQ_> struct TriEl {
   static constexpr bool TENSOR = false;
+  static constexpr bool CURVED = false;
   static constexpr int DIM = 2, P = P_, NQ = NQ_, N1 = P_ + 1;
   static constexpr int NPE = (P_ + 1) * (P_ + 2) / 2, NQV = NQ_ * NQ_;
   static constexpr int NF = 3, NFN = P_ + 1, NFQ = NQ_;

@@ -286,7 +286,119 @@ const std::vector<std::vector<int>>& face_vertices(int etype) {
 }
 }  // namespace
 
-bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* vid, MeshPrep& out, std::string& err) {
+namespace {
+// 1-D Lagrange basis on the m+1 equispaced points of [-1, 1] and its derivative at t
+void lagr_equi(int m, double t, double* l, double* dl) {
+  for (int a = 0; a <= m; ++a) {
+    const double ta = -1.0 + 2.0 * a / m;
+    double den = 1.0, num = 1.0, der = 0.0;
+    for (int b = 0; b <= m; ++b) {
+      if (b == a) continue;
+      const double tb = -1.0 + 2.0 * b / m;
+      den *= ta - tb;
+      der = der * (t - tb) + num;
+      num *= t - tb;
+    }
+    l[a] = num / den;
+    dl[a] = der / den;
+  }
+}
+// curved quadrilateral map: x and J[d][k] = d x_d / d xi_k at xi
+void curved_point(int pg, const double* X, const double* xi, double* x, double J[2][2]) {
+  double l0[16], d0[16], l1[16], d1[16];
+  lagr_equi(pg, xi[0], l0, d0);
+  lagr_equi(pg, xi[1], l1, d1);
+  x[0] = x[1] = 0.0;
+  J[0][0] = J[0][1] = J[1][0] = J[1][1] = 0.0;
+  for (int b = 0; b <= pg; ++b)
+    for (int a = 0; a <= pg; ++a) {
+      const double* P = X + (a + (pg + 1) * b) * 2;
+      for (int d = 0; d < 2; ++d) {
+        x[d] += P[d] * l0[a] * l1[b];
+        J[d][0] += P[d] * d0[a] * l1[b];
+        J[d][1] += P[d] * l0[a] * d1[b];
+      }
+    }
+}
+}  // namespace
+
+bool prepare_curved(const RefOps& R, int64_t E, int pg, const double* xgeo, CurvedPrep& out, std::string& err) {
+  if (R.etype != E_QUAD || pg < 1 || pg > 15 || !xgeo) {
+    err = "curved elements are quadrilaterals with map degree 1..15";
+    return false;
+  }
+  const int nq = R.nq, n1 = R.p + 1, npe = R.npe, nqv = R.nqv, nf = R.nf, nfq = R.nfq;
+  std::vector<double> gx, gw;
+  gauss_legendre(nq, gx, gw);
+  const double* B = R.blob.data();   // B[nq][n1]
+  out.rec = nqv * 5 + nf * nfq * 3;
+  out.xrec = nqv * 2 + nf * nfq * 2;
+  out.geo.assign((size_t)E * out.rec, 0.0);
+  out.x.assign((size_t)E * out.xrec, 0.0);
+  out.minv.assign((size_t)E * npe * npe, 0.0);
+  out.xnode.assign((size_t)E * npe * 2, 0.0);
+  std::vector<double> rn;
+  ref_nodes(R, rn);
+  const size_t mstride = (size_t)(pg + 1) * (pg + 1) * 2;
+  std::vector<double> M(npe * npe), Mi;
+  for (int64_t e = 0; e < E; ++e) {
+    const double* X = xgeo + e * mstride;
+    double* g = &out.geo[(size_t)e * out.rec];
+    double* xo = &out.x[(size_t)e * out.xrec];
+    std::fill(M.begin(), M.end(), 0.0);
+    for (int q1 = 0; q1 < nq; ++q1)
+      for (int q0 = 0; q0 < nq; ++q0) {
+        const int q = q0 + nq * q1;
+        const double xi[2] = {gx[q0], gx[q1]};
+        double x[2], J[2][2];
+        curved_point(pg, X, xi, x, J);
+        const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        if (!(det > 0.0)) { err = "curved element " + std::to_string(e) + " has a non-positive Jacobian"; return false; }
+        const double w = gw[q0] * gw[q1] * det;
+        // w det J (d xi_k / d x_d): the cofactors of J times the weight
+        g[q * 5 + 0] = gw[q0] * gw[q1] * J[1][1];
+        g[q * 5 + 1] = -gw[q0] * gw[q1] * J[0][1];
+        g[q * 5 + 2] = -gw[q0] * gw[q1] * J[1][0];
+        g[q * 5 + 3] = gw[q0] * gw[q1] * J[0][0];
+        g[q * 5 + 4] = w;
+        xo[q * 2] = x[0];
+        xo[q * 2 + 1] = x[1];
+        for (int i = 0; i < npe; ++i) {
+          const double pi = B[q0 * n1 + i % n1] * B[q1 * n1 + i / n1];
+          for (int j = 0; j < npe; ++j) M[i * npe + j] += w * pi * B[q0 * n1 + j % n1] * B[q1 * n1 + j / n1];
+        }
+      }
+    for (int n = 0; n < npe; ++n) {
+      double J[2][2];
+      curved_point(pg, X, &rn[n * 2], &out.xnode[((size_t)e * npe + n) * 2], J);
+    }
+    if (!invert(M, npe, Mi)) { err = "singular element mass matrix"; return false; }
+    std::copy(Mi.begin(), Mi.end(), out.minv.begin() + (size_t)e * npe * npe);
+    for (int f = 0; f < nf; ++f)
+      for (int k = 0; k < nfq; ++k) {
+        double xi[3], x[2], J[2][2];
+        ref_face_point(R, f, k, xi);
+        curved_point(pg, X, xi, x, J);
+        const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        if (!(det > 0.0)) { err = "curved element " + std::to_string(e) + " has a non-positive Jacobian"; return false; }
+        // Nanson: n sJ = +-det J J^{-T} e_axis = +- (row `axis` of the cofactor matrix)
+        const int ax = f >> 1;
+        const double sg = (f & 1) ? 1.0 : -1.0;
+        const double m0 = sg * (ax == 0 ? J[1][1] : -J[1][0]), m1 = sg * (ax == 0 ? -J[0][1] : J[0][0]);
+        const double sj = std::sqrt(m0 * m0 + m1 * m1);
+        double* fr = g + nqv * 5 + (f * nfq + k) * 3;
+        fr[0] = m0 / sj;
+        fr[1] = m1 / sj;
+        fr[2] = gw[k] * sj;
+        xo[nqv * 2 + (f * nfq + k) * 2] = x[0];
+        xo[nqv * 2 + (f * nfq + k) * 2 + 1] = x[1];
+      }
+  }
+  return true;
+}
+
+bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* vid, MeshPrep& out, std::string& err,
+                  int pg, const double* xgeo) {
   const int dim = R.dim, nf = R.nf;
   const int nv = R.etype == E_TRI ? 3 : (1 << dim);
   const int GEO = dim * dim + 1 + dim + dim * dim + nf * (dim + 1);
@@ -313,7 +425,7 @@ bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* 
     // J[d][k] = (x_{axis vertex k} - x_0)_d / 2
     for (int d = 0; d < dim; ++d)
       for (int k = 0; k < dim; ++k) J[d * dim + k] = 0.5 * (X[axis_vert[k] * dim + d] - X[d]);
-    if (R.etype != E_TRI) {
+    if (R.etype != E_TRI && pg == 0) {
       for (int vtx = 0; vtx < nv; ++vtx)
         for (int d = 0; d < dim; ++d) {
           double pr = X[d];
@@ -334,7 +446,7 @@ bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* 
       Ji[3] = (J[5] * J[6] - J[3] * J[8]) / det; Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det; Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
       Ji[6] = (J[3] * J[7] - J[4] * J[6]) / det; Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det; Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
     }
-    if (!(det > 0.0)) { err = "element " + std::to_string(e) + " has non-positive Jacobian"; return false; }
+    if (!(det > 0.0) && pg == 0) { err = "element " + std::to_string(e) + " has non-positive Jacobian"; return false; }
     double* g = &out.geo[(size_t)e * GEO];
     for (int i = 0; i < dim * dim; ++i) g[i] = Ji[i];
     g[dim * dim] = det;
@@ -391,6 +503,12 @@ bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* 
     const double* g = &out.geo[(size_t)e * GEO];
     for (int k = 0; k < R.nfq; ++k) {
       const double* xi = &fref[((size_t)f * R.nfq + k) * 3];
+      if (pg > 0) {
+        double x[2], J[2][2];
+        curved_point(pg, xgeo + (size_t)e * (pg + 1) * (pg + 1) * 2, xi, x, J);
+        for (int d = 0; d < 2; ++d) P[k * 3 + d] = x[d] + (shift ? shift[d] : 0.0);
+        continue;
+      }
       for (int d = 0; d < dim; ++d) {
         double s = g[dim * dim + 1 + d];
         for (int kk = 0; kk < dim; ++kk) s += g[dim * dim + 1 + dim + d * dim + kk] * xi[kk];

@@ -29,9 +29,24 @@ struct MeshPrep {
 
 // Geometry (Jacobians, normals, surface Jacobians by Nanson's formula) and face
 // connectivity with face-point orientation permutations, from per-element vertex
-// coordinates xyz [E][nv][dim] and topological vertex ids vid [E][nv].
+// coordinates xyz [E][nv][dim] and topological vertex ids vid [E][nv]. With pg > 0
+// the quadrilaterals are curved (map points xgeo, see prepare_curved): the affine
+// record is then not checked, and face points are matched through the curved maps.
 bool prepare_mesh(const RefOps& ref, int64_t E, const double* xyz, const int64_t* vid, MeshPrep& out,
-                  std::string& err);
+                  std::string& err, int pg = 0, const double* xgeo = nullptr);
+
+// Curved quadrilaterals: the element map is the degree-pg Lagrange interpolant of
+// the map points xgeo [E][(pg+1)^2][2] at the equispaced reference points
+// (-1 + 2a/pg, -1 + 2b/pg), a fastest. Sampled at the quadrature points:
+struct CurvedPrep {
+  int rec = 0, xrec = 0;
+  std::vector<double> geo;    // [E][rec]: per volume point w det J d xi_k / d x_d (k, d) and w det J;
+                              //           per face point the outward unit normal and w sJ
+  std::vector<double> x;      // [E][xrec]: physical coordinates of the volume, then face points
+  std::vector<double> minv;   // [E][npe][npe]: inverse element mass matrices
+  std::vector<double> xnode;  // [E][npe][2]: physical coordinates of the element's nodes
+};
+bool prepare_curved(const RefOps& ref, int64_t E, int pg, const double* xgeo, CurvedPrep& out, std::string& err);
 
 // Reference coordinates of face point k of face f and of volume point q (for host-side projection).
 void ref_face_point(const RefOps& ref, int f, int k, double* xi);

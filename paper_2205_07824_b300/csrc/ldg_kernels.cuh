@@ -51,7 +51,12 @@ struct KArgs {
   const void* hist;           // [E][NCU][NPE]     BDF history term, or null
   void* out;                  // [E][NCU][NPE] residual / J.v, or [E][NCU][DIM][NPE] q
   const double* geo;          // [E][GEO] per-element affine geometry
-  const int* nbr;             // [E][NF] neighbour element, -1 on the boundary
+  const double* cgeo;         // curved quadrilaterals: [E][CGeo::SIZE] per-point metrics (FP64) ...
+  const float* cgeof;         // ... and their FP32 copy
+  const double* cx;           // curved: [E][CGeo::XSIZE] physical coordinates of volume and face points
+  const double* minv;         // curved: [E][NPE][NPE] inverse element mass matrices (FP64) ...
+  const float* minvf;         // ... and their FP32 copy
+  const int* nbr;             // [E][NF] neighbour element; -1 data boundary face, -2 wall face
   const unsigned char* nbf;   // [E][NF] neighbour's local face | (orientation code << 3)
   const double* ops;          // reference operator blob (element traits), FP64
   const float* opsf;          // the same blob in FP32 (for FP32-compute instances)
@@ -89,6 +94,29 @@ template <int DIM> struct Geo {
   static constexpr int JINV = 0, DETJ = DIM * DIM, XM = DETJ + 1, JAC = XM + DIM, FACE = JAC + DIM * DIM;
   static constexpr int size(int nf) { return FACE + nf * (DIM + 1); }
 };
+
+// Per-element record of a curved quadrilateral: at each volume point the metric
+// w det J d xi_k / d x_d (k, d) and w det J; at each face point the outward unit
+// normal and w sJ (reference face weight folded in). Physical coordinates of the
+// volume and face points are a separate record (read only for data).
+template <class EL> struct CGeo {
+  static constexpr int DIM = EL::DIM, NV = DIM * DIM + 1, NFR = DIM + 1;
+  static constexpr int VG = 0, FG = EL::NQV * NV, SIZE = FG + EL::NF * EL::NFQ * NFR;
+  static constexpr int XV = 0, XF = EL::NQV * DIM, XSIZE = XF + EL::NF * EL::NFQ * DIM;
+};
+template <class EL> constexpr int geo_size() {
+  if constexpr (EL::CURVED) return CGeo<EL>::SIZE;
+  else return Geo<EL::DIM>::size(EL::NF);
+}
+// Geometry records in the kernel's compute precision.
+template <class EL, class R> __device__ __forceinline__ const R* geo_src(const KArgs& a) {
+  if constexpr (EL::CURVED) {
+    if constexpr (sizeof(R) == 8) return (const R*)a.cgeo;
+    else return (const R*)a.cgeof;
+  } else {
+    return nullptr;
+  }
+}
 
 __host__ __device__ constexpr int al16(int b) { return (b + 15) & ~15; }
 
@@ -172,6 +200,45 @@ template <int DIM, class R> __device__ __forceinline__ void phys_x(const R* g, c
     double s = (double)g[Geo<DIM>::XM + d];
     for (int k = 0; k < DIM; ++k) s += (double)g[Geo<DIM>::JAC + d * DIM + k] * (double)xi[k];
     x[d] = s;
+  }
+}
+
+// Outward unit normal (pointer to DIM values) and quadrature weight w sJ of face
+// point k of face f; g is the element's geometry record.
+template <class EL, class R>
+__device__ __forceinline__ const R* face_frame(const R* g, const R* ops, int f, int k, R& w) {
+  if constexpr (EL::CURVED) {
+    const R* fr = g + CGeo<EL>::FG + (f * EL::NFQ + k) * CGeo<EL>::NFR;
+    w = fr[EL::DIM];
+    return fr;
+  } else {
+    const R* nrm = g + Geo<EL::DIM>::FACE + f * (EL::DIM + 1);
+    w = face_w<EL>(ops, k) * nrm[EL::DIM];
+    return nrm;
+  }
+}
+// Physical coordinates of face point k of face f of element eg (global index).
+template <class EL, class R>
+__device__ __forceinline__ void face_phys(const KArgs& a, const R* g, const R* ops, int eg, int f, int k, double* x) {
+  if constexpr (EL::CURVED) {
+    const double* c = a.cx + (size_t)eg * CGeo<EL>::XSIZE + CGeo<EL>::XF + (f * EL::NFQ + k) * EL::DIM;
+    for (int d = 0; d < EL::DIM; ++d) x[d] = c[d];
+  } else {
+    R xi[3];
+    face_xi<EL>(ops, f, k, xi);
+    phys_x<EL::DIM>(g, xi, x);
+  }
+}
+// Physical coordinates of volume point q of element eg.
+template <class EL, class R>
+__device__ __forceinline__ void vol_phys(const KArgs& a, const R* g, const R* ops, int eg, int q, double* x) {
+  if constexpr (EL::CURVED) {
+    const double* c = a.cx + (size_t)eg * CGeo<EL>::XSIZE + CGeo<EL>::XV + q * EL::DIM;
+    for (int d = 0; d < EL::DIM; ++d) x[d] = c[d];
+  } else {
+    R xi[3], w;
+    vol_xi<EL>(ops, q, xi, w);
+    phys_x<EL::DIM>(g, xi, x);
   }
 }
 
@@ -380,17 +447,17 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
     if (nb >= 0) {
       int code = a.nbf[(size_t)(e0 + e) * NF + f] >> 3;
       kp = a.perm[code * NFQ + k];
-    } else if (MODE == MODE_R) {
-      R xi[3];
+    } else if (MODE == MODE_R && nb == -1) {
       double x[3];
-      face_xi<EL>(OPS, f, k, xi);
-      phys_x<DIM>(g, xi, x);
+      face_phys<EL>(a, g, OPS, e0 + e, f, k, x);
       exact_state<DIM>(elem_mp(a, e0 + e), NCU, x, a.t_dev ? *a.t_dev : a.t, gb);
     }
     for (int c = 0; c < NCU; ++c) {
       int base = ((e * NF + f) * NCU + c) * NFQ;
       R um = TRm[base + k];
-      R uh = nb >= 0 ? (um + TRp[base + kp]) * R(0.5) : R(gb[c]);
+      // wall faces (gas models): the trace (rho-, 0, 0, (rho E)-), linear in u
+      R uh = nb >= 0 ? (um + TRp[base + kp]) * R(0.5)
+                     : (nb == -2 ? ((c == 0 || c == NCU - 1) ? um : R(0)) : R(gb[c]));
       // TRm is overwritten in place: only this thread reads entry (e,f,c,k)
       TRm[base + k] = (um - uh) * w;
     }
@@ -428,12 +495,167 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
   }
 }
 
+// ============================================================ curved q-stage
+// Curved quadrilaterals: the weak form of Eq. 1a with the element's own mass matrix,
+//   (M_K q_d)_i = sum_q w det J u_h d_d phi_i - sum_f sum_k w sJ uhat n_d phi_i,
+// the volume term by the sum-factorised transposed derivatives of the per-point
+// metric times u_h, the face term by lifting -uhat n_d w per point, then q_d by the
+// precomputed inverse M_K^{-1} (the strong form no longer equals it when the
+// quadrature is inexact on curved elements).
+template <class EL, class MD, class R, class TL> struct QLayoutC {
+  static constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, M = Sizes<EL>::M;
+  static constexpr int GEO = CGeo<EL>::SIZE;
+  static constexpr int B_GEO = al16(GEO * sizeof(R)), B_U = al16(NCU * EL::NPE * sizeof(R)),
+                       B_LF = al16(NF * NCU * DIM * EL::NFN * sizeof(R));
+  static constexpr int B_FN = al16(NF * NCU * EL::NFN * sizeof(R)), B_TR = al16(NF * NCU * EL::NFQ * sizeof(R)),
+                       B_TD = al16(NF * NCU * DIM * EL::NFQ * sizeof(R)),
+                       B_FT = al16(NF * NCU * DIM * Sizes<EL>::MF * sizeof(R));
+  static constexpr int PHASE_F = 2 * B_FN + 2 * B_TR + B_TD + B_FT;
+  static constexpr int B_Q = al16(NCU * M * sizeof(R)), B_RV = al16(NCU * EL::NPE * sizeof(R)),
+                       B_BV = al16(NCU * DIM * EL::NPE * sizeof(R));
+  static constexpr int PHASE_V = (1 + DIM + 2) * B_Q + B_RV + B_BV;   // u at points, DIM slabs, 2 temporaries
+  static constexpr int PER_ELEM = B_GEO + B_U + B_LF + (PHASE_F > PHASE_V ? PHASE_F : PHASE_V);
+  static constexpr int NE_ = TL::BUDGET_Q / PER_ELEM;
+  static constexpr int NE = NE_ < 1 ? 1 : (NE_ > TL::NE_MAX ? TL::NE_MAX : NE_);
+  static constexpr int SMEM = NE * PER_ELEM;
+};
+
+template <class EL, class MD, int MODE, class R, class TL>
+__global__ void __launch_bounds__(256) k_qstage_curved(KArgs a) {
+  typedef QLayoutC<EL, MD, R, TL> L;
+  typedef CGeo<EL> CG;
+  constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ, NQV = EL::NQV;
+  constexpr int NE = L::NE, GEO = L::GEO, M = Sizes<EL>::M;
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int e0 = blockIdx.x * NE;
+  const int ne = min(NE, a.E - e0);
+  if (!cta_active(a, e0, ne)) return;
+  const R* OPS = ops_of<R>(a);
+  const R* GSRC = geo_src<EL, R>(a);
+  R* Gs = (R*)smem;
+  R* Us = (R*)(smem + NE * L::B_GEO);
+  R* LF = (R*)(smem + NE * (L::B_GEO + L::B_U));     // [NE][NF][NCU][DIM][NFN]
+  unsigned char* arena = smem + NE * (L::B_GEO + L::B_U + L::B_LF);
+  const double* u = (const double*)a.u;
+
+  for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = GSRC[(size_t)e0 * GEO + i];
+  for (int i = threadIdx.x; i < NE * NCU * NPE; i += blockDim.x)
+    Us[i] = i < ne * NCU * NPE ? R(u[(size_t)e0 * NCU * NPE + i]) : R(0);
+  __syncthreads();
+
+  // ---- faces: -uhat n_d w at every face point, lifted to the face nodes
+  {
+    R* FNm = (R*)arena;
+    R* FNp = (R*)(arena + NE * L::B_FN);
+    R* TRm = (R*)(arena + NE * 2 * L::B_FN);
+    R* TRp = (R*)(arena + NE * (2 * L::B_FN + L::B_TR));
+    R* TD = (R*)(arena + NE * (2 * L::B_FN + 2 * L::B_TR));
+    R* TMP = (R*)(arena + NE * (2 * L::B_FN + 2 * L::B_TR + L::B_TD));
+    for (int it = threadIdx.x; it < NE * NF * NCU * NFN; it += blockDim.x) {
+      const int j = it % NFN, c = (it / NFN) % NCU, f = (it / (NFN * NCU)) % NF, e = it / (NFN * NCU * NF);
+      R vm = R(0), vp = R(0);
+      if (e < ne) {
+        vm = Us[(e * NCU + c) * NPE + EL::face_node(f, j)];
+        const int nb = a.nbr[(size_t)(e0 + e) * NF + f];
+        if (nb >= 0) {
+          const int nf = a.nbf[(size_t)(e0 + e) * NF + f] & 7;
+          vp = R(u[((size_t)nb * NCU + c) * NPE + EL::face_node(nf, j)]);
+        }
+      }
+      FNm[it] = vm;
+      FNp[it] = vp;
+    }
+    __syncthreads();
+    face_trace<EL>(FNm, TRm, TMP, OPS, NE * NF * NCU);
+    __syncthreads();
+    face_trace<EL>(FNp, TRp, TMP, OPS, NE * NF * NCU);
+    __syncthreads();
+    for (int it = threadIdx.x; it < NE * NF * NFQ; it += blockDim.x) {
+      const int k = it % NFQ, f = (it / NFQ) % NF, e = it / (NFQ * NF);
+      if (e >= ne) {
+        for (int cd = 0; cd < NCU * DIM; ++cd) TD[((e * NF + f) * NCU * DIM + cd) * NFQ + k] = R(0);
+        continue;
+      }
+      const R* g = Gs + e * GEO;
+      R w;
+      const R* nrm = face_frame<EL>(g, OPS, f, k, w);
+      const int nb = a.nbr[(size_t)(e0 + e) * NF + f];
+      double gb[4] = {0.0, 0.0, 0.0, 0.0};
+      int kp = k;
+      if (nb >= 0) {
+        kp = a.perm[(a.nbf[(size_t)(e0 + e) * NF + f] >> 3) * NFQ + k];
+      } else if (MODE == MODE_R && nb == -1) {
+        double x[3];
+        face_phys<EL>(a, g, OPS, e0 + e, f, k, x);
+        exact_state<DIM>(elem_mp(a, e0 + e), NCU, x, a.t_dev ? *a.t_dev : a.t, gb);
+      }
+      for (int c = 0; c < NCU; ++c) {
+        const int base = ((e * NF + f) * NCU + c) * NFQ;
+        const R um = TRm[base + k];
+        const R uh = nb >= 0 ? (um + TRp[base + kp]) * R(0.5)
+                             : (nb == -2 ? ((c == 0 || c == NCU - 1) ? um : R(0)) : R(gb[c]));
+        for (int d = 0; d < DIM; ++d) TD[(((e * NF + f) * NCU + c) * DIM + d) * NFQ + k] = -uh * nrm[d] * w;
+      }
+    }
+    __syncthreads();
+    face_lift<EL>(TD, LF, TMP, OPS, NE * NF * NCU * DIM);
+    __syncthreads();
+  }
+
+  // ---- volume: sum_k D_k^T (metric_kd u_h) per d, plus the face moments; then M_K^{-1}
+  R* UQ = (R*)arena;                                              // [NE][NCU][NQV]
+  R* SL = (R*)(arena + NE * L::B_Q);                              // DIM slabs [NE][NCU][NQV]
+  R* T1 = (R*)(arena + NE * (1 + DIM) * L::B_Q);
+  R* T2 = (R*)(arena + NE * (2 + DIM) * L::B_Q);
+  R* RV = (R*)(arena + NE * (3 + DIM) * L::B_Q);                  // [NE][NCU][NPE]
+  R* BV = (R*)(arena + NE * ((3 + DIM) * L::B_Q + L::B_RV));      // [NE][NCU][DIM][NPE]
+  constexpr int SLS = NE * L::B_Q / (int)sizeof(R);               // slab stride (elements)
+  vol_interp<EL>(Us, UQ, T1, OPS, NE * NCU);
+  __syncthreads();
+  for (int d = 0; d < DIM; ++d) {
+    for (int it = threadIdx.x; it < NE * NCU * NQV; it += blockDim.x) {
+      const int q = it % NQV, e = it / (NQV * NCU);
+      const R* g = Gs + e * GEO + CG::VG + q * CG::NV;
+      for (int k = 0; k < DIM; ++k) SL[k * SLS + it] = e < ne ? g[k * DIM + d] * UQ[it] : R(0);
+    }
+    __syncthreads();
+    vol_integrate<EL, false>(0, SL, RV, T1, T2, OPS, NE * NCU);
+    __syncthreads();
+    for (int k = 1; k < DIM; ++k) {
+      vol_integrate<EL, true>(k, SL + k * SLS, RV, T1, T2, OPS, NE * NCU);
+      __syncthreads();
+    }
+    for (int it = threadIdx.x; it < NE * NCU * NPE; it += blockDim.x) {
+      const int n = it % NPE, c = (it / NPE) % NCU, e = it / (NPE * NCU);
+      R sacc = RV[it];
+      for_node_faces<EL>(n, [&](int f, int j) { sacc += LF[(((e * NF + f) * NCU + c) * DIM + d) * NFN + j]; });
+      BV[((e * NCU + c) * DIM + d) * NPE + n] = sacc;
+    }
+    __syncthreads();
+  }
+  const R* MI;
+  if constexpr (sizeof(R) == 8) MI = (const R*)a.minv;
+  else MI = (const R*)a.minvf;
+  double* qo = (double*)a.out;
+  for (int it = threadIdx.x; it < ne * NCU * DIM * NPE; it += blockDim.x) {
+    const int n = it % NPE, b = it / NPE, e = b / (NCU * DIM);
+    const R* mi = MI + ((size_t)(e0 + e) * NPE + n) * NPE;
+    const R* bv = BV + b * NPE;
+    R sacc = R(0);
+#pragma unroll 4
+    for (int m = 0; m < NPE; ++m) sacc += mi[m] * bv[m];
+    qo[(size_t)e0 * NCU * DIM * NPE + it] = (double)sacc;
+  }
+  (void)M;
+}
+
 // ==================================================================== residual
 template <class EL, class MD, int MODE, class R, class TL> struct RLayout {
   typedef typename std::conditional<MODE == MODE_JV, Dual<R>, R>::type S;
   static constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF;
   static constexpr int NCV = NCU * (1 + (MD::HASQ ? DIM : 0));      // u and q fields
-  static constexpr int GEO = Geo<DIM>::size(NF);
+  static constexpr int GEO = geo_size<EL>();
   static constexpr int B_GEO = al16(GEO * sizeof(R)), B_X = al16(NCV * EL::NPE * sizeof(S)),
                        B_LF = al16(NF * NCU * EL::NFN * sizeof(R));
   // face phase
@@ -476,7 +698,12 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
   const double* q = (const double*)a.q;
   const double* dq = (const double*)a.dq;
 
-  for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = R(a.geo[(size_t)e0 * GEO + i]);
+  if constexpr (EL::CURVED) {
+    const R* src = geo_src<EL, R>(a);
+    for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = src[(size_t)e0 * GEO + i];
+  } else {
+    for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = R(a.geo[(size_t)e0 * GEO + i]);
+  }
   for (int i = threadIdx.x; i < NE * NCV * NPE; i += blockDim.x) {
     int n = i % NPE, fld = (i / NPE) % NCV, e = i / (NPE * NCV);
     S val = S(R(0));
@@ -539,8 +766,8 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
         continue;
       }
       const R* g = Gs + e * GEO;
-      const R* nrm = g + Geo<DIM>::FACE + f * (DIM + 1);
-      const R w = face_w<EL>(OPS, k) * nrm[DIM];
+      R w;
+      const R* nrm = face_frame<EL>(g, OPS, f, k, w);
       int nb = a.nbr[(size_t)(e0 + e) * NF + f];
       S um[NCU], qm[NCU * DIM + 1], fh[NCU];
       for (int fld = 0; fld < NCV; ++fld) {
@@ -555,13 +782,13 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
           if (fld < NCU) up[fld] = val; else qp[fld - NCU] = val;
         }
         MD::fhat(um, up, qm, qp, nrm, fh, MPs[e]);
+      } else if (MD::NCU == 4 && nb == -2) {
+        if constexpr (MD::NCU == 4) MD::fhat_wall(um, qm, nrm, fh, MPs[e]);
       } else {
         R gb[4] = {R(0), R(0), R(0), R(0)};
         if (MODE != MODE_HOM) {
-          R xi[3];
           double x[3], gd[4] = {0.0, 0.0, 0.0, 0.0};
-          face_xi<EL>(OPS, f, k, xi);
-          phys_x<DIM>(g, xi, x);
+          face_phys<EL>(a, g, OPS, e0 + e, f, k, x);
           exact_state<DIM>(elem_mp(a, e0 + e), NCU, x, a.t_dev ? *a.t_dev : a.t, gd);
           for (int c = 0; c < 4; ++c) gb[c] = R(gd[c]);
         }
@@ -601,22 +828,33 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
       S val = XQ[(e * NCV + fld) * NQV + qp];
       if (fld < NCU) uq[fld] = val; else qq[fld - NCU] = val;
     }
-    R xi[3], w;
-    vol_xi<EL>(OPS, qp, xi, w);
     const R* g = Gs + e * GEO;
-    const R wj = w * g[Geo<DIM>::DETJ];
+    R wj;
+    if constexpr (EL::CURVED) {
+      wj = g[CGeo<EL>::VG + qp * CGeo<EL>::NV + DIM * DIM];
+    } else {
+      R xi[3], w;
+      vol_xi<EL>(OPS, qp, xi, w);
+      wj = w * g[Geo<DIM>::DETJ];
+    }
     R src = R(0);
     if (MODE == MODE_R && e < ne && MD::SOURCE) {
       double x[3];
-      phys_x<DIM>(g, xi, x);
+      vol_phys<EL>(a, g, OPS, e0 + e, qp, x);
       src = R(source_term<DIM>(elem_mp(a, e0 + e), MD::KIND == M_CONVDIFF, x));
     }
     MD::flux(uq, qq, f, MPs[e]);
     for (int c = 0; c < NCU; ++c) {
       for (int k = 0; k < DIM; ++k) {
         R s = R(0);
-        for (int d = 0; d < DIM; ++d) s += outp(f[c * DIM + d]) * g[Geo<DIM>::JINV + k * DIM + d];
-        GK[((k + 1) * NE * NCU + e * NCU + c) * NQV + qp] = (e < ne) ? -s * wj : R(0);
+        if constexpr (EL::CURVED) {
+          // the per-point metric already carries w det J
+          for (int d = 0; d < DIM; ++d) s += outp(f[c * DIM + d]) * g[CGeo<EL>::VG + qp * CGeo<EL>::NV + k * DIM + d];
+          GK[((k + 1) * NE * NCU + e * NCU + c) * NQV + qp] = (e < ne) ? -s : R(0);
+        } else {
+          for (int d = 0; d < DIM; ++d) s += outp(f[c * DIM + d]) * g[Geo<DIM>::JINV + k * DIM + d];
+          GK[((k + 1) * NE * NCU + e * NCU + c) * NQV + qp] = (e < ne) ? -s * wj : R(0);
+        }
       }
       R tt = outp(uq[c]) * a0dt;
       if (hist) tt += HQ[(e * NCU + c) * NQV + qp];
@@ -679,7 +917,7 @@ __global__ void __launch_bounds__(256) k_block_columns(KArgs a, int col0) {
   typedef typename L::S S;
   constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ, NQV = EL::NQV;
   constexpr int NE = L::NE, GEO = L::GEO, NCO = L::NCO, NLOC = NCU * NPE;
-  static_assert(!MD::HASQ, "block columns by dual numbers are for models without q");
+  static_assert(!MD::HASQ && !EL::CURVED, "block columns by dual numbers: affine models without q");
   extern __shared__ __align__(16) unsigned char smem[];
   const int e0 = blockIdx.x * NE;
   const int ne = min(NE, a.E - e0);
@@ -751,6 +989,8 @@ __global__ void __launch_bounds__(256) k_block_columns(KArgs a, int col0) {
         S up[NCU], qp[1];
         for (int c = 0; c < NCU; ++c) up[c] = S(TRp[((e * NF + f) * NCU + c) * NFQ + kp]);
         MD::fhat(um, up, qm, qp, nrm, fh, MPs[e]);
+      } else if (nb == -2) {
+        MD::fhat_wall(um, qm, nrm, fh, MPs[e]);
       } else {
         R gb[4] = {R(0), R(0), R(0), R(0)};
         R xi[3];

@@ -21,6 +21,7 @@ struct KernelSet {
   int etype, p, nq, model;
   int tile;           // tile variant (Tile0 .. Tile3)
   bool linear;        // linear model: J.v is the homogeneous operator (MODE_HOM)
+  bool curved;        // curved quadrilaterals (per-point geometry records)
   StageFn qstage;     // FP64 compute. Models with q: MODE_R / MODE_HOM; null otherwise
   StageFn residual;   // FP64 compute. MODE_R / MODE_HOM (linear models) / MODE_JV (nonlinear models)
   StageFn qstage32;   // FP32 compute, MODE_HOM (models with q); null otherwise
@@ -54,6 +55,17 @@ template <class EL, class MD, int MODE, class R, class TL> cudaError_t launch_re
   return cudaGetLastError();
 }
 template <class EL, class MD, int MODE, class R, class TL> cudaError_t launch_q1(const KArgs& a, cudaStream_t s) {
+  if constexpr (EL::CURVED) {
+    typedef QLayoutC<EL, MD, R, TL> L;
+    static const cudaError_t attr = cudaFuncSetAttribute(k_qstage_curved<EL, MD, MODE, R, TL>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+    if (attr != cudaSuccess) return attr;
+    if (a.E <= 0) return cudaSuccess;
+    int grid = (a.E + L::NE - 1) / L::NE;
+    k_qstage_curved<EL, MD, MODE, R, TL><<<grid, 256, L::SMEM, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+  }
   typedef QLayout<EL, MD, R, TL> L;
   static const cudaError_t attr = cudaFuncSetAttribute(k_qstage<EL, MD, MODE, R, TL>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
@@ -104,6 +116,7 @@ template <class EL, class MD, class TL = Tile0> void add_set(std::vector<KernelS
   k.etype = etype; k.p = EL::P; k.nq = EL::NQ; k.model = MD::KIND;
   k.tile = tile_id<TL>();
   k.linear = MD::LINEAR;
+  k.curved = EL::CURVED;
   k.residual = &stage_res<EL, MD, double, TL>;
   k.residual32 = &stage_res32<EL, MD, TL>;
   k.ne_r = RLayout<EL, MD, MODE_R, double, TL>::NE;
@@ -111,8 +124,13 @@ template <class EL, class MD, class TL = Tile0> void add_set(std::vector<KernelS
   if constexpr (MD::HASQ) {
     k.qstage = &stage_q<EL, MD, double, TL>;
     k.qstage32 = &stage_q32<EL, MD, TL>;
-    k.ne_q = QLayout<EL, MD, double, TL>::NE;
-    k.smem_q = QLayout<EL, MD, double, TL>::SMEM;
+    if constexpr (EL::CURVED) {
+      k.ne_q = QLayoutC<EL, MD, double, TL>::NE;
+      k.smem_q = QLayoutC<EL, MD, double, TL>::SMEM;
+    } else {
+      k.ne_q = QLayout<EL, MD, double, TL>::NE;
+      k.smem_q = QLayout<EL, MD, double, TL>::SMEM;
+    }
     constexpr int JM = MD::LINEAR ? MODE_HOM : MODE_JV;
     k.ne_j = RLayout<EL, MD, JM, double, TL>::NE;
     k.smem_j = RLayout<EL, MD, JM, double, TL>::SMEM;
@@ -122,7 +140,8 @@ template <class EL, class MD, class TL = Tile0> void add_set(std::vector<KernelS
     k.qstage = nullptr;
     k.qstage32 = nullptr;
     k.blocks = nullptr;
-    k.blocks32 = &launch_blk<EL, MD, float, TL>;
+    if constexpr (EL::CURVED) k.blocks32 = nullptr;   // curved: one tangent per launch
+    else k.blocks32 = &launch_blk<EL, MD, float, TL>;
     k.ne_q = 0; k.smem_q = 0;
     k.ne_j = RLayout<EL, MD, MODE_JV, double, TL>::NE;
     k.smem_j = RLayout<EL, MD, MODE_JV, double, TL>::SMEM;
@@ -135,6 +154,8 @@ template <class TL> void register_tri_t(std::vector<KernelSet>& reg);
 template <class TL> void register_quad_t(std::vector<KernelSet>& reg);
 template <class TL> void register_hex_t(std::vector<KernelSet>& reg);
 template <class TL> void register_ns_t(std::vector<KernelSet>& reg);
+template <class TL> void register_curved_scalar_t(std::vector<KernelSet>& reg);
+template <class TL> void register_curved_gas_t(std::vector<KernelSet>& reg);
 void register_all(std::vector<KernelSet>& reg);
 
 }  // namespace ldg

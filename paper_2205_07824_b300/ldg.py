@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libldg.so")
 
 TRI, QUAD, HEX = 0, 1, 2
 POISSON, CONVDIFF, EULER, NS = 0, 1, 2, 3
-CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST, CASE_ROTATION = range(8)
+(CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST, CASE_ROTATION,
+ CASE_CYLINDER, CASE_REST) = range(10)
 STEADY, BDF1, BDF2 = 0, 1, 2
 FP64, FP32 = 0, 1
 PC_NONE, PC_BJACOBI, PC_MLP = 0, 1, 2
@@ -33,7 +34,29 @@ class LDGError(RuntimeError):
 
 class _Mesh(ctypes.Structure):
     _fields_ = [("elem_type", ctypes.c_int), ("n_elem", ctypes.c_int64),
-                ("xyz", ctypes.POINTER(ctypes.c_double)), ("vid", ctypes.POINTER(ctypes.c_int64))]
+                ("xyz", ctypes.POINTER(ctypes.c_double)), ("vid", ctypes.POINTER(ctypes.c_int64)),
+                ("geom_order", ctypes.c_int), ("xgeo", ctypes.POINTER(ctypes.c_double)),
+                ("bc", ctypes.POINTER(ctypes.c_uint8))]
+
+
+def _mesh_desc(mesh, keep):
+    """ldg_mesh_desc of a mesh (curved map points and wall marks when it has them);
+    the arrays it points to are appended to ``keep``."""
+    xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    vid = np.ascontiguousarray(mesh.vid, dtype=np.int64)
+    keep += [xyz, vid]
+    pg = int(getattr(mesh, "pg", 0) or 0)
+    xgeo = bc = None
+    if pg > 0:
+        xgeo = np.ascontiguousarray(mesh.xgeo, dtype=np.float64)
+        keep.append(xgeo)
+    if getattr(mesh, "bc", None) is not None:
+        bc = np.ascontiguousarray(mesh.bc, dtype=np.uint8)
+        keep.append(bc)
+    return _Mesh(mesh.etype, mesh.n_elem, xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                 vid.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), pg,
+                 xgeo.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if xgeo is not None else None,
+                 bc.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if bc is not None else None)
 
 
 class _Model(ctypes.Structure):
@@ -162,8 +185,8 @@ class LDG:
         self._xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
         self._vid = np.ascontiguousarray(mesh.vid, dtype=np.int64)
         self._mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float64).reshape(-1))
-        md = _Mesh(mesh.etype, mesh.n_elem, self._xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                   self._vid.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+        self._keep_mesh = []
+        md = _mesh_desc(mesh, self._keep_mesh)
         mo = _Model(model, case, len(self._mu),
                     self._mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(self._mu) else None)
         op = _Options(nq1, gmres_m, max_restarts, max_newton, newton_rtol, gmres_rtol, krylov_precision, precond,
@@ -377,8 +400,7 @@ class Batch:
             vid = np.ascontiguousarray(m.vid, dtype=np.int64)
             mu = np.ascontiguousarray(np.asarray(mus[i], dtype=np.float64).reshape(-1))
             self._keep += [xyz, vid, mu]
-            md[i] = _Mesh(m.etype, m.n_elem, xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                          vid.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+            md[i] = _mesh_desc(m, self._keep)
             mo[i] = _Model(model, int(cases[i]), len(mu),
                            mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(mu) else None)
         pa = (ctypes.c_int * n)(*[int(p) for p in ps])
