@@ -182,20 +182,30 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_mode(LDG, mesh, kprec, pc, steps, warmup, flush, stream, launches):
-    """Advance the vortex `warmup` + `steps` BDF2 steps; time the last `steps`.
+def vortex_problem(LDG, mesh):
+    """The vortex: context factory (preconditioner, Krylov precision), initial states, dt."""
+    from paper_2205_07824_b300.ldg import EULER, CASE_VORTEX
+
+    def make(p, kprec):
+        return LDG(mesh, P, EULER, CASE_VORTEX, (1.4,), gmres_m=30, newton_rtol=1e-8, gmres_rtol=1e-3,
+                   krylov_precision=kprec, precond=p)
+    return dict(make=make, init=lambda g: (g.interpolate(0.0), g.interpolate(-DT)), dt=DT, n_elem=mesh.n_elem)
+
+
+def run_mode(prob, kprec, pc, steps, warmup, flush, stream, launches):
+    """Advance the problem `warmup` + `steps` BDF2 steps; time the last `steps`.
 
     pc = 2 (learned): the warm-up steps run the block-Jacobi solver and collect its
     (v, M^{-1} v, u) triples, the network is trained on them once (reported, not in
     the timed steps), one more untimed step runs with the learned preconditioner,
     then the timed steps."""
     import torch
-    from paper_2205_07824_b300.ldg import BDF2, EULER, CASE_VORTEX
-    mk = lambda p: LDG(mesh, P, EULER, CASE_VORTEX, (1.4,), gmres_m=30, newton_rtol=1e-8, gmres_rtol=1e-3,
-                       krylov_precision=kprec, precond=p)
+    from paper_2205_07824_b300.ldg import BDF2
+    DT = prob["dt"]
+    mk = lambda p: prob["make"](p, kprec)
     g = mk(1 if pc == 2 else pc)
     g.autotune()                       # tile of the kernels (cached per shape in the process)
-    un, unm1 = g.interpolate(0.0), g.interpolate(-DT)
+    un, unm1 = prob["init"](g)
     u = torch.empty_like(un)
     state = {"t": 0.0, "g": g}
     nloc = g.n_cu * g.n_pe
@@ -221,7 +231,9 @@ def run_mode(LDG, mesh, kprec, pc, steps, warmup, flush, stream, launches):
         state["t"] = t1
         return rep
 
-    for _ in range(warmup):
+    # the learned form spends its last warm-up step on the learned preconditioner (after
+    # training), so every form ends its timed steps at the same time level
+    for _ in range(max(1, warmup - 1) if cap else warmup):
         step(collect=bool(cap))
     if cap:
         torch.cuda.synchronize()
@@ -230,7 +242,8 @@ def run_mode(LDG, mesh, kprec, pc, steps, warmup, flush, stream, launches):
         g.mlp_init(seed=1)
         rep_t = g.mlp_train(bufs[0][:nd], bufs[1][:nd], bufs[2][:nd], epochs=8, batch=4096, lr=1e-3)
         torch.cuda.synchronize()
-        train = {"pairs": state["used"] * mesh.n_elem, "vectors": state["used"], "seconds": time.perf_counter() - t0,
+        train = {"pairs": state["used"] * prob["n_elem"], "vectors": state["used"],
+                 "seconds": time.perf_counter() - t0,
                  "adam_steps": rep_t["steps"], "loss_first": rep_t["loss_first"], "loss_last": rep_t["loss_last"],
                  "data": "Arnoldi vectors of the block-Jacobi warm-up steps with their block corrections"}
         gm = mk(2)
@@ -512,6 +525,157 @@ def run_hex(args):
     print(json.dumps(line), flush=True)
 
 
+CYL_WORKLOAD = ("2D compressible Navier-Stokes flow past a cylinder (radius 0.5 at the origin, domain "
+                "[-10,30]x[-10,10]), {E} curved quadrilaterals ({nr} advancing layers x {nt} around, first layer "
+                "0.01, map degree 3, seeded node jitter, seed 7), p=3, Re={re:.1f} (uniform [100,1000], seed {rs}), "
+                "Mach 0.2 free stream, no-slip adiabatic wall, BDF2 dt=0.1 from the free stream blended to rest "
+                "at the wall (velocity x tanh((r-0.5)/0.1)), Newton-GMRES(30) to 1e-8 (FP64 residual)")
+
+
+def cylinder_problem(LDG, mesh, re):
+    """Far-field data: the uniform Mach 0.2 free stream. Initial state (both BDF2 levels):
+    the free stream with its velocity scaled by tanh((r - 0.5) / 0.1), which meets the
+    no-slip wall (an impulsive start, free stream up to the wall, is not a state the
+    full-step Newton iteration reaches 1e-8 from in one dt = 0.1 step)."""
+    from paper_2205_07824_b300.ldg import NS, CASE_CYLINDER, CASE_CYLINDER_START
+
+    def make(p, kprec):
+        return LDG(mesh, 3, NS, CASE_CYLINDER, (1.4, re, 0.72), gmres_m=30, newton_rtol=1e-8, gmres_rtol=1e-3,
+                   krylov_precision=kprec, precond=p)
+
+    def init(g):
+        g0 = LDG(mesh, 3, NS, CASE_CYLINDER_START, (1.4, re, 0.72))
+        u0 = g0.interpolate(0.0)
+        return u0, u0.clone()
+    return dict(make=make, init=init, dt=0.1, n_elem=mesh.n_elem)
+
+
+def run_cylinder(args):
+    """The cylinder workload: time-to-1e-8 per BDF2 step for the plain FP64 block-Jacobi
+    form, the mixed form with block-Jacobi, and the learned + mixed form (the MLP
+    trained on the warm-up steps' block-Jacobi data), on the same seeds; the Krylov J.v
+    kernel pair timed alone against its HBM roofline."""
+    import numpy as np
+    import torch
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, kernel_launches
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    nr, nt = args.cyl_layers, args.cyl_around
+    mesh = synth.cylinder_mesh(nr, nt, 3, seed=7)
+    re = float(np.random.default_rng(args.re_seed + rank).uniform(100.0, 1000.0))
+    prob = cylinder_problem(LDG, mesh, re)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(local)
+    clocks.start()
+    forms = {}
+    sols = {}
+    headline = None
+    all_forms = (("fp64_bjacobi", 0, 1), ("fp32_bjacobi", 1, 1), ("fp32_learned", 1, 2))
+    want = args.cyl_forms.split(",")
+    for name, kp, pc in [f for f in all_forms if f[0] in want]:
+        g, u, times, tot, launches, t_end, train = run_mode(prob, kp, pc, args.steps, args.warmup, flush, stream,
+                                                            kernel_launches)
+        ms = sum(times) / args.steps
+        forms[name] = {"ms_per_step": ms, "newton_iters_per_step": tot["newton"] / args.steps,
+                       "gmres_iters_per_step": tot["gmres"] / args.steps,
+                       "jv_applications_per_step": tot["jv"] / args.steps, "pc_fallbacks": tot["pc_fallbacks"],
+                       "jv_gdofs": g.n_dof * tot["jv"] / (sum(times) * 1e-3) / 1e9, "gpu_launches": int(launches)}
+        if train:
+            forms[name]["learned_pc_training"] = train
+        sols[name] = u.clone()
+        headline = (g, u, times, tot, launches)   # the last form run is the headline
+    clk = clocks.stop()
+    ref = sols.get("fp64_bjacobi", next(iter(sols.values())))
+    base_ms = forms.get("fp64_bjacobi", next(iter(forms.values())))["ms_per_step"]
+    for name in forms:
+        forms[name]["solution_rel_diff_vs_fp64_bjacobi"] = float(torch.linalg.norm(sols[name] - ref) /
+                                                                 torch.linalg.norm(ref))
+        forms[name]["speedup_vs_fp64_bjacobi"] = base_ms / forms[name]["ms_per_step"]
+    g, u, times, tot, launches = headline
+    n = g.n_dof
+    # the Krylov J.v as the solver runs it (q(u) of the step's residual reused), FP32 arithmetic
+    v = torch.randn(n, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    jv = torch.empty_like(v)
+    g.residual(u)
+    jvt = {}
+    for kp in (1, 0):
+        for _ in range(5):
+            g.jvp_after_residual(kp, u, v, jv)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.jv_reps):
+            g.jvp_after_residual(kp, u, v, jv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        jvt[kp] = e0.elapsed_time(e1) / args.jv_reps
+    jv32 = g.jvp_after_residual(1, u, v)
+    jv64 = g.jvp_after_residual(0, u, v)
+    jv_err = float(torch.linalg.norm(jv32 - jv64) / torch.linalg.norm(jv64))
+    # algorithmic bytes per J.v (FP64 storage): read u, v, q(u) (2 per DOF), write and read
+    # Q v (2 + 2), write J.v: 9 x 8 B per DOF; plus the curved-geometry records the two
+    # kernels read in FP32: per-point metrics twice and the element mass inverse once
+    npe = g.n_pe
+    nq1, nf = 5, 4
+    geo_rec = nq1 * nq1 * 5 + nf * nq1 * 3
+    geo_bytes = (2 * geo_rec + npe * npe) * 4 * mesh.n_elem
+    b_alg = 72.0 * n + geo_bytes
+    hbm = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm = float(json.load(f)["hbm_gbs"])
+        peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except Exception:
+        hbm, peak_src = 6400.0, "fallback 6.4 TB/s (of fallback)"
+    achieved = b_alg / (jvt[1] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": hbm, "frac": achieved / hbm,
+                "traffic": None, "peak_source": peak_src,
+                "kernel": "k_qstage_curved<CurvedQuadEl<3,5>, NSModel, MODE_HOM, float> + "
+                          "k_residual<CurvedQuadEl<3,5>, NSModel, MODE_JV, float>",
+                "launch_pair_ms": jvt[1], "fp64_pair_ms": jvt[0], "bytes_per_jv": b_alg,
+                "bytes_definition": "72 B/DOF state traffic (u, v, q(u), Q v written and read, J.v) + FP32 "
+                                    "curved metrics (read by both kernels) and element mass inverses",
+                "jv_gdofs_kernel_fp32": n / (jvt[1] * 1e-3) / 1e9, "jv_gdofs_kernel_fp64": n / (jvt[0] * 1e-3) / 1e9,
+                "jv_fp32_rel_err_vs_fp64": jv_err}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        o = oracle.Oracle(mesh, 3, oracle.NS, oracle.CASE_CYLINDER, (1.4, re, 0.72))
+        un = o.interpolate()
+        o.set_time(2, 0.1, 0.1, un, un)
+        uh, vh = u.cpu().numpy(), v.cpu().numpy()
+        elems = np.arange(0, mesh.n_elem, 40)
+        calls, t0 = 0, time.perf_counter()
+        while True:
+            o.jvp_some(uh, vh, elems)
+            calls += 1
+            el = time.perf_counter() - t0
+            if el > 12.0 or calls >= 20:
+                break
+        dofs = len(elems) * o.npe * o.ncu * calls
+        cpu = {"value": dofs / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{calls} oracle J.v evaluations on every 40th element ({len(elems)} elements, their q "
+                         f"neighbourhoods included), {el:.1f} s single-threaded"}
+    total_ms, gdofs = aggregate(times, n * tot["jv"], world, rank)
+    if rank == 0:
+        line = {"metric": METRIC, "value": gdofs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+                "config": {"workload": CYL_WORKLOAD.format(E=mesh.n_elem, nr=nr, nt=nt, re=re, rs=args.re_seed),
+                           "n_dof": int(n), "n_elem": int(mesh.n_elem),
+                           "value_definition": "learned + mixed form: J.v applications of the whole solve x DOF / "
+                                               "timed step time",
+                           "forms": forms, "headline_form": list(forms)[-1],
+                           "l2": "flushed (256 MiB write) before each timed step, outside its event window",
+                           "parallelism": f"{world} independent instance(s), one per GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": None, "gpu_launches": int(launches),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -530,9 +694,16 @@ def main():
     ap.add_argument("--host-loops", action="store_true",
                     help="run the solver's Newton / restart / Arnoldi loops from the host instead of the CUDA "
                          "graph's WHILE nodes (same kernels; for profilers that do not follow graph nodes)")
-    ap.add_argument("--workload", default="vortex", choices=["vortex", "batch", "hex"],
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "batch", "hex", "cylinder"],
                     help="vortex: the 64x64 p=3 Euler BDF2 step; batch: 256 parametrised convection-diffusion "
-                         "solves in one graph launch; hex: the 48^3 convection-diffusion J.v sweep p=1..6")
+                         "solves in one graph launch; hex: the 48^3 convection-diffusion J.v sweep p=1..6; "
+                         "cylinder: Navier-Stokes past a cylinder on 40,000 curved quads, learned + mixed vs "
+                         "plain FP64 block-Jacobi")
+    ap.add_argument("--cyl-layers", type=int, default=100, help="cylinder mesh: layers across the domain")
+    ap.add_argument("--cyl-around", type=int, default=400, help="cylinder mesh: elements around the cylinder")
+    ap.add_argument("--re-seed", type=int, default=0, help="cylinder: seed of the Reynolds-number draw")
+    ap.add_argument("--cyl-forms", default="fp64_bjacobi,fp32_bjacobi,fp32_learned",
+                    help="cylinder: forms to run (the last one is the headline)")
     args = ap.parse_args()
     if args.host_loops:
         os.environ["LDG_SOLVER_HOST_LOOPS"] = "1"
@@ -544,6 +715,9 @@ def main():
         return
     if args.workload == "hex":
         run_hex(args)
+        return
+    if args.workload == "cylinder":
+        run_cylinder(args)
         return
 
     import numpy as np
@@ -566,7 +740,8 @@ def main():
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    g, u, times, tot, launches, t_end, train = run_mode(LDG, mesh, kprec, pc, args.steps, args.warmup, flush, stream,
+    prob = vortex_problem(LDG, mesh)
+    g, u, times, tot, launches, t_end, train = run_mode(prob, kprec, pc, args.steps, args.warmup, flush, stream,
                                                         kernel_launches)
     if world > 1:
         dist.barrier()
@@ -578,8 +753,7 @@ def main():
     # the plain FP64 block-Jacobi form on the same box, same steps (the benchmark spec comparison)
     base = None
     if not args.no_fp64_baseline and (kprec, pc) != (0, 1):
-        gb, ub, tb, totb, _, _, _ = run_mode(LDG, mesh, 0, 1, args.steps, args.warmup, flush, stream,
-                                             kernel_launches)
+        gb, ub, tb, totb, _, _, _ = run_mode(prob, 0, 1, args.steps, args.warmup, flush, stream, kernel_launches)
         base = {"form": "FP64 Krylov J.v + block-Jacobi", "ms_per_step": sum(tb) / args.steps,
                 "gmres_iters_per_step": totb["gmres"] / args.steps,
                 "solution_rel_diff_vs_headline": float(torch.linalg.norm(ub - u) / torch.linalg.norm(ub))}

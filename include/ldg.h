@@ -52,7 +52,8 @@ enum {
   LDG_CASE_CONST = 6,   /* uniform Euler free stream rho = 1, v = (1,1), p = 1 */
   LDG_CASE_ROTATION = 7, /* rigid rotation v = (-y, x)/2, rho = 1 + x/10 + y/20, internal energy 2 */
   LDG_CASE_CYLINDER = 8, /* cylinder free stream rho = 1, v = (1, 0), Mach 0.2 (p = 1 / (gamma 0.04)) */
-  LDG_CASE_REST = 9      /* gas at rest rho = 1, v = 0, p = 1 */
+  LDG_CASE_REST = 9,     /* gas at rest rho = 1, v = 0, p = 1 */
+  LDG_CASE_CYLINDER_START = 10 /* cylinder start: the Mach 0.2 free stream with velocity (tanh((r - 0.5)/0.1), 0) */
 };
 
 typedef enum {
@@ -197,6 +198,15 @@ int ldg_jvp(ldg_ctx* ctx, const double* u_dev, const double* v_dev, double* jv_d
 /* J.v in a chosen arithmetic: LDG_FP64 (same as ldg_jvp) or LDG_FP32 (inputs and
  * output FP64 in memory; every operation of the operator in FP32). */
 int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u_dev, const double* v_dev, double* jv_dev);
+
+/* J(u) v reusing the q(u) that the last ldg_residual(ctx, u, ...) call on this context
+ * computed: the form of J.v inside Newton-GMRES, where every Krylov product of a
+ * Newton step is taken at the state whose residual was just evaluated. Nonlinear
+ * models with q (Navier-Stokes) skip their q(u) stage; other models compute exactly
+ * what ldg_jvp_prec does. The caller guarantees that u is the state of that residual
+ * call, unchanged since, and that no other residual call intervened (the result is
+ * otherwise the Jacobian at the other state). precision: LDG_FP64 or LDG_FP32. */
+int ldg_jvp_after_residual(ldg_ctx* ctx, int precision, const double* u_dev, const double* v_dev, double* jv_dev);
 
 /* Exact element-diagonal blocks of J(u): blocks_dev [n_elem][n_loc][n_loc], column-major
  * per element (column l at offset l * n_loc), n_loc = n_cu * n_pe. Convection models use

@@ -18,7 +18,7 @@ _LIB = os.path.join(_HERE, "libldg_oracle.so")
 
 POISSON, CONVDIFF, EULER, NS = 0, 1, 2, 3
 (CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST, CASE_ROTATION,
- CASE_CYLINDER, CASE_REST) = range(10)
+ CASE_CYLINDER, CASE_REST, CASE_CYLINDER_START) = range(11)
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.POINTER(ctypes.c_int64)

@@ -331,7 +331,8 @@ struct Ref {
 // ------------------------------------------------------------------ models
 enum { POISSON = 0, CONVDIFF = 1, EULER = 2, NS = 3 };
 enum { CASE_ZERO = 0, CASE_SINSIN = 1, CASE_EXPSIN = 2, CASE_POLY2 = 3, CASE_LINEAR = 4,
-       CASE_VORTEX = 5, CASE_CONST = 6, CASE_ROTATION = 7, CASE_CYLINDER = 8, CASE_REST = 9 };
+       CASE_VORTEX = 5, CASE_CONST = 6, CASE_ROTATION = 7, CASE_CYLINDER = 8, CASE_REST = 9,
+       CASE_CYLINDER_START = 10 };
 
 struct Model {
   int kind, cas, nd, ncu;
@@ -365,6 +366,12 @@ struct Model {
         // free stream of the cylinder flow: rho = 1, v = (1, 0), Mach 0.2: p = 1 / (gamma 0.2^2)
         const double pr = 1.0 / (gamma * 0.04);
         u[0] = 1; u[1] = 1; u[2] = 0; u[3] = pr / (gamma - 1) + 0.5;
+      } else if (cas == CASE_CYLINDER_START) {
+        // start of the cylinder flow: the free stream with its velocity scaled by
+        // tanh((r - 0.5) / 0.1), zero on the wall (pressure and density uniform)
+        const double pr = 1.0 / (gamma * 0.04), r = std::sqrt(x[0] * x[0] + x[1] * x[1]);
+        const double vx = std::tanh((r - 0.5) / 0.1);
+        u[0] = 1; u[1] = vx; u[2] = 0; u[3] = pr / (gamma - 1) + 0.5 * vx * vx;
       } else if (cas == CASE_REST) {
         // gas at rest: rho = 1, v = 0, p = 1
         u[0] = 1; u[1] = 0; u[2] = 0; u[3] = 1.0 / (gamma - 1);

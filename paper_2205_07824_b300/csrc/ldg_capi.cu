@@ -309,12 +309,18 @@ int do_blocks(ldg_ctx* ctx, const double* u, int prec, double* blocks) {
     }
     return LDG_OK;
   }
-  // linear models: coloured probing, J applied to the sum of unit vectors of one colour
+  // models with q: coloured probing, J applied to the sum of unit vectors of one colour;
+  // a nonlinear model's q(u) is formed once for all probes
+  if (!ctx->ks->linear) {
+    KArgs a = base_args(ctx);
+    a.u = u; a.out = ctx->d_q;
+    CK(ctx->ks->qstage(MODE_R, a, ctx->stream));
+  }
   for (int c = 0; c < ctx->ncolour; ++c)
     for (int l = 0; l < nloc; ++l) {
       k_probe<<<grid_for(E * nloc), 256, 0, ctx->stream>>>(ctx->d_probe, ctx->d_colour, c, l, nloc, E);
       count_launch();
-      if ((rc = jvp_args(ctx, base_args(ctx), u, ctx->d_probe, ctx->d_jp, prec))) return rc;
+      if ((rc = jvp_args(ctx, base_args(ctx), u, ctx->d_probe, ctx->d_jp, prec, true))) return rc;
       k_extract<<<grid_for(E * nloc), 256, 0, ctx->stream>>>(ctx->d_jp, ctx->d_colour, c, l, nloc, E, blocks);
       count_launch();
       CK(cudaGetLastError());
@@ -1183,6 +1189,11 @@ int ldg_jvp(ldg_ctx* ctx, const double* u, const double* v, double* jv) {
 int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u, const double* v, double* jv) {
   if (!ctx || !ctx->ks || !u || !v || !jv || (precision != LDG_FP64 && precision != LDG_FP32)) return LDG_ERR_ARG;
   return jvp_args(ctx, base_args(ctx), u, v, jv, precision);
+}
+
+int ldg_jvp_after_residual(ldg_ctx* ctx, int precision, const double* u, const double* v, double* jv) {
+  if (!ctx || !ctx->ks || !u || !v || !jv || (precision != LDG_FP64 && precision != LDG_FP32)) return LDG_ERR_ARG;
+  return jvp_args(ctx, base_args(ctx), u, v, jv, precision, true);
 }
 
 int ldg_diag_blocks(ldg_ctx* ctx, int precision, const double* u, double* blocks) {

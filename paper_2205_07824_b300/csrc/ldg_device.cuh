@@ -146,7 +146,7 @@ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 // ----------------------------------------------------------------- models
 enum { M_POISSON = 0, M_CONVDIFF = 1, M_EULER = 2, M_NS = 3 };
 enum { C_ZERO = 0, C_SINSIN = 1, C_EXPSIN = 2, C_POLY2 = 3, C_LINEAR = 4, C_VORTEX = 5, C_CONST = 6,
-       C_ROTATION = 7, C_CYLINDER = 8, C_REST = 9 };
+       C_ROTATION = 7, C_CYLINDER = 8, C_REST = 9, C_CYLINDER_START = 10 };
 
 // kappa: diffusivity, or the dynamic viscosity 1/Re of Navier-Stokes; tau: the
 // LDG jump penalty; pr: the Prandtl number (Navier-Stokes)
@@ -183,6 +183,11 @@ __device__ void exact_state(const ModelParams& mp, int ncu, const double* x, dou
       // cylinder free stream: rho = 1, v = (1, 0), Mach 0.2
       const double p = 1.0 / (mp.gamma * 0.04);
       g[0] = 1.0; g[1] = 1.0; g[2] = 0.0; g[3] = p / (mp.gamma - 1.0) + 0.5;
+    } else if (mp.cas == C_CYLINDER_START) {
+      // start of the cylinder flow: free stream with velocity tanh((r - 0.5) / 0.1)
+      const double p = 1.0 / (mp.gamma * 0.04), r = sqrt(x[0] * x[0] + x[1] * x[1]);
+      const double vx = tanh((r - 0.5) / 0.1);
+      g[0] = 1.0; g[1] = vx; g[2] = 0.0; g[3] = p / (mp.gamma - 1.0) + 0.5 * vx * vx;
     } else if (mp.cas == C_REST) {
       g[0] = 1.0; g[1] = 0.0; g[2] = 0.0; g[3] = 1.0 / (mp.gamma - 1.0);
     } else {

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libldg.so")
 TRI, QUAD, HEX = 0, 1, 2
 POISSON, CONVDIFF, EULER, NS = 0, 1, 2, 3
 (CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST, CASE_ROTATION,
- CASE_CYLINDER, CASE_REST) = range(10)
+ CASE_CYLINDER, CASE_REST, CASE_CYLINDER_START) = range(11)
 STEADY, BDF1, BDF2 = 0, 1, 2
 FP64, FP32 = 0, 1
 PC_NONE, PC_BJACOBI, PC_MLP = 0, 1, 2
@@ -119,6 +119,7 @@ def lib():
         L.ldg_jvp.argtypes = [vp, dp, dp, dp]
         L.ldg_jvp_noalloc.argtypes = [vp, dp, dp, dp]
         L.ldg_jvp_prec.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+        L.ldg_jvp_after_residual.argtypes = [vp, ctypes.c_int, dp, dp, dp]
         L.ldg_diag_blocks.argtypes = [vp, ctypes.c_int, dp, dp]
         L.ldg_precond_setup.argtypes = [vp, dp]
         L.ldg_precond_apply.argtypes = [vp, dp, dp]
@@ -260,6 +261,14 @@ class LDG:
         out = self.empty() if out is None else out
         n = self.n_dof
         self._check(lib().ldg_jvp_prec(self._h, precision, _ptr(u, n, "u"), _ptr(v, n, "v"), _ptr(out, n, "out")))
+        return out
+
+    def jvp_after_residual(self, precision: int, u, v, out=None):
+        """J.v at the state of the last residual call, reusing its q(u) (Newton-Krylov form)."""
+        out = self.empty() if out is None else out
+        n = self.n_dof
+        self._check(lib().ldg_jvp_after_residual(self._h, precision, _ptr(u, n, "u"), _ptr(v, n, "v"),
+                                                 _ptr(out, n, "out")))
         return out
 
     def diag_blocks(self, u, precision: int = 0, out=None):

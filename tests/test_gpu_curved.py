@@ -90,6 +90,8 @@ def test_interpolation_and_free_stream():
     o, g = _pair(mesh, 3, oracle.NS, oracle.CASE_CYLINDER, NS_MU)
     ui = host(g.interpolate(0.0))
     assert_parity(ui, o.interpolate(), what="interpolate")
+    o0, g0 = _pair(mesh, 3, oracle.NS, oracle.CASE_CYLINDER_START, NS_MU)
+    assert_parity(host(g0.interpolate(0.0)), o0.interpolate(), what="interpolate start state")
     # away from walls the free stream is preserved: far-field-only O-grid
     m2 = synth.o_grid(3, 16, 3, outer=("circle", 3.0), jitter=0.3, wall=False)
     o2, g2 = _pair(m2, 3, oracle.NS, oracle.CASE_CYLINDER, NS_MU)

@@ -68,6 +68,10 @@ def test_every_tile_and_noalloc():
     out = cuda(np.zeros(o.ndof))
     g.jvp_noalloc(cuda(u), cuda(v), out)
     assert np.array_equal(host(out), jv)
+    # the Newton-Krylov form: q(u) of the last residual reused
+    cu = cuda(u)
+    g.residual(cu)
+    assert np.array_equal(host(g.jvp_after_residual(0, cu, cuda(v))), jv)
 
 
 def test_fp32_jvp_error():
