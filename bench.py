@@ -182,6 +182,36 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def graph_time_ms(g, fn, reps):
+    """Device time of one call of fn (launches on context g, no allocation): `reps` calls
+    captured back to back in a CUDA graph, one replay timed with CUDA events, so that
+    the host's per-call overhead does not hide the kernels' own duration."""
+    import torch
+    old = g.stream
+    s = torch.cuda.Stream()
+    g.set_stream(s)
+    try:
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                fn()
+        torch.cuda.synchronize()
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, stream=s):
+            for _ in range(reps):
+                fn()
+        cg.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cur = torch.cuda.current_stream()
+        e0.record(cur)
+        cg.replay()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    finally:
+        g.set_stream(old)
+
+
 def vortex_problem(LDG, mesh):
     """The vortex: context factory (preconditioner, Krylov precision), initial states, dt."""
     from paper_2205_07824_b300.ldg import EULER, CASE_VORTEX
@@ -602,16 +632,7 @@ def run_cylinder(args):
     g.residual(u)
     jvt = {}
     for kp in (1, 0):
-        for _ in range(5):
-            g.jvp_after_residual(kp, u, v, jv)
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.jv_reps):
-            g.jvp_after_residual(kp, u, v, jv)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        jvt[kp] = e0.elapsed_time(e1) / args.jv_reps
+        jvt[kp] = graph_time_ms(g, lambda: g.jvp_after_residual(kp, u, v, jv), args.jv_reps)
     jv32 = g.jvp_after_residual(1, u, v)
     jv64 = g.jvp_after_residual(0, u, v)
     jv_err = float(torch.linalg.norm(jv32 - jv64) / torch.linalg.norm(jv64))
@@ -763,16 +784,7 @@ def main():
     # the Krylov J.v kernel alone (the dominant kernel), CUDA events on the launching stream
     v = torch.randn(n, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
     jv = torch.empty_like(v)
-    for _ in range(5):
-        g.jvp_prec(kprec, u, v, jv)
-    flush.zero_()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.jv_reps):
-        g.jvp_prec(kprec, u, v, jv)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    jv_ms = e0.elapsed_time(e1) / args.jv_reps
+    jv_ms = graph_time_ms(g, lambda: g.jvp_prec(kprec, u, v, jv), args.jv_reps)
     jv64 = g.jvp_prec(0, u, v)
     jv_err = float(torch.linalg.norm(jv - jv64) / torch.linalg.norm(jv64)) if kprec else 0.0
     fpe = JV_FLOP_PER_ELEM[kprec]
@@ -780,7 +792,9 @@ def main():
     peak = FP32_PEAK_TFLOPS if kprec else FP64_PEAK_TFLOPS
     roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
                 "traffic": None,
-                "kernel": f"k_residual<TensorEl<2,3,5>, EulerModel, MODE_JV, {'float' if kprec else 'double'}>",
+                "kernel": (f"k_residual<TensorEl<2,3,5>, EulerModel, MODE_JV, {'float' if kprec else 'double'}, "
+                           f"Tile{g.get_tile()[0]}>"),
+                "timing": "CUDA graph of jv_reps back-to-back J.v launches, one replay timed with CUDA events",
                 "launch_ms": jv_ms, "jv_gdofs_kernel": n / (jv_ms * 1e-3) / 1e9,
                 "flop_per_elem": fpe, "flop_source": "ncu thread-instruction counts (FMA x2 + ADD + MUL)",
                 "peak_source": ("FP32 ALU: 148 SMs x 128 FMA/clk x 2 FLOP x 2.032 GHz (derived)" if kprec else

@@ -221,6 +221,11 @@ class LDG:
             raise LDGError(rc, lib().ldg_last_error(self._h).decode())
 
     # ------------------------------------------------------------- tiles
+    def set_stream(self, stream):
+        """Stream of all later launches of this context (a torch.cuda.Stream)."""
+        self._check(lib().ldg_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)))
+        self.stream = stream
+
     def autotune(self, force: bool = False):
         """Times the compiled tiles on this mesh and keeps the fastest J.v; returns (tile, ms)."""
         t, ms = ctypes.c_int(), ctypes.c_double()

@@ -194,3 +194,4 @@ def test_newton_c2_bdf2_step_small():
     # both satisfy ||R|| <= 1e-8 ||R0||; the solutions agree to the solve tolerance
     assert np.linalg.norm(ug - uo) <= 1e-7 * np.linalg.norm(uo)
     assert np.linalg.norm(o.residual(ug)) <= 1.5e-8 * st["r0"]
+
