@@ -47,6 +47,7 @@ def lib():
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _D,
                                         ctypes.c_void_p]
         L.orc_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_set_radd.argtypes = [ctypes.c_void_p, _D]
         L.orc_ndof.restype = ctypes.c_int64
         L.orc_ndof.argtypes = [ctypes.c_void_p]
         L.orc_set_time.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
@@ -87,6 +88,42 @@ def _c(a, dtype=np.float64):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+DIRK11, DIRK22, DIRK33, DIRK34 = 1, 2, 3, 4
+
+
+def dirk_tableau(scheme):
+    """Butcher tableaus (A, b, c) of singly diagonally implicit Runge-Kutta schemes:
+    DIRK11 backward Euler; DIRK22 and DIRK33 the L-stable, stiffly accurate schemes
+    of Alexander (1977), two stages order 2 and three stages order 3; DIRK34 the
+    three-stage order-4 A-stable scheme of Crouzeix (1975). Each diagonal gamma is
+    computed from its defining equation."""
+    if scheme == DIRK11:
+        return [[1.0]], [1.0], [1.0]
+    if scheme == DIRK22:
+        g = 1.0 - 1.0 / np.sqrt(2.0)                     # root of g^2 - 2 g + 1/2 in (0, 1)
+        return [[g, 0.0], [1.0 - g, g]], [1.0 - g, g], [g, 1.0]
+    if scheme == DIRK33:
+        # gamma: the root in (1/3, 1/2) of g^3 - 3 g^2 + 3/2 g - 1/6 = 0
+        lo, hi = 1.0 / 3.0, 0.5
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if (mid ** 3 - 3 * mid ** 2 + 1.5 * mid - 1.0 / 6.0) * (lo ** 3 - 3 * lo ** 2 + 1.5 * lo - 1.0 / 6.0) > 0:
+                lo = mid
+            else:
+                hi = mid
+        g = 0.5 * (lo + hi)
+        t2 = (1.0 + g) / 2.0
+        b1 = -(6 * g * g - 16 * g + 1) / 4.0
+        b2 = (6 * g * g - 20 * g + 5) / 4.0
+        return [[g, 0.0, 0.0], [t2 - g, g, 0.0], [b1, b2, g]], [b1, b2, g], [g, t2, 1.0]
+    if scheme == DIRK34:
+        g = np.cos(np.pi / 18.0) / np.sqrt(3.0) + 0.5
+        d = 1.0 / (6.0 * (2.0 * g - 1.0) ** 2)
+        return ([[g, 0.0, 0.0], [0.5 - g, g, 0.0], [2 * g, 1 - 4 * g, g]], [d, 1 - 2 * d, d],
+                [g, 0.5, 1.0 - g])
+    raise ValueError("unknown DIRK scheme")
+
+
 class Oracle:
     """One LDG problem (mesh, p, quadrature, model) on the CPU in FP64."""
 
@@ -125,6 +162,49 @@ class Oracle:
         unm1 = None if unm1 is None else _c(unm1)
         lib().orc_set_time(self._h, scheme, t, dt, _p(un) if un is not None else None,
                            _p(unm1) if unm1 is not None else None)
+
+    def set_radd(self, radd=None):
+        """A constant vector added to every later residual (None clears it)."""
+        self._radd = None if radd is None else _c(radd)
+        lib().orc_set_radd(self._h, _p(self._radd) if self._radd is not None else None)
+
+    def dirk_step(self, u, t, dt, scheme, **newton_kw):
+        """One DIRK step of M du/dt + R_s(u) = 0 from (t, u) to t + dt (Section 2.2 names
+        DIRK as the paper's time scheme). Stage i solves
+            M (U_i - u) / (dt a_ii) + R_s(U_i) + sum_{j<i} (a_ij / a_ii) R_s(U_j) = 0
+        by Newton-GMRES (BDF1 residual with step dt a_ii at t + c_i dt, plus the constant
+        sum), with R_s(U_j) the spatial residual of the converged stage. Stage slopes
+        K_i = -M^{-1} R_s(U_i) follow from U_i = u + dt sum_{j<=i} a_ij K_j, and the step
+        returns u + dt sum_i b_i K_i. Returns (u_new, total Newton stats)."""
+        A, b, c = dirk_tableau(scheme)
+        s = len(b)
+        un = _c(u).copy()
+        Rs, Ks = [], []
+        Ui = un.copy()
+        stats = {"newton_iters": 0, "gmres_iters": 0}
+        for i in range(s):
+            g = A[i][i]
+            radd = np.zeros(self.ndof)
+            for j in range(i):
+                radd += (A[i][j] / g) * Rs[j]
+            self.set_time(1, t + c[i] * dt, g * dt, un)
+            self.set_radd(radd)
+            Ui, rc, st = self.newton(Ui, **newton_kw)
+            if rc != 0:
+                raise RuntimeError(f"oracle DIRK stage {i} did not converge (rc {rc})")
+            stats["newton_iters"] += st["newton_iters"]
+            stats["gmres_iters"] += st["gmres_iters"]
+            self.set_radd(None)
+            self.set_time(0, t + c[i] * dt, 1.0)
+            Rs.append(self.residual(Ui))
+            k = (Ui - un) / (g * dt)
+            for j in range(i):
+                k -= (A[i][j] / g) * Ks[j]
+            Ks.append(k)
+        unew = un.copy()
+        for i in range(s):
+            unew += dt * b[i] * Ks[i]
+        return unew, stats
 
     def residual(self, u):
         u = _c(u)

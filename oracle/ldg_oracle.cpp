@@ -594,6 +594,7 @@ struct Problem {
   int scheme = 0;                             // 0 steady, 1 BDF1, 2 BDF2
   double t = 0, dt = 1;
   std::vector<double> un, unm1;
+  std::vector<double> radd;   // optional constant added to the residual ([E][ncu][npe])
   std::string msg;
 
   // Curved quadrilaterals: x(xi) = sum_a xgeo[K][a] l_a(xi), the degree-pg Lagrange
@@ -1032,6 +1033,9 @@ void residual_elem(const Problem& P, const S* u, int64_t K, QOF qof, S* r) {
         for (int i = 0; i < npe; ++i) r[c * npe + i] = r[c * npe + i] + w * fh[c] * phi[i];
     }
   }
+  // a constant vector added to the residual (the earlier stages' terms of a DIRK stage)
+  if (!P.radd.empty())
+    for (int i = 0; i < ncu * npe; ++i) r[i] = r[i] + P.radd[K * ncu * npe + i];
 }
 
 // Full residual over all elements.
@@ -1201,6 +1205,13 @@ void orc_set_time(void* h, int scheme, double t, double dt, const double* un, co
   P->un.assign(n, 0.0); P->unm1.assign(n, 0.0);
   if (un) std::copy(un, un + n, P->un.begin());
   if (unm1) std::copy(unm1, unm1 + n, P->unm1.begin());
+}
+
+// radd (or null to clear): a constant vector added to every later residual
+void orc_set_radd(void* h, const double* radd) {
+  Problem* P = (Problem*)h;
+  if (radd) P->radd.assign(radd, radd + P->ndof());
+  else P->radd.clear();
 }
 
 void orc_residual(void* h, const double* u, double* r) {

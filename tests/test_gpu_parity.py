@@ -195,3 +195,23 @@ def test_newton_c2_bdf2_step_small():
     assert np.linalg.norm(ug - uo) <= 1e-7 * np.linalg.norm(uo)
     assert np.linalg.norm(o.residual(ug)) <= 1.5e-8 * st["r0"]
 
+
+@pytest.mark.parametrize("model", [oracle.EULER, oracle.NS, oracle.CONVDIFF])
+def test_finite_difference_jvp(model):
+    """The FD variant against the exact J.v: the forward difference is off by O(eps),
+    the central one by O(eps^2) plus rounding, well below the forward one; for the
+    linear model both reproduce R(v) - R(0) up to rounding / eps."""
+    mesh = synth.quad_box((5, 4), hi=(10.0, 10.0), periodic=(True, True), affine=SHEAR2)
+    mu = {oracle.EULER: (1.4,), oracle.NS: (1.4, 10.0, 0.72), oracle.CONVDIFF: (0.05, 0.3, 1.0, 0.5)}[model]
+    o, g = pair(mesh, 3, model, oracle.CASE_VORTEX if model != oracle.CONVDIFF else oracle.CASE_SINSIN, mu=mu)
+    u, v = state(o, mesh, 3), synth.random_vector(o.ndof, 4)
+    ref = o.jvp(u, v)
+    nrm = np.linalg.norm(ref)
+    e1 = np.linalg.norm(host(g.jvp_fd(cuda(u), cuda(v), 1)) - ref) / nrm
+    e2 = np.linalg.norm(host(g.jvp_fd(cuda(u), cuda(v), 2)) - ref) / nrm
+    print(f"FD J.v relative error, model {model}: forward {e1:.2e}, central {e2:.2e}")
+    assert e1 < 1e-5 and e2 < 1e-6
+    if model != oracle.CONVDIFF:
+        assert e2 < 0.1 * e1
+    assert np.all(host(g.jvp_fd(cuda(u), cuda(np.zeros(o.ndof)), 2)) == 0.0)
+

@@ -536,3 +536,52 @@ def test_curved_annulus_area():
     exact = np.pi * 3.75
     e1, e2 = abs(area(3, 8) - exact), abs(area(3, 16) - exact)
     assert e2 < e1 and np.log2(e1 / e2) > 3.8, (e1, e2)
+
+
+# ------------------------------------------------------------------- DIRK time stepping
+def test_dirk_tableaus_meet_their_order_conditions():
+    """Butcher order conditions: row sums c_i = sum_j a_ij; order 1 (sum b = 1), 2
+    (b.c = 1/2), 3 (b.c^2 = 1/3, b.A c = 1/6), 4 (b.c^3 = 1/4, b.(c A c) = 1/8,
+    b.A c^2 = 1/12, b.A A c = 1/24), to each scheme's order; DIRK22/33 are stiffly
+    accurate (b = last row of A)."""
+    conds = [lambda A, b, c: b.sum() - 1,
+             lambda A, b, c: b @ c - 1 / 2,
+             lambda A, b, c: b @ c ** 2 - 1 / 3, lambda A, b, c: b @ A @ c - 1 / 6,
+             lambda A, b, c: b @ c ** 3 - 1 / 4, lambda A, b, c: b @ (c * (A @ c)) - 1 / 8,
+             lambda A, b, c: b @ A @ c ** 2 - 1 / 12, lambda A, b, c: b @ A @ A @ c - 1 / 24]
+    n_conds = {1: 1, 2: 2, 3: 4, 4: 8}
+    for sch, order in ((oracle.DIRK11, 1), (oracle.DIRK22, 2), (oracle.DIRK33, 3), (oracle.DIRK34, 4)):
+        A, b, c = (np.array(x) for x in oracle.dirk_tableau(sch))
+        assert np.allclose(A.sum(1), c, atol=1e-15)
+        assert np.allclose(np.triu(A, 1), 0) and len(set(np.diag(A))) == 1    # singly diagonally implicit
+        for k in range(n_conds[order]):
+            assert abs(conds[k](A, b, c)) < 1e-14, (sch, k)
+        if sch in (oracle.DIRK22, oracle.DIRK33):
+            assert np.allclose(A[-1], b, atol=1e-15)
+
+
+def test_dirk_temporal_order_against_matrix_exponential():
+    """On a linear semi-discrete problem M u' = -(A u + r0) (convection-diffusion on a
+    periodic mesh), DIRK steps converge to the exact solution
+    u* + expm(-t M^-1 A)(u0 - u*) at the scheme's order."""
+    import scipy.linalg as sl
+    mesh = synth.quad_box(3, hi=(2.0, 2.0), periodic=(True, True))
+    o = oracle.Oracle(mesh, 2, oracle.CONVDIFF, oracle.CASE_SINSIN, (0.02, 0.3, 1.0, 0.5))
+    n = o.ndof
+    A = o.jacobian_cs(np.zeros(n))
+    r0 = o.residual(np.zeros(n))
+    M = np.stack([o.mass(e) for e in np.eye(n)], 1)
+    ustar = -np.linalg.solve(A, r0)
+    u0 = o.interpolate()
+    T = 0.25
+    yT = ustar + sl.expm(-T * np.linalg.solve(M, A)) @ (u0 - ustar)
+    for sch, order in ((oracle.DIRK11, 1), (oracle.DIRK22, 2), (oracle.DIRK33, 3), (oracle.DIRK34, 4)):
+        errs = []
+        for N in (16, 32):
+            u, t, dt = u0.copy(), 0.0, T / N
+            for _ in range(N):
+                u, _ = o.dirk_step(u, t, dt, sch, newton_rtol=1e-12, gmres_rtol=1e-12, m=30, max_gmres=5000)
+                t += dt
+            errs.append(np.linalg.norm(u - yT) / np.linalg.norm(yT))
+        rate = np.log2(errs[0] / errs[1])
+        assert rate > order - 0.3, (sch, errs, rate)
