@@ -208,6 +208,14 @@ int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u_dev, const double*
  * otherwise the Jacobian at the other state). precision: LDG_FP64 or LDG_FP32. */
 int ldg_jvp_after_residual(ldg_ctx* ctx, int precision, const double* u_dev, const double* v_dev, double* jv_dev);
 
+/* Finite-difference J(u) v, the variant of Section 3.3 beside the exact derivative:
+ * order 1: (R(u + eps v) - R(u)) / eps; order 2: (R(u + eps v) - R(u - eps v)) / (2 eps),
+ * eps = 2^-26 (1 + ||u||_2) / ||v||_2 (0 when v = 0, giving J v = 0). Two residual
+ * evaluations in FP64, time term included. Truncation error O(eps) (order 1) or
+ * O(eps^2) (order 2), plus rounding of order 2^-52 ||R|| / eps. The first call
+ * allocates 3 n_dof + 4 doubles of context scratch. order not 1 or 2: LDG_ERR_ARG. */
+int ldg_jvp_fd(ldg_ctx* ctx, int order, const double* u_dev, const double* v_dev, double* jv_dev);
+
 /* Exact element-diagonal blocks of J(u): blocks_dev [n_elem][n_loc][n_loc], column-major
  * per element (column l at offset l * n_loc), n_loc = n_cu * n_pe. Convection models use
  * dual numbers with a unit tangent on each element and none on its neighbours; diffusion
@@ -269,6 +277,25 @@ int ldg_newton_gmres(ldg_ctx* ctx, double* u_dev, ldg_solve_report* rep);
 
 /* The same solve with u in HOST memory: copied to the device, solved, copied back. */
 int ldg_newton_gmres_host(ldg_ctx* ctx, double* u_host, ldg_solve_report* rep);
+
+/* DIRK time schemes of ldg_dirk_step (Section 2.2 names DIRK as the paper's scheme):
+ * singly diagonally implicit Runge-Kutta with the tableaus of backward Euler, of
+ * Alexander (1977; L-stable, stiffly accurate; 2 stages order 2, 3 stages order 3)
+ * and of Crouzeix (1975; 3 stages order 4, A-stable). */
+enum { LDG_DIRK11 = 1, LDG_DIRK22 = 2, LDG_DIRK33 = 3, LDG_DIRK34 = 4 };
+
+/* One DIRK step of M du/dt + R_s(u) = 0 from time t to t + dt; u_dev (device, n_dof)
+ * holds u(t) on entry and u(t + dt) on return. Stage i solves, by the context's
+ * Newton-GMRES (same options, preconditioner and graph engine as ldg_newton_gmres),
+ *   M (U_i - u(t)) / (dt a_ii) + R_s(U_i) + sum_{j<i} (a_ij / a_ii) R_s(U_j) = 0
+ * with boundary data at t + c_i dt and U_i starting from the previous stage; R_s(U_j)
+ * is then re-evaluated, the slope K_i follows from U_i = u(t) + dt sum_{j<=i} a_ij K_j,
+ * and u(t + dt) = u(t) + dt sum_i b_i K_i. The context is left steady at t + dt
+ * (ldg_set_time's BDF state is replaced). rep (optional) sums the stages'
+ * iterations; r0 is the first stage's ||R(U_0)||, rfinal the largest stage ratio
+ * ||R(U_i)|| / ||R(U_i^0)|| at exit. The first call allocates 8 n_dof doubles of
+ * context scratch. Errors: a stage's solver status; LDG_ERR_ARG for a bad scheme/dt. */
+int ldg_dirk_step(ldg_ctx* ctx, int scheme, double t, double dt, double* u_dev, ldg_solve_report* rep);
 
 /* J(u) v without any device allocation (the paper has no counterpart; this is a
  * service for callers that cannot allocate). It computes the same product as

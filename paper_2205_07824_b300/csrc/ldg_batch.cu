@@ -64,6 +64,7 @@ struct ldg_batch {
   std::vector<const KernelSet*> cap_ks;   // per group: kernels, time scheme and a0/dt the graph holds
   std::vector<int> cap_scheme;
   std::vector<double> cap_a0dt;
+  std::vector<char> cap_radd;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long k_pre = 0, k_a = 0, k_b = 0, k_c = 0;   // kernels per graph part (captured)
@@ -653,7 +654,8 @@ int ldg_batch_solve(ldg_batch* b, double* u_dev, int use_graph, ldg_solve_report
     bool stale = false;
     for (size_t i = 0; i < b->groups.size(); ++i) {
       const ldg_ctx* c = b->groups[i].ctx;
-      stale |= c->ks != b->cap_ks[i] || c->scheme != b->cap_scheme[i] || c->a0dt != b->cap_a0dt[i];
+      stale |= c->ks != b->cap_ks[i] || c->scheme != b->cap_scheme[i] || c->a0dt != b->cap_a0dt[i] ||
+               c->radd_on != (bool)b->cap_radd[i];
     }
     if (stale) {
       cudaGraphExecDestroy(b->exec);
@@ -674,11 +676,12 @@ int ldg_batch_solve(ldg_batch* b, double* u_dev, int use_graph, ldg_solve_report
       rc = build_graph(b);
       for (BGroup& g : b->groups) g.ctx->stream = s;
       if (rc) return rc;
-      b->cap_ks.clear(); b->cap_scheme.clear(); b->cap_a0dt.clear();
+      b->cap_ks.clear(); b->cap_scheme.clear(); b->cap_a0dt.clear(); b->cap_radd.clear();
       for (const BGroup& g : b->groups) {
         b->cap_ks.push_back(g.ctx->ks);
         b->cap_scheme.push_back(g.ctx->scheme);
         b->cap_a0dt.push_back(g.ctx->a0dt);
+        b->cap_radd.push_back(g.ctx->radd_on ? 1 : 0);
       }
     }
     BK(cudaGraphLaunch(b->exec, s));

@@ -104,6 +104,22 @@ __global__ void k_hist(int64_t n, double c1, const double* a, double c2, const d
   if (i < n) out[i] = c1 * a[i] + (b ? c2 * b[i] : 0.0);
 }
 
+// Finite-difference step eps = sqrt(2^-52) (1 + ||u||) / ||v|| from the squared norms
+// nn = (u.u, v.v): eps[0] = eps, eps[1] = -eps, eps[2] = the difference's weight.
+__global__ void k_fd_eps(const double* nn, double* eps, int order) {
+  const double nu = sqrt(nn[0]), nv = sqrt(nn[1]);
+  const double e = nv > 0.0 ? 1.4901161193847656e-08 * (1.0 + nu) / nv : 0.0;
+  eps[0] = e;
+  eps[1] = -e;
+  eps[2] = e > 0.0 ? (order == 2 ? 0.5 / e : 1.0 / e) : 0.0;
+}
+// out = (a - b) * s[0]
+__global__ void k_fd_diff(const double* a, const double* b, const double* s, double* out, int64_t n) {
+  const double w = *s;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (a[i] - b[i]) * w;
+}
+
 KArgs base_args(ldg_ctx* c) {
   KArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -111,6 +127,7 @@ KArgs base_args(ldg_ctx* c) {
   a.a0dt = c->a0dt; a.t = c->t; a.mp = c->mp; a.E = (int)c->E;
   a.inst = c->ext_inst; a.mtab = c->ext_mtab; a.t_dev = c->d_t;
   a.cgeo = c->d_cgeo; a.cgeof = c->d_cgeof; a.cx = c->d_cx; a.minv = c->d_minv; a.minvf = c->d_minvf;
+  a.radd = c->radd_on ? c->d_radd : nullptr;
   a.blk_col = -1;
   return a;
 }
@@ -944,7 +961,7 @@ int ldg_destroy(ldg_ctx* ctx) {
   cudaFree(ctx->d_ops); cudaFree(ctx->d_opsf); cudaFree(ctx->d_geo); cudaFree(ctx->d_nbr); cudaFree(ctx->d_nbf); cudaFree(ctx->d_perm);
   cudaFree(ctx->d_xn); cudaFree(ctx->d_q); cudaFree(ctx->d_dq); cudaFree(ctx->d_hist);
   cudaFree(ctx->d_cgeo); cudaFree(ctx->d_cgeof); cudaFree(ctx->d_cx); cudaFree(ctx->d_minv); cudaFree(ctx->d_minvf);
-  cudaFree(ctx->d_xnode);
+  cudaFree(ctx->d_xnode); cudaFree(ctx->d_fd); cudaFree(ctx->d_radd); cudaFree(ctx->d_dirk);
   cudaFree(ctx->d_V); cudaFree(ctx->d_r); cudaFree(ctx->d_w); cudaFree(ctx->d_res); cudaFree(ctx->d_x); cudaFree(ctx->d_small); cudaFree(ctx->d_part);
   cudaFree(ctx->d_flags); cudaFree(ctx->d_ticket); cudaFree(ctx->d_t);
   cudaFree(ctx->d_colour); cudaFree(ctx->d_blocks); cudaFree(ctx->d_binv); cudaFree(ctx->d_Z);
@@ -1189,6 +1206,176 @@ int ldg_jvp(ldg_ctx* ctx, const double* u, const double* v, double* jv) {
 int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u, const double* v, double* jv) {
   if (!ctx || !ctx->ks || !u || !v || !jv || (precision != LDG_FP64 && precision != LDG_FP32)) return LDG_ERR_ARG;
   return jvp_args(ctx, base_args(ctx), u, v, jv, precision);
+}
+
+// out = sum_k c[k] x[k] over the non-null x[k] (k < 4); out may alias none of them
+__global__ void k_lincomb4(double* out, int64_t n, double c0, const double* x0, double c1, const double* x1, double c2,
+                           const double* x2, double c3, const double* x3) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    if (x0) s += c0 * x0[i];
+    if (x1) s += c1 * x1[i];
+    if (x2) s += c2 * x2[i];
+    if (x3) s += c3 * x3[i];
+    out[i] = s;
+  }
+}
+
+namespace {
+// Singly diagonally implicit Runge-Kutta tableaus: backward Euler; the L-stable,
+// stiffly accurate two- and three-stage schemes of Alexander (1977) (orders 2, 3);
+// the three-stage order-4 A-stable scheme of Crouzeix (1975).
+struct Dirk {
+  int s = 0;
+  double A[3][3] = {}, b[3] = {}, c[3] = {};
+};
+bool dirk_tableau(int scheme, Dirk& d) {
+  if (scheme == LDG_DIRK11) {
+    d.s = 1; d.A[0][0] = 1.0; d.b[0] = 1.0; d.c[0] = 1.0;
+  } else if (scheme == LDG_DIRK22) {
+    const double g = 1.0 - std::sqrt(0.5);            // g^2 - 2 g + 1/2 = 0
+    d.s = 2;
+    d.A[0][0] = g; d.A[1][0] = 1.0 - g; d.A[1][1] = g;
+    d.b[0] = 1.0 - g; d.b[1] = g; d.c[0] = g; d.c[1] = 1.0;
+  } else if (scheme == LDG_DIRK33) {
+    // g: the root in (1/3, 1/2) of g^3 - 3 g^2 + 3 g / 2 - 1/6 (bisection)
+    auto f = [](double x) { return ((x - 3.0) * x + 1.5) * x - 1.0 / 6.0; };
+    double lo = 1.0 / 3.0, hi = 0.5;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (f(mid) * f(lo) > 0.0) lo = mid; else hi = mid;
+    }
+    const double g = 0.5 * (lo + hi), t2 = 0.5 * (1.0 + g);
+    const double b1 = -(6.0 * g * g - 16.0 * g + 1.0) / 4.0, b2 = (6.0 * g * g - 20.0 * g + 5.0) / 4.0;
+    d.s = 3;
+    d.A[0][0] = g; d.A[1][0] = t2 - g; d.A[1][1] = g; d.A[2][0] = b1; d.A[2][1] = b2; d.A[2][2] = g;
+    d.b[0] = b1; d.b[1] = b2; d.b[2] = g; d.c[0] = g; d.c[1] = t2; d.c[2] = 1.0;
+  } else if (scheme == LDG_DIRK34) {
+    const double g = std::cos(M_PI / 18.0) / std::sqrt(3.0) + 0.5;
+    const double del = 1.0 / (6.0 * (2.0 * g - 1.0) * (2.0 * g - 1.0));
+    d.s = 3;
+    d.A[0][0] = g; d.A[1][0] = 0.5 - g; d.A[1][1] = g; d.A[2][0] = 2.0 * g; d.A[2][1] = 1.0 - 4.0 * g; d.A[2][2] = g;
+    d.b[0] = del; d.b[1] = 1.0 - 2.0 * del; d.b[2] = del; d.c[0] = g; d.c[1] = 0.5; d.c[2] = 1.0 - g;
+  } else {
+    return false;
+  }
+  return true;
+}
+}  // namespace
+
+// Spatial residual R_s(u): no time term, no stage constant.
+int do_residual_spatial(ldg_ctx* ctx, const double* u, double* r) {
+  KArgs a = base_args(ctx);
+  if (ctx->ks->qstage) {
+    a.u = u; a.out = ctx->d_q;
+    CK(ctx->ks->qstage(MODE_R, a, ctx->stream));
+    a = base_args(ctx);
+    a.q = ctx->d_q;
+  }
+  a.u = u; a.out = r;
+  a.hist = nullptr; a.a0dt = 0.0; a.radd = nullptr;
+  CK(ctx->ks->residual(MODE_R, a, ctx->stream));
+  return LDG_OK;
+}
+
+int ldg_dirk_step(ldg_ctx* ctx, int scheme, double t, double dt, double* u, ldg_solve_report* rep) {
+  Dirk d;
+  if (!ctx || !ctx->ks || !u || !(dt > 0) || !dirk_tableau(scheme, d)) return LDG_ERR_ARG;
+  const int64_t n = ctx->ndof;
+  if (!ctx->d_radd) CK(cudaMalloc(&ctx->d_radd, n * sizeof(double)));
+  if (!ctx->d_dirk) CK(cudaMalloc(&ctx->d_dirk, (size_t)7 * n * sizeof(double)));
+  double* un = ctx->d_dirk;                      // u at the start of the step
+  double* Rs[3] = {un + n, un + 2 * n, un + 3 * n};      // spatial residuals of the stages
+  double* K[3] = {un + 4 * n, un + 5 * n, un + 6 * n};   // stage slopes
+  const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8);
+  CK(cudaMemcpyAsync(un, u, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  ldg_solve_report total{};
+  int rc = LDG_OK;
+  for (int i = 0; i < d.s && !rc; ++i) {
+    const double g = d.A[i][i];
+    // radd = sum_{j<i} (a_ij / a_ii) R_s(U_j)
+    const double* x[3] = {nullptr, nullptr, nullptr};
+    double cf[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < i; ++j) { x[j] = Rs[j]; cf[j] = d.A[i][j] / g; }
+    k_lincomb4<<<g1, 256, 0, ctx->stream>>>(ctx->d_radd, n, cf[0], x[0], cf[1], x[1], cf[2], x[2], 0.0, nullptr);
+    count_launch();
+    CK(cudaGetLastError());
+    // stage residual: M (U - u^n) / (g dt) + R_s(U) + radd, at t + c_i dt
+    if ((rc = ldg_set_time(ctx, LDG_BDF1, t + d.c[i] * dt, g * dt, un, nullptr))) break;
+    ctx->radd_on = true;
+    ldg_solve_report r{};
+    rc = ldg_newton_gmres(ctx, u, &r);
+    ctx->radd_on = false;
+    total.newton_iters += r.newton_iters;
+    total.gmres_iters += r.gmres_iters;
+    total.jv_calls += r.jv_calls;
+    total.residual_calls += r.residual_calls;
+    total.pc_setups += r.pc_setups;
+    total.pc_fallbacks += r.pc_fallbacks;
+    if (i == 0) total.r0 = r.r0;
+    total.rfinal = std::max(total.rfinal, r.rfinal / (r.r0 > 0 ? r.r0 : 1.0));
+    total.lin_resid = std::max(total.lin_resid, r.lin_resid);
+    if (rc) break;
+    if ((rc = do_residual_spatial(ctx, u, Rs[i]))) break;
+    // K_i = (U_i - u^n) / (g dt) - sum_{j<i} (a_ij / g) K_j
+    const double* kx[3] = {nullptr, nullptr, nullptr};
+    double kc[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < i; ++j) { kx[j] = K[j]; kc[j] = -d.A[i][j] / g; }
+    k_lincomb4<<<g1, 256, 0, ctx->stream>>>(K[i], n, 1.0 / (g * dt), u, -1.0 / (g * dt), un, kc[0], kx[0],
+                                            kc[1], kx[1]);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+  if (!rc) {
+    // u^{n+1} = u^n + dt sum_i b_i K_i
+    k_lincomb4<<<g1, 256, 0, ctx->stream>>>(u, n, 1.0, un, dt * d.b[0], K[0], d.s > 1 ? dt * d.b[1] : 0.0,
+                                            d.s > 1 ? K[1] : nullptr, d.s > 2 ? dt * d.b[2] : 0.0,
+                                            d.s > 2 ? K[2] : nullptr);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+  // the context is left steady at the end time
+  const int rc2 = ldg_set_time(ctx, LDG_STEADY, t + dt, 1.0, nullptr, nullptr);
+  if (rep) {
+    total.status = rc;
+    total.elapsed_ms = 0.0;
+    *rep = total;
+  }
+  return rc ? rc : rc2;
+}
+
+int ldg_jvp_fd(ldg_ctx* ctx, int order, const double* u, const double* v, double* jv) {
+  if (!ctx || !ctx->ks || !u || !v || !jv || (order != 1 && order != 2)) return LDG_ERR_ARG;
+  const int64_t n = ctx->ndof;
+  if (!ctx->d_fd) CK(cudaMalloc(&ctx->d_fd, (3 * n + 4) * sizeof(double)));
+  double* w = ctx->d_fd;
+  double* rp = w + n;
+  double* rm = w + 2 * n;
+  double* sc = w + 3 * n;   // u.u, v.v, then (eps, -eps, weight) from sc + 2 on
+  int rc;
+  if ((rc = dots(ctx, u, n, 1, u, sc, nullptr))) return rc;
+  if ((rc = dots(ctx, v, n, 1, v, sc + 1, nullptr))) return rc;
+  // scalars move to sc[0..2] only after both norms are read
+  double* eps = sc;
+  k_fd_eps<<<1, 1, 0, ctx->stream>>>(sc, eps, order);
+  count_launch();
+  const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8);
+  CK(cudaMemcpyAsync(w, u, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  k_axpy_dev<<<g1, 256, 0, ctx->stream>>>(v, eps, w, n);
+  count_launch();
+  if ((rc = do_residual(ctx, w, rp))) return rc;
+  if (order == 2) {
+    CK(cudaMemcpyAsync(w, u, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    k_axpy_dev<<<g1, 256, 0, ctx->stream>>>(v, eps + 1, w, n);
+    count_launch();
+    if ((rc = do_residual(ctx, w, rm))) return rc;
+  } else {
+    if ((rc = do_residual(ctx, u, rm))) return rc;
+  }
+  k_fd_diff<<<g1, 256, 0, ctx->stream>>>(rp, rm, eps + 2, jv, n);
+  count_launch();
+  CK(cudaGetLastError());
+  return LDG_OK;
 }
 
 int ldg_jvp_after_residual(ldg_ctx* ctx, int precision, const double* u, const double* v, double* jv) {

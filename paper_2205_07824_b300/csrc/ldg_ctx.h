@@ -38,6 +38,9 @@ struct ldg_ctx {
   double* d_q = nullptr;       // q(u) scratch [E][ncu][dim][npe]
   double* d_dq = nullptr;      // q(v) scratch
   double* d_hist = nullptr;    // BDF history term
+  double* d_radd = nullptr;    // DIRK stage: constant added to the residual (active when radd_on)
+  bool radd_on = false;
+  double* d_dirk = nullptr;    // DIRK work: u^n, then the stages' spatial residuals and slopes
   // time scheme
   int scheme = LDG_STEADY;
   double t = 0.0, dt = 1.0, a0dt = 0.0;
@@ -66,6 +69,7 @@ struct ldg_ctx {
   void* d_binv = nullptr;      // their inverses (float or double)
   int binv_prec = -1;
   double* d_Z = nullptr;       // [m][ndof] preconditioned Krylov vectors (flexible GMRES)
+  double* d_fd = nullptr;      // finite-difference J.v: three work vectors and four scalars
   double* d_probe = nullptr;   // probing work vectors (linear models)
   double* d_jp = nullptr;
   int* d_status = nullptr;

@@ -49,6 +49,7 @@ struct KArgs {
   const void* q;              // [E][NCU][DIM][NPE] q(u) (R, JV) or q(v) (HOM), models with q
   const void* dq;             // [E][NCU][DIM][NPE] Q v, the tangent of q (JV, nonlinear models with q)
   const void* hist;           // [E][NCU][NPE]     BDF history term, or null
+  const double* radd;         // [E][NCU][NPE]     constant added to R in MODE_R (DIRK stage terms), or null
   void* out;                  // [E][NCU][NPE] residual / J.v, or [E][NCU][DIM][NPE] q
   const double* geo;          // [E][GEO] per-element affine geometry
   const double* cgeo;         // curved quadrilaterals: [E][CGeo::SIZE] per-point metrics (FP64) ...
@@ -878,6 +879,9 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
     if (MODE == MODE_JV && a.blk_col >= 0) {
       constexpr int NLOC = NCU * NPE;
       a.blk_out[((size_t)(e0 + e) * NLOC + a.blk_col) * NLOC + (it - e * NLOC)] = (double)s;
+    } else if (MODE == MODE_R && a.radd) {
+      const size_t gi = (size_t)e0 * NCU * NPE + it;
+      out[gi] = (double)s + a.radd[gi];
     } else {
       out[(size_t)e0 * NCU * NPE + it] = (double)s;
     }

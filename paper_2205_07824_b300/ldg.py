@@ -20,6 +20,7 @@ POISSON, CONVDIFF, EULER, NS = 0, 1, 2, 3
 (CASE_ZERO, CASE_SINSIN, CASE_EXPSIN, CASE_POLY2, CASE_LINEAR, CASE_VORTEX, CASE_CONST, CASE_ROTATION,
  CASE_CYLINDER, CASE_REST, CASE_CYLINDER_START) = range(11)
 STEADY, BDF1, BDF2 = 0, 1, 2
+DIRK11, DIRK22, DIRK33, DIRK34 = 1, 2, 3, 4
 FP64, FP32 = 0, 1
 PC_NONE, PC_BJACOBI, PC_MLP = 0, 1, 2
 STATUS = {0: "LDG_OK", -1: "LDG_ERR_ARG", -2: "LDG_ERR_CUDA", -3: "LDG_ERR_UNSUPPORTED",
@@ -120,6 +121,8 @@ def lib():
         L.ldg_jvp_noalloc.argtypes = [vp, dp, dp, dp]
         L.ldg_jvp_prec.argtypes = [vp, ctypes.c_int, dp, dp, dp]
         L.ldg_jvp_after_residual.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+        L.ldg_jvp_fd.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+        L.ldg_dirk_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, ctypes.c_void_p]
         L.ldg_diag_blocks.argtypes = [vp, ctypes.c_int, dp, dp]
         L.ldg_precond_setup.argtypes = [vp, dp]
         L.ldg_precond_apply.argtypes = [vp, dp, dp]
@@ -266,6 +269,21 @@ class LDG:
         out = self.empty() if out is None else out
         n = self.n_dof
         self._check(lib().ldg_jvp_prec(self._h, precision, _ptr(u, n, "u"), _ptr(v, n, "v"), _ptr(out, n, "out")))
+        return out
+
+    def dirk_step(self, u, t: float, dt: float, scheme: int = 3, check=True):
+        """One DIRK step in place from t to t + dt (scheme: DIRK11/22/33/34 = 1..4)."""
+        rep = SolveReport()
+        rc = lib().ldg_dirk_step(self._h, scheme, t, dt, _ptr(u, self.n_dof, "u"), ctypes.byref(rep))
+        if check:
+            self._check(rc)
+        return rep.as_dict()
+
+    def jvp_fd(self, u, v, order: int = 1, out=None):
+        """Finite-difference J.v (order 1 forward, 2 central) from two FP64 residuals."""
+        out = self.empty() if out is None else out
+        n = self.n_dof
+        self._check(lib().ldg_jvp_fd(self._h, order, _ptr(u, n, "u"), _ptr(v, n, "v"), _ptr(out, n, "out")))
         return out
 
     def jvp_after_residual(self, precision: int, u, v, out=None):
