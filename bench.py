@@ -187,6 +187,7 @@ def graph_time_ms(g, fn, reps):
     captured back to back in a CUDA graph, one replay timed with CUDA events, so that
     the host's per-call overhead does not hide the kernels' own duration."""
     import torch
+    reps = max(int(reps), 20)     # one replay of a short graph carries launch overhead
     old = g.stream
     s = torch.cuda.Stream()
     g.set_stream(s)
@@ -199,7 +200,8 @@ def graph_time_ms(g, fn, reps):
         with torch.cuda.graph(cg, stream=s):
             for _ in range(reps):
                 fn()
-        cg.replay()
+        for _ in range(2):
+            cg.replay()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         cur = torch.cuda.current_stream()
@@ -652,8 +654,14 @@ def run_cylinder(args):
     except Exception:
         hbm, peak_src = 6400.0, "fallback 6.4 TB/s (of fallback)"
     achieved = b_alg / (jvt[1] * 1e-3) / 1e9
+    # DRAM reads of the pair per DOF from one ncu capture of the same kernels on the
+    # 1/16-scaled cylinder mesh (profiles/ncu_c5_ns_jv_pair_curved_p3_scaled16.md),
+    # scaled by the DOF count (traffic grows with the elements)
+    traffic = (9.679104e6 + 5.784832e6) / 160000.0 * n
     roofline = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": hbm, "frac": achieved / hbm,
-                "traffic": None, "peak_source": peak_src,
+                "traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum of the pair on the 2,500-element "
+                                                      "mesh, scaled by DOF (writes stayed in L2 in that capture)",
+                "peak_source": peak_src,
                 "kernel": "k_qstage_curved<CurvedQuadEl<3,5>, NSModel, MODE_HOM, float> + "
                           "k_residual<CurvedQuadEl<3,5>, NSModel, MODE_JV, float>",
                 "launch_pair_ms": jvt[1], "fp64_pair_ms": jvt[0], "bytes_per_jv": b_alg,
