@@ -129,7 +129,7 @@ class Oracle:
 
     def __init__(self, mesh, p: int, model: int, case: int, mu=(), nq1: int | None = None):
         if nq1 is None:
-            nq1 = p + 2 if (model in (EULER, NS) or mesh.etype == 0) else p + 1
+            nq1 = p + 2 if (model in (EULER, NS) or mesh.etype in (0, 3)) else p + 1
         self.mesh, self.p, self.nq1, self.model, self.case = mesh, p, nq1, model, case
         xyz = _c(mesh.xyz)
         vid = _c(mesh.vid, np.int64)
@@ -289,7 +289,7 @@ class Oracle:
         return u, rc, {k: getattr(st, k) for k, _ in _Stats._fields_}
 
     def neighbours(self):
-        nf = {0: 3, 1: 4, 2: 6}[self.mesh.etype]
+        nf = {0: 3, 1: 4, 2: 6, 3: 4}[self.mesh.etype]
         nb = np.empty(self.mesh.n_elem * nf, dtype=np.int64)
         lib().orc_neighbours(self._h, nb.ctypes.data_as(_I64))
         return nb.reshape(self.mesh.n_elem, nf)

@@ -196,14 +196,14 @@ void lu_solve(const std::vector<double>& LU, int n, const std::vector<int>& piv,
 }
 
 // ------------------------------------------------------- reference elements
-enum { TRI = 0, QUAD = 1, HEX = 2 };
+enum { TRI = 0, QUAD = 1, HEX = 2, TET = 3 };
 
 struct Ref {
   int type, nd, p, npe, nv, nf, nq1, nfq;
   std::vector<double> gll;                       // tensor elements: 1-D nodes
   std::vector<std::array<double, 3>> node;       // reference node coordinates
-  std::vector<std::array<int, 2>> mono;          // triangle: monomial exponents
-  std::vector<double> coef;                      // triangle: phi_i = sum_m coef[m*npe+i] mono_m
+  std::vector<std::array<int, 3>> mono;          // simplices: monomial exponents
+  std::vector<double> coef;                      // simplices: phi_i = sum_m coef[m*npe+i] mono_m
   std::vector<std::array<double, 3>> qx;         // volume quadrature
   std::vector<double> qw;
   std::vector<std::array<double, 2>> fs;         // face quadrature (face parameter)
@@ -222,13 +222,13 @@ struct Ref {
         for (int i = 0; i + j <= p; ++i)
           node.push_back({-1.0 + 2.0 * i / p, -1.0 + 2.0 * j / p, 0.0});
       for (int a = 0; a <= p; ++a)
-        for (int b = 0; a + b <= p; ++b) mono.push_back({a, b});
+        for (int b = 0; a + b <= p; ++b) mono.push_back({a, b, 0});
       // phi_i is the unique degree-p polynomial with phi_i(node_j) = delta_ij:
       // coef = V^{-1}, V[j][m] = mono_m(node_j).
       std::vector<double> V(npe * npe);
       for (int j = 0; j < npe; ++j)
         for (int m = 0; m < npe; ++m)
-          V[j * npe + m] = std::pow(node[j][0], mono[m][0]) * std::pow(node[j][1], mono[m][1]);
+          V[j * npe + m] = std::pow(node[j][0], mono[m][0]) * std::pow(node[j][1], mono[m][1]);   // 2-D
       std::vector<int> piv;
       lu_factor(V, npe, piv);
       coef.assign(npe * npe, 0.0);
@@ -248,6 +248,50 @@ struct Ref {
       for (int k = 0; k < nq1; ++k) { fs.push_back({gx[k], 0.0}); fw.push_back(gw[k]); }
       fverts = {{0, 1}, {1, 2}, {2, 0}};
       axisv = {1, 2};
+    } else if (type == TET) {
+      // reference tetrahedron with vertices (-1,-1,-1), (1,-1,-1), (-1,1,-1), (-1,-1,1)
+      nd = 3; nv = 4; nf = 4;
+      npe = (p + 1) * (p + 2) * (p + 3) / 6;
+      for (int k = 0; k <= p; ++k)
+        for (int j = 0; j + k <= p; ++j)
+          for (int i = 0; i + j + k <= p; ++i)
+            node.push_back({-1.0 + 2.0 * i / p, -1.0 + 2.0 * j / p, -1.0 + 2.0 * k / p});
+      for (int a = 0; a <= p; ++a)
+        for (int b = 0; a + b <= p; ++b)
+          for (int c = 0; a + b + c <= p; ++c) mono.push_back({a, b, c});
+      std::vector<double> V(npe * npe);
+      for (int j = 0; j < npe; ++j)
+        for (int m = 0; m < npe; ++m)
+          V[j * npe + m] = std::pow(node[j][0], mono[m][0]) * std::pow(node[j][1], mono[m][1]) *
+                           std::pow(node[j][2], mono[m][2]);
+      std::vector<int> piv;
+      lu_factor(V, npe, piv);
+      coef.assign(npe * npe, 0.0);
+      for (int i = 0; i < npe; ++i) {
+        std::vector<double> e(npe, 0.0);
+        e[i] = 1.0;
+        lu_solve(V, npe, piv, e.data());
+        for (int m = 0; m < npe; ++m) coef[m * npe + i] = e[m];
+      }
+      // collapsed (Duffy) Gauss rule: xi = (1+a)(1-b)(1-c)/4 - 1, eta = (1+b)(1-c)/2 - 1,
+      // zeta = c, with Jacobian (1-b)(1-c)^2 / 8
+      for (int kc = 0; kc < nq1; ++kc)
+        for (int jb = 0; jb < nq1; ++jb)
+          for (int ia = 0; ia < nq1; ++ia) {
+            const double a = gx[ia], b = gx[jb], c = gx[kc];
+            qx.push_back({(1 + a) * (1 - b) * (1 - c) / 4 - 1, (1 + b) * (1 - c) / 2 - 1, c});
+            qw.push_back(gw[ia] * gw[jb] * gw[kc] * (1 - b) * (1 - c) * (1 - c) / 8);
+          }
+      // faces: the collapsed triangle rule in the face parameters (s, t) of the reference
+      // triangle, face f opposite vertex f
+      for (int jb = 0; jb < nq1; ++jb)
+        for (int ia = 0; ia < nq1; ++ia) {
+          const double a = gx[ia], b = gx[jb];
+          fs.push_back({(1 + a) * (1 - b) / 2 - 1, b});
+          fw.push_back(gw[ia] * gw[jb] * (1 - b) / 2);
+        }
+      fverts = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+      axisv = {1, 2, 3};
     } else {
       nd = (type == QUAD) ? 2 : 3;
       nv = 1 << nd; nf = 2 * nd;
@@ -281,6 +325,13 @@ struct Ref {
 
   // Reference coordinates of face parameter s on face f.
   void face_xi(int f, const double* s, double* xi) const {
+    if (type == TET) {
+      static const double V[4][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+      const int A = fverts[f][0], B = fverts[f][1], C = fverts[f][2];
+      for (int d = 0; d < 3; ++d)
+        xi[d] = V[A][d] + 0.5 * (1 + s[0]) * (V[B][d] - V[A][d]) + 0.5 * (1 + s[1]) * (V[C][d] - V[A][d]);
+      return;
+    }
     if (type == TRI) {
       static const double V[3][2] = {{-1, -1}, {1, -1}, {-1, 1}};
       const int A = fverts[f][0], B = fverts[f][1];
@@ -296,6 +347,22 @@ struct Ref {
 
   // Basis values phi[i] and reference gradients dphi[i*nd + k] at reference point xi.
   void basis(const double* xi, double* phi, double* dphi) const {
+    if (type == TET) {
+      for (int i = 0; i < npe; ++i) { phi[i] = 0; dphi[3 * i] = 0; dphi[3 * i + 1] = 0; dphi[3 * i + 2] = 0; }
+      for (int m = 0; m < npe; ++m) {
+        const int a = mono[m][0], b = mono[m][1], c = mono[m][2];
+        const double X = std::pow(xi[0], a), Y = std::pow(xi[1], b), Z = std::pow(xi[2], c);
+        const double v = X * Y * Z;
+        const double dx = a ? a * std::pow(xi[0], a - 1) * Y * Z : 0.0;
+        const double dy = b ? b * X * std::pow(xi[1], b - 1) * Z : 0.0;
+        const double dz = c ? c * X * Y * std::pow(xi[2], c - 1) : 0.0;
+        for (int i = 0; i < npe; ++i) {
+          const double cf = coef[m * npe + i];
+          phi[i] += cf * v; dphi[3 * i] += cf * dx; dphi[3 * i + 1] += cf * dy; dphi[3 * i + 2] += cf * dz;
+        }
+      }
+      return;
+    }
     if (type == TRI) {
       for (int i = 0; i < npe; ++i) { phi[i] = 0; dphi[2 * i] = 0; dphi[2 * i + 1] = 0; }
       for (int m = 0; m < npe; ++m) {
@@ -755,7 +822,7 @@ bool setup(Problem& P, int etype, int p, int nq1, int64_t E, const double* xyz, 
     for (int k = 0; k < nd; ++k)
       for (int d = 0; d < nd; ++d) M[d][k] = X[P.ref.axisv[k] * nd + d] - X[d];
     // affine elements only: every vertex must be the affine image of its reference vertex
-    if (etype != TRI && !P.curved())
+    if (etype != TRI && etype != TET && !P.curved())
       for (int v = 0; v < nv; ++v)
         for (int d = 0; d < nd; ++d) {
           double e = X[d];
@@ -1172,7 +1239,7 @@ void* orc_create_curved(int etype, int p, int nq1, int64_t E, const double* xyz,
   Problem* P = new Problem();
   P->model.kind = model;
   P->model.cas = cas;
-  int nd = etype == HEX ? 3 : 2;
+  int nd = (etype == HEX || etype == TET) ? 3 : 2;
   P->model.nd = nd;
   P->model.ncu = (model == EULER || model == NS) ? 4 : 1;
   if (model == POISSON) { if (nmu > 0) P->model.kappa = mu[0]; if (nmu > 1) P->model.tau = mu[1]; }

@@ -30,9 +30,9 @@ from dataclasses import dataclass
 
 import numpy as np
 
-TRI, QUAD, HEX = 0, 1, 2
-NV = {TRI: 3, QUAD: 4, HEX: 8}
-ND = {TRI: 2, QUAD: 2, HEX: 3}
+TRI, QUAD, HEX, TET = 0, 1, 2, 3
+NV = {TRI: 3, QUAD: 4, HEX: 8, TET: 4}
+ND = {TRI: 2, QUAD: 2, HEX: 3, TET: 3}
 
 
 @dataclass
@@ -272,6 +272,42 @@ def cylinder_mesh(n_r: int = 100, n_theta: int = 400, pg: int = 3, seed: int = 7
     first layer of thickness 0.01, interior nodes jittered by +- 10% of the spacing."""
     return o_grid(n_r, n_theta, pg, 0.5, ("rect", (-10.0, 30.0, -10.0, 10.0)), first=0.01, jitter=0.2,
                   seed=seed)
+
+
+def tet_cube(n: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(False, False, False),
+             affine: np.ndarray | None = None) -> Mesh:
+    """n^3 cubes of the box [lo, hi], each split into the 6 tetrahedra that share its
+    (0,0,0)-(1,1,1) diagonal (one per monotone path along the cube's edges), so that
+    neighbouring cubes' faces match: 6 n^3 elements. Each tetrahedron's vertices are
+    ordered so that its three edges from the first vertex are right-handed."""
+    h = [(hi[a] - lo[a]) / n for a in range(3)]
+    vid = _grid_ids((n, n, n), periodic)
+    paths = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    E = 6 * n ** 3
+    xyz = np.empty((E, 4, 3))
+    ids = np.empty((E, 4), dtype=np.int64)
+    e = 0
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                for path in paths:
+                    corner = [0, 0, 0]
+                    verts = [tuple(corner)]
+                    for ax in path:
+                        corner[ax] += 1
+                        verts.append(tuple(corner))
+                    pts = [np.array([lo[0] + (i + a) * h[0], lo[1] + (j + b) * h[1], lo[2] + (k + c) * h[2]])
+                           for a, b, c in verts]
+                    vv = [vid(i + a, j + b, k + c) for a, b, c in verts]
+                    if np.linalg.det(np.stack([pts[1] - pts[0], pts[2] - pts[0], pts[3] - pts[0]])) < 0:
+                        pts[1], pts[2] = pts[2], pts[1]
+                        vv[1], vv[2] = vv[2], vv[1]
+                    xyz[e] = pts
+                    ids[e] = vv
+                    e += 1
+    if affine is not None:
+        xyz = xyz @ np.asarray(affine, dtype=np.float64).T
+    return Mesh(TET, xyz, ids, f"tet{n}")
 
 
 def random_vector(n: int, seed: int, scale: float = 1.0) -> np.ndarray:

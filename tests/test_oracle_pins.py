@@ -22,7 +22,7 @@ SHEAR3 = np.array([[1.0, 0.2, 0.1], [0.0, 0.9, 0.15], [0.05, 0.0, 1.1]])
 
 
 def _mesh(etype, n, **kw):
-    return {0: synth.tri_square, 1: synth.quad_box, 2: synth.hex_box}[etype](n, **kw)
+    return {0: synth.tri_square, 1: synth.quad_box, 2: synth.hex_box, 3: synth.tet_cube}[etype](n, **kw)
 
 
 # ---------------------------------------------------------------- reference rules
@@ -63,6 +63,38 @@ def test_triangle_rule_exactness(nq1):
             assert abs(got - _tri_monomial_integral(a, b)) < 1e-13, (a, b)
 
 
+def _tet_monomial_integral(a, b, c):
+    # integral of xi^a eta^b zeta^c over the reference tetrahedron: with xi = 2s - 1 etc.
+    # on the unit tetrahedron, int s^m t^n r^l = m! n! l! / (m + n + l + 3)!
+    tot = 0.0
+    for m in range(a + 1):
+        for n in range(b + 1):
+            for l in range(c + 1):
+                cf = (math.comb(a, m) * math.comb(b, n) * math.comb(c, l) * 2 ** (m + n + l)
+                      * (-1) ** (a - m + b - n + c - l))
+                tot += cf * math.factorial(m) * math.factorial(n) * math.factorial(l) / math.factorial(m + n + l + 3)
+    return 8 * tot
+
+
+@pytest.mark.parametrize("nq1", [2, 3, 4])
+def test_tetrahedron_rule_exactness(nq1):
+    """The collapsed Gauss rule with nq1 points per direction is exact to total degree
+    2 nq1 - 3 (its Jacobian factor (1-b)(1-c)^2 / 8 spends two degrees in c)."""
+    o = oracle.Oracle(synth.tet_cube(1), 1, oracle.POISSON, oracle.CASE_ZERO, nq1=nq1)
+    _, qx, qw, fs, fw = o.ref_rules()
+    deg = 2 * nq1 - 3
+    for a in range(deg + 1):
+        for b in range(deg + 1 - a):
+            for c in range(deg + 1 - a - b):
+                got = np.sum(qw * qx[:, 0] ** a * qx[:, 1] ** b * qx[:, 2] ** c)
+                assert abs(got - _tet_monomial_integral(a, b, c)) < 1e-13, (a, b, c)
+    # faces: the collapsed triangle rule in the face parameters
+    for a in range(2 * nq1 - 1):
+        for b in range(2 * nq1 - 1 - a):
+            got = np.sum(fw * fs[:, 0] ** a * fs[:, 1] ** b)
+            assert abs(got - _tri_monomial_integral(a, b)) < 1e-13, (a, b)
+
+
 @pytest.mark.parametrize("etype", [1, 2])
 def test_tensor_rule_exactness(etype):
     nq1 = 3
@@ -80,7 +112,8 @@ def test_tensor_rule_exactness(etype):
             assert abs(got - ref) < 1e-13
 
 
-@pytest.mark.parametrize("etype,p", [(0, 1), (0, 2), (0, 3), (1, 1), (1, 3), (1, 5), (2, 2), (2, 4)])
+@pytest.mark.parametrize("etype,p", [(0, 1), (0, 2), (0, 3), (1, 1), (1, 3), (1, 5), (2, 2), (2, 4), (3, 1), (3, 2),
+                                     (3, 3)])
 def test_basis_partition_and_kronecker(etype, p):
     o = oracle.Oracle(_mesh(etype, 1), p, oracle.POISSON, oracle.CASE_ZERO)
     nodes = o.ref_rules()[0]
@@ -90,6 +123,11 @@ def test_basis_partition_and_kronecker(etype, p):
     pts = rng.uniform(-1, 1, (20, 3))
     if etype == 0:
         pts[:, :2] = np.where((pts[:, 0] + pts[:, 1] > 0)[:, None], -pts[:, :2], pts[:, :2])
+    if etype == 3:
+        # points of the reference tetrahedron: barycentric draws
+        lam = rng.dirichlet(np.ones(4), 20)
+        V = np.array([[-1, -1, -1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=float)
+        pts = lam @ V
     phi, dphi = o.basis(pts)
     assert np.allclose(phi.sum(1), 1, atol=1e-12)
     assert np.allclose(dphi.sum(1), 0, atol=1e-11)
@@ -100,11 +138,13 @@ def test_basis_partition_and_kronecker(etype, p):
     (0, 1, oracle.POISSON, oracle.CASE_LINEAR), (0, 2, oracle.POISSON, oracle.CASE_POLY2),
     (0, 3, oracle.CONVDIFF, oracle.CASE_POLY2), (1, 1, oracle.CONVDIFF, oracle.CASE_LINEAR),
     (1, 2, oracle.POISSON, oracle.CASE_POLY2), (1, 3, oracle.CONVDIFF, oracle.CASE_POLY2),
-    (2, 2, oracle.CONVDIFF, oracle.CASE_POLY2), (2, 1, oracle.POISSON, oracle.CASE_LINEAR)])
+    (2, 2, oracle.CONVDIFF, oracle.CASE_POLY2), (2, 1, oracle.POISSON, oracle.CASE_LINEAR),
+    (3, 1, oracle.POISSON, oracle.CASE_LINEAR), (3, 2, oracle.CONVDIFF, oracle.CASE_POLY2),
+    (3, 3, oracle.POISSON, oracle.CASE_POLY2)])
 def test_patch_test(etype, p, model, case):
     """Consistency + uniqueness of LDG: a polynomial of degree <= p (with q = -grad u
     and the matching source/boundary data) has zero residual."""
-    aff = SHEAR3 if etype == 2 else SHEAR2
+    aff = SHEAR3 if etype >= 2 else SHEAR2
     mesh = _mesh(etype, 3 if etype < 2 else 2, affine=aff)
     mu = (0.7, 1.3) if model == oracle.POISSON else (0.05, 0.4, 1.0, -0.6, 0.3)
     o = oracle.Oracle(mesh, p, model, case, mu)
@@ -117,12 +157,12 @@ NS_MU = (1.4, 10.0, 0.72)          # gamma, Re, Pr (penalty tau = 1/Re)
 
 
 @pytest.mark.parametrize("etype,model", [(0, oracle.POISSON), (1, oracle.CONVDIFF), (2, oracle.CONVDIFF),
-                                         (1, oracle.EULER), (1, oracle.NS)])
+                                         (1, oracle.EULER), (1, oracle.NS), (3, oracle.CONVDIFF)])
 def test_conservation_periodic(etype, model):
     """Single-valued numerical fluxes and sum_i phi_i = 1: on a periodic mesh with no
     source, the sum of all element residuals vanishes for any state."""
     n = 3
-    nd = 3 if etype == 2 else 2
+    nd = 3 if etype in (2, 3) else 2
     mesh = _mesh(etype, n, hi=(2.0,) * nd, periodic=(True,) * nd)
     mu = {oracle.POISSON: (1.0, 1.0), oracle.CONVDIFF: (0.1, 0.2, 1.0, 0.5, 0.25), oracle.EULER: (1.4,),
           oracle.NS: NS_MU}[model]
@@ -232,14 +272,14 @@ def test_euler_riemann_jump_closed_form():
 
 # ------------------------------------------------------------------- J.v pins
 @pytest.mark.parametrize("etype,model", [(0, oracle.POISSON), (2, oracle.CONVDIFF), (1, oracle.EULER),
-                                         (1, oracle.NS)])
+                                         (1, oracle.NS), (3, oracle.CONVDIFF)])
 def test_jvp_matches_complex_step_jacobian(etype, model):
     if model in (oracle.EULER, oracle.NS):
         mesh = synth.quad_box(3, hi=(10.0, 10.0), periodic=(True, True), affine=SHEAR2)
         o = oracle.Oracle(mesh, 2, model, oracle.CASE_VORTEX, (1.4,) if model == oracle.EULER else NS_MU)
         u = synth.random_euler_state(mesh.n_elem, o.npe, 11)
     else:
-        mesh = _mesh(etype, 2, affine=SHEAR3 if etype == 2 else SHEAR2)
+        mesh = _mesh(etype, 2, affine=SHEAR3 if etype >= 2 else SHEAR2)
         o = oracle.Oracle(mesh, 1 if etype == 2 else 2, model, oracle.CASE_SINSIN,
                           (1.0, 1.0) if model == oracle.POISSON else (0.1, 0.3, 1.0, 0.5, 0.25))
         u = synth.random_vector(o.ndof, 11)
@@ -585,3 +625,23 @@ def test_dirk_temporal_order_against_matrix_exponential():
             errs.append(np.linalg.norm(u - yT) / np.linalg.norm(yT))
         rate = np.log2(errs[0] / errs[1])
         assert rate > order - 0.3, (sch, errs, rate)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_tetrahedral_rates_match_table3(p):
+    """Section 4.1 / Table 3: Poisson with u = sin(pi x) sin(pi y) sin(pi z) on structured
+    tetrahedral meshes of the unit cube. Between the table's first two refinements
+    (1/n = 2, 4) the rates of u_h and q_h agree with the table's within 0.3 (the traces
+    and penalty of the paper are not given, so the error values themselves differ), and
+    they already exceed p + 1/2 and p - 1/3."""
+    gold = json.load(open(os.path.join(GOLD, "table3_rates.json")))
+    errs = []
+    for n in (2, 4):
+        o = oracle.Oracle(synth.tet_cube(n), p, oracle.POISSON, oracle.CASE_SINSIN, (1.0, 1.0))
+        errs.append(o.l2_error(_solve_linear(o)))
+    e = np.array(errs)
+    ru, rq = np.log2(e[0, 0] / e[1, 0]), np.log2(e[0, 1] / e[1, 1])
+    assert abs(ru - gold["u_rate_n2_to_n4"][str(p)]) < 0.3, ru
+    assert abs(rq - gold["q_rate_n2_to_n4"][str(p)]) < 0.3, rq
+    assert ru > p + 0.5 and rq > p - 1 / 3, (ru, rq)
+
