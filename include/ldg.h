@@ -32,9 +32,11 @@ extern "C" {
 
 typedef struct ldg_ctx ldg_ctx;
 
-/* element shapes: triangles (equispaced Lagrange nodes), quadrilaterals and
- * hexahedra (tensor Gauss-Lobatto-Legendre nodes); all elements affine */
-enum { LDG_TRI = 0, LDG_QUAD = 1, LDG_HEX = 2 };
+/* element shapes: triangles and tetrahedra (equispaced Lagrange nodes, collapsed
+ * Gauss rules), quadrilaterals and hexahedra (tensor Gauss-Lobatto-Legendre nodes);
+ * affine elements, and curved quadrilaterals (geom_order > 0 below). Tetrahedra
+ * (Section 4.1's Poisson study) carry the diffusion models, p = 1..3. */
+enum { LDG_TRI = 0, LDG_QUAD = 1, LDG_HEX = 2, LDG_TET = 3 };
 
 /* models of Table 1 (Section 2.1): Poisson and convection-diffusion are diffusion
  * models (with q, Eq. 1a); 2-D Euler is a convection model (no q); 2-D compressible
@@ -71,8 +73,9 @@ enum { LDG_STEADY = 0, LDG_BDF1 = 1, LDG_BDF2 = 2 };
 /* Mesh (Section 3.2): per-element vertex coordinates and topological vertex ids.
  * xyz [n_elem][nv][dim] (host), vid [n_elem][nv] (host). Quadrilaterals and
  * hexahedra list vertices in lexicographic order (x fastest), triangles
- * counter-clockwise. Faces whose sorted vertex ids match are neighbours; a
- * periodic mesh shares ids across the period while each element keeps its own
+ * counter-clockwise, tetrahedra with their three edges from vertex 0 right-handed.
+ * Faces whose sorted vertex ids match are neighbours; a periodic mesh shares ids
+ * across the period while each element keeps its own
  * (unwrapped) coordinates. Faces without a partner are boundary faces.
  *
  * Curved quadrilaterals (geom_order = pg > 0): element K's map is the degree-pg

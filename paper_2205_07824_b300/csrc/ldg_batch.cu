@@ -100,9 +100,11 @@ SegView seg_view(const ldg_batch* b) {
 }
 
 int default_nq(int etype, int model, int p) {
-  return (model == LDG_EULER || model == LDG_NS || etype == LDG_TRI) ? p + 2 : p + 1;
+  return (model == LDG_EULER || model == LDG_NS || etype == LDG_TRI || etype == LDG_TET) ? p + 2 : p + 1;
 }
-int verts_per_elem(int etype) { return etype == LDG_TRI ? 3 : etype == LDG_QUAD ? 4 : 8; }
+int verts_per_elem(int etype) {
+  return etype == LDG_TRI ? 3 : (etype == LDG_QUAD || etype == LDG_TET) ? 4 : 8;
+}
 
 // ------------------------------------------------------------ stage emission
 int emit_residual(ldg_batch* b, cudaStream_t s, const double* u, double* r, const int* skip) {
@@ -414,7 +416,7 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
   std::map<std::tuple<int, int, int, int, int>, std::vector<int>> keyed;
   for (int i = 0; i < n_inst; ++i) {
     const ldg_mesh_desc& M = meshes[i];
-    if (!M.xyz || !M.vid || M.n_elem <= 0 || M.elem_type < 0 || M.elem_type > 2)
+    if (!M.xyz || !M.vid || M.n_elem <= 0 || M.elem_type < 0 || M.elem_type > 3)
       return bfail(b, LDG_ERR_ARG, "instance " + std::to_string(i) + ": bad mesh");
     if (models[i].model < 0 || models[i].model > 3)
       return bfail(b, LDG_ERR_ARG, "instance " + std::to_string(i) + ": bad model");
@@ -433,7 +435,7 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
     int pg = 0;
     std::tie(g.etype, g.p, g.nq, g.model, pg) = kv.first;
     const std::vector<int>& ids = kv.second;
-    const int nv = verts_per_elem(g.etype), dim = g.etype == LDG_HEX ? 3 : 2;
+    const int nv = verts_per_elem(g.etype), dim = (g.etype == LDG_HEX || g.etype == LDG_TET) ? 3 : 2;
     int64_t E = 0;
     for (int i : ids) E += meshes[i].n_elem;
     if (E > (int64_t)0x7fffffff) return bfail(b, LDG_ERR_ARG, "group too large");
@@ -442,7 +444,7 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
     std::vector<int> inst;
     std::vector<double> xgeo;            // curved groups: map points, concatenated
     std::vector<unsigned char> bc;       // wall marks (0 where an instance gives none)
-    const int nfc = 2 * dim + (g.etype == LDG_TRI ? -1 : 0);
+    const int nfc = g.etype == LDG_TRI ? 3 : (g.etype == LDG_TET ? 4 : 2 * dim);
     bool any_bc = false;
     for (int i : ids) any_bc |= meshes[i].bc != nullptr;
     xyz.reserve((size_t)E * nv * dim);

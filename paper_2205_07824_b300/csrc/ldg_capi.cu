@@ -35,7 +35,8 @@ void register_all(std::vector<KernelSet>& reg) {
   register_tri_t<Tile1>(reg); register_quad_t<Tile1>(reg); register_hex_t<Tile1>(reg); register_ns_t<Tile1>(reg);
   register_tri_t<Tile2>(reg); register_quad_t<Tile2>(reg); register_hex_t<Tile2>(reg); register_ns_t<Tile2>(reg);
   register_tri_t<Tile3>(reg); register_quad_t<Tile3>(reg); register_hex_t<Tile3>(reg); register_ns_t<Tile3>(reg);
-  // curved quadrilaterals: two tile shapes
+  // tetrahedra and curved quadrilaterals: two tile shapes
+  register_tet_t<Tile0>(reg); register_tet_t<Tile1>(reg);
   register_curved_scalar_t<Tile0>(reg); register_curved_gas_t<Tile0>(reg);
   register_curved_scalar_t<Tile1>(reg); register_curved_gas_t<Tile1>(reg);
 }
@@ -1000,11 +1001,11 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->etype = mesh->elem_type;
   ctx->model = model->model;
-  if (ctx->etype < 0 || ctx->etype > 2 || ctx->model < 0 || ctx->model > 3) {
+  if (ctx->etype < 0 || ctx->etype > 3 || ctx->model < 0 || ctx->model > 3) {
     ldg_destroy(ctx);
     return LDG_ERR_ARG;
   }
-  ctx->dim = ctx->etype == LDG_HEX ? 3 : 2;
+  ctx->dim = (ctx->etype == LDG_HEX || ctx->etype == LDG_TET) ? 3 : 2;
   const bool gas = ctx->model == LDG_EULER || ctx->model == LDG_NS;
   if (gas && ctx->dim != 2) { ldg_destroy(ctx); return LDG_ERR_UNSUPPORTED; }
   ctx->pg = mesh->geom_order > 0 ? mesh->geom_order : 0;
@@ -1012,7 +1013,7 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   ctx->ncu = gas ? 4 : 1;
   ldg_options o{};
   if (opts) o = *opts;
-  if (o.nq1 <= 0) o.nq1 = (gas || ctx->etype == LDG_TRI) ? p + 2 : p + 1;
+  if (o.nq1 <= 0) o.nq1 = (gas || ctx->etype == LDG_TRI || ctx->etype == LDG_TET) ? p + 2 : p + 1;
   if (o.gmres_m <= 0) o.gmres_m = 30;
   if (o.gmres_m > 30) o.gmres_m = 30;
   if (o.max_restarts <= 0) o.max_restarts = 50;

@@ -462,6 +462,7 @@ struct NSModel {
 template <int DIM_, int P_, int NQ_> struct TensorEl {
   static constexpr bool TENSOR = true;
   static constexpr bool CURVED = false;   // affine (parallelogram / parallelepiped) geometry
+  static constexpr bool NODE_PERM = false;
   static constexpr int DIM = DIM_, P = P_, N1 = P_ + 1, NQ = NQ_;
   static constexpr int NPE = ipow(N1, DIM), NQV = ipow(NQ, DIM);
   static constexpr int NF = 2 * DIM, NFN = ipow(N1, DIM - 1), NFQ = ipow(NQ, DIM - 1);
@@ -493,6 +494,7 @@ template <int P_, int NQ_> struct CurvedQuadEl : TensorEl<2, P_, NQ_> {
 template <int P_, int NQ_> struct TriEl {
   static constexpr bool TENSOR = false;
   static constexpr bool CURVED = false;
+  static constexpr bool NODE_PERM = false;   // neighbour traces matched by face-point permutation
   static constexpr int DIM = 2, P = P_, NQ = NQ_, N1 = P_ + 1;
   static constexpr int NPE = (P_ + 1) * (P_ + 2) / 2, NQV = NQ_ * NQ_;
   static constexpr int NF = 3, NFN = P_ + 1, NFQ = NQ_;
@@ -500,6 +502,7 @@ template <int P_, int NQ_> struct TriEl {
                        OXQ = OWV + NQV, OBF = OXQ + 2 * NQV, OWF = OBF + NFQ * NFN, OSF = OWF + NFQ,
                        ODNR = OSF + NFQ, ODNS = ODNR + NPE * NPE, OMI = ODNS + NPE * NPE,
                        OXN = OMI + NPE * NPE, OPS = OXN + 2 * NPE;
+  static constexpr int ODT = 0, ODNT = 0;    // (no third axis)
   // node (i, j), i + j <= P, numbered row by row: j (P+1) - j (j-1)/2 + i
   __device__ static int nidx(int i, int j) { return j * (P + 1) - j * (j - 1) / 2 + i; }
   // edge nodes in the direction of the edge: f0 v0->v1, f1 v1->v2, f2 v2->v0
@@ -507,6 +510,57 @@ template <int P_, int NQ_> struct TriEl {
     if (f == 0) return nidx(t, 0);
     if (f == 1) return nidx(P - t, t);
     return nidx(0, P - t);
+  }
+};
+
+// Tetrahedron with equispaced nodes (i, j, k), i + j + k <= P, numbered k outer, then
+// j, then i; vertices V0 = (-1,-1,-1), V1 = (1,-1,-1), V2 = (-1,1,-1), V3 = (-1,-1,1);
+// face f lies opposite vertex f, with vertices (A, B, C) = (1,2,3), (0,2,3), (0,1,3),
+// (0,1,2) and face node (a, b) at V_A + a (V_B - V_A) / P + b (V_C - V_A) / P.
+// Full-matrix reference operators; faces carry the collapsed Gauss rule in their own
+// parameters, which is not symmetric, so a neighbour's trace is formed from its face
+// nodes permuted into this element's face-node order (NODE_PERM).
+template <int P_, int NQ_> struct TetEl {
+  static constexpr bool TENSOR = false;
+  static constexpr bool CURVED = false;
+  static constexpr bool NODE_PERM = true;
+  static constexpr int DIM = 3, P = P_, NQ = NQ_, N1 = P_ + 1;
+  static constexpr int NPE = (P_ + 1) * (P_ + 2) * (P_ + 3) / 6, NQV = NQ_ * NQ_ * NQ_;
+  static constexpr int NF = 4, NFN = (P_ + 1) * (P_ + 2) / 2, NFQ = NQ_ * NQ_;
+  static constexpr int OB = 0, ODR = OB + NQV * NPE, ODS = ODR + NQV * NPE, ODT = ODS + NQV * NPE,
+                       OWV = ODT + NQV * NPE, OXQ = OWV + NQV, OBF = OXQ + 3 * NQV, OWF = OBF + NFQ * NFN,
+                       OSF = OWF + NFQ, ODNR = OSF + 2 * NFQ, ODNS = ODNR + NPE * NPE, ODNT = ODNS + NPE * NPE,
+                       OMI = ODNT + NPE * NPE, OXN = OMI + NPE * NPE, OPS = OXN + 3 * NPE;
+  // node (i, j, k): the layers below k hold sum_{k' < k} (P - k' + 1)(P - k' + 2) / 2 nodes
+  __host__ __device__ static int nidx(int i, int j, int k) {
+    int off = 0;
+    for (int kk = 0; kk < k; ++kk) off += (P - kk + 1) * (P - kk + 2) / 2;
+    const int q = P - k;
+    return off + j * (q + 1) - j * (j - 1) / 2 + i;
+  }
+  // barycentric lattice coordinates of node n: l[0] = P - i - j - k, l[1..3] = (i, j, k)
+  __host__ __device__ static void lattice(int n, int* l) {
+    int k = 0, rem = n;
+    while (rem >= (P - k + 1) * (P - k + 2) / 2) { rem -= (P - k + 1) * (P - k + 2) / 2; ++k; }
+    const int q = P - k;
+    int j = 0;
+    while (rem > q - j) { rem -= q + 1 - j; ++j; }
+    l[1] = rem; l[2] = j; l[3] = k; l[0] = P - rem - j - k;
+  }
+  __host__ __device__ static void face_verts(int f, int& A, int& B, int& C) {
+    A = f == 0 ? 1 : 0;
+    B = f <= 1 ? 2 : 1;
+    C = f == 3 ? 2 : 3;
+  }
+  // local node of face-node jf = b (P + 1) - b (b - 1) / 2 + a on face f
+  __host__ __device__ static int face_node(int f, int jf) {
+    int b = 0, a = jf;
+    while (a > P - b) { a -= P + 1 - b; ++b; }
+    int A, B, C;
+    face_verts(f, A, B, C);
+    int l[4] = {0, 0, 0, 0};
+    l[A] = P - a - b; l[B] = a; l[C] = b;
+    return nidx(l[1], l[2], l[3]);
   }
 };
 

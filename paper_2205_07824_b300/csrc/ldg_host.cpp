@@ -155,6 +155,28 @@ void tri_basis(int p, double xi, double eta, double* phi, double* dr, double* ds
     }
 }
 
+// Silvester's form on the tetrahedron: phi_{i,j,k} = R_l(l0) R_i(l1) R_j(l2) R_k(l3),
+// l = p - i - j - k, barycentric l1 = (1 + xi)/2, l2 = (1 + eta)/2, l3 = (1 + zeta)/2,
+// l0 = -(1 + xi + eta + zeta)/2; nodes numbered k outer, then j, then i.
+void tet_basis(int p, const double* x, double* phi, double* dr, double* ds, double* dt) {
+  const double L[4] = {-(1.0 + x[0] + x[1] + x[2]) / 2.0, (1.0 + x[0]) / 2.0, (1.0 + x[1]) / 2.0,
+                       (1.0 + x[2]) / 2.0};
+  int n = 0;
+  for (int k = 0; k <= p; ++k)
+    for (int j = 0; j + k <= p; ++j)
+      for (int i = 0; i + j + k <= p; ++i, ++n) {
+        const int m[4] = {p - i - j - k, i, j, k};
+        double v[4], dv[4];
+        for (int a = 0; a < 4; ++a) { v[a] = silv(m[a], p, L[a]); dv[a] = dsilv(m[a], p, L[a]); }
+        phi[n] = v[0] * v[1] * v[2] * v[3];
+        // d l0 / d x_d = -1/2, d l_{d+1} / d x_d = 1/2
+        const double g0 = dv[0] * v[1] * v[2] * v[3];
+        dr[n] = 0.5 * (-g0 + v[0] * dv[1] * v[2] * v[3]);
+        ds[n] = 0.5 * (-g0 + v[0] * v[1] * dv[2] * v[3]);
+        dt[n] = 0.5 * (-g0 + v[0] * v[1] * v[2] * dv[3]);
+      }
+}
+
 }  // namespace
 
 bool build_ref_ops(int etype, int p, int nq, RefOps& R, std::string& err) {
@@ -209,6 +231,67 @@ bool build_ref_ops(int etype, int p, int nq, RefOps& R, std::string& err) {
     for (double v : xn) put(v);
     return true;
   }
+  if (etype == E_TET) {
+    R.dim = 3; R.npe = (p + 1) * (p + 2) * (p + 3) / 6; R.nqv = nq * nq * nq; R.nf = 4;
+    R.nfn = (p + 1) * (p + 2) / 2; R.nfq = nq * nq;
+    const int npe = R.npe, nqv = R.nqv, nfq = R.nfq, nfn = R.nfn;
+    // collapsed Gauss rule: xi = (1+a)(1-b)(1-c)/4 - 1, eta = (1+b)(1-c)/2 - 1, zeta = c
+    std::vector<double> qx(3 * nqv), qw(nqv);
+    for (int c = 0; c < nq; ++c)
+      for (int b = 0; b < nq; ++b)
+        for (int a = 0; a < nq; ++a) {
+          const int q = a + nq * (b + nq * c);
+          const double A = gx[a], Bv = gx[b], Cv = gx[c];
+          qx[3 * q] = (1.0 + A) * (1.0 - Bv) * (1.0 - Cv) / 4.0 - 1.0;
+          qx[3 * q + 1] = (1.0 + Bv) * (1.0 - Cv) / 2.0 - 1.0;
+          qx[3 * q + 2] = Cv;
+          qw[q] = gw[a] * gw[b] * gw[c] * (1.0 - Bv) * (1.0 - Cv) * (1.0 - Cv) / 8.0;
+        }
+    std::vector<double> B(nqv * npe), Dr(nqv * npe), Ds(nqv * npe), Dt(nqv * npe);
+    for (int q = 0; q < nqv; ++q) tet_basis(p, &qx[3 * q], &B[q * npe], &Dr[q * npe], &Ds[q * npe], &Dt[q * npe]);
+    std::vector<double> xn(3 * npe);
+    {
+      int n = 0;
+      for (int k = 0; k <= p; ++k)
+        for (int j = 0; j + k <= p; ++j)
+          for (int i = 0; i + j + k <= p; ++i, ++n) {
+            xn[3 * n] = -1.0 + 2.0 * i / p; xn[3 * n + 1] = -1.0 + 2.0 * j / p; xn[3 * n + 2] = -1.0 + 2.0 * k / p;
+          }
+    }
+    std::vector<double> Dnr(npe * npe), Dns(npe * npe), Dnt(npe * npe), tmp(npe);
+    for (int i = 0; i < npe; ++i) tet_basis(p, &xn[3 * i], tmp.data(), &Dnr[i * npe], &Dns[i * npe], &Dnt[i * npe]);
+    std::vector<double> M(npe * npe, 0.0), Mi;
+    for (int q = 0; q < nqv; ++q)
+      for (int i = 0; i < npe; ++i)
+        for (int j = 0; j < npe; ++j) M[i * npe + j] += qw[q] * B[q * npe + i] * B[q * npe + j];
+    if (!invert(M, npe, Mi)) { err = "singular reference mass matrix"; return false; }
+    // faces: the collapsed rule on the reference triangle of the face parameters (s, t),
+    // and the equispaced triangle basis in those parameters (face-node order b outer, a inner)
+    std::vector<double> sf(2 * nfq), wf(nfq), Bf(nfq * nfn), d1(nfn), d2(nfn);
+    for (int b = 0; b < nq; ++b)
+      for (int a = 0; a < nq; ++a) {
+        const int k = a + nq * b;
+        sf[2 * k] = (1.0 + gx[a]) * (1.0 - gx[b]) / 2.0 - 1.0;
+        sf[2 * k + 1] = gx[b];
+        wf[k] = gw[a] * gw[b] * (1.0 - gx[b]) / 2.0;
+        tri_basis(p, sf[2 * k], sf[2 * k + 1], &Bf[k * nfn], d1.data(), d2.data());
+      }
+    for (double v : B) put(v);
+    for (double v : Dr) put(v);
+    for (double v : Ds) put(v);
+    for (double v : Dt) put(v);
+    for (double v : qw) put(v);
+    for (double v : qx) put(v);
+    for (double v : Bf) put(v);
+    for (double v : wf) put(v);
+    for (double v : sf) put(v);
+    for (double v : Dnr) put(v);
+    for (double v : Dns) put(v);
+    for (double v : Dnt) put(v);
+    for (double v : Mi) put(v);
+    for (double v : xn) put(v);
+    return true;
+  }
   if (etype != E_QUAD && etype != E_HEX) { err = "unknown element type"; return false; }
   R.dim = etype == E_QUAD ? 2 : 3;
   const int n1 = p + 1;
@@ -246,6 +329,14 @@ bool build_ref_ops(int etype, int p, int nq, RefOps& R, std::string& err) {
 
 void ref_nodes(const RefOps& R, std::vector<double>& out) {
   out.assign((size_t)R.npe * R.dim, 0.0);
+  if (R.etype == E_TET) {
+    const int nq = R.nq, npe = R.npe, nqv = R.nqv;
+    const double* xn = R.blob.data() + 4 * (size_t)nqv * npe + nqv + 3 * nqv + (size_t)R.nfq * R.nfn + 3 * R.nfq +
+                       4 * (size_t)npe * npe;
+    (void)nq;
+    for (int i = 0; i < 3 * npe; ++i) out[i] = xn[i];
+    return;
+  }
   if (R.etype == E_TRI) {
     int n = 0;
     for (int j = 0; j <= R.p; ++j)
@@ -263,6 +354,13 @@ void ref_nodes(const RefOps& R, std::vector<double>& out) {
 void ref_face_point(const RefOps& R, int f, int k, double* xi) {
   std::vector<double> gx, gw;
   gauss_legendre(R.nq, gx, gw);
+  if (R.etype == E_TET) {
+    static const double V[4][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+    const int A = f == 0 ? 1 : 0, B = f <= 1 ? 2 : 1, C = f == 3 ? 2 : 3;
+    const double s = (1.0 + gx[k % R.nq]) * (1.0 - gx[k / R.nq]) / 2.0 - 1.0, t = gx[k / R.nq];
+    for (int d = 0; d < 3; ++d) xi[d] = V[A][d] + 0.5 * (1.0 + s) * (V[B][d] - V[A][d]) + 0.5 * (1.0 + t) * (V[C][d] - V[A][d]);
+    return;
+  }
   if (R.etype == E_TRI) {
     static const double V[3][2] = {{-1, -1}, {1, -1}, {-1, 1}};
     int a = f, b = (f + 1) % 3;
@@ -282,7 +380,8 @@ const std::vector<std::vector<int>>& face_vertices(int etype) {
   static const std::vector<std::vector<int>> quad = {{0, 2}, {1, 3}, {0, 1}, {2, 3}};
   static const std::vector<std::vector<int>> hex = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5},
                                                     {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
-  return etype == E_TRI ? tri : (etype == E_QUAD ? quad : hex);
+  static const std::vector<std::vector<int>> tet = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  return etype == E_TRI ? tri : (etype == E_QUAD ? quad : (etype == E_HEX ? hex : tet));
 }
 }  // namespace
 
@@ -400,13 +499,13 @@ bool prepare_curved(const RefOps& R, int64_t E, int pg, const double* xgeo, Curv
 bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* vid, MeshPrep& out, std::string& err,
                   int pg, const double* xgeo) {
   const int dim = R.dim, nf = R.nf;
-  const int nv = R.etype == E_TRI ? 3 : (1 << dim);
+  const int nv = R.etype == E_TRI ? 3 : (R.etype == E_TET ? 4 : (1 << dim));
   const int GEO = dim * dim + 1 + dim + dim * dim + nf * (dim + 1);
   out.E = E;
   out.geo.assign((size_t)E * GEO, 0.0);
   out.nbr.assign((size_t)E * nf, -1);
   out.nbf.assign((size_t)E * nf, 0);
-  const int axis_vert[3] = {1, 2, 4};
+  const int axis_vert[3] = {1, 2, R.etype == E_TET ? 3 : 4};
   // Reference outward normals and the length factor |d xi / d s| of each face parameter.
   auto ref_normal = [&](int f, double* N, double& ds) {
     for (int d = 0; d < 3; ++d) N[d] = 0.0;
@@ -415,6 +514,11 @@ bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* 
       if (f == 0) N[1] = -1.0;
       else if (f == 1) { N[0] = N[1] = 1.0 / std::sqrt(2.0); ds = std::sqrt(2.0); }
       else N[0] = -1.0;
+    } else if (R.etype == E_TET) {
+      // face f opposite vertex f; face 0 lies in xi + eta + zeta = -1, whose area is
+      // sqrt(3) times that of the face parameters' reference triangle
+      if (f == 0) { N[0] = N[1] = N[2] = 1.0 / std::sqrt(3.0); ds = std::sqrt(3.0); }
+      else N[f - 1] = -1.0;
     } else {
       N[f >> 1] = (f & 1) ? 1.0 : -1.0;
     }
@@ -425,7 +529,7 @@ bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* 
     // J[d][k] = (x_{axis vertex k} - x_0)_d / 2
     for (int d = 0; d < dim; ++d)
       for (int k = 0; k < dim; ++k) J[d * dim + k] = 0.5 * (X[axis_vert[k] * dim + d] - X[d]);
-    if (R.etype != E_TRI && pg == 0) {
+    if (R.etype != E_TRI && R.etype != E_TET && pg == 0) {
       for (int vtx = 0; vtx < nv; ++vtx)
         for (int d = 0; d < dim; ++d) {
           double pr = X[d];
@@ -495,14 +599,31 @@ bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* 
     }
   // face-point coordinates and orientation permutations
   std::map<std::vector<unsigned char>, int> codes;
-  std::vector<double> xs(R.nfq * 3), xt(R.nfq * 3);
-  std::vector<double> fref((size_t)nf * R.nfq * 3, 0.0);   // reference face points, computed once
+  // Matched positions: the face points, or for tetrahedra (whose face rule is not
+  // symmetric) the face nodes, whose permutation the kernels apply to the neighbour's
+  // face-node values.
+  const bool tet = R.etype == E_TET;
+  const int nmatch = tet ? R.nfn : R.nfq;
+  std::vector<double> xs(nmatch * 3), xt(nmatch * 3);
+  std::vector<double> fref((size_t)nf * nmatch * 3, 0.0);   // reference positions, computed once
   for (int f = 0; f < nf; ++f)
-    for (int k = 0; k < R.nfq; ++k) ref_face_point(R, f, k, &fref[((size_t)f * R.nfq + k) * 3]);
+    for (int k = 0; k < nmatch; ++k) {
+      double* xi = &fref[((size_t)f * nmatch + k) * 3];
+      if (tet) {
+        static const double V[4][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+        const int A = f == 0 ? 1 : 0, B = f <= 1 ? 2 : 1, C = f == 3 ? 2 : 3;
+        int b = 0, a = k;
+        while (a > R.p - b) { a -= R.p + 1 - b; ++b; }
+        for (int d = 0; d < 3; ++d)
+          xi[d] = V[A][d] + (double)a / R.p * (V[B][d] - V[A][d]) + (double)b / R.p * (V[C][d] - V[A][d]);
+      } else {
+        ref_face_point(R, f, k, xi);
+      }
+    }
   auto face_pts = [&](int64_t e, int f, double* P, const double* shift) {
     const double* g = &out.geo[(size_t)e * GEO];
-    for (int k = 0; k < R.nfq; ++k) {
-      const double* xi = &fref[((size_t)f * R.nfq + k) * 3];
+    for (int k = 0; k < nmatch; ++k) {
+      const double* xi = &fref[((size_t)f * nmatch + k) * 3];
       if (pg > 0) {
         double x[2], J[2][2];
         curved_point(pg, xgeo + (size_t)e * (pg + 1) * (pg + 1) * 2, xi, x, J);
@@ -535,13 +656,13 @@ bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* 
       }
       face_pts(e, f, xs.data(), nullptr);
       face_pts(e2, f2, xt.data(), shift);
-      std::vector<unsigned char> pm(R.nfq);
+      std::vector<unsigned char> pm(nmatch);
       double hscale = 0.0;
       for (int d = 0; d < dim; ++d) hscale = std::max(hscale, std::fabs(out.geo[(size_t)e * GEO + dim * dim + 1 + dim + d * dim]));
-      for (int k = 0; k < R.nfq; ++k) {
+      for (int k = 0; k < nmatch; ++k) {
         int best = -1;
         double bd = 1e300;
-        for (int k2 = 0; k2 < R.nfq; ++k2) {
+        for (int k2 = 0; k2 < nmatch; ++k2) {
           double dd = 0;
           for (int d = 0; d < dim; ++d) dd += (xs[k * 3 + d] - xt[k2 * 3 + d]) * (xs[k * 3 + d] - xt[k2 * 3 + d]);
           if (dd < bd) { bd = dd; best = k2; }
@@ -559,9 +680,9 @@ bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* 
     }
   }
   out.n_orient = (int)codes.size();
-  out.perm.assign((size_t)std::max(1, out.n_orient) * R.nfq, 0);
+  out.perm.assign((size_t)std::max(1, out.n_orient) * nmatch, 0);
   for (auto& kv : codes)
-    for (int k = 0; k < R.nfq; ++k) out.perm[kv.second * R.nfq + k] = kv.first[k];
+    for (int k = 0; k < nmatch; ++k) out.perm[kv.second * nmatch + k] = kv.first[k];
   out.n_boundary_faces = nb_faces;
   return true;
 }

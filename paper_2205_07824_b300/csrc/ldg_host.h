@@ -7,7 +7,7 @@
 
 namespace ldg {
 
-enum { E_TRI = 0, E_QUAD = 1, E_HEX = 2 };
+enum { E_TRI = 0, E_QUAD = 1, E_HEX = 2, E_TET = 3 };
 
 struct RefOps {
   int etype, p, nq, dim, npe, nqv, nf, nfn, nfq;

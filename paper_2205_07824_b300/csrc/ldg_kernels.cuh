@@ -138,7 +138,7 @@ template <class EL, class F> __device__ __forceinline__ void for_node_faces(int 
       if (i2 == 0) fn(4, i0 + N1 * i1);
       if (i2 == N1 - 1) fn(5, i0 + N1 * i1);
     }
-  } else {
+  } else if constexpr (EL::DIM == 2) {
     constexpr int P = EL::P;
     int j = 0, rem = n;
     while (rem > P - j) { rem -= P + 1 - j; ++j; }
@@ -146,7 +146,31 @@ template <class EL, class F> __device__ __forceinline__ void for_node_faces(int 
     if (j == 0) fn(0, i);
     if (i + j == P) fn(1, j);
     if (i == 0) fn(2, P - j);
+  } else {
+    // tetrahedron: node on face f when its barycentric coordinate l[f] is 0; its face
+    // coordinates (a, b) are l[B], l[C] of the face's vertices (A, B, C)
+    constexpr int P = EL::P;
+    int l[4];
+    EL::lattice(n, l);
+    auto fidx = [](int a, int b) { return b * (P + 1) - b * (b - 1) / 2 + a; };
+    if (l[0] == 0) fn(0, fidx(l[2], l[3]));
+    if (l[1] == 0) fn(1, fidx(l[2], l[3]));
+    if (l[2] == 0) fn(2, fidx(l[1], l[3]));
+    if (l[3] == 0) fn(3, fidx(l[1], l[2]));
   }
+}
+
+// Neighbour traces: the neighbour's local node that carries face node j of this
+// element's face, and the neighbour's face point that coincides with face point k.
+// Elements with NODE_PERM permute the face nodes (the face points are then this
+// element's own); the others permute the face points.
+template <class EL> __device__ __forceinline__ int nbr_face_node(const KArgs& a, int nbf, int j) {
+  if constexpr (EL::NODE_PERM) return EL::face_node(nbf & 7, a.perm[(nbf >> 3) * EL::NFN + j]);
+  else return EL::face_node(nbf & 7, j);
+}
+template <class EL> __device__ __forceinline__ int nbr_face_point(const KArgs& a, int nbf, int k) {
+  if constexpr (EL::NODE_PERM) return k;
+  else return a.perm[(nbf >> 3) * EL::NFQ + k];
 }
 
 // Reference coordinates of face point k on face f.
@@ -165,12 +189,19 @@ template <class EL, class R> __device__ __forceinline__ void face_xi(const R* op
       else if (ax == 1) { xi[0] = s0; xi[1] = fix; xi[2] = s1; }
       else { xi[0] = s0; xi[1] = s1; xi[2] = fix; }
     }
-  } else {
+  } else if constexpr (EL::DIM == 2) {
     const R V[3][2] = {{R(-1), R(-1)}, {R(1), R(-1)}, {R(-1), R(1)}};
     const int a = f, b = (f + 1) % 3;
     const R s = ops[EL::OSF + k];
     xi[0] = R(0.5) * (R(1) - s) * V[a][0] + R(0.5) * (R(1) + s) * V[b][0];
     xi[1] = R(0.5) * (R(1) - s) * V[a][1] + R(0.5) * (R(1) + s) * V[b][1];
+  } else {
+    const R V[4][3] = {{R(-1), R(-1), R(-1)}, {R(1), R(-1), R(-1)}, {R(-1), R(1), R(-1)}, {R(-1), R(-1), R(1)}};
+    int A, B, C;
+    EL::face_verts(f, A, B, C);
+    const R s = ops[EL::OSF + 2 * k], t = ops[EL::OSF + 2 * k + 1];
+    for (int d = 0; d < 3; ++d)
+      xi[d] = V[A][d] + R(0.5) * (R(1) + s) * (V[B][d] - V[A][d]) + R(0.5) * (R(1) + t) * (V[C][d] - V[A][d]);
   }
 }
 template <class EL, class R> __device__ __forceinline__ R face_w(const R* ops, int k) {
@@ -190,8 +221,7 @@ template <class EL, class R> __device__ __forceinline__ void vol_xi(const R* ops
     w = W[i0] * W[i1];
     if constexpr (EL::DIM == 3) { xi[2] = XQ[i2]; w *= W[i2]; }
   } else {
-    xi[0] = ops[EL::OXQ + 2 * q];
-    xi[1] = ops[EL::OXQ + 2 * q + 1];
+    for (int d = 0; d < EL::DIM; ++d) xi[d] = ops[EL::OXQ + EL::DIM * q + d];
     w = ops[EL::OWV + q];
   }
 }
@@ -314,7 +344,7 @@ __device__ __forceinline__ void vol_integrate(int k, const T* in, T* out, T* t1,
       contract<2, N1, N1, NQ, N1, true, ACC>(t2, out, k == 2 ? D : B, nb);
     }
   } else {
-    const OT* M = ops + (k == 0 ? EL::ODR : (k == 1 ? EL::ODS : EL::OB));
+    const OT* M = ops + (k == EL::DIM ? EL::OB : (k == 0 ? EL::ODR : (k == 1 ? EL::ODS : EL::ODT)));
     matvec<EL::NPE, EL::NQV, true, ACC>(in, out, M, nb);
   }
 }
@@ -332,7 +362,7 @@ template <class EL, class T, class OT> __device__ __forceinline__ void nodal_der
       else contract<2, N1, N1, N1, N1, false, false>(in, out, Dn, nb);
     }
   } else {
-    matvec<EL::NPE, EL::NPE, false, false>(in, out, ops + (k == 0 ? EL::ODNR : EL::ODNS), nb);
+    matvec<EL::NPE, EL::NPE, false, false>(in, out, ops + (k == 0 ? EL::ODNR : (k == 1 ? EL::ODNS : EL::ODNT)), nb);
   }
 }
 // reference mass inverse: [nb][NPE] -> [nb][NPE] (in is overwritten for tensor elements)
@@ -421,10 +451,7 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
     if (e < ne) {
       vm = Us[(e * NCU + c) * NPE + EL::face_node(f, j)];
       int nb = a.nbr[(size_t)(e0 + e) * NF + f];
-      if (nb >= 0) {
-        int nf = a.nbf[(size_t)(e0 + e) * NF + f] & 7;
-        vp = R(u[((size_t)nb * NCU + c) * NPE + EL::face_node(nf, j)]);
-      }
+      if (nb >= 0) vp = R(u[((size_t)nb * NCU + c) * NPE + nbr_face_node<EL>(a, a.nbf[(size_t)(e0 + e) * NF + f], j)]);
     }
     FNm[it] = vm;
     FNp[it] = vp;
@@ -446,8 +473,7 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
     double gb[4] = {0.0, 0.0, 0.0, 0.0};
     int kp = k;
     if (nb >= 0) {
-      int code = a.nbf[(size_t)(e0 + e) * NF + f] >> 3;
-      kp = a.perm[code * NFQ + k];
+      kp = nbr_face_point<EL>(a, a.nbf[(size_t)(e0 + e) * NF + f], k);
     } else if (MODE == MODE_R && nb == -1) {
       double x[3];
       face_phys<EL>(a, g, OPS, e0 + e, f, k, x);
@@ -739,8 +765,7 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
         vm = X[(e * NCV + fld) * NPE + EL::face_node(f, j)];
         int nb = a.nbr[(size_t)(e0 + e) * NF + f];
         if (nb >= 0) {
-          int nfc = a.nbf[(size_t)(e0 + e) * NF + f] & 7;
-          int nn = EL::face_node(nfc, j);
+          const int nn = nbr_face_node<EL>(a, a.nbf[(size_t)(e0 + e) * NF + f], j);
           if (fld < NCU) {
             size_t gi = ((size_t)nb * NCU + fld) * NPE + nn;
             if constexpr (MODE == MODE_JV) vp = S(R(u[gi]), a.blk_col >= 0 ? R(0) : R(v[gi]));
@@ -776,7 +801,7 @@ __global__ void __launch_bounds__(256) k_residual(KArgs a) {
         if (fld < NCU) um[fld] = val; else qm[fld - NCU] = val;
       }
       if (nb >= 0) {
-        int kp = a.perm[(a.nbf[(size_t)(e0 + e) * NF + f] >> 3) * NFQ + k];
+        const int kp = nbr_face_point<EL>(a, a.nbf[(size_t)(e0 + e) * NF + f], k);
         S up[NCU], qp[NCU * DIM + 1];
         for (int fld = 0; fld < NCV; ++fld) {
           S val = TRp[((e * NF + f) * NCV + fld) * NFQ + kp];

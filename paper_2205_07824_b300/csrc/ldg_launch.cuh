@@ -155,6 +155,7 @@ template <class TL> void register_quad_t(std::vector<KernelSet>& reg);
 template <class TL> void register_hex_t(std::vector<KernelSet>& reg);
 template <class TL> void register_ns_t(std::vector<KernelSet>& reg);
 template <class TL> void register_curved_scalar_t(std::vector<KernelSet>& reg);
+template <class TL> void register_tet_t(std::vector<KernelSet>& reg);
 template <class TL> void register_curved_gas_t(std::vector<KernelSet>& reg);
 void register_all(std::vector<KernelSet>& reg);
 
