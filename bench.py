@@ -557,6 +557,86 @@ def run_hex(args):
     print(json.dumps(line), flush=True)
 
 
+TET_WORKLOAD = ("Section 4.1 / Table 3: 3D Poisson -lap u = f on the unit cube, u = sin(pi x) sin(pi y) sin(pi z), "
+                "structured tetrahedral mesh 1/n = {n} (6 n^3 = {E} tetrahedra), p = {p}, Dirichlet data; one "
+                "Newton-GMRES(30) solve from u = 0 to 1e-8 (linear solves to 1e-3) with block-Jacobi")
+# Algorithmic HBM bytes per DOF of the 3-D linear J.v (FP64 storage): v read twice,
+# q(v) written and read (3 components), J.v written: (2 + 2 x 3 + 1) x 8
+TET_JV_BYTES_PER_DOF = 72.0
+
+
+def run_tet(args):
+    """Table 3's finest mesh on the GPU: the J.v (FP64 and FP32 arithmetic) against the
+    HBM roofline, and the time of the whole Newton-GMRES solve."""
+    import torch
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, POISSON, CASE_SINSIN, kernel_launches
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    n_side, p = args.tet_n, args.tet_p
+    mesh = synth.tet_cube(n_side)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = kernel_launches()
+    jv = {}
+    for prec in (1, 0):
+        g = LDG(mesh, p, POISSON, CASE_SINSIN, (1.0, 1.0), krylov_precision=prec, precond=1, newton_rtol=1e-8,
+                gmres_rtol=1e-3, max_restarts=400)
+        tile, _ = g.autotune()
+        u = g.interpolate(0.0)
+        v = torch.randn(g.n_dof, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+        out = torch.empty_like(v)
+        ms = graph_time_ms(g, lambda: g.jvp_prec(prec, u, v, out), args.jv_reps)
+        jv["fp32" if prec else "fp64"] = {"ms": ms, "gdofs": g.n_dof / (ms * 1e-3) / 1e9, "tile": tile,
+                                          "hbm_frac": TET_JV_BYTES_PER_DOF * g.n_dof / (ms * 1e-3) / 1e9 / hbm}
+        if prec:
+            g32 = g
+    # the solve: FP32 Krylov + block-Jacobi from u = 0, timed steps (each a full solve)
+    n = g32.n_dof
+    times, reps = [], []
+    for k in range(args.warmup + args.steps):
+        u = torch.zeros(n, dtype=torch.float64, device="cuda")
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = g32.newton_gmres(u)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+            reps.append(rep)
+    launches = kernel_launches() - l0
+    clk = clocks.stop()
+    assert all(r["status"] == 0 for r in reps), reps
+    ms_step = sum(times) / len(times)
+    jv_calls = sum(r["jv_calls"] for r in reps) / len(reps)
+    head = jv["fp32"]
+    achieved = TET_JV_BYTES_PER_DOF * n / (head["ms"] * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": head["gdofs"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": TET_WORKLOAD.format(n=n_side, E=mesh.n_elem, p=p), "n_dof": n,
+                       "value_definition": "FP32-arithmetic J.v of the solve, DOF / kernel time (graph-timed)",
+                       "jv": jv, "solve_ms": ms_step, "newton_iters": reps[-1]["newton_iters"],
+                       "gmres_iters": reps[-1]["gmres_iters"], "jv_calls_per_solve": jv_calls,
+                       "l2": "flushed (256 MiB write) before each timed solve; J.v graph-timed"},
+            "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": hbm, "frac": achieved / hbm,
+                         "traffic": None, "bytes_per_dof": TET_JV_BYTES_PER_DOF,
+                         "kernel": f"k_qstage + k_residual (MODE_HOM, float), TetEl<{p},{p + 2}>",
+                         "peak_source": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 CYL_WORKLOAD = ("2D compressible Navier-Stokes flow past a cylinder (radius 0.5 at the origin, domain "
                 "[-10,30]x[-10,10]), {E} curved quadrilaterals ({nr} advancing layers x {nt} around, first layer "
                 "0.01, map degree 3, seeded node jitter, seed 7), p=3, Re={re:.1f} (uniform [100,1000], seed {rs}), "
@@ -723,11 +803,13 @@ def main():
     ap.add_argument("--host-loops", action="store_true",
                     help="run the solver's Newton / restart / Arnoldi loops from the host instead of the CUDA "
                          "graph's WHILE nodes (same kernels; for profilers that do not follow graph nodes)")
-    ap.add_argument("--workload", default="vortex", choices=["vortex", "batch", "hex", "cylinder"],
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "batch", "hex", "cylinder", "tet"],
                     help="vortex: the 64x64 p=3 Euler BDF2 step; batch: 256 parametrised convection-diffusion "
                          "solves in one graph launch; hex: the 48^3 convection-diffusion J.v sweep p=1..6; "
                          "cylinder: Navier-Stokes past a cylinder on 40,000 curved quads, learned + mixed vs "
-                         "plain FP64 block-Jacobi")
+                         "plain FP64 block-Jacobi; tet: Table 3's Poisson problem on tetrahedra, 1/n = 32, p = 3")
+    ap.add_argument("--tet-n", type=int, default=32, help="tet: cubes per side (Table 3's 1/n)")
+    ap.add_argument("--tet-p", type=int, default=3, help="tet: polynomial order")
     ap.add_argument("--cyl-layers", type=int, default=100, help="cylinder mesh: layers across the domain")
     ap.add_argument("--cyl-around", type=int, default=400, help="cylinder mesh: elements around the cylinder")
     ap.add_argument("--re-seed", type=int, default=0, help="cylinder: seed of the Reynolds-number draw")
@@ -747,6 +829,9 @@ def main():
         return
     if args.workload == "cylinder":
         run_cylinder(args)
+        return
+    if args.workload == "tet":
+        run_tet(args)
         return
 
     import numpy as np

@@ -633,17 +633,19 @@ __device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict
 }
 
 // out[b][o] = sum_i Mat[o][i] in[b][i] (full matrix, NO x NI), or transposed.
+// The batch index runs fastest across the threads, so that a warp reads one (or a
+// few) matrix entries per step, broadcast to its lanes, instead of up to 32 rows.
 template <int NO, int NI, bool TRANS, bool ACC, class T, class TM>
 __device__ __forceinline__ void matvec(const T* __restrict__ in, T* __restrict__ out,
                                        const TM* __restrict__ Mat, int nbatch) {
   const int total = nbatch * NO;
   for (int it = threadIdx.x; it < total; it += blockDim.x) {
-    int b = it / NO, o = it - b * NO;
+    const int o = it / nbatch, b = it - o * nbatch, oi = b * NO + o;
     const T* src = in + b * NI;
-    T acc = ACC ? out[it] : T(0);
+    T acc = ACC ? out[oi] : T(0);
 #pragma unroll 4
     for (int i = 0; i < NI; ++i) acc += src[i] * (TRANS ? Mat[i * NO + o] : Mat[o * NI + i]);
-    out[it] = acc;
+    out[oi] = acc;
   }
 }
 
