@@ -700,8 +700,15 @@ template <class EL, class MD, int MODE, class R, class TL> struct RLayout {
   static constexpr int SMEM = NE * PER_ELEM;
 };
 
+// Minimum resident CTAs per SM asked of the register allocator: 3 for the FP32
+// dual-number J.v of the Navier-Stokes model (whose register count otherwise leaves
+// two 256-thread CTAs per SM), 1 otherwise.
+template <class MD, int MODE, class R> struct ResMinBlocks {
+  static constexpr int value = (MD::KIND == M_NS && MODE == MODE_JV && sizeof(R) == 4) ? 3 : 1;
+};
+
 template <class EL, class MD, int MODE, class R, class TL>
-__global__ void __launch_bounds__(256) k_residual(KArgs a) {
+__global__ void __launch_bounds__(256, ResMinBlocks<MD, MODE, R>::value) k_residual(KArgs a) {
   typedef RLayout<EL, MD, MODE, R, TL> L;
   typedef typename L::S S;
   constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ, NQV = EL::NQV;
