@@ -149,6 +149,8 @@ typedef struct {
   int status;
   int pc_setups;        /* preconditioner builds during the call */
   int pc_fallbacks;     /* linear solves redone with block-Jacobi after the learned one failed */
+  int newton_backtracks;  /* Newton step halvings: a step after which ||R|| grew more than
+                             tenfold (or became non-finite) is halved, up to ten times in a row */
 } ldg_solve_report;
 
 typedef struct {

@@ -51,6 +51,8 @@ struct ldg_batch {
   int *d_chunk_seg = nullptr, *d_seg_c0 = nullptr, *d_seg_nc = nullptr;
   int64_t *d_chunk_lo = nullptr, *d_chunk_hi = nullptr;
   double* d_part = nullptr;
+  int* d_bt = nullptr;         // [n_seg] Newton step being halved at the current iteration
+  double* d_ubase = nullptr;   // [n_total] last accepted Newton iterate
   unsigned int* d_tick = nullptr;
   double* d_small = nullptr;
   int* d_sflags = nullptr;
@@ -157,9 +159,10 @@ int emit_newton_head(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle hb
   KrySmall S{b->m};
   if ((rc = emit_residual(b, s, b->d_u, b->d_res, b->d_skip_newt))) return rc;
   kb_norm2<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_res, (int)(S.sc() + 5), b->d_skip_newt);
-  kb_newton_check<<<1, 256, 0, s>>>(b->d_ctl, sv, b->d_st, b->d_skip_newt, b->d_skip_gm, hb, use);
+  kb_newton_check<<<1, 256, 0, s>>>(b->d_ctl, sv, b->d_st, b->d_skip_newt, b->d_skip_gm, b->d_bt, hb, use);
+  kb_newton_step_control<<<b->nchunk, 256, 0, s>>>(sv, b->d_x, b->d_u, b->d_ubase, b->d_skip_newt, b->d_bt);
   kb_prep_linear<<<b->nchunk, 256, 0, s>>>(sv, b->d_res, b->d_r, b->d_x, b->d_skip_gm);
-  for (int i = 0; i < 3; ++i) count_launch();
+  for (int i = 0; i < 4; ++i) count_launch();
   BK(cudaGetLastError());
   return LDG_OK;
 }
@@ -167,7 +170,7 @@ int emit_newton_head(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle hb
 // Newton body, part 2: u -= delta, loop decision.
 int emit_newton_tail(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle ha, int use) {
   const SegView sv = seg_view(b);
-  kb_newton_update<<<b->nchunk, 256, 0, s>>>(sv, b->d_x, b->d_u, b->d_skip_newt);
+  kb_newton_update<<<b->nchunk, 256, 0, s>>>(sv, b->d_x, b->d_u, b->d_skip_newt, b->d_bt);
   kb_newton_end<<<1, 256, 0, s>>>(b->d_ctl, b->d_skip_newt, b->nseg, ha, use);
   count_launch();
   count_launch();
@@ -380,7 +383,8 @@ void free_batch(ldg_batch* b) {
                   (void*)b->d_chunk_lo, (void*)b->d_chunk_hi, (void*)b->d_part, (void*)b->d_tick, (void*)b->d_small,
                   (void*)b->d_sflags, (void*)b->d_st, (void*)b->d_ctl, (void*)b->d_skip_newt, (void*)b->d_skip_gm,
                   (void*)b->d_skip_arn, (void*)b->d_u, (void*)b->d_res, (void*)b->d_r, (void*)b->d_x, (void*)b->d_w,
-                  (void*)b->d_vcur, (void*)b->d_zcur, (void*)b->d_V, (void*)b->d_Z})
+                  (void*)b->d_vcur, (void*)b->d_zcur, (void*)b->d_V, (void*)b->d_Z, (void*)b->d_bt,
+                  (void*)b->d_ubase})
     cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
@@ -533,6 +537,9 @@ int finish_build(ldg_batch* b, const std::vector<int64_t>& seg_off, const std::v
     return rc;
   const size_t ks = KrySmall{b->m}.total();
   BK(cudaMalloc(&b->d_part, (size_t)3 * b->nchunk * KB_LDP * sizeof(double)));
+  BK(cudaMalloc(&b->d_bt, (size_t)b->nseg * sizeof(int)));
+  BK(cudaMemset(b->d_bt, 0, (size_t)b->nseg * sizeof(int)));
+  BK(cudaMalloc(&b->d_ubase, (size_t)b->ntot * sizeof(double)));
   BK(cudaMalloc(&b->d_tick, b->nseg * sizeof(unsigned int)));
   BK(cudaMemset(b->d_tick, 0, b->nseg * sizeof(unsigned int)));
   BK(cudaMalloc(&b->d_small, (size_t)b->nseg * ks * sizeof(double)));
@@ -721,6 +728,7 @@ int ldg_batch_solve(ldg_batch* b, double* u_dev, int use_graph, ldg_solve_report
     r.elapsed_ms = ms;
     r.status = q.status;
     r.pc_setups = b->pc ? 1 : 0;
+    r.newton_backtracks = q.backtracks;
   }
   if (worst != LDG_OK) return bfail(b, worst, "some instances did not converge (see the per-instance reports)");
   return LDG_OK;

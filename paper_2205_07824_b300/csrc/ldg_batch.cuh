@@ -47,7 +47,17 @@ struct SegView {
 struct SegState {
   double r0, rn, bnorm, lin_resid;
   int newton_done, gmres_active, status, newton_iters, gmres_iters, jv_calls, residual_calls, cycles;
+  double rprev;      // ||R|| at the last accepted iterate
+  int halvings;      // consecutive step halvings at the current iterate
+  int backtracks;    // step halvings over the solve
 };
+
+// Newton step control: a step after which ||R|| grew more than NEWTON_GROWTH times, or
+// became non-finite, is halved (u = u_accepted - delta / 2^h), at most NEWTON_HALVINGS
+// times in a row and while Newton iterations remain; a step that cannot be halved any
+// more is discarded (u = u_accepted) and the solve ends with LDG_ERR_MAXIT.
+constexpr double NEWTON_GROWTH = 10.0;
+constexpr int NEWTON_HALVINGS = 10;
 
 // Loop state of the batched solve (one record).
 struct BatchCtl {
@@ -397,11 +407,36 @@ __global__ void kb_prep_linear(SegView sv, const double* __restrict__ res, doubl
   }
 }
 
-// Newton update u_s -= x_s
-__global__ void kb_newton_update(SegView sv, const double* __restrict__ x, double* __restrict__ u, const int* skip) {
+// Newton update u_s -= x_s (not where the step is being halved: bt[s])
+__global__ void kb_newton_update(SegView sv, const double* __restrict__ x, double* __restrict__ u, const int* skip,
+                                 const int* bt) {
+  // (bt[s] == 2 instances are done: skip[s] is set)
   const int c = blockIdx.x, s = sv.chunk_seg[c];
-  if (skip[s]) return;
+  if (skip[s] || bt[s]) return;
   for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) u[i] -= x[i];
+}
+
+// After the Newton check: where the step is halved, x_s /= 2 and u_s = ub_s - x_s; at an
+// accepted iterate of an active instance, ub_s = u_s.
+// bt[s] == 2: the step is discarded, u_s = ub_s.
+__global__ void kb_newton_step_control(SegView sv, double* __restrict__ x, double* __restrict__ u,
+                                       double* __restrict__ ub, const int* skip_newt, const int* bt) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (bt[s] == 2) {
+    for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) u[i] = ub[i];
+    return;
+  }
+  if (skip_newt[s]) return;
+  const bool half = bt[s] != 0;
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) {
+    if (half) {
+      const double h = 0.5 * x[i];
+      x[i] = h;
+      u[i] = ub[i] - h;
+    } else {
+      ub[i] = u[i];
+    }
+  }
 }
 
 // ------------------------------------------------------------ loop control (one CTA)
@@ -416,6 +451,7 @@ __global__ void kb_init(BatchCtl* ctl, SegState* st, int nseg, int* skip_newt, i
     z.r0 = z.rn = z.bnorm = z.lin_resid = 0.0;
     z.newton_done = 0; z.gmres_active = 0; z.status = 0; z.newton_iters = 0; z.gmres_iters = 0;
     z.jv_calls = 0; z.residual_calls = 0; z.cycles = 0;
+    z.rprev = 0.0; z.halvings = 0; z.backtracks = 0;
     st[s] = z;
     skip_newt[s] = 0; skip_gm[s] = 1; skip_arn[s] = 1;
   }
@@ -429,7 +465,8 @@ __global__ void kb_init(BatchCtl* ctl, SegState* st, int nseg, int* skip_newt, i
 
 // After R(u_k) and ||R_s||^2 (sc[5]): Newton convergence test per instance; the ones
 // still active start a linear solve J delta = R with threshold gmres_rtol ||R_s||.
-__global__ void kb_newton_check(BatchCtl* ctl, SegView sv, SegState* st, int* skip_newt, int* skip_gm,
+// bt[s] = 1 where the last step is halved instead (no linear solve this iteration).
+__global__ void kb_newton_check(BatchCtl* ctl, SegView sv, SegState* st, int* skip_newt, int* skip_gm, int* bt,
                                 cudaGraphConditionalHandle hb, int use_cond) {
   const int k = ctl->k;
   KrySmall S{sv.m};
@@ -437,12 +474,30 @@ __global__ void kb_newton_check(BatchCtl* ctl, SegView sv, SegState* st, int* sk
   for (int s = threadIdx.x; s < sv.nseg; s += blockDim.x) {
     SegState& q = st[s];
     skip_gm[s] = 1;
+    bt[s] = 0;
     if (q.newton_done) continue;
     double* sc = sv.small + (size_t)s * sv.ks + S.sc();
     const double rn = sqrt(sc[5]);
     q.residual_calls++;
-    if (k == 0) q.r0 = rn;
+    if (k == 0) { q.r0 = rn; q.rprev = rn; }
     q.rn = rn;
+    if (k > 0 && !(rn <= NEWTON_GROWTH * q.rprev)) {
+      if (q.halvings < NEWTON_HALVINGS && k < ctl->max_newton) {
+        bt[s] = 1;
+        q.halvings++;
+        q.backtracks++;
+      } else {
+        // no acceptable step within the limits: back to the last accepted iterate
+        bt[s] = 2;
+        q.rn = q.rprev;
+        q.status = -5;                                                // LDG_ERR_MAXIT
+        q.newton_done = 1;
+        skip_newt[s] = 1;
+      }
+      continue;
+    }
+    q.halvings = 0;
+    q.rprev = rn;
     int done = 0;
     if (!isfinite(rn)) { q.status = -4; done = 1; }                 // LDG_ERR_NONFINITE
     else if (rn <= ctl->newton_rtol * q.r0) { q.status = 0; done = 1; }

@@ -810,12 +810,32 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
     k_axpy_dev<<<g1, 256, 0, ctx->stream>>>(del, sc + 6, u, n);
     count_launch();
     CK(cudaGetLastError());
+    const double rprev = rn;
     if ((rc = do_residual(ctx, u, res))) return rc;
     if (rep) rep->residual_calls++;
     if ((rc = dots(ctx, res, n, 1, res, sc + 5, nullptr))) return rc;
     if ((rc = read_scalars(ctx, sc + 5, 1))) return rc;
     rn = std::sqrt(ctx->h_pin[0]);
-    if (!std::isfinite(rn)) return fail(ctx, LDG_ERR_NONFINITE, "non-finite residual after a Newton step");
+    // step control (as in the batched engine): where ||R|| grew more than tenfold or
+    // became non-finite, halve the step (u += delta / 2, delta /= 2), up to ten times
+    for (int h = 0; h < 10 && !(rn <= 10.0 * rprev) && k + 1 < ctx->opt.max_newton; ++h) {
+      k_hist<<<grid_for(n), 256, 0, ctx->stream>>>(n, 0.5, del, 0.0, nullptr, del);
+      k_hist<<<grid_for(n), 256, 0, ctx->stream>>>(n, 1.0, u, 1.0, del, u);
+      count_launch();
+      count_launch();
+      if ((rc = do_residual(ctx, u, res))) return rc;
+      if (rep) { rep->residual_calls++; rep->newton_backtracks++; }
+      if ((rc = dots(ctx, res, n, 1, res, sc + 5, nullptr))) return rc;
+      if ((rc = read_scalars(ctx, sc + 5, 1))) return rc;
+      rn = std::sqrt(ctx->h_pin[0]);
+    }
+    if (!(rn <= 10.0 * rprev)) {
+      // no acceptable step within the limits: back to the last accepted iterate
+      k_hist<<<grid_for(n), 256, 0, ctx->stream>>>(n, 1.0, u, 1.0, del, u);
+      count_launch();
+      if (rep) { rep->newton_iters = k + 1; rep->rfinal = rprev; }
+      return fail(ctx, LDG_ERR_MAXIT, "no acceptable Newton step within the step-halving limits");
+    }
     ++k;
   }
   if (rep) {
@@ -1313,6 +1333,7 @@ int ldg_dirk_step(ldg_ctx* ctx, int scheme, double t, double dt, double* u, ldg_
     total.residual_calls += r.residual_calls;
     total.pc_setups += r.pc_setups;
     total.pc_fallbacks += r.pc_fallbacks;
+    total.newton_backtracks += r.newton_backtracks;
     if (i == 0) total.r0 = r.r0;
     total.rfinal = std::max(total.rfinal, r.rfinal / (r.r0 > 0 ? r.r0 : 1.0));
     total.lin_resid = std::max(total.lin_resid, r.lin_resid);

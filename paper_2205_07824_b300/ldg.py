@@ -75,7 +75,7 @@ class SolveReport(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("gmres_iters", ctypes.c_int), ("jv_calls", ctypes.c_int),
                 ("residual_calls", ctypes.c_int), ("r0", ctypes.c_double), ("rfinal", ctypes.c_double),
                 ("lin_resid", ctypes.c_double), ("elapsed_ms", ctypes.c_double), ("status", ctypes.c_int),
-                ("pc_setups", ctypes.c_int), ("pc_fallbacks", ctypes.c_int)]
+                ("pc_setups", ctypes.c_int), ("pc_fallbacks", ctypes.c_int), ("newton_backtracks", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -174,3 +174,22 @@ def test_batch_curved_instances():
         rep = g.newton_gmres(ui)
         assert reps[i]["status"] == 0 and reps[i]["newton_iters"] == rep["newton_iters"]
         assert np.linalg.norm(bu[sl] - host(ui)) <= 1e-7 * np.linalg.norm(host(ui))
+
+
+def test_newton_step_halving_keeps_the_impulsive_start_finite():
+    """The impulsively started cylinder (free stream up to the no-slip wall, Re = 673,
+    dt = 0.1) drives full Newton steps to non-finite states. With step control, a step
+    after which ||R|| grows more than tenfold (or becomes non-finite) is halved: the
+    solve reports its halvings and ends at the Newton cap with a finite state, not with
+    a non-finite one."""
+    from paper_2205_07824_b300.ldg import LDG
+    mesh = synth.cylinder_mesh(25, 100, 3, seed=7)
+    g = LDG(mesh, 3, oracle.NS, oracle.CASE_CYLINDER, (1.4, 673.0, 0.72), newton_rtol=1e-8, gmres_rtol=1e-3,
+            krylov_precision=1, precond=1, max_newton=10)
+    u0 = g.interpolate(0.0)
+    g.set_time(2, 0.1, 0.1, u0, u0.clone())
+    u = u0.clone()
+    rep = g.newton_gmres(u, check=False)
+    assert rep["newton_backtracks"] >= 1, rep
+    assert rep["status"] in (0, -5), rep
+    assert np.all(np.isfinite(host(u)))
