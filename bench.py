@@ -901,13 +901,15 @@ def main():
         h_unm1 = torch.empty(n, dtype=torch.float64, pin_memory=True)
         h_un.copy_(u)
         h_unm1.copy_(u)
-        h_u = np.empty(n, dtype=np.float64)
+        # the state handed to the host-buffer solve lives in pinned memory, like the inputs
+        h_u_t = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        h_u = h_u_t.numpy()
         d_un, d_unm1 = torch.empty_like(u), torch.empty_like(u)
         k2 = min(args.steps, 5)
         t_e2e, jv_e2e = 0.0, 0
         tt = t_end
         nloc = g.n_cu * g.n_pe
-        for _ in range(k2):
+        for it in range(k2 + 1):          # the first (untimed) step takes the one-time costs
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             d_un.copy_(h_un, non_blocking=True)
@@ -915,10 +917,11 @@ def main():
             g.set_time(BDF2, tt + DT, DT, d_un, d_unm1)
             h_u[:] = h_un.numpy()
             rep = g.newton_gmres_host(h_u)
-            t_e2e += time.perf_counter() - t0
-            jv_e2e += rep["jv_calls"] + rep["pc_setups"] * nloc
+            if it > 0:
+                t_e2e += time.perf_counter() - t0
+                jv_e2e += rep["jv_calls"] + rep["pc_setups"] * nloc
             h_unm1.copy_(h_un)
-            h_un.copy_(torch.from_numpy(h_u))
+            h_un.copy_(h_u_t)
             tt += DT
         e2e = {"value": n * jv_e2e / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": 3 * 8 * n,
                "d2h_bytes_per_step": 8 * n, "steps": k2, "ms_per_step": t_e2e / k2 * 1e3,
