@@ -662,6 +662,78 @@ def cylinder_problem(LDG, mesh, re):
     return dict(make=make, init=init, dt=0.1, n_elem=mesh.n_elem)
 
 
+def run_cylinder_sweep(args):
+    """Reynolds-number sweep: K cylinder instances (Re from seeds 0 .. K-1) on the same
+    mesh, solved together per BDF2 step by the batched engine in one CUDA graph launch
+    (FP32 Krylov J.v and block-Jacobi)."""
+    import numpy as np
+    import torch
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, Batch, NS, CASE_CYLINDER, CASE_CYLINDER_START, BDF2, kernel_launches
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    K = args.cyl_sweep
+    mesh = synth.cylinder_mesh(args.cyl_layers, args.cyl_around, 3, seed=7)
+    res = [float(np.random.default_rng(args.re_seed + k).uniform(100.0, 1000.0)) for k in range(K)]
+    mus = [(1.4, re, 0.72) for re in res]
+    b = Batch([mesh] * K, [3] * K, NS, CASE_CYLINDER, mus, gmres_m=30, newton_rtol=1e-8, gmres_rtol=1e-3,
+              krylov_precision=1, precond=1)
+    g0 = LDG(mesh, 3, NS, CASE_CYLINDER_START, mus[0])
+    u0 = g0.interpolate(0.0)
+    del g0
+    un = u0.repeat(K)
+    unm1 = un.clone()
+    u = torch.empty_like(un)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    dt, t = 0.1, 0.0
+    clocks = ClockSampler(local)
+    times, reps_all = [], []
+    l0 = None
+    for k in range(args.warmup + args.steps):
+        if k == args.warmup:
+            clocks.start()
+            l0 = kernel_launches()
+        b.set_time(BDF2, t + dt, dt, un, unm1)
+        u.copy_(un)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps, _ = b.solve(u)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        unm1.copy_(un)
+        un.copy_(u)
+        t += dt
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+            reps_all.append(reps)
+    launches = kernel_launches() - l0
+    clk = clocks.stop()
+    bad = [r for reps in reps_all for r in reps if r["status"] != 0 or r["rfinal"] > 1e-8 * r["r0"]]
+    assert not bad, bad[:2]
+    jv_dofs = sum(b.n_dof[i] * reps[i]["jv_calls"] for reps in reps_all for i in range(K))
+    total_ms, gdofs = aggregate(times, jv_dofs, world, rank)
+    if rank == 0:
+        per = [{"re": round(res[i], 1),
+                "gmres_iters_per_step": sum(r[i]["gmres_iters"] for r in reps_all) / len(reps_all),
+                "newton_iters_per_step": sum(r[i]["newton_iters"] for r in reps_all) / len(reps_all)}
+               for i in range(K)]
+        line = {"metric": METRIC, "value": gdofs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+                "config": {"workload": f"Reynolds-number sweep of the cylinder flow: {K} instances (Re from seeds "
+                                       f"{args.re_seed}..{args.re_seed + K - 1}) on the {mesh.n_elem}-element mesh, "
+                                       "p=3, one batched Newton-GMRES per BDF2 step (dt=0.1) in one CUDA graph launch, "
+                                       "FP32 Krylov J.v + block-Jacobi, each instance to 1e-8",
+                           "n_dof_total": int(b.n_total), "instances": per,
+                           "value_definition": "J.v applications of all instances x their DOF / timed step time",
+                           "l2": "flushed (256 MiB write) before each timed step"},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 def run_cylinder(args):
     """The cylinder workload: time-to-1e-8 per BDF2 step for the plain FP64 block-Jacobi
     form, the mixed form with block-Jacobi, and the learned + mixed form (the MLP
@@ -813,6 +885,8 @@ def main():
     ap.add_argument("--cyl-layers", type=int, default=100, help="cylinder mesh: layers across the domain")
     ap.add_argument("--cyl-around", type=int, default=400, help="cylinder mesh: elements around the cylinder")
     ap.add_argument("--re-seed", type=int, default=0, help="cylinder: seed of the Reynolds-number draw")
+    ap.add_argument("--cyl-sweep", type=int, default=1,
+                    help="cylinder: K > 1 solves K Reynolds numbers together in one batched graph launch per step")
     ap.add_argument("--cyl-forms", default="fp64_bjacobi,fp32_bjacobi,fp32_learned",
                     help="cylinder: forms to run (the last one is the headline)")
     args = ap.parse_args()
@@ -828,7 +902,10 @@ def main():
         run_hex(args)
         return
     if args.workload == "cylinder":
-        run_cylinder(args)
+        if args.cyl_sweep > 1:
+            run_cylinder_sweep(args)
+        else:
+            run_cylinder(args)
         return
     if args.workload == "tet":
         run_tet(args)
