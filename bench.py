@@ -941,7 +941,7 @@ def main():
     total_ms, gdofs = aggregate(times, n * tot["jv"], world, rank)
     ms_per_step = total_ms / args.steps
 
-    # the plain FP64 block-Jacobi form on the same box, same steps (the benchmark spec comparison)
+    # the plain FP64 block-Jacobi form on the same box, same steps
     base = None
     if not args.no_fp64_baseline and (kprec, pc) != (0, 1):
         gb, ub, tb, totb, _, _, _ = run_mode(prob, 0, 1, args.steps, args.warmup, flush, stream, kernel_launches)

@@ -107,12 +107,12 @@ def test_bitwise_reproducible():
 
 
 # ------------------------------------------------------------ full workloads
-def test_full_c1_poisson_triangles():
+def test_full_poisson_512_triangles_p2():
     """2-D Poisson, p = 2 on 16 x 16 squares split into 512 triangles."""
     _run_r_jv(synth.tri_square(16), 2, oracle.POISSON, oracle.CASE_SINSIN)
 
 
-def test_full_c2_euler_vortex_64x64_p3():
+def test_full_euler_vortex_64x64_p3():
     """Isentropic vortex, periodic [0,10]^2, 64 x 64 quadrilaterals, p = 3, BDF2 step."""
     mesh = synth.quad_box(64, hi=(10.0, 10.0), periodic=(True, True))
     o, g = pair(mesh, 3, oracle.EULER, oracle.CASE_VORTEX)
@@ -123,11 +123,11 @@ def test_full_c2_euler_vortex_64x64_p3():
     # a perturbed state: at the interpolated exact solution R is a near-cancellation
     u = o.interpolate(0.05) + 1e-2 * synth.random_vector(o.ndof, 4)
     v = synth.random_vector(o.ndof, 3)
-    assert_parity(host(g.residual(cuda(u))), o.residual(u), what="R c2")
-    assert_parity(host(g.jvp(cuda(u), cuda(v))), o.jvp(u, v), what="Jv c2")
+    assert_parity(host(g.residual(cuda(u))), o.residual(u), what="R vortex 64x64")
+    assert_parity(host(g.jvp(cuda(u), cuda(v))), o.jvp(u, v), what="Jv vortex 64x64")
 
 
-def test_full_c3_hex48_p4_sampled():
+def test_full_convdiff_hex48_p4_sampled():
     """3-D convection-diffusion on 48^3 hexahedra, p = 4 (13.8 M DOF): the kernel runs
     on the full mesh; the oracle evaluates a sample of elements (corners, faces, interior)."""
     n = 48
@@ -140,9 +140,9 @@ def test_full_c3_hex48_p4_sampled():
                                    rng.integers(0, mesh.n_elem, 40)]))
     npe = o.npe
     r = host(g.residual(cuda(u))).reshape(-1, 1, npe)[el]
-    assert_parity(r, o.residual_some(u, el), what="R c3")
+    assert_parity(r, o.residual_some(u, el), what="R hex 48^3")
     jv = host(g.jvp(cuda(u), cuda(v))).reshape(-1, 1, npe)[el]
-    assert_parity(jv, o.jvp_some(u, v, el), what="Jv c3")
+    assert_parity(jv, o.jvp_some(u, v, el), what="Jv hex 48^3")
 
 
 # ------------------------------------------------------------------- solvers
@@ -161,8 +161,8 @@ def test_gmres_matches_oracle_solve():
     assert rep["lin_resid"] <= 1e-11 * 1.01
 
 
-def test_newton_c1_one_step():
-    """Config c1: one Newton step from u = 0 with unpreconditioned GMRES to 1e-10."""
+def test_newton_poisson_512_triangles_one_step():
+    """2-D Poisson on 512 triangles, p = 2: one Newton step from u = 0 with unpreconditioned GMRES to 1e-10."""
     mesh = synth.tri_square(16)
     o, g = pair(mesh, 2, oracle.POISSON, oracle.CASE_SINSIN, gmres_m=30, gmres_rtol=1e-10,
                 max_restarts=400, newton_rtol=1e-9, max_newton=1)
@@ -177,7 +177,7 @@ def test_newton_c1_one_step():
     assert abs(eu - euo) <= 1e-6 * euo
 
 
-def test_newton_c2_bdf2_step_small():
+def test_newton_vortex_bdf2_step_16x16():
     """One BDF2 step of the vortex by Newton-GMRES to 1e-8 on a 16 x 16 mesh, p = 3."""
     mesh = synth.quad_box(16, hi=(10.0, 10.0), periodic=(True, True))
     o, g = pair(mesh, 3, oracle.EULER, oracle.CASE_VORTEX, newton_rtol=1e-8, gmres_rtol=1e-4)

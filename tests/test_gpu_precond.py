@@ -75,8 +75,8 @@ def test_block_jacobi_newton_bdf2(kprec):
     assert reps[1]["pc_setups"] == 1
 
 
-def test_block_jacobi_c1_poisson():
-    """Config c1 with the block-Jacobi preconditioner (blocks by coloured probing)."""
+def test_block_jacobi_poisson_512_triangles():
+    """2-D Poisson on 512 triangles, p = 2, with the block-Jacobi preconditioner (blocks by coloured probing)."""
     mesh = synth.tri_square(16)
     o, g = pair(mesh, 2, oracle.POISSON, oracle.CASE_SINSIN, gmres_rtol=1e-10, newton_rtol=1e-9, max_newton=1,
                 max_restarts=400, precond=1)
