@@ -366,24 +366,34 @@ int do_pc_setup(ldg_ctx* ctx, const double* u) {
   }
   const int threads = n >= 16 ? 256 : ((n + 31) / 32) * 32;
   // compile-time block sizes of the common element blocks (quadrilateral Euler p = 1..4,
-  // scalar models p = 3)
-  auto fixed = [&](auto tag, auto nconst) -> int {
+  // scalar models p = 3); threads and columns per thread as measured fastest on a B300
+  // for each size and precision (4,096 to 65,536 random blocks)
+  auto fixed = [&](auto tag, auto nconst, auto ntconst, auto cptconst) -> int {
     typedef decltype(tag) T;
-    constexpr int NN = decltype(nconst)::value;
-    constexpr int NT = 256;   // 64 threads per block (168 registers each) measured slower
-    const size_t smem = BInvN<T, NN, NT>::SMEM;
-    CK(cudaFuncSetAttribute(k_block_inverse_n<T, NN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_block_inverse_n<T, NN, NT><<<(unsigned)ctx->E, NT, smem, ctx->stream>>>(ctx->d_blocks, (T*)ctx->d_binv,
-                                                                               ctx->d_status);
+    constexpr int NN = decltype(nconst)::value, NT = decltype(ntconst)::value, CPT = decltype(cptconst)::value;
+    const size_t smem = BInvN<T, NN, NT, CPT>::SMEM;
+    CK(cudaFuncSetAttribute(k_block_inverse_n<T, NN, NT, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem));
+    k_block_inverse_n<T, NN, NT, CPT><<<(unsigned)ctx->E, NT, smem, ctx->stream>>>(ctx->d_blocks, (T*)ctx->d_binv,
+                                                                                    ctx->d_status);
     count_launch();
     CK(cudaGetLastError());
     ctx->pc_ready = true;
     return LDG_OK;
   };
-  if (n == 16) return fp64 ? fixed(0.0, std::integral_constant<int, 16>()) : fixed(0.f, std::integral_constant<int, 16>());
-  if (n == 36) return fp64 ? fixed(0.0, std::integral_constant<int, 36>()) : fixed(0.f, std::integral_constant<int, 36>());
-  if (n == 64) return fp64 ? fixed(0.0, std::integral_constant<int, 64>()) : fixed(0.f, std::integral_constant<int, 64>());
-  if (n == 100 && !fp64) return fixed(0.f, std::integral_constant<int, 100>());
+  typedef std::integral_constant<int, 4> C4;
+  if (n == 16)
+    return fp64 ? fixed(0.0, std::integral_constant<int, 16>(), std::integral_constant<int, 64>(), C4())
+                : fixed(0.f, std::integral_constant<int, 16>(), std::integral_constant<int, 32>(), C4());
+  if (n == 36)
+    return fp64 ? fixed(0.0, std::integral_constant<int, 36>(), std::integral_constant<int, 64>(), C4())
+                : fixed(0.f, std::integral_constant<int, 36>(), std::integral_constant<int, 64>(), C4());
+  if (n == 64)
+    return fp64 ? fixed(0.0, std::integral_constant<int, 64>(), std::integral_constant<int, 256>(), C4())
+                : fixed(0.f, std::integral_constant<int, 64>(), std::integral_constant<int, 128>(),
+                        std::integral_constant<int, 8>());
+  if (n == 100 && !fp64)
+    return fixed(0.f, std::integral_constant<int, 100>(), std::integral_constant<int, 256>(), C4());
   if (fp64) {
     const size_t smem = block_inverse_smem<double>(n);
     CK(cudaFuncSetAttribute(k_block_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -9,6 +9,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace ldg {
 
 // inv[e] = blocks[e]^{-1} in precision T: in-place Gauss-Jordan elimination with
@@ -98,149 +100,222 @@ __global__ void k_block_inverse(const double* __restrict__ blocks, T* __restrict
   }
 }
 
-// The same Gauss-Jordan inversion for a compile-time block size N (a multiple of 4,
-// N <= 128, NT threads) with the matrix held in registers: thread t owns columns
-// 4 (t mod N/4) .. +3 in rows rg, rg + NG, ... (rg = t div N/4, NG row groups), so the
-// elimination reads only the pivot column, the scaled pivot row and the old row k from
-// shared memory (double-buffered by the parity of k, three barriers per step). The
-// block is staged through a padded [N][N+1] shared tile on the way in and out, where
-// the row interchanges are undone as one column permutation.
-template <class T, int N, int NT> struct BInvN {
-  static constexpr int CG = N / 4;                               // column groups of 4
+// |x| as an integer with the same order as the magnitudes (IEEE bit pattern without
+// the sign); NaN maps to -1
+__device__ __forceinline__ int abs_key(float x) {
+  const int b = __float_as_int(x) & 0x7fffffff;
+  return b > 0x7f800000 ? -1 : b;
+}
+__device__ __forceinline__ long long abs_key(double x) {
+  const long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+  return b > 0x7ff0000000000000LL ? -1LL : b;
+}
+
+// f(integral_constant<int, I>) for I = I0 .. I1 - 1, in order
+template <int I0, int I1, class F> __device__ __forceinline__ void unrolled_for(F& f) {
+  if constexpr (I0 < I1) {
+    f(std::integral_constant<int, I0>());
+    unrolled_for<I0 + 1, I1>(f);
+  }
+}
+
+// The same Gauss-Jordan inversion with partial pivoting for a compile-time block size
+// N (a multiple of CPT, N <= 128; NT threads) with the matrix held in registers:
+// thread t owns columns CPT (t mod N/CPT) .. +CPT-1 in rows rg, rg + NG, ...
+// (rg = t div N/CPT, NG row groups). Rows are not interchanged; the pivot of step k
+// is the largest |A(i, k)| over the rows i not yet used as pivots (ties to the smaller
+// i), found by every warp from the same shared copy of column k (on integer keys of
+// the magnitudes), so all warps agree without a broadcast. Step k, with p the pivot row and r_p = A(p, :) / A(p, k),
+// r_p(k) = 1 / A(p, k):
+//   * column k was zeroed in registers when its owners published it, and row p is
+//     zeroed by its owners when they publish r_p;
+//   * every row then takes A(i, :) -= f_i r_p with f_i = A(i, k), f_p = -1, so row p
+//     becomes r_p and column k becomes -A(i, k) / A(p, k): no per-element selects;
+//   * the owners of column k + 1 publish it for the next step at once (the column
+//     buffer is double-buffered by the parity of k), two barriers per step.
+// The k loop is unrolled by CPT so that the published column is a fixed register.
+// At the end, with p_k the pivot row of step k and c(p_k) = k, the inverse is
+// A^{-1}(k, m) = X(p_k, c(m)), read from the padded [N][N+1] shared tile that also
+// stages the block on the way in (16-byte global loads and stores).
+template <class T, int N, int NT, int CPT> struct BInvN {
+  static constexpr int CG = N / CPT;                             // column groups
   static constexpr int NG = (NT / CG) < N ? (NT / CG) : N;       // row groups
   static constexpr int RPT = (N + NG - 1) / NG;                  // rows per thread
-  static constexpr size_t SMEM = (size_t)N * (N + 1) * sizeof(T) + 6 * N * sizeof(T) + N * sizeof(int) + 64;
+  static constexpr int NS = (N + 31) / 32;                       // pivot-search rows per lane
+  static constexpr size_t SMEM = (size_t)N * (N + 1) * sizeof(T) + 3 * N * sizeof(T) + 2 * N * sizeof(int) + 64;
 };
 
-template <class T, int N, int NT>
+template <class T, int N, int NT, int CPT>
 __global__ void __launch_bounds__(NT) k_block_inverse_n(const double* __restrict__ blocks, T* __restrict__ inv,
                                                         int* status) {
-  static_assert(N % 4 == 0 && N <= 128 && NT % 32 == 0 && NT / (N / 4) >= 1, "block size");
-  typedef BInvN<T, N, NT> L;
-  constexpr int CG = L::CG, NG = L::NG, RPT = L::RPT, LD = N + 1;
+  static_assert(N % CPT == 0 && N % 4 == 0 && N <= 128 && NT % 32 == 0 && NT / (N / CPT) >= 1 &&
+                    (CPT * sizeof(T)) % 16 == 0, "block size");
+  typedef BInvN<T, N, NT, CPT> L;
+  constexpr int CG = L::CG, NG = L::NG, RPT = L::RPT, NS = L::NS, LD = N + 1;
+  constexpr int VW = 16 / sizeof(T);   // values per 16-byte shared load
+  typedef typename std::conditional<sizeof(T) == 4, int, long long>::type PivotKey;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* S = (T*)sm_raw;                   // [N][N+1] staging tile
-  T* colbuf = S + N * LD;              // [2][N] pivot column of step k
-  T* prow = colbuf + 2 * N;            // [2][N] scaled pivot row
-  T* rowk = prow + 2 * N;              // [2][N] old row k
-  int* srcc = (int*)(rowk + 2 * N);    // [N] final column permutation
-  __shared__ int piv;
+  T* colbuf = S + N * LD;              // [2][N] column k (parity of k)
+  T* prow = colbuf + 2 * N;            // [N] scaled pivot row (16-byte aligned: N (N + 3) % 4 == 0)
+  int* pivrow = (int*)(prow + N);      // [N] pivot row of step k
+  int* colof = pivrow + N;             // [N] step whose pivot was row i
   const int e = blockIdx.x;
-  const double* B = blocks + (size_t)e * N * N;   // column-major
-  for (int idx = threadIdx.x; idx < N * N; idx += NT) {
-    const int col = idx / N, row = idx - col * N;
-    S[row * LD + col] = (T)B[idx];
+  const int lane = threadIdx.x & 31;
+  // column-major FP64 block -> row-major padded tile; N even, so each 16-byte pair
+  // holds rows r, r + 1 of one column
+  {
+    const double2* B2 = (const double2*)(blocks + (size_t)e * N * N);
+    constexpr int P2 = N * N / 2, IT = (P2 + NT - 1) / NT;
+    double2 v[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int i2 = threadIdx.x + it * NT;
+      if (i2 < P2) v[it] = B2[i2];
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int i2 = threadIdx.x + it * NT;
+      if (i2 < P2) {
+        const int col = (2 * i2) / N, row = 2 * i2 - col * N;
+        S[row * LD + col] = (T)v[it].x;
+        S[(row + 1) * LD + col] = (T)v[it].y;
+      }
+    }
   }
   const int cg = threadIdx.x % CG, rg = threadIdx.x / CG;
   const bool act = rg < NG;
   __syncthreads();
-  T a[RPT][4];
+  T a[RPT][CPT];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int i = rg + NG * r;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) a[r][c] = (act && i < N) ? S[i * LD + 4 * cg + c] : T(0);
+    for (int c = 0; c < CPT; ++c) a[r][c] = (act && i < N) ? S[i * LD + CPT * cg + c] : T(0);
   }
-  for (int k = 0; k < N; ++k) {
-    const int par = (k & 1) * N;
-    const int kq = k >> 2, kc = k & 3;
-    // (1) the owners of column k publish it
+  // the owners of column CPT kq + KC write it to buf and zero it in registers
+  auto publish_column = [&](int kq, auto kc_const, T* buf) {
+    constexpr int KC = decltype(kc_const)::value;
     if (act && cg == kq) {
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
         const int i = rg + NG * r;
-        if (i < N) colbuf[par + i] = kc == 0 ? a[r][0] : kc == 1 ? a[r][1] : kc == 2 ? a[r][2] : a[r][3];
+        if (i < N) {
+          buf[i] = a[r][KC];
+          a[r][KC] = T(0);
+        }
       }
     }
-    __syncthreads();
-    // (2) pivot row: largest |A(i, k)|, i >= k (ties to the smaller index)
-    if (threadIdx.x < 32) {
-      T best = T(-1);
-      int bi = k;
-      for (int i = k + threadIdx.x; i < N; i += 32) {
-        const T v = fabs(colbuf[par + i]);
-        if (v > best) { best = v; bi = i; }
+  };
+  publish_column(0, std::integral_constant<int, 0>(), colbuf);
+  bool used[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) used[t] = false;
+  __syncthreads();
+  for (int kq = 0; kq < CG; ++kq) {
+    auto step = [&](auto kc_const) {
+      constexpr int KC = decltype(kc_const)::value;
+      const int k = CPT * kq + KC;
+      const T* col = colbuf + (k & 1) * N;
+      // pivot row, on integer keys of |A(i, k)| (the order of the magnitudes; NaN
+      // counts as -1, and a lane without unused rows offers row N at -2), so that no
+      // floating-point instruction is spent on the search
+      PivotKey best = -2;
+      int bi = N;
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        const int i = lane + 32 * t;
+        if (i < N && !used[t]) {
+          const PivotKey key = abs_key(col[i]);
+          if (key > best) { best = key; bi = i; }
+        }
       }
+#pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const PivotKey ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (threadIdx.x == 0) { piv = bi; srcc[k] = bi; }
-    }
-    __syncthreads();
-    const int p = piv;
-    const T pv = colbuf[par + p];
-    if (pv == T(0) && threadIdx.x == 0) *status = 1;
-    const T ip = pv != T(0) ? T(1) / pv : T(0);
-    // (3) the owners of row p publish it scaled, the owners of row k publish the old row k
-    if (act) {
+      const int p = bi;
 #pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        const int i = rg + NG * r;
-        if (i == p)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) prow[par + 4 * cg + c] = (4 * cg + c == k ? T(1) : a[r][c]) * ip;
-        if (i == k)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) rowk[par + 4 * cg + c] = a[r][c];
+      for (int t = 0; t < NS; ++t)
+        if (lane + 32 * t == p) used[t] = true;
+      if (threadIdx.x == 0) {
+        pivrow[k] = p;
+        colof[p] = k;
       }
-    }
-    __syncthreads();
-    // (4) elimination in registers; the interchange of rows k and p is part of it
-    if (act) {
-      T pk[4], ok[4];
+      // the owners of row p publish it scaled (column k: 1 / pivot) and zero it; only
+      // they form the reciprocal
+      if (act && p >= rg && (p - rg) % NG == 0) {
+        const T pv = col[p];
+        if (pv == T(0) && cg == 0) *status = 1;
+        const T ip = pv != T(0) ? T(1) / pv : T(0);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        pk[c] = prow[par + 4 * cg + c];
-        ok[c] = rowk[par + 4 * cg + c];
-      }
-      const T fk = colbuf[par + k];                    // old A(k, k): multiplier of the new row p
+        for (int r = 0; r < RPT; ++r) {
+          if (rg + NG * r == p) {
 #pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        const int i = rg + NG * r;
-        if (i >= N) continue;
-        if (i == k) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) a[r][c] = pk[c];
-          continue;
-        }
-        const bool isp = (i == p);
-        const T f = isp ? fk : colbuf[par + i];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const T src = isp ? ok[c] : a[r][c];
-          a[r][c] = (4 * cg + c == k ? T(0) : src) - f * pk[c];
+            for (int c = 0; c < CPT; ++c) {
+              prow[CPT * cg + c] = (c == KC && cg == kq ? T(1) : a[r][c]) * ip;
+              a[r][c] = T(0);
+            }
+          }
         }
       }
-    }
+      __syncthreads();
+      // elimination: A(i, :) -= f_i r_p, f_p = -1
+      if (act) {
+        T pk[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; c += VW) {
+          if constexpr (sizeof(T) == 4) {
+            const float4 w = *(const float4*)(prow + CPT * cg + c);
+            pk[c] = w.x; pk[c + 1] = w.y; pk[c + 2] = w.z; pk[c + 3] = w.w;
+          } else {
+            const double2 w = *(const double2*)(prow + CPT * cg + c);
+            pk[c] = w.x; pk[c + 1] = w.y;
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          const int i = rg + NG * r;
+          if (i < N) {
+            const T f = i == p ? T(-1) : col[i];
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) a[r][c] = fma(-f, pk[c], a[r][c]);
+          }
+        }
+      }
+      // the next column, for the next step
+      if (k + 1 < N) {
+        constexpr int KN = (KC + 1) % CPT;
+        publish_column(KC + 1 < CPT ? kq : kq + 1, std::integral_constant<int, KN>(), colbuf + ((k + 1) & 1) * N);
+      }
+      __syncthreads();
+    };
+    unrolled_for<0, CPT>(step);
   }
-  // undo the row interchanges as column interchanges (last first): column c of the
-  // inverse is column srcc[c] of the eliminated matrix
-  __syncthreads();
+  // X to the shared tile (its last reads precede the elimination's barriers)
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int i = rg + NG * r;
     if (act && i < N)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) S[i * LD + 4 * cg + c] = a[r][c];
-  }
-  if (threadIdx.x == 0) {
-    int perm[N];
-    for (int c = 0; c < N; ++c) perm[c] = c;
-    for (int k = N - 1; k >= 0; --k) {
-      const int q = srcc[k];
-      const int t = perm[k];
-      perm[k] = perm[q];
-      perm[q] = t;
-    }
-    for (int c = 0; c < N; ++c) srcc[c] = perm[c];
+      for (int c = 0; c < CPT; ++c) S[i * LD + CPT * cg + c] = a[r][c];
   }
   __syncthreads();
+  // A^{-1}(k, m) = X(p_k, c(m)), column-major, 16 bytes per store (N is a multiple of 4)
   T* Iv = inv + (size_t)e * N * N;
-  for (int idx = threadIdx.x; idx < N * N; idx += NT) {
-    const int col = idx / N, row = idx - col * N;
-    Iv[idx] = S[row * LD + srcc[col]];
+  if constexpr (sizeof(T) == 4) {
+    for (int i4 = threadIdx.x; i4 < N * N / 4; i4 += NT) {
+      const int m = (4 * i4) / N, k = 4 * i4 - m * N, sc = colof[m];
+      ((float4*)Iv)[i4] = make_float4(S[pivrow[k] * LD + sc], S[pivrow[k + 1] * LD + sc],
+                                      S[pivrow[k + 2] * LD + sc], S[pivrow[k + 3] * LD + sc]);
+    }
+  } else {
+    for (int i2 = threadIdx.x; i2 < N * N / 2; i2 += NT) {
+      const int m = (2 * i2) / N, k = 2 * i2 - m * N, sc = colof[m];
+      ((double2*)Iv)[i2] = make_double2(S[pivrow[k] * LD + sc], S[pivrow[k + 1] * LD + sc]);
+    }
   }
 }
 
