@@ -132,10 +132,17 @@ typedef struct {
                            linear solve misses its tolerance) */
   int pc_refresh;       /* rebuild the preconditioner every pc_refresh Newton iterations
                            (0 = once per ldg_newton_gmres call, at the initial guess) */
+  int newton_forcing;   /* linear tolerance eta_k of Newton step k (inexact Newton):
+                           LDG_FORCING_FIXED (default): eta_k = gmres_rtol;
+                           LDG_FORCING_LAST: eta_k = max(gmres_rtol,
+                           1/2 newton_rtol ||R(u_0)|| / ||R(u_k)||), so that no step, in
+                           practice the last one, is solved further than the Newton
+                           tolerance needs */
 } ldg_options;
 
 enum { LDG_FP64 = 0, LDG_FP32 = 1 };
 enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1, LDG_PC_MLP = 2 };
+enum { LDG_FORCING_FIXED = 0, LDG_FORCING_LAST = 1 };
 
 typedef struct {
   int newton_iters;

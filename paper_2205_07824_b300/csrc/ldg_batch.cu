@@ -411,6 +411,7 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
   if (o.gmres_rtol <= 0) o.gmres_rtol = 1e-3;
   if (o.krylov_precision != LDG_FP32) o.krylov_precision = LDG_FP64;
   if (o.precond != LDG_PC_BJACOBI) o.precond = LDG_PC_NONE;
+  if (o.newton_forcing != LDG_FORCING_LAST) o.newton_forcing = LDG_FORCING_FIXED;
   b->opt = o;
   b->m = o.gmres_m;
   b->pc = o.precond == LDG_PC_BJACOBI;
@@ -551,7 +552,7 @@ int finish_build(ldg_batch* b, const std::vector<int64_t>& seg_off, const std::v
   BatchCtl ctl;
   std::memset(&ctl, 0, sizeof(ctl));
   ctl.max_newton = o.max_newton; ctl.max_restarts = o.max_restarts; ctl.m = b->m;
-  ctl.newton_rtol = o.newton_rtol; ctl.gmres_rtol = o.gmres_rtol;
+  ctl.newton_rtol = o.newton_rtol; ctl.gmres_rtol = o.gmres_rtol; ctl.forcing = o.newton_forcing;
   BK(cudaMemcpy(b->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice));
   for (int** q : {&b->d_skip_newt, &b->d_skip_gm, &b->d_skip_arn}) {
     BK(cudaMalloc(q, b->nseg * sizeof(int)));

@@ -68,6 +68,7 @@ struct BatchCtl {
   int n_newton, n_gmres, n_arn;      // instances active in each loop
   int max_newton, max_restarts, m;
   double newton_rtol, gmres_rtol;
+  int forcing;    // ldg_options::newton_forcing
   long long trips_a, trips_b, trips_c;   // loop bodies executed
 };
 
@@ -319,8 +320,15 @@ __global__ void __launch_bounds__(KRY_T) kb_scale(SegView sv, const BatchCtl* ct
     if (threadIdx.x == 0 && done) skip[s] = 1;
     return;
   }
-  const double nr = sqrt(nrm2);
-  const double f = nr > 0.0 ? 1.0 / nr : 0.0;
+  // 1 / ||w|| once per CTA: FP64 square roots and divisions in every thread would
+  // cost the FP64 pipe more than the scaling itself
+  __shared__ double f_s;
+  if (threadIdx.x == 0) {
+    const double nr = sqrt(nrm2);
+    f_s = nr > 0.0 ? 1.0 / nr : 0.0;
+  }
+  __syncthreads();
+  const double f = f_s;
   double* out = V + (size_t)(j + 1) * ldv;
   for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += KRY_T) {
     const double t = w[i] * f;
@@ -335,8 +343,13 @@ __global__ void kb_cycle_start(SegView sv, const double* __restrict__ r, double*
   const int c = blockIdx.x, s = sv.chunk_seg[c];
   if (skip[s]) return;
   KrySmall S{sv.m};
-  const double nr = sqrt(sv.small[(size_t)s * sv.ks + S.sc() + 4]);
-  const double f = nr > 0.0 ? 1.0 / nr : 0.0;
+  __shared__ double f_s;
+  if (threadIdx.x == 0) {
+    const double nr = sqrt(sv.small[(size_t)s * sv.ks + S.sc() + 4]);
+    f_s = nr > 0.0 ? 1.0 / nr : 0.0;
+  }
+  __syncthreads();
+  const double f = f_s;
   for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) {
     const double t = r[i] * f;
     V0[i] = t;
@@ -464,7 +477,8 @@ __global__ void kb_init(BatchCtl* ctl, SegState* st, int nseg, int* skip_newt, i
 }
 
 // After R(u_k) and ||R_s||^2 (sc[5]): Newton convergence test per instance; the ones
-// still active start a linear solve J delta = R with threshold gmres_rtol ||R_s||.
+// still active start a linear solve J delta = R with threshold eta_k ||R_s||, eta_k the
+// forcing term (newton_forcing_eta).
 // bt[s] = 1 where the last step is halved instead (no linear solve this iteration).
 __global__ void kb_newton_check(BatchCtl* ctl, SegView sv, SegState* st, int* skip_newt, int* skip_gm, int* bt,
                                 cudaGraphConditionalHandle hb, int use_cond) {
@@ -506,7 +520,7 @@ __global__ void kb_newton_check(BatchCtl* ctl, SegView sv, SegState* st, int* sk
     q.gmres_active = 1;
     q.bnorm = rn;
     q.newton_iters++;
-    sc[3] = ctl->gmres_rtol * rn;
+    sc[3] = newton_forcing_eta(ctl->forcing, ctl->gmres_rtol, ctl->newton_rtol, q.r0, rn) * rn;
     sc[4] = rn * rn;
     skip_gm[s] = 0;
     ++active;

@@ -806,12 +806,13 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
       if (rep) rep->pc_setups++;
     }
     if (ctx->opt.precond == LDG_PC_MLP && k == 0 && (rc = ensure_pc_storage(ctx))) return rc;
-    rc = do_gmres(ctx, u, res, del, ctx->opt.gmres_rtol, rep);
+    const double eta = newton_forcing_eta(ctx->opt.newton_forcing, ctx->opt.gmres_rtol, ctx->opt.newton_rtol, r0, rn);
+    rc = do_gmres(ctx, u, res, del, eta, rep);
     if (rc == LDG_ERR_MAXIT && ctx->opt.precond == LDG_PC_MLP) {
       // the learned preconditioner did not reach the tolerance: fall back to block-Jacobi
       ctx->opt.precond = LDG_PC_BJACOBI;
       rc = do_pc_setup(ctx, u);
-      if (!rc) rc = do_gmres(ctx, u, res, del, ctx->opt.gmres_rtol, rep);
+      if (!rc) rc = do_gmres(ctx, u, res, del, eta, rep);
       ctx->opt.precond = LDG_PC_MLP;
       if (rep) { rep->pc_fallbacks++; rep->pc_setups++; }
     }
@@ -1053,6 +1054,7 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if (o.krylov_precision != LDG_FP32) o.krylov_precision = LDG_FP64;
   if (o.precond != LDG_PC_BJACOBI && o.precond != LDG_PC_MLP) o.precond = LDG_PC_NONE;
   if (o.pc_refresh < 0) o.pc_refresh = 0;
+  if (o.newton_forcing != LDG_FORCING_LAST) o.newton_forcing = LDG_FORCING_FIXED;
   ctx->opt = o;
   ctx->p = p; ctx->nq = o.nq1;
   ctx->mp = make_params(model);

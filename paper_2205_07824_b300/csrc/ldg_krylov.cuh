@@ -13,6 +13,16 @@ namespace ldg {
 
 constexpr int KRY_T = 256;
 
+// Forcing term of an inexact Newton step at ||R(u_k)|| = rn: gmres_rtol, or with
+// LDG_FORCING_LAST at least half of what the Newton tolerance still asks for, so that
+// the last linear solve is not taken further than the Newton test needs.
+__host__ __device__ inline double newton_forcing_eta(int forcing, double gmres_rtol, double newton_rtol, double r0,
+                                                     double rn) {
+  if (forcing != 1 || !(rn > 0.0)) return gmres_rtol;
+  const double need = 0.5 * newton_rtol * r0 / rn;
+  return need > gmres_rtol ? need : gmres_rtol;
+}
+
 // Layout of the small FP64 work area of one GMRES(m) solve.
 struct KrySmall {
   int m;

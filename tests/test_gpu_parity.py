@@ -196,6 +196,36 @@ def test_newton_vortex_bdf2_step_16x16():
     assert np.linalg.norm(o.residual(ug)) <= 1.5e-8 * st["r0"]
 
 
+@pytest.mark.parametrize("kprec,pc", [(0, 0), (1, 1)])
+def test_newton_forcing_last_step(kprec, pc):
+    """newton_forcing = LAST loosens only the linear tolerance that the Newton test does
+    not need (at least half of newton_rtol ||R0|| / ||Rk||): the BDF2 vortex step still
+    reaches ||R|| <= 1e-8 ||R0||, with no more GMRES iterations than the fixed forcing
+    term, and both solutions agree with the oracle's tight solve."""
+    from paper_2205_07824_b300.ldg import FORCING_FIXED, FORCING_LAST
+    mesh = synth.quad_box(16, hi=(10.0, 10.0), periodic=(True, True))
+    dt = 0.05
+    reps, sols = {}, {}
+    for forcing in (FORCING_FIXED, FORCING_LAST):
+        o, g = pair(mesh, 3, oracle.EULER, oracle.CASE_VORTEX, newton_rtol=1e-8, gmres_rtol=1e-3,
+                    krylov_precision=kprec, precond=pc, newton_forcing=forcing)
+        un, unm1 = o.interpolate(0.0), o.interpolate(-dt)
+        g.set_time(2, dt, dt, cuda(un), cuda(unm1))
+        u = cuda(un)
+        reps[forcing] = g.newton_gmres(u)
+        sols[forcing] = host(u)
+    o.set_time(2, dt, dt, un, unm1)
+    uo, rc, st = o.newton(un.copy(), m=30, newton_rtol=1e-10, gmres_rtol=1e-6)
+    assert rc == 0
+    print({f: (r["newton_iters"], r["gmres_iters"], r["rfinal"] / r["r0"]) for f, r in reps.items()})
+    for forcing, rep in reps.items():
+        assert rep["rfinal"] <= 1e-8 * rep["r0"]
+        assert np.linalg.norm(sols[forcing] - uo) <= 1e-7 * np.linalg.norm(uo)
+        assert np.linalg.norm(o.residual(sols[forcing])) <= 1.5e-8 * st["r0"]
+    assert reps[FORCING_LAST]["gmres_iters"] <= reps[FORCING_FIXED]["gmres_iters"]
+    assert reps[FORCING_LAST]["newton_iters"] == reps[FORCING_FIXED]["newton_iters"]
+
+
 @pytest.mark.parametrize("model", [oracle.EULER, oracle.NS, oracle.CONVDIFF])
 def test_finite_difference_jvp(model):
     """The FD variant against the exact J.v: the forward difference is off by O(eps),
