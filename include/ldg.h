@@ -138,6 +138,13 @@ typedef struct {
                            1/2 newton_rtol ||R(u_0)|| / ||R(u_k)||), so that no step, in
                            practice the last one, is solved further than the Newton
                            tolerance needs */
+  int pc_reuse;         /* graph-driven solves (ldg_newton_gmres without the learned
+                           preconditioner, ldg_batch_solve): the block-Jacobi blocks are built
+                           at the initial guess of every pc_reuse-th solve call and reused by
+                           the calls in between (a preconditioner lagged over time steps);
+                           a call whose time-scheme coefficient a0/dt differs from the one
+                           the blocks were built with rebuilds them. 0 or 1 (default): every
+                           call */
 } ldg_options;
 
 enum { LDG_FP64 = 0, LDG_FP32 = 1 };

@@ -33,6 +33,9 @@ struct BGroup {
   int64_t off = 0, ndof = 0;   // slice of the batch vector
   int* d_inst = nullptr;       // [E] instance (segment) of each element
   int etype = 0, p = 0, nq = 0, model = 0;
+  bool pc_built = false;       // blocks built by this batch, with the coefficients below
+  int pc_scheme = 0;
+  double pc_a0dt = 0.0;
 };
 
 }  // namespace
@@ -62,6 +65,7 @@ struct ldg_batch {
   double *d_u = nullptr, *d_res = nullptr, *d_r = nullptr, *d_x = nullptr, *d_w = nullptr;
   double *d_vcur = nullptr, *d_zcur = nullptr, *d_V = nullptr, *d_Z = nullptr;
   bool pc = false;
+  long long solves = 0;            // ldg_batch_solve calls (block-Jacobi reuse)
   bool borrowed = false;           // one instance whose context belongs to the caller
   std::vector<const KernelSet*> cap_ks;   // per group: kernels, time scheme and a0/dt the graph holds
   std::vector<int> cap_scheme;
@@ -412,6 +416,7 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
   if (o.krylov_precision != LDG_FP32) o.krylov_precision = LDG_FP64;
   if (o.precond != LDG_PC_BJACOBI) o.precond = LDG_PC_NONE;
   if (o.newton_forcing != LDG_FORCING_LAST) o.newton_forcing = LDG_FORCING_FIXED;
+  if (o.pc_reuse < 1) o.pc_reuse = 1;
   b->opt = o;
   b->m = o.gmres_m;
   b->pc = o.precond == LDG_PC_BJACOBI;
@@ -653,11 +658,23 @@ int ldg_batch_solve(ldg_batch* b, double* u_dev, int use_graph, ldg_solve_report
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = b->stream;
   BK(cudaMemcpyAsync(b->d_u, u_dev, (size_t)b->ntot * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  if (b->pc)
+  // block-Jacobi: built at this call's initial guess every pc_reuse calls, or when the
+  // time-scheme coefficient changed since the blocks were built
+  bool pc_built_now = false;
+  if (b->pc) {
+    const bool due = b->solves % b->opt.pc_reuse == 0;
     for (BGroup& g : b->groups) {
       g.ctx->stream = s;
-      if ((rc = do_pc_setup(g.ctx, b->d_u + g.off))) return gfail(b, g, rc);
+      if (due || !g.pc_built || !g.ctx->pc_ready || g.pc_scheme != g.ctx->scheme || g.pc_a0dt != g.ctx->a0dt) {
+        if ((rc = do_pc_setup(g.ctx, b->d_u + g.off))) return gfail(b, g, rc);
+        g.pc_built = true;
+        g.pc_scheme = g.ctx->scheme;
+        g.pc_a0dt = g.ctx->a0dt;
+        pc_built_now = true;
+      }
     }
+  }
+  b->solves++;
   long long before = launch_counter();
   if (b->exec) {
     // the captured kernels hold the tile, the time scheme and a0/dt of every group
@@ -728,7 +745,7 @@ int ldg_batch_solve(ldg_batch* b, double* u_dev, int use_graph, ldg_solve_report
     r.lin_resid = q.lin_resid;
     r.elapsed_ms = ms;
     r.status = q.status;
-    r.pc_setups = b->pc ? 1 : 0;
+    r.pc_setups = pc_built_now ? 1 : 0;
     r.newton_backtracks = q.backtracks;
   }
   if (worst != LDG_OK) return bfail(b, worst, "some instances did not converge (see the per-instance reports)");

@@ -1055,6 +1055,7 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if (o.precond != LDG_PC_BJACOBI && o.precond != LDG_PC_MLP) o.precond = LDG_PC_NONE;
   if (o.pc_refresh < 0) o.pc_refresh = 0;
   if (o.newton_forcing != LDG_FORCING_LAST) o.newton_forcing = LDG_FORCING_FIXED;
+  if (o.pc_reuse < 1) o.pc_reuse = 1;
   ctx->opt = o;
   ctx->p = p; ctx->nq = o.nq1;
   ctx->mp = make_params(model);

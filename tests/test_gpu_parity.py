@@ -226,6 +226,37 @@ def test_newton_forcing_last_step(kprec, pc):
     assert reps[FORCING_LAST]["newton_iters"] == reps[FORCING_FIXED]["newton_iters"]
 
 
+def test_block_jacobi_reuse_over_time_steps():
+    """pc_reuse = 3: the block-Jacobi blocks are built at the first of every three solve
+    calls and reused in between (reported pc_setups 1, 0, 0, 1), a change of dt rebuilds
+    them, and every step still reaches the Newton tolerance with a solution that agrees
+    with the one rebuilt every step."""
+    mesh = synth.quad_box(16, hi=(10.0, 10.0), periodic=(True, True))
+    dt = 0.05
+    sols, setups = {}, {}
+    for reuse in (1, 3):
+        o, g = pair(mesh, 3, oracle.EULER, oracle.CASE_VORTEX, newton_rtol=1e-8, gmres_rtol=1e-3,
+                    krylov_precision=1, precond=1, pc_reuse=reuse)
+        um1, u0 = o.interpolate(-dt), o.interpolate(0.0)
+        prev, cur = cuda(um1), cuda(u0)
+        setups[reuse], sols[reuse] = [], []
+        for step in range(4):
+            g.set_time(2, (step + 1) * dt, dt, cur, prev)
+            u = cur.clone()
+            rep = g.newton_gmres(u)
+            assert rep["rfinal"] <= 1e-8 * rep["r0"]
+            setups[reuse].append(rep["pc_setups"])
+            sols[reuse].append(host(u))
+            prev, cur = cur, u
+        # a new dt changes the BDF mass coefficient: the blocks are rebuilt at once
+        g.set_time(2, 5 * dt, 0.5 * dt, cur, prev)
+        setups[reuse].append(g.newton_gmres(cur.clone())["pc_setups"])
+    assert setups[1] == [1, 1, 1, 1, 1]
+    assert setups[3] == [1, 0, 0, 1, 1]
+    for a, b in zip(sols[1], sols[3]):
+        assert np.linalg.norm(a - b) <= 1e-7 * np.linalg.norm(a)
+
+
 @pytest.mark.parametrize("model", [oracle.EULER, oracle.NS, oracle.CONVDIFF])
 def test_finite_difference_jvp(model):
     """The FD variant against the exact J.v: the forward difference is off by O(eps),
