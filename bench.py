@@ -215,6 +215,17 @@ def graph_time_ms(g, fn, reps):
         g.set_stream(old)
 
 
+def forcing_of(args):
+    """ldg newton_forcing value of the --forcing choice."""
+    return 1 if args.forcing == "last" else 0
+
+
+def linear_tolerance(args):
+    """The linear-solve tolerance rule of the --forcing choice, for the JSON config."""
+    return ("max(1e-3, 0.5e-8 ||R0|| / ||Rk||) per Newton step k (every form)" if args.forcing == "last"
+            else "1e-3 per Newton step")
+
+
 def vortex_problem(LDG, mesh, forcing=0, pc_reuse=1):
     """The vortex: context factory (preconditioner, Krylov precision), initial states, dt."""
     from paper_2205_07824_b300.ldg import EULER, CASE_VORTEX
@@ -340,7 +351,7 @@ def run_batch(args):
 
     def make(kp):
         return Batch(meshes, ps, CONVDIFF, CASE_SINSIN, mus, gmres_m=30, newton_rtol=1e-8, gmres_rtol=1e-3,
-                     krylov_precision=kp, precond=pc)
+                     krylov_precision=kp, precond=pc, newton_forcing=forcing_of(args))
 
     def timed(b, steps, warmup, use_graph=True):
         u = b.empty()
@@ -455,7 +466,7 @@ def run_batch(args):
         line = {"metric": METRIC, "value": gdofs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if kprec == 0 else "f64+f32", "data": "synthetic",
-                "config": {"workload": BATCH_WORKLOAD, "n_inst": b.n_inst, "n_dof_total": int(b.n_total),
+                "config": {"linear_tolerance": linear_tolerance(args), "workload": BATCH_WORKLOAD, "n_inst": b.n_inst, "n_dof_total": int(b.n_total),
                            "order_groups": b.n_groups, "tiles_autotuned": tiles,
                            "value_definition": "sum over instances of DOF x J.v applications (Arnoldi and true "
                                                "residual; block probing excluded) / timed batched solve time",
@@ -645,7 +656,7 @@ CYL_WORKLOAD = ("2D compressible Navier-Stokes flow past a cylinder (radius 0.5 
                 "at the wall (velocity x tanh((r-0.5)/0.1)), Newton-GMRES(30) to 1e-8 (FP64 residual)")
 
 
-def cylinder_problem(LDG, mesh, re):
+def cylinder_problem(LDG, mesh, re, forcing=0):
     """Far-field data: the uniform Mach 0.2 free stream. Initial state (both BDF2 levels):
     the free stream with its velocity scaled by tanh((r - 0.5) / 0.1), which meets the
     no-slip wall (an impulsive start, free stream up to the wall, is not a state the
@@ -654,7 +665,7 @@ def cylinder_problem(LDG, mesh, re):
 
     def make(p, kprec):
         return LDG(mesh, 3, NS, CASE_CYLINDER, (1.4, re, 0.72), gmres_m=30, newton_rtol=1e-8, gmres_rtol=1e-3,
-                   krylov_precision=kprec, precond=p)
+                   krylov_precision=kprec, precond=p, newton_forcing=forcing)
 
     def init(g):
         g0 = LDG(mesh, 3, NS, CASE_CYLINDER_START, (1.4, re, 0.72))
@@ -679,7 +690,7 @@ def run_cylinder_sweep(args):
     res = [float(np.random.default_rng(args.re_seed + k).uniform(100.0, 1000.0)) for k in range(K)]
     mus = [(1.4, re, 0.72) for re in res]
     b = Batch([mesh] * K, [3] * K, NS, CASE_CYLINDER, mus, gmres_m=30, newton_rtol=1e-8, gmres_rtol=1e-3,
-              krylov_precision=1, precond=1)
+              krylov_precision=1, precond=1, newton_forcing=forcing_of(args))
     g0 = LDG(mesh, 3, NS, CASE_CYLINDER_START, mus[0])
     u0 = g0.interpolate(0.0)
     del g0
@@ -724,7 +735,7 @@ def run_cylinder_sweep(args):
         line = {"metric": METRIC, "value": gdofs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-                "config": {"workload": f"Reynolds-number sweep of the cylinder flow: {K} instances (Re from seeds "
+                "config": {"linear_tolerance": linear_tolerance(args), "workload": f"Reynolds-number sweep of the cylinder flow: {K} instances (Re from seeds "
                                        f"{args.re_seed}..{args.re_seed + K - 1}) on the {mesh.n_elem}-element mesh, "
                                        "p=3, one batched Newton-GMRES per BDF2 step (dt=0.1) in one CUDA graph launch, "
                                        "FP32 Krylov J.v + block-Jacobi, each instance to 1e-8",
@@ -750,7 +761,7 @@ def run_cylinder(args):
     nr, nt = args.cyl_layers, args.cyl_around
     mesh = synth.cylinder_mesh(nr, nt, 3, seed=7)
     re = float(np.random.default_rng(args.re_seed + rank).uniform(100.0, 1000.0))
-    prob = cylinder_problem(LDG, mesh, re)
+    prob = cylinder_problem(LDG, mesh, re, forcing_of(args))
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     clocks = ClockSampler(local)
@@ -846,7 +857,7 @@ def run_cylinder(args):
         line = {"metric": METRIC, "value": gdofs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-                "config": {"workload": CYL_WORKLOAD.format(E=mesh.n_elem, nr=nr, nt=nt, re=re, rs=args.re_seed),
+                "config": {"linear_tolerance": linear_tolerance(args), "workload": CYL_WORKLOAD.format(E=mesh.n_elem, nr=nr, nt=nt, re=re, rs=args.re_seed),
                            "n_dof": int(n), "n_elem": int(mesh.n_elem),
                            "value_definition": "learned + mixed form: J.v applications of the whole solve x DOF / "
                                                "timed step time",
@@ -874,8 +885,9 @@ def main():
     ap.add_argument("--krylov", default="fp32", choices=["fp64", "fp32"],
                     help="arithmetic of the J.v inside GMRES (Newton residual and Arnoldi stay FP64)")
     ap.add_argument("--forcing", default="last", choices=["fixed", "last"],
-                    help="vortex: linear tolerance of each Newton step, gmres_rtol throughout (fixed) or "
-                         "max(gmres_rtol, 1/2 newton_rtol ||R0|| / ||Rk||) (last; every form compared)")
+                    help="Newton-GMRES workloads (vortex, batch, cylinder): linear tolerance of each Newton "
+                         "step, gmres_rtol throughout (fixed) or max(gmres_rtol, 1/2 newton_rtol ||R0|| / ||Rk||) "
+                         "(last; every form compared)")
     ap.add_argument("--no-lagged-pc", action="store_true")
     ap.add_argument("--pc-reuse", type=int, default=1,
                     help="vortex: build the block-Jacobi blocks every K implicit steps (every form compared)")
@@ -938,7 +950,7 @@ def main():
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    forcing = 1 if args.forcing == "last" else 0
+    forcing = forcing_of(args)
     prob = vortex_problem(LDG, mesh, forcing, max(1, args.pc_reuse))
     g, u, times, tot, launches, t_end, train = run_mode(prob, kprec, pc, args.steps, args.warmup, flush, stream,
                                                         kernel_launches)
@@ -1052,8 +1064,7 @@ def main():
                            "precision": "FP64 throughout" if kprec == 0 else
                            "Krylov J.v and preconditioner in FP32 arithmetic; Newton residual, Arnoldi, Givens, "
                            "vectors FP64",
-                           "linear_tolerance": "max(1e-3, 0.5e-8 ||R0|| / ||Rk||) per Newton step k (every form)"
-                           if args.forcing == "last" else "1e-3 per Newton step",
+                           "linear_tolerance": linear_tolerance(args),
                            "l2": "flushed (256 MiB write) before each timed step, outside its event window",
                            "parallelism": f"{world} independent instance(s), one per GPU",
                            "fp64_bjacobi_baseline": base, "lagged_block_jacobi": lagged},
