@@ -45,3 +45,31 @@ def test_invalid_arguments_are_rejected_without_a_gpu(built_lib):
     assert L.ldg_residual(None, None, None) == -1
     L.ldg_destroy.argtypes = [ctypes.c_void_p]
     assert L.ldg_destroy(None) == 0
+
+
+def _struct_fields(name):
+    """Field names, in order, of `typedef struct { ... } name;` in include/ldg.h."""
+    src = open(os.path.join(ROOT, "include", "ldg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", src).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "type a, b" or "const double* mu": the names follow the type, separated by commas
+        head, *rest = decl.split(",")
+        fields.append(re.findall(r"[A-Za-z_][A-Za-z0-9_]*", head)[-1])
+        fields += [r.strip().lstrip("*").strip() for r in rest]
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("ldg_mesh_desc", "_Mesh"), ("ldg_model_desc", "_Model"),
+                                          ("ldg_options", "_Options"), ("ldg_solve_report", "SolveReport"),
+                                          ("ldg_train_opts", "TrainOpts"), ("ldg_train_report", "TrainReport")])
+def test_binding_structs_follow_the_header(cname, pyname):
+    """Every ctypes mirror in the binding has the header's fields in the header's order,
+    so an option added to the C struct cannot silently shift the ones after it."""
+    from paper_2205_07824_b300 import ldg
+    py = [f for f, _ in getattr(ldg, pyname)._fields_]
+    assert py == _struct_fields(cname)
