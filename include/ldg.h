@@ -145,11 +145,20 @@ typedef struct {
                            a call whose time-scheme coefficient a0/dt differs from the one
                            the blocks were built with rebuilds them. 0 or 1 (default): every
                            call */
+  int krylov_basis;     /* graph-driven solves: storage and arithmetic of the Gram-Schmidt
+                           sweeps. LDG_BASIS_FP64 (default): FP64 basis and FP64 FMAs.
+                           LDG_BASIS_F32X2: the basis and the vector being orthogonalised as
+                           (hi, lo) float pairs, about 48 significand bits (emulated FP64),
+                           with error-free products and compensated sums on the FP32 pipes;
+                           Hessenberg, Givens, Newton residual and solution stay FP64. The
+                           host-driven solves (learned preconditioner, ldg_gmres) always use
+                           FP64. */
 } ldg_options;
 
 enum { LDG_FP64 = 0, LDG_FP32 = 1 };
 enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1, LDG_PC_MLP = 2 };
 enum { LDG_FORCING_FIXED = 0, LDG_FORCING_LAST = 1 };
+enum { LDG_BASIS_FP64 = 0, LDG_BASIS_F32X2 = 1 };
 
 typedef struct {
   int newton_iters;

@@ -64,6 +64,8 @@ struct ldg_batch {
   int *d_skip_newt = nullptr, *d_skip_gm = nullptr, *d_skip_arn = nullptr;
   double *d_u = nullptr, *d_res = nullptr, *d_r = nullptr, *d_x = nullptr, *d_w = nullptr;
   double *d_vcur = nullptr, *d_zcur = nullptr, *d_V = nullptr, *d_Z = nullptr;
+  float2* d_wf = nullptr;          // pair basis: the vector being orthogonalised, as (hi, lo) floats
+  bool ff = false;                 // krylov_basis == LDG_BASIS_F32X2: V holds (hi, lo) float pairs
   bool pc = false;
   long long solves = 0;            // ldg_batch_solve calls (block-Jacobi reuse)
   bool borrowed = false;           // one instance whose context belongs to the caller
@@ -186,7 +188,10 @@ int emit_newton_tail(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle ha
 int emit_cycle_head(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle hc, int use) {
   const SegView sv = seg_view(b);
   kb_cycle_init<<<1, 256, 0, s>>>(b->d_ctl, sv, b->d_skip_gm, b->d_skip_arn, hc, use);
-  kb_cycle_start<<<b->nchunk, 256, 0, s>>>(sv, b->d_r, b->d_V, b->d_vcur, b->d_skip_gm);
+  if (b->ff)
+    kb_cycle_start_ff<<<b->nchunk, 256, 0, s>>>(sv, b->d_r, (float2*)b->d_V, b->d_vcur, b->d_skip_gm);
+  else
+    kb_cycle_start<<<b->nchunk, 256, 0, s>>>(sv, b->d_r, b->d_V, b->d_vcur, b->d_skip_gm);
   count_launch();
   count_launch();
   BK(cudaGetLastError());
@@ -198,7 +203,10 @@ int emit_cycle_tail(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle hb,
   int rc;
   const SegView sv = seg_view(b);
   kb_backsolve<<<(b->nseg + 127) / 128, 128, 0, s>>>(sv, b->d_skip_gm);
-  kb_solution_update<<<b->nchunk, 256, 0, s>>>(sv, b->pc ? b->d_Z : b->d_V, b->ntot, b->d_x, b->d_skip_gm);
+  if (b->ff && !b->pc)
+    kb_solution_update_ff<<<b->nchunk, 256, 0, s>>>(sv, (const float2*)b->d_V, b->ntot, b->d_x, b->d_skip_gm);
+  else
+    kb_solution_update<<<b->nchunk, 256, 0, s>>>(sv, b->pc ? b->d_Z : b->d_V, b->ntot, b->d_x, b->d_skip_gm);
   count_launch();
   count_launch();
   BK(cudaGetLastError());
@@ -227,6 +235,24 @@ int emit_arnoldi(ldg_batch* b, cudaStream_t s, cudaGraphConditionalHandle hc, in
   double* part2 = b->d_part + (size_t)b->nchunk * KB_LDP;
   double* part3 = b->d_part + (size_t)2 * b->nchunk * KB_LDP;
   KrySmall S{b->m};
+  if (b->ff) {
+    // the same two passes on the pair basis (emulated FP64 on the FP32 pipes)
+    float2* V2 = (float2*)b->d_V;
+    float2 *q1 = (float2*)part1, *q2 = (float2*)part2, *q3 = (float2*)part3;
+    kb_mdot_ff<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, V2, b->ntot, b->d_w, b->d_wf, q1,
+                                           b->pc ? b->d_zcur : nullptr, b->d_Z, b->d_skip_arn);
+    kb_update_ff<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, V2, b->ntot, q1, (int)S.h1(), b->d_wf, nullptr,
+                                             b->d_skip_arn);
+    kb_mdot_ff<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, V2, b->ntot, nullptr, b->d_wf, q2, nullptr, nullptr,
+                                           b->d_skip_arn);
+    kb_update_ff<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, V2, b->ntot, q2, (int)S.h2(), b->d_wf, q3, b->d_skip_arn);
+    kb_scale_ff<<<b->nseg + b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_wf, q3, V2, b->ntot, b->d_vcur,
+                                                      b->d_skip_arn);
+    kb_arnoldi_end<<<1, 256, 0, s>>>(b->d_ctl, b->d_skip_arn, b->nseg, hc, use);
+    for (int i = 0; i < 6; ++i) count_launch();
+    BK(cudaGetLastError());
+    return LDG_OK;
+  }
   kb_mdot<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, b->d_w, part1, b->pc ? b->d_zcur : nullptr,
                                       b->d_Z, b->d_skip_arn);
   kb_update<<<b->nchunk, KRY_T, 0, s>>>(sv, b->d_ctl, b->d_V, b->ntot, part1, (int)S.h1(), b->d_w, nullptr, nullptr,
@@ -388,7 +414,7 @@ void free_batch(ldg_batch* b) {
                   (void*)b->d_sflags, (void*)b->d_st, (void*)b->d_ctl, (void*)b->d_skip_newt, (void*)b->d_skip_gm,
                   (void*)b->d_skip_arn, (void*)b->d_u, (void*)b->d_res, (void*)b->d_r, (void*)b->d_x, (void*)b->d_w,
                   (void*)b->d_vcur, (void*)b->d_zcur, (void*)b->d_V, (void*)b->d_Z, (void*)b->d_bt,
-                  (void*)b->d_ubase})
+                  (void*)b->d_ubase, (void*)b->d_wf})
     cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
@@ -417,6 +443,7 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
   if (o.precond != LDG_PC_BJACOBI) o.precond = LDG_PC_NONE;
   if (o.newton_forcing != LDG_FORCING_LAST) o.newton_forcing = LDG_FORCING_FIXED;
   if (o.pc_reuse < 1) o.pc_reuse = 1;
+  if (o.krylov_basis != LDG_BASIS_F32X2) o.krylov_basis = LDG_BASIS_FP64;
   b->opt = o;
   b->m = o.gmres_m;
   b->pc = o.precond == LDG_PC_BJACOBI;
@@ -568,8 +595,10 @@ int finish_build(ldg_batch* b, const std::vector<int64_t>& seg_off, const std::v
     BK(cudaMalloc(q, nb));
     BK(cudaMemset(*q, 0, nb));
   }
-  BK(cudaMalloc(&b->d_V, (size_t)(b->m + 1) * nb));
+  BK(cudaMalloc(&b->d_V, (size_t)(b->m + 1) * nb));   // FP64 vectors, or float pairs of the same size
   if (b->pc) BK(cudaMalloc(&b->d_Z, (size_t)b->m * nb));
+  b->ff = o.krylov_basis == LDG_BASIS_F32X2;
+  if (b->ff) BK(cudaMalloc(&b->d_wf, (size_t)b->ntot * sizeof(float2)));
   BK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   return LDG_OK;
 }

@@ -337,6 +337,284 @@ __global__ void __launch_bounds__(KRY_T) kb_scale(SegView sv, const BatchCtl* ct
   }
 }
 
+// ------------------------------------------------ double-FP32 Krylov basis
+// With ldg_options::krylov_basis = LDG_BASIS_F32X2 the Arnoldi basis V and the vector
+// being orthogonalised are held as pairs of floats, value = hi + lo, and the
+// Gram-Schmidt sweeps run on the FP32 pipes. A pair carries about 48 significand bits
+// (emulated FP64). Building blocks, from the published error-free transformations:
+// Knuth's TwoSum, the FMA form of Dekker's exact product, Dekker's pair addition, and
+// the compensated dot product of Ogita, Rump and Oishi (2005).
+struct f32x2 {
+  float hi, lo;
+};
+
+// a + b = s + e exactly (Knuth)
+__device__ __forceinline__ f32x2 ff_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+// a + b = s + e exactly when |a| >= |b| or a = 0
+__device__ __forceinline__ f32x2 ff_quick_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ f32x2 ff_normalise(f32x2 a) { return ff_quick_two_sum(a.hi, a.lo); }
+__device__ __forceinline__ f32x2 ff_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - (double)hi)};
+}
+__device__ __forceinline__ double ff_to_double(f32x2 a) { return (double)a.hi + (double)a.lo; }
+// a * b as an unnormalised pair: the exact product of the leading parts (p + e, e from
+// one FMA) plus the two cross terms; the lo * lo term is below the pair's precision
+__device__ __forceinline__ f32x2 ff_prod(f32x2 a, f32x2 b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);
+  return {p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e))};
+}
+// compensated accumulation s += t: the leading parts by TwoSum, every error term into
+// s.lo (normalise once at the end)
+__device__ __forceinline__ void ff_accumulate(f32x2& s, f32x2 t) {
+  const f32x2 u = ff_two_sum(s.hi, t.hi);
+  s.hi = u.hi;
+  s.lo += u.lo + t.lo;
+}
+// the sum of two normalised pairs, normalised (Dekker's addition with both error terms)
+__device__ __forceinline__ f32x2 ff_add(f32x2 a, f32x2 b) {
+  f32x2 s = ff_two_sum(a.hi, b.hi);
+  const f32x2 t = ff_two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = ff_quick_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return ff_quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ f32x2 ff_load(const float2* p, int64_t i) {
+  const float2 v = p[i];
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void ff_store(float2* p, int64_t i, f32x2 a) { p[i] = make_float2(a.hi, a.lo); }
+__device__ __forceinline__ f32x2 ff_warp_sum(f32x2 a) {
+  a = ff_normalise(a);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const f32x2 b = {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+    a = ff_add(a, b);
+  }
+  return a;
+}
+
+// out[k] (shared memory) = sum over the chunks of segment s of the pair partials
+// part[c][k], in chunk order with a fixed-shape tree (every CTA gets the same bits)
+__device__ __forceinline__ void seg_sum_ff(const SegView& sv, const float2* part, int s, int nvec, f32x2* out) {
+  __shared__ f32x2 gred[KRY_T];
+  int kw = 1;
+  while (kw < nvec) kw <<= 1;
+  const int groups = KRY_T / kw;
+  const int k = threadIdx.x % kw, grp = threadIdx.x / kw;
+  const int c0 = sv.seg_c0[s], nc = sv.seg_nc[s];
+  f32x2 t = {0.f, 0.f};
+  if (k < nvec)
+    for (int b = grp; b < nc; b += groups) t = ff_add(t, ff_load(part, (int64_t)(c0 + b) * KB_LDP + k));
+  gred[threadIdx.x] = t;
+  __syncthreads();
+  for (int st = groups >> 1; st > 0; st >>= 1) {
+    if (grp < st) gred[threadIdx.x] = ff_add(gred[threadIdx.x], gred[threadIdx.x + st * kw]);
+    __syncthreads();
+  }
+  if ((int)threadIdx.x < nvec) out[threadIdx.x] = gred[threadIdx.x];
+  __syncthreads();
+}
+
+// kb_mdot on the pair basis: part[c][k] = V[k] . w over chunk c, k <= j, as pairs. With
+// wsrc (the first pass), the chunk of the FP64 vector w is split into pairs and also
+// stored to wf for the kernels after it; otherwise w is read from wf. zsrc/Z as kb_mdot.
+__global__ void __launch_bounds__(KRY_T) kb_mdot_ff(SegView sv, const BatchCtl* ctl, const float2* __restrict__ V,
+                                                   int64_t ldv, const double* __restrict__ wsrc,
+                                                   float2* __restrict__ wf, float2* __restrict__ part,
+                                                   const double* __restrict__ zsrc, double* __restrict__ Z,
+                                                   const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  __shared__ f32x2 ws[KB_CHUNK];
+  __shared__ f32x2 red[KB_NV][KB_CHUNK / KB_RB];
+  const int j = ctl->j, nvec = j + 1;
+  const int64_t lo = sv.chunk_lo[c];
+  const int len = (int)(sv.chunk_hi[c] - lo);
+  for (int t = threadIdx.x; t < len; t += KRY_T) {
+    if (wsrc) {
+      ws[t] = ff_from_double(wsrc[lo + t]);
+      ff_store(wf, lo + t, ws[t]);
+    } else {
+      ws[t] = ff_load(wf, lo + t);
+    }
+    if (zsrc) Z[j * ldv + lo + t] = zsrc[lo + t];
+  }
+  __syncthreads();
+  const int nb = (len + KB_RB - 1) / KB_RB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int u = warp; u < nvec * nb; u += KRY_T / 32) {
+    const int k = u / nb, b = u - k * nb;
+    const int r0 = b * KB_RB + lane;
+    const float2* col = V + k * ldv + lo;
+    // four independent compensated accumulators per lane (the chains are latency-bound)
+    f32x2 acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int t = 0; t < KB_RB / 32; ++t) {
+      const int r = r0 + 32 * t;
+      if (r < len) ff_accumulate(acc[t & 3], ff_prod(ff_load(col, r), ws[r]));
+    }
+    f32x2 a = ff_add(ff_add(ff_normalise(acc[0]), ff_normalise(acc[1])),
+                     ff_add(ff_normalise(acc[2]), ff_normalise(acc[3])));
+    a = ff_warp_sum(a);
+    if (lane == 0) red[k][b] = a;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nvec) {
+    f32x2 t = {0.f, 0.f};
+    for (int b = 0; b < nb; ++b) t = ff_add(t, red[threadIdx.x][b]);
+    ff_store(part, (int64_t)c * KB_LDP + threadIdx.x, t);
+  }
+}
+
+// kb_update on the pair basis: h_s = sum of the pair partials (kept at small_s + h_off in
+// FP64 by the instance's first chunk), then wf_s -= V[0..j]_s h_s; with part_norm, the
+// chunk's share of ||w_new||^2 goes to part_norm[c][0].
+__global__ void __launch_bounds__(KRY_T) kb_update_ff(SegView sv, const BatchCtl* ctl, const float2* __restrict__ V,
+                                                     int64_t ldv, const float2* __restrict__ part_in, int h_off,
+                                                     float2* __restrict__ wf, float2* __restrict__ part_norm,
+                                                     const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  const int j = ctl->j, nvec = j + 1;
+  __shared__ f32x2 hs[KB_NV];
+  seg_sum_ff(sv, part_in, s, nvec, hs);
+  if (c == sv.seg_c0[s] && (int)threadIdx.x < nvec)
+    sv.small[(size_t)s * sv.ks + h_off + threadIdx.x] = ff_to_double(hs[threadIdx.x]);
+  const int64_t lo = sv.chunk_lo[c], hi = sv.chunk_hi[c];
+  f32x2 nacc = {0.f, 0.f};
+  for (int64_t base = lo + threadIdx.x; base < hi; base += 4 * KRY_T) {
+    // per row two independent compensated accumulators, over the even and the odd
+    // columns (the chains are latency-bound), added at the end
+    f32x2 t[4], t2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = base + q * KRY_T;
+      t[q] = i < hi ? ff_load(wf, i) : f32x2{0.f, 0.f};
+      t2[q] = f32x2{0.f, 0.f};
+    }
+#pragma unroll 2
+    for (int k = 0; k < nvec; k += 2) {
+      const bool two = k + 1 < nvec;
+      const f32x2 hk = hs[k], hk1 = two ? hs[k + 1] : f32x2{0.f, 0.f};
+      const float2* col = V + k * ldv;
+      const float2* col1 = col + ldv;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t i = base + q * KRY_T;
+        if (i < hi) {
+          const f32x2 p = ff_prod(ff_load(col, i), hk);
+          ff_accumulate(t[q], f32x2{-p.hi, -p.lo});
+          if (two) {
+            const f32x2 p1 = ff_prod(ff_load(col1, i), hk1);
+            ff_accumulate(t2[q], f32x2{-p1.hi, -p1.lo});
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = base + q * KRY_T;
+      if (i < hi) {
+        t[q] = ff_add(ff_normalise(t[q]), ff_normalise(t2[q]));
+        ff_store(wf, i, t[q]);
+        if (part_norm) ff_accumulate(nacc, ff_prod(t[q], t[q]));
+      }
+    }
+  }
+  if (part_norm) {
+    __shared__ f32x2 red[KRY_T / 32];
+    const f32x2 v = ff_warp_sum(nacc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      f32x2 t = {0.f, 0.f};
+      for (int q = 0; q < KRY_T / 32; ++q) t = ff_add(t, red[q]);
+      ff_store(part_norm, (int64_t)c * KB_LDP, t);
+    }
+  }
+}
+
+// kb_scale on the pair basis: ||w_s||^2 from the pair partials; V[j+1]_s = w_s / ||w_s||
+// as pairs and vcur_s = the same in FP64 for the preconditioner and J.v. CTAs
+// 0 .. nseg-1 complete the Arnoldi column and its Givens rotation as in kb_scale.
+__global__ void __launch_bounds__(KRY_T) kb_scale_ff(SegView sv, const BatchCtl* ctl, const float2* __restrict__ wf,
+                                                    const float2* __restrict__ part_norm, float2* __restrict__ V,
+                                                    int64_t ldv, double* __restrict__ vcur, int* skip) {
+  const int b = blockIdx.x;
+  const bool givens = b < sv.nseg;
+  const int c = givens ? -1 : b - sv.nseg;
+  const int s = givens ? b : sv.chunk_seg[c];
+  if (skip[s]) return;
+  __shared__ f32x2 nrm_s[1];
+  seg_sum_ff(sv, part_norm, s, 1, nrm_s);
+  const double nrm2 = ff_to_double(nrm_s[0]);
+  const int j = ctl->j;
+  if (givens) {
+    const int done = arnoldi_column_block(sv.small + (size_t)s * sv.ks, sv.m, j, nrm2, sv.sflags + 4 * s);
+    if (threadIdx.x == 0 && done) skip[s] = 1;
+    return;
+  }
+  __shared__ f32x2 f_s;
+  if (threadIdx.x == 0) {
+    const double nr = sqrt(nrm2);
+    f_s = ff_from_double(nr > 0.0 ? 1.0 / nr : 0.0);
+  }
+  __syncthreads();
+  const f32x2 f = f_s;
+  float2* out = V + (size_t)(j + 1) * ldv;
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += KRY_T) {
+    const f32x2 t = ff_normalise(ff_prod(ff_load(wf, i), f));
+    ff_store(out, i, t);
+    vcur[i] = ff_to_double(t);
+  }
+}
+
+// Cycle start on the pair basis: V[0]_s = r_s / ||r_s|| as pairs, vcur_s in FP64.
+__global__ void kb_cycle_start_ff(SegView sv, const double* __restrict__ r, float2* __restrict__ V0,
+                                  double* __restrict__ vcur, const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  KrySmall S{sv.m};
+  __shared__ double f_s;
+  if (threadIdx.x == 0) {
+    const double nr = sqrt(sv.small[(size_t)s * sv.ks + S.sc() + 4]);
+    f_s = nr > 0.0 ? 1.0 / nr : 0.0;
+  }
+  __syncthreads();
+  const double f = f_s;
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) {
+    const f32x2 t = ff_from_double(r[i] * f);
+    ff_store(V0, i, t);
+    vcur[i] = ff_to_double(t);
+  }
+}
+
+// x_s += sum_{l < k_s} V[l]_s y_s[l] with the pair basis (no preconditioner)
+__global__ void kb_solution_update_ff(SegView sv, const float2* __restrict__ V, int64_t ldv, double* __restrict__ x,
+                                      const int* skip) {
+  const int c = blockIdx.x, s = sv.chunk_seg[c];
+  if (skip[s]) return;
+  __shared__ double ys[KB_NV];
+  KrySmall S{sv.m};
+  const int k = sv.sflags[4 * s + 1];
+  if ((int)threadIdx.x < k) ys[threadIdx.x] = sv.small[(size_t)s * sv.ks + S.y() + threadIdx.x];
+  __syncthreads();
+  for (int64_t i = sv.chunk_lo[c] + threadIdx.x; i < sv.chunk_hi[c]; i += blockDim.x) {
+    double t = x[i];
+    for (int l = 0; l < k; ++l) t = fma(ff_to_double(ff_load(V, l * ldv + i)), ys[l], t);
+    x[i] = t;
+  }
+}
+
 // Cycle start: V[0]_s = vcur_s = r_s / ||r_s|| (||r_s||^2 in sc[4]).
 __global__ void kb_cycle_start(SegView sv, const double* __restrict__ r, double* __restrict__ V0,
                                double* __restrict__ vcur, const int* skip) {

@@ -1056,6 +1056,7 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if (o.pc_refresh < 0) o.pc_refresh = 0;
   if (o.newton_forcing != LDG_FORCING_LAST) o.newton_forcing = LDG_FORCING_FIXED;
   if (o.pc_reuse < 1) o.pc_reuse = 1;
+  if (o.krylov_basis != LDG_BASIS_F32X2) o.krylov_basis = LDG_BASIS_FP64;
   ctx->opt = o;
   ctx->p = p; ctx->nq = o.nq1;
   ctx->mp = make_params(model);

@@ -24,6 +24,7 @@ DIRK11, DIRK22, DIRK33, DIRK34 = 1, 2, 3, 4
 FP64, FP32 = 0, 1
 PC_NONE, PC_BJACOBI, PC_MLP = 0, 1, 2
 FORCING_FIXED, FORCING_LAST = 0, 1
+BASIS_FP64, BASIS_F32X2 = 0, 1
 STATUS = {0: "LDG_OK", -1: "LDG_ERR_ARG", -2: "LDG_ERR_CUDA", -3: "LDG_ERR_UNSUPPORTED",
           -4: "LDG_ERR_NONFINITE", -5: "LDG_ERR_MAXIT", -6: "LDG_ERR_MESH"}
 
@@ -70,7 +71,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("nq1", ctypes.c_int), ("gmres_m", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("max_newton", ctypes.c_int), ("newton_rtol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
                 ("krylov_precision", ctypes.c_int), ("precond", ctypes.c_int), ("pc_refresh", ctypes.c_int),
-                ("newton_forcing", ctypes.c_int), ("pc_reuse", ctypes.c_int)]
+                ("newton_forcing", ctypes.c_int), ("pc_reuse", ctypes.c_int), ("krylov_basis", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -183,7 +184,7 @@ class LDG:
     def __init__(self, mesh, p: int, model: int, case: int, mu=(), nq1: int = 0, gmres_m: int = 30,
                  max_restarts: int = 50, max_newton: int = 20, newton_rtol: float = 1e-8,
                  gmres_rtol: float = 1e-3, krylov_precision: int = 0, precond: int = 0, pc_refresh: int = 0,
-                 newton_forcing: int = 0, pc_reuse: int = 1, stream=None):
+                 newton_forcing: int = 0, pc_reuse: int = 1, krylov_basis: int = 0, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("LDG needs a CUDA device (no CPU fallback)")
@@ -196,7 +197,7 @@ class LDG:
         mo = _Model(model, case, len(self._mu),
                     self._mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(self._mu) else None)
         op = _Options(nq1, gmres_m, max_restarts, max_newton, newton_rtol, gmres_rtol, krylov_precision, precond,
-                      pc_refresh, newton_forcing, pc_reuse)
+                      pc_refresh, newton_forcing, pc_reuse, krylov_basis)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -419,7 +420,7 @@ class Batch:
     def __init__(self, meshes, ps, model: int, cases, mus, nq1: int = 0, gmres_m: int = 30,
                  max_restarts: int = 50, max_newton: int = 20, newton_rtol: float = 1e-8,
                  gmres_rtol: float = 1e-3, krylov_precision: int = 0, precond: int = 0, newton_forcing: int = 0,
-                 pc_reuse: int = 1, stream=None):
+                 pc_reuse: int = 1, krylov_basis: int = 0, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Batch needs a CUDA device (no CPU fallback)")
@@ -440,7 +441,7 @@ class Batch:
                            mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(mu) else None)
         pa = (ctypes.c_int * n)(*[int(p) for p in ps])
         op = _Options(nq1, gmres_m, max_restarts, max_newton, newton_rtol, gmres_rtol, krylov_precision, precond, 0,
-                      newton_forcing, pc_reuse)
+                      newton_forcing, pc_reuse, krylov_basis)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

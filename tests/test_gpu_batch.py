@@ -212,3 +212,28 @@ def test_batch_bdf2_euler_matches_single_context():
                 assert np.linalg.norm(got - ref) <= 1e-7 * np.linalg.norm(ref), (n_inst, k, i)
                 assert reps[i]["status"] == 0 and reps[i]["rfinal"] <= 1e-8 * reps[i]["r0"]
                 assert reps[i]["newton_iters"] == rep["newton_iters"]
+
+
+@pytest.mark.parametrize("pc", [0, 1])
+def test_pair_basis_batch_matches_fp64_basis(pc):
+    """krylov_basis = F32X2 (Gram-Schmidt on (hi, lo) float pairs, emulated FP64) on the
+    mixed batch: graph and host-driven loops give the same bits, every instance meets the
+    Newton tolerance against the oracle, and the solutions agree with the FP64-basis solve
+    to the solve tolerance with about the same GMRES iterations."""
+    from paper_2205_07824_b300.ldg import BASIS_F32X2
+    spec = _instances()
+    b64 = _batch(spec, precond=pc, gmres_m=20, newton_rtol=1e-8, gmres_rtol=1e-3)
+    u64 = cuda(np.zeros(b64.n_total))
+    reps64, _ = b64.solve(u64)
+    bff = _batch(spec, precond=pc, gmres_m=20, newton_rtol=1e-8, gmres_rtol=1e-3, krylov_basis=BASIS_F32X2)
+    ue = cuda(np.zeros(bff.n_total))
+    reps_e, _ = bff.solve(ue, use_graph=False)
+    ug = cuda(np.zeros(bff.n_total))
+    reps_g, _ = bff.solve(ug)
+    assert np.array_equal(host(ue), host(ug))
+    _check_solution(bff, spec, host(ug), reps_g, 1e-8)
+    a, c = host(u64), host(ug)
+    for i in range(len(spec)):
+        sl = slice(bff.offsets[i], bff.offsets[i] + bff.n_dof[i])
+        assert np.linalg.norm(a[sl] - c[sl]) <= 1e-6 * np.linalg.norm(a[sl])
+        assert abs(reps_g[i]["gmres_iters"] - reps64[i]["gmres_iters"]) <= max(2, reps64[i]["gmres_iters"] // 10)

@@ -257,6 +257,34 @@ def test_block_jacobi_reuse_over_time_steps():
         assert np.linalg.norm(a - b) <= 1e-7 * np.linalg.norm(a)
 
 
+@pytest.mark.parametrize("kprec,pc", [(0, 0), (1, 1)])
+def test_pair_basis_vortex_step(kprec, pc):
+    """The BDF2 vortex step with the Gram-Schmidt sweeps on (hi, lo) float pairs reaches
+    the Newton tolerance, agrees with the oracle's tight solve like the FP64-basis solve,
+    and needs about the same GMRES iterations."""
+    from paper_2205_07824_b300.ldg import BASIS_FP64, BASIS_F32X2
+    mesh = synth.quad_box(16, hi=(10.0, 10.0), periodic=(True, True))
+    dt = 0.05
+    reps, sols = {}, {}
+    for basis in (BASIS_FP64, BASIS_F32X2):
+        o, g = pair(mesh, 3, oracle.EULER, oracle.CASE_VORTEX, newton_rtol=1e-8, gmres_rtol=1e-3,
+                    krylov_precision=kprec, precond=pc, krylov_basis=basis)
+        un, unm1 = o.interpolate(0.0), o.interpolate(-dt)
+        g.set_time(2, dt, dt, cuda(un), cuda(unm1))
+        u = cuda(un)
+        reps[basis] = g.newton_gmres(u)
+        sols[basis] = host(u)
+    o.set_time(2, dt, dt, un, unm1)
+    uo, rc, st = o.newton(un.copy(), m=30, newton_rtol=1e-10, gmres_rtol=1e-6)
+    assert rc == 0
+    print({b: (r["newton_iters"], r["gmres_iters"]) for b, r in reps.items()})
+    for basis, rep in reps.items():
+        assert rep["rfinal"] <= 1e-8 * rep["r0"]
+        assert np.linalg.norm(sols[basis] - uo) <= 1e-7 * np.linalg.norm(uo)
+    n64, nff = reps[BASIS_FP64]["gmres_iters"], reps[BASIS_F32X2]["gmres_iters"]
+    assert abs(nff - n64) <= max(2, n64 // 10)
+
+
 @pytest.mark.parametrize("model", [oracle.EULER, oracle.NS, oracle.CONVDIFF])
 def test_finite_difference_jvp(model):
     """The FD variant against the exact J.v: the forward difference is off by O(eps),
