@@ -285,6 +285,23 @@ def test_pair_basis_vortex_step(kprec, pc):
     assert abs(nff - n64) <= max(2, n64 // 10)
 
 
+def test_host_buffer_solve_equals_device_solve():
+    """ldg_newton_gmres_host (state in host memory, copied in and out by the library)
+    gives the bits and the report of ldg_newton_gmres on a device buffer."""
+    mesh = synth.quad_box(8, hi=(10.0, 10.0), periodic=(True, True))
+    dt = 0.05
+    o, g = pair(mesh, 3, oracle.EULER, oracle.CASE_VORTEX, newton_rtol=1e-8, gmres_rtol=1e-3,
+                krylov_precision=1, precond=1)
+    un, unm1 = o.interpolate(0.0), o.interpolate(-dt)
+    g.set_time(2, dt, dt, cuda(un), cuda(unm1))
+    ud = cuda(un)
+    rd = g.newton_gmres(ud)
+    uh = np.ascontiguousarray(un.copy())
+    rh = g.newton_gmres_host(uh)
+    assert np.array_equal(uh, host(ud))
+    assert (rh["newton_iters"], rh["gmres_iters"], rh["status"]) == (rd["newton_iters"], rd["gmres_iters"], 0)
+
+
 @pytest.mark.parametrize("model", [oracle.EULER, oracle.NS, oracle.CONVDIFF])
 def test_finite_difference_jvp(model):
     """The FD variant against the exact J.v: the forward difference is off by O(eps),
