@@ -237,3 +237,32 @@ def test_pair_basis_batch_matches_fp64_basis(pc):
         sl = slice(bff.offsets[i], bff.offsets[i] + bff.n_dof[i])
         assert np.linalg.norm(a[sl] - c[sl]) <= 1e-6 * np.linalg.norm(a[sl])
         assert abs(reps_g[i]["gmres_iters"] - reps64[i]["gmres_iters"]) <= max(2, reps64[i]["gmres_iters"] // 10)
+
+
+def test_batch_forcing_last_step_per_instance():
+    """newton_forcing = LAST on the mixed batch: each instance's linear tolerance follows
+    its own ||R0|| / ||Rk||, every instance still meets the Newton tolerance against the
+    oracle, and no instance needs more GMRES iterations than with the fixed forcing term."""
+    from paper_2205_07824_b300.ldg import FORCING_LAST
+    spec = _instances()
+    reps = {}
+    for forcing in (0, FORCING_LAST):
+        b = _batch(spec, precond=1, gmres_m=20, newton_rtol=1e-8, gmres_rtol=1e-3, newton_forcing=forcing)
+        u = cuda(np.zeros(b.n_total))
+        reps[forcing], _ = b.solve(u)
+        _check_solution(b, spec, host(u), reps[forcing], 1e-8)
+    assert sum(r["gmres_iters"] for r in reps[FORCING_LAST]) <= sum(r["gmres_iters"] for r in reps[0])
+
+
+def test_batch_block_jacobi_reuse_across_solves():
+    """pc_reuse = 2 on the mixed batch: the blocks are built by the first of two solve calls
+    and reused by the second (pc_setups 1 then 0), which still converges."""
+    spec = _instances()
+    b = _batch(spec, precond=1, gmres_m=20, newton_rtol=1e-8, gmres_rtol=1e-3, pc_reuse=2)
+    setups = []
+    for _ in range(3):
+        u = cuda(np.zeros(b.n_total))
+        reps, _ = b.solve(u)
+        setups.append(reps[0]["pc_setups"])
+        _check_solution(b, spec, host(u), reps, 1e-8)
+    assert setups == [1, 0, 1]
