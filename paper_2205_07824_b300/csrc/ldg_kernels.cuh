@@ -700,15 +700,19 @@ template <class EL, class MD, int MODE, class R, class TL> struct RLayout {
   static constexpr int SMEM = NE * PER_ELEM;
 };
 
-// Minimum resident CTAs per SM asked of the register allocator: 3 for the FP32
-// dual-number J.v of the Navier-Stokes model (whose register count otherwise leaves
-// two 256-thread CTAs per SM), 1 otherwise.
-template <class MD, int MODE, class R> struct ResMinBlocks {
-  static constexpr int value = (MD::KIND == M_NS && MODE == MODE_JV && sizeof(R) == 4) ? 3 : 1;
+// Minimum resident CTAs per SM asked of the register allocator. For the FP32
+// dual-number J.v of the Navier-Stokes model, whose register count otherwise leaves two
+// 256-thread CTAs per SM: as many as the tile's shared-memory budget lets reside, at
+// most 4 (64 registers; measured 9% faster than 3 on the 40,000-element cylinder, with
+// about 100 bytes of spills per thread). 1 otherwise.
+template <class MD, int MODE, class R, class TL> struct ResMinBlocks {
+  static constexpr int BY_SMEM = (228 * 1024) / (TL::BUDGET_R + 1024);
+  static constexpr int value =
+      (MD::KIND == M_NS && MODE == MODE_JV && sizeof(R) == 4) ? (BY_SMEM < 1 ? 1 : (BY_SMEM > 4 ? 4 : BY_SMEM)) : 1;
 };
 
 template <class EL, class MD, int MODE, class R, class TL>
-__global__ void __launch_bounds__(256, ResMinBlocks<MD, MODE, R>::value) k_residual(KArgs a) {
+__global__ void __launch_bounds__(256, ResMinBlocks<MD, MODE, R, TL>::value) k_residual(KArgs a) {
   typedef RLayout<EL, MD, MODE, R, TL> L;
   typedef typename L::S S;
   constexpr int DIM = EL::DIM, NCU = MD::NCU, NF = EL::NF, NPE = EL::NPE, NFN = EL::NFN, NFQ = EL::NFQ, NQV = EL::NQV;
