@@ -1010,8 +1010,13 @@ def main():
     fpe = JV_FLOP_PER_ELEM[kprec]
     achieved = fpe * mesh.n_elem / (jv_ms * 1e-3) / 1e12
     peak = FP32_PEAK_TFLOPS if kprec else FP64_PEAK_TFLOPS
+    # DRAM bytes per launch of the FP32 kernel (tile 8) from one ncu capture inside the step
+    # (profiles/ncu_c2_euler_jv_fp32_p3.md): the state is L2-resident
+    traffic = (1.792e3 + 1.024e3) if kprec else None
     roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                "traffic": None,
+                "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (Tile<8>) inside "
+                                  "the step; the 6.3 MB of state per launch come from L2" if kprec else None,
                 "kernel": (f"k_residual<TensorEl<2,3,5>, EulerModel, MODE_JV, {'float' if kprec else 'double'}, "
                            f"Tile{g.get_tile()[0]}>"),
                 "timing": "CUDA graph of jv_reps back-to-back J.v launches, one replay timed with CUDA events",
