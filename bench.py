@@ -497,16 +497,39 @@ HEX_WORKLOAD = ("3D steady convection-diffusion on [0,1]^3, 48^3 affine hexahedr
 # Algorithmic HBM bytes per DOF of the 3-D linear J.v: v read twice (8 + 8), q(v) written
 # and read (2 x 24), J.v written (8).
 HEX_JV_BYTES_PER_DOF = 72.0
+TRI_WORKLOAD = ("2D steady convection-diffusion on [0,1]^2, 256 x 256 squares split into 131,072 affine "
+                "triangles, beta = (1, 0.5), kappa = 1e-2, manufactured u = exp(x+y) sin(pi xy); equispaced nodes, "
+                "p + 2 collapsed Gauss points per direction; J.v throughput sweep p = 1..6 in FP64 and FP32 "
+                "arithmetic (FP64 storage)")
+# Algorithmic HBM bytes per DOF of the 2-D linear J.v: v read twice (8 + 8), q(v) written
+# and read (2 x 16), J.v written (8).
+TRI_JV_BYTES_PER_DOF = 56.0
 
 
 def run_hex(args):
     """J.v throughput of the 3-D convection-diffusion operator, p = 1..6 (p = 4 is the headline)."""
-    import torch
     from paper_2205_07824_b300 import synth
+    jv_sweep(args, lambda: synth.hex_box(48), (1e-2, 1.0, 1.0, 0.5, 0.25), 4, HEX_JV_BYTES_PER_DOF, HEX_WORKLOAD,
+             "k_qstage + k_residual (MODE_HOM, float), hex p = 4")
+
+
+def run_tri(args):
+    """J.v throughput of the 2-D convection-diffusion operator on triangles, p = 1..6
+    (p = 6 is the headline)."""
+    from paper_2205_07824_b300 import synth
+    jv_sweep(args, lambda: synth.tri_square(256), (1e-2, 1.0, 1.0, 0.5), 6, TRI_JV_BYTES_PER_DOF, TRI_WORKLOAD,
+             "k_qstage + k_residual (MODE_HOM, float), triangles p = 6")
+
+
+def jv_sweep(args, make_mesh, mu, head_p, bytes_per_dof, workload, kernel_label):
+    """Median J.v time (L2 flushed before each) of the linear convection-diffusion operator
+    on one mesh for p = 1..6 in FP64 and FP32 arithmetic; the FP32 p = head_p row is the
+    headline."""
+    import torch
     from paper_2205_07824_b300.ldg import LDG, CONVDIFF, CASE_EXPSIN, kernel_launches
     world, rank, local = _dist()
     torch.cuda.set_device(local)
-    mesh = synth.hex_box(48)
+    mesh = make_mesh()
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     peaks = {}
@@ -524,7 +547,7 @@ def run_hex(args):
     for p in range(1, 7):
         row = {"p": p}
         for prec in (0, 1):
-            g = LDG(mesh, p, CONVDIFF, CASE_EXPSIN, (1e-2, 1.0, 1.0, 0.5, 0.25), krylov_precision=prec)
+            g = LDG(mesh, p, CONVDIFF, CASE_EXPSIN, mu, krylov_precision=prec)
             tile, _ = g.autotune()
             u = g.interpolate(0.0)
             v = torch.randn(g.n_dof, dtype=torch.float64, device="cuda",
@@ -544,9 +567,9 @@ def run_hex(args):
             ms = sorted(times)[len(times) // 2]
             key = "fp64" if prec == 0 else "fp32"
             row[key] = {"ms": ms, "gdofs": g.n_dof / (ms * 1e-3) / 1e9, "tile": tile,
-                        "hbm_frac": HEX_JV_BYTES_PER_DOF * g.n_dof / (ms * 1e-3) / 1e9 / hbm}
+                        "hbm_frac": bytes_per_dof * g.n_dof / (ms * 1e-3) / 1e9 / hbm}
             row["n_dof"] = g.n_dof
-            if p == 4 and prec == 1:
+            if p == head_p and prec == 1:
                 head = (g.n_dof, ms, tile)
             del g, u, v, out
             torch.cuda.empty_cache()
@@ -554,16 +577,17 @@ def run_hex(args):
     launches = kernel_launches() - l0
     clk = clocks.stop()
     n, ms, tile = head
-    achieved = HEX_JV_BYTES_PER_DOF * n / (ms * 1e-3) / 1e9
+    achieved = bytes_per_dof * n / (ms * 1e-3) / 1e9
     line = {"metric": METRIC, "value": n / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": HEX_WORKLOAD, "n_dof_p4": n, "step": "one J.v application (median of the timed ones)",
-                       "headline": "p = 4, FP32 arithmetic", "sweep": sweep,
+            "config": {"workload": workload, f"n_dof_p{head_p}": n,
+                       "step": "one J.v application (median of the timed ones)",
+                       "headline": f"p = {head_p}, FP32 arithmetic", "sweep": sweep,
                        "l2": "flushed (256 MiB write) before each timed J.v"},
             "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": hbm, "frac": achieved / hbm,
-                         "traffic": None, "bytes_per_dof": HEX_JV_BYTES_PER_DOF,
-                         "kernel": "k_qstage + k_residual (MODE_HOM, float), hex p = 4",
+                         "traffic": None, "bytes_per_dof": bytes_per_dof,
+                         "kernel": kernel_label,
                          "peak_source": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"},
             "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -895,9 +919,10 @@ def main():
     ap.add_argument("--host-loops", action="store_true",
                     help="run the solver's Newton / restart / Arnoldi loops from the host instead of the CUDA "
                          "graph's WHILE nodes (same kernels; for profilers that do not follow graph nodes)")
-    ap.add_argument("--workload", default="vortex", choices=["vortex", "batch", "hex", "cylinder", "tet"],
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "batch", "hex", "tri", "cylinder", "tet"],
                     help="vortex: the 64x64 p=3 Euler BDF2 step; batch: 256 parametrised convection-diffusion "
                          "solves in one graph launch; hex: the 48^3 convection-diffusion J.v sweep p=1..6; "
+                         "tri: the same sweep on 131,072 triangles; "
                          "cylinder: Navier-Stokes past a cylinder on 40,000 curved quads, learned + mixed vs "
                          "plain FP64 block-Jacobi; tet: Table 3's Poisson problem on tetrahedra, 1/n = 32, p = 3")
     ap.add_argument("--tet-n", type=int, default=32, help="tet: cubes per side (Table 3's 1/n)")
@@ -920,6 +945,9 @@ def main():
         return
     if args.workload == "hex":
         run_hex(args)
+        return
+    if args.workload == "tri":
+        run_tri(args)
         return
     if args.workload == "cylinder":
         if args.cyl_sweep > 1:

@@ -23,7 +23,7 @@ def _run_r_jv(mesh, p, model, case, seed=1):
     return o, g
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("model,case", [(oracle.POISSON, oracle.CASE_SINSIN), (oracle.CONVDIFF, oracle.CASE_EXPSIN)])
 def test_triangles(p, model, case):
     _run_r_jv(synth.tri_square(7, affine=SHEAR2), p, model, case)
