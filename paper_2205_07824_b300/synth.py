@@ -144,6 +144,37 @@ def tri_square(n: int, lo=(0.0, 0.0), hi=(1.0, 1.0), periodic=(False, False),
     return Mesh(TRI, xyz, ids, f"tri{n}x{n}")
 
 
+def tri_unstructured(n: int, seed: int = 0, jitter: float = 0.25) -> Mesh:
+    """Seeded triangle mesh of [0, 1]^2 with unstructured topology and shapes: n x n
+    squares, each split along a diagonal drawn at random (vertex degrees 3 to 8), interior
+    vertices moved by up to jitter cell sizes in each direction, each triangle's vertex
+    list rotated at random (still counter-clockwise, so neighbours see their shared edge
+    under every local numbering), and the elements shuffled: 2 n^2 affine triangles."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n
+    pts = np.stack(np.meshgrid(np.linspace(0.0, 1.0, n + 1), np.linspace(0.0, 1.0, n + 1), indexing="ij"), -1)
+    move = rng.uniform(-jitter * h, jitter * h, pts.shape)
+    move[0, :] = move[-1, :] = 0.0
+    move[:, 0] = move[:, -1] = 0.0
+    pts = pts + move
+    tris = []
+    for j in range(n):
+        for i in range(n):
+            a, b, c, d = (i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)
+            pair = ((a, b, c), (a, c, d)) if rng.random() < 0.5 else ((a, b, d), (b, c, d))
+            for t in pair:
+                r = int(rng.integers(3))
+                tris.append(t[r:] + t[:r])
+    order = rng.permutation(len(tris))
+    xyz = np.empty((len(tris), 3, 2))
+    ids = np.empty((len(tris), 3), dtype=np.int64)
+    for e, k in enumerate(order):
+        for v, (ii, jj) in enumerate(tris[k]):
+            xyz[e, v] = pts[ii, jj]
+            ids[e, v] = ii + (n + 1) * jj
+    return Mesh(TRI, xyz, ids, f"tri_unstructured{n}_s{seed}")
+
+
 def _curved_quads(params, node_id, n0, n1, G, pg, bc_of, name):
     """Quadrilaterals of a structured n0 x n1 grid of parameter points: element (i, j)
     (i fastest) has corners params[i..i+1, j..j+1]; its map sends reference point
@@ -308,6 +339,37 @@ def tet_cube(n: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(False, Fa
     if affine is not None:
         xyz = xyz @ np.asarray(affine, dtype=np.float64).T
     return Mesh(TET, xyz, ids, f"tet{n}")
+
+
+def tet_unstructured(n: int, seed: int = 0, jitter: float = 0.15) -> Mesh:
+    """Seeded tetrahedral mesh of [0, 1]^3 with distorted shapes and no element order:
+    tet_cube(n) with every interior vertex moved by up to jitter cell sizes in each
+    direction (right-handed vertex order restored where needed) and the elements
+    shuffled: 6 n^3 affine tetrahedra."""
+    rng = np.random.default_rng(seed)
+    base = tet_cube(n)
+    pos = {}
+    for e in range(base.n_elem):
+        for v in range(4):
+            pos.setdefault(int(base.vid[e, v]), base.xyz[e, v].copy())
+    h = 1.0 / n
+    moved = {}
+    for vid_ in sorted(pos):
+        x = pos[vid_]
+        inner = np.all((x > 0.5 * h) & (x < 1.0 - 0.5 * h))
+        moved[vid_] = x + (rng.uniform(-jitter * h, jitter * h, 3) if inner else 0.0)
+    order = rng.permutation(base.n_elem)
+    xyz = np.empty((base.n_elem, 4, 3))
+    ids = np.empty((base.n_elem, 4), dtype=np.int64)
+    for e, k in enumerate(order):
+        vv = [int(t) for t in base.vid[k]]
+        pts = [moved[t] for t in vv]
+        if np.linalg.det(np.stack([pts[1] - pts[0], pts[2] - pts[0], pts[3] - pts[0]])) < 0:
+            pts[1], pts[2] = pts[2], pts[1]
+            vv[1], vv[2] = vv[2], vv[1]
+        xyz[e] = pts
+        ids[e] = vv
+    return Mesh(TET, xyz, ids, f"tet_unstructured{n}_s{seed}")
 
 
 def random_vector(n: int, seed: int, scale: float = 1.0) -> np.ndarray:

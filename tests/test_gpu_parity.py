@@ -29,6 +29,15 @@ def test_triangles(p, model, case):
     _run_r_jv(synth.tri_square(7, affine=SHEAR2), p, model, case)
 
 
+@pytest.mark.parametrize("kind,p", [("tri", 1), ("tri", 3), ("tri", 6), ("tet", 1), ("tet", 3)])
+@pytest.mark.parametrize("model,case", [(oracle.POISSON, oracle.CASE_SINSIN), (oracle.CONVDIFF, oracle.CASE_EXPSIN)])
+def test_unstructured_simplices(kind, p, model, case):
+    """R and J.v on unstructured simplex meshes (random diagonals, jittered vertices,
+    rotated local numbering, shuffled elements; several tiles with a ragged last one)."""
+    mesh = synth.tri_unstructured(9, seed=7) if kind == "tri" else synth.tet_unstructured(3, seed=4)
+    _run_r_jv(mesh, p, model, case)
+
+
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 @pytest.mark.parametrize("model,case", [(oracle.POISSON, oracle.CASE_SINSIN), (oracle.CONVDIFF, oracle.CASE_EXPSIN)])
 def test_quads_dirichlet(p, model, case):

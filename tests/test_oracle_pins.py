@@ -229,6 +229,33 @@ def test_poisson_jacobian_symmetric_positive_definite():
     assert np.linalg.eigvalsh(0.5 * (J + J.T)).min() > 0
 
 
+@pytest.mark.parametrize("mesh_kind,p,model,case", [
+    ("tri", 2, oracle.POISSON, oracle.CASE_POLY2), ("tri", 3, oracle.CONVDIFF, oracle.CASE_POLY2),
+    ("tri", 5, oracle.POISSON, oracle.CASE_POLY2), ("tet", 2, oracle.CONVDIFF, oracle.CASE_POLY2),
+    ("tet", 3, oracle.POISSON, oracle.CASE_POLY2)])
+def test_patch_test_unstructured_simplices(mesh_kind, p, model, case):
+    """The patch test on unstructured simplex meshes: random diagonals (vertex degrees 3
+    to 8), jittered vertices, rotated local vertex numbering and shuffled elements; a
+    polynomial of degree <= p still has zero residual, so faces are paired and oriented
+    correctly under every local numbering."""
+    mesh = synth.tri_unstructured(5, seed=11) if mesh_kind == "tri" else synth.tet_unstructured(2, seed=5)
+    mu = (0.7, 1.3) if model == oracle.POISSON else ((0.05, 0.4, 1.0, -0.6) if mesh_kind == "tri"
+                                                    else (0.05, 0.4, 1.0, -0.6, 0.3))
+    o = oracle.Oracle(mesh, p, model, case, mu)
+    u = o.interpolate()
+    r = o.residual(u)
+    assert np.abs(r).max() < 1e-12 * max(1.0, np.abs(o.residual(np.zeros_like(u))).max())
+
+
+def test_poisson_jacobian_spd_on_unstructured_triangles():
+    """The LDG Poisson operator (central traces with a jump penalty) is symmetric positive
+    definite; so it stays on a random-diagonal, jittered mesh."""
+    o = oracle.Oracle(synth.tri_unstructured(3, seed=2), 2, oracle.POISSON, oracle.CASE_SINSIN, (1.0, 1.0))
+    J = o.jacobian_cs(np.zeros(o.ndof))
+    assert np.linalg.norm(J - J.T) <= 1e-13 * np.linalg.norm(J)
+    assert np.linalg.eigvalsh(0.5 * (J + J.T)).min() > 0
+
+
 def test_upwind_dissipation():
     """Pure convection with the upwind flux on a periodic mesh: u^T R(u) =
     1/2 sum_faces int |beta.n| [u]^2 > 0; a constant state gives zero."""
