@@ -79,7 +79,7 @@ def _tet_monomial_integral(a, b, c):
     return float(8 * tot)
 
 
-@pytest.mark.parametrize("nq1", [2, 3, 4])
+@pytest.mark.parametrize("nq1", [2, 3, 4, 5, 6])
 def test_tetrahedron_rule_exactness(nq1):
     """The collapsed Gauss rule with nq1 points per direction is exact to total degree
     2 nq1 - 3 (its Jacobian factor (1-b)(1-c)^2 / 8 spends two degrees in c)."""
@@ -116,7 +116,7 @@ def test_tensor_rule_exactness(etype):
 
 
 @pytest.mark.parametrize("etype,p", [(0, 1), (0, 2), (0, 3), (0, 4), (0, 5), (0, 6), (1, 1), (1, 3), (1, 5), (2, 2),
-                                     (2, 4), (3, 1), (3, 2), (3, 3)])
+                                     (2, 4), (3, 1), (3, 2), (3, 3), (3, 4)])
 def test_basis_partition_and_kronecker(etype, p):
     o = oracle.Oracle(_mesh(etype, 1), p, oracle.POISSON, oracle.CASE_ZERO)
     nodes = o.ref_rules()[0]
@@ -144,7 +144,8 @@ def test_basis_partition_and_kronecker(etype, p):
     (2, 2, oracle.CONVDIFF, oracle.CASE_POLY2), (2, 1, oracle.POISSON, oracle.CASE_LINEAR),
     (3, 1, oracle.POISSON, oracle.CASE_LINEAR), (3, 2, oracle.CONVDIFF, oracle.CASE_POLY2),
     (3, 3, oracle.POISSON, oracle.CASE_POLY2), (0, 4, oracle.POISSON, oracle.CASE_POLY2),
-    (0, 5, oracle.CONVDIFF, oracle.CASE_LINEAR), (0, 6, oracle.CONVDIFF, oracle.CASE_POLY2)])
+    (0, 5, oracle.CONVDIFF, oracle.CASE_LINEAR), (0, 6, oracle.CONVDIFF, oracle.CASE_POLY2),
+    (3, 4, oracle.CONVDIFF, oracle.CASE_POLY2)])
 def test_patch_test(etype, p, model, case):
     """Consistency + uniqueness of LDG: a polynomial of degree <= p (with q = -grad u
     and the matching source/boundary data) has zero residual."""
