@@ -1,7 +1,7 @@
 """Tetrahedra on the GPU against the FP64 CPU oracle (Section 4.1's element).
 
 Residual, q and J.v meet the FP64 parity bar for Poisson and convection-diffusion,
-p = 1..3, on sheared, ragged and periodic meshes and with both tile shapes (the
+p = 1..4, on sheared, ragged and periodic meshes and with both tile shapes (the
 neighbour traces come from face nodes permuted into each element's own face-node
 order); the element-diagonal blocks equal the oracle's complex-step Jacobian blocks;
 and the GPU solves of Section 4.1's Poisson problem on the unit cube reproduce
@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
 @pytest.mark.parametrize("model", [oracle.POISSON, oracle.CONVDIFF])
 @pytest.mark.parametrize("periodic", [False, True])
 def test_residual_q_jvp(p, model, periodic):
@@ -49,7 +49,7 @@ def test_diag_blocks_match_complex_step():
     assert_parity(blk.transpose(0, 2, 1), ref, what="diag blocks")
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_table3_rates_on_gpu(p):
     """Section 4.1: -lap u = f on the unit cube, u = sin(pi x) sin(pi y) sin(pi z),
     structured tetrahedral meshes, 1/n = 4, 8, 16. The GPU solves (Newton-GMRES with
