@@ -179,7 +179,15 @@ def kernel_launches() -> int:
 
 
 class LDG:
-    """One LDG operator (mesh, order p, model) resident on the current CUDA device."""
+    """One LDG operator (mesh, order p, model) resident on the current CUDA device.
+
+    The keyword options mirror ``ldg_options`` in ``include/ldg.h``: solver sizes and
+    tolerances, ``krylov_precision`` (FP64 or FP32 Krylov J.v and preconditioner),
+    ``precond`` (none, block-Jacobi, learned), ``pc_refresh``, and three solve policies
+    that default to their plain form: ``newton_forcing`` (FORCING_LAST: a Newton step's
+    linear solve stops at what the Newton tolerance still needs), ``pc_reuse`` (the
+    block-Jacobi blocks are built every pc_reuse solve calls) and ``krylov_basis``
+    (BASIS_F32X2: Gram-Schmidt on (hi, lo) float pairs, an emulated FP64)."""
 
     def __init__(self, mesh, p: int, model: int, case: int, mu=(), nq1: int = 0, gmres_m: int = 30,
                  max_restarts: int = 50, max_newton: int = 20, newton_rtol: float = 1e-8,
@@ -415,6 +423,8 @@ class Batch:
     meshes: list of synth.Mesh; ps: orders; mus: per-instance parameter sequences;
     cases: per-instance analytic case (int or list). The batch vector is one float64
     CUDA tensor of ``n_total`` entries; instance i is ``u[offsets[i]:offsets[i] + n_dof[i]]``.
+    The solver options are those of ``LDG`` (``pc_refresh`` aside); the forcing term is
+    applied per instance.
     """
 
     def __init__(self, meshes, ps, model: int, cases, mus, nq1: int = 0, gmres_m: int = 30,
