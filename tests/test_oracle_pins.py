@@ -223,6 +223,58 @@ def test_navier_stokes_viscous_terms_vanish_for_rigid_rotation():
     assert np.linalg.norm(on2.residual(u2) - oe2.residual(u2)) > 1e-3 * np.linalg.norm(oe2.residual(u2))
 
 
+def _quad_node_xy(o, mesh):
+    """Physical positions [E][npe][2] of the nodes of parallelogram elements: the
+    bilinear vertex map (vertices in lexicographic order) at the reference nodes."""
+    s, t = o.ref_rules()[0][:, 0], o.ref_rules()[0][:, 1]
+    N = np.stack([(1 - s) * (1 - t), (1 + s) * (1 - t), (1 - s) * (1 + t), (1 + s) * (1 + t)], 1) / 4
+    return np.einsum("na,ead->end", N, mesh.xyz)
+
+
+def _ns_viscous_sums(rho, m, rhoE, p=2, n=6, mu=(1.4, 5.0, 0.72)):
+    """Per-element sums over test functions of R_NS - R_Euler, for a state given as
+    nodal functions of position, on the elements of an n x n box that are at least two
+    faces away from its boundary (their q and neighbour q see no boundary data)."""
+    mesh = synth.quad_box(n)
+    on = oracle.Oracle(mesh, p, oracle.NS, oracle.CASE_CONST, mu)
+    oe = oracle.Oracle(mesh, p, oracle.EULER, oracle.CASE_CONST, mu[:1])
+    X = _quad_node_xy(on, mesh)
+    x, y = X[..., 0], X[..., 1]
+    u = np.stack([rho(x, y), m(x, y)[0], m(x, y)[1], rhoE(x, y)], 1).ravel()
+    d = (on.residual(u) - oe.residual(u)).reshape(mesh.n_elem, 4, on.npe).sum(-1)
+    inner = [i + n * j for j in range(2, n - 2) for i in range(2, n - 2)]
+    return d[inner], 1.0 / n ** 2
+
+
+def test_navier_stokes_viscous_stress_closed_form():
+    """Section 2.1's viscous flux pinned by a closed form. Constant density and internal
+    energy with the uniform dilatation v = a (x, y): the Stokes stress is the constant
+    (2/3) mu a I (bulk coefficient -2/3: 2a - (2/3)(2a)), so the momentum sums vanish and
+    the energy flux v . tau = (2/3) mu a^2 (x, y) has divergence (4/3) mu a^2. The state is
+    quadratic, exact in Q2, and continuous, so the LDG q is -grad u exactly and every face
+    jump is zero: summed over the test functions, R_NS - R_Euler on an element K is
+    -int_dK Fv . n = -(4/3) mu a^2 |K| in the energy and 0 elsewhere. A bulk coefficient of
+    -1/3 gives -(8/3) mu a^2 |K|."""
+    r0, a, e0, mu = 1.3, 0.4, 2.0, 1.0 / 5.0
+    d, area = _ns_viscous_sums(lambda x, y: r0 + 0 * x, lambda x, y: (r0 * a * x, r0 * a * y),
+                               lambda x, y: r0 * (e0 + 0.5 * a * a * (x * x + y * y)))
+    want = np.array([0.0, 0.0, 0.0, -(4.0 / 3.0) * mu * a * a * area])
+    assert np.abs(d - want).max() <= 1e-12, (d, want)
+
+
+def test_navier_stokes_heat_flux_closed_form():
+    """The Fourier heat flux (mu gamma / Pr) grad e pinned by a closed form: gas at rest
+    with constant density and internal energy e = b x^2 has no stress and the energy flux
+    (mu gamma / Pr)(2 b x, 0), so summed over the test functions R_NS - R_Euler on an
+    element K is -(mu gamma / Pr) 2 b |K| in the energy and 0 elsewhere. A heat flux
+    without gamma, or on grad E, fails it."""
+    r0, b, mu, gam, pr = 1.3, 0.7, 1.0 / 5.0, 1.4, 0.72
+    d, area = _ns_viscous_sums(lambda x, y: r0 + 0 * x, lambda x, y: (0 * x, 0 * x),
+                               lambda x, y: r0 * b * x * x)
+    want = np.array([0.0, 0.0, 0.0, -(mu * gam / pr) * 2.0 * b * area])
+    assert np.abs(d - want).max() <= 1e-12, (d, want)
+
+
 def test_poisson_jacobian_symmetric_positive_definite():
     o = oracle.Oracle(synth.tri_square(2, affine=SHEAR2), 2, oracle.POISSON, oracle.CASE_SINSIN, (1.0, 1.0))
     J = o.jacobian_cs(np.zeros(o.ndof))
@@ -486,6 +538,44 @@ def test_adam_reduces_a_quadratic():
     assert np.abs(theta).max() < 1e-2
 
 
+def test_adam_first_step_and_constant_gradient():
+    """Adam (Kingma & Ba 2015) from zero moments: the bias corrections make the first
+    step exactly lr g / (|g| + eps) for any g, and under a constant gradient every
+    later step is the same (m_hat = g and v_hat = g^2 at every t). A missing bias
+    correction scales the first step by (1 - b1) / sqrt(1 - b2) ~ 3.2."""
+    from oracle import mlp
+    rng = np.random.default_rng(7)
+    g = rng.standard_normal(16) * np.exp(rng.uniform(-6, 6, 16))
+    theta = rng.standard_normal(16)
+    m, v = np.zeros(16), np.zeros(16)
+    lr, eps = 0.01, 1e-8
+    prev = theta.copy()
+    for t in range(1, 6):
+        mlp.adam_step(theta, g, m, v, t, lr=lr)
+        step = theta - prev
+        assert np.allclose(step, -lr * g / (np.abs(g) + eps), rtol=1e-12, atol=0), t
+        prev = theta.copy()
+
+
+def test_adam_second_step_closed_forms():
+    """Two Adam steps from zero moments in closed form, with the published defaults
+    b1 = 0.9, b2 = 0.999 (eps negligible for |g| ~ 1):
+    gradients (g, -g): m_hat_2 = -g (1 - b1)/(1 + b1), v_hat_2 = g^2, so the second step
+    is +lr (1 - b1)/(1 + b1) sign(g) = lr / 19;
+    gradients (g, 2g): m_hat_2 = g (b1 + 2)/(1 + b1), v_hat_2 = g^2 (b2 + 4)/(1 + b2), so
+    the second step is -lr (2.9 / 1.9) / sqrt(4.999 / 1.999) sign(g). A wrong b1 fails the
+    first, a wrong b2 the second."""
+    from oracle import mlp
+    lr = 0.01
+    for g2f, want in ((-1.0, lr / 19.0), (2.0, -lr * (2.9 / 1.9) / math.sqrt(4.999 / 1.999))):
+        g = np.array([1.0, -1.0])
+        theta, m, v = np.zeros(2), np.zeros(2), np.zeros(2)
+        mlp.adam_step(theta, g, m, v, 1, lr=lr)
+        t1 = theta.copy()
+        mlp.adam_step(theta, g2f * g, m, v, 2, lr=lr)
+        assert np.allclose(theta - t1, want * np.sign(g), rtol=1e-7, atol=0), (g2f, theta - t1)
+
+
 def test_bf16_rounding_matches_torch_and_ties_to_even():
     """The oracle's BF16 rounding (storage precision of the tensor-core inference
     path) against torch's float32 -> bfloat16 conversion, plus the tie cases."""
@@ -673,6 +763,39 @@ def test_dirk_temporal_order_against_matrix_exponential():
             errs.append(np.linalg.norm(u - yT) / np.linalg.norm(yT))
         rate = np.log2(errs[0] / errs[1])
         assert rate > order - 0.3, (sch, errs, rate)
+
+
+def test_bdf2_temporal_order_against_matrix_exponential():
+    """BDF2 time term M (3 u^{n+1} - 4 u^n + u^{n-1}) / (2 dt) of the workloads' implicit
+    steps, pinned by its temporal order: on the linear semi-discrete problem
+    M u' = -(A u + r0) (convection-diffusion on a periodic mesh), started from the exact
+    solution at t = 0 and t = dt, the error at T against u* + expm(-t M^-1 A)(u0 - u*)
+    falls at order 2 over three halvings of dt. A wrong coefficient of u^{n-1} makes
+    the scheme inconsistent; a missing 1/2 solves a different ODE."""
+    import scipy.linalg as sl
+    mesh = synth.quad_box(3, hi=(2.0, 2.0), periodic=(True, True))
+    o = oracle.Oracle(mesh, 2, oracle.CONVDIFF, oracle.CASE_SINSIN, (0.02, 0.3, 1.0, 0.5))
+    n = o.ndof
+    A = o.jacobian_cs(np.zeros(n))
+    r0 = o.residual(np.zeros(n))
+    M = np.stack([o.mass(e) for e in np.eye(n)], 1)
+    ustar = -np.linalg.solve(A, r0)
+    u0 = o.interpolate()
+    L = np.linalg.solve(M, A)
+    exact = lambda t: ustar + sl.expm(-t * L) @ (u0 - ustar)
+    T = 0.5
+    errs = []
+    for N in (16, 32, 64, 128):
+        dt = T / N
+        unm1, un = u0.copy(), exact(dt)
+        for k in range(1, N):
+            o.set_time(2, (k + 1) * dt, dt, un, unm1)
+            u, rc, _ = o.newton(un, newton_rtol=1e-10, gmres_rtol=1e-12, m=30, max_gmres=5000)
+            assert rc == 0
+            unm1, un = un, u
+        errs.append(np.linalg.norm(un - exact(T)) / np.linalg.norm(exact(T)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(rates - 2.0) < 0.2), (errs, rates)
 
 
 @pytest.mark.parametrize("p", [1, 2])
