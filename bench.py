@@ -1,23 +1,31 @@
 #!/usr/bin/env python
-"""Benchmark of the B300 LDG hot path on the 2-D Euler isentropic-vortex workload.
+"""Benchmark of the B300 LDG hot path.
 
-Workload: periodic [0,10]^2, 64 x 64 affine quadrilaterals, p = 3 (Gauss-Lobatto
-nodes, 5 x 5 Gauss points), local Lax-Friedrichs flux, BDF2 with dt = 0.05.
-One *step* is one implicit BDF2 time step: matrix-free Newton-GMRES (Section 3.3)
-from u^n until ||R(u)||_2 <= 1e-8 ||R(u^n)||_2 in FP64, every J.v exact (dual
-numbers), Arnoldi with two-pass classical Gram-Schmidt and Givens rotations in
-FP64. The default form is the mixed one: the Krylov J.v and the block-Jacobi
-preconditioner in FP32 arithmetic (FP64 in memory); the plain FP64 block-Jacobi
-form is timed in the same run for comparison. The L2 cache is flushed (a 256 MiB
-write) before every timed step, outside the step's event window.
+Default workload (`--workload jv`): the exact Jacobian-vector product of 3-D steady
+convection-diffusion div(beta u - kappa grad u) = f on [0,1]^3 with 48^3 affine
+hexahedra, p = 4 (Gauss-Lobatto nodes, 5^3 Gauss points), beta = (1, 0.5, 0.25),
+kappa = 1e-2, manufactured u = exp(x+y+z) sin(pi xyz): 13,824,000 DOF. One *step*
+is one FP64 J.v application on the full state (the q-stage of Eq. 1a on the
+direction, then the residual stage of Eq. 1b), with v drawn N(0, 1). The inputs
+and scratch of one J.v (v 110.6 MB, q(v) 331.8 MB, J.v 110.6 MB) exceed the 126 MB
+L2, so no flush is needed between steps.
 
-Metric: J.v GDOF/s = (DOFs x J.v applications of the whole solve) / step time,
-over the K timed steps; ms_per_step is the Newton-GMRES time to 1e-8 per
-implicit step.
+Metric: J.v GDOF/s = DOF x steps / time of the K timed steps (CUDA events on the
+launching stream), with the %HBM roofline of the algorithmic bytes per DOF and the
+FP64-ALU fraction. The same line reports the FP32-arithmetic J.v (with its error
+against the FP64 oracle on sampled elements), the J.v end to end through the
+host-buffer C-ABI call, the Newton-GMRES time to 1e-8 of the 2-D vortex BDF2 step
+(FP32 Krylov + block-Jacobi against plain FP64 block-Jacobi, and through the
+host-buffer solve call), and the FP64 oracle timed on the host cores.
+
+Other workloads: vortex (the 64x64 p=3 Euler BDF2 step), batch (256 parametrised
+solves in one graph launch), hex (the 48^3 J.v sweep p = 1..6), tri, tet (Table 3's
+problem), cylinder (Navier-Stokes past a cylinder, learned + mixed against plain
+FP64 block-Jacobi).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-With N > 1 (torchrun), every rank advances its own vortex instance (weak scaling,
-no collective on the data path); rank 0 prints one JSON line.
+With N > 1 (torchrun), every rank runs its own instance (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -42,12 +50,28 @@ N_SIDE, P, DT = 64, 3, 0.05
 LAGGED_PC_REUSE = 4    # implicit steps per block-Jacobi build in the lagged form
 # FLOPs per element of one J.v launch (dual-number Euler kernel, p = 3, 5 x 5 Gauss points),
 # counted by ncu as 2*FMA + ADD + MUL thread instructions: FP64 instance (index 0) and
-# FP32 instance (index 1); see profiles/.
+# FP32 instance (index 1).
 JV_FLOP_PER_ELEM = (18449.0, 17027.0)
 # ALU peaks derived from the unit counts and the maximum SM clock (2.032 GHz):
 # FP64 148 SMs x 2 FMA/clk x 2 FLOP; FP32 148 SMs x 128 FMA/clk x 2 FLOP.
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# Per-DOF FP64 FLOPs and DRAM bytes of one J.v of the default workload, by kernel
+# variant (ncu thread-instruction counts and dram__bytes_read.sum + dram__bytes_write.sum
+# of one capture); a variant not listed reports the HBM roofline only.
+JV_FLOP_PER_DOF = {}
+JV_TRAFFIC_PER_DOF = {}
+
+
+# Default workload: the FP64 J.v of 3-D convection-diffusion on 48^3 hexahedra, p = 4.
+JV_N, JV_P = 48, 4
+JV_MU = (1e-2, 1.0, 1.0, 0.5, 0.25)          # kappa, tau, beta
+JV_WORKLOAD = ("3D steady convection-diffusion div(beta u - kappa grad u) = f on [0,1]^3, 48^3 hexahedra, p=4 "
+               "(GLL nodes, 5^3 Gauss points), beta=(1,0.5,0.25), kappa=1e-2, tau=1, u=exp(x+y+z) sin(pi xyz); "
+               "one exact J.v application on the full 13,824,000-DOF state per step")
+# Algorithmic HBM bytes per DOF of one linear 3-D J.v with FP64 storage: v read, q(v)
+# written and read (3 components), J.v written: (1 + 2 x 3 + 1) x 8.
+JV_BYTES_PER_DOF = 64.0
 
 
 def _dist():
@@ -213,6 +237,206 @@ def graph_time_ms(g, fn, reps):
         return e0.elapsed_time(e1) / reps
     finally:
         g.set_stream(old)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def jv_oracle_sample(mesh, u_h, v_h, stride, seconds=None):
+    """The FP64 oracle's J.v on every `stride`-th element (with the q-neighbourhood it
+    needs); returns (element ids, oracle J.v rows [n][n_pe], seconds)."""
+    import numpy as np
+    import oracle
+    o = oracle.Oracle(mesh, JV_P, oracle.CONVDIFF, oracle.CASE_EXPSIN, JV_MU)
+    el = np.arange(0, mesh.n_elem, stride, dtype=np.int64)
+    t0 = time.perf_counter()
+    ref = o.jvp_some(u_h, v_h, el)
+    return el, ref.reshape(len(el), -1), time.perf_counter() - t0
+
+
+def run_jv(args):
+    """The default workload: FP64 J.v GDOF/s on 48^3 hexahedra, p = 4."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, CONVDIFF, CASE_EXPSIN, kernel_launches
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    mesh = synth.hex_box(JV_N)
+    stream = torch.cuda.current_stream()
+    g = LDG(mesh, JV_P, CONVDIFF, CASE_EXPSIN, JV_MU, krylov_precision=0)
+    tile, _ = g.autotune()
+    n = g.n_dof
+    u = g.interpolate(0.0)
+    v = torch.randn(n, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1 + rank))
+    out = torch.empty_like(v)
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            g.jvp_prec(prec, u, v, out)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = kernel_launches()
+        e0.record(stream)
+        for _ in range(steps):
+            g.jvp_prec(prec, u, v, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return e0.elapsed_time(e1), kernel_launches() - l0
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    t64, launches = timed(0, args.steps, args.warmup)
+    clk = clocks.stop()
+    jv64 = out.clone()
+    total_ms, gdofs = aggregate([t64], n * args.steps, world, rank)
+    ms = t64 / args.steps
+
+    # the FP32-arithmetic J.v (FP64 storage) on the same inputs
+    t32, _ = timed(1, args.steps, args.warmup)
+    jv32 = out.clone()
+    ms32 = t32 / args.steps
+
+    peaks = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    hbm64 = JV_BYTES_PER_DOF * n / (ms * 1e-3) / 1e9
+    hbm32 = JV_BYTES_PER_DOF * n / (ms32 * 1e-3) / 1e9
+    kname = g.jv_kernels(0)
+    fpd = JV_FLOP_PER_DOF.get(kname)
+    roofline = {"bound": "alu" if fpd else "hbm",
+                "unit": "TFLOP/s" if fpd else "GB/s",
+                "achieved": (fpd * n / (ms * 1e-3) / 1e12) if fpd else hbm64,
+                "peak": FP64_PEAK_TFLOPS if fpd else hbm,
+                "traffic": JV_TRAFFIC_PER_DOF.get(kname, 0) * n or None,
+                "kernel": kname + " (one J.v: all its launches)",
+                "timing": "CUDA events on the launching stream around the K timed J.v applications",
+                "flop_per_dof": fpd,
+                "flop_source": "ncu thread-instruction counts of the kernels (DFMA x2 + DADD + DMUL)" if fpd else None,
+                "peak_source": "FP64 ALU: 148 SMs x 2 FMA/clk x 2 FLOP x 2.032 GHz (derived)" if fpd else
+                               ("measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"),
+                "hbm": {"bytes_per_dof": JV_BYTES_PER_DOF, "achieved_gbs": hbm64, "peak_gbs": hbm,
+                        "frac": hbm64 / hbm,
+                        "peak_source": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"}}
+    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+
+    # FP32 and FP64 J.v against the FP64 oracle on sampled elements (rank 0)
+    samp = None
+    cpu = None
+    if rank == 0:
+        uh, vh = u.cpu().numpy(), v.cpu().numpy()
+        el, ref, _ = jv_oracle_sample(mesh, uh, vh, 1103)
+        npe = g.n_pe
+        r64 = jv64.view(-1, npe).cpu().numpy()[el]
+        r32 = jv32.view(-1, npe).cpu().numpy()[el]
+        nr = np.linalg.norm(ref)
+        samp = {"elements": int(len(el)), "stride": 1103,
+                "fp64_rel_err_vs_oracle": float(np.linalg.norm(r64 - ref) / nr),
+                "fp32_rel_err_vs_oracle": float(np.linalg.norm(r32 - ref) / nr)}
+        if not args.no_cpu_baseline:
+            el_c, _, sec = jv_oracle_sample(mesh, uh, vh, 251)
+            cpu = {"value": len(el_c) * npe / sec / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"the FP64 oracle's J.v on every 251st element ({len(el_c)} elements, each with "
+                             f"the q-stage of its face neighbours), {sec:.1f} s single-threaded; "
+                             "DOF of the sampled elements / time"}
+
+    # end to end through the host-buffer C-ABI call: v in, J.v out, per step
+    e2e = None
+    if not args.no_e2e:
+        hv = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        hv.copy_(v)
+        ho = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        k2 = max(3, min(args.steps, 10))
+        g.jvp_host(0, None, hv, ho)                  # staging buffers allocated once
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            g.jvp_host(0, None, hv, ho)
+        te = time.perf_counter() - t0
+        tmax, e2e_gdofs = aggregate([te * 1e3], n * k2, world, rank)
+        e2e = {"value": e2e_gdofs, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+               "steps": k2, "ms_per_step": tmax / k2,
+               "call": "ldg_jvp_host (FP64): v copied from pinned host memory, J.v on the device, J.v copied "
+                       "back, stream synchronised; host wall clock (a linear model's J.v does not read u)"}
+
+    solve = None
+    if not args.no_solve:
+        solve = vortex_solve_summary(args, stream)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": gdofs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": JV_WORKLOAD, "n_dof": int(n), "n_elem": int(mesh.n_elem),
+                           "step": "one FP64 J.v application (q-stage of the direction, then the residual stage)",
+                           "tile": tile,
+                           "l2": "not flushed: the inputs and scratch of each J.v (553 MB) exceed the 126 MB L2",
+                           "parallelism": f"{world} independent instance(s), one per GPU",
+                           "fp32_jv": {"ms": ms32, "gdofs": n / (ms32 * 1e-3) / 1e9, "hbm_gbs": hbm32,
+                                       "hbm_frac": hbm32 / hbm, "kernel": g.jv_kernels(1),
+                                       "arithmetic": "FP32 (inputs, output and q scratch FP64 in memory)"},
+                           "oracle_sample": samp,
+                           "solve_time_to_1e-8": solve},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def vortex_solve_summary(args, stream):
+    """Newton-GMRES time to 1e-8 of the 64x64 p=3 vortex BDF2 step: FP32 Krylov J.v +
+    block-Jacobi against plain FP64 block-Jacobi (same steps, same forcing rule), and the
+    same step end to end through the host-buffer solve call."""
+    import torch
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, BDF2, kernel_launches
+    mesh = synth.quad_box(N_SIDE, hi=(10.0, 10.0), periodic=(True, True))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    steps = max(3, min(args.steps, 10))
+    prob = vortex_problem(LDG, mesh, forcing_of(args), 1)
+    forms = {}
+    sol = {}
+    for name, kp in (("fp32_krylov_bjacobi", 1), ("fp64_bjacobi", 0)):
+        g, u, times, tot, _, t_end, _ = run_mode(prob, kp, 1, steps, 3, flush, stream, kernel_launches)
+        forms[name] = {"ms_per_step": sum(times) / steps, "gmres_iters_per_step": tot["gmres"] / steps,
+                       "newton_iters_per_step": tot["newton"] / steps}
+        sol[name] = u.clone()
+        if kp == 1:
+            # the same step end to end: u^n from host memory through ldg_newton_gmres_host
+            import numpy as np
+            un = u.cpu().numpy()
+            g.set_time(BDF2, t_end + DT, DT, u, u)
+            hu = np.array(un)
+            g.newton_gmres_host(hu)                       # untimed first call
+            k2 = 3
+            t0 = time.perf_counter()
+            for _ in range(k2):
+                hu[:] = un
+                rep = g.newton_gmres_host(hu)
+            te = (time.perf_counter() - t0) / k2
+            forms[name]["e2e_host_call_ms"] = te * 1e3
+            forms[name]["e2e_note"] = ("ldg_newton_gmres_host: u^n copied in from host memory, solved to 1e-8, "
+                                       "solution copied back; host wall clock")
+        del g
+    forms["speedup_fp32_vs_fp64"] = forms["fp64_bjacobi"]["ms_per_step"] / forms["fp32_krylov_bjacobi"]["ms_per_step"]
+    forms["solution_rel_diff"] = float(torch.linalg.norm(sol["fp32_krylov_bjacobi"] - sol["fp64_bjacobi"]) /
+                                       torch.linalg.norm(sol["fp64_bjacobi"]))
+    forms["workload"] = WORKLOAD
+    return forms
 
 
 def forcing_of(args):
@@ -843,7 +1067,7 @@ def run_cylinder(args):
         hbm, peak_src = 6400.0, "fallback 6.4 TB/s (of fallback)"
     achieved = b_alg / (jvt[1] * 1e-3) / 1e9
     # DRAM reads of the pair per DOF from one ncu capture of the same kernels on the
-    # 1/16-scaled cylinder mesh (profiles/ncu_c5_ns_jv_pair_curved_p3_scaled16.md),
+    # 1/16-scaled cylinder mesh (ncu capture of the pair on that mesh),
     # scaled by the DOF count (traffic grows with the elements)
     traffic = (9.679104e6 + 5.784832e6) / 160000.0 * n
     roofline = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": hbm, "frac": achieved / hbm,
@@ -896,7 +1120,7 @@ def run_cylinder(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -919,8 +1143,10 @@ def main():
     ap.add_argument("--host-loops", action="store_true",
                     help="run the solver's Newton / restart / Arnoldi loops from the host instead of the CUDA "
                          "graph's WHILE nodes (same kernels; for profilers that do not follow graph nodes)")
-    ap.add_argument("--workload", default="vortex", choices=["vortex", "batch", "hex", "tri", "cylinder", "tet"],
-                    help="vortex: the 64x64 p=3 Euler BDF2 step; batch: 256 parametrised convection-diffusion "
+    ap.add_argument("--no-solve", action="store_true", help="jv: skip the vortex time-to-1e-8 comparison")
+    ap.add_argument("--workload", default="jv", choices=["jv", "vortex", "batch", "hex", "tri", "cylinder", "tet"],
+                    help="jv (default): the FP64 J.v of 48^3 p=4 convection-diffusion; "
+                         "vortex: the 64x64 p=3 Euler BDF2 step; batch: 256 parametrised convection-diffusion "
                          "solves in one graph launch; hex: the 48^3 convection-diffusion J.v sweep p=1..6; "
                          "tri: the same sweep on 131,072 triangles; "
                          "cylinder: Navier-Stokes past a cylinder on 40,000 curved quads, learned + mixed vs "
@@ -939,6 +1165,9 @@ def main():
         os.environ["LDG_SOLVER_HOST_LOOPS"] = "1"
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "jv":
+        run_jv(args)
         return
     if args.workload == "batch":
         run_batch(args)
@@ -1038,8 +1267,8 @@ def main():
     fpe = JV_FLOP_PER_ELEM[kprec]
     achieved = fpe * mesh.n_elem / (jv_ms * 1e-3) / 1e12
     peak = FP32_PEAK_TFLOPS if kprec else FP64_PEAK_TFLOPS
-    # DRAM bytes per launch of the FP32 kernel (tile 8) from one ncu capture inside the step
-    # (profiles/ncu_c2_euler_jv_fp32_p3.md): the state is L2-resident
+    # DRAM bytes per launch of the FP32 kernel (tile 8) from one ncu capture inside the step:
+    # the state is L2-resident
     traffic = (1.792e3 + 1.024e3) if kprec else None
     roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
                 "traffic": traffic,

@@ -153,12 +153,18 @@ typedef struct {
                            Hessenberg, Givens, Newton residual and solution stay FP64. The
                            host-driven solves (learned preconditioner, ldg_gmres) always use
                            FP64. */
+  int jv_form;          /* linear models on affine quadrilaterals / hexahedra with p + 1 Gauss
+                           points: LDG_JV_AUTO (default) takes the nodal J.v kernels (the same
+                           operator in exact nodal form, one thread per node, two launches);
+                           LDG_JV_STAGE keeps the quadrature-point stage kernels of every
+                           other case. Results agree to rounding. */
 } ldg_options;
 
 enum { LDG_FP64 = 0, LDG_FP32 = 1 };
 enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1, LDG_PC_MLP = 2 };
 enum { LDG_FORCING_FIXED = 0, LDG_FORCING_LAST = 1 };
 enum { LDG_BASIS_FP64 = 0, LDG_BASIS_F32X2 = 1 };
+enum { LDG_JV_AUTO = 0, LDG_JV_STAGE = 1 };
 
 typedef struct {
   int newton_iters;
@@ -196,10 +202,15 @@ const char* ldg_version(void);
 /* Number of CUDA kernels this library has launched in this process (all contexts). */
 int64_t ldg_kernel_launches(void);
 
-/* Creates a context: builds the reference element, the affine geometry, the face
- * connectivity and orientation tables on the host, uploads them, and allocates
- * the work space. `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
- * Returns LDG_ERR_UNSUPPORTED when no kernel is compiled for the combination. */
+/* Creates a context for the discretisation of Section 2.2: the LDG method of order p
+ * on the mesh of Section 3.2 for the model of Section 2.1 (Eq. 1a-1b), solved by the
+ * Newton-GMRES of Section 3.3 with `opts`. It builds the reference element, the affine
+ * (or sampled curved) geometry, the face connectivity and orientation tables on the
+ * host, uploads them, and allocates the work space. `cuda_stream` is a cudaStream_t
+ * (NULL = legacy default stream). *out receives the context (NULL on error).
+ * Returns LDG_ERR_ARG for null or empty inputs, LDG_ERR_MESH for a rejected mesh,
+ * LDG_ERR_UNSUPPORTED when no kernel is compiled for the (element, p, quadrature,
+ * model), LDG_ERR_CUDA when an allocation or copy fails. */
 int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_desc* model,
                const ldg_options* opts, void* cuda_stream);
 int ldg_destroy(ldg_ctx* ctx);
@@ -226,6 +237,20 @@ int ldg_jvp(ldg_ctx* ctx, const double* u_dev, const double* v_dev, double* jv_d
 /* J.v in a chosen arithmetic: LDG_FP64 (same as ldg_jvp) or LDG_FP32 (inputs and
  * output FP64 in memory; every operation of the operator in FP32). */
 int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u_dev, const double* v_dev, double* jv_dev);
+
+/* Names the kernels that form this context's J.v in `precision` (LDG_FP64 / LDG_FP32)
+ * and the case they serve, e.g. "k_lin_q + k_lin_r [hex p=4 nq=5 convdiff fp64, ...]".
+ * The string stays valid until the calling thread's next call of this function. */
+const char* ldg_jv_describe(const ldg_ctx* ctx, int precision);
+
+/* The same J.v with HOST buffers (end-to-end form): u_host and v_host (n_dof doubles
+ * each) are copied to the device, J(u) v is formed in `precision` (as ldg_jvp_prec) and
+ * copied back to jv_host; the call returns after the copy back has finished. Pinned
+ * (page-locked) host memory gives the fastest copies. u_host may be NULL for linear
+ * models, whose J.v does not depend on u. The first call allocates 3 n_dof doubles of
+ * context staging memory. Errors: LDG_ERR_ARG (null v_host / jv_host, NULL u_host for a
+ * nonlinear model, bad precision), LDG_ERR_CUDA. */
+int ldg_jvp_host(ldg_ctx* ctx, int precision, const double* u_host, const double* v_host, double* jv_host);
 
 /* J(u) v reusing the q(u) that the last ldg_residual(ctx, u, ...) call on this context
  * computed: the form of J.v inside Newton-GMRES, where every Krylov product of a
@@ -291,6 +316,25 @@ int ldg_q(ldg_ctx* ctx, const double* u_dev, double* q_dev);
 /* Nodal interpolant of the context's analytic case at time t. */
 int ldg_interpolate(ldg_ctx* ctx, double t, double* u_dev);
 
+/* L2 projection of the context's analytic case at time t onto the element space
+ * (the projected initial or exact field beside Section 4.1's error study):
+ * u_K = M_K^{-1} (phi, u_exact)_K per element, with integrals by a Gauss rule of
+ * p + 3 points per direction (collapsed on simplices). u_dev: n_dof doubles,
+ * written. Affine elements only: curved quadrilaterals return LDG_ERR_UNSUPPORTED.
+ * The first call builds the rule (a few host arrays and p + 3-point tables on the
+ * device, plus 4 n_elem + 2 doubles of error partials). */
+int ldg_project(ldg_ctx* ctx, double t, double* u_dev);
+
+/* Relative L2 errors of Section 4.1 / Table 3 against the analytic case at time t:
+ *   err_u = ||u_h - u||_L2 / ||u||_L2 (all components),
+ *   err_q = ||q_h - q||_L2 / ||q||_L2 with q = -grad u and q_h from the q-stage of
+ *           Eq. 1a (Poisson and convection-diffusion; 0 for the gas models),
+ * integrated by the rule of ldg_project (a zero denominator counts as 1). u_dev is a
+ * device vector; err_u and err_q (may be NULL) are host doubles, written after the
+ * call has synchronised the context's stream. Overwrites the context's q scratch.
+ * Affine elements only (LDG_ERR_UNSUPPORTED for curved quadrilaterals). */
+int ldg_l2_error(ldg_ctx* ctx, const double* u_dev, double t, double* err_u, double* err_q);
+
 /* GMRES(m) on J(u) x = b from x = 0 (classical Gram-Schmidt with one
  * re-orthogonalisation, Givens rotations, FP64), to gmres_rtol. */
 int ldg_gmres(ldg_ctx* ctx, const double* u_dev, const double* b_dev, double* x_dev, ldg_solve_report* rep);
@@ -329,22 +373,24 @@ int ldg_dirk_step(ldg_ctx* ctx, int scheme, double t, double dt, double* u_dev, 
  * service for callers that cannot allocate). It computes the same product as
  * ldg_jvp, but the scratch that product needs (q of the direction v for Poisson
  * and convection-diffusion, n_dof * dim doubles; q(u) and q of v for Navier-Stokes,
- * twice that) lives in a static device array inside this library instead of the
- * context's work space.
+ * twice that; none for Euler) lives in a static device array inside this library
+ * instead of the context's work space.
  *
- * Who needs it: code that must not call cudaMalloc at this point, for example a
- * CUDA stream being captured into a graph in global capture mode (where
- * allocation is not permitted), or an application whose device memory is held
- * entirely by its own pool or caching allocator. The call itself performs no
- * cudaMalloc, cudaFree or allocating library routine.
+ * Who needs it: callers that must not call cudaMalloc at this point. An application
+ * whose device memory is held entirely by its own pool or caching allocator has no
+ * memory left for a library to take, and a host loop with a fixed latency budget
+ * cannot wait on an allocation, or on the device-wide synchronisation that cudaFree
+ * implies. The call itself performs no cudaMalloc, cudaFree or allocating library
+ * routine.
  *
  * Limits and behaviour:
  *  - The static array holds LDG_NOALLOC_SCRATCH_DOUBLES doubles (32 MiB). Every
  *    device that loads this library keeps it for the life of the process.
  *    An operator needing more returns LDG_ERR_ARG with a message naming both sizes.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture begins.
+ *    (cudaGetSymbolAddress) with that device current and caches it; host threads
+ *    may make that first call concurrently. The cached address does not survive
+ *    cudaDeviceReset: do not call this function on a device after resetting it.
  *  - All calls, from every context on a device, share the one array and the
  *    array keeps the last call's contents. The kernels overwrite every entry
  *    they read, so nothing needs clearing; but calls whose work overlaps on the

@@ -17,6 +17,8 @@
 #include "ldg_tc.cuh"
 #include <cudaTypedefs.h>
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <random>
 #include <map>
 #include <numeric>
@@ -64,7 +66,10 @@ const std::vector<KernelSet>& registry() {
 constexpr size_t kNoAllocScratchDoubles = (size_t)LDG_NOALLOC_SCRATCH_DOUBLES;
 __device__ __align__(256) double noalloc_scratch[kNoAllocScratchDoubles];
 constexpr int kMaxDevices = 64;
-double* noalloc_addr[kMaxDevices] = {nullptr};
+// Per-device address cache, filled under a lock on the first call on that device
+// (two host threads may make their first calls at once).
+std::atomic<double*> noalloc_addr[kMaxDevices];
+std::mutex noalloc_lock;
 
 int fail(ldg_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -125,6 +130,7 @@ KArgs base_args(ldg_ctx* c) {
   KArgs a;
   std::memset(&a, 0, sizeof(a));
   a.geo = c->d_geo; a.nbr = c->d_nbr; a.nbf = c->d_nbf; a.ops = c->d_ops; a.opsf = c->d_opsf; a.perm = c->d_perm;
+  a.lops = c->d_lops; a.lopsf = c->d_lopsf;
   a.a0dt = c->a0dt; a.t = c->t; a.mp = c->mp; a.E = (int)c->E;
   a.inst = c->ext_inst; a.mtab = c->ext_mtab; a.t_dev = c->d_t;
   a.cgeo = c->d_cgeo; a.cgeof = c->d_cgeof; a.cx = c->d_cx; a.minv = c->d_minv; a.minvf = c->d_minvf;
@@ -206,7 +212,11 @@ int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv
   StageFn qs = f32 ? ctx->ks->qstage32 : ctx->ks->qstage;
   StageFn rs = f32 ? ctx->ks->residual32 : ctx->ks->residual;
   KArgs b = a;   // skip flags, instance map and model data of the caller
-  if (ctx->ks->linear && ctx->ks->qstage) {
+  if (ctx->ks->linear && ctx->ks->qstage && (f32 ? ctx->lin32 : ctx->lin64)) {
+    // linear model on affine tensor elements: the nodal form of the same operator
+    b.u = v; b.out = jv;
+    CK((f32 ? ctx->lin32 : ctx->lin64)(b, ctx->d_dq, ctx->stream));
+  } else if (ctx->ks->linear && ctx->ks->qstage) {
     // linear model: J v = R(v) - R(0), the homogeneous operator applied to v
     b.u = v; b.out = ctx->d_dq;
     CK(qs(MODE_HOM, b, ctx->stream));
@@ -998,6 +1008,8 @@ int ldg_destroy(ldg_ctx* ctx) {
   cudaFree(ctx->d_flags); cudaFree(ctx->d_ticket); cudaFree(ctx->d_t);
   cudaFree(ctx->d_colour); cudaFree(ctx->d_blocks); cudaFree(ctx->d_binv); cudaFree(ctx->d_Z);
   cudaFree(ctx->d_probe); cudaFree(ctx->d_jp); cudaFree(ctx->d_status);
+  cudaFree(ctx->d_stage); cudaFree(ctx->d_lops); cudaFree(ctx->d_lopsf);
+  cudaFree(ctx->d_er_xi); cudaFree(ctx->d_er_w); cudaFree(ctx->d_er_B); cudaFree(ctx->d_er_P); cudaFree(ctx->d_l2);
   {
     auto& M = ctx->mlp;
     for (void* p : {(void*)M.Xbf, (void*)M.H1bf, (void*)M.H2bf, (void*)M.wtc, (void*)M.d_err})
@@ -1111,6 +1123,43 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
     std::vector<float> bf(ref.blob.begin(), ref.blob.end());
     CK(cudaMalloc(&ctx->d_opsf, bf.size() * sizeof(float)));
     CK(cudaMemcpy(ctx->d_opsf, bf.data(), bf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  // nodal J.v kernels of the linear models on affine tensor elements (exact when the
+  // quadrature has at least p + 1 points; the face-node permutations equal the face-point
+  // ones when it has exactly p + 1)
+  if ((ctx->etype == LDG_QUAD || ctx->etype == LDG_HEX) && ctx->pg == 0 &&
+      (ctx->model == LDG_POISSON || ctx->model == LDG_CONVDIFF) && o.nq1 == p + 1 && o.jv_form != LDG_JV_STAGE) {
+    const bool conv = ctx->model == LDG_CONVDIFF;
+    ctx->lin64 = lin_launcher(ctx->dim, p, conv, 0);
+    ctx->lin32 = lin_launcher(ctx->dim, p, conv, 1);
+    std::vector<double> lb;
+    if (ctx->lin64 && ctx->lin32 && build_lin_ops(p, lb, err)) {
+      std::vector<float> lf(lb.begin(), lb.end());
+      CK(cudaMalloc(&ctx->d_lops, lb.size() * sizeof(double)));
+      CK(cudaMemcpy(ctx->d_lops, lb.data(), lb.size() * sizeof(double), cudaMemcpyHostToDevice));
+      CK(cudaMalloc(&ctx->d_lopsf, lf.size() * sizeof(float)));
+      CK(cudaMemcpy(ctx->d_lopsf, lf.data(), lf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+      ctx->lin64 = ctx->lin32 = nullptr;
+    }
+  }
+  // the same on triangles and tetrahedra, whose stage kernels integrate exactly with at
+  // least p + 2 collapsed points per direction
+  if ((ctx->etype == LDG_TRI || ctx->etype == LDG_TET) && (ctx->model == LDG_POISSON || ctx->model == LDG_CONVDIFF) &&
+      o.nq1 >= p + 2 && o.jv_form != LDG_JV_STAGE) {
+    const bool conv = ctx->model == LDG_CONVDIFF;
+    ctx->lin64 = lin_simplex_launcher(ctx->etype, p, conv, 0);
+    ctx->lin32 = lin_simplex_launcher(ctx->etype, p, conv, 1);
+    std::vector<double> lb;
+    if (ctx->lin64 && ctx->lin32 && build_lin_simplex_ops(ctx->etype, p, lb, err)) {
+      std::vector<float> lf(lb.begin(), lb.end());
+      CK(cudaMalloc(&ctx->d_lops, lb.size() * sizeof(double)));
+      CK(cudaMemcpy(ctx->d_lops, lb.data(), lb.size() * sizeof(double), cudaMemcpyHostToDevice));
+      CK(cudaMalloc(&ctx->d_lopsf, lf.size() * sizeof(float)));
+      CK(cudaMemcpy(ctx->d_lopsf, lf.data(), lf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+      ctx->lin64 = ctx->lin32 = nullptr;
+    }
   }
   CK(cudaMemcpy(ctx->d_geo, mp_.geo.data(), mp_.geo.size() * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_nbr, mp_.nbr.data(), mp_.nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1241,6 +1290,42 @@ int ldg_jvp(ldg_ctx* ctx, const double* u, const double* v, double* jv) {
 int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u, const double* v, double* jv) {
   if (!ctx || !ctx->ks || !u || !v || !jv || (precision != LDG_FP64 && precision != LDG_FP32)) return LDG_ERR_ARG;
   return jvp_args(ctx, base_args(ctx), u, v, jv, precision);
+}
+
+const char* ldg_jv_describe(const ldg_ctx* ctx, int precision) {
+  if (!ctx || !ctx->ks) return "";
+  static thread_local std::string s;
+  const bool f32 = precision == LDG_FP32;
+  static const char* el[] = {"tri", "quad", "hex", "tet"};
+  static const char* md[] = {"poisson", "convdiff", "euler", "ns"};
+  const std::string what = std::string(el[ctx->etype]) + (ctx->pg ? " curved" : "") + " p=" + std::to_string(ctx->p) +
+                           " nq=" + std::to_string(ctx->nq) + " " + md[ctx->model] + (f32 ? " fp32" : " fp64");
+  if (ctx->ks->linear && (f32 ? ctx->lin32 : ctx->lin64))
+    s = std::string(ctx->etype == LDG_TRI || ctx->etype == LDG_TET ? "k_sim_q + k_sim_r [" : "k_lin_q + k_lin_r [") +
+        what + ", q scratch " + (f32 ? "fp32" : "fp64") + "]";
+  else if (ctx->ks->qstage)
+    s = std::string(ctx->pg ? "k_qstage_curved" : "k_qstage") + " + k_residual [" + what + ", tile " +
+        std::to_string(ctx->ks->tile) + "]";
+  else
+    s = "k_residual [" + what + ", tile " + std::to_string(ctx->ks->tile) + "]";
+  return s.c_str();
+}
+
+int ldg_jvp_host(ldg_ctx* ctx, int precision, const double* u_host, const double* v_host, double* jv_host) {
+  if (!ctx || !ctx->ks || !v_host || !jv_host || (precision != LDG_FP64 && precision != LDG_FP32)) return LDG_ERR_ARG;
+  if (!u_host && !ctx->ks->linear)
+    return fail(ctx, LDG_ERR_ARG, "ldg_jvp_host: u_host may be NULL only for linear models");
+  const size_t n = (size_t)ctx->ndof, bytes = n * sizeof(double);
+  if (!ctx->d_stage) CK(cudaMalloc(&ctx->d_stage, 3 * bytes));
+  double *du = ctx->d_stage, *dv = du + n, *djv = dv + n;
+  if (u_host) CK(cudaMemcpyAsync(du, u_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(dv, v_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  // a linear model's J.v does not read u: the direction stands in for it
+  int rc = jvp_args(ctx, base_args(ctx), u_host ? du : dv, dv, djv, precision);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(jv_host, djv, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LDG_OK;
 }
 
 // out = sum_k c[k] x[k] over the non-null x[k] (k < 4); out may alias none of them
@@ -1690,12 +1775,17 @@ int ldg_jvp_noalloc(ldg_ctx* ctx, const double* u, const double* v, double* jv) 
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(ctx, LDG_ERR_ARG, "ldg_jvp_noalloc: device ordinal out of range");
-  if (!noalloc_addr[dev]) {
-    void* p = nullptr;
-    CK(cudaGetSymbolAddress(&p, noalloc_scratch));
-    noalloc_addr[dev] = (double*)p;
+  double* dq = noalloc_addr[dev].load(std::memory_order_acquire);
+  if (!dq) {
+    std::lock_guard<std::mutex> hold(noalloc_lock);
+    dq = noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!dq) {
+      void* p = nullptr;
+      CK(cudaGetSymbolAddress(&p, noalloc_scratch));
+      dq = (double*)p;
+      noalloc_addr[dev].store(dq, std::memory_order_release);
+    }
   }
-  double* dq = noalloc_addr[dev];
   // each q-stage overwrites every entry that is later read: nothing to clear
   KArgs a = base_args(ctx);
   a.u = v; a.out = dq;

@@ -41,6 +41,15 @@ struct ldg_ctx {
   double* d_radd = nullptr;    // DIRK stage: constant added to the residual (active when radd_on)
   bool radd_on = false;
   double* d_dirk = nullptr;    // DIRK work: u^n, then the stages' spatial residuals and slopes
+  // nodal J.v kernels of linear models on affine tensor elements (null when not applicable)
+  ldg::LinFn lin64 = nullptr, lin32 = nullptr;
+  double* d_lops = nullptr;
+  float* d_lopsf = nullptr;
+  double* d_stage = nullptr;   // ldg_jvp_host: device copies of u, v and J.v (3 n_dof, first use)
+  // L2 projection / error rule (built on first use): points, weights, basis values,
+  // projection operator, and per-element error partials [E][4]
+  int er_nqp = 0;
+  double *d_er_xi = nullptr, *d_er_w = nullptr, *d_er_B = nullptr, *d_er_P = nullptr, *d_l2 = nullptr;
   // time scheme
   int scheme = LDG_STEADY;
   double t = 0.0, dt = 1.0, a0dt = 0.0;

@@ -221,11 +221,12 @@ __device__ void exact_state(const ModelParams& mp, int ncu, const double* x, dou
   g[0] = u;
 }
 
-// Source s of Eq. 1b such that div(beta u - kappa grad u) = s for the scalar cases.
+// Gradient and Laplacian of the exact solution of the scalar cases.
 template <int DIM>
-__device__ double source_term(const ModelParams& mp, bool conv, const double* x) {
+__device__ void scalar_derivs(const ModelParams& mp, const double* x, double* grad, double& lap) {
   const double PI = 3.141592653589793238462643;
-  double grad[3] = {0.0, 0.0, 0.0}, lap = 0.0;
+  grad[0] = grad[1] = grad[2] = 0.0;
+  lap = 0.0;
   switch (mp.cas) {
     case C_SINSIN: {
       double sn[3], cs[3];
@@ -268,6 +269,13 @@ __device__ double source_term(const ModelParams& mp, bool conv, const double* x)
     case C_LINEAR: { grad[0] = 0.5; grad[1] = -0.3; if (DIM == 3) grad[DIM - 1] = 0.25; break; }
     default: break;
   }
+}
+
+// Source s of Eq. 1b such that div(beta u - kappa grad u) = s for the scalar cases.
+template <int DIM>
+__device__ double source_term(const ModelParams& mp, bool conv, const double* x) {
+  double grad[3], lap;
+  scalar_derivs<DIM>(mp, x, grad, lap);
   double bg = 0.0;
   if (conv) for (int d = 0; d < DIM; ++d) bg += mp.beta[d] * grad[d];
   return bg - mp.kappa * lap;

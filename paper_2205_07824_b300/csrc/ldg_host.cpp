@@ -327,6 +327,244 @@ bool build_ref_ops(int etype, int p, int nq, RefOps& R, std::string& err) {
   return true;
 }
 
+bool build_lin_ops(int p, std::vector<double>& blob, std::string& err) {
+  if (p < 1 || p > 8) { err = "unsupported order"; return false; }
+  const int n1 = p + 1;
+  std::vector<double> xn, gx, gw;
+  gauss_lobatto(n1, xn);
+  gauss_legendre(n1, gx, gw);
+  Bary bl(xn);
+  std::vector<double> Dn = bl.dmat();
+  std::vector<double> B(n1 * n1), D(n1 * n1, 0.0);
+  for (int q = 0; q < n1; ++q) bl.values(gx[q], &B[q * n1]);
+  for (int q = 0; q < n1; ++q)
+    for (int j = 0; j < n1; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < n1; ++i) s += Dn[i * n1 + j] * B[q * n1 + i];
+      D[q * n1 + j] = s;
+    }
+  std::vector<double> M1(n1 * n1, 0.0), C(n1 * n1, 0.0), M1i;
+  for (int q = 0; q < n1; ++q)
+    for (int i = 0; i < n1; ++i)
+      for (int j = 0; j < n1; ++j) {
+        M1[i * n1 + j] += gw[q] * B[q * n1 + i] * B[q * n1 + j];
+        C[i * n1 + j] += gw[q] * D[q * n1 + i] * B[q * n1 + j];
+      }
+  if (!invert(M1, n1, M1i)) { err = "singular 1-D mass matrix"; return false; }
+  blob.clear();
+  blob.insert(blob.end(), Dn.begin(), Dn.end());
+  blob.insert(blob.end(), M1.begin(), M1.end());
+  blob.insert(blob.end(), C.begin(), C.end());
+  for (int i = 0; i < n1; ++i) blob.push_back(M1i[i * n1]);
+  for (int i = 0; i < n1; ++i) blob.push_back(M1i[i * n1 + n1 - 1]);
+  return true;
+}
+
+namespace {
+// local node of face-node j on face f (numbering of tri_basis / tet_basis)
+int simplex_face_node(int etype, int p, int f, int j) {
+  auto tri_idx = [p](int i, int jj) { return jj * (p + 1) - jj * (jj - 1) / 2 + i; };
+  if (etype == E_TRI) {
+    if (f == 0) return tri_idx(j, 0);
+    if (f == 1) return tri_idx(p - j, j);
+    return tri_idx(0, p - j);
+  }
+  int b = 0, a = j;
+  while (a > p - b) { a -= p + 1 - b; ++b; }
+  const int A = f == 0 ? 1 : 0, B = f <= 1 ? 2 : 1, C = f == 3 ? 2 : 3;
+  int l[4] = {0, 0, 0, 0};
+  l[A] = p - a - b; l[B] = a; l[C] = b;
+  int off = 0;
+  for (int kk = 0; kk < l[3]; ++kk) off += (p - kk + 1) * (p - kk + 2) / 2;
+  const int q = p - l[3];
+  return off + l[2] * (q + 1) - l[2] * (l[2] - 1) / 2 + l[1];
+}
+}  // namespace
+
+bool build_lin_simplex_ops(int etype, int p, std::vector<double>& blob, std::string& err) {
+  if ((etype != E_TRI && etype != E_TET) || p < 1 || p > 6) { err = "unsupported simplex order"; return false; }
+  const int dim = etype == E_TRI ? 2 : 3, nf = dim + 1;
+  const int npe = etype == E_TRI ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6;
+  const int nfn = etype == E_TRI ? p + 1 : (p + 1) * (p + 2) / 2;
+  const int lda = npe | 1, ldl = nfn | 1;
+  const int nq = p + 3;   // collapsed Gauss rule, exact beyond degree 2p
+  std::vector<double> gx, gw;
+  gauss_legendre(nq, gx, gw);
+  // volume: M[i][j] = int phi_i phi_j, C_k[i][j] = int phi_j d_k phi_i
+  std::vector<double> M((size_t)npe * npe, 0.0), C((size_t)dim * npe * npe, 0.0);
+  std::vector<double> phi(npe), d0(npe), d1(npe), d2(npe);
+  const int nqv = dim == 2 ? nq * nq : nq * nq * nq;
+  for (int q = 0; q < nqv; ++q) {
+    const int a = q % nq, b = (q / nq) % nq, c = q / (nq * nq);
+    double w;
+    if (dim == 2) {
+      tri_basis(p, 0.5 * (1.0 + gx[a]) * (1.0 - gx[b]) - 1.0, gx[b], phi.data(), d0.data(), d1.data());
+      w = gw[a] * gw[b] * 0.5 * (1.0 - gx[b]);
+    } else {
+      const double x[3] = {(1.0 + gx[a]) * (1.0 - gx[b]) * (1.0 - gx[c]) / 4.0 - 1.0,
+                           (1.0 + gx[b]) * (1.0 - gx[c]) / 2.0 - 1.0, gx[c]};
+      tet_basis(p, x, phi.data(), d0.data(), d1.data(), d2.data());
+      w = gw[a] * gw[b] * gw[c] * (1.0 - gx[b]) * (1.0 - gx[c]) * (1.0 - gx[c]) / 8.0;
+    }
+    const double* dk[3] = {d0.data(), d1.data(), d2.data()};
+    for (int i = 0; i < npe; ++i)
+      for (int j = 0; j < npe; ++j) {
+        M[(size_t)i * npe + j] += w * phi[i] * phi[j];
+        for (int k = 0; k < dim; ++k) C[((size_t)k * npe + i) * npe + j] += w * phi[j] * dk[k][i];
+      }
+  }
+  std::vector<double> Mi;
+  if (!invert(M, npe, Mi)) { err = "singular reference mass matrix"; return false; }
+  // nodal derivatives Dn_k[n][m] = d_k phi_m (x_n)
+  std::vector<double> xn;
+  {
+    RefOps tmp;
+    tmp.etype = etype; tmp.p = p; tmp.npe = npe; tmp.dim = dim;
+    if (etype == E_TET) {
+      // tet_basis numbering: k outer, then j, then i
+      for (int k = 0; k <= p; ++k)
+        for (int j = 0; j + k <= p; ++j)
+          for (int i = 0; i + j + k <= p; ++i) {
+            xn.push_back(-1.0 + 2.0 * i / p); xn.push_back(-1.0 + 2.0 * j / p); xn.push_back(-1.0 + 2.0 * k / p);
+          }
+    } else {
+      for (int j = 0; j <= p; ++j)
+        for (int i = 0; i + j <= p; ++i) { xn.push_back(-1.0 + 2.0 * i / p); xn.push_back(-1.0 + 2.0 * j / p); }
+    }
+  }
+  std::vector<double> Dn((size_t)dim * npe * npe, 0.0);
+  for (int n = 0; n < npe; ++n) {
+    if (dim == 2) tri_basis(p, xn[2 * n], xn[2 * n + 1], phi.data(), d0.data(), d1.data());
+    else tet_basis(p, &xn[3 * n], phi.data(), d0.data(), d1.data(), d2.data());
+    const double* dk[3] = {d0.data(), d1.data(), d2.data()};
+    for (int k = 0; k < dim; ++k)
+      for (int m = 0; m < npe; ++m) Dn[((size_t)k * npe + n) * npe + m] = dk[k][m];
+  }
+  // face mass in the face parameters (the measure the geometry's sJ scales):
+  // triangles: the equispaced Lagrange basis on s in [-1, 1]; tetrahedra: the triangle basis
+  std::vector<double> MF((size_t)nfn * nfn, 0.0);
+  if (dim == 2) {
+    std::vector<double> en(p + 1), l(p + 1);
+    for (int t = 0; t <= p; ++t) en[t] = -1.0 + 2.0 * t / p;
+    Bary eb(en);
+    for (int k = 0; k < nq; ++k) {
+      eb.values(gx[k], l.data());
+      for (int a = 0; a <= p; ++a)
+        for (int b = 0; b <= p; ++b) MF[a * nfn + b] += gw[k] * l[a] * l[b];
+    }
+  } else {
+    std::vector<double> fp(nfn), e1(nfn), e2(nfn);
+    for (int b = 0; b < nq; ++b)
+      for (int a = 0; a < nq; ++a) {
+        tri_basis(p, (1.0 + gx[a]) * (1.0 - gx[b]) / 2.0 - 1.0, gx[b], fp.data(), e1.data(), e2.data());
+        const double w = gw[a] * gw[b] * (1.0 - gx[b]) / 2.0;
+        for (int i = 0; i < nfn; ++i)
+          for (int j = 0; j < nfn; ++j) MF[(size_t)i * nfn + j] += w * fp[i] * fp[j];
+      }
+  }
+  // lift of face f: M^{-1} E_f M_f
+  std::vector<double> LIFT((size_t)nf * npe * nfn, 0.0);
+  for (int f = 0; f < nf; ++f)
+    for (int n = 0; n < npe; ++n)
+      for (int j = 0; j < nfn; ++j) {
+        double s = 0.0;
+        for (int b = 0; b < nfn; ++b) s += Mi[(size_t)n * npe + simplex_face_node(etype, p, f, b)] * MF[(size_t)b * nfn + j];
+        LIFT[((size_t)f * npe + n) * nfn + j] = s;
+      }
+  // padded layout: DN, C (dim x npe x lda), M (npe x lda), LIFT (nf x npe x ldl), MF (nfn x ldl)
+  blob.assign((size_t)(2 * dim + 1) * npe * lda + (size_t)nf * npe * ldl + (size_t)nfn * ldl, 0.0);
+  size_t o = 0;
+  for (int k = 0; k < dim; ++k)
+    for (int n = 0; n < npe; ++n)
+      for (int m = 0; m < npe; ++m) blob[o + ((size_t)k * npe + n) * lda + m] = Dn[((size_t)k * npe + n) * npe + m];
+  o += (size_t)dim * npe * lda;
+  for (int k = 0; k < dim; ++k)
+    for (int n = 0; n < npe; ++n)
+      for (int m = 0; m < npe; ++m) blob[o + ((size_t)k * npe + n) * lda + m] = C[((size_t)k * npe + n) * npe + m];
+  o += (size_t)dim * npe * lda;
+  for (int n = 0; n < npe; ++n)
+    for (int m = 0; m < npe; ++m) blob[o + (size_t)n * lda + m] = M[(size_t)n * npe + m];
+  o += (size_t)npe * lda;
+  for (int f = 0; f < nf; ++f)
+    for (int n = 0; n < npe; ++n)
+      for (int j = 0; j < nfn; ++j) blob[o + ((size_t)f * npe + n) * ldl + j] = LIFT[((size_t)f * npe + n) * nfn + j];
+  o += (size_t)nf * npe * ldl;
+  for (int i = 0; i < nfn; ++i)
+    for (int j = 0; j < nfn; ++j) blob[o + (size_t)i * ldl + j] = MF[(size_t)i * nfn + j];
+  return true;
+}
+
+bool build_err_rule(int etype, int p, int nqe, ErrRule& R, std::string& err) {
+  if (p < 1 || p > 8 || nqe < 1 || nqe > 12) { err = "unsupported order for the error rule"; return false; }
+  std::vector<double> gx, gw;
+  gauss_legendre(nqe, gx, gw);
+  int dim = (etype == E_QUAD || etype == E_TRI) ? 2 : 3;
+  int npe;
+  if (etype == E_TRI) npe = (p + 1) * (p + 2) / 2;
+  else if (etype == E_TET) npe = (p + 1) * (p + 2) * (p + 3) / 6;
+  else npe = dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1);
+  int nqp = dim == 2 ? nqe * nqe : nqe * nqe * nqe;
+  R.nqp = nqp;
+  R.xi.assign((size_t)nqp * dim, 0.0);
+  R.w.assign(nqp, 0.0);
+  R.B.assign((size_t)nqp * npe, 0.0);
+  // points and weights: tensor Gauss rules, collapsed (Duffy) on simplices
+  for (int q = 0; q < nqp; ++q) {
+    const int a = q % nqe, b = (q / nqe) % nqe, c = q / (nqe * nqe);
+    double* x = &R.xi[(size_t)q * dim];
+    if (etype == E_TRI) {
+      x[0] = 0.5 * (1.0 + gx[a]) * (1.0 - gx[b]) - 1.0;
+      x[1] = gx[b];
+      R.w[q] = gw[a] * gw[b] * 0.5 * (1.0 - gx[b]);
+    } else if (etype == E_TET) {
+      x[0] = (1.0 + gx[a]) * (1.0 - gx[b]) * (1.0 - gx[c]) / 4.0 - 1.0;
+      x[1] = (1.0 + gx[b]) * (1.0 - gx[c]) / 2.0 - 1.0;
+      x[2] = gx[c];
+      R.w[q] = gw[a] * gw[b] * gw[c] * (1.0 - gx[b]) * (1.0 - gx[c]) * (1.0 - gx[c]) / 8.0;
+    } else {
+      x[0] = gx[a]; x[1] = gx[b];
+      R.w[q] = gw[a] * gw[b];
+      if (dim == 3) { x[2] = gx[c]; R.w[q] *= gw[c]; }
+    }
+  }
+  // basis values at the points
+  std::vector<double> d1(npe), d2(npe), d3(npe);
+  if (etype == E_TRI) {
+    for (int q = 0; q < nqp; ++q) tri_basis(p, R.xi[2 * q], R.xi[2 * q + 1], &R.B[(size_t)q * npe], d1.data(), d2.data());
+  } else if (etype == E_TET) {
+    for (int q = 0; q < nqp; ++q) tet_basis(p, &R.xi[3 * q], &R.B[(size_t)q * npe], d1.data(), d2.data(), d3.data());
+  } else {
+    const int n1 = p + 1;
+    std::vector<double> xn;
+    gauss_lobatto(n1, xn);
+    Bary bl(xn);
+    std::vector<double> l(3 * n1);
+    for (int q = 0; q < nqp; ++q) {
+      for (int d = 0; d < dim; ++d) bl.values(R.xi[(size_t)q * dim + d], &l[d * n1]);
+      for (int n = 0; n < npe; ++n) {
+        const int id[3] = {n % n1, (n / n1) % n1, n / (n1 * n1)};
+        double v = 1.0;
+        for (int d = 0; d < dim; ++d) v *= l[d * n1 + id[d]];
+        R.B[(size_t)q * npe + n] = v;
+      }
+    }
+  }
+  // projection operator P = Mref^{-1} B^T W
+  std::vector<double> M((size_t)npe * npe, 0.0), Mi;
+  for (int q = 0; q < nqp; ++q)
+    for (int i = 0; i < npe; ++i)
+      for (int j = 0; j < npe; ++j) M[(size_t)i * npe + j] += R.w[q] * R.B[(size_t)q * npe + i] * R.B[(size_t)q * npe + j];
+  if (!invert(M, npe, Mi)) { err = "singular reference mass matrix"; return false; }
+  R.P.assign((size_t)npe * nqp, 0.0);
+  for (int i = 0; i < npe; ++i)
+    for (int q = 0; q < nqp; ++q) {
+      double s = 0.0;
+      for (int j = 0; j < npe; ++j) s += Mi[(size_t)i * npe + j] * R.B[(size_t)q * npe + j];
+      R.P[(size_t)i * nqp + q] = s * R.w[q];
+    }
+  return true;
+}
+
 void ref_nodes(const RefOps& R, std::vector<double>& out) {
   out.assign((size_t)R.npe * R.dim, 0.0);
   if (R.etype == E_TET) {

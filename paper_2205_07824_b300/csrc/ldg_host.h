@@ -48,6 +48,27 @@ struct CurvedPrep {
 };
 bool prepare_curved(const RefOps& ref, int64_t E, int pg, const double* xgeo, CurvedPrep& out, std::string& err);
 
+// A richer reference rule for L2 projections and errors: Gauss with nqe points per
+// direction (collapsed on simplices). xi [nqp][dim] points, w [nqp] weights, B [nqp][npe]
+// basis values, P = Mref^{-1} B^T W [npe][nqp] the reference L2 projection.
+struct ErrRule {
+  int nqp = 0;
+  std::vector<double> xi, w, B, P;
+};
+bool build_err_rule(int etype, int p, int nqe, ErrRule& out, std::string& err);
+
+// 1-D operators of the nodal linear J.v kernels for order p (Gauss-Lobatto basis l_i):
+// Dn[i][j] = l_j'(x_i), M1[i][j] = int l_i l_j, C[i][j] = int l_i' l_j (Gauss rule of
+// p + 1 points, exact), then columns 0 and p of M1^{-1}.
+bool build_lin_ops(int p, std::vector<double>& blob, std::string& err);
+
+// Dense reference operators of the nodal linear J.v kernels on triangles and
+// tetrahedra (equispaced nodes), exact integrals, rows padded to odd lengths
+// (lda = n_pe | 1, ldl = n_fn | 1): Dn_k[n][m] = d_k phi_m(x_n); C_k[i][j] =
+// int phi_j d_k phi_i; M; LIFT_f = M^{-1} E_f M_f (face f's nodes); the face mass M_f
+// in face-node order (the same on every face).
+bool build_lin_simplex_ops(int etype, int p, std::vector<double>& blob, std::string& err);
+
 // Reference coordinates of face point k of face f and of volume point q (for host-side projection).
 void ref_face_point(const RefOps& ref, int f, int k, double* xi);
 void ref_nodes(const RefOps& ref, std::vector<double>& xn);   // [npe][dim]

@@ -62,6 +62,8 @@ struct KArgs {
   const double* ops;          // reference operator blob (element traits), FP64
   const float* opsf;          // the same blob in FP32 (for FP32-compute instances)
   const unsigned char* perm;  // [n_orient][NFQ] face-point permutations
+  const double* lops;         // 1-D operators of the nodal linear J.v kernels (ldg_linear.cuh), FP64 ...
+  const float* lopsf;         // ... and FP32
   const int* skip;            // optional: the kernel returns at once when *skip != 0
   int blk_col;                // MODE_JV block extraction (models without q): -1 off; else the element's own tangent is
                               // unit vector blk_col, neighbours' tangents are zero, and column blk_col

@@ -159,4 +159,12 @@ template <class TL> void register_tet_t(std::vector<KernelSet>& reg);
 template <class TL> void register_curved_gas_t(std::vector<KernelSet>& reg);
 void register_all(std::vector<KernelSet>& reg);
 
+// Nodal J.v kernels of the linear models on affine quadrilaterals / hexahedra
+// (ldg_linear.cuh): both stages, q of the direction stored in qbuf.
+typedef cudaError_t (*LinFn)(const KArgs& a, void* qbuf, cudaStream_t s);
+// The launcher for (dim, p, convection?, precision LDG_FP64 / LDG_FP32), or null.
+LinFn lin_launcher(int dim, int p, bool conv, int prec);
+// The same on triangles (etype 0) and tetrahedra (etype 3), or null.
+LinFn lin_simplex_launcher(int etype, int p, bool conv, int prec);
+
 }  // namespace ldg

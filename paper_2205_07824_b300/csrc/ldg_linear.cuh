@@ -1,0 +1,598 @@
+// Nodal form of the homogeneous operator (J.v) of the linear diffusion models
+// (Poisson, convection-diffusion) on affine quadrilaterals and hexahedra with
+// Gauss-Lobatto nodes (Section 2.2, Eq. 1a-1b; Section 3.3's J.v).
+//
+// For a linear model every integrand of R(v) - R(0) is a polynomial of degree <= 2p
+// on an affine element, and the quadrature of the stage kernels (p + 1 Gauss points per
+// direction) integrates it exactly. The same operator therefore has an exact form on
+// the nodal values alone, with the 1-D matrices of the Gauss-Lobatto basis l_i:
+//   M1[i][j] = int l_i l_j,   C[i][j] = int l_i' l_j,   Dn[i][j] = l_j'(x_i),
+// and the columns L0 = M1^{-1} e_0, L1 = M1^{-1} e_p:
+//
+//  q-stage (Eq. 1a, strong form): the face mass matrix of face f is sJ (M1 x M1), so
+//  lifting the weighted trace difference and applying the element's inverse mass matrix
+//  M^{-1} = (M1 x M1 x M1)^{-1} / det J cancels the tangential factors:
+//    q_d = -sum_k Jinv[k][d] D_k v + sum_f n_{f,d} (sJ_f / det J) L_f(i_axis) Delta_f,
+//    Delta_f = v- - vhat at the face nodes ((v- - v+)/2 inside, v- on Dirichlet faces).
+//  residual (Eq. 1b): with the nodal flux g_k = det J sum_d Jinv[k][d] (beta_d v + kappa q_d),
+//    R = -(C x M1 x M1) g_0 - (M1 x C x M1) g_1 - (M1 x M1 x C) g_2
+//        + sum_f sJ_f (M1 x M1) Fhat_f + a0/dt det J (M1 x M1 x M1) v,
+//    Fhat_f = beta.n v_upwind + kappa/2 (q- + q+).n + tau (v- - v+) at the face nodes
+//    (Dirichlet faces: beta.n v- if beta.n >= 0, kappa q-.n + tau v-).
+// Each stage is one kernel with one thread per node; contractions along an axis read
+// the node's line from shared memory. q of the direction is stored in QT (double, or
+// float for the FP32-arithmetic J.v: it is internal scratch of the product).
+#pragma once
+#include "ldg_kernels.cuh"
+
+namespace ldg {
+
+// Blob of 1-D operators (N1 = p + 1 values per axis): Dn, M1, C, then L0 and L1.
+template <int N1> struct LinOff {
+  static constexpr int DN = 0, M1 = N1 * N1, C = 2 * N1 * N1, L = 3 * N1 * N1, SIZE = 3 * N1 * N1 + 2 * N1;
+};
+
+// Elements per CTA (one thread per node, elements packed back to back) and threads.
+template <int DIM, int N1> struct LinShape {
+  static constexpr int NPE = ipow(N1, DIM), NFN = ipow(N1, DIM - 1), NF = 2 * DIM;
+  static constexpr int NE = NPE >= 256 ? 1 : 256 / NPE;
+  static constexpr int NT = (NE * NPE + 31) / 32 * 32;
+  static constexpr int GEO = Geo<DIM>::size(NF);
+};
+
+// local node of face-node j on face f = 2 axis + side (free axes ascending, first fastest)
+template <int DIM, int N1> __device__ __forceinline__ int lin_face_node(int f, int j) {
+  const int ax = f >> 1, fix = (f & 1) ? N1 - 1 : 0;
+  if constexpr (DIM == 2) return ax == 0 ? fix + N1 * j : j + N1 * fix;
+  else {
+    const int a = j % N1, b = j / N1;
+    if (ax == 0) return fix + N1 * (a + N1 * b);
+    if (ax == 1) return a + N1 * (fix + N1 * b);
+    return a + N1 * (b + N1 * fix);
+  }
+}
+// face-node index of node (i0, i1, i2) on a face of axis ax
+template <int DIM, int N1> __device__ __forceinline__ int lin_face_index(int ax, const int* id) {
+  if constexpr (DIM == 2) return id[1 - ax];
+  else return ax == 0 ? id[1] + N1 * id[2] : (ax == 1 ? id[0] + N1 * id[2] : id[0] + N1 * id[1]);
+}
+
+template <class R> __device__ __forceinline__ const R* lin_ops(const KArgs& a) {
+  if constexpr (sizeof(R) == 8) return (const R*)a.lops;
+  else return (const R*)a.lopsf;
+}
+
+// ------------------------------------------------------------------ q-stage
+template <int DIM, int N1, class R, class QT>
+__global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_q(KArgs a) {
+  typedef LinShape<DIM, N1> S;
+  typedef LinOff<N1> O;
+  typedef Geo<DIM> G;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NF = S::NF, NE = S::NE, NT = S::NT, GEO = S::GEO;
+  if (a.skip && *a.skip) return;
+  const int e0 = blockIdx.x * NE;
+  const int ne = min(NE, a.E - e0);
+  if (!cta_active(a, e0, ne)) return;
+  __shared__ R ops[O::SIZE];
+  __shared__ R Gs[NE][GEO];
+  __shared__ R Vs[NE][NPE];
+  __shared__ R Ds[NE][NF][NFN];
+  const int t = threadIdx.x;
+  const R* lo = lin_ops<R>(a);
+  for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
+  for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
+  const double* v = (const double*)a.u;
+  const int e = t / NPE, n = t - e * NPE;
+  const bool own = e < ne;
+  if (own) Vs[e][n] = R(v[(size_t)(e0 + e) * NPE + n]);
+  __syncthreads();
+
+  // Delta_f (sJ_f / det J) at the face nodes
+  for (int it = t; it < NE * NF * NFN; it += NT) {
+    const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+    R d = R(0);
+    if (el < ne) {
+      const R vm = Vs[el][lin_face_node<DIM, N1>(f, j)];
+      const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
+      if (nb >= 0) {
+        const int code = a.nbf[(size_t)(e0 + el) * NF + f];
+        const int jn = a.perm[(code >> 3) * NFN + j];
+        const R vp = R(v[(size_t)nb * NPE + lin_face_node<DIM, N1>(code & 7, jn)]);
+        d = R(0.5) * (vm - vp);
+      } else {
+        d = vm;
+      }
+      d *= Gs[el][G::FACE + f * (DIM + 1) + DIM] / Gs[el][G::DETJ];
+    }
+    Ds[el][f][j] = d;
+  }
+  __syncthreads();
+  if (!own) return;
+
+  const int id[3] = {n % N1, (n / N1) % N1, DIM == 3 ? n / (N1 * N1) : 0};
+  constexpr int STR[3] = {1, N1, N1 * N1};
+  R gk[DIM];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const R* line = &Vs[e][n - id[k] * STR[k]];
+    const R* dn = ops + O::DN + id[k] * N1;
+    R s = R(0);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) s += dn[m] * line[m * STR[k]];
+    gk[k] = s;
+  }
+  R qd[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    R s = R(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) s -= Gs[e][G::JINV + k * DIM + d] * gk[k];
+    qd[d] = s;
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int ax = f >> 1, side = f & 1;
+    const R lf = ops[O::L + side * N1 + id[ax]] * Ds[e][f][lin_face_index<DIM, N1>(ax, id)];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) qd[d] += Gs[e][G::FACE + f * (DIM + 1) + d] * lf;
+  }
+  QT* q = (QT*)a.out;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) q[((size_t)(e0 + e) * DIM + d) * NPE + n] = QT(qd[d]);
+}
+
+// ----------------------------------------------------------------- residual
+template <int DIM, int N1, bool CONV, class R, class QT>
+__global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_r(KArgs a) {
+  typedef LinShape<DIM, N1> S;
+  typedef LinOff<N1> O;
+  typedef Geo<DIM> G;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NF = S::NF, NE = S::NE, NT = S::NT, GEO = S::GEO;
+  if (a.skip && *a.skip) return;
+  const int e0 = blockIdx.x * NE;
+  const int ne = min(NE, a.E - e0);
+  if (!cta_active(a, e0, ne)) return;
+  __shared__ R ops[O::SIZE];
+  __shared__ R Gs[NE][GEO];
+  __shared__ MPar<R> MPs[NE];
+  __shared__ R Gk[NE][DIM][NPE];      // nodal fluxes g_k, later the axis-1 stage (3-D)
+  __shared__ R Tk[NE][DIM][NPE];      // axis-0 stage
+  __shared__ R Hs[NE][NPE];           // a0/dt det J v (time term)
+  __shared__ R FV[NE][NF][NFN];       // own v at the face nodes, later the first face contraction
+  __shared__ R FQ[NE][NF][NFN];       // own q.n at the face nodes, later the second face contraction
+  __shared__ R FF[NE][NF][NFN];       // sJ Fhat at the face nodes
+  const int t = threadIdx.x;
+  const R* lo = lin_ops<R>(a);
+  for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
+  for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
+  for (int i = t; i < NE; i += NT) MPs[i] = mpar<R>(i < ne ? elem_mp(a, e0 + i) : a.mp);
+  const double* v = (const double*)a.u;
+  const QT* q = (const QT*)a.q;
+  const R a0dt = R(a.a0dt);
+  const bool tterm = a.a0dt != 0.0;
+  const int e = t / NPE, n = t - e * NPE;
+  const bool own = e < ne;
+  const int id[3] = {n % N1, (n / N1) % N1, DIM == 3 ? n / (N1 * N1) : 0};
+  constexpr int STR[3] = {1, N1, N1 * N1};
+  R vn = R(0), qn[DIM];
+  if (own) {
+    vn = R(v[(size_t)(e0 + e) * NPE + n]);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) qn[d] = R(q[((size_t)(e0 + e) * DIM + d) * NPE + n]);
+  }
+  __syncthreads();
+  if (own) {
+    const MPar<R>& mp = MPs[e];
+    R fl[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) fl[d] = CONV ? mp.kappa * qn[d] + mp.beta[d] * vn : mp.kappa * qn[d];
+    const R dj = Gs[e][G::DETJ];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      R s = R(0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) s += Gs[e][G::JINV + k * DIM + d] * fl[d];
+      Gk[e][k][n] = dj * s;
+    }
+    if (tterm) Hs[e][n] = a0dt * dj * vn;
+    // own v and q.n at the face nodes this node lies on
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int ax = f >> 1, fix = (f & 1) ? N1 - 1 : 0;
+      if (id[ax] != fix) continue;
+      const int j = lin_face_index<DIM, N1>(ax, id);
+      R s = R(0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) s += Gs[e][G::FACE + f * (DIM + 1) + d] * qn[d];
+      FV[e][f][j] = vn;
+      FQ[e][f][j] = s;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 1: numerical flux at the face nodes; volume contractions along axis 0
+  for (int it = t; it < NE * NF * NFN; it += NT) {
+    const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+    R fh = R(0);
+    if (el < ne) {
+      const MPar<R>& mp = MPs[el];
+      const R* nrm = &Gs[el][G::FACE + f * (DIM + 1)];
+      const R vm = FV[el][f][j], qmn = FQ[el][f][j];
+      R bn = R(0);
+      if (CONV) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) bn += mp.beta[d] * nrm[d];
+      }
+      const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
+      if (nb >= 0) {
+        const int code = a.nbf[(size_t)(e0 + el) * NF + f];
+        const int jn = a.perm[(code >> 3) * NFN + j];
+        const int node = lin_face_node<DIM, N1>(code & 7, jn);
+        const R vp = R(v[(size_t)nb * NPE + node]);
+        R qpn = R(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) qpn += nrm[d] * R(q[((size_t)nb * DIM + d) * NPE + node]);
+        fh = mp.tau * (vm - vp) + (R(0.5) * mp.kappa) * (qmn + qpn);
+        if (CONV) fh += bn * (bn >= R(0) ? vm : vp);
+      } else {
+        fh = mp.tau * vm + mp.kappa * qmn;
+        if (CONV && bn >= R(0)) fh += bn * vm;
+      }
+      fh *= nrm[DIM];
+    }
+    FF[el][f][j] = fh;
+  }
+  R rv = R(0);
+  if (own) {
+    const R* cr = ops + O::C + id[0] * N1;
+    const R* mr = ops + O::M1 + id[0] * N1;
+    const int b0 = n - id[0];
+    R ta = R(0), tb = R(0), tc = R(0);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) {
+      ta += cr[m] * Gk[e][0][b0 + m];
+      tb += mr[m] * Gk[e][1][b0 + m];
+      if constexpr (DIM == 3) tc += mr[m] * Gk[e][2][b0 + m];
+    }
+    if (tterm) {
+#pragma unroll
+      for (int m = 0; m < N1; ++m) ta -= mr[m] * Hs[e][b0 + m];
+    }
+    Tk[e][0][n] = ta;
+    Tk[e][1][n] = tb;
+    if constexpr (DIM == 3) Tk[e][2][n] = tc;
+  }
+  __syncthreads();
+
+  // ---- phase 2: face mass along the first free axis; volume along axis 1
+  for (int it = t; it < NE * NF * NFN; it += NT) {
+    const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+    const int t0 = j % N1, rest = j - t0;
+    const R* mr = ops + O::M1 + t0 * N1;
+    R s = R(0);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) s += mr[m] * FF[el][f][rest + m];
+    FV[el][f][j] = s;
+  }
+  if (own) {
+    const R* cr = ops + O::C + id[1] * N1;
+    const R* mr = ops + O::M1 + id[1] * N1;
+    const int b1 = n - id[1] * N1;
+    if constexpr (DIM == 2) {
+      R s = R(0);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) s += mr[m] * Tk[e][0][b1 + m * N1] + cr[m] * Tk[e][1][b1 + m * N1];
+      rv = -s;
+    } else {
+      R sa = R(0), sc = R(0);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        sa += mr[m] * Tk[e][0][b1 + m * N1] + cr[m] * Tk[e][1][b1 + m * N1];
+        sc += mr[m] * Tk[e][2][b1 + m * N1];
+      }
+      Gk[e][0][n] = sa;
+      Gk[e][1][n] = sc;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 3 (3-D): face mass along the second free axis; volume along axis 2
+  R (*FL)[NF][NFN] = FV;   // final face moments (2-D: after the one tangential contraction)
+  if constexpr (DIM == 3) {
+    for (int it = t; it < NE * NF * NFN; it += NT) {
+      const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+      const int t0 = j % N1, t1 = j / N1;
+      const R* mr = ops + O::M1 + t1 * N1;
+      R s = R(0);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) s += mr[m] * FV[el][f][t0 + m * N1];
+      FQ[el][f][j] = s;
+    }
+    if (own) {
+      const R* cr = ops + O::C + id[2] * N1;
+      const R* mr = ops + O::M1 + id[2] * N1;
+      const int b2 = n - id[2] * N1 * N1;
+      R s = R(0);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) s += mr[m] * Gk[e][0][b2 + m * N1 * N1] + cr[m] * Gk[e][1][b2 + m * N1 * N1];
+      rv = -s;
+    }
+    __syncthreads();
+    FL = FQ;
+  }
+
+  // ---- store: volume part plus the face moments of the faces this node lies on
+  if (!own) return;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int ax = f >> 1, fix = (f & 1) ? N1 - 1 : 0;
+    if (id[ax] == fix) rv += FL[e][f][lin_face_index<DIM, N1>(ax, id)];
+  }
+  ((double*)a.out)[(size_t)(e0 + e) * NPE + n] = (double)rv;
+}
+
+// Both stages of the J.v: v -> q(v) in qbuf (QT), then J v.
+template <int DIM, int N1, bool CONV, class R, class QT>
+cudaError_t launch_lin(const KArgs& a, void* qbuf, cudaStream_t s) {
+  typedef LinShape<DIM, N1> S;
+  if (a.E <= 0) return cudaSuccess;
+  const int grid = (a.E + S::NE - 1) / S::NE;
+  KArgs b = a;
+  b.out = qbuf;
+  k_lin_q<DIM, N1, R, QT><<<grid, S::NT, 0, s>>>(b);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  b = a;
+  b.q = qbuf;
+  k_lin_r<DIM, N1, CONV, R, QT><<<grid, S::NT, 0, s>>>(b);
+  count_launch();
+  return cudaGetLastError();
+}
+
+
+// ===================================================================== simplices
+// The same nodal form on triangles and tetrahedra (equispaced nodes): the element's
+// nodes on a face are the face's nodes, so the exact integrals become dense reference
+// matrices (built on the host, rows padded to odd lengths):
+//   Dn_k[n][m] = d_k phi_m(x_n),  C_k[i][j] = int phi_j d_k phi_i,  M = int phi_i phi_j,
+//   LIFT_f = M^{-1} E_f M_f (E_f embeds face f's nodes),  M_f the face mass matrix;
+//   q_d = -sum_k Jinv[k][d] Dn_k v + sum_f n_{f,d} (sJ_f / det J) LIFT_f Delta_f,
+//   R   = -sum_k C_k g_k + sum_f sJ_f E_f M_f Fhat_f + a0/dt det J M v.
+template <class EL> struct SimOff {
+  static constexpr int DIM = EL::DIM, NPE = EL::NPE, NFN = EL::NFN, NF = EL::NF;
+  static constexpr int LDA = NPE | 1, LDL = NFN | 1;
+  static constexpr int DN = 0, C = DIM * NPE * LDA, M = 2 * DIM * NPE * LDA, LIFT = (2 * DIM + 1) * NPE * LDA,
+                       MF = LIFT + NF * NPE * LDL, SIZE = MF + NFN * LDL;
+};
+template <class EL> struct SimShape {
+  static constexpr int NPE = EL::NPE;
+  static constexpr int NE = NPE >= 256 ? 1 : 256 / NPE;
+  static constexpr int NT = (NE * NPE + 31) / 32 * 32;
+  static constexpr int GEO = Geo<EL::DIM>::size(EL::NF);
+};
+
+// The neighbour's local node that carries face node j of this element's face: the
+// permuted face node (tetrahedra), or the edge walked the other way when the edge's
+// face points are (triangles).
+template <class EL> __device__ __forceinline__ int sim_nbr_node(const KArgs& a, int code, int j) {
+  if constexpr (EL::NODE_PERM) {
+    return EL::face_node(code & 7, a.perm[(code >> 3) * EL::NFN + j]);
+  } else {
+    const bool rev = a.perm[(code >> 3) * EL::NFQ] != 0;
+    return EL::face_node(code & 7, rev ? EL::NFN - 1 - j : j);
+  }
+}
+
+template <class EL, class R, class QT>
+__global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_q(KArgs a) {
+  typedef SimShape<EL> S;
+  typedef SimOff<EL> O;
+  typedef Geo<EL::DIM> G;
+  constexpr int DIM = EL::DIM, NPE = EL::NPE, NFN = EL::NFN, NF = EL::NF, NE = S::NE, NT = S::NT, GEO = S::GEO;
+  if (a.skip && *a.skip) return;
+  const int e0 = blockIdx.x * NE;
+  const int ne = min(NE, a.E - e0);
+  if (!cta_active(a, e0, ne)) return;
+  extern __shared__ __align__(16) unsigned char sim_dsm[];
+  R* ops = (R*)sim_dsm;
+  __shared__ R Gs[NE][GEO];
+  __shared__ R Vs[NE][NPE];
+  __shared__ R Ds[NE][NF][NFN];
+  const int t = threadIdx.x;
+  const R* lo = lin_ops<R>(a);
+  for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
+  for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
+  const double* v = (const double*)a.u;
+  const int e = t / NPE, n = t - e * NPE;
+  const bool own = e < ne;
+  if (own) Vs[e][n] = R(v[(size_t)(e0 + e) * NPE + n]);
+  __syncthreads();
+  for (int it = t; it < NE * NF * NFN; it += NT) {
+    const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+    R d = R(0);
+    if (el < ne) {
+      const R vm = Vs[el][EL::face_node(f, j)];
+      const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
+      if (nb >= 0) {
+        const int code = a.nbf[(size_t)(e0 + el) * NF + f];
+        d = R(0.5) * (vm - R(v[(size_t)nb * NPE + sim_nbr_node<EL>(a, code, j)]));
+      } else {
+        d = vm;
+      }
+      d *= Gs[el][G::FACE + f * (DIM + 1) + DIM] / Gs[el][G::DETJ];
+    }
+    Ds[el][f][j] = d;
+  }
+  __syncthreads();
+  if (!own) return;
+  R gk[DIM];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const R* row = ops + O::DN + (k * NPE + n) * O::LDA;
+    R s = R(0);
+#pragma unroll 8
+    for (int m = 0; m < NPE; ++m) s += row[m] * Vs[e][m];
+    gk[k] = s;
+  }
+  R qd[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    R s = R(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) s -= Gs[e][G::JINV + k * DIM + d] * gk[k];
+    qd[d] = s;
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const R* row = ops + O::LIFT + (f * NPE + n) * O::LDL;
+    R lf = R(0);
+#pragma unroll
+    for (int j = 0; j < NFN; ++j) lf += row[j] * Ds[e][f][j];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) qd[d] += Gs[e][G::FACE + f * (DIM + 1) + d] * lf;
+  }
+  QT* q = (QT*)a.out;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) q[((size_t)(e0 + e) * DIM + d) * NPE + n] = QT(qd[d]);
+}
+
+template <class EL, bool CONV, class R, class QT>
+__global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
+  typedef SimShape<EL> S;
+  typedef SimOff<EL> O;
+  typedef Geo<EL::DIM> G;
+  constexpr int DIM = EL::DIM, NPE = EL::NPE, NFN = EL::NFN, NF = EL::NF, NE = S::NE, NT = S::NT, GEO = S::GEO;
+  if (a.skip && *a.skip) return;
+  const int e0 = blockIdx.x * NE;
+  const int ne = min(NE, a.E - e0);
+  if (!cta_active(a, e0, ne)) return;
+  extern __shared__ __align__(16) unsigned char sim_dsm[];
+  R* ops = (R*)sim_dsm;
+  __shared__ R Gs[NE][GEO];
+  __shared__ MPar<R> MPs[NE];
+  __shared__ R Gk[NE][DIM][NPE];
+  __shared__ R Hs[NE][NPE];
+  __shared__ R FV[NE][NF][NFN];
+  __shared__ R FQ[NE][NF][NFN];
+  __shared__ R FF[NE][NF][NFN];
+  const int t = threadIdx.x;
+  const R* lo = lin_ops<R>(a);
+  for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
+  for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
+  for (int i = t; i < NE; i += NT) MPs[i] = mpar<R>(i < ne ? elem_mp(a, e0 + i) : a.mp);
+  const double* v = (const double*)a.u;
+  const QT* q = (const QT*)a.q;
+  const R a0dt = R(a.a0dt);
+  const bool tterm = a.a0dt != 0.0;
+  const int e = t / NPE, n = t - e * NPE;
+  const bool own = e < ne;
+  R vn = R(0), qn[DIM];
+  if (own) {
+    vn = R(v[(size_t)(e0 + e) * NPE + n]);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) qn[d] = R(q[((size_t)(e0 + e) * DIM + d) * NPE + n]);
+  }
+  __syncthreads();
+  if (own) {
+    const MPar<R>& mp = MPs[e];
+    R fl[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) fl[d] = CONV ? mp.kappa * qn[d] + mp.beta[d] * vn : mp.kappa * qn[d];
+    const R dj = Gs[e][G::DETJ];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      R s = R(0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) s += Gs[e][G::JINV + k * DIM + d] * fl[d];
+      Gk[e][k][n] = dj * s;
+    }
+    if (tterm) Hs[e][n] = a0dt * dj * vn;
+    for_node_faces<EL>(n, [&](int f, int j) {
+      R s = R(0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) s += Gs[e][G::FACE + f * (DIM + 1) + d] * qn[d];
+      FV[e][f][j] = vn;
+      FQ[e][f][j] = s;
+    });
+  }
+  __syncthreads();
+  for (int it = t; it < NE * NF * NFN; it += NT) {
+    const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+    R fh = R(0);
+    if (el < ne) {
+      const MPar<R>& mp = MPs[el];
+      const R* nrm = &Gs[el][G::FACE + f * (DIM + 1)];
+      const R vm = FV[el][f][j], qmn = FQ[el][f][j];
+      R bn = R(0);
+      if (CONV) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) bn += mp.beta[d] * nrm[d];
+      }
+      const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
+      if (nb >= 0) {
+        const int node = sim_nbr_node<EL>(a, a.nbf[(size_t)(e0 + el) * NF + f], j);
+        const R vp = R(v[(size_t)nb * NPE + node]);
+        R qpn = R(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) qpn += nrm[d] * R(q[((size_t)nb * DIM + d) * NPE + node]);
+        fh = mp.tau * (vm - vp) + (R(0.5) * mp.kappa) * (qmn + qpn);
+        if (CONV) fh += bn * (bn >= R(0) ? vm : vp);
+      } else {
+        fh = mp.tau * vm + mp.kappa * qmn;
+        if (CONV && bn >= R(0)) fh += bn * vm;
+      }
+      fh *= nrm[DIM];
+    }
+    FF[el][f][j] = fh;
+  }
+  __syncthreads();
+  if (!own) return;
+  R r = R(0);
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const R* row = ops + O::C + (k * NPE + n) * O::LDA;
+#pragma unroll 8
+    for (int m = 0; m < NPE; ++m) r -= row[m] * Gk[e][k][m];
+  }
+  if (tterm) {
+    const R* row = ops + O::M + n * O::LDA;
+#pragma unroll 8
+    for (int m = 0; m < NPE; ++m) r += row[m] * Hs[e][m];
+  }
+  for_node_faces<EL>(n, [&](int f, int j) {
+    const R* row = ops + O::MF + j * O::LDL;
+    R s = R(0);
+#pragma unroll
+    for (int b = 0; b < NFN; ++b) s += row[b] * FF[e][f][b];
+    r += s;
+  });
+  ((double*)a.out)[(size_t)(e0 + e) * NPE + n] = (double)r;
+}
+
+template <class EL, bool CONV, class R, class QT>
+cudaError_t launch_sim(const KArgs& a, void* qbuf, cudaStream_t s) {
+  typedef SimShape<EL> S;
+  constexpr size_t smem = SimOff<EL>::SIZE * sizeof(R);
+  static const cudaError_t at1 =
+      cudaFuncSetAttribute(k_sim_q<EL, R, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static const cudaError_t at2 =
+      cudaFuncSetAttribute(k_sim_r<EL, CONV, R, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (at1 != cudaSuccess) return at1;
+  if (at2 != cudaSuccess) return at2;
+  if (a.E <= 0) return cudaSuccess;
+  const int grid = (a.E + S::NE - 1) / S::NE;
+  KArgs b = a;
+  b.out = qbuf;
+  k_sim_q<EL, R, QT><<<grid, S::NT, smem, s>>>(b);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  b = a;
+  b.q = qbuf;
+  k_sim_r<EL, CONV, R, QT><<<grid, S::NT, smem, s>>>(b);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ldg

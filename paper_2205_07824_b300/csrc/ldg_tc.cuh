@@ -170,8 +170,11 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
         }
       tc_commit(&bar_mma);
     } else {
+      // the loads may still be landing in shared memory: give them a second bounded
+      // wait before the CTA exits (no MMA was issued, so the tensor memory is idle)
       ok_s = 0;
       atomicExch(g.err, 1);
+      (void)mbar_wait(&bar_tma, 0);
     }
   }
   __syncthreads();
@@ -179,7 +182,10 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     // every lane of a warp takes the same branch (tcgen05.ld is warp-collective)
     const bool mma_done = __all_sync(0xffffffffu, mbar_wait(&bar_mma, 0));
     if (!mma_done) {
+      // a second bounded wait for the MMAs still writing the accumulator, so that the
+      // tensor memory is not released under them
       atomicExch(g.err, 1);
+      (void)mbar_wait(&bar_mma, 0);
     } else {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int row = m0 + warp * 32 + lane;

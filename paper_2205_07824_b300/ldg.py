@@ -25,6 +25,7 @@ FP64, FP32 = 0, 1
 PC_NONE, PC_BJACOBI, PC_MLP = 0, 1, 2
 FORCING_FIXED, FORCING_LAST = 0, 1
 BASIS_FP64, BASIS_F32X2 = 0, 1
+JV_AUTO, JV_STAGE = 0, 1
 STATUS = {0: "LDG_OK", -1: "LDG_ERR_ARG", -2: "LDG_ERR_CUDA", -3: "LDG_ERR_UNSUPPORTED",
           -4: "LDG_ERR_NONFINITE", -5: "LDG_ERR_MAXIT", -6: "LDG_ERR_MESH"}
 
@@ -71,7 +72,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("nq1", ctypes.c_int), ("gmres_m", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("max_newton", ctypes.c_int), ("newton_rtol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
                 ("krylov_precision", ctypes.c_int), ("precond", ctypes.c_int), ("pc_refresh", ctypes.c_int),
-                ("newton_forcing", ctypes.c_int), ("pc_reuse", ctypes.c_int), ("krylov_basis", ctypes.c_int)]
+                ("newton_forcing", ctypes.c_int), ("pc_reuse", ctypes.c_int), ("krylov_basis", ctypes.c_int),
+                ("jv_form", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -140,6 +142,12 @@ def lib():
                                                ctypes.POINTER(SolveReport)]
         L.ldg_q.argtypes = [vp, dp, dp]
         L.ldg_interpolate.argtypes = [vp, ctypes.c_double, dp]
+        L.ldg_project.argtypes = [vp, ctypes.c_double, dp]
+        L.ldg_jvp_host.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+        L.ldg_jv_describe.restype = ctypes.c_char_p
+        L.ldg_jv_describe.argtypes = [vp, ctypes.c_int]
+        L.ldg_l2_error.argtypes = [vp, dp, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]
         L.ldg_gmres.argtypes = [vp, dp, dp, dp, ctypes.POINTER(SolveReport)]
         L.ldg_newton_gmres.argtypes = [vp, dp, ctypes.POINTER(SolveReport)]
         L.ldg_newton_gmres_host.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveReport)]
@@ -187,12 +195,15 @@ class LDG:
     that default to their plain form: ``newton_forcing`` (FORCING_LAST: a Newton step's
     linear solve stops at what the Newton tolerance still needs), ``pc_reuse`` (the
     block-Jacobi blocks are built every pc_reuse solve calls) and ``krylov_basis``
-    (BASIS_F32X2: Gram-Schmidt on (hi, lo) float pairs, an emulated FP64)."""
+    (BASIS_F32X2: Gram-Schmidt on (hi, lo) float pairs, an emulated FP64). ``jv_form``
+    (JV_STAGE) keeps the quadrature-point stage kernels for the J.v of linear models on
+    affine quadrilaterals and hexahedra, which otherwise take the nodal kernels."""
 
     def __init__(self, mesh, p: int, model: int, case: int, mu=(), nq1: int = 0, gmres_m: int = 30,
                  max_restarts: int = 50, max_newton: int = 20, newton_rtol: float = 1e-8,
                  gmres_rtol: float = 1e-3, krylov_precision: int = 0, precond: int = 0, pc_refresh: int = 0,
-                 newton_forcing: int = 0, pc_reuse: int = 1, krylov_basis: int = 0, stream=None):
+                 newton_forcing: int = 0, pc_reuse: int = 1, krylov_basis: int = 0, jv_form: int = 0,
+                 stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("LDG needs a CUDA device (no CPU fallback)")
@@ -205,7 +216,7 @@ class LDG:
         mo = _Model(model, case, len(self._mu),
                     self._mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(self._mu) else None)
         op = _Options(nq1, gmres_m, max_restarts, max_newton, newton_rtol, gmres_rtol, krylov_precision, precond,
-                      pc_refresh, newton_forcing, pc_reuse, krylov_basis)
+                      pc_refresh, newton_forcing, pc_reuse, krylov_basis, jv_form)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -390,6 +401,36 @@ class LDG:
         self._check(lib().ldg_interpolate(self._h, t, _ptr(out, self.n_dof, "out")))
         return out
 
+    def jv_kernels(self, precision: int = 0) -> str:
+        """The kernels that form this operator's J.v in `precision` (``ldg_jv_describe``)."""
+        return lib().ldg_jv_describe(self._h, int(precision)).decode()
+
+    def jvp_host(self, precision, u, v, out):
+        """J(u) v with HOST buffers (``ldg_jvp_host``): u (or None for linear models), v and
+        out are contiguous float64 numpy arrays or CPU tensors of n_dof entries."""
+        def hp(a, name):
+            if a is None:
+                return None
+            ok = a.dtype == np.float64 and a.size == self.n_dof if isinstance(a, np.ndarray) else \
+                (not a.is_cuda and str(a.dtype) == "torch.float64" and a.numel() == self.n_dof and a.is_contiguous())
+            if not ok or (isinstance(a, np.ndarray) and not a.flags.c_contiguous):
+                raise TypeError(f"{name}: expected a contiguous float64 host array of n_dof elements")
+            return ctypes.c_void_p(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
+        self._check(lib().ldg_jvp_host(self._h, int(precision), hp(u, "u"), hp(v, "v"), hp(out, "out")))
+        return out
+
+    def project(self, t: float = 0.0, out=None):
+        """L2 projection of the analytic case at time t (``ldg_project``)."""
+        out = self.empty() if out is None else out
+        self._check(lib().ldg_project(self._h, t, _ptr(out, self.n_dof, "out")))
+        return out
+
+    def l2_error(self, u, t: float = 0.0):
+        """Relative L2 errors (E(u_h), E(q_h)) against the analytic case (``ldg_l2_error``)."""
+        eu, eq = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().ldg_l2_error(self._h, _ptr(u, self.n_dof, "u"), t, ctypes.byref(eu), ctypes.byref(eq)))
+        return eu.value, eq.value
+
     def gmres(self, u, b, x=None):
         x = self.empty() if x is None else x
         rep = SolveReport()
@@ -430,7 +471,7 @@ class Batch:
     def __init__(self, meshes, ps, model: int, cases, mus, nq1: int = 0, gmres_m: int = 30,
                  max_restarts: int = 50, max_newton: int = 20, newton_rtol: float = 1e-8,
                  gmres_rtol: float = 1e-3, krylov_precision: int = 0, precond: int = 0, newton_forcing: int = 0,
-                 pc_reuse: int = 1, krylov_basis: int = 0, stream=None):
+                 pc_reuse: int = 1, krylov_basis: int = 0, jv_form: int = 0, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Batch needs a CUDA device (no CPU fallback)")
@@ -451,7 +492,7 @@ class Batch:
                            mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(mu) else None)
         pa = (ctypes.c_int * n)(*[int(p) for p in ps])
         op = _Options(nq1, gmres_m, max_restarts, max_newton, newton_rtol, gmres_rtol, krylov_precision, precond, 0,
-                      newton_forcing, pc_reuse, krylov_basis)
+                      newton_forcing, pc_reuse, krylov_basis, jv_form)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -24,7 +24,8 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ("ldg_create", "ldg_destroy", "ldg_residual", "ldg_jvp", "ldg_newton_gmres", "ldg_gmres",
-              "ldg_set_time", "ldg_q", "ldg_interpolate", "ldg_sizes", "ldg_last_error"):
+              "ldg_set_time", "ldg_q", "ldg_interpolate", "ldg_project", "ldg_l2_error", "ldg_sizes",
+              "ldg_last_error"):
         assert n in names
 
 

@@ -1,0 +1,121 @@
+"""The nodal J.v kernels of the linear models on affine quadrilaterals, hexahedra,
+triangles and tetrahedra (the same operator as the quadrature-point stage kernels, in
+exact nodal form) against the FP64 oracle and against the stage kernels: rotated local
+frames (non-trivial face orientations), unstructured simplex meshes, periodic seams,
+Dirichlet faces, the BDF mass term, ragged CTA tiles, per-instance parameters of a
+batch, and the FP32-arithmetic form's error."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_07824_b300 import synth
+from gpu_util import SHEAR2, SHEAR3, assert_parity, cuda, host, pair
+
+pytestmark = pytest.mark.gpu
+
+# vertex orders of a local frame turned by 90 degrees about the last axis (the
+# lexicographic order of the rotated frame; the Jacobian keeps its sign)
+ROT_QUAD = [1, 3, 0, 2]
+ROT_HEX = [1, 3, 0, 2, 5, 7, 4, 6]
+
+
+def _rotate_some(mesh, every=3):
+    """Turns the local frame of every `every`-th element (so faces between turned and
+    unturned elements carry non-identity orientations)."""
+    perm = ROT_QUAD if mesh.etype == synth.QUAD else ROT_HEX
+    m = synth.Mesh(mesh.etype, mesh.xyz.copy(), mesh.vid.copy(), mesh.name)
+    for e in range(0, m.n_elem, every):
+        m.xyz[e] = mesh.xyz[e][perm]
+        m.vid[e] = mesh.vid[e][perm]
+    return m
+
+
+MESHES = [
+    ("quad_rot_p1", lambda: _rotate_some(synth.quad_box((7, 5), affine=SHEAR2)), 1, oracle.POISSON),
+    ("quad_rot_p3", lambda: _rotate_some(synth.quad_box((7, 5), affine=SHEAR2)), 3, oracle.CONVDIFF),
+    ("quad_per_p4", lambda: _rotate_some(synth.quad_box((6, 5), hi=(2.0, 1.5), periodic=(True, True))), 4,
+     oracle.CONVDIFF),
+    ("hex_rot_p2", lambda: _rotate_some(synth.hex_box((3, 4, 3), affine=SHEAR3), 2), 2, oracle.CONVDIFF),
+    ("hex_per_p4", lambda: _rotate_some(synth.hex_box((3, 3, 3), hi=(1.5, 1.5, 1.5), periodic=(True, True, True),
+                                                      affine=SHEAR3)), 4, oracle.CONVDIFF),
+    ("hex_p6", lambda: synth.hex_box((2, 2, 3), affine=SHEAR3), 6, oracle.CONVDIFF),
+    ("hex_poisson_p1", lambda: _rotate_some(synth.hex_box((4, 3, 3))), 1, oracle.POISSON),
+    ("tri_p1", lambda: synth.tri_square(6, affine=SHEAR2), 1, oracle.POISSON),
+    ("tri_unstr_p3", lambda: synth.tri_unstructured(7, seed=5), 3, oracle.CONVDIFF),
+    ("tri_per_p6", lambda: synth.tri_square(4, hi=(2.0, 2.0), periodic=(True, True), affine=SHEAR2), 6,
+     oracle.CONVDIFF),
+    ("tet_p2", lambda: synth.tet_cube(2, affine=SHEAR3), 2, oracle.POISSON),
+    ("tet_unstr_p3", lambda: synth.tet_unstructured(3, seed=2), 3, oracle.CONVDIFF),
+    ("tet_per_p4", lambda: synth.tet_cube(3, hi=(1.5, 1.5, 1.5), periodic=(True, True, True)), 4, oracle.CONVDIFF),
+    ("tet_p1", lambda: synth.tet_cube(3, affine=SHEAR3), 1, oracle.CONVDIFF),
+]
+
+
+@pytest.mark.parametrize("name,mk,p,model", MESHES, ids=[m[0] for m in MESHES])
+def test_nodal_jv_matches_oracle_and_stage_form(name, mk, p, model):
+    from paper_2205_07824_b300.ldg import JV_STAGE
+    mesh = mk()
+    o, g = pair(mesh, p, model, oracle.CASE_EXPSIN)
+    simplex = mesh.etype in (synth.TRI, synth.TET)
+    assert g.jv_kernels(0).startswith("k_sim_q + k_sim_r" if simplex else "k_lin_q + k_lin_r"), g.jv_kernels(0)
+    _, gs = pair(mesh, p, model, oracle.CASE_EXPSIN, jv_form=JV_STAGE)
+    assert gs.jv_kernels(0).startswith("k_qstage + k_residual"), gs.jv_kernels(0)
+    u, v = synth.random_vector(o.ndof, 1), synth.random_vector(o.ndof, 2)
+    ref = o.jvp(u, v)
+    jv = host(g.jvp(cuda(u), cuda(v)))
+    assert_parity(jv, ref, what=f"{name} nodal J.v")
+    assert_parity(host(g.residual(cuda(u))), o.residual(u), what=f"{name} R")
+    assert_parity(jv, host(gs.jvp(cuda(u), cuda(v))), rtol2=1e-13, rtolmax=1e-12, what=f"{name} nodal vs stage")
+    jv32 = host(g.jvp_prec(1, cuda(u), cuda(v)))
+    e32 = np.linalg.norm(jv32 - ref) / np.linalg.norm(ref)
+    assert e32 <= 2e-6, (name, e32)
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_nodal_jv_with_bdf_mass_term(scheme):
+    mesh = _rotate_some(synth.hex_box((3, 2, 3), affine=SHEAR3))
+    o, g = pair(mesh, 3, oracle.CONVDIFF, oracle.CASE_EXPSIN)
+    u, un, unm1, v = (synth.random_vector(o.ndof, s) for s in (1, 2, 3, 4))
+    o.set_time(scheme, 0.0, 0.07, un, unm1)
+    g.set_time(scheme, 0.0, 0.07, cuda(un), cuda(unm1))
+    assert_parity(host(g.jvp(cuda(u), cuda(v))), o.jvp(u, v), what="nodal J.v with the BDF term")
+    assert_parity(host(g.jvp_prec(1, cuda(u), cuda(v))), o.jvp(u, v), rtol2=2e-6, rtolmax=2e-5,
+                  what="FP32 nodal J.v with the BDF term")
+
+
+def test_nodal_jv_with_bdf_mass_term_on_tetrahedra():
+    mesh = synth.tet_unstructured(2, seed=9)
+    o, g = pair(mesh, 2, oracle.CONVDIFF, oracle.CASE_EXPSIN)
+    u, un, v = (synth.random_vector(o.ndof, s) for s in (1, 2, 4))
+    o.set_time(1, 0.0, 0.05, un, None)
+    g.set_time(1, 0.0, 0.05, cuda(un), None)
+    assert_parity(host(g.jvp(cuda(u), cuda(v))), o.jvp(u, v), what="tet nodal J.v with the BDF1 term")
+
+
+def test_nodal_jv_ragged_tiles():
+    """Element counts that leave a partial last CTA (hex p = 2: 9 elements per CTA;
+    quad p = 2: 28 per CTA; tet p = 3: 12; tri p = 2: 42)."""
+    for mesh, p in ((synth.hex_box((5, 2, 1)), 2), (synth.quad_box((29, 1)), 2), (synth.tet_cube(2), 3),
+                    (synth.tri_square(5), 2)):
+        o, g = pair(mesh, p, oracle.CONVDIFF, oracle.CASE_EXPSIN)
+        u, v = synth.random_vector(o.ndof, 5), synth.random_vector(o.ndof, 6)
+        assert_parity(host(g.jvp(cuda(u), cuda(v))), o.jvp(u, v), what=f"ragged {mesh.etype} p={p}")
+
+
+def test_nodal_jv_in_a_batch_uses_each_instance_parameters():
+    """Batched groups look the model parameters up per element: the batch J.v of every
+    instance equals its own oracle's."""
+    import torch
+    from paper_2205_07824_b300.ldg import Batch
+    meshes = [synth.quad_box(5), synth.quad_box((4, 6)), synth.quad_box(3)]
+    ps = [3, 3, 2]
+    mus = [(0.05, 1.0, 1.0, 0.0), (0.002, 0.5, 0.6, -0.8), (0.1, 2.0, -1.0, 0.3)]
+    b = Batch(meshes, ps, oracle.CONVDIFF, oracle.CASE_SINSIN, mus)
+    u = torch.randn(b.n_total, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    v = torch.randn(b.n_total, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(4))
+    jv = host(b.jvp(u, v, 0))
+    uh, vh = host(u), host(v)
+    for i, (m, p, mu) in enumerate(zip(meshes, ps, mus)):
+        o = oracle.Oracle(m, p, oracle.CONVDIFF, oracle.CASE_SINSIN, mu)
+        sl = slice(b.offsets[i], b.offsets[i] + b.n_dof[i])
+        assert_parity(jv[sl], o.jvp(uh[sl], vh[sl]), what=f"batch instance {i}")

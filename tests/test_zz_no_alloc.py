@@ -1,8 +1,9 @@
 """ldg_jvp_noalloc: J.v whose scratch is a static device array, for callers that
-cannot allocate device memory at the point of the call (for example inside a
-global-mode stream capture, or when an application's own pool holds all device
-memory). Checked through the C-ABI against ldg_jvp, on two calls in a row. This
-file is collected last so that a failure here cannot hide an earlier one."""
+cannot allocate device memory at the point of the call (an application whose own
+pool or caching allocator holds all device memory, or a host loop that cannot wait
+on an allocation). Checked through the C-ABI against ldg_jvp, on two calls in a
+row, and with two contexts sharing the array. This file is collected last so that
+a failure here cannot hide an earlier one."""
 import ctypes
 
 import numpy as np
@@ -37,11 +38,30 @@ def test_noalloc_jvp_matches_jvp_twice(mesh, p, model, case):
         out = torch.full_like(u, float("nan"))
         assert _call(g, u, v, out) == 0
         assert_parity(host(out), ref, what="jvp_noalloc")
-    # a second operator on the same device reuses the array; results stay independent
+    # the same operator with a second direction: the array's old contents do not leak in
     v2 = cuda(synth.random_vector(o.ndof, 5))
     out = torch.empty_like(u)
     assert _call(g, u, v2, out) == 0
     assert_parity(host(out), host(g.jvp(u, v2)), what="jvp_noalloc second direction")
+
+
+def test_noalloc_two_contexts_share_the_array():
+    """Two contexts on one device (different meshes, orders and models) take turns on
+    the one static array, A then B then A on one stream; each result equals that
+    context's own ldg_jvp."""
+    import torch
+    ma = synth.hex_box((3, 2, 3), affine=SHEAR3)
+    mb = synth.quad_box((5, 4), hi=(2.0, 2.0), periodic=(True, True))
+    oa, ga = pair(ma, 2, oracle.CONVDIFF, oracle.CASE_EXPSIN, gmres_m=2)
+    ob, gb = pair(mb, 3, oracle.NS, oracle.CASE_ROTATION, gmres_m=2)
+    ua, va = cuda(synth.random_vector(oa.ndof, 6)), cuda(synth.random_vector(oa.ndof, 7))
+    ub = cuda(synth.random_euler_state(mb.n_elem, ob.npe, 8))
+    vb = cuda(synth.random_vector(ob.ndof, 9))
+    ref_a, ref_b = host(ga.jvp(ua, va)), host(gb.jvp(ub, vb))
+    for g, u, v, ref, what in ((ga, ua, va, ref_a, "A"), (gb, ub, vb, ref_b, "B"), (ga, ua, va, ref_a, "A again")):
+        out = torch.full_like(u, float("nan"))
+        assert _call(g, u, v, out) == 0
+        assert_parity(host(out), ref, what=f"jvp_noalloc context {what}")
 
 
 def test_noalloc_rejects_operators_beyond_the_static_maximum():
