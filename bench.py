@@ -59,8 +59,14 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # Per-DOF FP64 FLOPs and DRAM bytes of one J.v of the default workload, by kernel
 # variant (ncu thread-instruction counts and dram__bytes_read.sum + dram__bytes_write.sum
 # of one capture); a variant not listed reports the HBM roofline only.
-JV_FLOP_PER_DOF = {}
-JV_TRAFFIC_PER_DOF = {}
+JV_FLOP_PER_DOF = {
+    # 1303 + 2207 MFLOP per J.v of 13,824,000 DOF (k_lin_q, k_lin_r)
+    "k_lin_q + k_lin_r [hex p=4 nq=5 convdiff fp64, q scratch fp64]": 253.9,
+}
+JV_TRAFFIC_PER_DOF = {
+    # (155 + 276) + (487 + 100) MB of DRAM reads + writes per J.v (k_lin_q, k_lin_r)
+    "k_lin_q + k_lin_r [hex p=4 nq=5 convdiff fp64, q scratch fp64]": 73.6,
+}
 
 
 # Default workload: the FP64 J.v of 3-D convection-diffusion on 48^3 hexahedra, p = 4.
@@ -397,6 +403,25 @@ def run_jv(args):
         dist.destroy_process_group()
 
 
+def run_jv_probe(args):
+    """The default workload's J.v for profilers: the same context with a one-column Krylov
+    space (about 1.5 GB on the device), no autotuning, `warmup + steps` FP64 J.v applications
+    then as many FP32 ones; prints the kernels it ran."""
+    import torch
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, CONVDIFF, CASE_EXPSIN
+    g = LDG(synth.hex_box(JV_N), JV_P, CONVDIFF, CASE_EXPSIN, JV_MU, gmres_m=1)
+    u = g.interpolate(0.0)
+    v = torch.randn(g.n_dof, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    out = torch.empty_like(v)
+    for prec in (0, 1):
+        for _ in range(args.warmup + args.steps):
+            g.jvp_prec(prec, u, v, out)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": JV_WORKLOAD, "fp64": g.jv_kernels(0), "fp32": g.jv_kernels(1),
+                      "applications_each": args.warmup + args.steps}))
+
+
 def vortex_solve_summary(args, stream):
     """Newton-GMRES time to 1e-8 of the 64x64 p=3 vortex BDF2 step: FP32 Krylov J.v +
     block-Jacobi against plain FP64 block-Jacobi (same steps, same forcing rule), and the
@@ -463,22 +488,24 @@ def vortex_problem(LDG, mesh, forcing=0, pc_reuse=1, basis=0):
 def run_mode(prob, kprec, pc, steps, warmup, flush, stream, launches):
     """Advance the problem `warmup` + `steps` BDF2 steps; time the last `steps`.
 
-    pc = 2 (learned): the warm-up steps run the block-Jacobi solver and collect its
-    (v, M^{-1} v, u) triples, the network is trained on them once (reported, not in
-    the timed steps), one more untimed step runs with the learned preconditioner,
-    then the timed steps."""
+    pc = 2 (learned, distilled block-Jacobi): the warm-up steps run the block-Jacobi
+    solver and collect its (v, M^{-1} v, u) triples; pc = 3 (learned correction of
+    block-Jacobi): they collect the solver's (residual, update) pairs, its Newton steps
+    (R(u_k), delta_k) and its Arnoldi steps (J z_j, z_j), as block-Jacobi features. The
+    network is trained on them once (reported, not in the timed steps), one more untimed
+    step runs with the learned preconditioner, then the timed steps."""
     import torch
     from paper_2205_07824_b300.ldg import BDF2
     DT = prob["dt"]
     mk = lambda p: prob["make"](p, kprec)
-    g = mk(1 if pc == 2 else pc)
+    g = mk(1 if pc in (2, 3) else pc)
     g.autotune()                       # tile of the kernels (cached per shape in the process)
     un, unm1 = prob["init"](g)
     u = torch.empty_like(un)
     state = {"t": 0.0, "g": g}
     nloc = g.n_cu * g.n_pe
     train = None
-    cap = 160 if pc == 2 else 0
+    cap = 160 if pc in (2, 3) else 0
     if cap:
         bufs = [torch.empty(cap * g.n_dof, dtype=torch.float64, device="cuda") for _ in range(3)]
         state["used"] = 0
@@ -490,7 +517,10 @@ def run_mode(prob, kprec, pc, steps, warmup, flush, stream, launches):
         u.copy_(un)
         if collect and state["used"] < cap:
             o = state["used"] * gg.n_dof
-            c, rep = gg.newton_gmres_collect(u, bufs[0][o:], bufs[1][o:], bufs[2][o:], cap - state["used"])
+            if pc == 3:
+                c, rep = gg.newton_collect_updates(u, bufs[0][o:], bufs[1][o:], bufs[2][o:], cap - state["used"], 3)
+            else:
+                c, rep = gg.newton_gmres_collect(u, bufs[0][o:], bufs[1][o:], bufs[2][o:], cap - state["used"])
             state["used"] += c
         else:
             rep = gg.newton_gmres(u)
@@ -513,8 +543,10 @@ def run_mode(prob, kprec, pc, steps, warmup, flush, stream, launches):
         train = {"pairs": state["used"] * prob["n_elem"], "vectors": state["used"],
                  "seconds": time.perf_counter() - t0,
                  "adam_steps": rep_t["steps"], "loss_first": rep_t["loss_first"], "loss_last": rep_t["loss_last"],
-                 "data": "Arnoldi vectors of the block-Jacobi warm-up steps with their block corrections"}
-        gm = mk(2)
+                 "data": ("(residual, update) pairs of the block-Jacobi warm-up solves: Newton steps (R(u_k), delta_k) "
+                          "and Arnoldi steps (J z_j, z_j), as block-Jacobi images with neighbour traces" if pc == 3 else
+                          "Arnoldi vectors of the block-Jacobi warm-up steps with their block corrections")}
+        gm = mk(pc)
         gm.autotune()
         gm.mlp_init(seed=1)
         gm.mlp_params(g.mlp_params())
@@ -1017,7 +1049,8 @@ def run_cylinder(args):
     forms = {}
     sols = {}
     headline = None
-    all_forms = (("fp64_bjacobi", 0, 1), ("fp32_bjacobi", 1, 1), ("fp32_learned", 1, 2))
+    all_forms = (("fp64_bjacobi", 0, 1), ("fp32_bjacobi", 1, 1), ("fp32_learned_distilled", 1, 2),
+                 ("fp32_learned", 1, 3))
     want = args.cyl_forms.split(",")
     for name, kp, pc in [f for f in all_forms if f[0] in want]:
         g, u, times, tot, launches, t_end, train = run_mode(prob, kp, pc, args.steps, args.warmup, flush, stream,
@@ -1144,8 +1177,10 @@ def main():
                     help="run the solver's Newton / restart / Arnoldi loops from the host instead of the CUDA "
                          "graph's WHILE nodes (same kernels; for profilers that do not follow graph nodes)")
     ap.add_argument("--no-solve", action="store_true", help="jv: skip the vortex time-to-1e-8 comparison")
-    ap.add_argument("--workload", default="jv", choices=["jv", "vortex", "batch", "hex", "tri", "cylinder", "tet"],
-                    help="jv (default): the FP64 J.v of 48^3 p=4 convection-diffusion; "
+    ap.add_argument("--workload", default="jv",
+                    choices=["jv", "jvprobe", "vortex", "batch", "hex", "tri", "cylinder", "tet"],
+                    help="jv (default): the FP64 J.v of 48^3 p=4 convection-diffusion; jvprobe: its J.v "
+                         "applications alone, for profilers; "
                          "vortex: the 64x64 p=3 Euler BDF2 step; batch: 256 parametrised convection-diffusion "
                          "solves in one graph launch; hex: the 48^3 convection-diffusion J.v sweep p=1..6; "
                          "tri: the same sweep on 131,072 triangles; "
@@ -1168,6 +1203,9 @@ def main():
         return
     if args.workload == "jv":
         run_jv(args)
+        return
+    if args.workload == "jvprobe":
+        run_jv_probe(args)
         return
     if args.workload == "batch":
         run_batch(args)

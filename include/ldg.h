@@ -127,9 +127,10 @@ typedef struct {
   int krylov_precision; /* LDG_FP64 (default) or LDG_FP32: arithmetic of the J.v inside GMRES
                            and of the preconditioner. Newton residuals, Arnoldi, Givens and all
                            vectors stay FP64. */
-  int precond;          /* LDG_PC_NONE (default), LDG_PC_BJACOBI or LDG_PC_MLP (flexible right
-                           preconditioning; the learned one falls back to block-Jacobi when a
-                           linear solve misses its tolerance) */
+  int precond;          /* LDG_PC_NONE (default), LDG_PC_BJACOBI, LDG_PC_MLP or LDG_PC_MLP_BJ
+                           (flexible right preconditioning; the learned ones fall back to
+                           block-Jacobi when a linear solve misses its tolerance; see the
+                           learned-preconditioner section below) */
   int pc_refresh;       /* rebuild the preconditioner every pc_refresh Newton iterations
                            (0 = once per ldg_newton_gmres call, at the initial guess) */
   int newton_forcing;   /* linear tolerance eta_k of Newton step k (inexact Newton):
@@ -161,7 +162,7 @@ typedef struct {
 } ldg_options;
 
 enum { LDG_FP64 = 0, LDG_FP32 = 1 };
-enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1, LDG_PC_MLP = 2 };
+enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1, LDG_PC_MLP = 2, LDG_PC_MLP_BJ = 3 };
 enum { LDG_FORCING_FIXED = 0, LDG_FORCING_LAST = 1 };
 enum { LDG_BASIS_FP64 = 0, LDG_BASIS_F32X2 = 1 };
 enum { LDG_JV_AUTO = 0, LDG_JV_STAGE = 1 };
@@ -309,6 +310,36 @@ int ldg_mlp_apply(ldg_ctx* ctx, const double* u_dev, const double* x_dev, double
  * for the learned preconditioner. */
 int ldg_newton_gmres_collect(ldg_ctx* ctx, double* u_dev, double* X_dev, double* T_dev, double* U_dev, int capacity,
                              int* count, ldg_solve_report* rep);
+
+/* Learned correction of block-Jacobi (LDG_PC_MLP_BJ; the learned pattern of this build,
+ * trained on the (residual, Newton update) pairs the plain block-Jacobi solver itself
+ * generates). The same network as above acts on the block-Jacobi image z = BJ^{-1} v:
+ *   M(v)_K = ||z_K|| net(z_K / ||z_K||, h_K),
+ *   h_K[c][i] = (sum over the faces f of K that hold node i of the face neighbour's z at
+ *               the node in the same place) / ||z_K||   (0 at interior nodes, on boundary faces),
+ * so each element sees its neighbours' block-Jacobi corrections along its faces, the
+ * coupling block-Jacobi leaves out. Positively homogeneous in v. The blocks are those of
+ * the context's block-Jacobi set-up (built at each solve's initial guess).
+ *
+ * ldg_newton_collect_updates runs the plain block-Jacobi Newton-GMRES solve from u_dev and
+ * stores (residual, update) pairs that solve generates, as features and targets: an input
+ * r goes in as X = z = BJ^{-1} r and U = h (the scaled neighbour traces of z), its update
+ * d as T. `which` selects the pairs (bit mask):
+ *   1: every Newton step k: r = R(u_k), d = the Newton update delta_k (J delta_k = R(u_k),
+ *      solved to the linear tolerance);
+ *   2: every Arnoldi step j of every linear solve: r = J z_j, d = z_j, where z_j is the
+ *      block-Jacobi-preconditioned Krylov direction: exact pairs of J^{-1} on the Krylov
+ *      space the solver explores.
+ * n_dof doubles per pair in each of X_dev, T_dev, U_dev, up to `capacity` pairs; *count
+ * receives how many. Train on them with ldg_mlp_train(X, T, U).
+ * ldg_halo_features writes h for a given z (device vectors). ldg_mlp_bj_apply evaluates
+ * y = M(x) with the current blocks (after ldg_precond_setup) and BF16 weights.
+ * Errors: LDG_ERR_ARG (null pointers, no network for the apply), LDG_ERR_UNSUPPORTED
+ * (hexahedra whose quadrature size differs from p + 1: their face nodes cannot be matched). */
+int ldg_newton_collect_updates(ldg_ctx* ctx, double* u_dev, double* X_dev, double* T_dev, double* U_dev,
+                               int capacity, int which, int* count, ldg_solve_report* rep);
+int ldg_halo_features(ldg_ctx* ctx, const double* z_dev, double* h_dev);
+int ldg_mlp_bj_apply(ldg_ctx* ctx, const double* x_dev, double* y_dev);
 
 /* q of Eq. 1a for diffusion models: q_dev [n_elem][n_cu][dim][n_pe]. */
 int ldg_q(ldg_ctx* ctx, const double* u_dev, double* q_dev);

@@ -689,6 +689,94 @@ int mlp_apply(ldg_ctx* ctx, const double* u, const double* x, double* y, const i
   return LDG_OK;
 }
 
+// ------------------------------------------ learned correction of block-Jacobi
+// h[K][c][i] = (sum over the faces of K holding node i of the face neighbour's z at the
+// same place) / ||z_K||; one warp per element.
+__global__ void k_halo_feat(const double* __restrict__ z, const int* __restrict__ src, int64_t E, int npe, int ncu,
+                            double* __restrict__ h, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t K = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (K >= E) return;
+  const int nloc = npe * ncu;
+  const double* zk = z + K * nloc;
+  double s2 = 0.0;
+  for (int i = lane; i < nloc; i += 32) s2 += zk[i] * zk[i];
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  const double nrm = sqrt(s2);
+  const double inv = nrm > 1e-30 ? 1.0 / nrm : 0.0;
+  for (int i = lane; i < nloc; i += 32) {
+    const int c = i / npe, n = i - c * npe;
+    const int* sk = src + (K * npe + n) * 3;
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const int sidx = sk[t];
+      if (sidx >= 0) {
+        const int64_t nb = sidx / npe, nn = sidx - nb * npe;
+        acc += z[(nb * ncu + c) * npe + nn];
+      }
+    }
+    h[K * nloc + i] = acc * inv;
+  }
+}
+
+// The neighbour-node table of the halo features, built on the host at first use.
+int ensure_halo(ldg_ctx* ctx) {
+  if (ctx->d_halo) return LDG_OK;
+  const int et = ctx->etype, p = ctx->p, npe = ctx->npe, nf = ctx->nf;
+  const int nfn = et == LDG_QUAD ? p + 1 : (et == LDG_HEX ? (p + 1) * (p + 1) :
+                  (et == LDG_TRI ? p + 1 : (p + 1) * (p + 2) / 2));
+  const int nfq = ctx->nfq;
+  if (et == LDG_HEX && ctx->nq != p + 1)
+    return fail(ctx, LDG_ERR_UNSUPPORTED, "halo features on hexahedra need p + 1 quadrature points");
+  if (ctx->pg > 0) return fail(ctx, LDG_ERR_UNSUPPORTED, "halo features are built for affine elements");
+  std::vector<int> tab((size_t)ctx->E * npe * 3, -1);
+  for (int64_t K = 0; K < ctx->E; ++K)
+    for (int f = 0; f < nf; ++f) {
+      const int nb = ctx->h_nbr[K * nf + f];
+      if (nb < 0) continue;
+      const int code = ctx->h_nbf[K * nf + f], nface = code & 7, orient = code >> 3;
+      for (int j = 0; j < nfn; ++j) {
+        int jn;
+        if (et == LDG_TET) jn = ctx->h_perm[(size_t)orient * nfn + j];
+        else if (et == LDG_HEX) jn = ctx->h_perm[(size_t)orient * nfq + j];
+        else jn = ctx->h_perm[(size_t)orient * nfq] != 0 ? nfn - 1 - j : j;   // edges: same or reversed
+        const int own = face_node_host(et, p, f, j), other = face_node_host(et, p, nface, jn);
+        int* slot = &tab[((size_t)K * npe + own) * 3];
+        int t = 0;
+        while (t < 3 && slot[t] >= 0) ++t;
+        if (t == 3) return fail(ctx, LDG_ERR_MESH, "a node on more than three faces");
+        slot[t] = (int)(nb * npe + other);
+      }
+    }
+  CK(cudaMalloc(&ctx->d_halo, tab.size() * sizeof(int)));
+  CK(cudaMemcpy(ctx->d_halo, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return LDG_OK;
+}
+
+int halo_features(ldg_ctx* ctx, const double* z, double* h, const int* skip) {
+  int rc;
+  if ((rc = ensure_halo(ctx))) return rc;
+  k_halo_feat<<<(unsigned)((ctx->E * 32 + 255) / 256), 256, 0, ctx->stream>>>(z, ctx->d_halo, ctx->E, ctx->npe,
+                                                                             ctx->ncu, h, skip);
+  count_launch();
+  CK(cudaGetLastError());
+  return LDG_OK;
+}
+
+// y = M(x) of the learned block-Jacobi correction: z = BJ^{-1} x, h = halo(z), network.
+int mlp_bj_apply(ldg_ctx* ctx, const double* x, double* y, const int* skip) {
+  int rc;
+  if (!ctx->d_pcz) {
+    CK(cudaMalloc(&ctx->d_pcz, ctx->ndof * sizeof(double)));
+    CK(cudaMalloc(&ctx->d_pch, ctx->ndof * sizeof(double)));
+  }
+  if ((rc = pc_apply(ctx, x, ctx->d_pcz, skip))) return rc;
+  if ((rc = halo_features(ctx, ctx->d_pcz, ctx->d_pch, skip))) return rc;
+  return mlp_apply(ctx, ctx->d_pch, ctx->d_pcz, y, skip);
+}
+
 // GMRES(m) on J(u) x = b, x0 = 0, to ||b - J x|| <= rtol ||b||.
 // The host queues Arnoldi steps up to LAG steps ahead of the GPU; each step's
 // kernels return at once after the device-side convergence test has fired.
@@ -713,7 +801,8 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
   const double thr = rtol * bnorm;
   CK(cudaMemcpyAsync(sc + 3, &thr, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   const bool pc = (ctx->opt.precond == LDG_PC_BJACOBI && ctx->pc_ready) ||
-                  (ctx->opt.precond == LDG_PC_MLP && ctx->mlp.ready);
+                  (ctx->opt.precond == LDG_PC_MLP && ctx->mlp.ready) ||
+                  (ctx->opt.precond == LDG_PC_MLP_BJ && ctx->mlp.ready && ctx->pc_ready);
   // the preconditioned Krylov vectors Z must exist before their addresses are used
   if (pc && (rc = ensure_pc_storage(ctx))) return rc;
   const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8);
@@ -737,6 +826,8 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
         double* z = ctx->d_Z + (size_t)j * n;
         if (ctx->opt.precond == LDG_PC_MLP) {
           if ((rc = mlp_apply(ctx, u, dir, z, flags))) return rc;
+        } else if (ctx->opt.precond == LDG_PC_MLP_BJ) {
+          if ((rc = mlp_bj_apply(ctx, dir, z, flags))) return rc;
         } else {
           if ((rc = pc_apply(ctx, dir, z, flags))) return rc;
         }
@@ -770,7 +861,23 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
     CK(cudaStreamSynchronize(ctx->stream));
     const int cols = ctx->h_flags[60 * 4 + 1];
     if (rep) { rep->gmres_iters += cols; rep->jv_calls += cols + 1; }
-    if (pc && ctx->col_X && ctx->opt.precond == LDG_PC_BJACOBI) {
+    if (pc && ctx->col_X && (ctx->col_mode & 2) && ctx->opt.precond == LDG_PC_BJACOBI) {
+      // exact inverse pairs of the learned correction's training set: r = J z_j, d = z_j
+      // for the cycle's block-Jacobi-preconditioned directions z_j
+      if (!ctx->d_pcz) {
+        CK(cudaMalloc(&ctx->d_pcz, n * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_pch, n * sizeof(double)));
+      }
+      for (int jj = 0; jj < cols && ctx->col_count < ctx->col_cap; ++jj, ++ctx->col_count) {
+        const size_t o = (size_t)ctx->col_count * n;
+        const double* zj = ctx->d_Z + (size_t)jj * n;
+        if ((rc = jvp_args(ctx, base_args(ctx), u, zj, ctx->d_pcz, ctx->opt.krylov_precision))) return rc;
+        if ((rc = pc_apply(ctx, ctx->d_pcz, ctx->col_X + o, nullptr))) return rc;
+        if ((rc = halo_features(ctx, ctx->col_X + o, ctx->col_U + o, nullptr))) return rc;
+        CK(cudaMemcpyAsync(ctx->col_T + o, zj, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+    }
+    if (pc && ctx->col_X && ctx->col_mode == 0 && ctx->opt.precond == LDG_PC_BJACOBI) {
       // training triples for the learned preconditioner: (v_j, M^{-1} v_j, u)
       for (int jj = 0; jj < cols && ctx->col_count < ctx->col_cap; ++jj, ++ctx->col_count) {
         const size_t o = (size_t)ctx->col_count * n;
@@ -810,7 +917,7 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
   int k = 0;
   const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8);
   while (rn > ctx->opt.newton_rtol * r0 && k < ctx->opt.max_newton) {
-    if (ctx->opt.precond == LDG_PC_BJACOBI &&
+    if ((ctx->opt.precond == LDG_PC_BJACOBI || ctx->opt.precond == LDG_PC_MLP_BJ) &&
         (k == 0 || (ctx->opt.pc_refresh > 0 && k % ctx->opt.pc_refresh == 0))) {
       if ((rc = do_pc_setup(ctx, u))) return rc;
       if (rep) rep->pc_setups++;
@@ -818,15 +925,25 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
     if (ctx->opt.precond == LDG_PC_MLP && k == 0 && (rc = ensure_pc_storage(ctx))) return rc;
     const double eta = newton_forcing_eta(ctx->opt.newton_forcing, ctx->opt.gmres_rtol, ctx->opt.newton_rtol, r0, rn);
     rc = do_gmres(ctx, u, res, del, eta, rep);
-    if (rc == LDG_ERR_MAXIT && ctx->opt.precond == LDG_PC_MLP) {
+    if (rc == LDG_ERR_MAXIT && (ctx->opt.precond == LDG_PC_MLP || ctx->opt.precond == LDG_PC_MLP_BJ)) {
       // the learned preconditioner did not reach the tolerance: fall back to block-Jacobi
+      const int learned = ctx->opt.precond;
       ctx->opt.precond = LDG_PC_BJACOBI;
-      rc = do_pc_setup(ctx, u);
+      rc = learned == LDG_PC_MLP_BJ ? LDG_OK : do_pc_setup(ctx, u);
       if (!rc) rc = do_gmres(ctx, u, res, del, eta, rep);
-      ctx->opt.precond = LDG_PC_MLP;
-      if (rep) { rep->pc_fallbacks++; rep->pc_setups++; }
+      ctx->opt.precond = learned;
+      if (rep) { rep->pc_fallbacks++; if (learned == LDG_PC_MLP) rep->pc_setups++; }
     }
     if (rc && rc != LDG_ERR_MAXIT) return rc;
+    if (ctx->col_X && (ctx->col_mode & 1) && ctx->col_count < ctx->col_cap && ctx->pc_ready) {
+      // training data of the learned block-Jacobi correction: z = BJ^{-1} R(u_k), its
+      // neighbour traces h, and the Newton update delta_k
+      const size_t o = (size_t)ctx->col_count * n;
+      if ((rc = pc_apply(ctx, res, ctx->col_X + o, nullptr))) return rc;
+      if ((rc = halo_features(ctx, ctx->col_X + o, ctx->col_U + o, nullptr))) return rc;
+      CK(cudaMemcpyAsync(ctx->col_T + o, del, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+      ++ctx->col_count;
+    }
     // u <- u - delta   (sc[6] holds -1)
     k_axpy_dev<<<g1, 256, 0, ctx->stream>>>(del, sc + 6, u, n);
     count_launch();
@@ -1009,6 +1126,7 @@ int ldg_destroy(ldg_ctx* ctx) {
   cudaFree(ctx->d_colour); cudaFree(ctx->d_blocks); cudaFree(ctx->d_binv); cudaFree(ctx->d_Z);
   cudaFree(ctx->d_probe); cudaFree(ctx->d_jp); cudaFree(ctx->d_status);
   cudaFree(ctx->d_stage); cudaFree(ctx->d_lops); cudaFree(ctx->d_lopsf);
+  cudaFree(ctx->d_halo); cudaFree(ctx->d_pcz); cudaFree(ctx->d_pch);
   cudaFree(ctx->d_er_xi); cudaFree(ctx->d_er_w); cudaFree(ctx->d_er_B); cudaFree(ctx->d_er_P); cudaFree(ctx->d_l2);
   {
     auto& M = ctx->mlp;
@@ -1064,7 +1182,7 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if (o.newton_rtol <= 0) o.newton_rtol = 1e-8;
   if (o.gmres_rtol <= 0) o.gmres_rtol = 1e-3;
   if (o.krylov_precision != LDG_FP32) o.krylov_precision = LDG_FP64;
-  if (o.precond != LDG_PC_BJACOBI && o.precond != LDG_PC_MLP) o.precond = LDG_PC_NONE;
+  if (o.precond != LDG_PC_BJACOBI && o.precond != LDG_PC_MLP && o.precond != LDG_PC_MLP_BJ) o.precond = LDG_PC_NONE;
   if (o.pc_refresh < 0) o.pc_refresh = 0;
   if (o.newton_forcing != LDG_FORCING_LAST) o.newton_forcing = LDG_FORCING_FIXED;
   if (o.pc_reuse < 1) o.pc_reuse = 1;
@@ -1107,6 +1225,8 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   ctx->ndof = ctx->E * ctx->npe * ctx->ncu;
   ctx->nloc = ctx->npe * ctx->ncu;
   ctx->h_nbr = mp_.nbr;
+  ctx->h_nbf = mp_.nbf;
+  ctx->h_perm = mp_.perm;
   ctx->m = o.gmres_m;
   std::vector<double> xn;
   ref_nodes(ref, xn);
@@ -1703,6 +1823,35 @@ int ldg_newton_gmres_collect(ldg_ctx* ctx, double* u, double* X, double* T, doub
   return rc;
 }
 
+int ldg_newton_collect_updates(ldg_ctx* ctx, double* u, double* X, double* T, double* U, int capacity, int which,
+                               int* count, ldg_solve_report* rep) {
+  if (!ctx || !ctx->ks || !u || !X || !T || !U || capacity <= 0 || !count || which < 1 || which > 3)
+    return LDG_ERR_ARG;
+  int rc;
+  if ((rc = ensure_halo(ctx))) return rc;
+  const int pc = ctx->opt.precond;
+  ctx->opt.precond = LDG_PC_BJACOBI;
+  ctx->col_X = X; ctx->col_T = T; ctx->col_U = U; ctx->col_cap = capacity; ctx->col_count = 0;
+  ctx->col_mode = which;
+  rc = ldg_newton_gmres(ctx, u, rep);
+  *count = ctx->col_count;
+  ctx->col_X = nullptr; ctx->col_T = nullptr; ctx->col_U = nullptr; ctx->col_cap = 0; ctx->col_mode = 0;
+  ctx->opt.precond = pc;
+  return rc;
+}
+
+int ldg_halo_features(ldg_ctx* ctx, const double* z, double* h) {
+  if (!ctx || !ctx->ks || !z || !h) return LDG_ERR_ARG;
+  return halo_features(ctx, z, h, nullptr);
+}
+
+int ldg_mlp_bj_apply(ldg_ctx* ctx, const double* x, double* y) {
+  if (!ctx || !ctx->ks || !x || !y) return LDG_ERR_ARG;
+  if (!ctx->mlp.ready) return fail(ctx, LDG_ERR_ARG, "ldg_mlp_bj_apply: no trained network (ldg_mlp_init/train)");
+  if (!ctx->pc_ready) return fail(ctx, LDG_ERR_ARG, "ldg_mlp_bj_apply: no block-Jacobi blocks (ldg_precond_setup)");
+  return mlp_bj_apply(ctx, x, y, nullptr);
+}
+
 int ldg_q(ldg_ctx* ctx, const double* u, double* q) {
   if (!ctx || !ctx->ks || !u || !q) return LDG_ERR_ARG;
   if (!ctx->ks->qstage) return fail(ctx, LDG_ERR_ARG, "the model has no q (convection model)");
@@ -1742,7 +1891,8 @@ int ldg_newton_gmres(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
   int rc;
   // block-Jacobi built once per call, or no preconditioner: the graph-driven solver
   // (the whole Newton-GMRES one CUDA graph launch); otherwise the host-driven loop
-  if (ctx->opt.precond != LDG_PC_MLP && ctx->opt.pc_refresh == 0 && !ctx->col_X) {
+  if (ctx->opt.precond != LDG_PC_MLP && ctx->opt.precond != LDG_PC_MLP_BJ && ctx->opt.pc_refresh == 0 &&
+      !ctx->col_X) {
     if (!ctx->engine && (rc = batch_wrap(ctx, &ctx->engine))) {
       rep->status = rc;
       return rc;

@@ -72,6 +72,10 @@ struct ldg_ctx {
   // block-Jacobi preconditioner
   int nloc = 0;
   std::vector<int> h_nbr;      // host copy of the face neighbours (colouring)
+  std::vector<unsigned char> h_nbf, h_perm;   // host copies of the neighbour faces and permutations
+  int* d_halo = nullptr;       // [E][npe][3] neighbour node (nbr * npe + node) per face holding the node, -1 none
+  double* d_pcz = nullptr;     // learned block-Jacobi correction: z = BJ^{-1} v ...
+  double* d_pch = nullptr;     // ... and its neighbour-trace features
   int* d_colour = nullptr;
   int ncolour = 0;
   double* d_blocks = nullptr;  // [E][nloc][nloc] exact diagonal blocks, column-major
@@ -111,6 +115,8 @@ struct ldg_ctx {
   double* col_T = nullptr;
   double* col_U = nullptr;
   int col_cap = 0, col_count = 0;
+  int col_mode = 0;            // 0: Arnoldi triples (v, BJ^{-1} v, u); else a mask: 1 Newton updates,
+                               // 2 Arnoldi inverse pairs (J z_j, z_j), as (BJ^{-1} r, d, halo)
   // batched contexts: per-element instance ids and the per-instance parameter table
   // (owned by the batch, not by this context)
   const int* ext_inst = nullptr;

@@ -361,6 +361,22 @@ bool build_lin_ops(int p, std::vector<double>& blob, std::string& err) {
 }
 
 namespace {
+int simplex_face_node(int etype, int p, int f, int j);
+}  // namespace
+
+int face_node_host(int etype, int p, int f, int j) {
+  if (etype == E_QUAD || etype == E_HEX) {
+    const int n1 = p + 1, ax = f >> 1, fix = (f & 1) ? p : 0;
+    if (etype == E_QUAD) return ax == 0 ? fix + n1 * j : j + n1 * fix;
+    const int a = j % n1, b = j / n1;
+    if (ax == 0) return fix + n1 * (a + n1 * b);
+    if (ax == 1) return a + n1 * (fix + n1 * b);
+    return a + n1 * (b + n1 * fix);
+  }
+  return simplex_face_node(etype, p, f, j);
+}
+
+namespace {
 // local node of face-node j on face f (numbering of tri_basis / tet_basis)
 int simplex_face_node(int etype, int p, int f, int j) {
   auto tri_idx = [p](int i, int jj) { return jj * (p + 1) - jj * (jj - 1) / 2 + i; };

@@ -69,6 +69,9 @@ bool build_lin_ops(int p, std::vector<double>& blob, std::string& err);
 // in face-node order (the same on every face).
 bool build_lin_simplex_ops(int etype, int p, std::vector<double>& blob, std::string& err);
 
+// Local node of face-node j on face f (face-node numbering of the element kernels).
+int face_node_host(int etype, int p, int f, int j);
+
 // Reference coordinates of face point k of face f and of volume point q (for host-side projection).
 void ref_face_point(const RefOps& ref, int f, int k, double* xi);
 void ref_nodes(const RefOps& ref, std::vector<double>& xn);   // [npe][dim]

@@ -39,6 +39,12 @@ template <int DIM, int N1> struct LinShape {
   static constexpr int NT = (NE * NPE + 31) / 32 * 32;
   static constexpr int GEO = Geo<DIM>::size(NF);
 };
+// Resident 256-thread CTAs asked of the register allocator: eight (32 registers a
+// thread) for the FP32 kernels, whose face gathers and barriers want every warp slot;
+// six (40 registers) for FP64, whose doubles would spill at 32 (measured on 48^3 p = 4).
+template <int NT, class R> struct LinMinBlocks {
+  static constexpr int value = NT > 256 ? 1 : (sizeof(R) == 4 ? 8 : 6);
+};
 
 // local node of face-node j on face f = 2 axis + side (free axes ascending, first fastest)
 template <int DIM, int N1> __device__ __forceinline__ int lin_face_node(int f, int j) {
@@ -64,7 +70,7 @@ template <class R> __device__ __forceinline__ const R* lin_ops(const KArgs& a) {
 
 // ------------------------------------------------------------------ q-stage
 template <int DIM, int N1, class R, class QT>
-__global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_q(KArgs a) {
+__global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<DIM, N1>::NT, R>::value)) k_lin_q(KArgs a) {
   typedef LinShape<DIM, N1> S;
   typedef LinOff<N1> O;
   typedef Geo<DIM> G;
@@ -75,34 +81,55 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_q(KArgs a) {
   if (!cta_active(a, e0, ne)) return;
   __shared__ R ops[O::SIZE];
   __shared__ R Gs[NE][GEO];
+  __shared__ R Cf[NE][NF];            // sJ_f / det J
   __shared__ R Vs[NE][NPE];
   __shared__ R Ds[NE][NF][NFN];
   const int t = threadIdx.x;
   const R* lo = lin_ops<R>(a);
   for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
   for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
+  for (int i = t; i < ne * NF; i += NT) {
+    const double* g = a.geo + (size_t)(e0 + i / NF) * GEO;
+    Cf[i / NF][i % NF] = R(g[G::FACE + (i % NF) * (DIM + 1) + DIM] / g[G::DETJ]);
+  }
   const double* v = (const double*)a.u;
   const int e = t / NPE, n = t - e * NPE;
   const bool own = e < ne;
+  // the neighbours' face-node values of this thread's face items, loaded before the
+  // first barrier so that their latency overlaps the element's own loads
+  constexpr int NFI = NE * NF * NFN, ROUNDS = (NFI + NT - 1) / NT;
+  R vpre[ROUNDS];
+  int hasnb = 0;
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    vpre[r] = R(0);
+    if (it < NFI) {
+      const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+      if (el < ne) {
+        const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
+        if (nb >= 0) {
+          const int code = a.nbf[(size_t)(e0 + el) * NF + f];
+          const int jn = a.perm[(code >> 3) * NFN + j];
+          vpre[r] = R(v[(size_t)nb * NPE + lin_face_node<DIM, N1>(code & 7, jn)]);
+          hasnb |= 1 << r;
+        }
+      }
+    }
+  }
   if (own) Vs[e][n] = R(v[(size_t)(e0 + e) * NPE + n]);
   __syncthreads();
 
   // Delta_f (sJ_f / det J) at the face nodes
-  for (int it = t; it < NE * NF * NFN; it += NT) {
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    if (it >= NFI) break;
     const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
     R d = R(0);
     if (el < ne) {
       const R vm = Vs[el][lin_face_node<DIM, N1>(f, j)];
-      const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
-      if (nb >= 0) {
-        const int code = a.nbf[(size_t)(e0 + el) * NF + f];
-        const int jn = a.perm[(code >> 3) * NFN + j];
-        const R vp = R(v[(size_t)nb * NPE + lin_face_node<DIM, N1>(code & 7, jn)]);
-        d = R(0.5) * (vm - vp);
-      } else {
-        d = vm;
-      }
-      d *= Gs[el][G::FACE + f * (DIM + 1) + DIM] / Gs[el][G::DETJ];
+      d = (hasnb >> r) & 1 ? (vm - vpre[r]) * (R(0.5) * Cf[el][f]) : vm * Cf[el][f];
     }
     Ds[el][f][j] = d;
   }
@@ -143,7 +170,7 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_q(KArgs a) {
 
 // ----------------------------------------------------------------- residual
 template <int DIM, int N1, bool CONV, class R, class QT>
-__global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_r(KArgs a) {
+__global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<DIM, N1>::NT, R>::value)) k_lin_r(KArgs a) {
   typedef LinShape<DIM, N1> S;
   typedef LinOff<N1> O;
   typedef Geo<DIM> G;
@@ -155,6 +182,7 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_r(KArgs a) {
   __shared__ R ops[O::SIZE];
   __shared__ R Gs[NE][GEO];
   __shared__ MPar<R> MPs[NE];
+  __shared__ R Ak[NE][DIM][DIM + 1];  // g_k = sum_d Ak[k][d] q_d + Ak[k][DIM] v
   __shared__ R Gk[NE][DIM][NPE];      // nodal fluxes g_k, later the axis-1 stage (3-D)
   __shared__ R Tk[NE][DIM][NPE];      // axis-0 stage
   __shared__ R Hs[NE][NPE];           // a0/dt det J v (time term)
@@ -166,6 +194,19 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_r(KArgs a) {
   for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
   for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
   for (int i = t; i < NE; i += NT) MPs[i] = mpar<R>(i < ne ? elem_mp(a, e0 + i) : a.mp);
+  for (int i = t; i < ne * DIM; i += NT) {
+    // det J Jinv[k][.] (kappa q + beta v): per element kappa det J Jinv[k][d] and det J Jinv[k].beta
+    const int el = i / DIM, k = i % DIM;
+    const double* g = a.geo + (size_t)(e0 + el) * GEO;
+    const ModelParams mp = elem_mp(a, e0 + el);
+    double bsum = 0.0;
+    for (int d = 0; d < DIM; ++d) {
+      const double jd = g[G::DETJ] * g[G::JINV + k * DIM + d];
+      Ak[el][k][d] = R(mp.kappa * jd);
+      bsum += jd * mp.beta[d];
+    }
+    Ak[el][k][DIM] = CONV ? R(bsum) : R(0);
+  }
   const double* v = (const double*)a.u;
   const QT* q = (const QT*)a.q;
   const R a0dt = R(a.a0dt);
@@ -174,6 +215,31 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_r(KArgs a) {
   const bool own = e < ne;
   const int id[3] = {n % N1, (n / N1) % N1, DIM == 3 ? n / (N1 * N1) : 0};
   constexpr int STR[3] = {1, N1, N1 * N1};
+  // the neighbours' v and q at this thread's face items, loaded before the first barrier
+  constexpr int NFI = NE * NF * NFN, ROUNDS = (NFI + NT - 1) / NT;
+  R vpre[ROUNDS], qpre[ROUNDS][DIM];
+  int hasnb = 0;
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    vpre[r] = R(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) qpre[r][d] = R(0);
+    if (it < NFI) {
+      const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+      if (el < ne) {
+        const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
+        if (nb >= 0) {
+          const int code = a.nbf[(size_t)(e0 + el) * NF + f];
+          const int node = lin_face_node<DIM, N1>(code & 7, a.perm[(code >> 3) * NFN + j]);
+          vpre[r] = R(v[(size_t)nb * NPE + node]);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) qpre[r][d] = R(q[((size_t)nb * DIM + d) * NPE + node]);
+          hasnb |= 1 << r;
+        }
+      }
+    }
+  }
   R vn = R(0), qn[DIM];
   if (own) {
     vn = R(v[(size_t)(e0 + e) * NPE + n]);
@@ -182,19 +248,14 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_r(KArgs a) {
   }
   __syncthreads();
   if (own) {
-    const MPar<R>& mp = MPs[e];
-    R fl[DIM];
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) fl[d] = CONV ? mp.kappa * qn[d] + mp.beta[d] * vn : mp.kappa * qn[d];
-    const R dj = Gs[e][G::DETJ];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-      R s = R(0);
+      R s = CONV ? Ak[e][k][DIM] * vn : R(0);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) s += Gs[e][G::JINV + k * DIM + d] * fl[d];
-      Gk[e][k][n] = dj * s;
+      for (int d = 0; d < DIM; ++d) s += Ak[e][k][d] * qn[d];
+      Gk[e][k][n] = s;
     }
-    if (tterm) Hs[e][n] = a0dt * dj * vn;
+    if (tterm) Hs[e][n] = a0dt * Gs[e][G::DETJ] * vn;
     // own v and q.n at the face nodes this node lies on
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -211,7 +272,10 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_r(KArgs a) {
   __syncthreads();
 
   // ---- phase 1: numerical flux at the face nodes; volume contractions along axis 0
-  for (int it = t; it < NE * NF * NFN; it += NT) {
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    if (it >= NFI) break;
     const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
     R fh = R(0);
     if (el < ne) {
@@ -223,15 +287,11 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_r(KArgs a) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) bn += mp.beta[d] * nrm[d];
       }
-      const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
-      if (nb >= 0) {
-        const int code = a.nbf[(size_t)(e0 + el) * NF + f];
-        const int jn = a.perm[(code >> 3) * NFN + j];
-        const int node = lin_face_node<DIM, N1>(code & 7, jn);
-        const R vp = R(v[(size_t)nb * NPE + node]);
+      if ((hasnb >> r) & 1) {
+        const R vp = vpre[r];
         R qpn = R(0);
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) qpn += nrm[d] * R(q[((size_t)nb * DIM + d) * NPE + node]);
+        for (int d = 0; d < DIM; ++d) qpn += nrm[d] * qpre[r][d];
         fh = mp.tau * (vm - vp) + (R(0.5) * mp.kappa) * (qmn + qpn);
         if (CONV) fh += bn * (bn >= R(0) ? vm : vp);
       } else {
@@ -281,13 +341,17 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_r(KArgs a) {
     if constexpr (DIM == 2) {
       R s = R(0);
 #pragma unroll
-      for (int m = 0; m < N1; ++m) s += mr[m] * Tk[e][0][b1 + m * N1] + cr[m] * Tk[e][1][b1 + m * N1];
+      for (int m = 0; m < N1; ++m) {
+        s += mr[m] * Tk[e][0][b1 + m * N1];
+        s += cr[m] * Tk[e][1][b1 + m * N1];
+      }
       rv = -s;
     } else {
       R sa = R(0), sc = R(0);
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
-        sa += mr[m] * Tk[e][0][b1 + m * N1] + cr[m] * Tk[e][1][b1 + m * N1];
+        sa += mr[m] * Tk[e][0][b1 + m * N1];
+        sa += cr[m] * Tk[e][1][b1 + m * N1];
         sc += mr[m] * Tk[e][2][b1 + m * N1];
       }
       Gk[e][0][n] = sa;
@@ -314,7 +378,10 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT) k_lin_r(KArgs a) {
       const int b2 = n - id[2] * N1 * N1;
       R s = R(0);
 #pragma unroll
-      for (int m = 0; m < N1; ++m) s += mr[m] * Gk[e][0][b2 + m * N1 * N1] + cr[m] * Gk[e][1][b2 + m * N1 * N1];
+      for (int m = 0; m < N1; ++m) {
+        s += mr[m] * Gk[e][0][b2 + m * N1 * N1];
+        s += cr[m] * Gk[e][1][b2 + m * N1 * N1];
+      }
       rv = -s;
     }
     __syncthreads();
@@ -397,12 +464,17 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_q(KArgs a) {
   extern __shared__ __align__(16) unsigned char sim_dsm[];
   R* ops = (R*)sim_dsm;
   __shared__ R Gs[NE][GEO];
+  __shared__ R Cf[NE][NF];            // sJ_f / det J
   __shared__ R Vs[NE][NPE];
   __shared__ R Ds[NE][NF][NFN];
   const int t = threadIdx.x;
   const R* lo = lin_ops<R>(a);
   for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
   for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
+  for (int i = t; i < ne * NF; i += NT) {
+    const double* g = a.geo + (size_t)(e0 + i / NF) * GEO;
+    Cf[i / NF][i % NF] = R(g[G::FACE + (i % NF) * (DIM + 1) + DIM] / g[G::DETJ]);
+  }
   const double* v = (const double*)a.u;
   const int e = t / NPE, n = t - e * NPE;
   const bool own = e < ne;
@@ -416,11 +488,10 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_q(KArgs a) {
       const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
       if (nb >= 0) {
         const int code = a.nbf[(size_t)(e0 + el) * NF + f];
-        d = R(0.5) * (vm - R(v[(size_t)nb * NPE + sim_nbr_node<EL>(a, code, j)]));
+        d = (vm - R(v[(size_t)nb * NPE + sim_nbr_node<EL>(a, code, j)])) * (R(0.5) * Cf[el][f]);
       } else {
-        d = vm;
+        d = vm * Cf[el][f];
       }
-      d *= Gs[el][G::FACE + f * (DIM + 1) + DIM] / Gs[el][G::DETJ];
     }
     Ds[el][f][j] = d;
   }
@@ -471,6 +542,7 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
   R* ops = (R*)sim_dsm;
   __shared__ R Gs[NE][GEO];
   __shared__ MPar<R> MPs[NE];
+  __shared__ R Ak[NE][DIM][DIM + 1];  // g_k = sum_d Ak[k][d] q_d + Ak[k][DIM] v
   __shared__ R Gk[NE][DIM][NPE];
   __shared__ R Hs[NE][NPE];
   __shared__ R FV[NE][NF][NFN];
@@ -481,6 +553,18 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
   for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
   for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
   for (int i = t; i < NE; i += NT) MPs[i] = mpar<R>(i < ne ? elem_mp(a, e0 + i) : a.mp);
+  for (int i = t; i < ne * DIM; i += NT) {
+    const int el = i / DIM, k = i % DIM;
+    const double* g = a.geo + (size_t)(e0 + el) * GEO;
+    const ModelParams mp = elem_mp(a, e0 + el);
+    double bsum = 0.0;
+    for (int d = 0; d < DIM; ++d) {
+      const double jd = g[G::DETJ] * g[G::JINV + k * DIM + d];
+      Ak[el][k][d] = R(mp.kappa * jd);
+      bsum += jd * mp.beta[d];
+    }
+    Ak[el][k][DIM] = CONV ? R(bsum) : R(0);
+  }
   const double* v = (const double*)a.u;
   const QT* q = (const QT*)a.q;
   const R a0dt = R(a.a0dt);
@@ -495,19 +579,14 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
   }
   __syncthreads();
   if (own) {
-    const MPar<R>& mp = MPs[e];
-    R fl[DIM];
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) fl[d] = CONV ? mp.kappa * qn[d] + mp.beta[d] * vn : mp.kappa * qn[d];
-    const R dj = Gs[e][G::DETJ];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-      R s = R(0);
+      R s = CONV ? Ak[e][k][DIM] * vn : R(0);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) s += Gs[e][G::JINV + k * DIM + d] * fl[d];
-      Gk[e][k][n] = dj * s;
+      for (int d = 0; d < DIM; ++d) s += Ak[e][k][d] * qn[d];
+      Gk[e][k][n] = s;
     }
-    if (tterm) Hs[e][n] = a0dt * dj * vn;
+    if (tterm) Hs[e][n] = a0dt * Gs[e][G::DETJ] * vn;
     for_node_faces<EL>(n, [&](int f, int j) {
       R s = R(0);
 #pragma unroll

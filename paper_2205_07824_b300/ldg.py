@@ -22,7 +22,7 @@ POISSON, CONVDIFF, EULER, NS = 0, 1, 2, 3
 STEADY, BDF1, BDF2 = 0, 1, 2
 DIRK11, DIRK22, DIRK33, DIRK34 = 1, 2, 3, 4
 FP64, FP32 = 0, 1
-PC_NONE, PC_BJACOBI, PC_MLP = 0, 1, 2
+PC_NONE, PC_BJACOBI, PC_MLP, PC_MLP_BJ = 0, 1, 2, 3
 FORCING_FIXED, FORCING_LAST = 0, 1
 BASIS_FP64, BASIS_F32X2 = 0, 1
 JV_AUTO, JV_STAGE = 0, 1
@@ -138,6 +138,10 @@ def lib():
         L.ldg_mlp_train.argtypes = [vp, dp, dp, dp, ctypes.c_int64, ctypes.POINTER(TrainOpts),
                                     ctypes.POINTER(TrainReport)]
         L.ldg_mlp_apply.argtypes = [vp, dp, dp, dp]
+        L.ldg_newton_collect_updates.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(SolveReport)]
+        L.ldg_halo_features.argtypes = [vp, dp, dp]
+        L.ldg_mlp_bj_apply.argtypes = [vp, dp, dp]
         L.ldg_newton_gmres_collect.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(SolveReport)]
         L.ldg_q.argtypes = [vp, dp, dp]
@@ -384,6 +388,32 @@ class LDG:
                                                    _ptr(T, capacity * n, "T"), _ptr(U, capacity * n, "U"),
                                                    capacity, ctypes.byref(cnt), ctypes.byref(rep)))
         return cnt.value, rep.as_dict()
+
+    def newton_collect_updates(self, u, X, T, U, capacity, which=1):
+        """Block-Jacobi Newton-GMRES that stores (residual, update) pairs as features and
+        targets ([capacity][n_dof] each): X = BJ^-1 r, U = its scaled neighbour traces, T = the
+        update. which: 1 Newton steps (R(u_k), delta_k), 2 Arnoldi steps (J z_j, z_j), 3 both."""
+        rep = SolveReport()
+        cnt = ctypes.c_int(0)
+        n = self.n_dof
+        self._check(lib().ldg_newton_collect_updates(self._h, _ptr(u, n, "u"), _ptr(X, capacity * n, "X"),
+                                                     _ptr(T, capacity * n, "T"), _ptr(U, capacity * n, "U"),
+                                                     capacity, int(which), ctypes.byref(cnt), ctypes.byref(rep)))
+        return cnt.value, rep.as_dict()
+
+    def halo_features(self, z, out=None):
+        """Neighbour traces of z at each element's face nodes, scaled by 1 / ||z_K||."""
+        out = self.empty() if out is None else out
+        n = self.n_dof
+        self._check(lib().ldg_halo_features(self._h, _ptr(z, n, "z"), _ptr(out, n, "out")))
+        return out
+
+    def mlp_bj_apply(self, x, out=None):
+        """The learned block-Jacobi correction y = M(x) (after precond_setup)."""
+        out = self.empty() if out is None else out
+        n = self.n_dof
+        self._check(lib().ldg_mlp_bj_apply(self._h, _ptr(x, n, "x"), _ptr(out, n, "out")))
+        return out
 
     def jvp_noalloc(self, u, v, out):
         """J.v through ldg_jvp_noalloc (static device scratch; no allocation in the call)."""
