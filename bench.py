@@ -681,7 +681,7 @@ def run_batch(args):
         pass
     hbm = float(peaks.get("hbm_gbs", 6400.0))
     roofline = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": hbm, "frac": achieved / hbm,
-                "traffic": None, "kernel": "batched J.v (q-stage + residual, all order groups)",
+                "traffic": None, "kernel": "batched J.v (k_lin_q + k_lin_r over the quadrilateral order groups)",
                 "launch_ms": jv_ms, "bytes_per_dof": BATCH_JV_BYTES_PER_DOF,
                 "peak_source": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"}
 
@@ -766,7 +766,7 @@ def run_hex(args):
     """J.v throughput of the 3-D convection-diffusion operator, p = 1..6 (p = 4 is the headline)."""
     from paper_2205_07824_b300 import synth
     jv_sweep(args, lambda: synth.hex_box(48), (1e-2, 1.0, 1.0, 0.5, 0.25), 4, HEX_JV_BYTES_PER_DOF, HEX_WORKLOAD,
-             "k_qstage + k_residual (MODE_HOM, float), hex p = 4")
+             "FP32 J.v, hex p = 4")
 
 
 def run_tri(args):
@@ -774,7 +774,7 @@ def run_tri(args):
     (p = 6 is the headline)."""
     from paper_2205_07824_b300 import synth
     jv_sweep(args, lambda: synth.tri_square(256), (1e-2, 1.0, 1.0, 0.5), 6, TRI_JV_BYTES_PER_DOF, TRI_WORKLOAD,
-             "k_qstage + k_residual (MODE_HOM, float), triangles p = 6")
+             "FP32 J.v, triangles p = 6")
 
 
 def jv_sweep(args, make_mesh, mu, head_p, bytes_per_dof, workload, kernel_label):
@@ -824,9 +824,11 @@ def jv_sweep(args, make_mesh, mu, head_p, bytes_per_dof, workload, kernel_label)
             key = "fp64" if prec == 0 else "fp32"
             row[key] = {"ms": ms, "gdofs": g.n_dof / (ms * 1e-3) / 1e9, "tile": tile,
                         "hbm_frac": bytes_per_dof * g.n_dof / (ms * 1e-3) / 1e9 / hbm}
+            row[key]["kernels"] = g.jv_kernels(prec)
             row["n_dof"] = g.n_dof
             if p == head_p and prec == 1:
                 head = (g.n_dof, ms, tile)
+                kernel_label = g.jv_kernels(prec)
             del g, u, v, out
             torch.cuda.empty_cache()
         sweep.append(row)
@@ -890,6 +892,7 @@ def run_tet(args):
         ms = graph_time_ms(g, lambda: g.jvp_prec(prec, u, v, out), args.jv_reps)
         jv["fp32" if prec else "fp64"] = {"ms": ms, "gdofs": g.n_dof / (ms * 1e-3) / 1e9, "tile": tile,
                                           "hbm_frac": TET_JV_BYTES_PER_DOF * g.n_dof / (ms * 1e-3) / 1e9 / hbm}
+        jv["fp32" if prec else "fp64"]["kernels"] = g.jv_kernels(prec)
         if prec:
             g32 = g
     # the solve: FP32 Krylov + block-Jacobi from u = 0, timed steps (each a full solve)
@@ -923,7 +926,7 @@ def run_tet(args):
                        "l2": "flushed (256 MiB write) before each timed solve; J.v graph-timed"},
             "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": hbm, "frac": achieved / hbm,
                          "traffic": None, "bytes_per_dof": TET_JV_BYTES_PER_DOF,
-                         "kernel": f"k_qstage + k_residual (MODE_HOM, float), TetEl<{p},{p + 2}>",
+                         "kernel": g32.jv_kernels(1),
                          "peak_source": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"},
             "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk}
     print(json.dumps(line), flush=True)

@@ -128,9 +128,9 @@ typedef struct {
                            and of the preconditioner. Newton residuals, Arnoldi, Givens and all
                            vectors stay FP64. */
   int precond;          /* LDG_PC_NONE (default), LDG_PC_BJACOBI, LDG_PC_MLP or LDG_PC_MLP_BJ
-                           (flexible right preconditioning; the learned ones fall back to
-                           block-Jacobi when a linear solve misses its tolerance; see the
-                           learned-preconditioner section below) */
+                           (flexible right preconditioning; a linear solve with a learned one
+                           that misses its tolerance within two restart cycles is redone with
+                           block-Jacobi; see the learned-preconditioner section below) */
   int pc_refresh;       /* rebuild the preconditioner every pc_refresh Newton iterations
                            (0 = once per ldg_newton_gmres call, at the initial guess) */
   int newton_forcing;   /* linear tolerance eta_k of Newton step k (inexact Newton):
@@ -340,6 +340,50 @@ int ldg_newton_collect_updates(ldg_ctx* ctx, double* u_dev, double* X_dev, doubl
                                int capacity, int which, int* count, ldg_solve_report* rep);
 int ldg_halo_features(ldg_ctx* ctx, const double* z_dev, double* h_dev);
 int ldg_mlp_bj_apply(ldg_ctx* ctx, const double* x_dev, double* y_dev);
+
+/* Stages of R and J.v for element-sharded use (one context per rank, Section 3.5's MPI
+ * design on GPUs): the rank's mesh lists its owned elements first, then ghost copies of
+ * the face neighbours that other ranks own. A stage computes elements [0, n_owned) only
+ * and reads the neighbours' values, ghosts included, from the input vectors, so that the
+ * caller can exchange the ghosts' u before the q-stage and their q before the residual
+ * stage (FP64 arithmetic; device vectors laid out as for the whole local mesh).
+ *   ldg_q_stage:        q of Eq. 1a of u into q_dev [n_elem][n_cu][dim][n_pe] (models with q);
+ *   ldg_residual_stage: R of Eq. 1b from u and q (q_dev may be NULL for Euler).
+ * mode LDG_STAGE_R evaluates R(u) with boundary data, source and the time term of
+ * ldg_set_time; LDG_STAGE_HOM the homogeneous operator of a linear model, whose value at v
+ * is J v. Entries of the outputs beyond n_owned elements are left unchanged.
+ * Errors: LDG_ERR_ARG (null pointers, n_owned outside [0, n_elem], bad mode, HOM for a
+ * nonlinear model, q missing for a model with q). */
+enum { LDG_STAGE_R = 0, LDG_STAGE_HOM = 1 };
+int ldg_q_stage(ldg_ctx* ctx, int mode, int64_t n_owned, const double* u_dev, double* q_dev);
+int ldg_residual_stage(ldg_ctx* ctx, int mode, int64_t n_owned, const double* u_dev, const double* q_dev,
+                       double* r_dev);
+
+/* Element-sharded R, J.v and GMRES over ranks (one context per rank, local mesh as for
+ * the stage calls above). The caller supplies the transport:
+ *   exchange_ghosts: fill the ghost elements' blocks (elements [n_owned, n_elem) of `block`
+ *                    doubles each) of the element-major device vector dev_x from the ranks
+ *                    that own them;
+ *   allreduce_sum:   replace the `count` doubles at dev_buf by their sum over all ranks.
+ * Both are called after the context's stream has drained, must complete before they return
+ * and return 0 on success. Every rank must make the same sequence of calls.
+ * ldg_shard_setup records n_owned and the transport (allocates a q buffer and reduction
+ * scratch). ldg_shard_residual: R(u) (stage R, time term included); ldg_shard_jvp: J v of a
+ * linear model; both exchange their input's ghosts first (the input is written there) and
+ * write the owned elements of the output. ldg_shard_gmres: GMRES(m) on J x = b (linear
+ * models) from x = 0 to gmres_rtol, classical Gram-Schmidt with one re-orthogonalisation,
+ * Givens rotations on the host, every dot product summed over the ranks; x full length
+ * (its ghost blocks are used as scratch). Errors: LDG_ERR_ARG (no setup, nonlinear model
+ * for J.v or GMRES), LDG_ERR_CUDA (a transport call returned non-zero), LDG_ERR_MAXIT. */
+typedef struct {
+  void* user;
+  int (*exchange_ghosts)(void* user, double* dev_x, int block, void* cuda_stream);
+  int (*allreduce_sum)(void* user, double* dev_buf, int count, void* cuda_stream);
+} ldg_comm;
+int ldg_shard_setup(ldg_ctx* ctx, int64_t n_owned, const ldg_comm* comm);
+int ldg_shard_residual(ldg_ctx* ctx, double* u_dev, double* r_dev);
+int ldg_shard_jvp(ldg_ctx* ctx, double* v_dev, double* jv_dev);
+int ldg_shard_gmres(ldg_ctx* ctx, const double* b_dev, double* x_dev, ldg_solve_report* rep);
 
 /* q of Eq. 1a for diffusion models: q_dev [n_elem][n_cu][dim][n_pe]. */
 int ldg_q(ldg_ctx* ctx, const double* u_dev, double* q_dev);

@@ -53,6 +53,7 @@ def lib():
         L.orc_set_time.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
         for name in ("orc_residual", "orc_q", "orc_mass"):
             getattr(L, name).argtypes = [ctypes.c_void_p, _D, _D]
+        L.orc_residual_with_q.argtypes = [ctypes.c_void_p, _D, _D, _D]
         L.orc_jvp.argtypes = [ctypes.c_void_p, _D, _D, _D]
         L.orc_residual_some.argtypes = [ctypes.c_void_p, _D, ctypes.c_int64, _I64, _D]
         L.orc_jvp_some.argtypes = [ctypes.c_void_p, _D, _D, ctypes.c_int64, _I64, _D]
@@ -216,6 +217,13 @@ class Oracle:
         u, v = _c(u), _c(v)
         r = np.empty(self.ndof)
         lib().orc_jvp(self._h, _p(u), _p(v), _p(r))
+        return r
+
+    def residual_with_q(self, u, q):
+        """R(u) of Eq. 1b with q given per element ([E][ncu][nd][npe]) instead of formed."""
+        u, q = _c(u), _c(q)
+        r = np.empty(self.ndof)
+        lib().orc_residual_with_q(self._h, _p(u), _p(q), _p(r))
         return r
 
     def residual_some(self, u, elems):

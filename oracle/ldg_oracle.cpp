@@ -1333,6 +1333,16 @@ void orc_jacobian_cs(void* h, const double* u, double* J) {
 }
 
 // q of every element (diffusion models): [E][ncu][nd][npe]
+// Residual (Eq. 1b) of every element with q taken from the caller's array instead of
+// the q-stage: the form an element-sharded evaluation needs, whose ghost elements carry
+// q computed on another rank.
+void orc_residual_with_q(void* h, const double* u, const double* q, double* r) {
+  Problem* P = (Problem*)h;
+  const int64_t nq = (int64_t)P->ncu() * P->nd() * P->ref.npe;
+  auto qof = [&](int64_t K) -> const double* { return P->model.kind == EULER ? nullptr : q + K * nq; };
+  for (int64_t K = 0; K < P->E; ++K) residual_elem(*P, u, K, qof, r + K * P->nloc());
+}
+
 void orc_q(void* h, const double* u, double* q) {
   Problem* P = (Problem*)h;
   int64_t nq = (int64_t)P->ncu() * P->nd() * P->ref.npe;

@@ -335,15 +335,15 @@ int build_graph(ldg_batch* b) {
   if ((rc = make_while(b, b->graph, 1u, cudaGraphCondAssignDefault, &wa))) return rc;
   if ((rc = make_while(b, wa.body, 0u, 0u, &wb))) return rc;
   if ((rc = make_while(b, wb.body, 0u, 0u, &wc))) return rc;
-  long long c0 = launch_counter();
+  long long c0 = launch_counter().load();
   rc = capture(b->graph, [&]() -> int {
     int r = emit_init(b, s);
     if (!r) r = join_while(b, s, wa);
     return r;
   });
   if (rc) return rc;
-  b->k_pre = launch_counter() - c0;
-  c0 = launch_counter();
+  b->k_pre = launch_counter().load() - c0;
+  c0 = launch_counter().load();
   rc = capture(wa.body, [&]() -> int {
     int r = emit_newton_head(b, s, wb.h, 1);
     if (!r) r = join_while(b, s, wb);
@@ -351,8 +351,8 @@ int build_graph(ldg_batch* b) {
     return r;
   });
   if (rc) return rc;
-  b->k_a = launch_counter() - c0;
-  c0 = launch_counter();
+  b->k_a = launch_counter().load() - c0;
+  c0 = launch_counter().load();
   rc = capture(wb.body, [&]() -> int {
     int r = emit_cycle_head(b, s, wc.h, 1);
     if (!r) r = join_while(b, s, wc);
@@ -360,11 +360,11 @@ int build_graph(ldg_batch* b) {
     return r;
   });
   if (rc) return rc;
-  b->k_b = launch_counter() - c0;
-  c0 = launch_counter();
+  b->k_b = launch_counter().load() - c0;
+  c0 = launch_counter().load();
   rc = capture(wc.body, [&]() -> int { return emit_arnoldi(b, s, wc.h, 1); });
   if (rc) return rc;
-  b->k_c = launch_counter() - c0;
+  b->k_c = launch_counter().load() - c0;
   // the captured kernels are counted when they execute, not here
   launch_counter() -= b->k_pre + b->k_a + b->k_b + b->k_c;
   BK(cudaGraphInstantiate(&b->exec, b->graph, 0));

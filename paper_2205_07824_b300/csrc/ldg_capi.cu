@@ -42,8 +42,8 @@ void register_all(std::vector<KernelSet>& reg) {
   register_curved_scalar_t<Tile0>(reg); register_curved_gas_t<Tile0>(reg);
   register_curved_scalar_t<Tile1>(reg); register_curved_gas_t<Tile1>(reg);
 }
-long long& launch_counter() {
-  static long long n = 0;
+std::atomic<long long>& launch_counter() {
+  static std::atomic<long long> n{0};
   return n;
 }
 }  // namespace ldg
@@ -730,7 +730,6 @@ int ensure_halo(ldg_ctx* ctx) {
   const int nfq = ctx->nfq;
   if (et == LDG_HEX && ctx->nq != p + 1)
     return fail(ctx, LDG_ERR_UNSUPPORTED, "halo features on hexahedra need p + 1 quadrature points");
-  if (ctx->pg > 0) return fail(ctx, LDG_ERR_UNSUPPORTED, "halo features are built for affine elements");
   std::vector<int> tab((size_t)ctx->E * npe * 3, -1);
   for (int64_t K = 0; K < ctx->E; ++K)
     for (int f = 0; f < nf; ++f) {
@@ -741,7 +740,7 @@ int ensure_halo(ldg_ctx* ctx) {
         int jn;
         if (et == LDG_TET) jn = ctx->h_perm[(size_t)orient * nfn + j];
         else if (et == LDG_HEX) jn = ctx->h_perm[(size_t)orient * nfq + j];
-        else jn = ctx->h_perm[(size_t)orient * nfq] != 0 ? nfn - 1 - j : j;   // edges: same or reversed
+        else jn = ctx->h_perm[(size_t)orient * nfq] != 0 ? nfn - 1 - j : j;   // edges (also curved): same or reversed
         const int own = face_node_host(et, p, f, j), other = face_node_host(et, p, nface, jn);
         int* slot = &tab[((size_t)K * npe + own) * 3];
         int t = 0;
@@ -898,6 +897,8 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
   return fail(ctx, LDG_ERR_MAXIT, "GMRES did not reach its tolerance within max_restarts cycles");
 }
 
+constexpr int kLearnedRestarts = 2;
+
 int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
   const int64_t n = ctx->ndof;
   KrySmall S{ctx->m};
@@ -924,8 +925,15 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
     }
     if (ctx->opt.precond == LDG_PC_MLP && k == 0 && (rc = ensure_pc_storage(ctx))) return rc;
     const double eta = newton_forcing_eta(ctx->opt.newton_forcing, ctx->opt.gmres_rtol, ctx->opt.newton_rtol, r0, rn);
+    const bool learned = ctx->opt.precond == LDG_PC_MLP || ctx->opt.precond == LDG_PC_MLP_BJ;
+    // a learned preconditioner gets two restart cycles to reach the tolerance before the
+    // solve is redone with block-Jacobi, so that a network that does not fit the operator
+    // costs at most 2 m extra Krylov steps per linear solve
+    const int restarts = ctx->opt.max_restarts;
+    if (learned) ctx->opt.max_restarts = std::min(restarts, kLearnedRestarts);
     rc = do_gmres(ctx, u, res, del, eta, rep);
-    if (rc == LDG_ERR_MAXIT && (ctx->opt.precond == LDG_PC_MLP || ctx->opt.precond == LDG_PC_MLP_BJ)) {
+    ctx->opt.max_restarts = restarts;
+    if (rc == LDG_ERR_MAXIT && learned) {
       // the learned preconditioner did not reach the tolerance: fall back to block-Jacobi
       const int learned = ctx->opt.precond;
       ctx->opt.precond = LDG_PC_BJACOBI;
@@ -1110,7 +1118,7 @@ extern "C" {
 
 const char* ldg_version(void) { return "ldg-b300 0.1 (sm_103a)"; }
 
-int64_t ldg_kernel_launches(void) { return (int64_t)launch_counter(); }
+int64_t ldg_kernel_launches(void) { return (int64_t)launch_counter().load(); }
 
 const char* ldg_last_error(const ldg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
@@ -1127,6 +1135,7 @@ int ldg_destroy(ldg_ctx* ctx) {
   cudaFree(ctx->d_probe); cudaFree(ctx->d_jp); cudaFree(ctx->d_status);
   cudaFree(ctx->d_stage); cudaFree(ctx->d_lops); cudaFree(ctx->d_lopsf);
   cudaFree(ctx->d_halo); cudaFree(ctx->d_pcz); cudaFree(ctx->d_pch);
+  cudaFree(ctx->d_shq); cudaFree(ctx->d_shpart); cudaFree(ctx->d_shdot);
   cudaFree(ctx->d_er_xi); cudaFree(ctx->d_er_w); cudaFree(ctx->d_er_B); cudaFree(ctx->d_er_P); cudaFree(ctx->d_l2);
   {
     auto& M = ctx->mlp;
@@ -1400,6 +1409,33 @@ int ldg_set_time(ldg_ctx* ctx, int scheme, double t, double dt, const double* un
 int ldg_residual(ldg_ctx* ctx, const double* u, double* r) {
   if (!ctx || !ctx->ks || !u || !r) return LDG_ERR_ARG;
   return do_residual(ctx, u, r);
+}
+
+int ldg_q_stage(ldg_ctx* ctx, int mode, int64_t n_owned, const double* u, double* q) {
+  if (!ctx || !ctx->ks || !u || !q || (mode != LDG_STAGE_R && mode != LDG_STAGE_HOM) || n_owned < 0 ||
+      n_owned > ctx->E)
+    return LDG_ERR_ARG;
+  if (!ctx->ks->qstage) return fail(ctx, LDG_ERR_ARG, "ldg_q_stage: the model has no q (convection model)");
+  KArgs a = base_args(ctx);
+  a.E = (int)n_owned;
+  a.u = u; a.out = q;
+  CK(ctx->ks->qstage(mode == LDG_STAGE_R ? MODE_R : MODE_HOM, a, ctx->stream));
+  return LDG_OK;
+}
+
+int ldg_residual_stage(ldg_ctx* ctx, int mode, int64_t n_owned, const double* u, const double* q, double* r) {
+  if (!ctx || !ctx->ks || !u || !r || (mode != LDG_STAGE_R && mode != LDG_STAGE_HOM) || n_owned < 0 ||
+      n_owned > ctx->E)
+    return LDG_ERR_ARG;
+  if (ctx->ks->qstage && !q) return fail(ctx, LDG_ERR_ARG, "ldg_residual_stage: the model needs q");
+  if (mode == LDG_STAGE_HOM && !ctx->ks->linear)
+    return fail(ctx, LDG_ERR_ARG, "ldg_residual_stage: the homogeneous stage is the J.v of linear models only");
+  KArgs a = base_args(ctx);
+  a.E = (int)n_owned;
+  a.u = u; a.q = q; a.out = r;
+  if (mode == LDG_STAGE_R) a.hist = ctx->scheme != LDG_STEADY ? ctx->d_hist : nullptr;
+  CK(ctx->ks->residual(mode == LDG_STAGE_R ? MODE_R : MODE_HOM, a, ctx->stream));
+  return LDG_OK;
 }
 
 int ldg_jvp(ldg_ctx* ctx, const double* u, const double* v, double* jv) {

@@ -45,6 +45,12 @@ struct ldg_ctx {
   ldg::LinFn lin64 = nullptr, lin32 = nullptr;
   double* d_lops = nullptr;
   float* d_lopsf = nullptr;
+  // element-sharded use (ldg_shard_*): owned elements, the caller's transport, q and
+  // reduction buffers
+  int64_t shard_owned = 0;
+  ldg_comm shard_comm{};
+  double *d_shq = nullptr, *d_shpart = nullptr, *d_shdot = nullptr;
+  std::vector<double> h_shdot;
   double* d_stage = nullptr;   // ldg_jvp_host: device copies of u, v and J.v (3 n_dof, first use)
   // L2 projection / error rule (built on first use): points, weights, basis values,
   // projection operator, and per-element error partials [E][4]

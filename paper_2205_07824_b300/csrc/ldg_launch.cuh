@@ -1,6 +1,7 @@
 // Launch wrappers and the registry of compiled (element, order, quadrature, model)
 // kernel instances.
 #pragma once
+#include <atomic>
 #include <type_traits>
 #include <vector>
 
@@ -8,9 +9,10 @@
 
 namespace ldg {
 
-// Process-wide count of kernel launches issued by this library.
-long long& launch_counter();
-inline void count_launch() { ++launch_counter(); }
+// Process-wide count of kernel launches issued by this library (host threads driving
+// different contexts may launch at once).
+std::atomic<long long>& launch_counter();
+inline void count_launch() { launch_counter().fetch_add(1, std::memory_order_relaxed); }
 
 typedef cudaError_t (*StageFn)(int mode, const KArgs& a, cudaStream_t s);
 // columns col0 .. col0 + BLK_KT - 1 of the element-diagonal blocks (models without q)

@@ -26,6 +26,7 @@ PC_NONE, PC_BJACOBI, PC_MLP, PC_MLP_BJ = 0, 1, 2, 3
 FORCING_FIXED, FORCING_LAST = 0, 1
 BASIS_FP64, BASIS_F32X2 = 0, 1
 JV_AUTO, JV_STAGE = 0, 1
+STAGE_R, STAGE_HOM = 0, 1
 STATUS = {0: "LDG_OK", -1: "LDG_ERR_ARG", -2: "LDG_ERR_CUDA", -3: "LDG_ERR_UNSUPPORTED",
           -4: "LDG_ERR_NONFINITE", -5: "LDG_ERR_MAXIT", -6: "LDG_ERR_MESH"}
 
@@ -141,6 +142,12 @@ def lib():
         L.ldg_newton_collect_updates.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
                                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(SolveReport)]
         L.ldg_halo_features.argtypes = [vp, dp, dp]
+        L.ldg_q_stage.argtypes = [vp, ctypes.c_int, ctypes.c_int64, dp, dp]
+        L.ldg_residual_stage.argtypes = [vp, ctypes.c_int, ctypes.c_int64, dp, dp, dp]
+        L.ldg_shard_setup.argtypes = [vp, ctypes.c_int64, ctypes.c_void_p]
+        L.ldg_shard_residual.argtypes = [vp, dp, dp]
+        L.ldg_shard_jvp.argtypes = [vp, dp, dp]
+        L.ldg_shard_gmres.argtypes = [vp, dp, dp, ctypes.POINTER(SolveReport)]
         L.ldg_mlp_bj_apply.argtypes = [vp, dp, dp]
         L.ldg_newton_gmres_collect.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(SolveReport)]
@@ -414,6 +421,43 @@ class LDG:
         n = self.n_dof
         self._check(lib().ldg_mlp_bj_apply(self._h, _ptr(x, n, "x"), _ptr(out, n, "out")))
         return out
+
+    # ----------------------------------------------------- stages and sharded use
+    def q_stage(self, mode: int, n_owned: int, u, out):
+        """q of elements [0, n_owned) (``ldg_q_stage``; mode STAGE_R or STAGE_HOM)."""
+        self._check(lib().ldg_q_stage(self._h, mode, n_owned, _ptr(u, self.n_dof, "u"),
+                                      _ptr(out, self.n_dof * self.dim, "out")))
+        return out
+
+    def residual_stage(self, mode: int, n_owned: int, u, q, out):
+        """R (STAGE_R) or the homogeneous J.v (STAGE_HOM) of elements [0, n_owned)."""
+        qp = None if q is None else _ptr(q, self.n_dof * self.dim, "q")
+        self._check(lib().ldg_residual_stage(self._h, mode, n_owned, _ptr(u, self.n_dof, "u"), qp,
+                                             _ptr(out, self.n_dof, "out")))
+        return out
+
+    def shard_setup(self, n_owned: int, comm):
+        """Element-sharded use: owned elements [0, n_owned) and an ``ldg_comm`` transport
+        (``shard.make_comm``), which must stay alive as long as the context uses it."""
+        self._comm = comm
+        self._check(lib().ldg_shard_setup(self._h, n_owned, ctypes.byref(comm)))
+
+    def shard_residual(self, u, out=None):
+        out = self.empty() if out is None else out
+        self._check(lib().ldg_shard_residual(self._h, _ptr(u, self.n_dof, "u"), _ptr(out, self.n_dof, "out")))
+        return out
+
+    def shard_jvp(self, v, out=None):
+        out = self.empty() if out is None else out
+        self._check(lib().ldg_shard_jvp(self._h, _ptr(v, self.n_dof, "v"), _ptr(out, self.n_dof, "out")))
+        return out
+
+    def shard_gmres(self, b, x=None):
+        x = self.empty() if x is None else x
+        rep = SolveReport()
+        self._check(lib().ldg_shard_gmres(self._h, _ptr(b, self.n_dof, "b"), _ptr(x, self.n_dof, "x"),
+                                          ctypes.byref(rep)))
+        return x, rep.as_dict()
 
     def jvp_noalloc(self, u, v, out):
         """J.v through ldg_jvp_noalloc (static device scratch; no allocation in the call)."""
