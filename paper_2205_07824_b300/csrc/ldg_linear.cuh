@@ -81,17 +81,12 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   if (!cta_active(a, e0, ne)) return;
   __shared__ R ops[O::SIZE];
   __shared__ R Gs[NE][GEO];
-  __shared__ R Cf[NE][NF];            // sJ_f / det J
   __shared__ R Vs[NE][NPE];
   __shared__ R Ds[NE][NF][NFN];
   const int t = threadIdx.x;
   const R* lo = lin_ops<R>(a);
   for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
   for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
-  for (int i = t; i < ne * NF; i += NT) {
-    const double* g = a.geo + (size_t)(e0 + i / NF) * GEO;
-    Cf[i / NF][i % NF] = R(g[G::FACE + (i % NF) * (DIM + 1) + DIM] / g[G::DETJ]);
-  }
   const double* v = (const double*)a.u;
   const int e = t / NPE, n = t - e * NPE;
   const bool own = e < ne;
@@ -120,7 +115,7 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   if (own) Vs[e][n] = R(v[(size_t)(e0 + e) * NPE + n]);
   __syncthreads();
 
-  // Delta_f (sJ_f / det J) at the face nodes
+  // Delta_f = v- - vhat at the face nodes
 #pragma unroll
   for (int r = 0; r < ROUNDS; ++r) {
     const int it = t + r * NT;
@@ -129,13 +124,17 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
     R d = R(0);
     if (el < ne) {
       const R vm = Vs[el][lin_face_node<DIM, N1>(f, j)];
-      d = (hasnb >> r) & 1 ? (vm - vpre[r]) * (R(0.5) * Cf[el][f]) : vm * Cf[el][f];
+      d = (hasnb >> r) & 1 ? (vm - vpre[r]) * R(0.5) : vm;
     }
     Ds[el][f][j] = d;
   }
   __syncthreads();
   if (!own) return;
 
+  // On an affine element the outward normal of face xi_k = +-1 times its surface
+  // Jacobian is +-det J times row k of J^{-1} (Nanson's formula), so the lift of face
+  // 2k + side is +-Jinv[k][d] L_side(i_k) Delta and joins the derivative along axis k:
+  //   q_d = -sum_k Jinv[k][d] (D_k v - L_p(i_k) Delta_{2k+1} + L_0(i_k) Delta_{2k}).
   const int id[3] = {n % N1, (n / N1) % N1, DIM == 3 ? n / (N1 * N1) : 0};
   constexpr int STR[3] = {1, N1, N1 * N1};
   R gk[DIM];
@@ -143,7 +142,9 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   for (int k = 0; k < DIM; ++k) {
     const R* line = &Vs[e][n - id[k] * STR[k]];
     const R* dn = ops + O::DN + id[k] * N1;
-    R s = R(0);
+    const int jf = lin_face_index<DIM, N1>(k, id);
+    R s = ops[O::L + id[k]] * Ds[e][2 * k][jf];
+    s -= ops[O::L + N1 + id[k]] * Ds[e][2 * k + 1][jf];
 #pragma unroll
     for (int m = 0; m < N1; ++m) s += dn[m] * line[m * STR[k]];
     gk[k] = s;
@@ -155,13 +156,6 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
 #pragma unroll
     for (int k = 0; k < DIM; ++k) s -= Gs[e][G::JINV + k * DIM + d] * gk[k];
     qd[d] = s;
-  }
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    const int ax = f >> 1, side = f & 1;
-    const R lf = ops[O::L + side * N1 + id[ax]] * Ds[e][f][lin_face_index<DIM, N1>(ax, id)];
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) qd[d] += Gs[e][G::FACE + f * (DIM + 1) + d] * lf;
   }
   QT* q = (QT*)a.out;
 #pragma unroll
@@ -181,8 +175,8 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   if (!cta_active(a, e0, ne)) return;
   __shared__ R ops[O::SIZE];
   __shared__ R Gs[NE][GEO];
-  __shared__ MPar<R> MPs[NE];
   __shared__ R Ak[NE][DIM][DIM + 1];  // g_k = sum_d Ak[k][d] q_d + Ak[k][DIM] v
+  __shared__ R FC[NE][NF][DIM + 2];   // per face: kappa/2 sJ n_d, tau sJ, sJ beta.n
   __shared__ R Gk[NE][DIM][NPE];      // nodal fluxes g_k, later the axis-1 stage (3-D)
   __shared__ R Tk[NE][DIM][NPE];      // axis-0 stage
   __shared__ R Hs[NE][NPE];           // a0/dt det J v (time term)
@@ -193,7 +187,6 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   const R* lo = lin_ops<R>(a);
   for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
   for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
-  for (int i = t; i < NE; i += NT) MPs[i] = mpar<R>(i < ne ? elem_mp(a, e0 + i) : a.mp);
   for (int i = t; i < ne * DIM; i += NT) {
     // det J Jinv[k][.] (kappa q + beta v): per element kappa det J Jinv[k][d] and det J Jinv[k].beta
     const int el = i / DIM, k = i % DIM;
@@ -206,6 +199,19 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
       bsum += jd * mp.beta[d];
     }
     Ak[el][k][DIM] = CONV ? R(bsum) : R(0);
+  }
+  for (int i = t; i < ne * NF; i += NT) {
+    const int el = i / NF, f = i % NF;
+    const double* g = a.geo + (size_t)(e0 + el) * GEO + G::FACE + f * (DIM + 1);
+    const ModelParams mp = elem_mp(a, e0 + el);
+    const double sj = g[DIM];
+    double bn = 0.0;
+    for (int d = 0; d < DIM; ++d) {
+      FC[el][f][d] = R(0.5 * mp.kappa * sj * g[d]);
+      bn += mp.beta[d] * g[d];
+    }
+    FC[el][f][DIM] = R(mp.tau * sj);
+    FC[el][f][DIM + 1] = CONV ? R(sj * bn) : R(0);
   }
   const double* v = (const double*)a.u;
   const QT* q = (const QT*)a.q;
@@ -256,7 +262,7 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
       Gk[e][k][n] = s;
     }
     if (tterm) Hs[e][n] = a0dt * Gs[e][G::DETJ] * vn;
-    // own v and q.n at the face nodes this node lies on
+    // own v and kappa/2 sJ q.n at the face nodes this node lies on
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const int ax = f >> 1, fix = (f & 1) ? N1 - 1 : 0;
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
       const int j = lin_face_index<DIM, N1>(ax, id);
       R s = R(0);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) s += Gs[e][G::FACE + f * (DIM + 1) + d] * qn[d];
+      for (int d = 0; d < DIM; ++d) s += FC[e][f][d] * qn[d];
       FV[e][f][j] = vn;
       FQ[e][f][j] = s;
     }
@@ -277,28 +283,23 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
     const int it = t + r * NT;
     if (it >= NFI) break;
     const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+    // sJ fhat = tau sJ (v- - v+) + kappa/2 sJ (q- + q+).n + sJ beta.n v_upwind
+    // (Dirichlet faces: tau sJ v- + kappa sJ q-.n + sJ beta.n v- on outflow)
     R fh = R(0);
     if (el < ne) {
-      const MPar<R>& mp = MPs[el];
-      const R* nrm = &Gs[el][G::FACE + f * (DIM + 1)];
-      const R vm = FV[el][f][j], qmn = FQ[el][f][j];
-      R bn = R(0);
-      if (CONV) {
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) bn += mp.beta[d] * nrm[d];
-      }
+      const R* fc = FC[el][f];
+      const R vm = FV[el][f][j], qmn = FQ[el][f][j], bs = fc[DIM + 1];
       if ((hasnb >> r) & 1) {
         const R vp = vpre[r];
         R qpn = R(0);
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) qpn += nrm[d] * qpre[r][d];
-        fh = mp.tau * (vm - vp) + (R(0.5) * mp.kappa) * (qmn + qpn);
-        if (CONV) fh += bn * (bn >= R(0) ? vm : vp);
+        for (int d = 0; d < DIM; ++d) qpn += fc[d] * qpre[r][d];
+        fh = fc[DIM] * (vm - vp) + (qmn + qpn);
+        if (CONV) fh += bs * (bs >= R(0) ? vm : vp);
       } else {
-        fh = mp.tau * vm + mp.kappa * qmn;
-        if (CONV && bn >= R(0)) fh += bn * vm;
+        fh = fc[DIM] * vm + R(2) * qmn;
+        if (CONV && bs >= R(0)) fh += bs * vm;
       }
-      fh *= nrm[DIM];
     }
     FF[el][f][j] = fh;
   }
