@@ -315,6 +315,10 @@ def run_jv(args):
     t32, _ = timed(1, args.steps, args.warmup)
     jv32 = out.clone()
     ms32 = t32 / args.steps
+    # the (hi, lo) float-pair J.v (emulated FP64 on the FP32 pipes) on the same inputs
+    tff, _ = timed(2, args.steps, args.warmup)
+    jvff = out.clone()
+    msff = tff / args.steps
 
     peaks = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6400.0))
@@ -347,10 +351,12 @@ def run_jv(args):
         npe = g.n_pe
         r64 = jv64.view(-1, npe).cpu().numpy()[el]
         r32 = jv32.view(-1, npe).cpu().numpy()[el]
+        rff = jvff.view(-1, npe).cpu().numpy()[el]
         nr = np.linalg.norm(ref)
         samp = {"elements": int(len(el)), "stride": 1103,
                 "fp64_rel_err_vs_oracle": float(np.linalg.norm(r64 - ref) / nr),
-                "fp32_rel_err_vs_oracle": float(np.linalg.norm(r32 - ref) / nr)}
+                "fp32_rel_err_vs_oracle": float(np.linalg.norm(r32 - ref) / nr),
+                "f32x2_rel_err_vs_oracle": float(np.linalg.norm(rff - ref) / nr)}
         if not args.no_cpu_baseline:
             el_c, _, sec = jv_oracle_sample(mesh, uh, vh, 251)
             cpu = {"value": len(el_c) * npe / sec / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -394,6 +400,13 @@ def run_jv(args):
                            "fp32_jv": {"ms": ms32, "gdofs": n / (ms32 * 1e-3) / 1e9, "hbm_gbs": hbm32,
                                        "hbm_frac": hbm32 / hbm, "kernel": g.jv_kernels(1),
                                        "arithmetic": "FP32 (inputs, output and q scratch FP64 in memory)"},
+                           "f32x2_jv": {"ms": msff, "gdofs": n / (msff * 1e-3) / 1e9,
+                                        "hbm_gbs": JV_BYTES_PER_DOF * n / (msff * 1e-3) / 1e9,
+                                        "hbm_frac": JV_BYTES_PER_DOF * n / (msff * 1e-3) / 1e9 / hbm,
+                                        "kernel": g.jv_kernels(2),
+                                        "arithmetic": "(hi, lo) float pairs on the FP32 pipes, about 48 significand "
+                                                      "bits (emulated FP64); inputs and output FP64 in memory, q "
+                                                      "scratch float pairs"},
                            "oracle_sample": samp,
                            "solve_time_to_1e-8": solve},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -406,7 +419,7 @@ def run_jv(args):
 def run_jv_probe(args):
     """The default workload's J.v for profilers: the same context with a one-column Krylov
     space (about 1.5 GB on the device), no autotuning, `warmup + steps` FP64 J.v applications
-    then as many FP32 ones; prints the kernels it ran."""
+    then as many FP32 ones and as many float-pair ones; prints the kernels it ran."""
     import torch
     from paper_2205_07824_b300 import synth
     from paper_2205_07824_b300.ldg import LDG, CONVDIFF, CASE_EXPSIN
@@ -414,12 +427,12 @@ def run_jv_probe(args):
     u = g.interpolate(0.0)
     v = torch.randn(g.n_dof, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
     out = torch.empty_like(v)
-    for prec in (0, 1):
+    for prec in (0, 1, 2):
         for _ in range(args.warmup + args.steps):
             g.jvp_prec(prec, u, v, out)
     torch.cuda.synchronize()
     print(json.dumps({"probe": JV_WORKLOAD, "fp64": g.jv_kernels(0), "fp32": g.jv_kernels(1),
-                      "applications_each": args.warmup + args.steps}))
+                      "f32x2": g.jv_kernels(2), "applications_each": args.warmup + args.steps}))
 
 
 def vortex_solve_summary(args, stream):

@@ -124,9 +124,11 @@ typedef struct {
   int max_newton;       /* Newton iterations (default 20) */
   double newton_rtol;   /* stop when ||R(u_k)|| <= newton_rtol ||R(u_0)|| (default 1e-8) */
   double gmres_rtol;    /* linear solve: ||b - J x|| <= gmres_rtol ||b|| (default 1e-3) */
-  int krylov_precision; /* LDG_FP64 (default) or LDG_FP32: arithmetic of the J.v inside GMRES
-                           and of the preconditioner. Newton residuals, Arnoldi, Givens and all
-                           vectors stay FP64. */
+  int krylov_precision; /* LDG_FP64 (default), LDG_FP32 or LDG_F32X2: arithmetic of the J.v
+                           inside GMRES, and of the preconditioner for LDG_FP32 (LDG_F32X2 builds
+                           FP64 blocks). Newton residuals, Arnoldi, Givens and all vectors stay
+                           FP64. LDG_F32X2 is accepted where the float-pair J.v exists (see
+                           LDG_F32X2 below); ldg_create returns LDG_ERR_ARG elsewhere. */
   int precond;          /* LDG_PC_NONE (default), LDG_PC_BJACOBI, LDG_PC_MLP or LDG_PC_MLP_BJ
                            (flexible right preconditioning; a linear solve with a learned one
                            that misses its tolerance within two restart cycles is redone with
@@ -161,7 +163,15 @@ typedef struct {
                            other case. Results agree to rounding. */
 } ldg_options;
 
-enum { LDG_FP64 = 0, LDG_FP32 = 1 };
+/* Arithmetic of a J.v. LDG_FP64: FP64. LDG_FP32: every operation in FP32 (inputs and
+ * output FP64 in memory). LDG_F32X2: every operation on (hi, lo) float pairs carrying
+ * about 48 significand bits (Dekker's double-length arithmetic with error-free sums and
+ * products on the FP32 pipes: emulated FP64, accurate to a few 1e-14 relative where
+ * FP64 gives a few 1e-15); inputs and output FP64 in memory. LDG_F32X2 exists where the
+ * nodal J.v kernels serve: the linear models (Poisson, convection-diffusion) on affine
+ * quadrilaterals and hexahedra with p + 1 Gauss points per direction, and on triangles
+ * and tetrahedra with at least p + 2. */
+enum { LDG_FP64 = 0, LDG_FP32 = 1, LDG_F32X2 = 2 };
 enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1, LDG_PC_MLP = 2, LDG_PC_MLP_BJ = 3 };
 enum { LDG_FORCING_FIXED = 0, LDG_FORCING_LAST = 1 };
 enum { LDG_BASIS_FP64 = 0, LDG_BASIS_F32X2 = 1 };
@@ -235,12 +245,14 @@ int ldg_residual(ldg_ctx* ctx, const double* u_dev, double* r_dev);
  * for linear ones. */
 int ldg_jvp(ldg_ctx* ctx, const double* u_dev, const double* v_dev, double* jv_dev);
 
-/* J.v in a chosen arithmetic: LDG_FP64 (same as ldg_jvp) or LDG_FP32 (inputs and
- * output FP64 in memory; every operation of the operator in FP32). */
+/* J.v in a chosen arithmetic: LDG_FP64 (same as ldg_jvp), LDG_FP32 or LDG_F32X2 (inputs
+ * and output FP64 in memory; see the precision constants). LDG_ERR_ARG for LDG_F32X2 on
+ * a context without the float-pair kernels. */
 int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u_dev, const double* v_dev, double* jv_dev);
 
-/* Names the kernels that form this context's J.v in `precision` (LDG_FP64 / LDG_FP32)
- * and the case they serve, e.g. "k_lin_q + k_lin_r [hex p=4 nq=5 convdiff fp64, ...]".
+/* Names the kernels that form this context's J.v in `precision` (LDG_FP64 / LDG_FP32 /
+ * LDG_F32X2; "" where that arithmetic has no kernels) and the case they serve, e.g.
+ * "k_lin_q + k_lin_r [hex p=4 nq=5 convdiff fp64, ...]".
  * The string stays valid until the calling thread's next call of this function. */
 const char* ldg_jv_describe(const ldg_ctx* ctx, int precision);
 
@@ -259,7 +271,7 @@ int ldg_jvp_host(ldg_ctx* ctx, int precision, const double* u_host, const double
  * models with q (Navier-Stokes) skip their q(u) stage; other models compute exactly
  * what ldg_jvp_prec does. The caller guarantees that u is the state of that residual
  * call, unchanged since, and that no other residual call intervened (the result is
- * otherwise the Jacobian at the other state). precision: LDG_FP64 or LDG_FP32. */
+ * otherwise the Jacobian at the other state). precision: as ldg_jvp_prec. */
 int ldg_jvp_after_residual(ldg_ctx* ctx, int precision, const double* u_dev, const double* v_dev, double* jv_dev);
 
 /* Finite-difference J(u) v, the variant of Section 3.3 beside the exact derivative:

@@ -1,13 +1,15 @@
 // Compiled instances of the nodal J.v kernels of the linear models on simplices:
 // triangles p = 1..6 and tetrahedra p = 1..4 (Poisson and convection-diffusion), FP64
-// arithmetic with an FP64 q scratch and FP32 arithmetic with an FP32 q scratch. The
-// element traits' quadrature size does not enter these kernels.
+// arithmetic with an FP64 q scratch, FP32 arithmetic with an FP32 q scratch, and (hi, lo)
+// float-pair arithmetic with a float-pair q scratch. The element traits' quadrature size
+// does not enter these kernels.
 #include "ldg_launch.cuh"
 #include "ldg_linear.cuh"
 
 namespace ldg {
 
 template <class EL, bool CONV> LinFn sim_pick(int prec) {
+  if (prec == 2) return &launch_sim<EL, CONV, df, df>;
   return prec == 0 ? &launch_sim<EL, CONV, double, double> : &launch_sim<EL, CONV, float, float>;
 }
 
@@ -36,7 +38,7 @@ template <bool CONV> LinFn sim_by(int etype, int p, int prec) {
 }
 
 LinFn lin_simplex_launcher(int etype, int p, bool conv, int prec) {
-  if (prec != 0 && prec != 1) return nullptr;
+  if (prec < 0 || prec > 2) return nullptr;
   return conv ? sim_by<true>(etype, p, prec) : sim_by<false>(etype, p, prec);
 }
 

@@ -208,6 +208,18 @@ int do_residual(ldg_ctx* ctx, const double* u, double* r) {
 }
 
 int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv, int prec, bool q_ready) {
+  if (prec == LDG_F32X2) {
+    // float-pair arithmetic: the nodal kernels of the linear models only
+    if (!(ctx->ks->linear && ctx->ks->qstage && ctx->linff))
+      return fail(ctx, LDG_ERR_ARG,
+                  "LDG_F32X2: the float-pair J.v exists for the nodal kernels of the linear models only (affine "
+                  "quadrilaterals and hexahedra with p + 1 Gauss points, triangles and tetrahedra with at least "
+                  "p + 2)");
+    KArgs b = a;
+    b.u = v; b.out = jv;
+    CK(ctx->linff(b, ctx->d_dq, ctx->stream));
+    return LDG_OK;
+  }
   const bool f32 = prec == LDG_FP32;
   StageFn qs = f32 ? ctx->ks->qstage32 : ctx->ks->qstage;
   StageFn rs = f32 ? ctx->ks->residual32 : ctx->ks->residual;
@@ -361,7 +373,8 @@ int do_blocks(ldg_ctx* ctx, const double* u, int prec, double* blocks) {
 // elimination in shared memory), else FP64.
 int do_pc_setup(ldg_ctx* ctx, const double* u) {
   int rc;
-  const int prec = ctx->opt.krylov_precision;
+  // (a float-pair Krylov J.v takes FP64 blocks)
+  const int prec = ctx->opt.krylov_precision == LDG_FP32 ? LDG_FP32 : LDG_FP64;
   // the block storage must exist before its address is handed to the extraction
   if ((rc = ensure_pc_storage(ctx))) return rc;
   if ((rc = do_blocks(ctx, u, prec, ctx->d_blocks))) return rc;
@@ -1033,7 +1046,7 @@ const KernelSet* find_set(const ldg_ctx* ctx, int tile) {
 
 int autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms) {
   static std::map<std::tuple<int, int, int, int, int, int>, int> cache;
-  const int prec = ctx->opt.krylov_precision;
+  const int prec = ctx->opt.krylov_precision == LDG_FP32 ? LDG_FP32 : LDG_FP64;
   int eb = 0;
   while ((int64_t(1) << eb) < ctx->E) ++eb;
   // (curved elements are keyed apart as element type 3)
@@ -1190,7 +1203,7 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if (o.max_newton <= 0) o.max_newton = 20;
   if (o.newton_rtol <= 0) o.newton_rtol = 1e-8;
   if (o.gmres_rtol <= 0) o.gmres_rtol = 1e-3;
-  if (o.krylov_precision != LDG_FP32) o.krylov_precision = LDG_FP64;
+  if (o.krylov_precision != LDG_FP32 && o.krylov_precision != LDG_F32X2) o.krylov_precision = LDG_FP64;
   if (o.precond != LDG_PC_BJACOBI && o.precond != LDG_PC_MLP && o.precond != LDG_PC_MLP_BJ) o.precond = LDG_PC_NONE;
   if (o.pc_refresh < 0) o.pc_refresh = 0;
   if (o.newton_forcing != LDG_FORCING_LAST) o.newton_forcing = LDG_FORCING_FIXED;
@@ -1261,6 +1274,7 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
     const bool conv = ctx->model == LDG_CONVDIFF;
     ctx->lin64 = lin_launcher(ctx->dim, p, conv, 0);
     ctx->lin32 = lin_launcher(ctx->dim, p, conv, 1);
+    ctx->linff = lin_df_launcher(ctx->dim, p, conv);
     std::vector<double> lb;
     if (ctx->lin64 && ctx->lin32 && build_lin_ops(p, lb, err)) {
       std::vector<float> lf(lb.begin(), lb.end());
@@ -1269,7 +1283,7 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
       CK(cudaMalloc(&ctx->d_lopsf, lf.size() * sizeof(float)));
       CK(cudaMemcpy(ctx->d_lopsf, lf.data(), lf.size() * sizeof(float), cudaMemcpyHostToDevice));
     } else {
-      ctx->lin64 = ctx->lin32 = nullptr;
+      ctx->lin64 = ctx->lin32 = ctx->linff = nullptr;
     }
   }
   // the same on triangles and tetrahedra, whose stage kernels integrate exactly with at
@@ -1279,6 +1293,7 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
     const bool conv = ctx->model == LDG_CONVDIFF;
     ctx->lin64 = lin_simplex_launcher(ctx->etype, p, conv, 0);
     ctx->lin32 = lin_simplex_launcher(ctx->etype, p, conv, 1);
+    ctx->linff = lin_simplex_launcher(ctx->etype, p, conv, 2);
     std::vector<double> lb;
     if (ctx->lin64 && ctx->lin32 && build_lin_simplex_ops(ctx->etype, p, lb, err)) {
       std::vector<float> lf(lb.begin(), lb.end());
@@ -1287,8 +1302,14 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
       CK(cudaMalloc(&ctx->d_lopsf, lf.size() * sizeof(float)));
       CK(cudaMemcpy(ctx->d_lopsf, lf.data(), lf.size() * sizeof(float), cudaMemcpyHostToDevice));
     } else {
-      ctx->lin64 = ctx->lin32 = nullptr;
+      ctx->lin64 = ctx->lin32 = ctx->linff = nullptr;
     }
+  }
+  if (o.krylov_precision == LDG_F32X2 && !(ctx->ks->linear && ctx->linff)) {
+    ctx->err = "krylov_precision LDG_F32X2 needs the float-pair nodal J.v kernels: a linear model on affine "
+               "quadrilaterals or hexahedra with p + 1 Gauss points, or on triangles or tetrahedra with at least "
+               "p + 2";
+    return LDG_ERR_ARG;
   }
   CK(cudaMemcpy(ctx->d_geo, mp_.geo.data(), mp_.geo.size() * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_nbr, mp_.nbr.data(), mp_.nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1443,8 +1464,12 @@ int ldg_jvp(ldg_ctx* ctx, const double* u, const double* v, double* jv) {
   return jvp_args(ctx, base_args(ctx), u, v, jv, LDG_FP64);
 }
 
+static bool jv_precision_ok(int precision) {
+  return precision == LDG_FP64 || precision == LDG_FP32 || precision == LDG_F32X2;
+}
+
 int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u, const double* v, double* jv) {
-  if (!ctx || !ctx->ks || !u || !v || !jv || (precision != LDG_FP64 && precision != LDG_FP32)) return LDG_ERR_ARG;
+  if (!ctx || !ctx->ks || !u || !v || !jv || !jv_precision_ok(precision)) return LDG_ERR_ARG;
   return jvp_args(ctx, base_args(ctx), u, v, jv, precision);
 }
 
@@ -1454,8 +1479,16 @@ const char* ldg_jv_describe(const ldg_ctx* ctx, int precision) {
   const bool f32 = precision == LDG_FP32;
   static const char* el[] = {"tri", "quad", "hex", "tet"};
   static const char* md[] = {"poisson", "convdiff", "euler", "ns"};
-  const std::string what = std::string(el[ctx->etype]) + (ctx->pg ? " curved" : "") + " p=" + std::to_string(ctx->p) +
-                           " nq=" + std::to_string(ctx->nq) + " " + md[ctx->model] + (f32 ? " fp32" : " fp64");
+  std::string what = std::string(el[ctx->etype]) + (ctx->pg ? " curved" : "") + " p=" + std::to_string(ctx->p) +
+                     " nq=" + std::to_string(ctx->nq) + " " + md[ctx->model];
+  if (precision == LDG_F32X2) {
+    const bool sim = ctx->etype == LDG_TRI || ctx->etype == LDG_TET;
+    s = ctx->ks->linear && ctx->linff
+            ? std::string(sim ? "k_sim_q + k_sim_r [" : "k_lin_q + k_lin_r [") + what + " f32x2, q scratch f32x2]"
+            : "";
+    return s.c_str();
+  }
+  what += f32 ? " fp32" : " fp64";
   if (ctx->ks->linear && (f32 ? ctx->lin32 : ctx->lin64))
     s = std::string(ctx->etype == LDG_TRI || ctx->etype == LDG_TET ? "k_sim_q + k_sim_r [" : "k_lin_q + k_lin_r [") +
         what + ", q scratch " + (f32 ? "fp32" : "fp64") + "]";
@@ -1468,7 +1501,7 @@ const char* ldg_jv_describe(const ldg_ctx* ctx, int precision) {
 }
 
 int ldg_jvp_host(ldg_ctx* ctx, int precision, const double* u_host, const double* v_host, double* jv_host) {
-  if (!ctx || !ctx->ks || !v_host || !jv_host || (precision != LDG_FP64 && precision != LDG_FP32)) return LDG_ERR_ARG;
+  if (!ctx || !ctx->ks || !v_host || !jv_host || !jv_precision_ok(precision)) return LDG_ERR_ARG;
   if (!u_host && !ctx->ks->linear)
     return fail(ctx, LDG_ERR_ARG, "ldg_jvp_host: u_host may be NULL only for linear models");
   const size_t n = (size_t)ctx->ndof, bytes = n * sizeof(double);
@@ -1656,7 +1689,7 @@ int ldg_jvp_fd(ldg_ctx* ctx, int order, const double* u, const double* v, double
 }
 
 int ldg_jvp_after_residual(ldg_ctx* ctx, int precision, const double* u, const double* v, double* jv) {
-  if (!ctx || !ctx->ks || !u || !v || !jv || (precision != LDG_FP64 && precision != LDG_FP32)) return LDG_ERR_ARG;
+  if (!ctx || !ctx->ks || !u || !v || !jv || !jv_precision_ok(precision)) return LDG_ERR_ARG;
   return jvp_args(ctx, base_args(ctx), u, v, jv, precision, true);
 }
 

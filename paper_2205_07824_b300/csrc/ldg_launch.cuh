@@ -168,5 +168,7 @@ typedef cudaError_t (*LinFn)(const KArgs& a, void* qbuf, cudaStream_t s);
 LinFn lin_launcher(int dim, int p, bool conv, int prec);
 // The same on triangles (etype 0) and tetrahedra (etype 3), or null.
 LinFn lin_simplex_launcher(int etype, int p, bool conv, int prec);
+// The same hexahedron / quadrilateral kernels in double-float arithmetic (ldg_df.cuh).
+LinFn lin_df_launcher(int dim, int p, bool conv);
 
 }  // namespace ldg

@@ -23,6 +23,9 @@
 // the node's line from shared memory. q of the direction is stored in QT (double, or
 // float for the FP32-arithmetic J.v: it is internal scratch of the product).
 #pragma once
+#include <type_traits>
+
+#include "ldg_df.cuh"
 #include "ldg_kernels.cuh"
 
 namespace ldg {
@@ -41,9 +44,11 @@ template <int DIM, int N1> struct LinShape {
 };
 // Resident 256-thread CTAs asked of the register allocator: eight (32 registers a
 // thread) for the FP32 kernels, whose face gathers and barriers want every warp slot;
-// six (40 registers) for FP64, whose doubles would spill at 32 (measured on 48^3 p = 4).
+// six (40 registers) for FP64, whose doubles would spill at 32 (measured on 48^3 p = 4);
+// four (64 registers) for double-float, whose accumulators hold two floats and whose
+// error-free transformations keep several temporaries live.
 template <int NT, class R> struct LinMinBlocks {
-  static constexpr int value = NT > 256 ? 1 : (sizeof(R) == 4 ? 8 : 6);
+  static constexpr int value = NT > 256 ? 1 : (sizeof(R) == 4 ? 8 : (std::is_same<R, df>::value ? 4 : 6));
 };
 
 // local node of face-node j on face f = 2 axis + side (free axes ascending, first fastest)
@@ -63,9 +68,12 @@ template <int DIM, int N1> __device__ __forceinline__ int lin_face_index(int ax,
   else return ax == 0 ? id[1] + N1 * id[2] : (ax == 1 ? id[0] + N1 * id[2] : id[0] + N1 * id[1]);
 }
 
-template <class R> __device__ __forceinline__ const R* lin_ops(const KArgs& a) {
-  if constexpr (sizeof(R) == 8) return (const R*)a.lops;
-  else return (const R*)a.lopsf;
+// The operator blob a kernel in arithmetic R reads (double-float splits the FP64 one)
+template <class R> struct LinBlob { typedef double type; };
+template <> struct LinBlob<float> { typedef float type; };
+template <class R> __device__ __forceinline__ const typename LinBlob<R>::type* lin_ops(const KArgs& a) {
+  if constexpr (std::is_same<R, float>::value) return a.lopsf;
+  else return a.lops;
 }
 
 // ------------------------------------------------------------------ q-stage
@@ -75,6 +83,7 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   typedef LinOff<N1> O;
   typedef Geo<DIM> G;
   constexpr int NPE = S::NPE, NFN = S::NFN, NF = S::NF, NE = S::NE, NT = S::NT, GEO = S::GEO;
+  typedef typename AccOf<R>::type A;
   if (a.skip && *a.skip) return;
   const int e0 = blockIdx.x * NE;
   const int ne = min(NE, a.E - e0);
@@ -84,8 +93,8 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   __shared__ R Vs[NE][NPE];
   __shared__ R Ds[NE][NF][NFN];
   const int t = threadIdx.x;
-  const R* lo = lin_ops<R>(a);
-  for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
+  const auto* lo = lin_ops<R>(a);
+  for (int i = t; i < O::SIZE; i += NT) ops[i] = R(lo[i]);
   for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
   const double* v = (const double*)a.u;
   const int e = t / NPE, n = t - e * NPE;
@@ -143,19 +152,19 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
     const R* line = &Vs[e][n - id[k] * STR[k]];
     const R* dn = ops + O::DN + id[k] * N1;
     const int jf = lin_face_index<DIM, N1>(k, id);
-    R s = ops[O::L + id[k]] * Ds[e][2 * k][jf];
+    A s = A(ops[O::L + id[k]] * Ds[e][2 * k][jf]);
     s -= ops[O::L + N1 + id[k]] * Ds[e][2 * k + 1][jf];
 #pragma unroll
     for (int m = 0; m < N1; ++m) s += dn[m] * line[m * STR[k]];
-    gk[k] = s;
+    gk[k] = R(s);
   }
   R qd[DIM];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    R s = R(0);
+    A s = A(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) s -= Gs[e][G::JINV + k * DIM + d] * gk[k];
-    qd[d] = s;
+    qd[d] = R(s);
   }
   QT* q = (QT*)a.out;
 #pragma unroll
@@ -169,6 +178,7 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   typedef LinOff<N1> O;
   typedef Geo<DIM> G;
   constexpr int NPE = S::NPE, NFN = S::NFN, NF = S::NF, NE = S::NE, NT = S::NT, GEO = S::GEO;
+  typedef typename AccOf<R>::type A;
   if (a.skip && *a.skip) return;
   const int e0 = blockIdx.x * NE;
   const int ne = min(NE, a.E - e0);
@@ -184,8 +194,8 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   __shared__ R FQ[NE][NF][NFN];       // own q.n at the face nodes, later the second face contraction
   __shared__ R FF[NE][NF][NFN];       // sJ Fhat at the face nodes
   const int t = threadIdx.x;
-  const R* lo = lin_ops<R>(a);
-  for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
+  const auto* lo = lin_ops<R>(a);
+  for (int i = t; i < O::SIZE; i += NT) ops[i] = R(lo[i]);
   for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
   for (int i = t; i < ne * DIM; i += NT) {
     // det J Jinv[k][.] (kappa q + beta v): per element kappa det J Jinv[k][d] and det J Jinv[k].beta
@@ -256,23 +266,23 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   if (own) {
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-      R s = CONV ? Ak[e][k][DIM] * vn : R(0);
+      A s = CONV ? A(Ak[e][k][DIM] * vn) : A(0);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) s += Ak[e][k][d] * qn[d];
-      Gk[e][k][n] = s;
+      Gk[e][k][n] = R(s);
     }
-    if (tterm) Hs[e][n] = a0dt * Gs[e][G::DETJ] * vn;
+    if (tterm) Hs[e][n] = R(a0dt * Gs[e][G::DETJ]) * vn;
     // own v and kappa/2 sJ q.n at the face nodes this node lies on
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const int ax = f >> 1, fix = (f & 1) ? N1 - 1 : 0;
       if (id[ax] != fix) continue;
       const int j = lin_face_index<DIM, N1>(ax, id);
-      R s = R(0);
+      A s = A(0);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) s += FC[e][f][d] * qn[d];
       FV[e][f][j] = vn;
-      FQ[e][f][j] = s;
+      FQ[e][f][j] = R(s);
     }
   }
   __syncthreads();
@@ -291,10 +301,10 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
       const R vm = FV[el][f][j], qmn = FQ[el][f][j], bs = fc[DIM + 1];
       if ((hasnb >> r) & 1) {
         const R vp = vpre[r];
-        R qpn = R(0);
+        A qpn = A(0);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) qpn += fc[d] * qpre[r][d];
-        fh = fc[DIM] * (vm - vp) + (qmn + qpn);
+        fh = fc[DIM] * (vm - vp) + (qmn + R(qpn));
         if (CONV) fh += bs * (bs >= R(0) ? vm : vp);
       } else {
         fh = fc[DIM] * vm + R(2) * qmn;
@@ -308,7 +318,7 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
     const R* cr = ops + O::C + id[0] * N1;
     const R* mr = ops + O::M1 + id[0] * N1;
     const int b0 = n - id[0];
-    R ta = R(0), tb = R(0), tc = R(0);
+    A ta = A(0), tb = A(0), tc = A(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
       ta += cr[m] * Gk[e][0][b0 + m];
@@ -319,9 +329,9 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
 #pragma unroll
       for (int m = 0; m < N1; ++m) ta -= mr[m] * Hs[e][b0 + m];
     }
-    Tk[e][0][n] = ta;
-    Tk[e][1][n] = tb;
-    if constexpr (DIM == 3) Tk[e][2][n] = tc;
+    Tk[e][0][n] = R(ta);
+    Tk[e][1][n] = R(tb);
+    if constexpr (DIM == 3) Tk[e][2][n] = R(tc);
   }
   __syncthreads();
 
@@ -330,33 +340,33 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
     const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
     const int t0 = j % N1, rest = j - t0;
     const R* mr = ops + O::M1 + t0 * N1;
-    R s = R(0);
+    A s = A(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) s += mr[m] * FF[el][f][rest + m];
-    FV[el][f][j] = s;
+    FV[el][f][j] = R(s);
   }
   if (own) {
     const R* cr = ops + O::C + id[1] * N1;
     const R* mr = ops + O::M1 + id[1] * N1;
     const int b1 = n - id[1] * N1;
     if constexpr (DIM == 2) {
-      R s = R(0);
+      A s = A(0);
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
         s += mr[m] * Tk[e][0][b1 + m * N1];
         s += cr[m] * Tk[e][1][b1 + m * N1];
       }
-      rv = -s;
+      rv = -R(s);
     } else {
-      R sa = R(0), sc = R(0);
+      A sa = A(0), sc = A(0);
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
         sa += mr[m] * Tk[e][0][b1 + m * N1];
         sa += cr[m] * Tk[e][1][b1 + m * N1];
         sc += mr[m] * Tk[e][2][b1 + m * N1];
       }
-      Gk[e][0][n] = sa;
-      Gk[e][1][n] = sc;
+      Gk[e][0][n] = R(sa);
+      Gk[e][1][n] = R(sc);
     }
   }
   __syncthreads();
@@ -368,22 +378,22 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
       const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
       const int t0 = j % N1, t1 = j / N1;
       const R* mr = ops + O::M1 + t1 * N1;
-      R s = R(0);
+      A s = A(0);
 #pragma unroll
       for (int m = 0; m < N1; ++m) s += mr[m] * FV[el][f][t0 + m * N1];
-      FQ[el][f][j] = s;
+      FQ[el][f][j] = R(s);
     }
     if (own) {
       const R* cr = ops + O::C + id[2] * N1;
       const R* mr = ops + O::M1 + id[2] * N1;
       const int b2 = n - id[2] * N1 * N1;
-      R s = R(0);
+      A s = A(0);
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
         s += mr[m] * Gk[e][0][b2 + m * N1 * N1];
         s += cr[m] * Gk[e][1][b2 + m * N1 * N1];
       }
-      rv = -s;
+      rv = -R(s);
     }
     __syncthreads();
     FL = FQ;
@@ -458,6 +468,7 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_q(KArgs a) {
   typedef SimOff<EL> O;
   typedef Geo<EL::DIM> G;
   constexpr int DIM = EL::DIM, NPE = EL::NPE, NFN = EL::NFN, NF = EL::NF, NE = S::NE, NT = S::NT, GEO = S::GEO;
+  typedef typename AccOf<R>::type A;
   if (a.skip && *a.skip) return;
   const int e0 = blockIdx.x * NE;
   const int ne = min(NE, a.E - e0);
@@ -469,8 +480,8 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_q(KArgs a) {
   __shared__ R Vs[NE][NPE];
   __shared__ R Ds[NE][NF][NFN];
   const int t = threadIdx.x;
-  const R* lo = lin_ops<R>(a);
-  for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
+  const auto* lo = lin_ops<R>(a);
+  for (int i = t; i < O::SIZE; i += NT) ops[i] = R(lo[i]);
   for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
   for (int i = t; i < ne * NF; i += NT) {
     const double* g = a.geo + (size_t)(e0 + i / NF) * GEO;
@@ -502,27 +513,27 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_q(KArgs a) {
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
     const R* row = ops + O::DN + (k * NPE + n) * O::LDA;
-    R s = R(0);
+    A s = A(0);
 #pragma unroll 8
     for (int m = 0; m < NPE; ++m) s += row[m] * Vs[e][m];
-    gk[k] = s;
+    gk[k] = R(s);
   }
   R qd[DIM];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    R s = R(0);
+    A s = A(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) s -= Gs[e][G::JINV + k * DIM + d] * gk[k];
-    qd[d] = s;
+    qd[d] = R(s);
   }
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     const R* row = ops + O::LIFT + (f * NPE + n) * O::LDL;
-    R lf = R(0);
+    A lf = A(0);
 #pragma unroll
     for (int j = 0; j < NFN; ++j) lf += row[j] * Ds[e][f][j];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) qd[d] += Gs[e][G::FACE + f * (DIM + 1) + d] * lf;
+    for (int d = 0; d < DIM; ++d) qd[d] += Gs[e][G::FACE + f * (DIM + 1) + d] * R(lf);
   }
   QT* q = (QT*)a.out;
 #pragma unroll
@@ -535,6 +546,7 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
   typedef SimOff<EL> O;
   typedef Geo<EL::DIM> G;
   constexpr int DIM = EL::DIM, NPE = EL::NPE, NFN = EL::NFN, NF = EL::NF, NE = S::NE, NT = S::NT, GEO = S::GEO;
+  typedef typename AccOf<R>::type A;
   if (a.skip && *a.skip) return;
   const int e0 = blockIdx.x * NE;
   const int ne = min(NE, a.E - e0);
@@ -550,8 +562,8 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
   __shared__ R FQ[NE][NF][NFN];
   __shared__ R FF[NE][NF][NFN];
   const int t = threadIdx.x;
-  const R* lo = lin_ops<R>(a);
-  for (int i = t; i < O::SIZE; i += NT) ops[i] = lo[i];
+  const auto* lo = lin_ops<R>(a);
+  for (int i = t; i < O::SIZE; i += NT) ops[i] = R(lo[i]);
   for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
   for (int i = t; i < NE; i += NT) MPs[i] = mpar<R>(i < ne ? elem_mp(a, e0 + i) : a.mp);
   for (int i = t; i < ne * DIM; i += NT) {
@@ -582,18 +594,18 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
   if (own) {
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-      R s = CONV ? Ak[e][k][DIM] * vn : R(0);
+      A s = CONV ? A(Ak[e][k][DIM] * vn) : A(0);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) s += Ak[e][k][d] * qn[d];
-      Gk[e][k][n] = s;
+      Gk[e][k][n] = R(s);
     }
-    if (tterm) Hs[e][n] = a0dt * Gs[e][G::DETJ] * vn;
+    if (tterm) Hs[e][n] = R(a0dt * Gs[e][G::DETJ]) * vn;
     for_node_faces<EL>(n, [&](int f, int j) {
-      R s = R(0);
+      A s = A(0);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) s += Gs[e][G::FACE + f * (DIM + 1) + d] * qn[d];
       FV[e][f][j] = vn;
-      FQ[e][f][j] = s;
+      FQ[e][f][j] = R(s);
     });
   }
   __syncthreads();
@@ -613,10 +625,10 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
       if (nb >= 0) {
         const int node = sim_nbr_node<EL>(a, a.nbf[(size_t)(e0 + el) * NF + f], j);
         const R vp = R(v[(size_t)nb * NPE + node]);
-        R qpn = R(0);
+        A qpn = A(0);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) qpn += nrm[d] * R(q[((size_t)nb * DIM + d) * NPE + node]);
-        fh = mp.tau * (vm - vp) + (R(0.5) * mp.kappa) * (qmn + qpn);
+        fh = mp.tau * (vm - vp) + R(R(0.5) * mp.kappa) * (qmn + R(qpn));
         if (CONV) fh += bn * (bn >= R(0) ? vm : vp);
       } else {
         fh = mp.tau * vm + mp.kappa * qmn;
@@ -628,7 +640,7 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
   }
   __syncthreads();
   if (!own) return;
-  R r = R(0);
+  A r = A(0);
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
     const R* row = ops + O::C + (k * NPE + n) * O::LDA;
@@ -642,12 +654,10 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
   }
   for_node_faces<EL>(n, [&](int f, int j) {
     const R* row = ops + O::MF + j * O::LDL;
-    R s = R(0);
 #pragma unroll
-    for (int b = 0; b < NFN; ++b) s += row[b] * FF[e][f][b];
-    r += s;
+    for (int b = 0; b < NFN; ++b) r += row[b] * FF[e][f][b];
   });
-  ((double*)a.out)[(size_t)(e0 + e) * NPE + n] = (double)r;
+  ((double*)a.out)[(size_t)(e0 + e) * NPE + n] = (double)R(r);
 }
 
 template <class EL, bool CONV, class R, class QT>

@@ -3,7 +3,8 @@ triangles and tetrahedra (the same operator as the quadrature-point stage kernel
 exact nodal form) against the FP64 oracle and against the stage kernels: rotated local
 frames (non-trivial face orientations), unstructured simplex meshes, periodic seams,
 Dirichlet faces, the BDF mass term, ragged CTA tiles, per-instance parameters of a
-batch, and the FP32-arithmetic form's error."""
+batch, the FP32-arithmetic form's error, and the (hi, lo) float-pair form (emulated FP64)
+held to the FP64 bar."""
 import numpy as np
 import pytest
 
@@ -69,6 +70,12 @@ def test_nodal_jv_matches_oracle_and_stage_form(name, mk, p, model):
     jv32 = host(g.jvp_prec(1, cuda(u), cuda(v)))
     e32 = np.linalg.norm(jv32 - ref) / np.linalg.norm(ref)
     assert e32 <= 2e-6, (name, e32)
+    kff = g.jv_kernels(2)
+    assert kff.startswith("k_sim_q + k_sim_r" if simplex else "k_lin_q + k_lin_r") and "f32x2" in kff, kff
+    assert_parity(host(g.jvp_prec(2, cuda(u), cuda(v))), ref, what=f"{name} float-pair J.v")
+    assert gs.jv_kernels(2) == ""
+    with pytest.raises(RuntimeError):
+        gs.jvp_prec(2, cuda(u), cuda(v))
 
 
 @pytest.mark.parametrize("scheme", [1, 2])
@@ -81,6 +88,7 @@ def test_nodal_jv_with_bdf_mass_term(scheme):
     assert_parity(host(g.jvp(cuda(u), cuda(v))), o.jvp(u, v), what="nodal J.v with the BDF term")
     assert_parity(host(g.jvp_prec(1, cuda(u), cuda(v))), o.jvp(u, v), rtol2=2e-6, rtolmax=2e-5,
                   what="FP32 nodal J.v with the BDF term")
+    assert_parity(host(g.jvp_prec(2, cuda(u), cuda(v))), o.jvp(u, v), what="float-pair nodal J.v with the BDF term")
 
 
 def test_nodal_jv_with_bdf_mass_term_on_tetrahedra():
@@ -90,6 +98,7 @@ def test_nodal_jv_with_bdf_mass_term_on_tetrahedra():
     o.set_time(1, 0.0, 0.05, un, None)
     g.set_time(1, 0.0, 0.05, cuda(un), None)
     assert_parity(host(g.jvp(cuda(u), cuda(v))), o.jvp(u, v), what="tet nodal J.v with the BDF1 term")
+    assert_parity(host(g.jvp_prec(2, cuda(u), cuda(v))), o.jvp(u, v), what="tet float-pair J.v with the BDF1 term")
 
 
 def test_nodal_jv_ragged_tiles():
@@ -100,6 +109,7 @@ def test_nodal_jv_ragged_tiles():
         o, g = pair(mesh, p, oracle.CONVDIFF, oracle.CASE_EXPSIN)
         u, v = synth.random_vector(o.ndof, 5), synth.random_vector(o.ndof, 6)
         assert_parity(host(g.jvp(cuda(u), cuda(v))), o.jvp(u, v), what=f"ragged {mesh.etype} p={p}")
+        assert_parity(host(g.jvp_prec(2, cuda(u), cuda(v))), o.jvp(u, v), what=f"float-pair ragged {mesh.etype} p={p}")
 
 
 def test_nodal_jv_in_a_batch_uses_each_instance_parameters():
@@ -114,8 +124,58 @@ def test_nodal_jv_in_a_batch_uses_each_instance_parameters():
     u = torch.randn(b.n_total, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
     v = torch.randn(b.n_total, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(4))
     jv = host(b.jvp(u, v, 0))
+    jvff = host(b.jvp(u, v, 2))
     uh, vh = host(u), host(v)
     for i, (m, p, mu) in enumerate(zip(meshes, ps, mus)):
         o = oracle.Oracle(m, p, oracle.CONVDIFF, oracle.CASE_SINSIN, mu)
         sl = slice(b.offsets[i], b.offsets[i] + b.n_dof[i])
-        assert_parity(jv[sl], o.jvp(uh[sl], vh[sl]), what=f"batch instance {i}")
+        ref = o.jvp(uh[sl], vh[sl])
+        assert_parity(jv[sl], ref, what=f"batch instance {i}")
+        assert_parity(jvff[sl], ref, what=f"float-pair batch instance {i}")
+
+
+@pytest.mark.parametrize("scale", [1e-20, 1e-9, 1.0, 1e12, 1e25])
+def test_float_pair_jv_is_homogeneous_over_the_float_range(scale):
+    """J.v is linear: the float-pair form of J (c v) equals c times the FP64 J v to the
+    FP64 bar for c across the magnitudes a pair carries at full precision (the FP64 to
+    pair split takes its power of two in one or two factors on either side of 2^-74)."""
+    mesh = _rotate_some(synth.hex_box((3, 2, 3), affine=SHEAR3))
+    o, g = pair(mesh, 3, oracle.CONVDIFF, oracle.CASE_EXPSIN)
+    v = synth.random_vector(o.ndof, 8)
+    ref = host(g.jvp(cuda(v), cuda(v)))
+    got = host(g.jvp_prec(2, cuda(v * scale), cuda(v * scale))) / scale
+    assert_parity(got, ref, what=f"float-pair J.v at scale {scale:g}")
+
+
+def test_float_pair_jv_of_zero_is_zero_and_nonfinite_propagates():
+    mesh = synth.quad_box((5, 4), affine=SHEAR2)
+    o, g = pair(mesh, 3, oracle.CONVDIFF, oracle.CASE_EXPSIN)
+    z = np.zeros(o.ndof)
+    assert not np.any(host(g.jvp_prec(2, cuda(z), cuda(z))))
+    v = synth.random_vector(o.ndof, 3)
+    for bad in (np.nan, np.inf):
+        w = v.copy()
+        w[7] = bad
+        out = host(g.jvp_prec(2, cuda(w), cuda(w)))
+        assert not np.all(np.isfinite(out)), bad
+
+
+def test_float_pair_krylov_solve_reaches_the_fp64_solution():
+    """Newton-GMRES with the float-pair Krylov J.v (krylov_precision = F32X2) on a hexahedral
+    convection-diffusion problem: the same converged state as the FP64 solve, and a
+    context whose J.v has no float-pair kernels (the stage-kernel form) refuses the option
+    at creation."""
+    from paper_2205_07824_b300.ldg import F32X2, LDG, PC_BJACOBI
+    mesh = synth.hex_box((4, 3, 3), affine=SHEAR3)
+    kw = dict(gmres_m=30, gmres_rtol=1e-10, newton_rtol=1e-10, max_restarts=100, precond=PC_BJACOBI)
+    o, g64 = pair(mesh, 3, oracle.CONVDIFF, oracle.CASE_EXPSIN, **kw)
+    _, gff = pair(mesh, 3, oracle.CONVDIFF, oracle.CASE_EXPSIN, krylov_precision=F32X2, **kw)
+    u64, uff = cuda(np.zeros(o.ndof)), cuda(np.zeros(o.ndof))
+    r64, rff = g64.newton_gmres(u64), gff.newton_gmres(uff)
+    assert r64["status"] == 0 and rff["status"] == 0, (r64, rff)
+    assert np.linalg.norm(host(uff) - host(u64)) <= 1e-9 * np.linalg.norm(host(u64))
+    assert abs(rff["gmres_iters"] - r64["gmres_iters"]) <= 2, (rff, r64)
+    from paper_2205_07824_b300.ldg import JV_STAGE
+    with pytest.raises(RuntimeError):
+        LDG(mesh, 3, oracle.CONVDIFF, oracle.CASE_EXPSIN, (0.05, 0.3, 1.0, 0.5, 0.25), krylov_precision=F32X2,
+            jv_form=JV_STAGE)

@@ -151,7 +151,11 @@ def test_full_convdiff_hex48_p4_sampled():
     r = host(g.residual(cuda(u))).reshape(-1, 1, npe)[el]
     assert_parity(r, o.residual_some(u, el), what="R hex 48^3")
     jv = host(g.jvp(cuda(u), cuda(v))).reshape(-1, 1, npe)[el]
-    assert_parity(jv, o.jvp_some(u, v, el), what="Jv hex 48^3")
+    ref = o.jvp_some(u, v, el)
+    assert_parity(jv, ref, what="Jv hex 48^3")
+    # the (hi, lo) float-pair J.v of the same operator, held to the FP64 bar
+    jvff = host(g.jvp_prec(2, cuda(u), cuda(v))).reshape(-1, 1, npe)[el]
+    assert_parity(jvff, ref, what="float-pair Jv hex 48^3")
 
 
 # ------------------------------------------------------------------- solvers
