@@ -399,7 +399,7 @@ def run_jv(args):
                            "parallelism": f"{world} independent instance(s), one per GPU",
                            "fp32_jv": {"ms": ms32, "gdofs": n / (ms32 * 1e-3) / 1e9, "hbm_gbs": hbm32,
                                        "hbm_frac": hbm32 / hbm, "kernel": g.jv_kernels(1),
-                                       "arithmetic": "FP32 (inputs, output and q scratch FP64 in memory)"},
+                                       "arithmetic": "FP32 (inputs and output FP64 in memory, q scratch FP32)"},
                            "f32x2_jv": {"ms": msff, "gdofs": n / (msff * 1e-3) / 1e9,
                                         "hbm_gbs": JV_BYTES_PER_DOF * n / (msff * 1e-3) / 1e9,
                                         "hbm_frac": JV_BYTES_PER_DOF * n / (msff * 1e-3) / 1e9 / hbm,

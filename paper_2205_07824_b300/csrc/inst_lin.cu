@@ -2,12 +2,19 @@
 // p = 1..4 and hexahedra p = 1..6 (Poisson and convection-diffusion), FP64 arithmetic
 // with an FP64 q scratch and FP32 arithmetic with an FP32 q scratch.
 #include "ldg_launch.cuh"
-#include "ldg_linear.cuh"
+#include "ldg_hex_lines.cuh"
 
 namespace ldg {
 
+// One thread per node (ldg_linear.cuh) for quadrilaterals and for FP64 hexahedra, one
+// thread per line (ldg_hex_lines.cuh) for FP32 hexahedra. The FP64 J.v is bound by the
+// FP64 pipe either way and the per-node form keeps it busier (48^3, p = 4: 3.39 ms against
+// 3.49 ms); the FP32 J.v is bound by load-store instructions, which the line form cuts
+// (0.61 ms against 0.37 ms).
 template <int DIM, int N1, bool CONV> LinFn lin_pick(int prec) {
-  return prec == 0 ? &launch_lin<DIM, N1, CONV, double, double> : &launch_lin<DIM, N1, CONV, float, float>;
+  if (prec == 0) return &launch_lin<DIM, N1, CONV, double, double>;
+  if constexpr (DIM == 3) return &launch_hex<N1, CONV, float, float>;
+  else return &launch_lin<DIM, N1, CONV, float, float>;
 }
 
 template <int DIM, bool CONV> LinFn lin_by_p(int p, int prec) {

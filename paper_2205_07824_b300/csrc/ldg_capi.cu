@@ -130,7 +130,7 @@ KArgs base_args(ldg_ctx* c) {
   KArgs a;
   std::memset(&a, 0, sizeof(a));
   a.geo = c->d_geo; a.nbr = c->d_nbr; a.nbf = c->d_nbf; a.ops = c->d_ops; a.opsf = c->d_opsf; a.perm = c->d_perm;
-  a.lops = c->d_lops; a.lopsf = c->d_lopsf;
+  a.lops = c->d_lops; a.lopsf = c->d_lopsf; a.lops_host = c->h_lops.empty() ? nullptr : c->h_lops.data();
   a.a0dt = c->a0dt; a.t = c->t; a.mp = c->mp; a.E = (int)c->E;
   a.inst = c->ext_inst; a.mtab = c->ext_mtab; a.t_dev = c->d_t;
   a.cgeo = c->d_cgeo; a.cgeof = c->d_cgeof; a.cx = c->d_cx; a.minv = c->d_minv; a.minvf = c->d_minvf;
@@ -1277,6 +1277,7 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
     ctx->linff = lin_df_launcher(ctx->dim, p, conv);
     std::vector<double> lb;
     if (ctx->lin64 && ctx->lin32 && build_lin_ops(p, lb, err)) {
+      ctx->h_lops = lb;
       std::vector<float> lf(lb.begin(), lb.end());
       CK(cudaMalloc(&ctx->d_lops, lb.size() * sizeof(double)));
       CK(cudaMemcpy(ctx->d_lops, lb.data(), lb.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -1473,6 +1474,14 @@ int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u, const double* v, 
   return jvp_args(ctx, base_args(ctx), u, v, jv, precision);
 }
 
+// the nodal J.v kernels of the context's element type in `precision` (hexahedra: one
+// thread per line in FP32 and float pairs, one per node in FP64)
+static std::string nodal_names(const ldg_ctx* ctx, int precision) {
+  if (ctx->etype == LDG_TRI || ctx->etype == LDG_TET) return "k_sim_q + k_sim_r [";
+  if (ctx->etype == LDG_HEX && precision != LDG_FP64) return "k_hex_q + k_hex_r [";
+  return "k_lin_q + k_lin_r [";
+}
+
 const char* ldg_jv_describe(const ldg_ctx* ctx, int precision) {
   if (!ctx || !ctx->ks) return "";
   static thread_local std::string s;
@@ -1482,16 +1491,12 @@ const char* ldg_jv_describe(const ldg_ctx* ctx, int precision) {
   std::string what = std::string(el[ctx->etype]) + (ctx->pg ? " curved" : "") + " p=" + std::to_string(ctx->p) +
                      " nq=" + std::to_string(ctx->nq) + " " + md[ctx->model];
   if (precision == LDG_F32X2) {
-    const bool sim = ctx->etype == LDG_TRI || ctx->etype == LDG_TET;
-    s = ctx->ks->linear && ctx->linff
-            ? std::string(sim ? "k_sim_q + k_sim_r [" : "k_lin_q + k_lin_r [") + what + " f32x2, q scratch f32x2]"
-            : "";
+    s = ctx->ks->linear && ctx->linff ? nodal_names(ctx, precision) + what + " f32x2, q scratch f32x2]" : "";
     return s.c_str();
   }
   what += f32 ? " fp32" : " fp64";
   if (ctx->ks->linear && (f32 ? ctx->lin32 : ctx->lin64))
-    s = std::string(ctx->etype == LDG_TRI || ctx->etype == LDG_TET ? "k_sim_q + k_sim_r [" : "k_lin_q + k_lin_r [") +
-        what + ", q scratch " + (f32 ? "fp32" : "fp64") + "]";
+    s = nodal_names(ctx, precision) + what + ", q scratch " + (f32 ? "fp32" : "fp64") + "]";
   else if (ctx->ks->qstage)
     s = std::string(ctx->pg ? "k_qstage_curved" : "k_qstage") + " + k_residual [" + what + ", tile " +
         std::to_string(ctx->ks->tile) + "]";

@@ -43,7 +43,8 @@ struct ldg_ctx {
   double* d_dirk = nullptr;    // DIRK work: u^n, then the stages' spatial residuals and slopes
   // nodal J.v kernels of linear models on affine tensor elements (null when not applicable)
   ldg::LinFn lin64 = nullptr, lin32 = nullptr;
-  ldg::LinFn linff = nullptr;   // the same in (hi, lo) float-pair arithmetic (LDG_F32X2)
+  ldg::LinFn linff = nullptr;
+  std::vector<double> h_lops;    // host copy of the nodal kernels' FP64 operator blob   // the same in (hi, lo) float-pair arithmetic (LDG_F32X2)
   double* d_lops = nullptr;
   float* d_lopsf = nullptr;
   // element-sharded use (ldg_shard_*): owned elements, the caller's transport, q and

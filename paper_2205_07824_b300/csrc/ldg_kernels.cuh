@@ -64,6 +64,8 @@ struct KArgs {
   const unsigned char* perm;  // [n_orient][NFQ] face-point permutations
   const double* lops;         // 1-D operators of the nodal linear J.v kernels (ldg_linear.cuh), FP64 ...
   const float* lopsf;         // ... and FP32
+  const double* lops_host;    // the same FP64 blob in host memory (launchers that pass the
+                              // operators as a kernel parameter read it; kernels do not)
   const int* skip;            // optional: the kernel returns at once when *skip != 0
   int blk_col;                // MODE_JV block extraction (models without q): -1 off; else the element's own tangent is
                               // unit vector blk_col, neighbours' tangents are zero, and column blk_col

@@ -31,6 +31,12 @@ def _rotate_some(mesh, every=3):
     return m
 
 
+# the nodal J.v kernels of each element type (hexahedra: one thread per node in FP64, one
+# per line in FP32 and float pairs)
+KNAME = {synth.QUAD: "k_lin_q + k_lin_r", synth.HEX: "k_lin_q + k_lin_r", synth.TRI: "k_sim_q + k_sim_r",
+         synth.TET: "k_sim_q + k_sim_r"}
+KNAME_LOW = {**KNAME, synth.HEX: "k_hex_q + k_hex_r"}
+
 MESHES = [
     ("quad_rot_p1", lambda: _rotate_some(synth.quad_box((7, 5), affine=SHEAR2)), 1, oracle.POISSON),
     ("quad_rot_p3", lambda: _rotate_some(synth.quad_box((7, 5), affine=SHEAR2)), 3, oracle.CONVDIFF),
@@ -58,7 +64,7 @@ def test_nodal_jv_matches_oracle_and_stage_form(name, mk, p, model):
     mesh = mk()
     o, g = pair(mesh, p, model, oracle.CASE_EXPSIN)
     simplex = mesh.etype in (synth.TRI, synth.TET)
-    assert g.jv_kernels(0).startswith("k_sim_q + k_sim_r" if simplex else "k_lin_q + k_lin_r"), g.jv_kernels(0)
+    assert g.jv_kernels(0).startswith(KNAME[mesh.etype]), g.jv_kernels(0)
     _, gs = pair(mesh, p, model, oracle.CASE_EXPSIN, jv_form=JV_STAGE)
     assert gs.jv_kernels(0).startswith("k_qstage + k_residual"), gs.jv_kernels(0)
     u, v = synth.random_vector(o.ndof, 1), synth.random_vector(o.ndof, 2)
@@ -71,7 +77,8 @@ def test_nodal_jv_matches_oracle_and_stage_form(name, mk, p, model):
     e32 = np.linalg.norm(jv32 - ref) / np.linalg.norm(ref)
     assert e32 <= 2e-6, (name, e32)
     kff = g.jv_kernels(2)
-    assert kff.startswith("k_sim_q + k_sim_r" if simplex else "k_lin_q + k_lin_r") and "f32x2" in kff, kff
+    assert kff.startswith(KNAME_LOW[mesh.etype]) and "f32x2" in kff, kff
+    assert g.jv_kernels(1).startswith(KNAME_LOW[mesh.etype]), g.jv_kernels(1)
     assert_parity(host(g.jvp_prec(2, cuda(u), cuda(v))), ref, what=f"{name} float-pair J.v")
     assert gs.jv_kernels(2) == ""
     with pytest.raises(RuntimeError):
