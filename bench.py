@@ -1099,14 +1099,15 @@ def run_cylinder(args):
     jv32 = g.jvp_after_residual(1, u, v)
     jv64 = g.jvp_after_residual(0, u, v)
     jv_err = float(torch.linalg.norm(jv32 - jv64) / torch.linalg.norm(jv64))
-    # algorithmic bytes per J.v (FP64 storage): read u, v, q(u) (2 per DOF), write and read
-    # Q v (2 + 2), write J.v: 9 x 8 B per DOF; plus the curved-geometry records the two
-    # kernels read in FP32: per-point metrics twice and the element mass inverse once
+    # algorithmic bytes per FP32 J.v: the FP32 copies of u and q(u) (1 + 2 per DOF, 4 B),
+    # the FP64 direction v (8 B), Q v written and read in FP32 (2 + 2, 4 B) and J.v written
+    # in FP64 (8 B): 44 B per DOF; plus the curved-geometry records the two kernels read in
+    # FP32: per-point metrics twice and the element mass inverse once
     npe = g.n_pe
     nq1, nf = 5, 4
     geo_rec = nq1 * nq1 * 5 + nf * nq1 * 3
     geo_bytes = (2 * geo_rec + npe * npe) * 4 * mesh.n_elem
-    b_alg = 72.0 * n + geo_bytes
+    b_alg = 44.0 * n + geo_bytes
     hbm = None
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -1115,19 +1116,21 @@ def run_cylinder(args):
     except Exception:
         hbm, peak_src = 6400.0, "fallback 6.4 TB/s (of fallback)"
     achieved = b_alg / (jvt[1] * 1e-3) / 1e9
-    # DRAM reads of the pair per DOF from one ncu capture of the same kernels on the
-    # 1/16-scaled cylinder mesh (ncu capture of the pair on that mesh),
-    # scaled by the DOF count (traffic grows with the elements)
-    traffic = (9.679104e6 + 5.784832e6) / 160000.0 * n
+    # DRAM traffic of the pair per DOF from one ncu capture of the same kernels on the
+    # 1/16-scaled cylinder mesh (2,500 elements, 160,000 DOF), scaled by the DOF count
+    # (traffic grows with the elements)
+    traffic = (6.491392e6 + 1280 + 5.785088e6) / 160000.0 * n
     roofline = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": hbm, "frac": achieved / hbm,
-                "traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum of the pair on the 2,500-element "
-                                                      "mesh, scaled by DOF (writes stayed in L2 in that capture)",
+                "traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the pair "
+                                                      "on the 2,500-element mesh, scaled by DOF (its writes stay in "
+                                                      "L2 in that capture)",
                 "peak_source": peak_src,
                 "kernel": "k_qstage_curved<CurvedQuadEl<3,5>, NSModel, MODE_HOM, float> + "
                           "k_residual<CurvedQuadEl<3,5>, NSModel, MODE_JV, float>",
                 "launch_pair_ms": jvt[1], "fp64_pair_ms": jvt[0], "bytes_per_jv": b_alg,
-                "bytes_definition": "72 B/DOF state traffic (u, v, q(u), Q v written and read, J.v) + FP32 "
-                                    "curved metrics (read by both kernels) and element mass inverses",
+                "bytes_definition": "44 B/DOF state traffic (FP32 u and q(u), FP64 v, FP32 Q v written and read, "
+                                    "FP64 J.v) + FP32 curved metrics (read by both kernels) and element mass "
+                                    "inverses",
                 "jv_gdofs_kernel_fp32": n / (jvt[1] * 1e-3) / 1e9, "jv_gdofs_kernel_fp64": n / (jvt[0] * 1e-3) / 1e9,
                 "jv_fp32_rel_err_vs_fp64": jv_err}
     cpu = None

@@ -124,6 +124,7 @@ int emit_residual(ldg_batch* b, cudaStream_t s, const double* u, double* r, cons
     a.inst_skip = sk;
     if (g.ctx->ks->qstage) {
       a.u = u + g.off; a.out = g.ctx->d_q;
+      state_copies(g.ctx, a);
       BK(g.ctx->ks->qstage(MODE_R, a, s));
       a = base_args(g.ctx);
       a.inst_skip = sk;

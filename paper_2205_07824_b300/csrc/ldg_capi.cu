@@ -193,10 +193,16 @@ int read_scalars(ldg_ctx* ctx, const double* src, int n) {
   return LDG_OK;
 }
 
+void state_copies(ldg_ctx* ctx, KArgs& a) {
+  a.q32_out = ctx->d_q32;
+  a.u32_out = ctx->d_u32;
+}
+
 int do_residual(ldg_ctx* ctx, const double* u, double* r) {
   KArgs a = base_args(ctx);
   if (ctx->ks->qstage) {
     a.u = u; a.out = ctx->d_q;
+    state_copies(ctx, a);
     CK(ctx->ks->qstage(MODE_R, a, ctx->stream));
     a = base_args(ctx);
     a.q = ctx->d_q;
@@ -238,15 +244,23 @@ int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv
   } else if (ctx->ks->qstage) {
     // nonlinear model with q: dual numbers (u, v) and (q(u), Q v). q(u) is the FP64
     // q-stage of the residual (reused when the caller has just evaluated R(u))
+    // q-stage of the residual (reused when the caller has just evaluated R(u)). The FP32
+    // J.v reads the FP32 copies of u and q(u) that this q-stage writes beside q(u).
     if (!q_ready) {
       b.u = u; b.out = ctx->d_q;
+      state_copies(ctx, b);
       CK(ctx->ks->qstage(MODE_R, b, ctx->stream));
       b = a;
     }
     b.u = v; b.out = ctx->d_dq;
     CK(qs(MODE_HOM, b, ctx->stream));
     b = a;
-    b.u = u; b.v = v; b.q = ctx->d_q; b.dq = ctx->d_dq; b.out = jv;
+    if (f32) {
+      b.u = ctx->d_u32; b.q = ctx->d_q32;
+    } else {
+      b.u = u; b.q = ctx->d_q;
+    }
+    b.v = v; b.dq = ctx->d_dq; b.out = jv;
     CK(rs(MODE_JV, b, ctx->stream));
   } else {
     b.u = u; b.v = v; b.out = jv;
@@ -354,6 +368,7 @@ int do_blocks(ldg_ctx* ctx, const double* u, int prec, double* blocks) {
   if (!ctx->ks->linear) {
     KArgs a = base_args(ctx);
     a.u = u; a.out = ctx->d_q;
+    state_copies(ctx, a);
     CK(ctx->ks->qstage(MODE_R, a, ctx->stream));
   }
   for (int c = 0; c < ctx->ncolour; ++c)
@@ -1140,6 +1155,7 @@ int ldg_destroy(ldg_ctx* ctx) {
   if (ctx->engine) batch_free(ctx->engine);
   cudaFree(ctx->d_ops); cudaFree(ctx->d_opsf); cudaFree(ctx->d_geo); cudaFree(ctx->d_nbr); cudaFree(ctx->d_nbf); cudaFree(ctx->d_perm);
   cudaFree(ctx->d_xn); cudaFree(ctx->d_q); cudaFree(ctx->d_dq); cudaFree(ctx->d_hist);
+  cudaFree(ctx->d_q32); cudaFree(ctx->d_u32);
   cudaFree(ctx->d_cgeo); cudaFree(ctx->d_cgeof); cudaFree(ctx->d_cx); cudaFree(ctx->d_minv); cudaFree(ctx->d_minvf);
   cudaFree(ctx->d_xnode); cudaFree(ctx->d_fd); cudaFree(ctx->d_radd); cudaFree(ctx->d_dirk);
   cudaFree(ctx->d_V); cudaFree(ctx->d_r); cudaFree(ctx->d_w); cudaFree(ctx->d_res); cudaFree(ctx->d_x); cudaFree(ctx->d_small); cudaFree(ctx->d_part);
@@ -1337,6 +1353,11 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if (ctx->ks->qstage) {
     CK(cudaMalloc(&ctx->d_q, n * ctx->dim * sizeof(double)));
     CK(cudaMalloc(&ctx->d_dq, n * ctx->dim * sizeof(double)));
+    if (!ctx->ks->linear) {
+      // FP32 copies of u and q(u) for the FP32 Krylov J.v (written by the residual's q-stage)
+      CK(cudaMalloc(&ctx->d_q32, n * ctx->dim * sizeof(float)));
+      CK(cudaMalloc(&ctx->d_u32, n * sizeof(float)));
+    }
   }
   CK(cudaMalloc(&ctx->d_hist, n * sizeof(double)));
   if (!lean) CK(cudaMalloc(&ctx->d_V, (size_t)(ctx->m + 1) * n * sizeof(double)));
@@ -1582,6 +1603,7 @@ int do_residual_spatial(ldg_ctx* ctx, const double* u, double* r) {
   KArgs a = base_args(ctx);
   if (ctx->ks->qstage) {
     a.u = u; a.out = ctx->d_q;
+    state_copies(ctx, a);
     CK(ctx->ks->qstage(MODE_R, a, ctx->stream));
     a = base_args(ctx);
     a.q = ctx->d_q;

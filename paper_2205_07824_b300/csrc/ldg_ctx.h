@@ -36,7 +36,9 @@ struct ldg_ctx {
   float* d_minvf = nullptr;
   double* d_xnode = nullptr;   // [E][npe][dim] physical node coordinates
   double* d_q = nullptr;       // q(u) scratch [E][ncu][dim][npe]
-  double* d_dq = nullptr;      // q(v) scratch
+  double* d_dq = nullptr;      // q(v) scratch (FP32 values for the FP32 J.v)
+  float* d_q32 = nullptr;      // nonlinear models with q: FP32 copies of q(u) and u, written by
+  float* d_u32 = nullptr;      // the residual's q-stage and read by the FP32 J.v
   double* d_hist = nullptr;    // BDF history term
   double* d_radd = nullptr;    // DIRK stage: constant added to the residual (active when radd_on)
   bool radd_on = false;
@@ -140,6 +142,8 @@ namespace ldg {
 namespace impl {
 const std::vector<KernelSet>& registry();
 int fail(ldg_ctx* c, int code, const std::string& msg);
+// Have a residual's FP64 q-stage (MODE_R into ctx->d_q) write the FP32 copies of u and q(u).
+void state_copies(ldg_ctx* ctx, KArgs& a);
 KArgs base_args(ldg_ctx* c);
 int64_t grid_for(int64_t n, int t = 256);
 int do_residual(ldg_ctx* ctx, const double* u, double* r);

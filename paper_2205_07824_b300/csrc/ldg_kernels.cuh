@@ -66,6 +66,8 @@ struct KArgs {
   const float* lopsf;         // ... and FP32
   const double* lops_host;    // the same FP64 blob in host memory (launchers that pass the
                               // operators as a kernel parameter read it; kernels do not)
+  float* q32_out;             // optional, MODE_R q-stage (FP64): FP32 copy of q(u) ...
+  float* u32_out;             // ... and of u, read by the FP32 J.v of nonlinear models with q
   const int* skip;            // optional: the kernel returns at once when *skip != 0
   int blk_col;                // MODE_JV block extraction (models without q): -1 off; else the element's own tangent is
                               // unit vector blk_col, neighbours' tangents are zero, and column blk_col
@@ -421,6 +423,10 @@ template <class EL, class MD, class R, class TL> struct QLayout {
   static constexpr int SMEM = NE * PER_ELEM;
 };
 
+// Storage of q written by a q-stage in arithmetic R and read by the residual stage: FP64
+// for the FP64 kernels, FP32 for the FP32 ones (the Krylov J.v's scratch).
+template <class R> using QOut = typename std::conditional<sizeof(R) == 4, float, double>::type;
+
 template <class EL, class MD, int MODE, class R, class TL>
 __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
   typedef QLayout<EL, MD, R, TL> L;
@@ -439,8 +445,11 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
   const double* u = (const double*)a.u;
 
   for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = R(a.geo[(size_t)e0 * GEO + i]);
-  for (int i = threadIdx.x; i < NE * NCU * NPE; i += blockDim.x)
-    Us[i] = i < ne * NCU * NPE ? R(u[(size_t)e0 * NCU * NPE + i]) : R(0);
+  for (int i = threadIdx.x; i < NE * NCU * NPE; i += blockDim.x) {
+    const double x = i < ne * NCU * NPE ? u[(size_t)e0 * NCU * NPE + i] : 0.0;
+    Us[i] = R(x);
+    if (MODE == MODE_R && a.u32_out && i < ne * NCU * NPE) a.u32_out[(size_t)e0 * NCU * NPE + i] = (float)x;
+  }
   __syncthreads();
 
   // ---- faces: traces of u on both sides, (u- - uhat) weighted, lifted to face nodes
@@ -516,13 +525,14 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
   __syncthreads();
   mass_inv<EL>(BV, SC, OPS, NE * NCU * DIM);
   __syncthreads();
-  double* qo = (double*)a.out;
+  QOut<R>* qo = (QOut<R>*)a.out;
   for (int it = threadIdx.x; it < ne * NCU * DIM * NPE; it += blockDim.x) {
     int n = it % NPE, d = (it / NPE) % DIM, c = (it / (NPE * DIM)) % NCU, e = it / (NPE * DIM * NCU);
     const R* g = Gs + e * GEO;
     R s = SC[it] / g[Geo<DIM>::DETJ];
     for (int k = 0; k < DIM; ++k) s -= GR[(k * NE * NCU + e * NCU + c) * NPE + n] * g[Geo<DIM>::JINV + k * DIM + d];
-    qo[(size_t)e0 * NCU * DIM * NPE + it] = (double)s;
+    qo[(size_t)e0 * NCU * DIM * NPE + it] = (QOut<R>)s;
+    if (MODE == MODE_R && a.q32_out) a.q32_out[(size_t)e0 * NCU * DIM * NPE + it] = (float)s;
   }
 }
 
@@ -571,8 +581,11 @@ __global__ void __launch_bounds__(256) k_qstage_curved(KArgs a) {
   const double* u = (const double*)a.u;
 
   for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) Gs[i] = GSRC[(size_t)e0 * GEO + i];
-  for (int i = threadIdx.x; i < NE * NCU * NPE; i += blockDim.x)
-    Us[i] = i < ne * NCU * NPE ? R(u[(size_t)e0 * NCU * NPE + i]) : R(0);
+  for (int i = threadIdx.x; i < NE * NCU * NPE; i += blockDim.x) {
+    const double x = i < ne * NCU * NPE ? u[(size_t)e0 * NCU * NPE + i] : 0.0;
+    Us[i] = R(x);
+    if (MODE == MODE_R && a.u32_out && i < ne * NCU * NPE) a.u32_out[(size_t)e0 * NCU * NPE + i] = (float)x;
+  }
   __syncthreads();
 
   // ---- faces: -uhat n_d w at every face point, lifted to the face nodes
@@ -668,7 +681,7 @@ __global__ void __launch_bounds__(256) k_qstage_curved(KArgs a) {
   const R* MI;
   if constexpr (sizeof(R) == 8) MI = (const R*)a.minv;
   else MI = (const R*)a.minvf;
-  double* qo = (double*)a.out;
+  QOut<R>* qo = (QOut<R>*)a.out;
   for (int it = threadIdx.x; it < ne * NCU * DIM * NPE; it += blockDim.x) {
     const int n = it % NPE, b = it / NPE, e = b / (NCU * DIM);
     const R* mi = MI + ((size_t)(e0 + e) * NPE + n) * NPE;
@@ -676,7 +689,8 @@ __global__ void __launch_bounds__(256) k_qstage_curved(KArgs a) {
     R sacc = R(0);
 #pragma unroll 4
     for (int m = 0; m < NPE; ++m) sacc += mi[m] * bv[m];
-    qo[(size_t)e0 * NCU * DIM * NPE + it] = (double)sacc;
+    qo[(size_t)e0 * NCU * DIM * NPE + it] = (QOut<R>)sacc;
+    if (MODE == MODE_R && a.q32_out) a.q32_out[(size_t)e0 * NCU * DIM * NPE + it] = (float)sacc;
   }
   (void)M;
 }
@@ -735,10 +749,13 @@ __global__ void __launch_bounds__(256, ResMinBlocks<MD, MODE, R, TL>::value) k_r
   S* X = (S*)(smem + NE * L::B_GEO);                       // [NE][NCV][NPE]
   R* LF = (R*)(smem + NE * (L::B_GEO + L::B_X));           // [NE][NF][NCU][NFN]
   unsigned char* arena = smem + NE * (L::B_GEO + L::B_X + L::B_LF);
-  const double* u = (const double*)a.u;
+  // FP32 instances read q scratch in FP32, and a nonlinear model's state too (its FP32
+  // copy written by the FP64 q-stage of the residual)
+  typedef typename std::conditional<(sizeof(R) == 4 && MODE == MODE_JV && HASQ), float, double>::type UIn;
+  const UIn* u = (const UIn*)a.u;
   const double* v = (const double*)a.v;
-  const double* q = (const double*)a.q;
-  const double* dq = (const double*)a.dq;
+  const QOut<R>* q = (const QOut<R>*)a.q;
+  const QOut<R>* dq = (const QOut<R>*)a.dq;
 
   if constexpr (EL::CURVED) {
     const R* src = geo_src<EL, R>(a);

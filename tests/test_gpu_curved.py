@@ -107,6 +107,12 @@ def test_fp32_jvp_error():
     err = np.linalg.norm(host(g.jvp_prec(1, cuda(u), cuda(v))) - ref) / np.linalg.norm(ref)
     print(f"curved NS FP32 J.v relative error: {err:.2e}")
     assert 1e-10 < err < 2e-5
+    # the FP32 J.v reads FP32 copies of u and q(u) written by the residual's q-stage: after a
+    # residual at u it gives bitwise the J.v that forms q(u) itself
+    jv32 = host(g.jvp_prec(1, cuda(u), cuda(v)))
+    cu = cuda(u)
+    g.residual(cu)
+    assert np.array_equal(host(g.jvp_after_residual(1, cu, cuda(v))), jv32)
 
 
 @pytest.mark.parametrize("model", [oracle.EULER, oracle.NS])
