@@ -384,9 +384,10 @@ def run_jv(args):
                "call": "ldg_jvp_host (FP64): v copied from pinned host memory, J.v on the device, J.v copied "
                        "back, stream synchronised; host wall clock (a linear model's J.v does not read u)"}
 
-    solve = None
+    solve = c5 = None
     if not args.no_solve:
         solve = vortex_solve_summary(args, stream)
+        c5 = cylinder_solve_summary(args, stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": gdofs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -408,7 +409,8 @@ def run_jv(args):
                                                       "bits (emulated FP64); inputs and output FP64 in memory, q "
                                                       "scratch float pairs"},
                            "oracle_sample": samp,
-                           "solve_time_to_1e-8": solve},
+                           "solve_time_to_1e-8": solve,
+                           "c5_time_to_1e-8_scaled16": c5},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -474,6 +476,41 @@ def vortex_solve_summary(args, stream):
     forms["solution_rel_diff"] = float(torch.linalg.norm(sol["fp32_krylov_bjacobi"] - sol["fp64_bjacobi"]) /
                                        torch.linalg.norm(sol["fp64_bjacobi"]))
     forms["workload"] = WORKLOAD
+    return forms
+
+
+def cylinder_solve_summary(args, stream):
+    """Time to 1e-8 per BDF2 step of the Navier-Stokes cylinder on 1/16 of c5's mesh (25
+    layers x 100 around, 2,500 curved quadrilaterals, p = 3, Re from seed 0): plain FP64
+    block-Jacobi, FP32 Krylov J.v + block-Jacobi, and FP32 Krylov J.v + the learned
+    correction of block-Jacobi trained on the warm-up steps' block-Jacobi solves."""
+    import numpy as np
+    import torch
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, kernel_launches
+    mesh = synth.cylinder_mesh(25, 100, 3, seed=7)
+    re = float(np.random.default_rng(0).uniform(100.0, 1000.0))
+    prob = cylinder_problem(LDG, mesh, re, forcing_of(args))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    steps = 2
+    forms, sol = {}, {}
+    for name, kp, pc in (("fp64_bjacobi", 0, 1), ("fp32_bjacobi", 1, 1), ("fp32_learned", 1, 3)):
+        g, u, times, tot, _, _, train = run_mode(prob, kp, pc, steps, 3, flush, stream, kernel_launches)
+        forms[name] = {"ms_per_step": sum(times) / steps, "gmres_iters_per_step": tot["gmres"] / steps,
+                       "newton_iters_per_step": tot["newton"] / steps, "pc_fallbacks": tot["pc_fallbacks"]}
+        if train:
+            forms[name]["learned_pc_training"] = {k: train[k] for k in ("pairs", "vectors") if k in train}
+        sol[name] = u.clone()
+        del g
+    base = forms["fp64_bjacobi"]["ms_per_step"]
+    for name in ("fp32_bjacobi", "fp32_learned"):
+        forms[name]["speedup_vs_fp64_bjacobi"] = base / forms[name]["ms_per_step"]
+        forms[name]["solution_rel_diff_vs_fp64_bjacobi"] = float(
+            torch.linalg.norm(sol[name] - sol["fp64_bjacobi"]) / torch.linalg.norm(sol["fp64_bjacobi"]))
+    forms["workload"] = (f"2D compressible Navier-Stokes past a cylinder, 1/16 of the c5 mesh: 2,500 curved "
+                         f"quadrilaterals (25 layers x 100 around, seed 7), p=3, Re={re:.1f}, Mach 0.2, BDF2 "
+                         f"dt=0.1, Newton-GMRES(30) to 1e-8 (FP64 residual); {steps} timed steps after 3 warm-up "
+                         f"steps per form; the full 40,000-element case is bench.py --workload cylinder")
     return forms
 
 
