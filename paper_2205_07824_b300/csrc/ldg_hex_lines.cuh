@@ -123,18 +123,20 @@ __global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_q(KA
   for (int i = t; i < ne * NPE; i += NT) Vs[i / NPE][i % NPE] = R(v[(size_t)e0 * NPE + i]);
   __syncthreads();
   if (own) {
-    // line k of this thread: base node and stride
-    const int base[3] = {N1 * ia + NL * ib, ia + NL * ib, ia + N1 * ib};
-    constexpr int STR[3] = {1, N1, NL};
-#pragma unroll
+    // line k of this thread (one loop body for the three axes)
+#pragma unroll 1
     for (int k = 0; k < 3; ++k) {
+      const int base = k == 0 ? N1 * ia + NL * ib : (k == 1 ? ia + NL * ib : ia + N1 * ib);
+      const int str = k == 0 ? 1 : (k == 1 ? N1 : NL);
       R x[N1], g[N1];
 #pragma unroll
-      for (int m = 0; m < N1; ++m) x[m] = Vs[e][base[k] + m * STR[k]];
+      for (int m = 0; m < N1; ++m) x[m] = Vs[e][base + m * str];
       // Delta = v- - vhat at the line's two ends (faces 2k and 2k + 1)
       R d0 = x[0], d1 = x[N1 - 1];
-      if ((hasnb >> (2 * k)) & 1) d0 = (d0 - vnb[2 * k]) * R(0.5);
-      if ((hasnb >> (2 * k + 1)) & 1) d1 = (d1 - vnb[2 * k + 1]) * R(0.5);
+      const R vlo = k == 0 ? vnb[0] : (k == 1 ? vnb[2] : vnb[4]);
+      const R vhi = k == 0 ? vnb[1] : (k == 1 ? vnb[3] : vnb[5]);
+      if ((hasnb >> (2 * k)) & 1) d0 = (d0 - vlo) * R(0.5);
+      if ((hasnb >> (2 * k + 1)) & 1) d1 = (d1 - vhi) * R(0.5);
 #pragma unroll
       for (int i = 0; i < N1; ++i) {
         A s = A(P.l0[i] * d0);
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_q(KA
         g[i] = R(s);
       }
 #pragma unroll
-      for (int i = 0; i < N1; ++i) Gk[k][e][base[k] + i * STR[k]] = g[i];
+      for (int i = 0; i < N1; ++i) Gk[k][e][base + i * str] = g[i];
     }
   }
   __syncthreads();
@@ -286,59 +288,48 @@ __global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_r(KA
     }
   }
   __syncthreads();
-  // ---- phase 1: x-line (i1, i2) = (ia, ib); face lines along i0 (y- and z-face rows)
-  if (own) {
-    const int bx = N1 * ia + NL * ib;
-    R x[N1], y[N1];
-    if (tterm) {
-      // y = -M h, then C g0 accumulated onto it
+  // ---- phases 1 and 2, one loop body (the face-line code once):
+  //   phase 1: x-line (i1, i2) = (ia, ib): T0 = C g0 - M h, T1 = M g1, T2 = M g2;
+  //   phase 2: y-line (i0, i2) = (ia, ib): U = M T0 + C T1, W = M T2;
+  //   face lines along i0, then along i1
+#pragma unroll 1
+  for (int ph = 1; ph <= 2; ++ph) {
+    if (own) {
+      const int base = ph == 1 ? N1 * ia + NL * ib : ia + NL * ib;
+      const int str = ph == 1 ? 1 : N1;
+      R x[N1], y[N1];
+      // field 0: C g0 (phase 1, with -M h when there is a time term) or M T0 + C T1 (phase 2)
 #pragma unroll
-      for (int m = 0; m < N1; ++m) x[m] = Hs[e][bx + m];
-      hex_apply<N1, R, false>(P.m1, x, y);
+      for (int i = 0; i < N1; ++i) y[i] = R(0);
+      if (ph == 2 || tterm) {
+        const R* src = ph == 1 ? Hs[e] : Gk[0][e];
 #pragma unroll
-      for (int i = 0; i < N1; ++i) y[i] = -y[i];
+        for (int m = 0; m < N1; ++m) x[m] = src[base + m * str];
+        hex_apply<N1, R, false>(P.m1, x, y);
+        if (ph == 1) {
 #pragma unroll
-      for (int m = 0; m < N1; ++m) x[m] = Gk[0][e][bx + m];
+          for (int i = 0; i < N1; ++i) y[i] = -y[i];
+        }
+      }
+      const R* src = ph == 1 ? Gk[0][e] : Gk[1][e];
+#pragma unroll
+      for (int m = 0; m < N1; ++m) x[m] = src[base + m * str];
       hex_apply<N1, R, true>(P.c, x, y);
-    } else {
 #pragma unroll
-      for (int m = 0; m < N1; ++m) x[m] = Gk[0][e][bx + m];
-      hex_apply<N1, R, false>(P.c, x, y);
+      for (int i = 0; i < N1; ++i) Gk[0][e][base + i * str] = y[i];
+      // the fields that only take M: g1 and g2 (phase 1), T2 (phase 2)
+#pragma unroll 1
+      for (int k = ph == 1 ? 1 : 2; k < 3; ++k) {
+#pragma unroll
+        for (int m = 0; m < N1; ++m) x[m] = Gk[k][e][base + m * str];
+        hex_apply<N1, R, false>(P.m1, x, y);
+#pragma unroll
+        for (int i = 0; i < N1; ++i) Gk[k][e][base + i * str] = y[i];
+      }
+      for (int fl = l; fl < 4 * N1; fl += NL) hex_face_line<N1, R>(P, FF[e], ph, fl);
     }
-#pragma unroll
-    for (int i = 0; i < N1; ++i) Gk[0][e][bx + i] = y[i];
-#pragma unroll
-    for (int k = 1; k < 3; ++k) {
-#pragma unroll
-      for (int m = 0; m < N1; ++m) x[m] = Gk[k][e][bx + m];
-      hex_apply<N1, R, false>(P.m1, x, y);
-#pragma unroll
-      for (int i = 0; i < N1; ++i) Gk[k][e][bx + i] = y[i];
-    }
-    for (int fl = l; fl < 4 * N1; fl += NL) hex_face_line<N1, R>(P, FF[e], 1, fl);
+    __syncthreads();
   }
-  __syncthreads();
-  // ---- phase 2: y-line (i0, i2) = (ia, ib); face lines along i1 (x-face rows, z-face columns)
-  if (own) {
-    const int by = ia + NL * ib;
-    R x0[N1], x1[N1], y[N1];
-#pragma unroll
-    for (int m = 0; m < N1; ++m) {
-      x0[m] = Gk[0][e][by + N1 * m];
-      x1[m] = Gk[1][e][by + N1 * m];
-    }
-    hex_apply<N1, R, false>(P.m1, x0, y);
-    hex_apply<N1, R, true>(P.c, x1, y);
-#pragma unroll
-    for (int i = 0; i < N1; ++i) Gk[0][e][by + N1 * i] = y[i];
-#pragma unroll
-    for (int m = 0; m < N1; ++m) x0[m] = Gk[2][e][by + N1 * m];
-    hex_apply<N1, R, false>(P.m1, x0, y);
-#pragma unroll
-    for (int i = 0; i < N1; ++i) Gk[2][e][by + N1 * i] = y[i];
-    for (int fl = l; fl < 4 * N1; fl += NL) hex_face_line<N1, R>(P, FF[e], 2, fl);
-  }
-  __syncthreads();
   // ---- phase 3: z-line (i0, i1) = (ia, ib) into registers; face lines along i2 (x- and
   // y-face columns), then the face moments on the line and the store
   const int bz = ia + N1 * ib;
