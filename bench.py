@@ -829,8 +829,8 @@ def run_tri(args):
 
 def jv_sweep(args, make_mesh, mu, head_p, bytes_per_dof, workload, kernel_label):
     """Median J.v time (L2 flushed before each) of the linear convection-diffusion operator
-    on one mesh for p = 1..6 in FP64 and FP32 arithmetic; the FP32 p = head_p row is the
-    headline."""
+    on one mesh for p = 1..6 in FP64, FP32 and (hi, lo) float-pair arithmetic; the FP32
+    p = head_p row is the headline."""
     import torch
     from paper_2205_07824_b300.ldg import LDG, CONVDIFF, CASE_EXPSIN, kernel_launches
     world, rank, local = _dist()
@@ -852,7 +852,7 @@ def jv_sweep(args, make_mesh, mu, head_p, bytes_per_dof, workload, kernel_label)
     l0 = kernel_launches()
     for p in range(1, 7):
         row = {"p": p}
-        for prec in (0, 1):
+        for prec in (0, 1, 2):
             g = LDG(mesh, p, CONVDIFF, CASE_EXPSIN, mu, krylov_precision=prec)
             tile, _ = g.autotune()
             u = g.interpolate(0.0)
@@ -871,7 +871,7 @@ def jv_sweep(args, make_mesh, mu, head_p, bytes_per_dof, workload, kernel_label)
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1))
             ms = sorted(times)[len(times) // 2]
-            key = "fp64" if prec == 0 else "fp32"
+            key = ("fp64", "fp32", "f32x2")[prec]
             row[key] = {"ms": ms, "gdofs": g.n_dof / (ms * 1e-3) / 1e9, "tile": tile,
                         "hbm_frac": bytes_per_dof * g.n_dof / (ms * 1e-3) / 1e9 / hbm}
             row[key]["kernels"] = g.jv_kernels(prec)
@@ -910,8 +910,8 @@ TET_JV_BYTES_PER_DOF = 72.0
 
 
 def run_tet(args):
-    """Table 3's finest mesh on the GPU: the J.v (FP64 and FP32 arithmetic) against the
-    HBM roofline, and the time of the whole Newton-GMRES solve."""
+    """Table 3's finest mesh on the GPU: the J.v (FP64, FP32 and float-pair arithmetic)
+    against the HBM roofline, and the time of the whole Newton-GMRES solve."""
     import torch
     from paper_2205_07824_b300 import synth
     from paper_2205_07824_b300.ldg import LDG, POISSON, CASE_SINSIN, kernel_launches
@@ -932,7 +932,7 @@ def run_tet(args):
     clocks.start()
     l0 = kernel_launches()
     jv = {}
-    for prec in (1, 0):
+    for prec in (1, 0, 2):
         g = LDG(mesh, p, POISSON, CASE_SINSIN, (1.0, 1.0), krylov_precision=prec, precond=1, newton_rtol=1e-8,
                 gmres_rtol=1e-3, max_restarts=400)
         tile, _ = g.autotune()
@@ -940,10 +940,11 @@ def run_tet(args):
         v = torch.randn(g.n_dof, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
         out = torch.empty_like(v)
         ms = graph_time_ms(g, lambda: g.jvp_prec(prec, u, v, out), args.jv_reps)
-        jv["fp32" if prec else "fp64"] = {"ms": ms, "gdofs": g.n_dof / (ms * 1e-3) / 1e9, "tile": tile,
-                                          "hbm_frac": TET_JV_BYTES_PER_DOF * g.n_dof / (ms * 1e-3) / 1e9 / hbm}
-        jv["fp32" if prec else "fp64"]["kernels"] = g.jv_kernels(prec)
-        if prec:
+        key = ("fp64", "fp32", "f32x2")[prec]
+        jv[key] = {"ms": ms, "gdofs": g.n_dof / (ms * 1e-3) / 1e9, "tile": tile,
+                   "hbm_frac": TET_JV_BYTES_PER_DOF * g.n_dof / (ms * 1e-3) / 1e9 / hbm}
+        jv[key]["kernels"] = g.jv_kernels(prec)
+        if prec == 1:
             g32 = g
     # the solve: FP32 Krylov + block-Jacobi from u = 0, timed steps (each a full solve)
     n = g32.n_dof
