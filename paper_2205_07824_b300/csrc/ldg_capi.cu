@@ -390,6 +390,8 @@ int do_pc_setup(ldg_ctx* ctx, const double* u) {
   int rc;
   // (a float-pair Krylov J.v takes FP64 blocks)
   const int prec = ctx->opt.krylov_precision == LDG_FP32 ? LDG_FP32 : LDG_FP64;
+  ctx->pc_kappa = ctx->mp.kappa;
+  ctx->pc_a0dt = ctx->a0dt;
   // the block storage must exist before its address is handed to the extraction
   if ((rc = ensure_pc_storage(ctx))) return rc;
   if ((rc = do_blocks(ctx, u, prec, ctx->d_blocks))) return rc;
@@ -947,7 +949,7 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
   const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8);
   while (rn > ctx->opt.newton_rtol * r0 && k < ctx->opt.max_newton) {
     if ((ctx->opt.precond == LDG_PC_BJACOBI || ctx->opt.precond == LDG_PC_MLP_BJ) &&
-        (k == 0 || (ctx->opt.pc_refresh > 0 && k % ctx->opt.pc_refresh == 0))) {
+        ((k == 0 && !(ctx->pc_hold && ctx->pc_ready)) || (ctx->opt.pc_refresh > 0 && k % ctx->opt.pc_refresh == 0))) {
       if ((rc = do_pc_setup(ctx, u))) return rc;
       if (rep) rep->pc_setups++;
     }
@@ -1158,6 +1160,7 @@ int ldg_destroy(ldg_ctx* ctx) {
   cudaFree(ctx->d_q32); cudaFree(ctx->d_u32);
   cudaFree(ctx->d_cgeo); cudaFree(ctx->d_cgeof); cudaFree(ctx->d_cx); cudaFree(ctx->d_minv); cudaFree(ctx->d_minvf);
   cudaFree(ctx->d_xnode); cudaFree(ctx->d_fd); cudaFree(ctx->d_radd); cudaFree(ctx->d_dirk);
+  cudaFree(ctx->d_wave);
   cudaFree(ctx->d_V); cudaFree(ctx->d_r); cudaFree(ctx->d_w); cudaFree(ctx->d_res); cudaFree(ctx->d_x); cudaFree(ctx->d_small); cudaFree(ctx->d_part);
   cudaFree(ctx->d_flags); cudaFree(ctx->d_ticket); cudaFree(ctx->d_t);
   cudaFree(ctx->d_colour); cudaFree(ctx->d_blocks); cudaFree(ctx->d_binv); cudaFree(ctx->d_Z);
@@ -1676,6 +1679,139 @@ int ldg_dirk_step(ldg_ctx* ctx, int scheme, double t, double dt, double* u, ldg_
   if (rep) {
     total.status = rc;
     total.elapsed_ms = 0.0;
+    *rep = total;
+  }
+  return rc ? rc : rc2;
+}
+
+// ------------------------------------------------------------------ wave model
+// The wave model of Section 2.1: Eq. 1a becomes dq/dt + grad u = 0, Eq. 1b keeps
+// M du/dt + R_s(u, q) = 0, and the ODE Eq. 2, alpha dw/dt + beta w = u, recovers the
+// displacement. One step of a singly diagonally implicit DIRK scheme (Section 2.2).
+//
+// With f = kappa q linear in q, R_s(u, q) = A u + B q with B proportional to kappa, and the
+// q-stage of the diffusion model is the LDG form Qop(u) of -grad u. Stage i has
+//   Q_i = Qh_i + g dt Qop(U_i),  Qh_i = q^n + dt sum_{j<i} a_ij Qop(U_j),
+//   M (U_i - u^n) / (g dt) + R_s(U_i, Q_i) + sum_{j<i} (a_ij / g) R_s(U_j, Q_j) = 0,
+// and R_s(U, Qh + g dt Qop(U)) = R'(U) + B Qh, where R' is the diffusion residual with
+// kappa' = g dt kappa. So each stage is the context's own implicit solve with kappa'
+// and the constant radd = B Qh_i + sum_{j<i} (a_ij / g) R_s(U_j, Q_j); q and w follow node by
+// node. All a_ii are equal (g), so kappa' and the block-Jacobi blocks hold for every stage.
+namespace {
+
+// R_s(u, q) with the context's current kappa: the homogeneous residual stage, no time term
+int wave_rs(ldg_ctx* ctx, const double* u, const double* q, double* out) {
+  KArgs a = base_args(ctx);
+  a.u = u; a.q = q; a.out = out;
+  a.a0dt = 0.0; a.hist = nullptr; a.radd = nullptr;
+  CK(ctx->ks->residual(MODE_HOM, a, ctx->stream));
+  return LDG_OK;
+}
+
+}  // namespace
+
+int ldg_wave_step(ldg_ctx* ctx, int scheme, double t, double dt, double alpha, double beta, double* u, double* q,
+                  double* w, ldg_solve_report* rep) {
+  Dirk d;
+  if (!ctx || !ctx->ks || !u || !q || !(dt > 0) || !dirk_tableau(scheme, d)) return LDG_ERR_ARG;
+  if (ctx->model != LDG_POISSON || ctx->mp.cas != LDG_CASE_ZERO || ctx->ncu != 1)
+    return fail(ctx, LDG_ERR_ARG, "ldg_wave_step: the context must be a Poisson model of case LDG_CASE_ZERO");
+  const double g = d.A[0][0];
+  for (int i = 1; i < d.s; ++i)
+    if (d.A[i][i] != g) return fail(ctx, LDG_ERR_ARG, "ldg_wave_step: the scheme is not singly diagonally implicit");
+  if (w && !(std::fabs(alpha + beta * g * dt) > 0.0))
+    return fail(ctx, LDG_ERR_ARG, "ldg_wave_step: alpha + beta a_ii dt must not vanish");
+  const int64_t n = ctx->ndof, nq = n * ctx->dim;
+  if (!ctx->d_radd) CK(cudaMalloc(&ctx->d_radd, n * sizeof(double)));
+  if (!ctx->d_wave) CK(cudaMalloc(&ctx->d_wave, (size_t)(12 * n + 6 * nq) * sizeof(double)));
+  double* un = ctx->d_wave;
+  double* wn = un + n;
+  double* zero = wn + n;
+  double* Ku[3] = {zero + n, zero + 2 * n, zero + 3 * n};      // slopes of u
+  double* Rs[3] = {zero + 4 * n, zero + 5 * n, zero + 6 * n};  // R_s(U_j, Q_j)
+  double* Kw[3] = {zero + 7 * n, zero + 8 * n, zero + 9 * n};  // slopes of w
+  double* qn = zero + 10 * n;
+  double* Qs = qn + nq;                                        // Qh_i / (g dt)
+  double* Qt = Qs + nq;                                        // Q_i / (g dt)
+  double* Kq[3] = {Qt + nq, Qt + 2 * nq, Qt + 3 * nq};          // slopes of q: Qop(U_j)
+  const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8), gq = std::min<int64_t>(grid_for(nq), 148 * 8);
+  CK(cudaMemcpyAsync(un, u, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(qn, q, nq * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  if (w) CK(cudaMemcpyAsync(wn, w, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemsetAsync(zero, 0, n * sizeof(double), ctx->stream));
+  const double c2 = ctx->mp.kappa;
+  const double kp = g * dt * c2;
+  ctx->mp.kappa = kp;
+  // the blocks of an earlier step of the same operator are kept
+  ctx->pc_hold = ctx->pc_ready && ctx->pc_kappa == kp && ctx->pc_a0dt == 1.0 / (g * dt);
+  ldg_solve_report total{};
+  int rc = LDG_OK;
+  auto lin = [&](double* out, int64_t len, double c0, const double* x0, double c1, const double* x1, double cc2,
+                 const double* x2, double c3, const double* x3) -> int {
+    k_lincomb4<<<len == n ? g1 : gq, 256, 0, ctx->stream>>>(out, len, c0, x0, c1, x1, cc2, x2, c3, x3);
+    count_launch();
+    CK(cudaGetLastError());
+    return LDG_OK;
+  };
+  for (int i = 0; i < d.s && !rc; ++i) {
+    const double* kx[3] = {nullptr, nullptr, nullptr};
+    double kc[3] = {0.0, 0.0, 0.0};
+    // Qs = (q^n + dt sum_{j<i} a_ij Kq_j) / (g dt)
+    for (int j = 0; j < i; ++j) { kx[j] = Kq[j]; kc[j] = d.A[i][j] / g; }
+    if ((rc = lin(Qs, nq, 1.0 / (g * dt), qn, kc[0], kx[0], kc[1], kx[1], 0.0, nullptr))) break;
+    // radd = B Qh_i + sum_{j<i} (a_ij / g) R_s(U_j, Q_j); B Qh_i = R_s(0, Qs) with kappa'
+    if ((rc = wave_rs(ctx, zero, Qs, Ku[i]))) break;
+    for (int j = 0; j < 3; ++j) { kx[j] = j < i ? Rs[j] : nullptr; kc[j] = j < i ? d.A[i][j] / g : 0.0; }
+    if ((rc = lin(ctx->d_radd, n, 1.0, Ku[i], kc[0], kx[0], kc[1], kx[1], kc[2], kx[2]))) break;
+    // the stage solve: M (U - u^n) / (g dt) + R'(U) + radd = 0 at t + c_i dt
+    if ((rc = ldg_set_time(ctx, LDG_BDF1, t + d.c[i] * dt, g * dt, un, nullptr))) break;
+    ctx->radd_on = true;
+    ldg_solve_report r{};
+    rc = do_newton(ctx, u, &r);
+    ctx->radd_on = false;
+    ctx->pc_hold = true;
+    total.newton_iters += r.newton_iters;
+    total.gmres_iters += r.gmres_iters;
+    total.jv_calls += r.jv_calls;
+    total.residual_calls += r.residual_calls;
+    total.pc_setups += r.pc_setups;
+    total.pc_fallbacks += r.pc_fallbacks;
+    if (i == 0) total.r0 = r.r0;
+    total.rfinal = std::max(total.rfinal, r.rfinal / (r.r0 > 0 ? r.r0 : 1.0));
+    total.lin_resid = std::max(total.lin_resid, r.lin_resid);
+    if (rc) break;
+    // Kq_i = Qop(U_i); Q_i / (g dt) = Qs + Kq_i; R_s(U_i, Q_i)
+    {
+      KArgs a = base_args(ctx);
+      a.u = u; a.out = Kq[i];
+      cudaError_t e = ctx->ks->qstage(MODE_HOM, a, ctx->stream);
+      if (e != cudaSuccess) { rc = fail(ctx, LDG_ERR_CUDA, cudaGetErrorString(e)); break; }
+    }
+    if ((rc = lin(Qt, nq, 1.0, Qs, 1.0, Kq[i], 0.0, nullptr, 0.0, nullptr))) break;
+    if ((rc = wave_rs(ctx, u, Qt, Rs[i]))) break;
+    // Ku_i = (U_i - u^n) / (g dt) - sum_{j<i} (a_ij / g) Ku_j
+    for (int j = 0; j < 3; ++j) { kx[j] = j < i ? Ku[j] : nullptr; kc[j] = j < i ? -d.A[i][j] / g : 0.0; }
+    if ((rc = lin(Ku[i], n, 1.0 / (g * dt), u, -1.0 / (g * dt), un, kc[0], kx[0], kc[1], kx[1]))) break;
+    if (w) {
+      // alpha Kw_i + beta (w^n + dt sum_{j<=i} a_ij Kw_j) = U_i
+      const double den = alpha + beta * g * dt;
+      for (int j = 0; j < 3; ++j) { kx[j] = j < i ? Kw[j] : nullptr; kc[j] = j < i ? -beta * dt * d.A[i][j] / den : 0.0; }
+      if ((rc = lin(Kw[i], n, 1.0 / den, u, -beta / den, wn, kc[0], kx[0], kc[1], kx[1]))) break;
+    }
+  }
+  if (!rc) {
+    // y^{n+1} = y^n + dt sum_i b_i K_i for u, q and w
+    const double b1 = d.s > 1 ? dt * d.b[1] : 0.0, b2 = d.s > 2 ? dt * d.b[2] : 0.0;
+    rc = lin(u, n, 1.0, un, dt * d.b[0], Ku[0], b1, d.s > 1 ? Ku[1] : nullptr, b2, d.s > 2 ? Ku[2] : nullptr);
+    if (!rc) rc = lin(q, nq, 1.0, qn, dt * d.b[0], Kq[0], b1, d.s > 1 ? Kq[1] : nullptr, b2, d.s > 2 ? Kq[2] : nullptr);
+    if (!rc && w)
+      rc = lin(w, n, 1.0, wn, dt * d.b[0], Kw[0], b1, d.s > 1 ? Kw[1] : nullptr, b2, d.s > 2 ? Kw[2] : nullptr);
+  }
+  ctx->mp.kappa = c2;
+  ctx->pc_hold = false;
+  const int rc2 = ldg_set_time(ctx, LDG_STEADY, t + dt, 1.0, nullptr, nullptr);
+  if (rep) {
+    total.status = rc;
     *rep = total;
   }
   return rc ? rc : rc2;

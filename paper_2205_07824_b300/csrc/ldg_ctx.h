@@ -43,6 +43,9 @@ struct ldg_ctx {
   double* d_radd = nullptr;    // DIRK stage: constant added to the residual (active when radd_on)
   bool radd_on = false;
   double* d_dirk = nullptr;    // DIRK work: u^n, then the stages' spatial residuals and slopes
+  double* d_wave = nullptr;    // wave steps: u^n, q^n, w^n and the stages' slopes and residuals
+  double pc_kappa = 0.0, pc_a0dt = -1.0;  // kappa and a0/dt the block-Jacobi blocks were built with
+  bool pc_hold = false;        // do_newton keeps the built blocks (wave stages of one operator)
   // nodal J.v kernels of linear models on affine tensor elements (null when not applicable)
   ldg::LinFn lin64 = nullptr, lin32 = nullptr;
   ldg::LinFn linff = nullptr;

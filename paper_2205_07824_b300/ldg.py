@@ -129,6 +129,8 @@ def lib():
         L.ldg_jvp_after_residual.argtypes = [vp, ctypes.c_int, dp, dp, dp]
         L.ldg_jvp_fd.argtypes = [vp, ctypes.c_int, dp, dp, dp]
         L.ldg_dirk_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, ctypes.c_void_p]
+        L.ldg_wave_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, dp, dp, dp, ctypes.c_void_p]
         L.ldg_diag_blocks.argtypes = [vp, ctypes.c_int, dp, dp]
         L.ldg_precond_setup.argtypes = [vp, dp]
         L.ldg_precond_apply.argtypes = [vp, dp, dp]
@@ -310,6 +312,18 @@ class LDG:
         """One DIRK step in place from t to t + dt (scheme: DIRK11/22/33/34 = 1..4)."""
         rep = SolveReport()
         rc = lib().ldg_dirk_step(self._h, scheme, t, dt, _ptr(u, self.n_dof, "u"), ctypes.byref(rep))
+        if check:
+            self._check(rc)
+        return rep.as_dict()
+
+    def wave_step(self, u, q, w=None, t: float = 0.0, dt: float = 0.01, scheme: int = 3, alpha: float = 1.0,
+                  beta: float = 0.0, check=True):
+        """One DIRK step of the wave model in place (ldg_wave_step): u (n_dof), q (n_dof * dim)
+        and optionally w (n_dof), from t to t + dt."""
+        rep = SolveReport()
+        n = self.n_dof
+        rc = lib().ldg_wave_step(self._h, scheme, t, dt, alpha, beta, _ptr(u, n, "u"), _ptr(q, n * self.dim, "q"),
+                                 None if w is None else _ptr(w, n, "w"), ctypes.byref(rep))
         if check:
             self._check(rc)
         return rep.as_dict()

@@ -816,3 +816,116 @@ def test_tetrahedral_rates_match_table3(p):
     assert abs(rq - gold["q_rate_n2_to_n4"][str(p)]) < 0.3, rq
     assert ru > p + 0.5 and rq > p - 1 / 3, (ru, rq)
 
+
+
+# ---------------------------------------------------------------- wave model (Section 2.1)
+def _wave(mesh, p, c2, tau):
+    from oracle import wave
+    o = oracle.Oracle(mesh, p, oracle.POISSON, oracle.CASE_ZERO, (c2, tau))
+    L, M = wave.wave_operator(o)
+    return o, L, M
+
+
+def _energy_matrix(o, M, c2):
+    """blockdiag(M, c^2 M per q component) in the [E][dim][n_pe] layout of q."""
+    import scipy.linalg as sla
+    n, nd = o.ndof, o.nd
+    idx = np.arange(n * nd).reshape(o.mesh.n_elem, nd, o.npe)
+    Mq = np.zeros((n * nd, n * nd))
+    for d in range(nd):
+        sel = idx[:, d, :].ravel()
+        Mq[np.ix_(sel, sel)] = M
+    return sla.block_diag(M, c2 * Mq)
+
+
+@pytest.mark.parametrize("kind", ["quad_periodic", "quad_dirichlet", "tri_periodic", "hex_periodic"])
+def test_wave_operator_conserves_energy_without_penalty_and_dissipates_with_it(kind):
+    """E(u, q) = u.M u + c^2 q.M q is the wave's energy; d/dt E = 2 y.E L y. With central
+    traces and tau = 0 the LDG q-equation and the q-term of Eq. 1b are adjoint, so E L is
+    skew; with tau > 0 its symmetric part is negative semidefinite and not zero. A flipped
+    sign or a transposed coupling in either map, or a missing c^2, breaks the first."""
+    mesh = {"quad_periodic": lambda: synth.quad_box(3, periodic=(True, True), affine=np.array([[1.0, 0.3], [0.1, 0.9]])),
+            "quad_dirichlet": lambda: synth.quad_box(3),
+            "tri_periodic": lambda: synth.tri_square(3, periodic=(True, True)),
+            "hex_periodic": lambda: synth.hex_box(3, periodic=(True, True, True))}[kind]()
+    p = 1 if mesh.nd == 3 else 2
+    c2 = 0.7
+    o, L, M = _wave(mesh, p, c2, 0.0)
+    S = _energy_matrix(o, M, c2) @ L
+    assert np.linalg.norm(S + S.T) <= 1e-13 * np.linalg.norm(S), kind
+    o, L, M = _wave(mesh, p, c2, 1.0)
+    S = _energy_matrix(o, M, c2) @ L
+    ev = np.linalg.eigvalsh(0.5 * (S + S.T))
+    assert ev.max() <= 1e-13 * np.linalg.norm(S) and ev.min() < -1e-3 * np.linalg.norm(S), kind
+
+
+def _standing_wave(o, c):
+    from oracle import wave
+    X = wave.quad_node_coords(o)
+    sx = (np.sin(2 * np.pi * X[..., 0]) * np.sin(2 * np.pi * X[..., 1])).ravel()
+    return sx, c * 2 * np.pi * np.sqrt(2.0)
+
+
+@pytest.mark.parametrize("scheme,order", [(1, 1), (2, 2), (3, 3), (4, 4)])
+def test_wave_dirk_temporal_order_against_the_matrix_exponential(scheme, order):
+    """The DIRK step of the coupled (u, q) system against exp(T L) y0 for a smooth start
+    (a standing-wave displacement): the observed order of each scheme."""
+    import scipy.linalg as sla
+    from oracle import wave
+    o, L, M = _wave(synth.quad_box(4, periodic=(True, True)), 3, 1.0, 0.5)
+    n = o.ndof
+    sx, _ = _standing_wave(o, 1.0)
+    y0 = np.concatenate([np.zeros(n), o.q(sx)])
+    T = 0.2
+    ex = sla.expm(T * L) @ y0
+    errs = []
+    for N in (16, 32, 64):
+        u, q = y0[:n].copy(), y0[n:].copy()
+        for _ in range(N):
+            u, q, _ = wave.wave_step(L, n, u, q, None, T / N, scheme)
+        errs.append(np.linalg.norm(np.concatenate([u, q]) - ex) / np.linalg.norm(ex))
+    rate = math.log2(errs[1] / errs[2])
+    assert order - 0.3 < rate < order + 0.3, (scheme, errs)
+
+
+@pytest.mark.parametrize("p,lo,hi", [(1, 1.5, 2.6), (2, 2.5, 4.2)])
+def test_wave_displacement_converges_to_the_standing_wave(p, lo, hi):
+    """w = sin(2 pi x) sin(2 pi y) cos(omega t), omega = 2 pi sqrt(2) c, on the periodic unit
+    square, from w0, u0 = 0, q0 = Q(w0): the displacement the ODE (alpha = 1, beta = 0)
+    recovers at T = 0.15 after 60 DIRK34 steps converges under refinement 4 -> 8."""
+    import scipy.linalg as sla
+    from oracle import wave
+    c, T, N = 1.0, 0.15, 60
+    errs = []
+    for m in (4, 8):
+        o, L, M = _wave(synth.quad_box(m, periodic=(True, True)), p, c * c, 1.0)
+        n = o.ndof
+        sx, om = _standing_wave(o, c)
+        u, q, w = np.zeros(n), o.q(sx), sx.copy()
+        dt = T / N
+        A, b, cc = oracle.dirk_tableau(4)
+        lu = sla.lu_factor(np.eye(L.shape[0]) - dt * A[0][0] * L)
+        for _ in range(N):
+            u, q, w = wave.wave_step(L, n, u, q, w, dt, 4, solve=lambda a, r: sla.lu_solve(lu, r))
+        ex = sx * math.cos(om * T)
+        errs.append(np.linalg.norm(w - ex) / np.linalg.norm(ex))
+    rate = math.log2(errs[0] / errs[1])
+    assert lo < rate < hi, (p, errs)
+
+
+def test_wave_ode_closed_form_for_a_constant_velocity():
+    """A constant u on a periodic mesh is a steady state of the (u, q) system (Q(const) = 0,
+    R_s(const, 0) = 0); then alpha dw/dt + beta w = u has w(t) = u / beta + (w0 - u / beta)
+    exp(-beta t / alpha), which DIRK34 reaches to its truncation error."""
+    from oracle import wave
+    o, L, M = _wave(synth.quad_box(3, periodic=(True, True)), 2, 1.0, 1.0)
+    n = o.ndof
+    U0, alpha, beta, T, N = 0.8, 2.0, 3.0, 0.5, 20
+    u, q = np.full(n, U0), np.zeros(n * o.nd)
+    w0 = np.linspace(-1.0, 1.0, n)
+    w = w0.copy()
+    for _ in range(N):
+        u, q, w = wave.wave_step(L, n, u, q, w, T / N, 4, alpha=alpha, beta=beta)
+    assert np.abs(u - U0).max() < 1e-12 and np.abs(q).max() < 1e-12
+    ex = U0 / beta + (w0 - U0 / beta) * math.exp(-beta * T / alpha)
+    assert np.abs(w - ex).max() < 1e-6 * np.abs(ex).max()
