@@ -983,6 +983,73 @@ def run_tet(args):
     print(json.dumps(line), flush=True)
 
 
+WAVE_WORKLOAD = ("Section 2.1's wave model: w_tt = c^2 lap w as u = w_t, dq/dt + grad u = 0, du/dt + "
+                 "div(c^2 q) = 0 and the ODE dw/dt = u, on [0,1]^3 with 48^3 hexahedra, p = 4 (13,824,000 DOF "
+                 "of u, 41,472,000 of q), c = 1, tau = 1, homogeneous Dirichlet; from w = sin(pi x) sin(pi y) "
+                 "sin(pi z), u = 0, q = Q(w); DIRK34 steps of dt = h / 2, each stage a Newton-GMRES(30) "
+                 "solve to 1e-8 (linear solves to 1e-6, no preconditioner)")
+
+
+def run_wave(args):
+    """DIRK34 steps of the scalar wave equation (the wave model with the displacement ODE)
+    on 48^3 hexahedra, p = 4: time per step, the Krylov J.v count, and the displacement's
+    nodal error against the exact standing wave at the end."""
+    import math
+    import torch
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, CONVDIFF, CASE_ZERO, CASE_SINSIN, DIRK34, kernel_launches
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    n_side, p, c = 48, 4, 1.0
+    mesh = synth.hex_box(n_side)
+    # the diffusion operator with beta = 0 (the compiled hexahedral set of p = 4)
+    kprec = {"fp64": 0, "fp32": 1, "f32x2": 2}[args.krylov]
+    pc = {"none": 0, "bjacobi": 1, "mlp": 0}[args.precond]
+    g = LDG(mesh, p, CONVDIFF, CASE_ZERO, (c * c, 1.0, 0.0, 0.0, 0.0), gmres_m=30, newton_rtol=1e-8,
+            gmres_rtol=1e-6, max_newton=10, max_restarts=50, precond=pc, krylov_precision=kprec)
+    w0 = LDG(mesh, p, CONVDIFF, CASE_SINSIN, (1.0, 1.0, 0.0, 0.0, 0.0), gmres_m=1).interpolate(0.0)
+    u = torch.zeros_like(w0)
+    q = g.q(w0)
+    w = w0.clone()
+    dt = 0.5 / n_side / c
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t = 0.0
+    for _ in range(args.warmup):
+        g.wave_step(u, q, w, t=t, dt=dt, scheme=DIRK34)
+        t += dt
+    torch.cuda.synchronize()
+    l0 = kernel_launches()
+    reps = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        reps.append(g.wave_step(u, q, w, t=t, dt=dt, scheme=DIRK34))
+        t += dt
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = kernel_launches() - l0
+    clk = clocks.stop()
+    omega = c * math.pi * math.sqrt(3.0)
+    err = float(torch.linalg.norm(w - w0 * math.cos(omega * t)) / torch.linalg.norm(w0 * math.cos(omega * t)))
+    jv = sum(r["jv_calls"] for r in reps) / len(reps)
+    n = g.n_dof
+    line = {"metric": METRIC, "value": n / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WAVE_WORKLOAD, "n_dof": n, "dt": dt, "t_end": t,
+                       "value_definition": "DOF of u x DIRK34 steps / time (each step three stage solves)",
+                       "krylov_precision": args.krylov, "precond": ("none", "bjacobi")[pc],
+                       "jv_calls_per_step": jv,
+                       "gmres_iters_per_step": sum(r["gmres_iters"] for r in reps) / len(reps),
+                       "w_rel_err_vs_standing_wave": err,
+                       "l2": "not flushed: the state and the Krylov space (about 7 GB) exceed the 126 MB L2"},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 CYL_WORKLOAD = ("2D compressible Navier-Stokes flow past a cylinder (radius 0.5 at the origin, domain "
                 "[-10,30]x[-10,10]), {E} curved quadrilaterals ({nr} advancing layers x {nt} around, first layer "
                 "0.01, map degree 3, seeded node jitter, seed 7), p=3, Re={re:.1f} (uniform [100,1000], seed {rs}), "
@@ -1220,7 +1287,7 @@ def main():
     ap.add_argument("--precond", default="bjacobi", choices=["none", "bjacobi", "mlp"],
                     help="block-Jacobi: exact element-diagonal blocks, rebuilt once per implicit step; "
                          "mlp: the learned per-element preconditioner trained on the warm-up steps")
-    ap.add_argument("--krylov", default="fp32", choices=["fp64", "fp32"],
+    ap.add_argument("--krylov", default="fp32", choices=["fp64", "fp32", "f32x2"],
                     help="arithmetic of the J.v inside GMRES (Newton residual and Arnoldi stay FP64)")
     ap.add_argument("--forcing", default="last", choices=["fixed", "last"],
                     help="Newton-GMRES workloads (vortex, batch, cylinder): linear tolerance of each Newton "
@@ -1235,14 +1302,15 @@ def main():
                          "graph's WHILE nodes (same kernels; for profilers that do not follow graph nodes)")
     ap.add_argument("--no-solve", action="store_true", help="jv: skip the vortex time-to-1e-8 comparison")
     ap.add_argument("--workload", default="jv",
-                    choices=["jv", "jvprobe", "vortex", "batch", "hex", "tri", "cylinder", "tet"],
+                    choices=["jv", "jvprobe", "vortex", "batch", "hex", "tri", "cylinder", "tet", "wave"],
                     help="jv (default): the FP64 J.v of 48^3 p=4 convection-diffusion; jvprobe: its J.v "
                          "applications alone, for profilers; "
                          "vortex: the 64x64 p=3 Euler BDF2 step; batch: 256 parametrised convection-diffusion "
                          "solves in one graph launch; hex: the 48^3 convection-diffusion J.v sweep p=1..6; "
                          "tri: the same sweep on 131,072 triangles; "
                          "cylinder: Navier-Stokes past a cylinder on 40,000 curved quads, learned + mixed vs "
-                         "plain FP64 block-Jacobi; tet: Table 3's Poisson problem on tetrahedra, 1/n = 32, p = 3")
+                         "plain FP64 block-Jacobi; tet: Table 3's Poisson problem on tetrahedra, 1/n = 32, p = 3; "
+                         "wave: DIRK34 steps of the wave model on 48^3 hexahedra, p = 4")
     ap.add_argument("--tet-n", type=int, default=32, help="tet: cubes per side (Table 3's 1/n)")
     ap.add_argument("--tet-p", type=int, default=3, help="tet: polynomial order")
     ap.add_argument("--cyl-layers", type=int, default=100, help="cylinder mesh: layers across the domain")
@@ -1281,6 +1349,9 @@ def main():
         return
     if args.workload == "tet":
         run_tet(args)
+        return
+    if args.workload == "wave":
+        run_wave(args)
         return
 
     import numpy as np

@@ -461,9 +461,10 @@ int ldg_dirk_step(ldg_ctx* ctx, int scheme, double t, double dt, double* u_dev, 
  * s_w = u). With u the velocity, q = -grad w and f = kappa q, kappa = c^2, the system
  *   M du/dt + R_s(u, q) = 0,   dq/dt = Q(u),   alpha dw/dt + beta w = u
  * (Q the LDG q-stage map of Eq. 1a, R_s the spatial residual of Eq. 1b with q given)
- * is the scalar wave equation w_tt = c^2 lap w. The context must be a Poisson model of
- * case LDG_CASE_ZERO (no source, homogeneous Dirichlet or periodic faces): mu = {kappa,
- * tau}, the wave speed squared and the jump penalty.
+ * is the scalar wave equation w_tt = c^2 lap w. The context must be a Poisson model, or
+ * convection-diffusion with beta = 0 (the same operator), of case LDG_CASE_ZERO (no
+ * source, homogeneous Dirichlet or periodic faces): mu = {kappa, tau (, 0, 0, 0)}, the
+ * wave speed squared and the jump penalty.
  * One step of a DIRK scheme (LDG_DIRK11..34, all singly diagonally implicit) from t to
  * t + dt: u_dev (n_dof), q_dev (n_dof * dim, layout [E][dim][n_pe]) and w_dev (n_dof;
  * may be NULL to skip the ODE) hold the state at t on entry and at t + dt on return.
@@ -473,9 +474,8 @@ int ldg_dirk_step(ldg_ctx* ctx, int scheme, double t, double dt, double* u_dev, 
  * follow node by node. The blocks are built once per operator (kappa', a_ii dt) and kept
  * over stages and steps. The context's kappa is restored and its time scheme left
  * steady on return. rep (optional) sums the stages' iterations. The first call allocates
- * 12 n_dof + 6 n_dof dim doubles of context scratch. Errors: LDG_ERR_ARG (not a Poisson
- * context of case zero, bad scheme, dt <= 0, alpha + beta a_ii dt = 0), a stage's solver
- * status. */
+ * 12 n_dof + 6 n_dof dim doubles of context scratch. Errors: LDG_ERR_ARG (not such a
+ * context, bad scheme, dt <= 0, alpha + beta a_ii dt = 0), a stage's solver status. */
 int ldg_wave_step(ldg_ctx* ctx, int scheme, double t, double dt, double alpha, double beta, double* u_dev,
                   double* q_dev, double* w_dev, ldg_solve_report* rep);
 

@@ -1714,8 +1714,13 @@ int ldg_wave_step(ldg_ctx* ctx, int scheme, double t, double dt, double alpha, d
                   double* w, ldg_solve_report* rep) {
   Dirk d;
   if (!ctx || !ctx->ks || !u || !q || !(dt > 0) || !dirk_tableau(scheme, d)) return LDG_ERR_ARG;
-  if (ctx->model != LDG_POISSON || ctx->mp.cas != LDG_CASE_ZERO || ctx->ncu != 1)
-    return fail(ctx, LDG_ERR_ARG, "ldg_wave_step: the context must be a Poisson model of case LDG_CASE_ZERO");
+  const bool diffusion = ctx->model == LDG_POISSON ||
+                         (ctx->model == LDG_CONVDIFF && ctx->mp.beta[0] == 0.0 && ctx->mp.beta[1] == 0.0 &&
+                          ctx->mp.beta[2] == 0.0);
+  if (!diffusion || ctx->mp.cas != LDG_CASE_ZERO || ctx->ncu != 1)
+    return fail(ctx, LDG_ERR_ARG,
+                "ldg_wave_step: the context must be a Poisson model (or convection-diffusion with beta = 0) of case "
+                "LDG_CASE_ZERO");
   const double g = d.A[0][0];
   for (int i = 1; i < d.s; ++i)
     if (d.A[i][i] != g) return fail(ctx, LDG_ERR_ARG, "ldg_wave_step: the scheme is not singly diagonally implicit");

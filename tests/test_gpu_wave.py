@@ -74,9 +74,26 @@ def test_wave_step_rejects_other_models_and_cases():
     mesh = synth.quad_box(4)
     n = None
     for model, case, mu in ((oracle.CONVDIFF, oracle.CASE_ZERO, (0.1, 1.0, 1.0, 0.5)),
-                            (oracle.POISSON, oracle.CASE_SINSIN, (1.0, 1.0))):
+                            (oracle.POISSON, oracle.CASE_SINSIN, (1.0, 1.0)), (oracle.EULER, oracle.CASE_VORTEX, (1.4,))):
         g = LDG(mesh, 2, model, case, mu)
         n = g.n_dof
         u, q = cuda(np.zeros(n)), cuda(np.zeros(n * g.dim))
         with pytest.raises(RuntimeError):
             g.wave_step(u, q, None, dt=0.1)
+
+
+def test_wave_step_on_convection_diffusion_without_convection():
+    """Convection-diffusion with beta = 0 is the same operator: its wave step equals the
+    Poisson oracle's."""
+    mesh = synth.quad_box((4, 4), periodic=(True, True), affine=SHEAR2)
+    o, _ = pair(mesh, 2, oracle.POISSON, oracle.CASE_ZERO, mu=(C2, TAU))
+    from paper_2205_07824_b300.ldg import LDG
+    g = LDG(mesh, 2, oracle.CONVDIFF, oracle.CASE_ZERO, (C2, TAU, 0.0, 0.0), nq1=o.nq1, **SOLVE)
+    L, _ = wave.wave_operator(o)
+    n = o.ndof
+    rng = np.random.default_rng(4)
+    u, q = rng.standard_normal(n), rng.standard_normal(n * o.nd)
+    gu, gq = cuda(u), cuda(q)
+    g.wave_step(gu, gq, None, dt=0.03, scheme=2)
+    u1, q1, _ = wave.wave_step(L, n, u, q, None, 0.03, 2)
+    assert _rel(host(gu), u1) <= 1e-10 and _rel(host(gq), q1) <= 1e-10
