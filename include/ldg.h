@@ -129,10 +129,11 @@ typedef struct {
                            FP64 blocks). Newton residuals, Arnoldi, Givens and all vectors stay
                            FP64. LDG_F32X2 is accepted where the float-pair J.v exists (see
                            LDG_F32X2 below); ldg_create returns LDG_ERR_ARG elsewhere. */
-  int precond;          /* LDG_PC_NONE (default), LDG_PC_BJACOBI, LDG_PC_MLP or LDG_PC_MLP_BJ
-                           (flexible right preconditioning; a linear solve with a learned one
-                           that misses its tolerance within two restart cycles is redone with
-                           block-Jacobi; see the learned-preconditioner section below) */
+  int precond;          /* LDG_PC_NONE (default), LDG_PC_BJACOBI, LDG_PC_MLP, LDG_PC_MLP_BJ or
+                           LDG_PC_RB_BJ (flexible right preconditioning; a linear solve with a
+                           learned one that misses its tolerance within two restart cycles is
+                           redone with block-Jacobi; see the learned-preconditioner and the
+                           reduced-basis sections below) */
   int pc_refresh;       /* rebuild the preconditioner every pc_refresh Newton iterations
                            (0 = once per ldg_newton_gmres call, at the initial guess) */
   int newton_forcing;   /* linear tolerance eta_k of Newton step k (inexact Newton):
@@ -161,6 +162,7 @@ typedef struct {
                            operator in exact nodal form, one thread per node, two launches);
                            LDG_JV_STAGE keeps the quadrature-point stage kernels of every
                            other case. Results agree to rounding. */
+  int rb_size;          /* LDG_PC_RB_BJ: columns of the reduced basis (default 8, at most 32) */
 } ldg_options;
 
 /* Arithmetic of a J.v. LDG_FP64: FP64. LDG_FP32: every operation in FP32 (inputs and
@@ -172,7 +174,7 @@ typedef struct {
  * quadrilaterals and hexahedra with p + 1 Gauss points per direction, and on triangles
  * and tetrahedra with at least p + 2. */
 enum { LDG_FP64 = 0, LDG_FP32 = 1, LDG_F32X2 = 2 };
-enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1, LDG_PC_MLP = 2, LDG_PC_MLP_BJ = 3 };
+enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1, LDG_PC_MLP = 2, LDG_PC_MLP_BJ = 3, LDG_PC_RB_BJ = 4 };
 enum { LDG_FORCING_FIXED = 0, LDG_FORCING_LAST = 1 };
 enum { LDG_BASIS_FP64 = 0, LDG_BASIS_F32X2 = 1 };
 enum { LDG_JV_AUTO = 0, LDG_JV_STAGE = 1 };
@@ -294,6 +296,29 @@ int ldg_diag_blocks(ldg_ctx* ctx, int precision, const double* u_dev, double* bl
  * the context), and applies y = M^{-1} x (device vectors, n_dof doubles). */
 int ldg_precond_setup(ldg_ctx* ctx, const double* u_dev);
 int ldg_precond_apply(ldg_ctx* ctx, const double* x_dev, double* y_dev);
+
+/* ------------------------------------------------------------------------------------
+ * Reduced-basis preconditioner (Section 3.3: a preconditioner built by the reduced basis
+ * method and a low-rank approximation of the Jacobian; its construction is given in the
+ * paper's references, so this is a reading of the passage). The reduced basis W holds up
+ * to rb_size orthonormal vectors: the Newton updates of the solves so far (each update
+ * is orthogonalised against the basis and enters it, the oldest leaving once it is
+ * full), so that over a sequence of time steps it spans the directions the solution
+ * keeps moving in. At the first Newton step of a solve the solver forms J W (rb_size
+ * J.v in the Krylov arithmetic) and G = (J W)^T J W (its inverse on the host); each update
+ * entering the basis adds one J.v and a row and column of G. It applies
+ *   P^{-1} r = C r + B^{-1} (r - J C r),   C = W G^{-1} (J W)^T,
+ * with B the block-Jacobi preconditioner: C r is the minimal-residual solve on span(W)
+ * (J C the orthogonal projector onto span(J W)), block-Jacobi acts on the rest. On span(W)
+ * the preconditioned operator is the identity (P^{-1} J w = w). precond = LDG_PC_RB_BJ
+ * selects it (host-driven Newton-GMRES). */
+
+/* Replaces the reduced basis by the k columns of W_dev ([k][n_dof], device, row-major;
+ * k <= rb_size; orthonormalised on copy; k = 0 empties it). Errors: LDG_ERR_ARG. */
+int ldg_rb_set_basis(ldg_ctx* ctx, const double* W_dev, int k);
+
+/* The number of vectors in the reduced basis now. */
+int ldg_rb_count(const ldg_ctx* ctx);
 
 /* Learned per-element preconditioner (the learned pattern of this build; the paper's own
  * preconditioner, Section 3.3, is a reduced-basis one). A multilayer perceptron

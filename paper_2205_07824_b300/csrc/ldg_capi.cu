@@ -484,6 +484,208 @@ int pc_apply(ldg_ctx* ctx, const double* x, double* y, const int* skip, const in
   return LDG_OK;
 }
 
+// ------------------------------------------------------ reduced-basis preconditioner
+// P^{-1} r = C r + B^{-1} (r - J C r), C = W G^{-1} (J W)^T, G = (J W)^T J W (include/ldg.h).
+// Scratch d_rbS: [0, 32) (J W)^T x, [32, 64) y, [64, 64 + 1024) G by columns, then G^{-1}
+// (row-major, 1024), then two norms.
+constexpr int kRbMax = 32;
+constexpr int kRbA = 0, kRbY = 32, kRbM = 64, kRbJi = 64 + 1024, kRbN = 64 + 2048, kRbScratch = 64 + 2048 + 8;
+
+__global__ void k_rb_small(const double* Ji, const double* a, double* y, int k, const int* flags) {
+  if (flags && flags[0]) return;
+  const int i = threadIdx.x;
+  if (i < k) {
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += Ji[i * k + j] * a[j];
+    y[i] = s;
+  }
+}
+// c = sum_j y_j W_j, r = x - sum_j y_j (J W)_j
+__global__ void k_rb_combine(const double* W, const double* JW, const double* y, int k, const double* x, double* c,
+                             double* r, int64_t n, const int* flags) {
+  if (flags && flags[0]) return;
+  __shared__ double ys[kRbMax];
+  if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double cs = 0.0, rs = x[i];
+    for (int j = 0; j < k; ++j) {
+      cs += ys[j] * W[(size_t)j * n + i];
+      rs -= ys[j] * JW[(size_t)j * n + i];
+    }
+    c[i] = cs;
+    r[i] = rs;
+  }
+}
+__global__ void k_rb_add(double* z, const double* c, int64_t n, const int* flags) {
+  if (flags && flags[0]) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] += c[i];
+}
+// v -= sum_{j != skip} h_j W_j
+__global__ void k_rb_orth(const double* W, const double* h, int k, int skip, double* v, int64_t n) {
+  __shared__ double hs[kRbMax];
+  if (threadIdx.x < k) hs[threadIdx.x] = (int)threadIdx.x == skip ? 0.0 : h[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = v[i];
+    for (int j = 0; j < k; ++j) s -= hs[j] * W[(size_t)j * n + i];
+    v[i] = s;
+  }
+}
+__global__ void k_rb_scale(const double* v, double a, double* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = a * v[i];
+}
+
+int ensure_rb_storage(ldg_ctx* ctx) {
+  if (ctx->d_rbW || ctx->rb_cap <= 0) return LDG_OK;
+  const size_t n = (size_t)ctx->ndof;
+  CK(cudaMalloc(&ctx->d_rbW, (size_t)ctx->rb_cap * n * sizeof(double)));
+  CK(cudaMalloc(&ctx->d_rbJW, (size_t)ctx->rb_cap * n * sizeof(double)));
+  CK(cudaMalloc(&ctx->d_rbS, kRbScratch * sizeof(double)));
+  CK(cudaMalloc(&ctx->d_rbC, 2 * n * sizeof(double)));
+  return LDG_OK;
+}
+
+// Inverse of the rb_k x rb_k matrix ctx->h_rbJr (G; Gauss-Jordan with partial pivoting) into
+// the device scratch; a matrix singular to rounding leaves block-Jacobi alone.
+int rb_invert(ldg_ctx* ctx) {
+  const int k = ctx->rb_k;
+  ctx->rb_eff = 0;
+  if (k == 0) return LDG_OK;
+  std::vector<double> A((size_t)k * 2 * k, 0.0);
+  double amax = 0.0;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      A[(size_t)i * 2 * k + j] = ctx->h_rbJr[(size_t)i * kRbMax + j];
+      amax = std::max(amax, std::fabs(ctx->h_rbJr[(size_t)i * kRbMax + j]));
+    }
+  for (int i = 0; i < k; ++i) A[(size_t)i * 2 * k + k + i] = 1.0;
+  for (int c = 0; c < k; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < k; ++r)
+      if (std::fabs(A[(size_t)r * 2 * k + c]) > std::fabs(A[(size_t)piv * 2 * k + c])) piv = r;
+    const double d = A[(size_t)piv * 2 * k + c];
+    if (!(std::fabs(d) > 1e-12 * amax) || !std::isfinite(d)) return LDG_OK;
+    if (piv != c)
+      for (int j = 0; j < 2 * k; ++j) std::swap(A[(size_t)piv * 2 * k + j], A[(size_t)c * 2 * k + j]);
+    for (int j = 0; j < 2 * k; ++j) A[(size_t)c * 2 * k + j] /= d;
+    for (int r = 0; r < k; ++r) {
+      if (r == c) continue;
+      const double f = A[(size_t)r * 2 * k + c];
+      if (f != 0.0)
+        for (int j = 0; j < 2 * k; ++j) A[(size_t)r * 2 * k + j] -= f * A[(size_t)c * 2 * k + j];
+    }
+  }
+  std::vector<double> Ji((size_t)k * k);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) Ji[(size_t)i * k + j] = A[(size_t)i * 2 * k + k + j];
+  CK(cudaMemcpyAsync(ctx->d_rbS + kRbJi, Ji.data(), Ji.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->rb_eff = k;
+  return LDG_OK;
+}
+
+// Enter v (device, n) into the basis: orthogonalised twice against the vectors that stay,
+// skipped when nothing of it remains, normalised into a free slot or the oldest one.
+// With u given and the set-up current, the new column's J W_s = J(u) W_s and the row and
+// column s of G are formed (one J.v), so the set-up stays current; otherwise a later
+// rb_setup forms all of it.
+int rb_insert(ldg_ctx* ctx, const double* v, const double* u) {
+  int rc;
+  if (ctx->rb_cap <= 0) return LDG_OK;
+  if ((rc = ensure_rb_storage(ctx))) return rc;
+  const int64_t n = ctx->ndof;
+  const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8);
+  const int k = ctx->rb_k, full = k == ctx->rb_cap;
+  const int slot = full ? ctx->rb_next : k;
+  const bool current = u && ctx->rb_eff == k;
+  double* t = ctx->d_rbC;
+  double* S = ctx->d_rbS;
+  CK(cudaMemcpyAsync(t, v, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  if ((rc = dots(ctx, t, n, 1, t, S + kRbN, nullptr))) return rc;
+  for (int pass = 0; pass < 2 && k > 0; ++pass) {
+    if ((rc = dots(ctx, ctx->d_rbW, n, k, t, S + kRbA, nullptr))) return rc;
+    k_rb_orth<<<g1, 256, 0, ctx->stream>>>(ctx->d_rbW, S + kRbA, k, full ? slot : -1, t, n);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+  if ((rc = dots(ctx, t, n, 1, t, S + kRbN + 1, nullptr))) return rc;
+  if ((rc = read_scalars(ctx, S + kRbN, 2))) return rc;
+  const double n0 = std::sqrt(ctx->h_pin[0]), n1 = std::sqrt(ctx->h_pin[1]);
+  if (!(n1 > 1e-10 * n0) || !std::isfinite(n1)) return LDG_OK;   // nothing new in v
+  double* ws = ctx->d_rbW + (size_t)slot * n;
+  k_rb_scale<<<g1, 256, 0, ctx->stream>>>(t, 1.0 / n1, ws, n);
+  count_launch();
+  CK(cudaGetLastError());
+  if (full) ctx->rb_next = (ctx->rb_next + 1) % ctx->rb_cap;
+  else ++ctx->rb_k;
+  const int k1 = ctx->rb_k;
+  if (!current) { ctx->rb_eff = 0; return LDG_OK; }
+  // row and column s of G: (J W)_i . (J W)_s
+  double* jws = ctx->d_rbJW + (size_t)slot * n;
+  if ((rc = jvp_args(ctx, base_args(ctx), u, ws, jws, ctx->opt.krylov_precision))) return rc;
+  if ((rc = dots(ctx, ctx->d_rbJW, n, k1, jws, S + kRbM, nullptr))) return rc;
+  double cr[kRbMax];
+  CK(cudaMemcpyAsync(cr, S + kRbM, kRbMax * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->h_rbJr.empty()) ctx->h_rbJr.assign((size_t)kRbMax * kRbMax, 0.0);
+  for (int i = 0; i < k1; ++i) {
+    ctx->h_rbJr[(size_t)i * kRbMax + slot] = cr[i];
+    ctx->h_rbJr[(size_t)slot * kRbMax + i] = cr[i];
+  }
+  return rb_invert(ctx);
+}
+
+// J W at state u for every vector and G = (J W)^T J W, then its inverse.
+int rb_setup(ldg_ctx* ctx, const double* u) {
+  int rc;
+  ctx->rb_eff = 0;
+  const int k = ctx->rb_k;
+  if (k == 0) return LDG_OK;
+  const int64_t n = ctx->ndof;
+  double* S = ctx->d_rbS;
+  for (int j = 0; j < k; ++j) {
+    if ((rc = jvp_args(ctx, base_args(ctx), u, ctx->d_rbW + (size_t)j * n, ctx->d_rbJW + (size_t)j * n,
+                       ctx->opt.krylov_precision)))
+      return rc;
+  }
+  for (int j = 0; j < k; ++j)
+    if ((rc = dots(ctx, ctx->d_rbJW, n, k, ctx->d_rbJW + (size_t)j * n, S + kRbM + j * kRbMax, nullptr))) return rc;
+  std::vector<double> colmaj((size_t)k * kRbMax);
+  CK(cudaMemcpyAsync(colmaj.data(), S + kRbM, colmaj.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->h_rbJr.empty()) ctx->h_rbJr.assign((size_t)kRbMax * kRbMax, 0.0);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) ctx->h_rbJr[(size_t)i * kRbMax + j] = colmaj[(size_t)j * kRbMax + i];
+  return rb_invert(ctx);
+}
+
+// z = C x + B^{-1} (x - J C x); block-Jacobi alone while no reduced set-up is in force
+int rb_apply(ldg_ctx* ctx, const double* x, double* z, const int* flags) {
+  int rc;
+  const int k = ctx->rb_eff;
+  if (k == 0) return pc_apply(ctx, x, z, flags);
+  const int64_t n = ctx->ndof;
+  const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8);
+  double* S = ctx->d_rbS;
+  double* c = ctx->d_rbC;
+  double* r = c + n;
+  if ((rc = dots(ctx, ctx->d_rbJW, n, k, x, S + kRbA, flags))) return rc;
+  k_rb_small<<<1, kRbMax, 0, ctx->stream>>>(S + kRbJi, S + kRbA, S + kRbY, k, flags);
+  k_rb_combine<<<g1, 256, 0, ctx->stream>>>(ctx->d_rbW, ctx->d_rbJW, S + kRbY, k, x, c, r, n, flags);
+  count_launch();
+  count_launch();
+  CK(cudaGetLastError());
+  if ((rc = pc_apply(ctx, r, z, flags))) return rc;
+  k_rb_add<<<g1, 256, 0, ctx->stream>>>(z, c, n, flags);
+  count_launch();
+  CK(cudaGetLastError());
+  return LDG_OK;
+}
+
 // ------------------------------------------------------------ MLP preconditioner
 int mlp_reserve(ldg_ctx* ctx, int64_t rows) {
   auto& M = ctx->mlp;
@@ -829,7 +1031,7 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
   if (bnorm == 0.0) return LDG_OK;
   const double thr = rtol * bnorm;
   CK(cudaMemcpyAsync(sc + 3, &thr, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  const bool pc = (ctx->opt.precond == LDG_PC_BJACOBI && ctx->pc_ready) ||
+  const bool pc = ((ctx->opt.precond == LDG_PC_BJACOBI || ctx->opt.precond == LDG_PC_RB_BJ) && ctx->pc_ready) ||
                   (ctx->opt.precond == LDG_PC_MLP && ctx->mlp.ready) ||
                   (ctx->opt.precond == LDG_PC_MLP_BJ && ctx->mlp.ready && ctx->pc_ready);
   // the preconditioned Krylov vectors Z must exist before their addresses are used
@@ -857,6 +1059,8 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
           if ((rc = mlp_apply(ctx, u, dir, z, flags))) return rc;
         } else if (ctx->opt.precond == LDG_PC_MLP_BJ) {
           if ((rc = mlp_bj_apply(ctx, dir, z, flags))) return rc;
+        } else if (ctx->opt.precond == LDG_PC_RB_BJ) {
+          if ((rc = rb_apply(ctx, dir, z, flags))) return rc;
         } else {
           if ((rc = pc_apply(ctx, dir, z, flags))) return rc;
         }
@@ -948,11 +1152,16 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
   int k = 0;
   const int64_t g1 = std::min<int64_t>(grid_for(n), 148 * 8);
   while (rn > ctx->opt.newton_rtol * r0 && k < ctx->opt.max_newton) {
-    if ((ctx->opt.precond == LDG_PC_BJACOBI || ctx->opt.precond == LDG_PC_MLP_BJ) &&
+    if ((ctx->opt.precond == LDG_PC_BJACOBI || ctx->opt.precond == LDG_PC_MLP_BJ ||
+         ctx->opt.precond == LDG_PC_RB_BJ) &&
         ((k == 0 && !(ctx->pc_hold && ctx->pc_ready)) || (ctx->opt.pc_refresh > 0 && k % ctx->opt.pc_refresh == 0))) {
       if ((rc = do_pc_setup(ctx, u))) return rc;
       if (rep) rep->pc_setups++;
     }
+    // the reduced Jacobian: formed in full at the first Newton step of a solve (J at its
+    // initial state), then kept up to date as updates enter the basis
+    if (ctx->opt.precond == LDG_PC_RB_BJ && (k == 0 || ctx->rb_eff != ctx->rb_k) && (rc = rb_setup(ctx, u)))
+      return rc;
     if (ctx->opt.precond == LDG_PC_MLP && k == 0 && (rc = ensure_pc_storage(ctx))) return rc;
     const double eta = newton_forcing_eta(ctx->opt.newton_forcing, ctx->opt.gmres_rtol, ctx->opt.newton_rtol, r0, rn);
     const bool learned = ctx->opt.precond == LDG_PC_MLP || ctx->opt.precond == LDG_PC_MLP_BJ;
@@ -973,6 +1182,11 @@ int do_newton(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
       if (rep) { rep->pc_fallbacks++; if (learned == LDG_PC_MLP) rep->pc_setups++; }
     }
     if (rc && rc != LDG_ERR_MAXIT) return rc;
+    // the Newton update enters the reduced basis
+    if (ctx->opt.precond == LDG_PC_RB_BJ) {
+      const int rc2 = rb_insert(ctx, del, u);
+      if (rc2) return rc2;
+    }
     if (ctx->col_X && (ctx->col_mode & 1) && ctx->col_count < ctx->col_cap && ctx->pc_ready) {
       // training data of the learned block-Jacobi correction: z = BJ^{-1} R(u_k), its
       // neighbour traces h, and the Newton update delta_k
@@ -1158,6 +1372,7 @@ int ldg_destroy(ldg_ctx* ctx) {
   cudaFree(ctx->d_ops); cudaFree(ctx->d_opsf); cudaFree(ctx->d_geo); cudaFree(ctx->d_nbr); cudaFree(ctx->d_nbf); cudaFree(ctx->d_perm);
   cudaFree(ctx->d_xn); cudaFree(ctx->d_q); cudaFree(ctx->d_dq); cudaFree(ctx->d_hist);
   cudaFree(ctx->d_q32); cudaFree(ctx->d_u32);
+  cudaFree(ctx->d_rbW); cudaFree(ctx->d_rbJW); cudaFree(ctx->d_rbS); cudaFree(ctx->d_rbC);
   cudaFree(ctx->d_cgeo); cudaFree(ctx->d_cgeof); cudaFree(ctx->d_cx); cudaFree(ctx->d_minv); cudaFree(ctx->d_minvf);
   cudaFree(ctx->d_xnode); cudaFree(ctx->d_fd); cudaFree(ctx->d_radd); cudaFree(ctx->d_dirk);
   cudaFree(ctx->d_wave);
@@ -1223,12 +1438,17 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if (o.newton_rtol <= 0) o.newton_rtol = 1e-8;
   if (o.gmres_rtol <= 0) o.gmres_rtol = 1e-3;
   if (o.krylov_precision != LDG_FP32 && o.krylov_precision != LDG_F32X2) o.krylov_precision = LDG_FP64;
-  if (o.precond != LDG_PC_BJACOBI && o.precond != LDG_PC_MLP && o.precond != LDG_PC_MLP_BJ) o.precond = LDG_PC_NONE;
+  if (o.precond != LDG_PC_BJACOBI && o.precond != LDG_PC_MLP && o.precond != LDG_PC_MLP_BJ &&
+      o.precond != LDG_PC_RB_BJ)
+    o.precond = LDG_PC_NONE;
+  if (o.rb_size <= 0) o.rb_size = 8;
+  if (o.rb_size > kRbMax) o.rb_size = kRbMax;
   if (o.pc_refresh < 0) o.pc_refresh = 0;
   if (o.newton_forcing != LDG_FORCING_LAST) o.newton_forcing = LDG_FORCING_FIXED;
   if (o.pc_reuse < 1) o.pc_reuse = 1;
   if (o.krylov_basis != LDG_BASIS_F32X2) o.krylov_basis = LDG_BASIS_FP64;
   ctx->opt = o;
+  ctx->rb_cap = o.precond == LDG_PC_RB_BJ ? o.rb_size : 0;
   ctx->p = p; ctx->nq = o.nq1;
   ctx->mp = make_params(model);
   for (const KernelSet& k : registry())
@@ -1868,14 +2088,31 @@ int ldg_diag_blocks(ldg_ctx* ctx, int precision, const double* u, double* blocks
 
 int ldg_precond_setup(ldg_ctx* ctx, const double* u) {
   if (!ctx || !ctx->ks || !u) return LDG_ERR_ARG;
-  return do_pc_setup(ctx, u);
+  int rc = do_pc_setup(ctx, u);
+  if (!rc && ctx->opt.precond == LDG_PC_RB_BJ) rc = rb_setup(ctx, u);
+  return rc;
 }
 
 int ldg_precond_apply(ldg_ctx* ctx, const double* x, double* y) {
   if (!ctx || !ctx->ks || !x || !y) return LDG_ERR_ARG;
   if (!ctx->pc_ready) return fail(ctx, LDG_ERR_ARG, "ldg_precond_apply: call ldg_precond_setup first");
+  if (ctx->opt.precond == LDG_PC_RB_BJ) return rb_apply(ctx, x, y, nullptr);
   return pc_apply(ctx, x, y, nullptr);
 }
+
+int ldg_rb_set_basis(ldg_ctx* ctx, const double* W, int k) {
+  if (!ctx || !ctx->ks || k < 0 || (k > 0 && !W)) return LDG_ERR_ARG;
+  if (ctx->rb_cap <= 0) ctx->rb_cap = ctx->opt.rb_size;
+  if (k > ctx->rb_cap) return fail(ctx, LDG_ERR_ARG, "ldg_rb_set_basis: more vectors than rb_size");
+  ctx->rb_k = ctx->rb_next = ctx->rb_eff = 0;
+  for (int j = 0; j < k; ++j) {
+    const int rc = rb_insert(ctx, W + (size_t)j * ctx->ndof, nullptr);
+    if (rc) return rc;
+  }
+  return LDG_OK;
+}
+
+int ldg_rb_count(const ldg_ctx* ctx) { return ctx ? ctx->rb_k : 0; }
 
 int ldg_mlp_init(ldg_ctx* ctx, uint64_t seed) {
   if (!ctx || !ctx->ks) return LDG_ERR_ARG;
@@ -2128,8 +2365,8 @@ int ldg_newton_gmres(ldg_ctx* ctx, double* u, ldg_solve_report* rep) {
   int rc;
   // block-Jacobi built once per call, or no preconditioner: the graph-driven solver
   // (the whole Newton-GMRES one CUDA graph launch); otherwise the host-driven loop
-  if (ctx->opt.precond != LDG_PC_MLP && ctx->opt.precond != LDG_PC_MLP_BJ && ctx->opt.pc_refresh == 0 &&
-      !ctx->col_X) {
+  if (ctx->opt.precond != LDG_PC_MLP && ctx->opt.precond != LDG_PC_MLP_BJ && ctx->opt.precond != LDG_PC_RB_BJ &&
+      ctx->opt.pc_refresh == 0 && !ctx->col_X) {
     if (!ctx->engine && (rc = batch_wrap(ctx, &ctx->engine))) {
       rep->status = rc;
       return rc;

@@ -46,6 +46,14 @@ struct ldg_ctx {
   double* d_wave = nullptr;    // wave steps: u^n, q^n, w^n and the stages' slopes and residuals
   double pc_kappa = 0.0, pc_a0dt = -1.0;  // kappa and a0/dt the block-Jacobi blocks were built with
   bool pc_hold = false;        // do_newton keeps the built blocks (wave stages of one operator)
+  // reduced-basis preconditioner (LDG_PC_RB_BJ)
+  int rb_cap = 0, rb_k = 0, rb_next = 0;  // capacity, vectors held, slot replaced next when full
+  int rb_eff = 0;              // vectors the current set-up uses (0: block-Jacobi alone)
+  double* d_rbW = nullptr;     // [rb_cap][n] orthonormal reduced basis
+  double* d_rbJW = nullptr;    // [rb_cap][n] J W at the Newton state of the set-up
+  double* d_rbS = nullptr;     // small scratch: W^T x, y, J_r, J_r^{-1}, norms
+  double* d_rbC = nullptr;     // [2 n] scratch: C x and the remainder x - J C x
+  std::vector<double> h_rbJr;  // [32][32] G = (J W)^T J W (row-major), kept with rb_eff
   // nodal J.v kernels of linear models on affine tensor elements (null when not applicable)
   ldg::LinFn lin64 = nullptr, lin32 = nullptr;
   ldg::LinFn linff = nullptr;

@@ -22,7 +22,7 @@ POISSON, CONVDIFF, EULER, NS = 0, 1, 2, 3
 STEADY, BDF1, BDF2 = 0, 1, 2
 DIRK11, DIRK22, DIRK33, DIRK34 = 1, 2, 3, 4
 FP64, FP32, F32X2 = 0, 1, 2
-PC_NONE, PC_BJACOBI, PC_MLP, PC_MLP_BJ = 0, 1, 2, 3
+PC_NONE, PC_BJACOBI, PC_MLP, PC_MLP_BJ, PC_RB_BJ = 0, 1, 2, 3, 4
 FORCING_FIXED, FORCING_LAST = 0, 1
 BASIS_FP64, BASIS_F32X2 = 0, 1
 JV_AUTO, JV_STAGE = 0, 1
@@ -74,7 +74,7 @@ class _Options(ctypes.Structure):
                 ("max_newton", ctypes.c_int), ("newton_rtol", ctypes.c_double), ("gmres_rtol", ctypes.c_double),
                 ("krylov_precision", ctypes.c_int), ("precond", ctypes.c_int), ("pc_refresh", ctypes.c_int),
                 ("newton_forcing", ctypes.c_int), ("pc_reuse", ctypes.c_int), ("krylov_basis", ctypes.c_int),
-                ("jv_form", ctypes.c_int)]
+                ("jv_form", ctypes.c_int), ("rb_size", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -129,6 +129,8 @@ def lib():
         L.ldg_jvp_after_residual.argtypes = [vp, ctypes.c_int, dp, dp, dp]
         L.ldg_jvp_fd.argtypes = [vp, ctypes.c_int, dp, dp, dp]
         L.ldg_dirk_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, ctypes.c_void_p]
+        L.ldg_rb_set_basis.argtypes = [vp, dp, ctypes.c_int]
+        L.ldg_rb_count.argtypes = [vp]
         L.ldg_wave_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, dp, dp, dp, ctypes.c_void_p]
         L.ldg_diag_blocks.argtypes = [vp, ctypes.c_int, dp, dp]
@@ -205,7 +207,8 @@ class LDG:
     The keyword options mirror ``ldg_options`` in ``include/ldg.h``: solver sizes and
     tolerances, ``krylov_precision`` (FP64, FP32 or F32X2 Krylov J.v; FP32 preconditioner
     with FP32),
-    ``precond`` (none, block-Jacobi, learned), ``pc_refresh``, and three solve policies
+    ``precond`` (none, block-Jacobi, learned, reduced basis + block-Jacobi), ``rb_size``,
+    ``pc_refresh``, and three solve policies
     that default to their plain form: ``newton_forcing`` (FORCING_LAST: a Newton step's
     linear solve stops at what the Newton tolerance still needs), ``pc_reuse`` (the
     block-Jacobi blocks are built every pc_reuse solve calls) and ``krylov_basis``
@@ -217,7 +220,7 @@ class LDG:
                  max_restarts: int = 50, max_newton: int = 20, newton_rtol: float = 1e-8,
                  gmres_rtol: float = 1e-3, krylov_precision: int = 0, precond: int = 0, pc_refresh: int = 0,
                  newton_forcing: int = 0, pc_reuse: int = 1, krylov_basis: int = 0, jv_form: int = 0,
-                 stream=None):
+                 rb_size: int = 0, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("LDG needs a CUDA device (no CPU fallback)")
@@ -230,7 +233,7 @@ class LDG:
         mo = _Model(model, case, len(self._mu),
                     self._mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(self._mu) else None)
         op = _Options(nq1, gmres_m, max_restarts, max_newton, newton_rtol, gmres_rtol, krylov_precision, precond,
-                      pc_refresh, newton_forcing, pc_reuse, krylov_basis, jv_form)
+                      pc_refresh, newton_forcing, pc_reuse, krylov_basis, jv_form, rb_size)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -327,6 +330,16 @@ class LDG:
         if check:
             self._check(rc)
         return rep.as_dict()
+
+    def rb_set_basis(self, W):
+        """Replace the reduced basis of PC_RB_BJ by the rows of W ([k][n_dof] CUDA tensor)."""
+        k = 0 if W is None else int(W.shape[0])
+        ptr = None if k == 0 else _ptr(W, k * self.n_dof, "W")
+        self._check(lib().ldg_rb_set_basis(self._h, ptr, k))
+
+    def rb_count(self) -> int:
+        """Vectors in the reduced basis now."""
+        return int(lib().ldg_rb_count(self._h))
 
     def jvp_fd(self, u, v, order: int = 1, out=None):
         """Finite-difference J.v (order 1 forward, 2 central) from two FP64 residuals."""
@@ -582,7 +595,7 @@ class Batch:
                            mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if len(mu) else None)
         pa = (ctypes.c_int * n)(*[int(p) for p in ps])
         op = _Options(nq1, gmres_m, max_restarts, max_newton, newton_rtol, gmres_rtol, krylov_precision, precond, 0,
-                      newton_forcing, pc_reuse, krylov_basis, jv_form)
+                      newton_forcing, pc_reuse, krylov_basis, jv_form, 0)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
