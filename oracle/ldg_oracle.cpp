@@ -664,10 +664,13 @@ struct Problem {
   std::vector<double> radd;   // optional constant added to the residual ([E][ncu][npe])
   std::string msg;
 
-  // Curved quadrilaterals: x(xi) = sum_a xgeo[K][a] l_a(xi), the degree-pg Lagrange
-  // interpolant through (pg+1)^2 equispaced reference points (first axis fastest).
+  // Curved elements: x(xi) = sum_a xgeo[K][a] l_a(xi), the degree-pg Lagrange interpolant
+  // through the equispaced reference points of degree pg: (pg+1)^2 on quadrilaterals
+  // (first axis fastest), (pg+1)(pg+2)/2 on triangles (the node order of a degree-pg
+  // triangle, whose basis gref evaluates).
   int pg = 0;
-  std::vector<double> xgeo;           // [E][(pg+1)^2][2]
+  std::vector<double> xgeo;           // [E][points][2]
+  Ref gref;                           // curved triangles: the degree-pg triangle basis
   std::vector<unsigned char> bc;      // [E][nf]: 1 marks a wall face, 0 a data face
   bool curved() const { return pg > 0; }
   bool wall(int64_t K, int f) const {
@@ -699,6 +702,22 @@ struct Problem {
   }
   // curved map: x and J[d][k] = d x_d / d xi_k at xi
   void curved_map(int64_t K, const double* xi, double* x, double J[2][2]) const {
+    if (ref.type == TRI) {
+      const int np = gref.npe;
+      std::vector<double> phi(np), dphi(2 * np);
+      gref.basis(xi, phi.data(), dphi.data());
+      x[0] = x[1] = 0;
+      J[0][0] = J[0][1] = J[1][0] = J[1][1] = 0;
+      for (int a = 0; a < np; ++a) {
+        const double* X = &xgeo[((size_t)K * np + a) * 2];
+        for (int d = 0; d < 2; ++d) {
+          x[d] += X[d] * phi[a];
+          J[d][0] += X[d] * dphi[2 * a];
+          J[d][1] += X[d] * dphi[2 * a + 1];
+        }
+      }
+      return;
+    }
     double l0[16], d0[16], l1[16], d1[16];
     lagr(xi[0], l0, d0);
     lagr(xi[1], l1, d1);
@@ -746,6 +765,19 @@ struct Problem {
       sJ = F.sJ;
       return;
     }
+    if (ref.type == TRI) {
+      // the face runs from its vertex A to B (counter-clockwise), parameter s in [-1, 1]:
+      // tangent t = J d xi / ds, sJ = |t|, outward normal = t turned clockwise
+      static const double V[3][2] = {{-1, -1}, {1, -1}, {-1, 1}};
+      const int A = ref.fverts[f][0], B = ref.fverts[f][1];
+      const double dxi[2] = {0.5 * (V[B][0] - V[A][0]), 0.5 * (V[B][1] - V[A][1])};
+      double x[2], J[2][2];
+      curved_map(K, xi, x, J);
+      const double t0 = J[0][0] * dxi[0] + J[0][1] * dxi[1], t1 = J[1][0] * dxi[0] + J[1][1] * dxi[1];
+      sJ = std::sqrt(t0 * t0 + t1 * t1);
+      n[0] = t1 / sJ; n[1] = -t0 / sJ; n[2] = 0;
+      return;
+    }
     // n sJ = +-det J J^{-T} e_axis (Nanson), + on the face xi_axis = +1
     double Ji[9], det;
     jac(K, xi, Ji, det);
@@ -765,8 +797,11 @@ struct Problem {
     if (!curved()) return;
     // Damped Newton iteration on x(xi) = x (step halved while the misfit grows), from
     // the corner-based affine guess, then from the reference centre and the face
-    // centres; the first root found inside the reference square is taken.
-    const double starts[6][2] = {{xi[0], xi[1]}, {0, 0}, {-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    // centres; the first root found inside the reference element is taken.
+    const bool tri = ref.type == TRI;
+    const double sq[6][2] = {{xi[0], xi[1]}, {0, 0}, {-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    const double tr[6][2] = {{xi[0], xi[1]}, {-1.0 / 3, -1.0 / 3}, {0, -1}, {0, 0}, {-1, 0}, {-0.5, -0.5}};
+    const double (*starts)[2] = tri ? tr : sq;
     for (int st = 0; st < 6; ++st) {
       double z[2] = {starts[st][0], starts[st][1]};
       double y[2], J[2][2];
@@ -790,8 +825,9 @@ struct Problem {
         res = rn;
         if (step < 1e-15) break;
       }
-      if (std::fabs(z[0]) <= 1 + 1e-9 && std::fabs(z[1]) <= 1 + 1e-9 &&
-          res <= 1e-12 * (1 + std::fabs(x[0]) + std::fabs(x[1]))) {
+      const bool inside = tri ? (z[0] >= -1 - 1e-9 && z[1] >= -1 - 1e-9 && z[0] + z[1] <= 1e-9)
+                              : (std::fabs(z[0]) <= 1 + 1e-9 && std::fabs(z[1]) <= 1 + 1e-9);
+      if (inside && res <= 1e-12 * (1 + std::fabs(x[0]) + std::fabs(x[1]))) {
         xi[0] = z[0]; xi[1] = z[1];
         return;
       }
@@ -806,9 +842,14 @@ bool setup(Problem& P, int etype, int p, int nq1, int64_t E, const double* xyz, 
   P.err.init(etype, p, p + 3);
   P.E = E;
   if (pg > 0) {
-    if (etype != QUAD || !xgeo || pg > 15) { P.msg = "oracle: curved elements are quadrilaterals of degree <= 15"; return false; }
+    if ((etype != QUAD && etype != TRI) || !xgeo || pg > 15) {
+      P.msg = "oracle: curved elements are quadrilaterals or triangles of degree <= 15";
+      return false;
+    }
     P.pg = pg;
-    P.xgeo.assign(xgeo, xgeo + (size_t)E * (pg + 1) * (pg + 1) * 2);
+    const size_t npts = etype == TRI ? (size_t)(pg + 1) * (pg + 2) / 2 : (size_t)(pg + 1) * (pg + 1);
+    P.xgeo.assign(xgeo, xgeo + (size_t)E * npts * 2);
+    if (etype == TRI) P.gref.init(TRI, pg, 2);
   }
   if (bc) P.bc.assign(bc, bc + (size_t)E * P.ref.nf);
   const int nd = P.ref.nd, nv = P.ref.nv, nf = P.ref.nf;
@@ -1231,7 +1272,7 @@ void* orc_create(int etype, int p, int nq1, int64_t E, const double* xyz, const 
   return orc_create_curved(etype, p, nq1, E, xyz, vid, model, cas, nmu, mu, 0, nullptr, nullptr);
 }
 
-// pg > 0: curved quadrilaterals with map points xgeo [E][(pg+1)^2][2]; bc [E][nf]
+// pg > 0: curved quadrilaterals (map points xgeo [E][(pg+1)^2][2]) or triangles ([E][(pg+1)(pg+2)/2][2]); bc [E][nf]
 // (optional) marks wall faces with 1.
 void* orc_create_curved(int etype, int p, int nq1, int64_t E, const double* xyz, const int64_t* vid,
                         int model, int cas, int nmu, const double* mu, int pg, const double* xgeo,

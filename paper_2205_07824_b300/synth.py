@@ -15,12 +15,14 @@ Mesh convention
 * Vertex order: quadrilaterals and hexahedra list their vertices in
   lexicographic (tensor) order, x fastest; triangles counter-clockwise.
 
-Curved quadrilaterals additionally carry
+Curved elements additionally carry
 * ``pg``   the degree of the element map, and
-* ``xgeo`` float64 ``[E][(pg+1)^2][2]``: the physical positions of the
-  (pg+1)^2 equispaced reference points (-1 + 2a/pg, -1 + 2b/pg), a fastest;
-  the element map is their degree-pg Lagrange interpolant. Shared edges are
-  images of the same points, so neighbouring maps agree along them.
+* ``xgeo`` float64 ``[E][(pg+1)^2][2]`` (quadrilaterals): the physical positions of the
+  (pg+1)^2 equispaced reference points (-1 + 2a/pg, -1 + 2b/pg), a fastest; or
+  ``[E][(pg+1)(pg+2)/2][2]`` (triangles): the equispaced points (-1 + 2i/pg,
+  -1 + 2j/pg), i + j <= pg, row by row (j outer); the element map is their
+  degree-pg Lagrange interpolant. Shared edges are images of the same points,
+  so neighbouring maps agree along them.
 * ``bc``   uint8 ``[E][4]``: kind of each boundary face, 1 = solid wall,
   0 = data (Dirichlet or far field); ignored on interior faces.
 """
@@ -41,8 +43,8 @@ class Mesh:
     xyz: np.ndarray      # [E][nv][nd] float64
     vid: np.ndarray      # [E][nv] int64
     name: str = ""
-    pg: int = 0                       # curved quadrilaterals: degree of the element map
-    xgeo: np.ndarray | None = None    # [E][(pg+1)^2][2] map points
+    pg: int = 0                       # curved elements: degree of the element map
+    xgeo: np.ndarray | None = None    # [E][points][2] map points
     bc: np.ndarray | None = None      # [E][4] uint8 boundary kinds
 
     @property
@@ -142,6 +144,37 @@ def tri_square(n: int, lo=(0.0, 0.0), hi=(1.0, 1.0), periodic=(False, False),
     if affine is not None:
         xyz = xyz @ np.asarray(affine, dtype=np.float64).T
     return Mesh(TRI, xyz, ids, f"tri{n}x{n}")
+
+
+def tri_annulus(n_r: int, n_t: int, pg: int, r0: float = 0.5, r1: float = 1.0) -> Mesh:
+    """The annulus r0 <= r <= r1 as curved triangles of map degree pg: the (rho, theta)
+    parameter grid of n_r layers by n_t sectors (theta periodic), each cell split along its
+    diagonal into two triangles that are counter-clockwise in (rho, theta) and hence in
+    the plane, each mapped by (rho, theta) -> (rho cos theta, rho sin theta) at its
+    degree-pg lattice points. Shared edges are images of the same parameter points, so
+    neighbouring maps agree along them. 2 n_r n_t elements; the corners' coordinates are
+    the mapped vertices (no unwrapping: the seam's positions coincide)."""
+    G = lambda P: np.stack([P[..., 0] * np.cos(P[..., 1]), P[..., 0] * np.sin(P[..., 1])], -1)
+    vid = _grid_ids((n_r, n_t), (False, True))
+    lat = [(i, j) for j in range(pg + 1) for i in range(pg + 1 - j)]   # the degree-pg node order
+    E = 2 * n_r * n_t
+    xyz = np.empty((E, 3, 2))
+    ids = np.empty((E, 3), dtype=np.int64)
+    xgeo = np.empty((E, len(lat), 2))
+    par = lambda i, j: np.array([r0 + (r1 - r0) * i / n_r, 2.0 * np.pi * j / n_t])
+    e = 0
+    for j in range(n_t):
+        for i in range(n_r):
+            a, b, c, d = (i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)
+            for tri in ((a, b, c), (a, c, d)):
+                P = [par(*v) for v in tri]
+                for v in range(3):
+                    xyz[e, v] = G(P[v])
+                    ids[e, v] = vid(*tri[v])
+                pts = np.array([P[0] + (li / pg) * (P[1] - P[0]) + (lj / pg) * (P[2] - P[0]) for li, lj in lat])
+                xgeo[e] = G(pts)
+                e += 1
+    return Mesh(TRI, xyz, ids, f"tri_annulus{n_r}x{n_t}", pg=pg, xgeo=xgeo)
 
 
 def tri_unstructured(n: int, seed: int = 0, jitter: float = 0.25) -> Mesh:

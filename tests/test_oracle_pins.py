@@ -978,3 +978,47 @@ def test_reduced_basis_preconditioner_on_the_whole_space_is_the_inverse():
     V = np.random.default_rng(2).standard_normal((16, 16))
     x = np.random.default_rng(3).standard_normal(16)
     assert np.linalg.norm(rbpc.rb_apply(J, Binv, V, x) - np.linalg.solve(J, x)) <= 1e-10 * np.linalg.norm(x)
+
+
+# ---------------------------------------------------------- curved triangles (Section 4.2)
+def test_curved_triangle_maps_reproduce_the_annulus_area():
+    """sum_ij M_ij of the isoparametric triangles of the annulus 0.5 <= r <= 1: with
+    straight sides (map degree 1) exactly the area of the inscribed polygonal annulus,
+    n_t (r1^2 - r0^2) sin(2 pi / n_t) / 2; with degree 2 and 3 maps it approaches
+    pi (r1^2 - r0^2) at order 4 (a map point out of order or a wrong map Jacobian breaks
+    both)."""
+    def area(n, pg):
+        m = synth.tri_annulus(n, 4 * n, pg)
+        o = oracle.Oracle(m, max(pg, 1), oracle.POISSON, oracle.CASE_LINEAR, (1.0, 1.0))
+        return o.mass(np.ones(o.ndof)).sum()
+    n = 4
+    assert abs(area(n, 1) - 4 * n * 0.5 * 0.75 * math.sin(2 * math.pi / (4 * n))) < 1e-13
+    ex = math.pi * 0.75
+    for pg in (2, 3):
+        e1, e2 = abs(area(4, pg) - ex), abs(area(8, pg) - ex)
+        assert math.log2(e1 / e2) > 3.5, (pg, e1, e2)
+
+
+@pytest.mark.parametrize("pg,p", [(1, 1), (2, 2), (2, 3), (3, 3)])
+def test_curved_triangle_patch_test(pg, p):
+    """A linear exact solution (no source) is reproduced on curved triangles whenever the
+    map degree is at most p: the metric terms w det J dxi/dx and the face normals n sJ are
+    polynomial in the reference coordinates and the quadrature integrates them exactly, so
+    R(u) vanishes to rounding. A normal turned the wrong way or a transposed Jacobian fails it."""
+    m = synth.tri_annulus(2, 8, pg)
+    o = oracle.Oracle(m, p, oracle.POISSON, oracle.CASE_LINEAR, (1.0, 1.0), nq1=p + pg + 1)
+    u = o.interpolate(0.0)
+    assert np.abs(o.residual(u)).max() < 1e-12
+
+
+def test_curved_triangle_poisson_converges_on_the_annulus():
+    """Poisson with u = sin(pi x) sin(pi y) on the annulus, p = 2 with degree-2 maps: the
+    L2 error of u falls at order about p + 1 under refinement (2 x 8 -> 4 x 16)."""
+    errs = []
+    for n in (2, 4):
+        m = synth.tri_annulus(n, 4 * n, 2)
+        o = oracle.Oracle(m, 2, oracle.POISSON, oracle.CASE_SINSIN, (1.0, 1.0))
+        u, rc, _ = o.newton(np.zeros(o.ndof), newton_rtol=1e-12, gmres_rtol=1e-12, m=60, max_gmres=5000)
+        assert rc == 0
+        errs.append(o.l2_error(u)[0])
+    assert math.log2(errs[0] / errs[1]) > 2.6, errs
