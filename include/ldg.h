@@ -34,7 +34,7 @@ typedef struct ldg_ctx ldg_ctx;
 
 /* element shapes: triangles and tetrahedra (equispaced Lagrange nodes, collapsed
  * Gauss rules), quadrilaterals and hexahedra (tensor Gauss-Lobatto-Legendre nodes);
- * affine elements, and curved quadrilaterals (geom_order > 0 below). Tetrahedra
+ * affine elements, and curved quadrilaterals and triangles (geom_order > 0 below). Tetrahedra
  * (Section 4.1's Poisson study) carry the diffusion models, p = 1..3. */
 enum { LDG_TRI = 0, LDG_QUAD = 1, LDG_HEX = 2, LDG_TET = 3 };
 
@@ -80,8 +80,12 @@ enum { LDG_STEADY = 0, LDG_BDF1 = 1, LDG_BDF2 = 2 };
  *
  * Curved quadrilaterals (geom_order = pg > 0): element K's map is the degree-pg
  * Lagrange interpolant of the points xgeo [n_elem][(pg+1)^2][2] (host) placed at
- * the equispaced reference points (-1 + 2a/pg, -1 + 2b/pg), a fastest; its corner
- * points must equal xyz, and neighbouring maps must agree along shared edges
+ * the equispaced reference points (-1 + 2a/pg, -1 + 2b/pg), a fastest. Curved
+ * triangles: the points xgeo [n_elem][(pg+1)(pg+2)/2][2] at the lattice points
+ * (-1 + 2a/pg, -1 + 2b/pg), a + b <= pg, numbered b outer, a inner (the element's own
+ * node order at degree pg). Poisson and convection-diffusion only, p = 1..4 with
+ * p + 2 points (nq1) per direction. Either way the corner points must equal xyz, and
+ * neighbouring maps must agree along shared edges
  * (checked at the face quadrature points: LDG_ERR_MESH otherwise). The geometry
  * is sampled at the quadrature points once, at creation (metrics, normals and
  * the element mass matrices, whose inverses the q-stage applies). geom_order = 0
@@ -432,7 +436,7 @@ int ldg_interpolate(ldg_ctx* ctx, double t, double* u_dev);
  * (the projected initial or exact field beside Section 4.1's error study):
  * u_K = M_K^{-1} (phi, u_exact)_K per element, with integrals by a Gauss rule of
  * p + 3 points per direction (collapsed on simplices). u_dev: n_dof doubles,
- * written. Affine elements only: curved quadrilaterals return LDG_ERR_UNSUPPORTED.
+ * written. Affine elements only: curved elements return LDG_ERR_UNSUPPORTED.
  * The first call builds the rule (a few host arrays and p + 3-point tables on the
  * device, plus 4 n_elem + 2 doubles of error partials). */
 int ldg_project(ldg_ctx* ctx, double t, double* u_dev);
@@ -444,7 +448,7 @@ int ldg_project(ldg_ctx* ctx, double t, double* u_dev);
  * integrated by the rule of ldg_project (a zero denominator counts as 1). u_dev is a
  * device vector; err_u and err_q (may be NULL) are host doubles, written after the
  * call has synchronised the context's stream. Overwrites the context's q scratch.
- * Affine elements only (LDG_ERR_UNSUPPORTED for curved quadrilaterals). */
+ * Affine elements only (LDG_ERR_UNSUPPORTED for curved elements). */
 int ldg_l2_error(ldg_ctx* ctx, const double* u_dev, double t, double* err_u, double* err_q);
 
 /* GMRES(m) on J(u) x = b from x = 0 (classical Gram-Schmidt with one

@@ -501,7 +501,11 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
       }
       vshift += vmax + 1;
       inst.insert(inst.end(), (size_t)M.n_elem, seg);
-      if (pg > 0) xgeo.insert(xgeo.end(), M.xgeo, M.xgeo + (size_t)M.n_elem * (pg + 1) * (pg + 1) * 2);
+      if (pg > 0) {
+        // map points per element: (pg+1)^2 on quadrilaterals, (pg+1)(pg+2)/2 on triangles
+        const size_t np = g.etype == LDG_TRI ? (size_t)(pg + 1) * (pg + 2) / 2 : (size_t)(pg + 1) * (pg + 1);
+        xgeo.insert(xgeo.end(), M.xgeo, M.xgeo + (size_t)M.n_elem * np * 2);
+      }
       if (any_bc) {
         if (M.bc) bc.insert(bc.end(), M.bc, M.bc + (size_t)M.n_elem * nfc);
         else bc.insert(bc.end(), (size_t)M.n_elem * nfc, (unsigned char)0);

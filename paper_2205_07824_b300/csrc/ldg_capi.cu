@@ -37,10 +37,10 @@ void register_all(std::vector<KernelSet>& reg) {
   register_tri_t<Tile1>(reg); register_quad_t<Tile1>(reg); register_hex_t<Tile1>(reg); register_ns_t<Tile1>(reg);
   register_tri_t<Tile2>(reg); register_quad_t<Tile2>(reg); register_hex_t<Tile2>(reg); register_ns_t<Tile2>(reg);
   register_tri_t<Tile3>(reg); register_quad_t<Tile3>(reg); register_hex_t<Tile3>(reg); register_ns_t<Tile3>(reg);
-  // tetrahedra and curved quadrilaterals: two tile shapes
+  // tetrahedra and curved elements: two tile shapes
   register_tet_t<Tile0>(reg); register_tet_t<Tile1>(reg);
-  register_curved_scalar_t<Tile0>(reg); register_curved_gas_t<Tile0>(reg);
-  register_curved_scalar_t<Tile1>(reg); register_curved_gas_t<Tile1>(reg);
+  register_curved_scalar_t<Tile0>(reg); register_curved_gas_t<Tile0>(reg); register_curved_tri_t<Tile0>(reg);
+  register_curved_scalar_t<Tile1>(reg); register_curved_gas_t<Tile1>(reg); register_curved_tri_t<Tile1>(reg);
 }
 std::atomic<long long>& launch_counter() {
   static std::atomic<long long> n{0};
@@ -1280,8 +1280,8 @@ int autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms) {
   const int prec = ctx->opt.krylov_precision == LDG_FP32 ? LDG_FP32 : LDG_FP64;
   int eb = 0;
   while ((int64_t(1) << eb) < ctx->E) ++eb;
-  // (curved elements are keyed apart as element type 3)
-  const auto key = std::make_tuple(ctx->pg > 0 ? 3 : ctx->etype, ctx->p, ctx->nq, ctx->model, prec, eb);
+  // (curved elements are keyed apart from the affine ones of the same element type)
+  const auto key = std::make_tuple(ctx->etype + (ctx->pg > 0 ? 8 : 0), ctx->p, ctx->nq, ctx->model, prec, eb);
   if (best_ms) *best_ms = -1.0;
   if (!force) {
     auto it = cache.find(key);
@@ -1426,7 +1426,10 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   const bool gas = ctx->model == LDG_EULER || ctx->model == LDG_NS;
   if (gas && ctx->dim != 2) { ldg_destroy(ctx); return LDG_ERR_UNSUPPORTED; }
   ctx->pg = mesh->geom_order > 0 ? mesh->geom_order : 0;
-  if (ctx->pg > 0 && (ctx->etype != LDG_QUAD || !mesh->xgeo)) { ldg_destroy(ctx); return LDG_ERR_UNSUPPORTED; }
+  if (ctx->pg > 0 && ((ctx->etype != LDG_QUAD && ctx->etype != LDG_TRI) || !mesh->xgeo)) {
+    ldg_destroy(ctx);
+    return LDG_ERR_UNSUPPORTED;
+  }
   ctx->ncu = gas ? 4 : 1;
   ldg_options o{};
   if (opts) o = *opts;
@@ -1528,8 +1531,8 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   }
   // the same on triangles and tetrahedra, whose stage kernels integrate exactly with at
   // least p + 2 collapsed points per direction
-  if ((ctx->etype == LDG_TRI || ctx->etype == LDG_TET) && (ctx->model == LDG_POISSON || ctx->model == LDG_CONVDIFF) &&
-      o.nq1 >= p + 2 && o.jv_form != LDG_JV_STAGE) {
+  if ((ctx->etype == LDG_TRI || ctx->etype == LDG_TET) && ctx->pg == 0 &&
+      (ctx->model == LDG_POISSON || ctx->model == LDG_CONVDIFF) && o.nq1 >= p + 2 && o.jv_form != LDG_JV_STAGE) {
     const bool conv = ctx->model == LDG_CONVDIFF;
     ctx->lin64 = lin_simplex_launcher(ctx->etype, p, conv, 0);
     ctx->lin32 = lin_simplex_launcher(ctx->etype, p, conv, 1);

@@ -27,7 +27,7 @@ struct ldg_ctx {
   unsigned char* d_nbf = nullptr;
   unsigned char* d_perm = nullptr;
   double* d_xn = nullptr;      // reference node coordinates [npe][dim]
-  // curved quadrilaterals (pg > 0): per-point geometry records (see CurvedPrep)
+  // curved elements (pg > 0): per-point geometry records (see CurvedPrep)
   int pg = 0;
   double* d_cgeo = nullptr;
   float* d_cgeof = nullptr;

@@ -521,6 +521,13 @@ template <int P_, int NQ_> struct TriEl {
   }
 };
 
+// Curved triangle: the triangle's reference operators with per-point geometry (the
+// element map has its own degree; its metrics are sampled at the collapsed Gauss
+// points on the host).
+template <int P_, int NQ_> struct CurvedTriEl : TriEl<P_, NQ_> {
+  static constexpr bool CURVED = true;
+};
+
 // Tetrahedron with equispaced nodes (i, j, k), i + j + k <= P, numbered k outer, then
 // j, then i; vertices V0 = (-1,-1,-1), V1 = (1,-1,-1), V2 = (-1,1,-1), V3 = (-1,-1,1);
 // face f lies opposite vertex f, with vertices (A, B, C) = (1,2,3), (0,2,3), (0,1,3),

@@ -656,8 +656,26 @@ void lagr_equi(int m, double t, double* l, double* dl) {
     dl[a] = der / den;
   }
 }
-// curved quadrilateral map: x and J[d][k] = d x_d / d xi_k at xi
-void curved_point(int pg, const double* X, const double* xi, double* x, double J[2][2]) {
+// map points per element: (pg+1)^2 on quadrilaterals, (pg+1)(pg+2)/2 on triangles
+int curved_points(int etype, int pg) { return etype == E_TRI ? (pg + 1) * (pg + 2) / 2 : (pg + 1) * (pg + 1); }
+
+// curved element map (quadrilateral or triangle): x and J[d][k] = d x_d / d xi_k at xi
+void curved_point(int etype, int pg, const double* X, const double* xi, double* x, double J[2][2]) {
+  if (etype == E_TRI) {
+    // the degree-pg equispaced Lagrange basis of the triangle (tri_basis) at xi
+    const int np = curved_points(E_TRI, pg);
+    std::vector<double> phi(np), dr(np), ds(np);
+    tri_basis(pg, xi[0], xi[1], phi.data(), dr.data(), ds.data());
+    x[0] = x[1] = 0.0;
+    J[0][0] = J[0][1] = J[1][0] = J[1][1] = 0.0;
+    for (int a = 0; a < np; ++a)
+      for (int d = 0; d < 2; ++d) {
+        x[d] += X[a * 2 + d] * phi[a];
+        J[d][0] += X[a * 2 + d] * dr[a];
+        J[d][1] += X[a * 2 + d] * ds[a];
+      }
+    return;
+  }
   double l0[16], d0[16], l1[16], d1[16];
   lagr_equi(pg, xi[0], l0, d0);
   lagr_equi(pg, xi[1], l1, d1);
@@ -675,11 +693,81 @@ void curved_point(int pg, const double* X, const double* xi, double* x, double J
 }
 }  // namespace
 
+// Curved triangles: the same records at the collapsed Gauss points of the reference
+// triangle; the face frame from the tangent t = J d xi / ds of face f (vertex f to f + 1,
+// counter-clockwise): sJ = |t|, outward normal = t turned clockwise.
+bool prepare_curved_tri(const RefOps& R, int64_t E, int pg, const double* xgeo, CurvedPrep& out, std::string& err) {
+  const int npe = R.npe, nqv = R.nqv, nf = R.nf, nfq = R.nfq;
+  std::vector<double> gx, gw;
+  gauss_legendre(R.nq, gx, gw);
+  const double* B = R.blob.data();                    // B[nqv][npe]
+  const double* qw = B + 3 * (size_t)nqv * npe;       // reference weights
+  const double* qx = qw + nqv;                        // [nqv][2] reference points
+  out.rec = nqv * 5 + nf * nfq * 3;
+  out.xrec = nqv * 2 + nf * nfq * 2;
+  out.geo.assign((size_t)E * out.rec, 0.0);
+  out.x.assign((size_t)E * out.xrec, 0.0);
+  out.minv.assign((size_t)E * npe * npe, 0.0);
+  out.xnode.assign((size_t)E * npe * 2, 0.0);
+  std::vector<double> rn;
+  ref_nodes(R, rn);
+  const size_t mstride = (size_t)curved_points(E_TRI, pg) * 2;
+  static const double V[3][2] = {{-1, -1}, {1, -1}, {-1, 1}};
+  std::vector<double> M(npe * npe), Mi;
+  for (int64_t e = 0; e < E; ++e) {
+    const double* X = xgeo + e * mstride;
+    double* g = &out.geo[(size_t)e * out.rec];
+    double* xo = &out.x[(size_t)e * out.xrec];
+    std::fill(M.begin(), M.end(), 0.0);
+    for (int q = 0; q < nqv; ++q) {
+      double x[2], J[2][2];
+      curved_point(E_TRI, pg, X, &qx[2 * q], x, J);
+      const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      if (!(det > 0.0)) { err = "curved element " + std::to_string(e) + " has a non-positive Jacobian"; return false; }
+      const double w = qw[q] * det;
+      g[q * 5 + 0] = qw[q] * J[1][1];
+      g[q * 5 + 1] = -qw[q] * J[0][1];
+      g[q * 5 + 2] = -qw[q] * J[1][0];
+      g[q * 5 + 3] = qw[q] * J[0][0];
+      g[q * 5 + 4] = w;
+      xo[q * 2] = x[0];
+      xo[q * 2 + 1] = x[1];
+      for (int i = 0; i < npe; ++i)
+        for (int j = 0; j < npe; ++j) M[i * npe + j] += w * B[q * npe + i] * B[q * npe + j];
+    }
+    for (int n = 0; n < npe; ++n) {
+      double J[2][2];
+      curved_point(E_TRI, pg, X, &rn[n * 2], &out.xnode[((size_t)e * npe + n) * 2], J);
+    }
+    if (!invert(M, npe, Mi)) { err = "singular element mass matrix"; return false; }
+    std::copy(Mi.begin(), Mi.end(), out.minv.begin() + (size_t)e * npe * npe);
+    for (int f = 0; f < nf; ++f) {
+      const int a = f, b = (f + 1) % 3;
+      const double dxi[2] = {0.5 * (V[b][0] - V[a][0]), 0.5 * (V[b][1] - V[a][1])};
+      for (int k = 0; k < nfq; ++k) {
+        double xi[3], x[2], J[2][2];
+        ref_face_point(R, f, k, xi);
+        curved_point(E_TRI, pg, X, xi, x, J);
+        const double t0 = J[0][0] * dxi[0] + J[0][1] * dxi[1], t1 = J[1][0] * dxi[0] + J[1][1] * dxi[1];
+        const double sj = std::sqrt(t0 * t0 + t1 * t1);
+        double* fr = g + nqv * 5 + (f * nfq + k) * 3;
+        fr[0] = t1 / sj;
+        fr[1] = -t0 / sj;
+        fr[2] = gw[k] * sj;
+        xo[nqv * 2 + (f * nfq + k) * 2] = x[0];
+        xo[nqv * 2 + (f * nfq + k) * 2 + 1] = x[1];
+      }
+    }
+  }
+  return true;
+}
+
 bool prepare_curved(const RefOps& R, int64_t E, int pg, const double* xgeo, CurvedPrep& out, std::string& err) {
-  if (R.etype != E_QUAD || pg < 1 || pg > 15 || !xgeo) {
-    err = "curved elements are quadrilaterals with map degree 1..15";
+  if ((R.etype != E_QUAD && R.etype != E_TRI) || pg < 1 || pg > 15 || !xgeo) {
+    err = "curved elements are quadrilaterals or triangles with map degree 1..15";
     return false;
   }
+  if (R.etype == E_TRI) return prepare_curved_tri(R, E, pg, xgeo, out, err);
   const int nq = R.nq, n1 = R.p + 1, npe = R.npe, nqv = R.nqv, nf = R.nf, nfq = R.nfq;
   std::vector<double> gx, gw;
   gauss_legendre(nq, gx, gw);
@@ -704,7 +792,7 @@ bool prepare_curved(const RefOps& R, int64_t E, int pg, const double* xgeo, Curv
         const int q = q0 + nq * q1;
         const double xi[2] = {gx[q0], gx[q1]};
         double x[2], J[2][2];
-        curved_point(pg, X, xi, x, J);
+        curved_point(E_QUAD, pg, X, xi, x, J);
         const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
         if (!(det > 0.0)) { err = "curved element " + std::to_string(e) + " has a non-positive Jacobian"; return false; }
         const double w = gw[q0] * gw[q1] * det;
@@ -723,7 +811,7 @@ bool prepare_curved(const RefOps& R, int64_t E, int pg, const double* xgeo, Curv
       }
     for (int n = 0; n < npe; ++n) {
       double J[2][2];
-      curved_point(pg, X, &rn[n * 2], &out.xnode[((size_t)e * npe + n) * 2], J);
+      curved_point(E_QUAD, pg, X, &rn[n * 2], &out.xnode[((size_t)e * npe + n) * 2], J);
     }
     if (!invert(M, npe, Mi)) { err = "singular element mass matrix"; return false; }
     std::copy(Mi.begin(), Mi.end(), out.minv.begin() + (size_t)e * npe * npe);
@@ -731,7 +819,7 @@ bool prepare_curved(const RefOps& R, int64_t E, int pg, const double* xgeo, Curv
       for (int k = 0; k < nfq; ++k) {
         double xi[3], x[2], J[2][2];
         ref_face_point(R, f, k, xi);
-        curved_point(pg, X, xi, x, J);
+        curved_point(E_QUAD, pg, X, xi, x, J);
         const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
         if (!(det > 0.0)) { err = "curved element " + std::to_string(e) + " has a non-positive Jacobian"; return false; }
         // Nanson: n sJ = +-det J J^{-T} e_axis = +- (row `axis` of the cofactor matrix)
@@ -880,7 +968,7 @@ bool prepare_mesh(const RefOps& R, int64_t E, const double* xyz, const int64_t* 
       const double* xi = &fref[((size_t)f * nmatch + k) * 3];
       if (pg > 0) {
         double x[2], J[2][2];
-        curved_point(pg, xgeo + (size_t)e * (pg + 1) * (pg + 1) * 2, xi, x, J);
+        curved_point(R.etype, pg, xgeo + (size_t)e * curved_points(R.etype, pg) * 2, xi, x, J);
         for (int d = 0; d < 2; ++d) P[k * 3 + d] = x[d] + (shift ? shift[d] : 0.0);
         continue;
       }

@@ -52,7 +52,7 @@ struct KArgs {
   const double* radd;         // [E][NCU][NPE]     constant added to R in MODE_R (DIRK stage terms), or null
   void* out;                  // [E][NCU][NPE] residual / J.v, or [E][NCU][DIM][NPE] q
   const double* geo;          // [E][GEO] per-element affine geometry
-  const double* cgeo;         // curved quadrilaterals: [E][CGeo::SIZE] per-point metrics (FP64) ...
+  const double* cgeo;         // curved elements: [E][CGeo::SIZE] per-point metrics (FP64) ...
   const float* cgeof;         // ... and their FP32 copy
   const double* cx;           // curved: [E][CGeo::XSIZE] physical coordinates of volume and face points
   const double* minv;         // curved: [E][NPE][NPE] inverse element mass matrices (FP64) ...
@@ -102,7 +102,7 @@ template <int DIM> struct Geo {
   static constexpr int size(int nf) { return FACE + nf * (DIM + 1); }
 };
 
-// Per-element record of a curved quadrilateral: at each volume point the metric
+// Per-element record of a curved element: at each volume point the metric
 // w det J d xi_k / d x_d (k, d) and w det J; at each face point the outward unit
 // normal and w sJ (reference face weight folded in). Physical coordinates of the
 // volume and face points are a separate record (read only for data).
@@ -537,9 +537,10 @@ __global__ void __launch_bounds__(256) k_qstage(KArgs a) {
 }
 
 // ============================================================ curved q-stage
-// Curved quadrilaterals: the weak form of Eq. 1a with the element's own mass matrix,
+// Curved elements: the weak form of Eq. 1a with the element's own mass matrix,
 //   (M_K q_d)_i = sum_q w det J u_h d_d phi_i - sum_f sum_k w sJ uhat n_d phi_i,
-// the volume term by the sum-factorised transposed derivatives of the per-point
+// the volume term by the transposed reference derivatives (sum-factorised on
+// quadrilaterals) of the per-point
 // metric times u_h, the face term by lifting -uhat n_d w per point, then q_d by the
 // precomputed inverse M_K^{-1} (the strong form no longer equals it when the
 // quadrature is inexact on curved elements).

@@ -23,7 +23,7 @@ struct KernelSet {
   int etype, p, nq, model;
   int tile;           // tile variant (Tile0 .. Tile3)
   bool linear;        // linear model: J.v is the homogeneous operator (MODE_HOM)
-  bool curved;        // curved quadrilaterals (per-point geometry records)
+  bool curved;        // curved elements (per-point geometry records)
   StageFn qstage;     // FP64 compute. Models with q: MODE_R / MODE_HOM; null otherwise
   StageFn residual;   // FP64 compute. MODE_R / MODE_HOM (linear models) / MODE_JV (nonlinear models)
   StageFn qstage32;   // FP32 compute, MODE_HOM (models with q); null otherwise
@@ -159,6 +159,7 @@ template <class TL> void register_ns_t(std::vector<KernelSet>& reg);
 template <class TL> void register_curved_scalar_t(std::vector<KernelSet>& reg);
 template <class TL> void register_tet_t(std::vector<KernelSet>& reg);
 template <class TL> void register_curved_gas_t(std::vector<KernelSet>& reg);
+template <class TL> void register_curved_tri_t(std::vector<KernelSet>& reg);
 void register_all(std::vector<KernelSet>& reg);
 
 // Nodal J.v kernels of the linear models on affine quadrilaterals / hexahedra
