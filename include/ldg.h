@@ -128,11 +128,14 @@ typedef struct {
   int max_newton;       /* Newton iterations (default 20) */
   double newton_rtol;   /* stop when ||R(u_k)|| <= newton_rtol ||R(u_0)|| (default 1e-8) */
   double gmres_rtol;    /* linear solve: ||b - J x|| <= gmres_rtol ||b|| (default 1e-3) */
-  int krylov_precision; /* LDG_FP64 (default), LDG_FP32 or LDG_F32X2: arithmetic of the J.v
-                           inside GMRES, and of the preconditioner for LDG_FP32 (LDG_F32X2 builds
-                           FP64 blocks). Newton residuals, Arnoldi, Givens and all vectors stay
-                           FP64. LDG_F32X2 is accepted where the float-pair J.v exists (see
-                           LDG_F32X2 below); ldg_create returns LDG_ERR_ARG elsewhere. */
+  int krylov_precision; /* LDG_FP64 (default), LDG_FP32, LDG_F32X2, LDG_TC_BF16X3 or LDG_TC_BF16:
+                           arithmetic of the J.v inside GMRES, and of the preconditioner for
+                           LDG_FP32 and the tensor-core forms (FP32 blocks; LDG_F32X2 builds FP64
+                           blocks). Newton residuals, Arnoldi, Givens and all vectors stay FP64,
+                           so the outer iteration refines a low-precision J.v to the FP64
+                           tolerance. LDG_F32X2 and the tensor-core forms are accepted where their
+                           kernels exist (see the precision constants below); ldg_create returns
+                           LDG_ERR_ARG elsewhere. */
   int precond;          /* LDG_PC_NONE (default), LDG_PC_BJACOBI, LDG_PC_MLP, LDG_PC_MLP_BJ or
                            LDG_PC_RB_BJ (flexible right preconditioning; a linear solve with a
                            learned one that misses its tolerance within two restart cycles is
@@ -177,7 +180,17 @@ typedef struct {
  * nodal J.v kernels serve: the linear models (Poisson, convection-diffusion) on affine
  * quadrilaterals and hexahedra with p + 1 Gauss points per direction, and on triangles
  * and tetrahedra with at least p + 2. */
-enum { LDG_FP64 = 0, LDG_FP32 = 1, LDG_F32X2 = 2 };
+/* LDG_TC_BF16X3 and LDG_TC_BF16 put the interpolation, integration, lift and mass
+ * contractions of the residual of Eq. 1b on the tensor cores (tcgen05, FP32 accumulation
+ * in tensor memory), written as dense GEMMs over all nodes and points of an element with
+ * the elements' (element, component) pairs as rows; the pointwise Euler and Lax-Friedrichs
+ * fluxes with their tangents are FP32 dual numbers on the CUDA cores. LDG_TC_BF16X3 splits
+ * every operand into BF16 hi and lo parts and sums three products (about 1e-5 relative),
+ * LDG_TC_BF16 keeps one BF16 product (about 1e-2). Inputs and output FP64 in memory. They
+ * exist for the Euler model on affine quadrilaterals, p = 1..4, with p + 2 Gauss points
+ * per direction (the vortex and cylinder cases; the wall and far-field faces included).
+ * A tensor-core wait that runs out (about a second) leaves the affected outputs NaN. */
+enum { LDG_FP64 = 0, LDG_FP32 = 1, LDG_F32X2 = 2, LDG_TC_BF16X3 = 3, LDG_TC_BF16 = 4 };
 enum { LDG_PC_NONE = 0, LDG_PC_BJACOBI = 1, LDG_PC_MLP = 2, LDG_PC_MLP_BJ = 3, LDG_PC_RB_BJ = 4 };
 enum { LDG_FORCING_FIXED = 0, LDG_FORCING_LAST = 1 };
 enum { LDG_BASIS_FP64 = 0, LDG_BASIS_F32X2 = 1 };
@@ -251,13 +264,14 @@ int ldg_residual(ldg_ctx* ctx, const double* u_dev, double* r_dev);
  * for linear ones. */
 int ldg_jvp(ldg_ctx* ctx, const double* u_dev, const double* v_dev, double* jv_dev);
 
-/* J.v in a chosen arithmetic: LDG_FP64 (same as ldg_jvp), LDG_FP32 or LDG_F32X2 (inputs
- * and output FP64 in memory; see the precision constants). LDG_ERR_ARG for LDG_F32X2 on
- * a context without the float-pair kernels. */
+/* J.v in a chosen arithmetic: LDG_FP64 (same as ldg_jvp), LDG_FP32, LDG_F32X2,
+ * LDG_TC_BF16X3 or LDG_TC_BF16 (inputs and output FP64 in memory; see the precision
+ * constants). LDG_ERR_ARG for LDG_F32X2 or a tensor-core form on a context without
+ * those kernels. */
 int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u_dev, const double* v_dev, double* jv_dev);
 
-/* Names the kernels that form this context's J.v in `precision` (LDG_FP64 / LDG_FP32 /
- * LDG_F32X2; "" where that arithmetic has no kernels) and the case they serve, e.g.
+/* Names the kernels that form this context's J.v in `precision` (any of the precision
+ * constants; "" where that arithmetic has no kernels) and the case they serve, e.g.
  * "k_lin_q + k_lin_r [hex p=4 nq=5 convdiff fp64, ...]".
  * The string stays valid until the calling thread's next call of this function. */
 const char* ldg_jv_describe(const ldg_ctx* ctx, int precision);

@@ -136,12 +136,14 @@ class Oracle:
         vid = _c(mesh.vid, np.int64)
         mu = _c(np.asarray(mu, dtype=np.float64).reshape(-1))
         pg = int(getattr(mesh, "pg", 0) or 0)
-        if pg > 0:
-            xgeo = _c(mesh.xgeo)
-            bc = None if mesh.bc is None else np.ascontiguousarray(mesh.bc, dtype=np.uint8)
+        # wall marks (gas models) apply to affine and curved meshes alike
+        bc = None if getattr(mesh, "bc", None) is None else np.ascontiguousarray(mesh.bc, dtype=np.uint8)
+        if pg > 0 or bc is not None:
+            xgeo = _c(mesh.xgeo) if pg > 0 else None
             self._keep = (xgeo, bc)
             self._h = lib().orc_create_curved(mesh.etype, p, nq1, mesh.n_elem, _p(xyz), vid.ctypes.data_as(_I64),
-                                              model, case, len(mu), _p(mu) if len(mu) else None, pg, _p(xgeo),
+                                              model, case, len(mu), _p(mu) if len(mu) else None, pg,
+                                              _p(xgeo) if pg > 0 else None,
                                               None if bc is None else bc.ctypes.data)
         else:
             self._h = lib().orc_create(mesh.etype, p, nq1, mesh.n_elem, _p(xyz), vid.ctypes.data_as(_I64),

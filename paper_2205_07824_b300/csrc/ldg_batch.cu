@@ -440,6 +440,8 @@ int build_batch(ldg_batch* b, int n_inst, const ldg_mesh_desc* meshes, const int
   if (o.max_newton <= 0) o.max_newton = 20;
   if (o.newton_rtol <= 0) o.newton_rtol = 1e-8;
   if (o.gmres_rtol <= 0) o.gmres_rtol = 1e-3;
+  if (o.krylov_precision == LDG_TC_BF16X3 || o.krylov_precision == LDG_TC_BF16)
+    return bfail(b, LDG_ERR_UNSUPPORTED, "the batched solver takes LDG_FP64, LDG_FP32 or LDG_F32X2");
   if (o.krylov_precision != LDG_FP32 && o.krylov_precision != LDG_F32X2) o.krylov_precision = LDG_FP64;
   if (o.precond != LDG_PC_BJACOBI) o.precond = LDG_PC_NONE;
   if (o.newton_forcing != LDG_FORCING_LAST) o.newton_forcing = LDG_FORCING_FIXED;
@@ -667,6 +669,7 @@ int ldg_batch_residual(ldg_batch* b, const double* u, double* r) {
 
 int ldg_batch_jvp(ldg_batch* b, int precision, const double* u, const double* v, double* jv) {
   if (!b || b->groups.empty() || !u || !v || !jv) return LDG_ERR_ARG;
+  if (precision == LDG_TC_BF16X3 || precision == LDG_TC_BF16) return LDG_ERR_UNSUPPORTED;
   return emit_jv(b, b->stream, u, v, jv, precision == LDG_FP32 || precision == LDG_F32X2 ? precision : LDG_FP64,
                  nullptr, false);
 }

@@ -214,6 +214,16 @@ int do_residual(ldg_ctx* ctx, const double* u, double* r) {
 }
 
 int jvp_args(ldg_ctx* ctx, KArgs a, const double* u, const double* v, double* jv, int prec, bool q_ready) {
+  if (prec == LDG_TC_BF16X3 || prec == LDG_TC_BF16) {
+    if (!ctx->tcjv)
+      return fail(ctx, LDG_ERR_ARG,
+                  "the tensor-core J.v exists for the Euler model on affine quadrilaterals, p = 1..4, with p + 2 "
+                  "Gauss points");
+    KArgs b = a;
+    b.u = u; b.v = v; b.out = jv;
+    CK(ctx->tcjv(b, ctx->d_tcimg, prec == LDG_TC_BF16X3 ? 3 : 1, ctx->d_tcerr, ctx->stream));
+    return LDG_OK;
+  }
   if (prec == LDG_F32X2) {
     // float-pair arithmetic: the nodal kernels of the linear models only
     if (!(ctx->ks->linear && ctx->ks->qstage && ctx->linff))
@@ -388,8 +398,9 @@ int do_blocks(ldg_ctx* ctx, const double* u, int prec, double* blocks) {
 // elimination in shared memory), else FP64.
 int do_pc_setup(ldg_ctx* ctx, const double* u) {
   int rc;
-  // (a float-pair Krylov J.v takes FP64 blocks)
-  const int prec = ctx->opt.krylov_precision == LDG_FP32 ? LDG_FP32 : LDG_FP64;
+  // (a float-pair Krylov J.v takes FP64 blocks, the tensor-core forms FP32 ones)
+  const int kp = ctx->opt.krylov_precision;
+  const int prec = kp == LDG_FP32 || kp == LDG_TC_BF16X3 || kp == LDG_TC_BF16 ? LDG_FP32 : LDG_FP64;
   ctx->pc_kappa = ctx->mp.kappa;
   ctx->pc_a0dt = ctx->a0dt;
   // the block storage must exist before its address is handed to the extraction
@@ -1277,7 +1288,8 @@ const KernelSet* find_set(const ldg_ctx* ctx, int tile) {
 
 int autotune(ldg_ctx* ctx, int force, int* tile, double* best_ms) {
   static std::map<std::tuple<int, int, int, int, int, int>, int> cache;
-  const int prec = ctx->opt.krylov_precision == LDG_FP32 ? LDG_FP32 : LDG_FP64;
+  const int kp = ctx->opt.krylov_precision;
+  const int prec = kp == LDG_FP32 || kp == LDG_TC_BF16X3 || kp == LDG_TC_BF16 ? LDG_FP32 : LDG_FP64;
   int eb = 0;
   while ((int64_t(1) << eb) < ctx->E) ++eb;
   // (curved elements are keyed apart from the affine ones of the same element type)
@@ -1373,6 +1385,7 @@ int ldg_destroy(ldg_ctx* ctx) {
   cudaFree(ctx->d_xn); cudaFree(ctx->d_q); cudaFree(ctx->d_dq); cudaFree(ctx->d_hist);
   cudaFree(ctx->d_q32); cudaFree(ctx->d_u32);
   cudaFree(ctx->d_rbW); cudaFree(ctx->d_rbJW); cudaFree(ctx->d_rbS); cudaFree(ctx->d_rbC);
+  cudaFree(ctx->d_tcimg); cudaFree(ctx->d_tcerr);
   cudaFree(ctx->d_cgeo); cudaFree(ctx->d_cgeof); cudaFree(ctx->d_cx); cudaFree(ctx->d_minv); cudaFree(ctx->d_minvf);
   cudaFree(ctx->d_xnode); cudaFree(ctx->d_fd); cudaFree(ctx->d_radd); cudaFree(ctx->d_dirk);
   cudaFree(ctx->d_wave);
@@ -1440,7 +1453,9 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if (o.max_newton <= 0) o.max_newton = 20;
   if (o.newton_rtol <= 0) o.newton_rtol = 1e-8;
   if (o.gmres_rtol <= 0) o.gmres_rtol = 1e-3;
-  if (o.krylov_precision != LDG_FP32 && o.krylov_precision != LDG_F32X2) o.krylov_precision = LDG_FP64;
+  if (o.krylov_precision != LDG_FP32 && o.krylov_precision != LDG_F32X2 && o.krylov_precision != LDG_TC_BF16X3 &&
+      o.krylov_precision != LDG_TC_BF16)
+    o.krylov_precision = LDG_FP64;
   if (o.precond != LDG_PC_BJACOBI && o.precond != LDG_PC_MLP && o.precond != LDG_PC_MLP_BJ &&
       o.precond != LDG_PC_RB_BJ)
     o.precond = LDG_PC_NONE;
@@ -1547,6 +1562,22 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
     } else {
       ctx->lin64 = ctx->lin32 = ctx->linff = nullptr;
     }
+  }
+  // the tensor-core Euler J.v: affine quadrilaterals with p + 2 Gauss points
+  if (ctx->model == LDG_EULER && ctx->etype == LDG_QUAD && ctx->pg == 0 && o.nq1 == p + 2 && tcjv_launcher(p)) {
+    std::vector<unsigned char> img;
+    if (build_tcjv_image(p, ref.blob, img)) {
+      ctx->tcjv = tcjv_launcher(p);
+      CK(cudaMalloc(&ctx->d_tcimg, img.size()));
+      CK(cudaMemcpy(ctx->d_tcimg, img.data(), img.size(), cudaMemcpyHostToDevice));
+      CK(cudaMalloc(&ctx->d_tcerr, sizeof(int)));
+      CK(cudaMemset(ctx->d_tcerr, 0, sizeof(int)));
+    }
+  }
+  if ((o.krylov_precision == LDG_TC_BF16X3 || o.krylov_precision == LDG_TC_BF16) && !ctx->tcjv) {
+    ctx->err = "krylov_precision LDG_TC_BF16X3 / LDG_TC_BF16 needs the tensor-core J.v: the Euler model on affine "
+               "quadrilaterals, p = 1..4, with p + 2 Gauss points";
+    return LDG_ERR_ARG;
   }
   if (o.krylov_precision == LDG_F32X2 && !(ctx->ks->linear && ctx->linff)) {
     ctx->err = "krylov_precision LDG_F32X2 needs the float-pair nodal J.v kernels: a linear model on affine "
@@ -1713,7 +1744,8 @@ int ldg_jvp(ldg_ctx* ctx, const double* u, const double* v, double* jv) {
 }
 
 static bool jv_precision_ok(int precision) {
-  return precision == LDG_FP64 || precision == LDG_FP32 || precision == LDG_F32X2;
+  return precision == LDG_FP64 || precision == LDG_FP32 || precision == LDG_F32X2 || precision == LDG_TC_BF16X3 ||
+         precision == LDG_TC_BF16;
 }
 
 int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u, const double* v, double* jv) {
@@ -1739,6 +1771,12 @@ const char* ldg_jv_describe(const ldg_ctx* ctx, int precision) {
                      " nq=" + std::to_string(ctx->nq) + " " + md[ctx->model];
   if (precision == LDG_F32X2) {
     s = ctx->ks->linear && ctx->linff ? nodal_names(ctx, precision) + what + " f32x2, q scratch f32x2]" : "";
+    return s.c_str();
+  }
+  if (precision == LDG_TC_BF16X3 || precision == LDG_TC_BF16) {
+    s = ctx->tcjv ? "k_euler_jv_tc [" + what + (precision == LDG_TC_BF16X3 ? " bf16x3" : " bf16") +
+                        " tcgen05 contractions, fp32 pointwise, 32 elements per CTA]"
+                  : "";
     return s.c_str();
   }
   what += f32 ? " fp32" : " fp64";

@@ -57,6 +57,10 @@ struct ldg_ctx {
   // nodal J.v kernels of linear models on affine tensor elements (null when not applicable)
   ldg::LinFn lin64 = nullptr, lin32 = nullptr;
   ldg::LinFn linff = nullptr;
+  // Euler on affine quadrilaterals: the tensor-core J.v and its constant operand image
+  ldg::TcJvFn tcjv = nullptr;
+  unsigned char* d_tcimg = nullptr;
+  int* d_tcerr = nullptr;
   std::vector<double> h_lops;    // host copy of the nodal kernels' FP64 operator blob   // the same in (hi, lo) float-pair arithmetic (LDG_F32X2)
   double* d_lops = nullptr;
   float* d_lopsf = nullptr;

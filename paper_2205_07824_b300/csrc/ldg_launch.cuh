@@ -172,4 +172,14 @@ LinFn lin_simplex_launcher(int etype, int p, bool conv, int prec);
 // The same hexahedron / quadrilateral kernels in double-float arithmetic (ldg_df.cuh).
 LinFn lin_df_launcher(int dim, int p, bool conv);
 
+// Euler J.v with the element contractions on the tensor cores (ldg_tcjv.cu), affine
+// quadrilaterals with p + 2 Gauss points: passes 3 (BF16 hi/lo splits) or 1 (BF16).
+// img: the constant operand image of build_tcjv_image on the device; err: set to 1
+// when a wait timed out (the affected outputs are NaN).
+typedef cudaError_t (*TcJvFn)(const KArgs& a, const unsigned char* img, int passes, int* err, cudaStream_t s);
+TcJvFn tcjv_launcher(int p);   // p = 1..4, else null
+// The constant operands (basis, derivative, face, lift and mass matrices as BF16 hi/lo
+// images in the kernel's shared-memory layout) from the tensor element's FP64 blob.
+bool build_tcjv_image(int p, const std::vector<double>& blob, std::vector<unsigned char>& img);
+
 }  // namespace ldg

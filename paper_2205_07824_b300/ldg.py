@@ -22,6 +22,8 @@ POISSON, CONVDIFF, EULER, NS = 0, 1, 2, 3
 STEADY, BDF1, BDF2 = 0, 1, 2
 DIRK11, DIRK22, DIRK33, DIRK34 = 1, 2, 3, 4
 FP64, FP32, F32X2 = 0, 1, 2
+# tensor-core contractions (Euler on affine quadrilaterals): BF16 hi/lo splits, or one BF16 product
+TC_BF16X3, TC_BF16 = 3, 4
 PC_NONE, PC_BJACOBI, PC_MLP, PC_MLP_BJ, PC_RB_BJ = 0, 1, 2, 3, 4
 FORCING_FIXED, FORCING_LAST = 0, 1
 BASIS_FP64, BASIS_F32X2 = 0, 1
@@ -205,8 +207,8 @@ class LDG:
     """One LDG operator (mesh, order p, model) resident on the current CUDA device.
 
     The keyword options mirror ``ldg_options`` in ``include/ldg.h``: solver sizes and
-    tolerances, ``krylov_precision`` (FP64, FP32 or F32X2 Krylov J.v; FP32 preconditioner
-    with FP32),
+    tolerances, ``krylov_precision`` (FP64, FP32, F32X2, TC_BF16X3 or TC_BF16 Krylov J.v;
+    FP32 preconditioner with FP32 and the tensor-core forms),
     ``precond`` (none, block-Jacobi, learned, reduced basis + block-Jacobi), ``rb_size``,
     ``pc_refresh``, and three solve policies
     that default to their plain form: ``newton_forcing`` (FORCING_LAST: a Newton step's
@@ -304,8 +306,10 @@ class LDG:
         return out
 
     def jvp_prec(self, precision: int, u, v, out=None):
-        """J.v in FP64 (precision FP64), FP32 (FP32) or (hi, lo) float-pair arithmetic
-        (F32X2, emulated FP64; the nodal kernels of the linear models only); FP64 in memory."""
+        """J.v in FP64 (precision FP64), FP32 (FP32), (hi, lo) float-pair arithmetic
+        (F32X2, emulated FP64; the nodal kernels of the linear models only) or with the
+        contractions on the tensor cores (TC_BF16X3 / TC_BF16; Euler on affine
+        quadrilaterals); FP64 in memory."""
         out = self.empty() if out is None else out
         n = self.n_dof
         self._check(lib().ldg_jvp_prec(self._h, precision, _ptr(u, n, "u"), _ptr(v, n, "v"), _ptr(out, n, "out")))

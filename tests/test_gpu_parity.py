@@ -60,6 +60,16 @@ def test_euler_far_field_boundary():
     _run_r_jv(mesh, 2, oracle.EULER, oracle.CASE_VORTEX)
 
 
+def test_euler_walls_on_affine_quadrilaterals():
+    """Periodic in x, no-slip walls at y = 0 and y = 10 (wall marks on affine elements)."""
+    mesh = synth.quad_box((6, 5), hi=(10.0, 10.0), periodic=(True, False))
+    bc = np.zeros((mesh.n_elem, 4), dtype=np.uint8)
+    bc[:6, 2] = 1
+    bc[-6:, 3] = 1
+    mesh.bc = bc
+    _run_r_jv(mesh, 3, oracle.EULER, oracle.CASE_VORTEX)
+
+
 @pytest.mark.parametrize("p,n", [(1, (3, 4, 5)), (2, (3, 4, 5)), (3, (3, 3, 4)), (4, (3, 3, 3)), (5, (2, 2, 3)),
                                  (6, (2, 2, 2))])
 def test_hexes_convdiff(p, n):
