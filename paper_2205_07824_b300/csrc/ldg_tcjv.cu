@@ -52,11 +52,11 @@ __host__ __device__ inline uint32_t sw_off(int rows, int r, int k) {
                     (k & 7) * 2);
 }
 
-template <int P> struct TcShape {
+template <int P, int TH = 256> struct TcShape {
   static constexpr int N1 = P + 1, NQ = P + 2, NPE = N1 * N1, NQV = NQ * NQ, NFP = 4 * NQ;
   // padded GEMM extents (multiples of 16): nodes, volume points, face points, face nodes
   static constexpr int KN = r16(NPE), NV = r16(NQV), NFPp = r16(NFP), KF = r16(4 * N1), NN = KN;
-  static constexpr int EPC = 32, ROWS = 128, THREADS = 256;
+  static constexpr int EPC = 32, ROWS = 128, THREADS = TH;
   // constant operands, rows x K with the hi part in the first K / 2 columns and the lo
   // part in the second (host-built images, concatenated in this order)
   static constexpr int B_BV = op_bytes(NV, 2 * KN), B_BF = op_bytes(NFPp, 2 * KN), B_BN = op_bytes(NFPp, 2 * KF),
@@ -93,7 +93,7 @@ template <int P> struct TcShape {
   static constexpr int SMEM_RAW = S_END + 1024;   // + alignment slack of the dynamic buffer
   static constexpr int SMEM_CAP = (228 * 1024) / (MAXC + 1) - 3 * 1024;
   static constexpr int SMEM = SMEM_RAW > SMEM_CAP ? SMEM_RAW : SMEM_CAP;
-  static constexpr int MINB = SMEM <= 110 * 1024 ? 2 : 1;   // register budget for 2 CTAs per SM
+  static constexpr int MINB = TH == 256 && SMEM <= 110 * 1024 ? 2 : 1;   // register budget for 2 CTAs per SM
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -148,9 +148,9 @@ __device__ __forceinline__ void mma_split(uint32_t d, const unsigned char* A, in
 }
 
 
-template <int P, int PASSES>
-__global__ void __launch_bounds__(256, TcShape<P>::MINB) k_euler_jv_tc(KArgs a, const unsigned char* __restrict__ cimg, int* err) {
-  typedef TcShape<P> T;
+template <int P, int PASSES, int TH>
+__global__ void __launch_bounds__(TH, TcShape<P, TH>::MINB) k_euler_jv_tc(KArgs a, const unsigned char* __restrict__ cimg, int* err) {
+  typedef TcShape<P, TH> T;
   typedef TensorEl<2, P, P + 2> EL;
   typedef Dual<float> S;
   constexpr int GEO = Geo<2>::FACE + 4 * 3;   // doubles per element record
@@ -310,14 +310,15 @@ __global__ void __launch_bounds__(256, TcShape<P>::MINB) k_euler_jv_tc(KArgs a, 
   // through the warp's transpose tile, after which lane (e, c) holds all components at
   // the points c and c + 4 of the eight.
   if (ok_a) {
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, group = warp >> 2;
+    constexpr int NGROUPS = T::THREADS / 128;
     const int c = lane & 3, el = lane >> 2, e = quarter * 8 + el;
     const uint32_t lrow = tmem + ((uint32_t)(quarter * 32) << 16);
     constexpr int NVC = T::NV / 16, NFC = T::NFPp / 16;
     float* wt = (float*)(sm + T::S_W) + warp * (T::B_W / 4) + el * T::WSTR;
     const bool live = e < ne;
     const float* ge = gs + e * T::GEOF;
-    for (int ch = half; ch < NVC + NFC; ch += 2) {   // warp-uniform
+    for (int ch = group; ch < NVC + NFC; ch += NGROUPS) {   // warp-uniform
       if (ch < NVC) {
         const int q0 = ch * 16;
         float U[16], V[16];
@@ -553,25 +554,28 @@ template <int P> void build_image(const std::vector<double>& blob, std::vector<u
     }
 }
 
+template <int P, int PASSES, int TH> cudaError_t launch_th(const KArgs& a, const unsigned char* img, int* err, unsigned grid,
+                                                          cudaStream_t s) {
+  typedef TcShape<P, TH> T;
+  static const cudaError_t attr = cudaFuncSetAttribute(k_euler_jv_tc<P, PASSES, TH>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
+  if (attr != cudaSuccess) return attr;
+  k_euler_jv_tc<P, PASSES, TH><<<grid, TH, T::SMEM, s>>>(a, img, err);
+  return cudaGetLastError();
+}
+
+// A grid of at most two CTAs per SM runs one 512-thread CTA per SM; larger grids run
+// 256-thread CTAs, two per SM where shared memory and tensor memory allow.
 template <int P, int PASSES> cudaError_t launch(const KArgs& a, const unsigned char* img, int* err, cudaStream_t s) {
-  typedef TcShape<P> T;
-  // a grid of at most two CTAs per SM is spread one per SM: its launch asks for more
-  // than half an SM's shared memory
-  constexpr int SMEM_ONE = 116 * 1024 > T::SMEM ? 116 * 1024 : T::SMEM;
-  static const cudaError_t attr = cudaFuncSetAttribute(k_euler_jv_tc<P, PASSES>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_ONE);
   static const int n_sm = [] {
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return 148;
     return n;
   }();
-  if (attr != cudaSuccess) return attr;
   if (a.E <= 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((a.E + T::EPC - 1) / T::EPC);
-  const int smem = (int)grid <= 2 * n_sm ? SMEM_ONE : T::SMEM;
-  k_euler_jv_tc<P, PASSES><<<grid, T::THREADS, smem, s>>>(a, img, err);
-  return cudaGetLastError();
+  const unsigned grid = (unsigned)((a.E + 31) / 32);
+  return (int)grid <= 2 * n_sm ? launch_th<P, PASSES, 512>(a, img, err, grid, s) : launch_th<P, PASSES, 256>(a, img, err, grid, s);
 }
 
 template <int P> cudaError_t launch_p(const KArgs& a, const unsigned char* img, int passes, int* err, cudaStream_t s) {
