@@ -450,7 +450,8 @@ def vortex_solve_summary(args, stream):
     prob = vortex_problem(LDG, mesh, forcing_of(args), 1)
     forms = {}
     sol = {}
-    for name, kp in (("fp32_krylov_bjacobi", 1), ("fp64_bjacobi", 0)):
+    for name, kp in (("fp32_krylov_bjacobi", 1), ("fp64_bjacobi", 0), ("tc_bf16x3_krylov_bjacobi", 3),
+                     ("tc_bf16_krylov_bjacobi", 4)):
         g, u, times, tot, _, t_end, _ = run_mode(prob, kp, 1, steps, 3, flush, stream, kernel_launches)
         forms[name] = {"ms_per_step": sum(times) / steps, "gmres_iters_per_step": tot["gmres"] / steps,
                        "newton_iters_per_step": tot["newton"] / steps}
@@ -475,8 +476,92 @@ def vortex_solve_summary(args, stream):
     forms["speedup_fp32_vs_fp64"] = forms["fp64_bjacobi"]["ms_per_step"] / forms["fp32_krylov_bjacobi"]["ms_per_step"]
     forms["solution_rel_diff"] = float(torch.linalg.norm(sol["fp32_krylov_bjacobi"] - sol["fp64_bjacobi"]) /
                                        torch.linalg.norm(sol["fp64_bjacobi"]))
+    for name in ("tc_bf16x3_krylov_bjacobi", "tc_bf16_krylov_bjacobi"):
+        forms[name]["speedup_vs_fp64_bjacobi"] = forms["fp64_bjacobi"]["ms_per_step"] / forms[name]["ms_per_step"]
+        forms[name]["solution_rel_diff_vs_fp64_bjacobi"] = float(
+            torch.linalg.norm(sol[name] - sol["fp64_bjacobi"]) / torch.linalg.norm(sol["fp64_bjacobi"]))
     forms["workload"] = WORKLOAD
+    forms["jv_kernels"] = vortex_jv_kernels(mesh, sol["fp64_bjacobi"], args)
     return forms
+
+
+# tensor-core MMA flops per element of the Euler J.v at p = 3 (padded GEMM extents, 32
+# elements per CTA): interpolation of u and v (2 x 128 x 32 x 16 x 2), own and neighbour
+# face traces (4 x 128 x 32 x 16 x 2), mass (128 x 16 x 16 x 2), volume integration
+# (128 x 16 x 64 x 2) and lift (128 x 16 x 32 x 2), per CTA / 32, times the passes
+TC_MMA_FLOP_PER_ELEM_P3 = (2 * 128 * 32 * 16 * 2 + 4 * 128 * 32 * 16 * 2 + 128 * 16 * 16 * 2 + 128 * 16 * 64 * 2 +
+                           128 * 16 * 32 * 2) / 32
+
+
+def vortex_jv_kernels(mesh, u, args):
+    """The c2 J.v (64 x 64 quadrilaterals, p = 3, Euler) in every arithmetic: graph-timed
+    kernel time at the state u and a random direction, and each form's error against the
+    FP64 oracle's J.v on the same inputs."""
+    import numpy as np
+    import torch
+    from paper_2205_07824_b300.ldg import LDG, EULER, CASE_VORTEX
+    g = LDG(mesh, P, EULER, CASE_VORTEX, (1.4,), gmres_m=2)
+    g.autotune()
+    v = torch.randn(g.n_dof, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    out = torch.empty_like(v)
+    peaks = _peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1800.0))
+    rows = {}
+    res = {}
+    for name, kp in (("fp64", 0), ("fp32", 1), ("tc_bf16x3", 3), ("tc_bf16", 4)):
+        ms = graph_time_ms(g, lambda: g.jvp_prec(kp, u, v, out), args.jv_reps)
+        g.jvp_prec(kp, u, v, out)
+        res[name] = out.cpu().numpy().copy()
+        rows[name] = {"us": ms * 1e3, "gdofs": g.n_dof / (ms * 1e-3) / 1e9, "kernel": g.jv_kernels(kp)}
+        if kp >= 3:
+            passes = 3 if kp == 3 else 1
+            tf = TC_MMA_FLOP_PER_ELEM_P3 * passes * mesh.n_elem / (ms * 1e-3) / 1e12
+            rows[name]["tensor_tflops"] = tf
+            rows[name]["tensor_frac_of_bf16_peak"] = tf / bf16
+    if not args.no_cpu_baseline:
+        # the FP64 oracle's J.v on the same inputs (rank 0, after the timed regions)
+        import oracle
+        o = oracle.Oracle(mesh, P, oracle.EULER, oracle.CASE_VORTEX, (1.4,))
+        ref = o.jvp(u.cpu().numpy(), v.cpu().numpy())
+        for name in rows:
+            rows[name]["rel_err_vs_fp64_oracle"] = float(np.linalg.norm(res[name] - ref) / np.linalg.norm(ref))
+    rows["timing"] = "CUDA graph of jv_reps back-to-back J.v launches, one replay timed with CUDA events"
+    rows["bf16_peak_source"] = "measured cuBLAS bf16 (burst)" if "bf16_tflops" in peaks else "fallback 1.8 PFLOP/s"
+    del g
+    return rows
+
+
+def run_tc_probe(args):
+    """The Euler J.v (periodic vortex box, p = 3) in FP64, FP32 and with the tensor-core
+    contractions (BF16 hi/lo splits and one BF16 product) on square meshes of the given
+    sides: graph-timed kernel time per launch, one JSON line; also the command a profiler
+    captures the tensor-core kernel under (--tc-sides 256)."""
+    import torch
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, EULER, CASE_VORTEX
+    torch.cuda.set_device(0)
+    peaks = _peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1800.0))
+    table = {}
+    for side in (int(x) for x in args.tc_sides.split(",")):
+        mesh = synth.quad_box(side, hi=(10.0, 10.0), periodic=(True, True))
+        g = LDG(mesh, P, EULER, CASE_VORTEX, (1.4,), gmres_m=2, krylov_precision=1)
+        g.autotune()
+        u = g.interpolate(0.0)
+        v = torch.randn(g.n_dof, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+        out = torch.empty_like(v)
+        row = {"n_dof": int(g.n_dof)}
+        for name, kp in (("fp64", 0), ("fp32", 1), ("tc_bf16x3", 3), ("tc_bf16", 4)):
+            ms = graph_time_ms(g, lambda: g.jvp_prec(kp, u, v, out), args.jv_reps)
+            row[name] = {"us": ms * 1e3, "gdofs": g.n_dof / (ms * 1e-3) / 1e9}
+            if kp >= 3:
+                tf = TC_MMA_FLOP_PER_ELEM_P3 * (3 if kp == 3 else 1) * mesh.n_elem / (ms * 1e-3) / 1e12
+                row[name]["tensor_frac_of_bf16_peak"] = tf / bf16
+        table[f"{side}x{side}"] = row
+        del g
+    print(json.dumps({"workload": "Euler J.v, periodic isentropic-vortex box [0,10]^2, p=3, 5 Gauss points per "
+                                  "direction", "timing": "CUDA graph of jv_reps back-to-back J.v launches, one "
+                                  "replay timed with CUDA events", "table": table}), flush=True)
 
 
 def cylinder_solve_summary(args, stream):
@@ -1287,7 +1372,7 @@ def main():
     ap.add_argument("--precond", default="bjacobi", choices=["none", "bjacobi", "mlp"],
                     help="block-Jacobi: exact element-diagonal blocks, rebuilt once per implicit step; "
                          "mlp: the learned per-element preconditioner trained on the warm-up steps")
-    ap.add_argument("--krylov", default="fp32", choices=["fp64", "fp32", "f32x2"],
+    ap.add_argument("--krylov", default="fp32", choices=["fp64", "fp32", "f32x2", "tc_bf16x3", "tc_bf16"],
                     help="arithmetic of the J.v inside GMRES (Newton residual and Arnoldi stay FP64)")
     ap.add_argument("--forcing", default="last", choices=["fixed", "last"],
                     help="Newton-GMRES workloads (vortex, batch, cylinder): linear tolerance of each Newton "
@@ -1302,7 +1387,7 @@ def main():
                          "graph's WHILE nodes (same kernels; for profilers that do not follow graph nodes)")
     ap.add_argument("--no-solve", action="store_true", help="jv: skip the vortex time-to-1e-8 comparison")
     ap.add_argument("--workload", default="jv",
-                    choices=["jv", "jvprobe", "vortex", "batch", "hex", "tri", "cylinder", "tet", "wave"],
+                    choices=["jv", "jvprobe", "vortex", "batch", "hex", "tri", "cylinder", "tet", "wave", "tcprobe"],
                     help="jv (default): the FP64 J.v of 48^3 p=4 convection-diffusion; jvprobe: its J.v "
                          "applications alone, for profilers; "
                          "vortex: the 64x64 p=3 Euler BDF2 step; batch: 256 parametrised convection-diffusion "
@@ -1310,7 +1395,9 @@ def main():
                          "tri: the same sweep on 131,072 triangles; "
                          "cylinder: Navier-Stokes past a cylinder on 40,000 curved quads, learned + mixed vs "
                          "plain FP64 block-Jacobi; tet: Table 3's Poisson problem on tetrahedra, 1/n = 32, p = 3; "
-                         "wave: DIRK34 steps of the wave model on 48^3 hexahedra, p = 4")
+                         "wave: DIRK34 steps of the wave model on 48^3 hexahedra, p = 4; tcprobe: the Euler J.v "
+                         "in FP64, FP32 and with tensor-core contractions on square vortex meshes")
+    ap.add_argument("--tc-sides", default="64,128,256,512", help="tcprobe: square mesh sides")
     ap.add_argument("--tet-n", type=int, default=32, help="tet: cubes per side (Table 3's 1/n)")
     ap.add_argument("--tet-p", type=int, default=3, help="tet: polynomial order")
     ap.add_argument("--cyl-layers", type=int, default=100, help="cylinder mesh: layers across the domain")
@@ -1353,6 +1440,9 @@ def main():
     if args.workload == "wave":
         run_wave(args)
         return
+    if args.workload == "tcprobe":
+        run_tc_probe(args)
+        return
 
     import numpy as np
     import torch
@@ -1367,7 +1457,7 @@ def main():
     mesh = synth.quad_box(N_SIDE, hi=(10.0, 10.0), periodic=(True, True))
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
-    kprec = 1 if args.krylov == "fp32" else 0
+    kprec = {"fp64": 0, "fp32": 1, "f32x2": 2, "tc_bf16x3": 3, "tc_bf16": 4}[args.krylov]
     pc = {"none": 0, "bjacobi": 1, "mlp": 2}[args.precond]
 
     if world > 1:
@@ -1430,13 +1520,27 @@ def main():
     jv_ms = graph_time_ms(g, lambda: g.jvp_prec(kprec, u, v, jv), args.jv_reps)
     jv64 = g.jvp_prec(0, u, v)
     jv_err = float(torch.linalg.norm(jv - jv64) / torch.linalg.norm(jv64)) if kprec else 0.0
-    fpe = JV_FLOP_PER_ELEM[kprec]
+    if kprec >= 3:
+        # tensor-core J.v: its MMA flops against the measured bf16 peak (the pointwise
+        # fluxes between the MMA phases run on the CUDA cores and bound it)
+        peaks = _peaks()
+        passes = 3 if kprec == 3 else 1
+        bf16 = float(peaks.get("bf16_tflops", 1800.0))
+        achieved = TC_MMA_FLOP_PER_ELEM_P3 * passes * mesh.n_elem / (jv_ms * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "unit": "TFLOP/s", "achieved": achieved, "peak": bf16,
+                    "frac": achieved / bf16, "traffic": None, "kernel": g.jv_kernels(kprec),
+                    "timing": "CUDA graph of jv_reps back-to-back J.v launches, one replay timed with CUDA events",
+                    "launch_ms": jv_ms, "jv_gdofs_kernel": n / (jv_ms * 1e-3) / 1e9,
+                    "mma_flop_per_elem": TC_MMA_FLOP_PER_ELEM_P3 * passes,
+                    "peak_source": "measured cuBLAS bf16 (burst)" if "bf16_tflops" in peaks else "fallback 1.8 PFLOP/s",
+                    "jv_rel_err_vs_fp64": jv_err}
+    fpe = JV_FLOP_PER_ELEM[min(kprec, 1)]
     achieved = fpe * mesh.n_elem / (jv_ms * 1e-3) / 1e12
     peak = FP32_PEAK_TFLOPS if kprec else FP64_PEAK_TFLOPS
     # DRAM bytes per launch of the FP32 kernel (tile 8) from one ncu capture inside the step:
     # the state is L2-resident
     traffic = (1.792e3 + 1.024e3) if kprec else None
-    roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+    roofline = roofline if kprec >= 3 else {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
                 "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (Tile<8>) inside "
                                   "the step; the 6.3 MB of state per launch come from L2" if kprec else None,
@@ -1490,7 +1594,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": gdofs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if kprec == 0 else "f64+f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": {0: "f64", 1: "f64+f32", 3: "f64+bf16x3", 4: "f64+bf16"}[kprec],
+                "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_dof": int(n), "n_elem": int(mesh.n_elem),
                            "value_definition": "J.v applications of the whole solve (Arnoldi, true residual, "
                                                "block extraction) x DOF / timed step time",
