@@ -172,6 +172,18 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
 }
 
 // ----------------------------------------------------------------- residual
+// The face terms need no contraction of their own. Face f of axis k carries sJ (M1 x M1)
+// over its two free axes, which are the axes other than k, so sJ Fhat_f placed at the
+// end nodes of the axis-k lines, beside their C contraction, picks up exactly those two
+// factors from the volume passes that follow:
+//   R = -[M1_z (M1_y X + M1_x Y) + M1_x M1_y Z],
+//   X = C_x g_0 - E_x Fhat_x - M1_x (a0/dt det J v),  Y = C_y g_1 - E_y Fhat_y,
+//   Z = C_z g_2 - E_z Fhat_z     (2-D: R = -(M1_y X + M1_x Y)),
+// E_k Fhat_k placing the two faces of axis k at the nodes i_k = 0 and i_k = p. The
+// fluxes are formed one face node per thread, spread over the whole CTA, and written as
+// the initial values of the X, Y, Z accumulators; the other nodes start at zero. The
+// FP64 pipe issues whole warps, masked lanes included, so every FP64 instruction here is
+// executed by converged warps.
 template <int DIM, int N1, bool CONV, class R, class QT>
 __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<DIM, N1>::NT, R>::value)) k_lin_r(KArgs a) {
   typedef LinShape<DIM, N1> S;
@@ -184,19 +196,18 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   const int ne = min(NE, a.E - e0);
   if (!cta_active(a, e0, ne)) return;
   __shared__ R ops[O::SIZE];
-  __shared__ R Gs[NE][GEO];
   __shared__ R Ak[NE][DIM][DIM + 1];  // g_k = sum_d Ak[k][d] q_d + Ak[k][DIM] v
   __shared__ R FC[NE][NF][DIM + 2];   // per face: kappa/2 sJ n_d, tau sJ, sJ beta.n
-  __shared__ R Gk[NE][DIM][NPE];      // nodal fluxes g_k, later the axis-1 stage (3-D)
-  __shared__ R Tk[NE][DIM][NPE];      // axis-0 stage
-  __shared__ R Hs[NE][NPE];           // a0/dt det J v (time term)
-  __shared__ R FV[NE][NF][NFN];       // own v at the face nodes, later the first face contraction
-  __shared__ R FQ[NE][NF][NFN];       // own q.n at the face nodes, later the second face contraction
-  __shared__ R FF[NE][NF][NFN];       // sJ Fhat at the face nodes
+  __shared__ R DJ[NE];                // a0/dt det J
+  __shared__ unsigned char FK[NE][NF];  // bit 0: the face has a neighbour; bit 1: beta.n >= 0
+  __shared__ R Vs[NE][NPE];           // v
+  __shared__ R Qs[NE][DIM][NPE];      // q
+  __shared__ R Gk[NE][DIM][NPE];      // nodal fluxes g_k, later the axis-2 inputs (3-D)
+  __shared__ R Tk[NE][DIM][NPE];      // X, Y, Z (face fluxes first)
   const int t = threadIdx.x;
   const auto* lo = lin_ops<R>(a);
   for (int i = t; i < O::SIZE; i += NT) ops[i] = R(lo[i]);
-  for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
+  for (int i = t; i < ne; i += NT) DJ[i] = R(a.a0dt * a.geo[(size_t)(e0 + i) * GEO + G::DETJ]);
   for (int i = t; i < ne * DIM; i += NT) {
     // det J Jinv[k][.] (kappa q + beta v): per element kappa det J Jinv[k][d] and det J Jinv[k].beta
     const int el = i / DIM, k = i % DIM;
@@ -222,10 +233,10 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
     }
     FC[el][f][DIM] = R(mp.tau * sj);
     FC[el][f][DIM + 1] = CONV ? R(sj * bn) : R(0);
+    FK[el][f] = (a.nbr[(size_t)(e0 + el) * NF + f] >= 0 ? 1 : 0) | (!CONV || bn >= 0.0 ? 2 : 0);
   }
   const double* v = (const double*)a.u;
   const QT* q = (const QT*)a.q;
-  const R a0dt = R(a.a0dt);
   const bool tterm = a.a0dt != 0.0;
   const int e = t / NPE, n = t - e * NPE;
   const bool own = e < ne;
@@ -234,7 +245,6 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   // the neighbours' v and q at this thread's face items, loaded before the first barrier
   constexpr int NFI = NE * NF * NFN, ROUNDS = (NFI + NT - 1) / NT;
   R vpre[ROUNDS], qpre[ROUNDS][DIM];
-  int hasnb = 0;
 #pragma unroll
   for (int r = 0; r < ROUNDS; ++r) {
     const int it = t + r * NT;
@@ -251,18 +261,27 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
           vpre[r] = R(v[(size_t)nb * NPE + node]);
 #pragma unroll
           for (int d = 0; d < DIM; ++d) qpre[r][d] = R(q[((size_t)nb * DIM + d) * NPE + node]);
-          hasnb |= 1 << r;
         }
       }
     }
   }
   R vn = R(0), qn[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) qn[d] = R(0);
   if (own) {
     vn = R(v[(size_t)(e0 + e) * NPE + n]);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) qn[d] = R(q[((size_t)(e0 + e) * DIM + d) * NPE + n]);
+    Vs[e][n] = vn;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) Qs[e][d][n] = qn[d];
   }
   __syncthreads();
+
+  // ---- phase 0: nodal fluxes g_k; zero X, Y, Z off the faces of their axis; sJ fhat =
+  //   tau sJ (v- - v+) + kappa/2 sJ (q- + q+).n + sJ beta.n v_upwind
+  // at every face node, placed as -sJ fhat into the accumulator of the face's axis
+  // (Dirichlet faces: v+ = 0, q+ = q-, and no inflow)
   if (own) {
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
@@ -270,143 +289,93 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
 #pragma unroll
       for (int d = 0; d < DIM; ++d) s += Ak[e][k][d] * qn[d];
       Gk[e][k][n] = R(s);
-    }
-    if (tterm) Hs[e][n] = R(a0dt * Gs[e][G::DETJ]) * vn;
-    // own v and kappa/2 sJ q.n at the face nodes this node lies on
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const int ax = f >> 1, fix = (f & 1) ? N1 - 1 : 0;
-      if (id[ax] != fix) continue;
-      const int j = lin_face_index<DIM, N1>(ax, id);
-      A s = A(0);
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) s += FC[e][f][d] * qn[d];
-      FV[e][f][j] = vn;
-      FQ[e][f][j] = R(s);
+      if (id[k] != 0 && id[k] != N1 - 1) Tk[e][k][n] = R(0);
     }
   }
-  __syncthreads();
-
-  // ---- phase 1: numerical flux at the face nodes; volume contractions along axis 0
 #pragma unroll
   for (int r = 0; r < ROUNDS; ++r) {
     const int it = t + r * NT;
     if (it >= NFI) break;
     const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
-    // sJ fhat = tau sJ (v- - v+) + kappa/2 sJ (q- + q+).n + sJ beta.n v_upwind
-    // (Dirichlet faces: tau sJ v- + kappa sJ q-.n + sJ beta.n v- on outflow)
-    R fh = R(0);
-    if (el < ne) {
-      const R* fc = FC[el][f];
-      const R vm = FV[el][f][j], qmn = FQ[el][f][j], bs = fc[DIM + 1];
-      if ((hasnb >> r) & 1) {
-        const R vp = vpre[r];
-        A qpn = A(0);
+    if (el >= ne) continue;
+    const int node = lin_face_node<DIM, N1>(f, j);
+    const R* fc = FC[el][f];
+    const int fk = FK[el][f];
+    const bool nb = fk & 1;
+    const R vm = Vs[el][node];
+    A s = A(fc[DIM] * (vm - vpre[r]));
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) qpn += fc[d] * qpre[r][d];
-        fh = fc[DIM] * (vm - vp) + (qmn + R(qpn));
-        if (CONV) fh += bs * (bs >= R(0) ? vm : vp);
-      } else {
-        fh = fc[DIM] * vm + R(2) * qmn;
-        if (CONV && bs >= R(0)) fh += bs * vm;
-      }
+    for (int d = 0; d < DIM; ++d) {
+      const R qm = Qs[el][d][node];
+      s += fc[d] * (qm + (nb ? qpre[r][d] : qm));
     }
-    FF[el][f][j] = fh;
+    if (CONV) s += fc[DIM + 1] * ((fk & 2) ? vm : vpre[r]);
+    Tk[el][f >> 1][node] = -R(s);
   }
+  __syncthreads();
+
+  // ---- phase 1: C along each axis onto the face values, and the time term's M1 along
+  // axis 0
+  if (own) {
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const R* cr = ops + O::C + id[k] * N1;
+      const R* line = &Gk[e][k][n - id[k] * STR[k]];
+      A acc = A(Tk[e][k][n]);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) acc += cr[m] * line[m * STR[k]];
+      if (k == 0 && tterm) {
+        const R* mr = ops + O::M1 + id[0] * N1;
+        const R* vl = &Vs[e][n - id[0]];
+        A h = A(0);
+#pragma unroll
+        for (int m = 0; m < N1; ++m) h += mr[m] * vl[m];
+        acc -= DJ[e] * R(h);
+      }
+      Tk[e][k][n] = R(acc);
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2: M1 along axis 1 of X and Z, along axis 0 of Y
   R rv = R(0);
   if (own) {
-    const R* cr = ops + O::C + id[0] * N1;
-    const R* mr = ops + O::M1 + id[0] * N1;
-    const int b0 = n - id[0];
-    A ta = A(0), tb = A(0), tc = A(0);
-#pragma unroll
-    for (int m = 0; m < N1; ++m) {
-      ta += cr[m] * Gk[e][0][b0 + m];
-      tb += mr[m] * Gk[e][1][b0 + m];
-      if constexpr (DIM == 3) tc += mr[m] * Gk[e][2][b0 + m];
-    }
-    if (tterm) {
-#pragma unroll
-      for (int m = 0; m < N1; ++m) ta -= mr[m] * Hs[e][b0 + m];
-    }
-    Tk[e][0][n] = R(ta);
-    Tk[e][1][n] = R(tb);
-    if constexpr (DIM == 3) Tk[e][2][n] = R(tc);
-  }
-  __syncthreads();
-
-  // ---- phase 2: face mass along the first free axis; volume along axis 1
-  for (int it = t; it < NE * NF * NFN; it += NT) {
-    const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
-    const int t0 = j % N1, rest = j - t0;
-    const R* mr = ops + O::M1 + t0 * N1;
+    const R* m1 = ops + O::M1 + id[1] * N1;
+    const R* m0 = ops + O::M1 + id[0] * N1;
+    const int b1 = n - id[1] * N1, b0 = n - id[0];
     A s = A(0);
 #pragma unroll
-    for (int m = 0; m < N1; ++m) s += mr[m] * FF[el][f][rest + m];
-    FV[el][f][j] = R(s);
-  }
-  if (own) {
-    const R* cr = ops + O::C + id[1] * N1;
-    const R* mr = ops + O::M1 + id[1] * N1;
-    const int b1 = n - id[1] * N1;
+    for (int m = 0; m < N1; ++m) {
+      s += m1[m] * Tk[e][0][b1 + m * N1];
+      s += m0[m] * Tk[e][1][b0 + m];
+    }
     if constexpr (DIM == 2) {
-      A s = A(0);
-#pragma unroll
-      for (int m = 0; m < N1; ++m) {
-        s += mr[m] * Tk[e][0][b1 + m * N1];
-        s += cr[m] * Tk[e][1][b1 + m * N1];
-      }
       rv = -R(s);
     } else {
-      A sa = A(0), sc = A(0);
+      A z = A(0);
 #pragma unroll
-      for (int m = 0; m < N1; ++m) {
-        sa += mr[m] * Tk[e][0][b1 + m * N1];
-        sa += cr[m] * Tk[e][1][b1 + m * N1];
-        sc += mr[m] * Tk[e][2][b1 + m * N1];
-      }
-      Gk[e][0][n] = R(sa);
-      Gk[e][1][n] = R(sc);
+      for (int m = 0; m < N1; ++m) z += m1[m] * Tk[e][2][b1 + m * N1];
+      Gk[e][0][n] = R(s);
+      Gk[e][1][n] = R(z);
     }
   }
-  __syncthreads();
-
-  // ---- phase 3 (3-D): face mass along the second free axis; volume along axis 2
-  R (*FL)[NF][NFN] = FV;   // final face moments (2-D: after the one tangential contraction)
+  // ---- phase 3 (3-D): M1 along axis 2 of M1_y X + M1_x Y, along axis 0 of M1_y Z
   if constexpr (DIM == 3) {
-    for (int it = t; it < NE * NF * NFN; it += NT) {
-      const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
-      const int t0 = j % N1, t1 = j / N1;
-      const R* mr = ops + O::M1 + t1 * N1;
-      A s = A(0);
-#pragma unroll
-      for (int m = 0; m < N1; ++m) s += mr[m] * FV[el][f][t0 + m * N1];
-      FQ[el][f][j] = R(s);
-    }
+    __syncthreads();
     if (own) {
-      const R* cr = ops + O::C + id[2] * N1;
-      const R* mr = ops + O::M1 + id[2] * N1;
-      const int b2 = n - id[2] * N1 * N1;
+      const R* m2 = ops + O::M1 + id[2] * N1;
+      const R* m0 = ops + O::M1 + id[0] * N1;
+      const int b2 = n - id[2] * N1 * N1, b0 = n - id[0];
       A s = A(0);
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
-        s += mr[m] * Gk[e][0][b2 + m * N1 * N1];
-        s += cr[m] * Gk[e][1][b2 + m * N1 * N1];
+        s += m2[m] * Gk[e][0][b2 + m * N1 * N1];
+        s += m0[m] * Gk[e][1][b0 + m];
       }
       rv = -R(s);
     }
-    __syncthreads();
-    FL = FQ;
   }
-
-  // ---- store: volume part plus the face moments of the faces this node lies on
-  if (!own) return;
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    const int ax = f >> 1, fix = (f & 1) ? N1 - 1 : 0;
-    if (id[ax] == fix) rv += FL[e][f][lin_face_index<DIM, N1>(ax, id)];
-  }
-  ((double*)a.out)[(size_t)(e0 + e) * NPE + n] = (double)rv;
+  if (own) ((double*)a.out)[(size_t)(e0 + e) * NPE + n] = (double)rv;
 }
 
 // Both stages of the J.v: v -> q(v) in qbuf (QT), then J v.
