@@ -5,26 +5,26 @@
 
 namespace ldg {
 
-template <int DIM, int N1, bool CONV> LinFn lin_df_pick() {
+template <int DIM, int N1, bool CONV> LinFn lin_df_pick(bool cart) {
   if constexpr (DIM == 3) return &launch_hex<N1, CONV, df, df>;
-  else return &launch_lin<DIM, N1, CONV, df, df>;
+  else return cart ? &launch_lin<DIM, N1, CONV, df, df, true> : &launch_lin<DIM, N1, CONV, df, df, false>;
 }
 
-template <int DIM, bool CONV> LinFn lin_df_by_p(int p) {
+template <int DIM, bool CONV> LinFn lin_df_by_p(int p, bool cart) {
   switch (p) {
-    case 1: return lin_df_pick<DIM, 2, CONV>();
-    case 2: return lin_df_pick<DIM, 3, CONV>();
-    case 3: return lin_df_pick<DIM, 4, CONV>();
-    case 4: return lin_df_pick<DIM, 5, CONV>();
-    case 5: if constexpr (DIM == 3) return lin_df_pick<DIM, 6, CONV>(); else return nullptr;
-    case 6: if constexpr (DIM == 3) return lin_df_pick<DIM, 7, CONV>(); else return nullptr;
+    case 1: return lin_df_pick<DIM, 2, CONV>(cart);
+    case 2: return lin_df_pick<DIM, 3, CONV>(cart);
+    case 3: return lin_df_pick<DIM, 4, CONV>(cart);
+    case 4: return lin_df_pick<DIM, 5, CONV>(cart);
+    case 5: if constexpr (DIM == 3) return lin_df_pick<DIM, 6, CONV>(cart); else return nullptr;
+    case 6: if constexpr (DIM == 3) return lin_df_pick<DIM, 7, CONV>(cart); else return nullptr;
     default: return nullptr;
   }
 }
 
-LinFn lin_df_launcher(int dim, int p, bool conv) {
-  if (dim == 2) return conv ? lin_df_by_p<2, true>(p) : lin_df_by_p<2, false>(p);
-  if (dim == 3) return conv ? lin_df_by_p<3, true>(p) : lin_df_by_p<3, false>(p);
+LinFn lin_df_launcher(int dim, int p, bool conv, bool cart) {
+  if (dim == 2) return conv ? lin_df_by_p<2, true>(p, cart) : lin_df_by_p<2, false>(p, cart);
+  if (dim == 3) return conv ? lin_df_by_p<3, true>(p, cart) : lin_df_by_p<3, false>(p, cart);
   return nullptr;
 }
 

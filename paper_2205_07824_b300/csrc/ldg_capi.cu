@@ -1422,6 +1422,25 @@ int ldg_create(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
 
 namespace ldg {
 namespace impl {
+// Every element is an axis-aligned box: the off-diagonal entries of J^{-1} and the
+// off-axis components of each face normal (face f lies on local axis f / 2) are exactly
+// zero in the geometry records (layout of Geo<DIM>).
+static bool cartesian_elements(const std::vector<double>& geo, int dim, int64_t nelem) {
+  const int nf = 2 * dim, stride = dim * dim + 1 + dim + dim * dim + nf * (dim + 1);
+  const int face = dim * dim + 1 + dim + dim * dim;
+  if (nelem <= 0 || (int64_t)geo.size() < nelem * stride) return false;
+  for (int64_t e = 0; e < nelem; ++e) {
+    const double* g = geo.data() + e * stride;
+    for (int k = 0; k < dim; ++k)
+      for (int d = 0; d < dim; ++d)
+        if (k != d && g[k * dim + d] != 0.0) return false;
+    for (int f = 0; f < nf; ++f)
+      for (int d = 0; d < dim; ++d)
+        if (d != f / 2 && g[face + f * (dim + 1) + d] != 0.0) return false;
+  }
+  return true;
+}
+
 int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_desc* model, const ldg_options* opts,
                void* cuda_stream, bool lean) {
   if (!out || !mesh || !model || !mesh->xyz || !mesh->vid || mesh->n_elem <= 0) return LDG_ERR_ARG;
@@ -1529,9 +1548,10 @@ int create_ctx(ldg_ctx** out, const ldg_mesh_desc* mesh, int p, const ldg_model_
   if ((ctx->etype == LDG_QUAD || ctx->etype == LDG_HEX) && ctx->pg == 0 &&
       (ctx->model == LDG_POISSON || ctx->model == LDG_CONVDIFF) && o.nq1 == p + 1 && o.jv_form != LDG_JV_STAGE) {
     const bool conv = ctx->model == LDG_CONVDIFF;
-    ctx->lin64 = lin_launcher(ctx->dim, p, conv, 0);
-    ctx->lin32 = lin_launcher(ctx->dim, p, conv, 1);
-    ctx->linff = lin_df_launcher(ctx->dim, p, conv);
+    ctx->lin_cart = cartesian_elements(mp_.geo, ctx->dim, ctx->E);
+    ctx->lin64 = lin_launcher(ctx->dim, p, conv, 0, ctx->lin_cart);
+    ctx->lin32 = lin_launcher(ctx->dim, p, conv, 1, ctx->lin_cart);
+    ctx->linff = lin_df_launcher(ctx->dim, p, conv, ctx->lin_cart);
     std::vector<double> lb;
     if (ctx->lin64 && ctx->lin32 && build_lin_ops(p, lb, err)) {
       ctx->h_lops = lb;
@@ -1770,7 +1790,10 @@ const char* ldg_jv_describe(const ldg_ctx* ctx, int precision) {
   std::string what = std::string(el[ctx->etype]) + (ctx->pg ? " curved" : "") + " p=" + std::to_string(ctx->p) +
                      " nq=" + std::to_string(ctx->nq) + " " + md[ctx->model];
   if (precision == LDG_F32X2) {
-    s = ctx->ks->linear && ctx->linff ? nodal_names(ctx, precision) + what + " f32x2, q scratch f32x2]" : "";
+    s = ctx->ks->linear && ctx->linff ? nodal_names(ctx, precision) + what +
+                                            (ctx->lin_cart && ctx->etype == LDG_QUAD ? " cartesian" : "") +
+                                            " f32x2, q scratch f32x2]"
+                                      : "";
     return s.c_str();
   }
   if (precision == LDG_TC_BF16X3 || precision == LDG_TC_BF16) {
@@ -1781,7 +1804,8 @@ const char* ldg_jv_describe(const ldg_ctx* ctx, int precision) {
   }
   what += f32 ? " fp32" : " fp64";
   if (ctx->ks->linear && (f32 ? ctx->lin32 : ctx->lin64))
-    s = nodal_names(ctx, precision) + what + ", q scratch " + (f32 ? "fp32" : "fp64") + "]";
+    s = nodal_names(ctx, precision) + what + (ctx->lin_cart && !(f32 && ctx->etype == LDG_HEX) ? " cartesian" : "") +
+        ", q scratch " + (f32 ? "fp32" : "fp64") + "]";
   else if (ctx->ks->qstage)
     s = std::string(ctx->pg ? "k_qstage_curved" : "k_qstage") + " + k_residual [" + what + ", tile " +
         std::to_string(ctx->ks->tile) + "]";

@@ -57,6 +57,7 @@ struct ldg_ctx {
   // nodal J.v kernels of linear models on affine tensor elements (null when not applicable)
   ldg::LinFn lin64 = nullptr, lin32 = nullptr;
   ldg::LinFn linff = nullptr;
+  bool lin_cart = false;   // the nodal kernels' axis-aligned-box instances (every element a box)
   // Euler on affine quadrilaterals: the tensor-core J.v and its constant operand image
   ldg::TcJvFn tcjv = nullptr;
   unsigned char* d_tcimg = nullptr;

@@ -165,12 +165,13 @@ void register_all(std::vector<KernelSet>& reg);
 // Nodal J.v kernels of the linear models on affine quadrilaterals / hexahedra
 // (ldg_linear.cuh): both stages, q of the direction stored in qbuf.
 typedef cudaError_t (*LinFn)(const KArgs& a, void* qbuf, cudaStream_t s);
-// The launcher for (dim, p, convection?, precision LDG_FP64 / LDG_FP32), or null.
-LinFn lin_launcher(int dim, int p, bool conv, int prec);
+// The launcher for (dim, p, convection?, precision LDG_FP64 / LDG_FP32), or null. cart:
+// every element is an axis-aligned box (diagonal J^{-1}, face normals along their axes).
+LinFn lin_launcher(int dim, int p, bool conv, int prec, bool cart);
 // The same on triangles (etype 0) and tetrahedra (etype 3), or null.
 LinFn lin_simplex_launcher(int etype, int p, bool conv, int prec);
 // The same hexahedron / quadrilateral kernels in double-float arithmetic (ldg_df.cuh).
-LinFn lin_df_launcher(int dim, int p, bool conv);
+LinFn lin_df_launcher(int dim, int p, bool conv, bool cart);
 
 // Euler J.v with the element contractions on the tensor cores (ldg_tcjv.cu), affine
 // quadrilaterals with p + 2 Gauss points: passes 3 (BF16 hi/lo splits) or 1 (BF16).

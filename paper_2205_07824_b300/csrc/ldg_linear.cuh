@@ -77,7 +77,10 @@ template <class R> __device__ __forceinline__ const typename LinBlob<R>::type* l
 }
 
 // ------------------------------------------------------------------ q-stage
-template <int DIM, int N1, class R, class QT>
+// CART: every element is an axis-aligned box (J and J^{-1} diagonal, each face normal
+// along its own axis), so the products with the zero entries of J^{-1} and of the face
+// normals are left out. Those products are exact zeros, so the sums are the same.
+template <int DIM, int N1, class R, class QT, bool CART>
 __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<DIM, N1>::NT, R>::value)) k_lin_q(KArgs a) {
   typedef LinShape<DIM, N1> S;
   typedef LinOff<N1> O;
@@ -161,10 +164,14 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   R qd[DIM];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    A s = A(0);
+    if constexpr (CART) {
+      qd[d] = R(-(Gs[e][G::JINV + d * DIM + d] * gk[d]));
+    } else {
+      A s = A(0);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) s -= Gs[e][G::JINV + k * DIM + d] * gk[k];
-    qd[d] = R(s);
+      for (int k = 0; k < DIM; ++k) s -= Gs[e][G::JINV + k * DIM + d] * gk[k];
+      qd[d] = R(s);
+    }
   }
   QT* q = (QT*)a.out;
 #pragma unroll
@@ -184,7 +191,7 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
 // the initial values of the X, Y, Z accumulators; the other nodes start at zero. The
 // FP64 pipe issues whole warps, masked lanes included, so every FP64 instruction here is
 // executed by converged warps.
-template <int DIM, int N1, bool CONV, class R, class QT>
+template <int DIM, int N1, bool CONV, class R, class QT, bool CART>
 __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<DIM, N1>::NT, R>::value)) k_lin_r(KArgs a) {
   typedef LinShape<DIM, N1> S;
   typedef LinOff<N1> O;
@@ -243,14 +250,15 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   const int id[3] = {n % N1, (n / N1) % N1, DIM == 3 ? n / (N1 * N1) : 0};
   constexpr int STR[3] = {1, N1, N1 * N1};
   // the neighbours' v and q at this thread's face items, loaded before the first barrier
-  constexpr int NFI = NE * NF * NFN, ROUNDS = (NFI + NT - 1) / NT;
-  R vpre[ROUNDS], qpre[ROUNDS][DIM];
+  // (CART: only the component of q along the face's axis, the normal's only one)
+  constexpr int NFI = NE * NF * NFN, ROUNDS = (NFI + NT - 1) / NT, NQP = CART ? 1 : DIM;
+  R vpre[ROUNDS], qpre[ROUNDS][NQP];
 #pragma unroll
   for (int r = 0; r < ROUNDS; ++r) {
     const int it = t + r * NT;
     vpre[r] = R(0);
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) qpre[r][d] = R(0);
+    for (int d = 0; d < NQP; ++d) qpre[r][d] = R(0);
     if (it < NFI) {
       const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
       if (el < ne) {
@@ -259,8 +267,12 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
           const int code = a.nbf[(size_t)(e0 + el) * NF + f];
           const int node = lin_face_node<DIM, N1>(code & 7, a.perm[(code >> 3) * NFN + j]);
           vpre[r] = R(v[(size_t)nb * NPE + node]);
+          if constexpr (CART) {
+            qpre[r][0] = R(q[((size_t)nb * DIM + (f >> 1)) * NPE + node]);
+          } else {
 #pragma unroll
-          for (int d = 0; d < DIM; ++d) qpre[r][d] = R(q[((size_t)nb * DIM + d) * NPE + node]);
+            for (int d = 0; d < DIM; ++d) qpre[r][d] = R(q[((size_t)nb * DIM + d) * NPE + node]);
+          }
         }
       }
     }
@@ -286,8 +298,12 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       A s = CONV ? A(Ak[e][k][DIM] * vn) : A(0);
+      if constexpr (CART) {
+        s += Ak[e][k][k] * qn[k];
+      } else {
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) s += Ak[e][k][d] * qn[d];
+        for (int d = 0; d < DIM; ++d) s += Ak[e][k][d] * qn[d];
+      }
       Gk[e][k][n] = R(s);
       if (id[k] != 0 && id[k] != N1 - 1) Tk[e][k][n] = R(0);
     }
@@ -304,10 +320,15 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
     const bool nb = fk & 1;
     const R vm = Vs[el][node];
     A s = A(fc[DIM] * (vm - vpre[r]));
+    if constexpr (CART) {
+      const R qm = Qs[el][f >> 1][node];
+      s += fc[f >> 1] * (qm + (nb ? qpre[r][0] : qm));
+    } else {
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const R qm = Qs[el][d][node];
-      s += fc[d] * (qm + (nb ? qpre[r][d] : qm));
+      for (int d = 0; d < DIM; ++d) {
+        const R qm = Qs[el][d][node];
+        s += fc[d] * (qm + (nb ? qpre[r][d] : qm));
+      }
     }
     if (CONV) s += fc[DIM + 1] * ((fk & 2) ? vm : vpre[r]);
     Tk[el][f >> 1][node] = -R(s);
@@ -379,20 +400,20 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
 }
 
 // Both stages of the J.v: v -> q(v) in qbuf (QT), then J v.
-template <int DIM, int N1, bool CONV, class R, class QT>
+template <int DIM, int N1, bool CONV, class R, class QT, bool CART>
 cudaError_t launch_lin(const KArgs& a, void* qbuf, cudaStream_t s) {
   typedef LinShape<DIM, N1> S;
   if (a.E <= 0) return cudaSuccess;
   const int grid = (a.E + S::NE - 1) / S::NE;
   KArgs b = a;
   b.out = qbuf;
-  k_lin_q<DIM, N1, R, QT><<<grid, S::NT, 0, s>>>(b);
+  k_lin_q<DIM, N1, R, QT, CART><<<grid, S::NT, 0, s>>>(b);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   b = a;
   b.q = qbuf;
-  k_lin_r<DIM, N1, CONV, R, QT><<<grid, S::NT, 0, s>>>(b);
+  k_lin_r<DIM, N1, CONV, R, QT, CART><<<grid, S::NT, 0, s>>>(b);
   count_launch();
   return cudaGetLastError();
 }

@@ -65,6 +65,7 @@ def test_nodal_jv_matches_oracle_and_stage_form(name, mk, p, model):
     o, g = pair(mesh, p, model, oracle.CASE_EXPSIN)
     simplex = mesh.etype in (synth.TRI, synth.TET)
     assert g.jv_kernels(0).startswith(KNAME[mesh.etype]), g.jv_kernels(0)
+    assert "cartesian" not in g.jv_kernels(0)   # sheared or turned by 90 degrees
     _, gs = pair(mesh, p, model, oracle.CASE_EXPSIN, jv_form=JV_STAGE)
     assert gs.jv_kernels(0).startswith("k_qstage + k_residual"), gs.jv_kernels(0)
     u, v = synth.random_vector(o.ndof, 1), synth.random_vector(o.ndof, 2)
@@ -83,6 +84,59 @@ def test_nodal_jv_matches_oracle_and_stage_form(name, mk, p, model):
     assert gs.jv_kernels(2) == ""
     with pytest.raises(RuntimeError):
         gs.jvp_prec(2, cuda(u), cuda(v))
+
+
+# vertex orders of a local frame turned by 180 degrees about the last axis: J stays
+# diagonal (two negative entries), and faces between turned and unturned elements meet
+# with non-identity orientations
+TURN_QUAD = [3, 2, 1, 0]
+TURN_HEX = [3, 2, 1, 0, 7, 6, 5, 4]
+
+
+def _turn_some(mesh, every=3):
+    perm = TURN_QUAD if mesh.etype == synth.QUAD else TURN_HEX
+    m = synth.Mesh(mesh.etype, mesh.xyz.copy(), mesh.vid.copy(), mesh.name)
+    for e in range(0, m.n_elem, every):
+        m.xyz[e] = mesh.xyz[e][perm]
+        m.vid[e] = mesh.vid[e][perm]
+    return m
+
+
+CART_MESHES = [
+    ("quad_box_p3", lambda: synth.quad_box((7, 5)), 3, oracle.CONVDIFF),
+    ("quad_turned_per_p4", lambda: _turn_some(synth.quad_box((6, 5), hi=(2.0, 1.5), periodic=(True, True))), 4,
+     oracle.CONVDIFF),
+    ("quad_turned_p2", lambda: _turn_some(synth.quad_box((5, 6))), 2, oracle.POISSON),
+    ("hex_box_p4", lambda: synth.hex_box((3, 4, 3)), 4, oracle.CONVDIFF),
+    ("hex_turned_per_p2", lambda: _turn_some(synth.hex_box((3, 3, 3), hi=(1.5, 1.5, 1.5),
+                                                          periodic=(True, True, True))), 2, oracle.POISSON),
+    ("hex_turned_p3", lambda: _turn_some(synth.hex_box((3, 2, 4), hi=(1.0, 0.5, 2.0))), 3, oracle.CONVDIFF),
+    ("hex_box_p6", lambda: synth.hex_box((2, 2, 3)), 6, oracle.CONVDIFF),
+]
+
+
+@pytest.mark.parametrize("name,mk,p,model", CART_MESHES, ids=[m[0] for m in CART_MESHES])
+def test_cartesian_nodal_jv(name, mk, p, model):
+    """Meshes of axis-aligned boxes take the nodal instances that leave out the zero
+    entries of J^-1 and of the face normals; the result meets the same bars as the general
+    instances (oracle, stage form, FP32 error, float pairs), with and without the BDF term."""
+    from paper_2205_07824_b300.ldg import JV_STAGE
+    mesh = mk()
+    o, g = pair(mesh, p, model, oracle.CASE_EXPSIN)
+    assert "cartesian" in g.jv_kernels(0), g.jv_kernels(0)
+    _, gs = pair(mesh, p, model, oracle.CASE_EXPSIN, jv_form=JV_STAGE)
+    u, v = synth.random_vector(o.ndof, 11), synth.random_vector(o.ndof, 12)
+    ref = o.jvp(u, v)
+    jv = host(g.jvp(cuda(u), cuda(v)))
+    assert_parity(jv, ref, what=f"{name} Cartesian nodal J.v")
+    assert_parity(jv, host(gs.jvp(cuda(u), cuda(v))), rtol2=1e-13, rtolmax=1e-12, what=f"{name} nodal vs stage")
+    e32 = np.linalg.norm(host(g.jvp_prec(1, cuda(u), cuda(v))) - ref) / np.linalg.norm(ref)
+    assert e32 <= 2e-6, (name, e32)
+    assert_parity(host(g.jvp_prec(2, cuda(u), cuda(v))), ref, what=f"{name} float-pair J.v")
+    un, unm1 = synth.random_vector(o.ndof, 13), synth.random_vector(o.ndof, 14)
+    o.set_time(2, 0.0, 0.05, un, unm1)
+    g.set_time(2, 0.0, 0.05, cuda(un), cuda(unm1))
+    assert_parity(host(g.jvp(cuda(u), cuda(v))), o.jvp(u, v), what=f"{name} Cartesian nodal J.v, BDF2")
 
 
 @pytest.mark.parametrize("scheme", [1, 2])
