@@ -16,7 +16,8 @@ namespace ldg {
 template <int DIM, int N1, bool CONV> LinFn lin_pick(int prec, bool cart) {
   if (prec == 0) return cart ? &launch_lin<DIM, N1, CONV, double, double, true>
                              : &launch_lin<DIM, N1, CONV, double, double, false>;
-  if constexpr (DIM == 3) return &launch_hex<N1, CONV, float, float>;
+  if constexpr (DIM == 3)
+    return cart ? &launch_hex<N1, CONV, float, float, true> : &launch_hex<N1, CONV, float, float, false>;
   else return cart ? &launch_lin<DIM, N1, CONV, float, float, true> : &launch_lin<DIM, N1, CONV, float, float, false>;
 }
 

@@ -6,7 +6,7 @@
 namespace ldg {
 
 template <int DIM, int N1, bool CONV> LinFn lin_df_pick(bool cart) {
-  if constexpr (DIM == 3) return &launch_hex<N1, CONV, df, df>;
+  if constexpr (DIM == 3) return cart ? &launch_hex<N1, CONV, df, df, true> : &launch_hex<N1, CONV, df, df, false>;
   else return cart ? &launch_lin<DIM, N1, CONV, df, df, true> : &launch_lin<DIM, N1, CONV, df, df, false>;
 }
 

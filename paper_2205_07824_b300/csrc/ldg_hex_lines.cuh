@@ -15,13 +15,19 @@
 // q-stage (Eq. 1a): g_k = D_k v + L0(i_k) Delta_{2k} - Lp(i_k) Delta_{2k+1} on the
 //   owner's k-line, then q_d = -sum_k Jinv[k][d] g_k per node.
 // residual (Eq. 1b): with g_k = sum_d Ak[k][d] q_d + Ak[k][3] v per node,
-//   phase 1 (x-lines): T0 = C g0 - M h, T1 = M g1, T2 = M g2;
-//   phase 2 (y-lines): U = M T0 + C T1, W = M T2;
-//   phase 3 (z-lines): R = -(M U + C W) + the face moments of the line's nodes,
-//   where h = a0/dt det J v (the BDF mass term). The face flux arrays sJ fhat are
-//   contracted with M1 along their two free axes in the same phases, one face line per
-//   thread (4 N1 lines a phase, so every thread of a warp does the same work).
+//   R = -[M_z (M_y X + M_x Y) + M_x M_y Z],
+//   X = C_x g0 - E_x Fhat_x - M_x h,  Y = C_y g1 - E_y Fhat_y,  Z = C_z g2 - E_z Fhat_z,
+// h = a0/dt det J v (the BDF mass term) and E_k Fhat_k the flux sJ fhat of the two faces
+// of axis k placed at the ends of the axis-k lines: the face mass sJ (M1 x M1) acts on
+// the two free axes of the face, which the volume passes after C supply. So
+//   phase 1: X on the x-lines, Y on the y-lines, Z on the z-lines (C, then the face fluxes
+//            at the line's two ends, the thread's own six face nodes);
+//   phase 2: X <- M_y X (y-lines), Y <- M_x Y (x-lines), Z <- M_x Z (x-lines);
+//   phase 3: r = M_z (X + Y) on the z-line into registers, Z <- M_y Z (y-lines);
+//   store: R = -(r + Z) on the z-line.
 // Each phase updates its lines in place: a line is read and written by one thread only.
+// CART (every element an axis-aligned box): the products with the zero entries of J^{-1}
+// and of the face normals are left out, and only q along the face axis is gathered.
 #pragma once
 #include "ldg_linear.cuh"
 
@@ -62,31 +68,8 @@ template <int N1, class R, bool ACC> __device__ __forceinline__ void hex_apply(c
   }
 }
 
-// One of the 4 N1 face lines contracted with M1 in phase `ph` of the residual, in place
-// in the element's face arrays FF[6][N1^2] (face index over the free axes, first fastest).
-// Line fl: set fl / (2 N1), side (fl / N1) % 2, row or column fl % N1:
-//   phase 1, along i0: rows of the y-faces (set 0) and of the z-faces (set 1);
-//   phase 2, along i1: rows of the x-faces, columns of the z-faces;
-//   phase 3, along i2: columns of the x-faces and of the y-faces.
-// After the three phases each face array holds its moments sJ (M1 x M1) fhat.
-template <int N1, class R> __device__ __forceinline__ void hex_face_line(const HexCoef<N1, R>& P, R (*FF)[N1 * N1],
-                                                                        int ph, int fl) {
-  const int set = fl / (2 * N1), side = (fl / N1) & 1, rc = fl % N1;
-  int f, base, str;
-  if (ph == 1) { f = (set ? 4 : 2) + side; base = N1 * rc; str = 1; }
-  else if (ph == 2) { f = set ? 4 + side : side; base = set ? rc : N1 * rc; str = set ? N1 : 1; }
-  else { f = (set ? 2 : 0) + side; base = rc; str = N1; }
-  R* line = &FF[f][base];
-  R x[N1], y[N1];
-#pragma unroll
-  for (int m = 0; m < N1; ++m) x[m] = line[m * str];
-  hex_apply<N1, R, false>(P.m1, x, y);
-#pragma unroll
-  for (int i = 0; i < N1; ++i) line[i * str] = y[i];
-}
-
 // ------------------------------------------------------------------ q-stage
-template <int N1, class R, class QT>
+template <int N1, class R, class QT, bool CART>
 __global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_q(KArgs a, HexCoef<N1, R> P) {
   typedef HexShape<N1, R> S;
   typedef Geo<3> G;
@@ -155,23 +138,30 @@ __global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_q(KA
   for (int i = t; i < ne * NPE; i += NT) {
     const int el = i / NPE, n = i - el * NPE;
     const R g0 = Gk[0][el][n], g1 = Gk[1][el][n], g2 = Gk[2][el][n];
+    if constexpr (CART) {
+      q[((size_t)(e0 + el) * 3 + 0) * NPE + n] = QT(R(-(Gs[el][G::JINV] * g0)));
+      q[((size_t)(e0 + el) * 3 + 1) * NPE + n] = QT(R(-(Gs[el][G::JINV + 4] * g1)));
+      q[((size_t)(e0 + el) * 3 + 2) * NPE + n] = QT(R(-(Gs[el][G::JINV + 8] * g2)));
+    } else {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      A s = A(0);
-      s -= Gs[el][G::JINV + d] * g0;
-      s -= Gs[el][G::JINV + 3 + d] * g1;
-      s -= Gs[el][G::JINV + 6 + d] * g2;
-      q[((size_t)(e0 + el) * 3 + d) * NPE + n] = QT(R(s));
+      for (int d = 0; d < 3; ++d) {
+        A s = A(0);
+        s -= Gs[el][G::JINV + d] * g0;
+        s -= Gs[el][G::JINV + 3 + d] * g1;
+        s -= Gs[el][G::JINV + 6 + d] * g2;
+        q[((size_t)(e0 + el) * 3 + d) * NPE + n] = QT(R(s));
+      }
     }
   }
 }
 
 // ----------------------------------------------------------------- residual
-template <int N1, bool CONV, class R, class QT>
+template <int N1, bool CONV, class R, class QT, bool CART>
 __global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_r(KArgs a, HexCoef<N1, R> P) {
   typedef HexShape<N1, R> S;
   typedef Geo<3> G;
   constexpr int NPE = S::NPE, NL = S::NL, NE = S::NE, NT = S::NT, GEO = S::GEO;
+  constexpr int NQ = CART ? 1 : 3;   // components of q read at a face node
   typedef typename AccOf<R>::type A;
   if (a.skip && *a.skip) return;
   const int e0 = blockIdx.x * NE;
@@ -180,31 +170,38 @@ __global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_r(KA
   __shared__ R Ak[NE][3][4];       // g_k = sum_d Ak[k][d] q_d + Ak[k][3] v
   __shared__ R FC[NE][6][5];       // per face: kappa/2 sJ n_d, tau sJ, sJ beta.n
   __shared__ R DJ[NE];             // a0/dt det J
-  __shared__ R Gk[3][NE][NPE];     // g_k, then the phase results in place
-  __shared__ R Hs[NE][NPE];        // a0/dt det J v (time term)
-  __shared__ R FF[NE][6][NL];      // own v at the face nodes, then sJ fhat, then its moments
-  __shared__ R FQ[NE][6][NL];      // own kappa/2 sJ q.n at the face nodes
+  __shared__ R Gk[3][NE][NPE];     // g_k, then X, Y, Z in place
+  __shared__ R Vs[NE][NPE];        // v
+  __shared__ R Qs[CART ? 1 : NE][CART ? 1 : 3][CART ? 1 : NPE];   // q (general elements)
   const int t = threadIdx.x;
   const int e = t / NL, l = t - e * NL, ia = l % N1, ib = l / N1;
   const bool own = e < ne;
   const double* v = (const double*)a.u;
   const QT* q = (const QT*)a.q;
-  // neighbours' v and q at this thread's six face nodes, loaded first
+  // neighbours' v and q at this thread's six face nodes (the ends of its x-, y- and
+  // z-lines, face index ia + N1 ib), loaded first; CART: also the own q along the face
+  // axis at those nodes
   const int jf = ia + N1 * ib;
-  R vnb[6], qnb[6][3];
+  R vnb[6], qnb[6][NQ], qown[6];
   int hasnb = 0;
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
     vnb[f] = R(0);
+    qown[f] = R(0);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) qnb[f][d] = R(0);
+    for (int d = 0; d < NQ; ++d) qnb[f][d] = R(0);
     if (own) {
+      if constexpr (CART) {
+        const int node = lin_face_node<3, N1>(f, jf);
+        qown[f] = R(q[((size_t)(e0 + e) * 3 + (f >> 1)) * NPE + node]);
+      }
       const int nb = a.nbr[(size_t)(e0 + e) * 6 + f];
       if (nb >= 0) {
         const int node = hex_nbr_node<N1>(a, a.nbf[(size_t)(e0 + e) * 6 + f], jf);
         vnb[f] = R(v[(size_t)nb * NPE + node]);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) qnb[f][d] = R(q[((size_t)nb * 3 + d) * NPE + node]);
+        for (int d = 0; d < NQ; ++d)
+          qnb[f][d] = R(q[((size_t)nb * 3 + (CART ? (f >> 1) : d)) * NPE + node]);
         hasnb |= 1 << f;
       }
     }
@@ -237,7 +234,28 @@ __global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_r(KA
   const bool tterm = a.a0dt != 0.0;
   for (int i = t; i < ne; i += NT) DJ[i] = R(a.a0dt * a.geo[(size_t)(e0 + i) * GEO + G::DETJ]);
   __syncthreads();
-  // nodal fluxes g_k, the time term and the own face values, node by node (coalesced loads)
+  // the part of sJ fhat at each of the six face nodes that does not depend on the own v:
+  //   kappa/2 sJ (q- + q+).n - tau sJ v+ + (sJ beta.n v+ on inflow)
+  // (Dirichlet faces: v+ = 0 and q+ = q-; general elements: the q- term joins in phase 1)
+  R np[6];
+  if (own) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const R* fc = FC[e][f];
+      const bool nb = (hasnb >> f) & 1;
+      A s = A(0);
+      if constexpr (CART) {
+        s += fc[f >> 1] * (qown[f] + (nb ? qnb[f][0] : qown[f]));
+      } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) s += fc[d] * qnb[f][d];
+      }
+      s -= fc[3] * vnb[f];
+      if (CONV && !(fc[4] >= R(0))) s += fc[4] * vnb[f];
+      np[f] = R(s);
+    }
+  }
+  // nodal fluxes g_k and v (and q on general elements), node by node (coalesced loads)
   for (int i = t; i < ne * NPE; i += NT) {
     const int el = i / NPE, n = i - el * NPE;
     const R vn = R(v[(size_t)(e0 + el) * NPE + n]);
@@ -247,124 +265,96 @@ __global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_r(KA
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       A s = CONV ? A(Ak[el][k][3] * vn) : A(0);
+      if constexpr (CART) {
+        s += Ak[el][k][k] * qn[k];
+      } else {
 #pragma unroll
-      for (int d = 0; d < 3; ++d) s += Ak[el][k][d] * qn[d];
+        for (int d = 0; d < 3; ++d) s += Ak[el][k][d] * qn[d];
+      }
       Gk[k][el][n] = R(s);
     }
-    if (tterm) Hs[el][n] = DJ[el] * vn;
-    const int i0 = n % N1, i1 = (n / N1) % N1, i2 = n / NL;
-    const int id[3] = {i0, i1, i2};
+    Vs[el][n] = vn;
+    if constexpr (!CART) {
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      const int ax = f >> 1;
-      if (id[ax] != ((f & 1) ? N1 - 1 : 0)) continue;
-      const int j = lin_face_index<3, N1>(ax, id);
-      A s = A(0);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) s += FC[el][f][d] * qn[d];
-      FF[el][f][j] = vn;
-      FQ[el][f][j] = R(s);
+      for (int d = 0; d < 3; ++d) Qs[el][d][n] = qn[d];
     }
   }
   __syncthreads();
-  // sJ fhat at this thread's six face nodes (in place of the own v)
+  // ---- phase 1: C on the thread's k-line of g_k, then -sJ fhat at its two ends:
+  //   sJ fhat = tau sJ (v- - v+) + kappa/2 sJ (q- + q+).n + sJ beta.n v_upwind
+  // (Dirichlet faces: v+ = 0, q+ = q-, no inflow); X also takes -M_x h
   if (own) {
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+      const int base = k == 0 ? N1 * ia + NL * ib : (k == 1 ? ia + NL * ib : ia + N1 * ib);
+      const int str = k == 0 ? 1 : (k == 1 ? N1 : NL);
+      R x[N1], y[N1];
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      const R* fc = FC[e][f];
-      const R vm = FF[e][f][jf], qmn = FQ[e][f][jf], bs = fc[4];
-      R fh;
-      if ((hasnb >> f) & 1) {
-        A qpn = A(0);
+      for (int m = 0; m < N1; ++m) x[m] = Gk[k][e][base + m * str];
+      hex_apply<N1, R, false>(P.c, x, y);
+      if (k == 0 && tterm) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) qpn += fc[d] * qnb[f][d];
-        fh = fc[3] * (vm - vnb[f]) + (qmn + R(qpn));
-        if (CONV) fh += bs * (bs >= R(0) ? vm : vnb[f]);
-      } else {
-        fh = fc[3] * vm + R(2) * qmn;
-        if (CONV && bs >= R(0)) fh += bs * vm;
+        for (int m = 0; m < N1; ++m) x[m] = R(-(DJ[e] * Vs[e][base + m]));
+        hex_apply<N1, R, true>(P.m1, x, y);
       }
-      FF[e][f][jf] = fh;
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int f = 2 * k + sd, node = base + sd * (N1 - 1) * str;
+        const R* fc = FC[e][f];
+        const R vm = Vs[e][node];
+        A fs = A(fc[3] * vm);
+        fs += k == 0 ? np[sd] : (k == 1 ? np[2 + sd] : np[4 + sd]);
+        if constexpr (!CART) {
+          A qs = A(0);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) qs += fc[d] * Qs[e][d][node];
+          const R qm = R(qs);
+          fs += qm;
+          fs += ((hasnb >> f) & 1) ? R(0) : qm;
+        }
+        if (CONV) fs += fc[4] * (fc[4] >= R(0) ? vm : R(0));
+        y[sd ? N1 - 1 : 0] -= R(fs);
+      }
+#pragma unroll
+      for (int i = 0; i < N1; ++i) Gk[k][e][base + i * str] = y[i];
     }
   }
   __syncthreads();
-  // ---- phases 1 and 2, one loop body (the face-line code once):
-  //   phase 1: x-line (i1, i2) = (ia, ib): T0 = C g0 - M h, T1 = M g1, T2 = M g2;
-  //   phase 2: y-line (i0, i2) = (ia, ib): U = M T0 + C T1, W = M T2;
-  //   face lines along i0, then along i1
+  // ---- phase 2: X <- M_y X, Y <- M_x Y, Z <- M_x Z
+  if (own) {
 #pragma unroll 1
-  for (int ph = 1; ph <= 2; ++ph) {
-    if (own) {
-      const int base = ph == 1 ? N1 * ia + NL * ib : ia + NL * ib;
-      const int str = ph == 1 ? 1 : N1;
+    for (int k = 0; k < 3; ++k) {
+      const int base = k == 0 ? ia + NL * ib : N1 * ia + NL * ib;
+      const int str = k == 0 ? N1 : 1;
       R x[N1], y[N1];
-      // field 0: C g0 (phase 1, with -M h when there is a time term) or M T0 + C T1 (phase 2)
 #pragma unroll
-      for (int i = 0; i < N1; ++i) y[i] = R(0);
-      if (ph == 2 || tterm) {
-        const R* src = ph == 1 ? Hs[e] : Gk[0][e];
+      for (int m = 0; m < N1; ++m) x[m] = Gk[k][e][base + m * str];
+      hex_apply<N1, R, false>(P.m1, x, y);
 #pragma unroll
-        for (int m = 0; m < N1; ++m) x[m] = src[base + m * str];
-        hex_apply<N1, R, false>(P.m1, x, y);
-        if (ph == 1) {
-#pragma unroll
-          for (int i = 0; i < N1; ++i) y[i] = -y[i];
-        }
-      }
-      const R* src = ph == 1 ? Gk[0][e] : Gk[1][e];
-#pragma unroll
-      for (int m = 0; m < N1; ++m) x[m] = src[base + m * str];
-      hex_apply<N1, R, true>(P.c, x, y);
-#pragma unroll
-      for (int i = 0; i < N1; ++i) Gk[0][e][base + i * str] = y[i];
-      // the fields that only take M: g1 and g2 (phase 1), T2 (phase 2)
-#pragma unroll 1
-      for (int k = ph == 1 ? 1 : 2; k < 3; ++k) {
-#pragma unroll
-        for (int m = 0; m < N1; ++m) x[m] = Gk[k][e][base + m * str];
-        hex_apply<N1, R, false>(P.m1, x, y);
-#pragma unroll
-        for (int i = 0; i < N1; ++i) Gk[k][e][base + i * str] = y[i];
-      }
-      for (int fl = l; fl < 4 * N1; fl += NL) hex_face_line<N1, R>(P, FF[e], ph, fl);
+      for (int i = 0; i < N1; ++i) Gk[k][e][base + i * str] = y[i];
     }
-    __syncthreads();
   }
-  // ---- phase 3: z-line (i0, i1) = (ia, ib) into registers; face lines along i2 (x- and
-  // y-face columns), then the face moments on the line and the store
+  __syncthreads();
+  // ---- phase 3: r = M_z (X + Y) on the z-line (ia, ib); Z <- M_y Z on the y-line
   const int bz = ia + N1 * ib;
   R r[N1];
   if (own) {
-    R x0[N1], x1[N1];
+    R x[N1], y[N1];
 #pragma unroll
-    for (int m = 0; m < N1; ++m) {
-      x0[m] = Gk[0][e][bz + NL * m];
-      x1[m] = Gk[2][e][bz + NL * m];
-    }
-    hex_apply<N1, R, false>(P.m1, x0, r);
-    hex_apply<N1, R, true>(P.c, x1, r);
-    for (int fl = l; fl < 4 * N1; fl += NL) hex_face_line<N1, R>(P, FF[e], 3, fl);
+    for (int m = 0; m < N1; ++m) x[m] = Gk[0][e][bz + NL * m] + Gk[1][e][bz + NL * m];
+    hex_apply<N1, R, false>(P.m1, x, r);
+    const int by = ia + NL * ib;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) x[m] = Gk[2][e][by + N1 * m];
+    hex_apply<N1, R, false>(P.m1, x, y);
+#pragma unroll
+    for (int i = 0; i < N1; ++i) Gk[2][e][by + N1 * i] = y[i];
   }
   __syncthreads();
   if (!own) return;
-#pragma unroll
-  for (int i = 0; i < N1; ++i) r[i] = -r[i];
-  if (ia == 0 || ia == N1 - 1) {   // x-face moments at (ia, ib, i2)
-    const R* fm = &FF[e][ia != 0][ib];
-#pragma unroll
-    for (int i = 0; i < N1; ++i) r[i] += fm[N1 * i];
-  }
-  if (ib == 0 || ib == N1 - 1) {   // y-face moments at (ia, ib, i2)
-    const R* fm = &FF[e][2 + (ib != 0)][ia];
-#pragma unroll
-    for (int i = 0; i < N1; ++i) r[i] += fm[N1 * i];
-  }
-  // z-faces at the line's ends
-  r[0] += FF[e][4][bz];
-  r[N1 - 1] += FF[e][5][bz];
   double* out = (double*)a.out + (size_t)(e0 + e) * NPE + bz;
 #pragma unroll
-  for (int i = 0; i < N1; ++i) out[NL * i] = (double)r[i];
+  for (int i = 0; i < N1; ++i) out[NL * i] = (double)(-(r[i] + Gk[2][e][bz + NL * i]));
 }
 
 // The 1-D operators of the blob (Dn, M1, C, L0, Lp; FP64) in the kernel's arithmetic.
@@ -392,7 +382,7 @@ template <int N1, class R> HexCoef<N1, R> hex_coef(const double* blob) {
 }
 
 // Both stages of the hexahedral J.v: v -> q(v) in qbuf (QT), then J v.
-template <int N1, bool CONV, class R, class QT>
+template <int N1, bool CONV, class R, class QT, bool CART>
 cudaError_t launch_hex(const KArgs& a, void* qbuf, cudaStream_t s) {
   typedef HexShape<N1, R> S;
   if (a.E <= 0) return cudaSuccess;
@@ -401,13 +391,13 @@ cudaError_t launch_hex(const KArgs& a, void* qbuf, cudaStream_t s) {
   const int grid = (a.E + S::NE - 1) / S::NE;
   KArgs b = a;
   b.out = qbuf;
-  k_hex_q<N1, R, QT><<<grid, S::NT, 0, s>>>(b, P);
+  k_hex_q<N1, R, QT, CART><<<grid, S::NT, 0, s>>>(b, P);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   b = a;
   b.q = qbuf;
-  k_hex_r<N1, CONV, R, QT><<<grid, S::NT, 0, s>>>(b, P);
+  k_hex_r<N1, CONV, R, QT, CART><<<grid, S::NT, 0, s>>>(b, P);
   count_launch();
   return cudaGetLastError();
 }

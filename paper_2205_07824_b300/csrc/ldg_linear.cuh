@@ -530,6 +530,9 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_q(KArgs a) {
   for (int d = 0; d < DIM; ++d) q[((size_t)(e0 + e) * DIM + d) * NPE + n] = QT(qd[d]);
 }
 
+// The face terms are formed one face node per thread over the whole CTA (flux, then its
+// face-mass moment), so that the FP64 work runs in converged warps; a node then adds the
+// moments of the faces it lies on.
 template <class EL, bool CONV, class R, class QT>
 __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
   typedef SimShape<EL> S;
@@ -543,19 +546,18 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
   if (!cta_active(a, e0, ne)) return;
   extern __shared__ __align__(16) unsigned char sim_dsm[];
   R* ops = (R*)sim_dsm;
-  __shared__ R Gs[NE][GEO];
-  __shared__ MPar<R> MPs[NE];
   __shared__ R Ak[NE][DIM][DIM + 1];  // g_k = sum_d Ak[k][d] q_d + Ak[k][DIM] v
+  __shared__ R FC[NE][NF][DIM + 2];   // per face: kappa/2 sJ n_d, tau sJ, sJ beta.n
+  __shared__ R DJ[NE];                // a0/dt det J
   __shared__ R Gk[NE][DIM][NPE];
-  __shared__ R Hs[NE][NPE];
-  __shared__ R FV[NE][NF][NFN];
-  __shared__ R FQ[NE][NF][NFN];
-  __shared__ R FF[NE][NF][NFN];
+  __shared__ R Vs[NE][NPE];
+  __shared__ R Qs[NE][DIM][NPE];
+  __shared__ R FF[NE][NF][NFN];       // sJ fhat at the face nodes
+  __shared__ R FM[NE][NF][NFN];       // its face-mass moments M_f (sJ fhat)
   const int t = threadIdx.x;
   const auto* lo = lin_ops<R>(a);
   for (int i = t; i < O::SIZE; i += NT) ops[i] = R(lo[i]);
-  for (int i = t; i < ne * GEO; i += NT) Gs[i / GEO][i % GEO] = R(a.geo[(size_t)e0 * GEO + i]);
-  for (int i = t; i < NE; i += NT) MPs[i] = mpar<R>(i < ne ? elem_mp(a, e0 + i) : a.mp);
+  for (int i = t; i < ne; i += NT) DJ[i] = R(a.a0dt * a.geo[(size_t)(e0 + i) * GEO + G::DETJ]);
   for (int i = t; i < ne * DIM; i += NT) {
     const int el = i / DIM, k = i % DIM;
     const double* g = a.geo + (size_t)(e0 + el) * GEO;
@@ -568,19 +570,62 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
     }
     Ak[el][k][DIM] = CONV ? R(bsum) : R(0);
   }
+  for (int i = t; i < ne * NF; i += NT) {
+    const int el = i / NF, f = i % NF;
+    const double* g = a.geo + (size_t)(e0 + el) * GEO + G::FACE + f * (DIM + 1);
+    const ModelParams mp = elem_mp(a, e0 + el);
+    const double sj = g[DIM];
+    double bn = 0.0;
+    for (int d = 0; d < DIM; ++d) {
+      FC[el][f][d] = R(0.5 * mp.kappa * sj * g[d]);
+      bn += mp.beta[d] * g[d];
+    }
+    FC[el][f][DIM] = R(mp.tau * sj);
+    FC[el][f][DIM + 1] = CONV ? R(sj * bn) : R(0);
+  }
   const double* v = (const double*)a.u;
   const QT* q = (const QT*)a.q;
-  const R a0dt = R(a.a0dt);
   const bool tterm = a.a0dt != 0.0;
   const int e = t / NPE, n = t - e * NPE;
   const bool own = e < ne;
+  // the neighbours' v and q at this thread's face items, loaded before the first barrier
+  constexpr int NFI = NE * NF * NFN, ROUNDS = (NFI + NT - 1) / NT;
+  R vpre[ROUNDS], qpre[ROUNDS][DIM];
+  int hasnb = 0;
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    vpre[r] = R(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) qpre[r][d] = R(0);
+    if (it < NFI) {
+      const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+      if (el < ne) {
+        const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
+        if (nb >= 0) {
+          const int node = sim_nbr_node<EL>(a, a.nbf[(size_t)(e0 + el) * NF + f], j);
+          vpre[r] = R(v[(size_t)nb * NPE + node]);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) qpre[r][d] = R(q[((size_t)nb * DIM + d) * NPE + node]);
+          hasnb |= 1 << r;
+        }
+      }
+    }
+  }
   R vn = R(0), qn[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) qn[d] = R(0);
   if (own) {
     vn = R(v[(size_t)(e0 + e) * NPE + n]);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) qn[d] = R(q[((size_t)(e0 + e) * DIM + d) * NPE + n]);
+    Vs[e][n] = vn;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) Qs[e][d][n] = qn[d];
   }
   __syncthreads();
+  // nodal fluxes; sJ fhat = tau sJ (v- - v+) + kappa/2 sJ (q- + q+).n + sJ beta.n v_upwind
+  // at the face nodes (Dirichlet faces: v+ = 0, q+ = q-, no inflow)
   if (own) {
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
@@ -589,64 +634,59 @@ __global__ void __launch_bounds__(SimShape<EL>::NT) k_sim_r(KArgs a) {
       for (int d = 0; d < DIM; ++d) s += Ak[e][k][d] * qn[d];
       Gk[e][k][n] = R(s);
     }
-    if (tterm) Hs[e][n] = R(a0dt * Gs[e][G::DETJ]) * vn;
-    for_node_faces<EL>(n, [&](int f, int j) {
-      A s = A(0);
+  }
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) s += Gs[e][G::FACE + f * (DIM + 1) + d] * qn[d];
-      FV[e][f][j] = vn;
-      FQ[e][f][j] = R(s);
-    });
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    if (it >= NFI) break;
+    const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+    if (el >= ne) continue;
+    const int node = EL::face_node(f, j);
+    const R* fc = FC[el][f];
+    const bool nb = (hasnb >> r) & 1;
+    const R vm = Vs[el][node];
+    A s = A(fc[DIM] * (vm - vpre[r]));
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const R qm = Qs[el][d][node];
+      s += fc[d] * (qm + (nb ? qpre[r][d] : qm));
+    }
+    if (CONV) s += fc[DIM + 1] * (fc[DIM + 1] >= R(0) ? vm : vpre[r]);
+    FF[el][f][j] = R(s);
   }
   __syncthreads();
-  for (int it = t; it < NE * NF * NFN; it += NT) {
+  // face-mass moments of the fluxes; volume terms of the residual
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    if (it >= NFI) break;
     const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
-    R fh = R(0);
-    if (el < ne) {
-      const MPar<R>& mp = MPs[el];
-      const R* nrm = &Gs[el][G::FACE + f * (DIM + 1)];
-      const R vm = FV[el][f][j], qmn = FQ[el][f][j];
-      R bn = R(0);
-      if (CONV) {
+    if (el >= ne) continue;
+    const R* row = ops + O::MF + j * O::LDL;
+    A s = A(0);
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) bn += mp.beta[d] * nrm[d];
-      }
-      const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
-      if (nb >= 0) {
-        const int node = sim_nbr_node<EL>(a, a.nbf[(size_t)(e0 + el) * NF + f], j);
-        const R vp = R(v[(size_t)nb * NPE + node]);
-        A qpn = A(0);
+    for (int b = 0; b < NFN; ++b) s += row[b] * FF[el][f][b];
+    FM[el][f][j] = R(s);
+  }
+  A r = A(0);
+  if (own) {
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) qpn += nrm[d] * R(q[((size_t)nb * DIM + d) * NPE + node]);
-        fh = mp.tau * (vm - vp) + R(R(0.5) * mp.kappa) * (qmn + R(qpn));
-        if (CONV) fh += bn * (bn >= R(0) ? vm : vp);
-      } else {
-        fh = mp.tau * vm + mp.kappa * qmn;
-        if (CONV && bn >= R(0)) fh += bn * vm;
-      }
-      fh *= nrm[DIM];
+    for (int k = 0; k < DIM; ++k) {
+      const R* row = ops + O::C + (k * NPE + n) * O::LDA;
+#pragma unroll 8
+      for (int m = 0; m < NPE; ++m) r -= row[m] * Gk[e][k][m];
     }
-    FF[el][f][j] = fh;
+    if (tterm) {
+      const R* row = ops + O::M + n * O::LDA;
+      A h = A(0);
+#pragma unroll 8
+      for (int m = 0; m < NPE; ++m) h += row[m] * Vs[e][m];
+      r += DJ[e] * R(h);
+    }
   }
   __syncthreads();
   if (!own) return;
-  A r = A(0);
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    const R* row = ops + O::C + (k * NPE + n) * O::LDA;
-#pragma unroll 8
-    for (int m = 0; m < NPE; ++m) r -= row[m] * Gk[e][k][m];
-  }
-  if (tterm) {
-    const R* row = ops + O::M + n * O::LDA;
-#pragma unroll 8
-    for (int m = 0; m < NPE; ++m) r += row[m] * Hs[e][m];
-  }
-  for_node_faces<EL>(n, [&](int f, int j) {
-    const R* row = ops + O::MF + j * O::LDL;
-#pragma unroll
-    for (int b = 0; b < NFN; ++b) r += row[b] * FF[e][f][b];
-  });
+  for_node_faces<EL>(n, [&](int f, int j) { r += FM[e][f][j]; });
   ((double*)a.out)[(size_t)(e0 + e) * NPE + n] = (double)R(r);
 }
 
