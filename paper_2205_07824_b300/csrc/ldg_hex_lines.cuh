@@ -45,11 +45,14 @@ template <int N1, class R> struct HexShape {
   static constexpr int NT = (NE * NL + 31) / 32 * 32;
   static constexpr int GEO = Geo<3>::size(NF);
 };
-// Resident CTAs asked of the register allocator: five, which leaves 51 registers a thread
-// in FP32 and 102 with 8-byte values, enough for the lines and the prefetched neighbour
-// values without spills (measured on 48^3, p = 4: six CTAs spill and are 12% slower in
-// FP32, 6% in float pairs; four are 3% and 6% slower).
-constexpr int kHexMinBlocks = 5;
+// Resident CTAs asked of the register allocator. FP32 q-stage: eight (32 registers a
+// thread, no spills), every warp slot for its gathers. FP32 residual: six (40 registers).
+// Float pairs: five, which leaves 102 registers with 8-byte values, enough for the lines
+// and the prefetched neighbour values without spills (measured on 48^3, p = 4: six CTAs
+// spill and are 6% slower, four are 6% slower).
+template <class R, bool QSTAGE> struct HexMinBlocks {
+  static constexpr int value = sizeof(R) == 4 ? (QSTAGE ? 8 : 6) : 5;
+};
 
 // the neighbour's local node of face node j on this element's face f
 template <int N1> __device__ __forceinline__ int hex_nbr_node(const KArgs& a, int code, int j) {
@@ -70,7 +73,7 @@ template <int N1, class R, bool ACC> __device__ __forceinline__ void hex_apply(c
 
 // ------------------------------------------------------------------ q-stage
 template <int N1, class R, class QT, bool CART>
-__global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_q(KArgs a, HexCoef<N1, R> P) {
+__global__ void __launch_bounds__(HexShape<N1, R>::NT, (HexMinBlocks<R, true>::value)) k_hex_q(KArgs a, HexCoef<N1, R> P) {
   typedef HexShape<N1, R> S;
   typedef Geo<3> G;
   constexpr int NPE = S::NPE, NL = S::NL, NE = S::NE, NT = S::NT, GEO = S::GEO;
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_q(KA
 
 // ----------------------------------------------------------------- residual
 template <int N1, bool CONV, class R, class QT, bool CART>
-__global__ void __launch_bounds__(HexShape<N1, R>::NT, kHexMinBlocks) k_hex_r(KArgs a, HexCoef<N1, R> P) {
+__global__ void __launch_bounds__(HexShape<N1, R>::NT, (HexMinBlocks<R, false>::value)) k_hex_r(KArgs a, HexCoef<N1, R> P) {
   typedef HexShape<N1, R> S;
   typedef Geo<3> G;
   constexpr int NPE = S::NPE, NL = S::NL, NE = S::NE, NT = S::NT, GEO = S::GEO;
