@@ -62,14 +62,14 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 JV_FLOP_PER_DOF = {
     # 820 + 1655 MFLOP per J.v of 13,824,000 DOF (k_lin_q, k_lin_r; general affine elements)
     "k_lin_q + k_lin_r [hex p=4 nq=5 convdiff fp64, q scratch fp64]": 179.07,
-    # 613 + 1390 MFLOP (the instances for axis-aligned boxes, the 48^3 box mesh)
-    "k_lin_q + k_lin_r [hex p=4 nq=5 convdiff fp64 cartesian, q scratch fp64]": 144.87,
+    # 266 + 1472 MFLOP (the trace form for axis-aligned boxes, the 48^3 box mesh)
+    "k_lin_qt + k_lin_rt [hex p=4 nq=5 convdiff fp64 cartesian, q scratch fp64]": 125.72,
 }
 JV_TRAFFIC_PER_DOF = {
     # (154.6 + 274.9) + (486.4 + 99.7) MB of DRAM reads + writes per J.v (k_lin_q, k_lin_r)
     "k_lin_q + k_lin_r [hex p=4 nq=5 convdiff fp64, q scratch fp64]": 73.47,
-    # (154.6 + 275.0) + (486.4 + 99.0) MB
-    "k_lin_q + k_lin_r [hex p=4 nq=5 convdiff fp64 cartesian, q scratch fp64]": 73.43,
+    # (135.2 + 96.1) + (287.4 + 92.3) MB
+    "k_lin_qt + k_lin_rt [hex p=4 nq=5 convdiff fp64 cartesian, q scratch fp64]": 44.20,
 }
 
 

@@ -357,6 +357,19 @@ bool build_lin_ops(int p, std::vector<double>& blob, std::string& err) {
   blob.insert(blob.end(), C.begin(), C.end());
   for (int i = 0; i < n1; ++i) blob.push_back(M1i[i * n1]);
   for (int i = 0; i < n1; ++i) blob.push_back(M1i[i * n1 + n1 - 1]);
+  // products with C for the residual of axis-aligned boxes: C Dn, C L0, C Lp
+  for (int i = 0; i < n1; ++i)
+    for (int l = 0; l < n1; ++l) {
+      double s = 0.0;
+      for (int m = 0; m < n1; ++m) s += C[i * n1 + m] * Dn[m * n1 + l];
+      blob.push_back(s);
+    }
+  for (int c = 0; c < 2; ++c)
+    for (int i = 0; i < n1; ++i) {
+      double s = 0.0;
+      for (int m = 0; m < n1; ++m) s += C[i * n1 + m] * M1i[m * n1 + (c ? n1 - 1 : 0)];
+      blob.push_back(s);
+    }
   return true;
 }
 

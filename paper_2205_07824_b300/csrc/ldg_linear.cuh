@@ -30,9 +30,11 @@
 
 namespace ldg {
 
-// Blob of 1-D operators (N1 = p + 1 values per axis): Dn, M1, C, then L0 and L1.
+// Blob of 1-D operators (N1 = p + 1 values per axis): Dn, M1, C, then L0 and L1, then
+// the products C Dn, C L0 and C L1 (for the residual of axis-aligned boxes).
 template <int N1> struct LinOff {
   static constexpr int DN = 0, M1 = N1 * N1, C = 2 * N1 * N1, L = 3 * N1 * N1, SIZE = 3 * N1 * N1 + 2 * N1;
+  static constexpr int CD = SIZE, CL = CD + N1 * N1, SIZE_T = CL + 2 * N1;
 };
 
 // Elements per CTA (one thread per node, elements packed back to back) and threads.
@@ -77,10 +79,7 @@ template <class R> __device__ __forceinline__ const typename LinBlob<R>::type* l
 }
 
 // ------------------------------------------------------------------ q-stage
-// CART: every element is an axis-aligned box (J and J^{-1} diagonal, each face normal
-// along its own axis), so the products with the zero entries of J^{-1} and of the face
-// normals are left out. Those products are exact zeros, so the sums are the same.
-template <int DIM, int N1, class R, class QT, bool CART>
+template <int DIM, int N1, class R, class QT>
 __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<DIM, N1>::NT, R>::value)) k_lin_q(KArgs a) {
   typedef LinShape<DIM, N1> S;
   typedef LinOff<N1> O;
@@ -164,14 +163,10 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   R qd[DIM];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    if constexpr (CART) {
-      qd[d] = R(-(Gs[e][G::JINV + d * DIM + d] * gk[d]));
-    } else {
-      A s = A(0);
+    A s = A(0);
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) s -= Gs[e][G::JINV + k * DIM + d] * gk[k];
-      qd[d] = R(s);
-    }
+    for (int k = 0; k < DIM; ++k) s -= Gs[e][G::JINV + k * DIM + d] * gk[k];
+    qd[d] = R(s);
   }
   QT* q = (QT*)a.out;
 #pragma unroll
@@ -191,7 +186,7 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
 // the initial values of the X, Y, Z accumulators; the other nodes start at zero. The
 // FP64 pipe issues whole warps, masked lanes included, so every FP64 instruction here is
 // executed by converged warps.
-template <int DIM, int N1, bool CONV, class R, class QT, bool CART>
+template <int DIM, int N1, bool CONV, class R, class QT>
 __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<DIM, N1>::NT, R>::value)) k_lin_r(KArgs a) {
   typedef LinShape<DIM, N1> S;
   typedef LinOff<N1> O;
@@ -250,15 +245,14 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   const int id[3] = {n % N1, (n / N1) % N1, DIM == 3 ? n / (N1 * N1) : 0};
   constexpr int STR[3] = {1, N1, N1 * N1};
   // the neighbours' v and q at this thread's face items, loaded before the first barrier
-  // (CART: only the component of q along the face's axis, the normal's only one)
-  constexpr int NFI = NE * NF * NFN, ROUNDS = (NFI + NT - 1) / NT, NQP = CART ? 1 : DIM;
-  R vpre[ROUNDS], qpre[ROUNDS][NQP];
+  constexpr int NFI = NE * NF * NFN, ROUNDS = (NFI + NT - 1) / NT;
+  R vpre[ROUNDS], qpre[ROUNDS][DIM];
 #pragma unroll
   for (int r = 0; r < ROUNDS; ++r) {
     const int it = t + r * NT;
     vpre[r] = R(0);
 #pragma unroll
-    for (int d = 0; d < NQP; ++d) qpre[r][d] = R(0);
+    for (int d = 0; d < DIM; ++d) qpre[r][d] = R(0);
     if (it < NFI) {
       const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
       if (el < ne) {
@@ -267,12 +261,8 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
           const int code = a.nbf[(size_t)(e0 + el) * NF + f];
           const int node = lin_face_node<DIM, N1>(code & 7, a.perm[(code >> 3) * NFN + j]);
           vpre[r] = R(v[(size_t)nb * NPE + node]);
-          if constexpr (CART) {
-            qpre[r][0] = R(q[((size_t)nb * DIM + (f >> 1)) * NPE + node]);
-          } else {
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) qpre[r][d] = R(q[((size_t)nb * DIM + d) * NPE + node]);
-          }
+          for (int d = 0; d < DIM; ++d) qpre[r][d] = R(q[((size_t)nb * DIM + d) * NPE + node]);
         }
       }
     }
@@ -298,12 +288,8 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       A s = CONV ? A(Ak[e][k][DIM] * vn) : A(0);
-      if constexpr (CART) {
-        s += Ak[e][k][k] * qn[k];
-      } else {
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) s += Ak[e][k][d] * qn[d];
-      }
+      for (int d = 0; d < DIM; ++d) s += Ak[e][k][d] * qn[d];
       Gk[e][k][n] = R(s);
       if (id[k] != 0 && id[k] != N1 - 1) Tk[e][k][n] = R(0);
     }
@@ -320,15 +306,10 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
     const bool nb = fk & 1;
     const R vm = Vs[el][node];
     A s = A(fc[DIM] * (vm - vpre[r]));
-    if constexpr (CART) {
-      const R qm = Qs[el][f >> 1][node];
-      s += fc[f >> 1] * (qm + (nb ? qpre[r][0] : qm));
-    } else {
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        const R qm = Qs[el][d][node];
-        s += fc[d] * (qm + (nb ? qpre[r][d] : qm));
-      }
+    for (int d = 0; d < DIM; ++d) {
+      const R qm = Qs[el][d][node];
+      s += fc[d] * (qm + (nb ? qpre[r][d] : qm));
     }
     if (CONV) s += fc[DIM + 1] * ((fk & 2) ? vm : vpre[r]);
     Tk[el][f >> 1][node] = -R(s);
@@ -399,7 +380,271 @@ __global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<
   if (own) ((double*)a.out)[(size_t)(e0 + e) * NPE + n] = (double)rv;
 }
 
-// Both stages of the J.v: v -> q(v) in qbuf (QT), then J v.
+// ------------------------------------------- axis-aligned boxes: the trace form
+// When every element is an axis-aligned box (J and J^{-1} diagonal, s_k = Jinv[k][k],
+// each face normal along its own axis), q enters the residual in two places only:
+//  * the volume term C_k g_k with g_k = a_k q_k + b_k v (a_k = kappa det J s_k,
+//    b_k = det J s_k beta_k) and q_k = -s_k (D_k v + L0 Delta_{2k} - Lp Delta_{2k+1}):
+//      C_k g_k = W_k v + c0_k (C L0) Delta_{2k} - c0_k (C Lp) Delta_{2k+1},
+//      W_k = -a_k s_k (C Dn) + b_k C,  c0_k = -a_k s_k,
+//    with the 1-D products C Dn, C L0, C Lp formed on the host;
+//  * the face fluxes, which need only q_k at the face nodes of the faces of axis k.
+// So the q-stage forms q_k at the face nodes only (k_lin_qt, output [E][NF][NFN]) and
+// the residual (k_lin_rt) applies W_k to v. The products with the zero entries of J^{-1}
+// and of the normals drop out; the rest is the same operator as k_lin_q / k_lin_r.
+template <int DIM, int N1, class R, class QT>
+__global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinShape<DIM, N1>::NT > 256 ? 1 : 8)) k_lin_qt(KArgs a) {
+  typedef LinShape<DIM, N1> S;
+  typedef LinOff<N1> O;
+  typedef Geo<DIM> G;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NF = S::NF, NE = S::NE, NT = S::NT, GEO = S::GEO;
+  typedef typename AccOf<R>::type A;
+  if (a.skip && *a.skip) return;
+  const int e0 = blockIdx.x * NE;
+  const int ne = min(NE, a.E - e0);
+  if (!cta_active(a, e0, ne)) return;
+  __shared__ R ops[O::SIZE];
+  __shared__ R SK[NE][DIM];           // -Jinv[k][k]
+  __shared__ R Vs[NE][NPE];
+  __shared__ R Ds[NE][NF][NFN];       // Delta_f = v- - vhat at the face nodes
+  const int t = threadIdx.x;
+  const auto* lo = lin_ops<R>(a);
+  for (int i = t; i < O::SIZE; i += NT) ops[i] = R(lo[i]);
+  for (int i = t; i < ne * DIM; i += NT)
+    SK[i / DIM][i % DIM] = R(-a.geo[(size_t)(e0 + i / DIM) * GEO + G::JINV + (i % DIM) * (DIM + 1)]);
+  const double* v = (const double*)a.u;
+  constexpr int NFI = NE * NF * NFN, ROUNDS = (NFI + NT - 1) / NT;
+  R vpre[ROUNDS];
+  int hasnb = 0;
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    vpre[r] = R(0);
+    if (it < NFI) {
+      const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+      if (el < ne) {
+        const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
+        if (nb >= 0) {
+          const int code = a.nbf[(size_t)(e0 + el) * NF + f];
+          vpre[r] = R(v[(size_t)nb * NPE + lin_face_node<DIM, N1>(code & 7, a.perm[(code >> 3) * NFN + j])]);
+          hasnb |= 1 << r;
+        }
+      }
+    }
+  }
+  for (int i = t; i < ne * NPE; i += NT) Vs[i / NPE][i % NPE] = R(v[(size_t)e0 * NPE + i]);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    if (it >= NFI) break;
+    const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+    if (el >= ne) continue;
+    const R vm = Vs[el][lin_face_node<DIM, N1>(f, j)];
+    Ds[el][f][j] = (hasnb >> r) & 1 ? (vm - vpre[r]) * R(0.5) : vm;
+  }
+  __syncthreads();
+  // q_k at face node j of face f = 2k + side: the axis-k line through it, at its end i_k
+  constexpr int STR[3] = {1, N1, N1 * N1};
+  QT* qt = (QT*)a.out;
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    if (it >= NFI) break;
+    const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+    if (el >= ne) continue;
+    const int k = f >> 1, ik = (f & 1) ? N1 - 1 : 0;
+    const int node = lin_face_node<DIM, N1>(f, j), base = node - ik * STR[k];
+    const R* dn = ops + O::DN + ik * N1;
+    A s = A(ops[O::L + ik] * Ds[el][2 * k][j]);
+    s -= ops[O::L + N1 + ik] * Ds[el][2 * k + 1][j];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) s += dn[m] * Vs[el][base + m * STR[k]];
+    qt[(size_t)e0 * NF * NFN + it] = QT(SK[el][k] * R(s));
+  }
+}
+
+template <int DIM, int N1, bool CONV, class R, class QT>
+__global__ void __launch_bounds__(LinShape<DIM, N1>::NT, (LinMinBlocks<LinShape<DIM, N1>::NT, R>::value)) k_lin_rt(KArgs a) {
+  typedef LinShape<DIM, N1> S;
+  typedef LinOff<N1> O;
+  typedef Geo<DIM> G;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NF = S::NF, NE = S::NE, NT = S::NT, GEO = S::GEO;
+  typedef typename AccOf<R>::type A;
+  if (a.skip && *a.skip) return;
+  const int e0 = blockIdx.x * NE;
+  const int ne = min(NE, a.E - e0);
+  if (!cta_active(a, e0, ne)) return;
+  __shared__ R M1s[N1 * N1];
+  __shared__ R AB[NE][DIM][2];        // a_k s_k, b_k
+  __shared__ R W[NE][DIM][N1 * N1];   // W_k = -a_k s_k (C Dn) + b_k C
+  __shared__ R WL[NE][DIM][2][N1];    // -a_k s_k (C L0), +a_k s_k (C Lp)
+  __shared__ R FC[NE][NF][3];         // per face: kappa/2 sJ n_k, tau sJ, sJ beta.n
+  __shared__ R DJ[NE];                // a0/dt det J
+  __shared__ unsigned char FK[NE][NF];  // bit 0: the face has a neighbour; bit 1: beta.n >= 0
+  __shared__ R Vs[NE][NPE];
+  __shared__ R Ds[NE][NF][NFN];       // Delta_f (as in the q-stage)
+  __shared__ R Tk[NE][DIM][NPE];      // X, Y, Z (face fluxes first)
+  __shared__ R Gk[NE][2][NPE];        // axis-2 inputs (3-D)
+  const int t = threadIdx.x;
+  const auto* lo = lin_ops<R>(a);
+  for (int i = t; i < N1 * N1; i += NT) M1s[i] = R(lo[O::M1 + i]);
+  for (int i = t; i < ne * DIM; i += NT) {
+    const int el = i / DIM, k = i % DIM;
+    const double* g = a.geo + (size_t)(e0 + el) * GEO;
+    const ModelParams mp = elem_mp(a, e0 + el);
+    const double sk = g[G::JINV + k * (DIM + 1)], dj = g[G::DETJ];
+    const double bk = k == 0 ? mp.beta[0] : (k == 1 ? mp.beta[1] : mp.beta[DIM - 1]);
+    AB[el][k][0] = R(mp.kappa * dj * sk * sk);
+    AB[el][k][1] = CONV ? R(dj * sk * bk) : R(0);
+  }
+  for (int i = t; i < ne * NF; i += NT) {
+    const int el = i / NF, f = i % NF, k = f >> 1;
+    const double* g = a.geo + (size_t)(e0 + el) * GEO + G::FACE + f * (DIM + 1);
+    const ModelParams mp = elem_mp(a, e0 + el);
+    const double bk = k == 0 ? mp.beta[0] : (k == 1 ? mp.beta[1] : mp.beta[DIM - 1]);
+    const double nk = k == 0 ? g[0] : (k == 1 ? g[1] : g[DIM - 1]);
+    const double sj = g[DIM], bn = bk * nk;
+    FC[el][f][0] = R(0.5 * mp.kappa * sj * nk);
+    FC[el][f][1] = R(mp.tau * sj);
+    FC[el][f][2] = CONV ? R(sj * bn) : R(0);
+    FK[el][f] = (a.nbr[(size_t)(e0 + el) * NF + f] >= 0 ? 1 : 0) | (!CONV || bn >= 0.0 ? 2 : 0);
+  }
+  for (int i = t; i < ne; i += NT) DJ[i] = R(a.a0dt * a.geo[(size_t)(e0 + i) * GEO + G::DETJ]);
+  const double* v = (const double*)a.u;
+  const QT* qt = (const QT*)a.q;
+  const bool tterm = a.a0dt != 0.0;
+  const int e = t / NPE, n = t - e * NPE;
+  const bool own = e < ne;
+  const int id[3] = {n % N1, (n / N1) % N1, DIM == 3 ? n / (N1 * N1) : 0};
+  constexpr int STR[3] = {1, N1, N1 * N1};
+  // the neighbour's v and q_k at this thread's face items, loaded before the first barrier
+  constexpr int NFI = NE * NF * NFN, ROUNDS = (NFI + NT - 1) / NT;
+  R vpre[ROUNDS], qpre[ROUNDS];
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    vpre[r] = R(0);
+    qpre[r] = R(0);
+    if (it < NFI) {
+      const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+      if (el < ne) {
+        const int nb = a.nbr[(size_t)(e0 + el) * NF + f];
+        if (nb >= 0) {
+          const int code = a.nbf[(size_t)(e0 + el) * NF + f];
+          const int jn = a.perm[(code >> 3) * NFN + j];
+          vpre[r] = R(v[(size_t)nb * NPE + lin_face_node<DIM, N1>(code & 7, jn)]);
+          qpre[r] = R(qt[((size_t)nb * NF + (code & 7)) * NFN + jn]);
+        }
+      }
+    }
+  }
+  if (own) Vs[e][n] = R(v[(size_t)(e0 + e) * NPE + n]);
+  __syncthreads();
+
+  // ---- phase 0: the element operators W_k and the lift coefficients; Delta and sJ fhat
+  // at the face nodes (-sJ fhat into the accumulator of the face's axis); zero X, Y, Z
+  // off the faces of their axis
+  for (int i = t; i < ne * DIM * N1 * N1; i += NT) {
+    const int el = i / (DIM * N1 * N1), k = (i / (N1 * N1)) % DIM, c = i % (N1 * N1);
+    const R as = AB[el][k][0], bk = AB[el][k][1];
+    W[el][k][c] = bk * R(lo[O::C + c]) + (-(as * R(lo[O::CD + c])));
+    if (c < 2 * N1) WL[el][k][c / N1][c % N1] = R((c < N1 ? -as : as) * R(lo[O::CL + c]));
+  }
+  if (own) {
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+      if (id[k] != 0 && id[k] != N1 - 1) Tk[e][k][n] = R(0);
+  }
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int it = t + r * NT;
+    if (it >= NFI) break;
+    const int j = it % NFN, f = (it / NFN) % NF, el = it / (NFN * NF);
+    if (el >= ne) continue;
+    const int node = lin_face_node<DIM, N1>(f, j);
+    const R qm = R(qt[(size_t)e0 * NF * NFN + it]);
+    const R* fc = FC[el][f];
+    const int fk = FK[el][f];
+    const bool nb = fk & 1;
+    const R vm = Vs[el][node];
+    const R dv = vm - vpre[r];
+    Ds[el][f][j] = nb ? dv * R(0.5) : vm;
+    A s = A(fc[1] * dv);
+    s += fc[0] * (qm + (nb ? qpre[r] : qm));
+    if (CONV) s += fc[2] * ((fk & 2) ? vm : vpre[r]);
+    Tk[el][f >> 1][node] = -R(s);
+  }
+  __syncthreads();
+
+  // ---- phase 1: W_k along each axis onto the face values, the lift of Delta, and the
+  // time term's M1 along axis 0
+  if (own) {
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const R* wr = &W[e][k][id[k] * N1];
+      const R* line = &Vs[e][n - id[k] * STR[k]];
+      const int j = lin_face_index<DIM, N1>(k, id);
+      A acc = A(Tk[e][k][n]);
+      acc += WL[e][k][0][id[k]] * Ds[e][2 * k][j];
+      acc += WL[e][k][1][id[k]] * Ds[e][2 * k + 1][j];
+#pragma unroll
+      for (int m = 0; m < N1; ++m) acc += wr[m] * line[m * STR[k]];
+      if (k == 0 && tterm) {
+        const R* mr = M1s + id[0] * N1;
+        A h = A(0);
+#pragma unroll
+        for (int m = 0; m < N1; ++m) h += mr[m] * line[m];
+        acc -= DJ[e] * R(h);
+      }
+      Tk[e][k][n] = R(acc);
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2: M1 along axis 1 of X and Z, along axis 0 of Y
+  R rv = R(0);
+  if (own) {
+    const R* m1 = M1s + id[1] * N1;
+    const R* m0 = M1s + id[0] * N1;
+    const int b1 = n - id[1] * N1, b0 = n - id[0];
+    A s = A(0);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) {
+      s += m1[m] * Tk[e][0][b1 + m * N1];
+      s += m0[m] * Tk[e][1][b0 + m];
+    }
+    if constexpr (DIM == 2) {
+      rv = -R(s);
+    } else {
+      A z = A(0);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) z += m1[m] * Tk[e][2][b1 + m * N1];
+      Gk[e][0][n] = R(s);
+      Gk[e][1][n] = R(z);
+    }
+  }
+  // ---- phase 3 (3-D): M1 along axis 2 of M1_y X + M1_x Y, along axis 0 of M1_y Z
+  if constexpr (DIM == 3) {
+    __syncthreads();
+    if (own) {
+      const R* m2 = M1s + id[2] * N1;
+      const R* m0 = M1s + id[0] * N1;
+      const int b2 = n - id[2] * N1 * N1, b0 = n - id[0];
+      A s = A(0);
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        s += m2[m] * Gk[e][0][b2 + m * N1 * N1];
+        s += m0[m] * Gk[e][1][b0 + m];
+      }
+      rv = -R(s);
+    }
+  }
+  if (own) ((double*)a.out)[(size_t)(e0 + e) * NPE + n] = (double)rv;
+}
+
+// Both stages of the J.v: v -> q(v) in qbuf (QT), then J v (CART: the trace form for
+// axis-aligned boxes, q_k at the face nodes in qbuf).
 template <int DIM, int N1, bool CONV, class R, class QT, bool CART>
 cudaError_t launch_lin(const KArgs& a, void* qbuf, cudaStream_t s) {
   typedef LinShape<DIM, N1> S;
@@ -407,13 +652,15 @@ cudaError_t launch_lin(const KArgs& a, void* qbuf, cudaStream_t s) {
   const int grid = (a.E + S::NE - 1) / S::NE;
   KArgs b = a;
   b.out = qbuf;
-  k_lin_q<DIM, N1, R, QT, CART><<<grid, S::NT, 0, s>>>(b);
+  if constexpr (CART) k_lin_qt<DIM, N1, R, QT><<<grid, S::NT, 0, s>>>(b);
+  else k_lin_q<DIM, N1, R, QT><<<grid, S::NT, 0, s>>>(b);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   b = a;
   b.q = qbuf;
-  k_lin_r<DIM, N1, CONV, R, QT, CART><<<grid, S::NT, 0, s>>>(b);
+  if constexpr (CART) k_lin_rt<DIM, N1, CONV, R, QT><<<grid, S::NT, 0, s>>>(b);
+  else k_lin_r<DIM, N1, CONV, R, QT><<<grid, S::NT, 0, s>>>(b);
   count_launch();
   return cudaGetLastError();
 }
