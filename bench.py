@@ -92,19 +92,42 @@ def _dist():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms in a thread."""
+    """SM clock and clock-event (throttle) reasons during the timed region: read through
+    NVML every 5 ms in a thread (a timed region can be a few tens of milliseconds), or from
+    `nvidia-smi -lms 200` when NVML cannot be loaded."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, index: int, period_s: float = 0.005):
+        # NVML numbers the GPUs of the machine; CUDA_VISIBLE_DEVICES may renumber them
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [x.strip() for x in vis.split(",") if x.strip()]
+        self.index = int(ids[index]) if index < len(ids) and ids[index].isdigit() else index
+        self.period = period_s
         self.proc = None
         self.lines = []
+        self.samples = []
         self.thread = None
+        self.halt = threading.Event()
+        self.nvml = None
 
     def start(self):
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            handle = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            self.nvml = (pynvml, handle)
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            while not self.samples and self.thread.is_alive():
+                time.sleep(0.001)
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -115,11 +138,39 @@ class ClockSampler:
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
 
+    def _poll(self):
+        nv, h = self.nvml
+        bits = (nv.nvmlClocksEventReasonHwSlowdown, nv.nvmlClocksEventReasonHwThermalSlowdown,
+                nv.nvmlClocksEventReasonSwThermalSlowdown, nv.nvmlClocksEventReasonSwPowerCap)
+        while not self.halt.is_set():
+            try:
+                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+                smax = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+                r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+            except Exception:
+                return
+            self.samples.append((float(sm), float(smax), [nm for nm, b in zip(self.NAMES, bits) if r & b]))
+            self.halt.wait(self.period)
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            self.halt.set()
+            self.thread.join(timeout=5)
+            # the first sample is taken before the work starts: keep the ones under load
+            loaded = self.samples[1:] or self.samples
+            sm = [x[0] for x in loaded]
+            smax = [x[1] for x in loaded]
+            reasons = {nm for x in loaded for nm in x[2]}
+            try:
+                self.nvml[0].nvmlShutdown()
+            except Exception:
+                pass
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                    "reasons": sorted(reasons), "samples": len(sm), "source": "NVML, every 5 ms"}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -128,7 +179,6 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 8:
@@ -138,11 +188,11 @@ class ClockSampler:
                 smax.append(float(parts[1]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[4:8]):
+            for nm, val in zip(self.NAMES, parts[4:8]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, every 200 ms"}
 
 
 def aggregate(local_times_ms, local_jv_dofs, world, rank):

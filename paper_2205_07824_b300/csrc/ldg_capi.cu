@@ -1777,7 +1777,7 @@ int ldg_jvp_prec(ldg_ctx* ctx, int precision, const double* u, const double* v, 
 // thread per line in FP32 and float pairs, one per node in FP64)
 static std::string nodal_names(const ldg_ctx* ctx, int precision) {
   if (ctx->etype == LDG_TRI || ctx->etype == LDG_TET) return "k_sim_q + k_sim_r [";
-  if (ctx->etype == LDG_HEX && precision != LDG_FP64) return "k_hex_q + k_hex_r [";
+  if (ctx->etype == LDG_HEX && precision != LDG_FP64) return ctx->lin_cart ? "k_hex_qt + k_hex_rt [" : "k_hex_q + k_hex_r [";
   return ctx->lin_cart ? "k_lin_qt + k_lin_rt [" : "k_lin_q + k_lin_r [";
 }
 
