@@ -113,15 +113,31 @@ class ClockSampler:
         self.thread = None
         self.halt = threading.Event()
         self.nvml = None
+        self.nvml_error = None
+
+    # NVML's clock-event reason bits (nvml.h) and its SM clock domain
+    BITS = (0x8, 0x40, 0x20, 0x4)   # hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+    CLOCK_SM = 1
+
+    def _open_nvml(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit_v2 failed")
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0 and \
+                lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(0), ctypes.byref(h)) != 0:
+            raise OSError("nvmlDeviceGetHandleByIndex_v2 failed")
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, reasons
 
     def start(self):
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            handle = pynvml.nvmlDeviceGetHandleByIndex(self.index)
-            self.nvml = (pynvml, handle)
-        except Exception:
+            self.nvml = self._open_nvml()
+        except Exception as exc:
             self.nvml = None
+            self.nvml_error = repr(exc)[:200]
         if self.nvml is not None:
             self.thread = threading.Thread(target=self._poll, daemon=True)
             self.thread.start()
@@ -139,17 +155,17 @@ class ClockSampler:
         self.thread.start()
 
     def _poll(self):
-        nv, h = self.nvml
-        bits = (nv.nvmlClocksEventReasonHwSlowdown, nv.nvmlClocksEventReasonHwThermalSlowdown,
-                nv.nvmlClocksEventReasonSwThermalSlowdown, nv.nvmlClocksEventReasonSwPowerCap)
+        import ctypes
+        lib, h, get_reasons = self.nvml
+        sm, smax, r = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
         while not self.halt.is_set():
-            try:
-                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
-                smax = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
-                r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-            except Exception:
+            if (lib.nvmlDeviceGetClockInfo(h, self.CLOCK_SM, ctypes.byref(sm)) != 0 or
+                    lib.nvmlDeviceGetMaxClockInfo(h, self.CLOCK_SM, ctypes.byref(smax)) != 0 or
+                    get_reasons(h, ctypes.byref(r)) != 0):
+                self.nvml_error = "an NVML query failed"
                 return
-            self.samples.append((float(sm), float(smax), [nm for nm, b in zip(self.NAMES, bits) if r & b]))
+            self.samples.append((float(sm.value), float(smax.value),
+                                 [nm for nm, b in zip(self.NAMES, self.BITS) if r.value & b]))
             self.halt.wait(self.period)
 
     def _read(self):
@@ -169,8 +185,11 @@ class ClockSampler:
                 self.nvml[0].nvmlShutdown()
             except Exception:
                 pass
-            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                    "reasons": sorted(reasons), "samples": len(sm), "source": "NVML, every 5 ms"}
+            out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                   "reasons": sorted(reasons), "samples": len(sm), "source": "NVML, every 5 ms"}
+            if self.nvml_error:
+                out["nvml_error"] = self.nvml_error
+            return out
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -191,8 +210,11 @@ class ClockSampler:
             for nm, val in zip(self.NAMES, parts[4:8]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, every 200 ms"}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+               "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, every 200 ms"}
+        if self.nvml_error:
+            out["nvml_error"] = self.nvml_error
+        return out
 
 
 def aggregate(local_times_ms, local_jv_dofs, world, rank):
