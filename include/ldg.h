@@ -285,6 +285,23 @@ const char* ldg_jv_describe(const ldg_ctx* ctx, int precision);
  * nonlinear model, bad precision), LDG_ERR_CUDA. */
 int ldg_jvp_host(ldg_ctx* ctx, int precision, const double* u_host, const double* v_host, double* jv_host);
 
+/* J(u) v_i for `count` directions in HOST memory (the end-to-end form of a sequence of
+ * Jacobian-vector products of Section 3.3, e.g. for a Krylov method that keeps its
+ * vectors on the host), with the copies of each direction overlapped with the J.v of its
+ * neighbours: v_host[i] is copied in on one copy stream while the J.v of direction i - 1
+ * runs on the context's stream and J(u) v_{i-2} is copied out to jv_host[i] on another,
+ * through two device slots. Each result equals ldg_jvp_host's for that direction.
+ * u_host: as in ldg_jvp_host (copied once). v_host[i], jv_host[i]: n_dof doubles of host
+ * memory each, caller-owned; pinned (page-locked) memory lets the copies run beside the
+ * kernels, pageable memory gives the same results without the overlap. Outputs are
+ * written in order, so several jv_host[i] may name one buffer (it keeps the last); an
+ * output buffer must not be the input of a later direction. The call returns after the
+ * last copy back has finished. The first call allocates 5 n_dof doubles of context
+ * staging memory, two streams and six events. Errors: LDG_ERR_ARG (count < 1, null
+ * arrays or entries, NULL u_host for a nonlinear model, bad precision), LDG_ERR_CUDA. */
+int ldg_jvp_host_many(ldg_ctx* ctx, int precision, const double* u_host, int count, const double* const* v_host,
+                      double* const* jv_host);
+
 /* J(u) v reusing the q(u) that the last ldg_residual(ctx, u, ...) call on this context
  * computed: the form of J.v inside Newton-GMRES, where every Krylov product of a
  * Newton step is taken at the state whose residual was just evaluated. Nonlinear

@@ -1393,7 +1393,14 @@ int ldg_destroy(ldg_ctx* ctx) {
   cudaFree(ctx->d_flags); cudaFree(ctx->d_ticket); cudaFree(ctx->d_t);
   cudaFree(ctx->d_colour); cudaFree(ctx->d_blocks); cudaFree(ctx->d_binv); cudaFree(ctx->d_Z);
   cudaFree(ctx->d_probe); cudaFree(ctx->d_jp); cudaFree(ctx->d_status);
-  cudaFree(ctx->d_stage); cudaFree(ctx->d_lops); cudaFree(ctx->d_lopsf);
+  cudaFree(ctx->d_stage); cudaFree(ctx->d_lops); cudaFree(ctx->d_lopsf); cudaFree(ctx->d_stage_many);
+  if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
+  if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
+  for (int k = 0; k < 2; ++k) {
+    if (ctx->ev_in[k]) cudaEventDestroy(ctx->ev_in[k]);
+    if (ctx->ev_done[k]) cudaEventDestroy(ctx->ev_done[k]);
+    if (ctx->ev_out[k]) cudaEventDestroy(ctx->ev_out[k]);
+  }
   cudaFree(ctx->d_halo); cudaFree(ctx->d_pcz); cudaFree(ctx->d_pch);
   cudaFree(ctx->d_shq); cudaFree(ctx->d_shpart); cudaFree(ctx->d_shdot);
   cudaFree(ctx->d_er_xi); cudaFree(ctx->d_er_w); cudaFree(ctx->d_er_B); cudaFree(ctx->d_er_P); cudaFree(ctx->d_l2);
@@ -1827,6 +1834,59 @@ int ldg_jvp_host(ldg_ctx* ctx, int precision, const double* u_host, const double
   int rc = jvp_args(ctx, base_args(ctx), u_host ? du : dv, dv, djv, precision);
   if (rc) return rc;
   CK(cudaMemcpyAsync(jv_host, djv, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LDG_OK;
+}
+
+int ldg_jvp_host_many(ldg_ctx* ctx, int precision, const double* u_host, int count, const double* const* v_host,
+                      double* const* jv_host) {
+  if (!ctx || !ctx->ks || count < 1 || !v_host || !jv_host || !jv_precision_ok(precision)) return LDG_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (!v_host[i] || !jv_host[i]) return fail(ctx, LDG_ERR_ARG, "ldg_jvp_host_many: null direction or output");
+  if (!u_host && !ctx->ks->linear)
+    return fail(ctx, LDG_ERR_ARG, "ldg_jvp_host_many: u_host may be NULL only for linear models");
+  const size_t n = (size_t)ctx->ndof, bytes = n * sizeof(double);
+  if (!ctx->d_stage_many) CK(cudaMalloc(&ctx->d_stage_many, 5 * bytes));
+  if (!ctx->s_in) {
+    CK(cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaEventCreateWithFlags(&ctx->ev_in[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_done[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_out[k], cudaEventDisableTiming));
+    }
+  }
+  double* du = ctx->d_stage_many;
+  double* dv[2] = {du + n, du + 2 * n};
+  double* djv[2] = {du + 3 * n, du + 4 * n};
+  // the copy streams start after the work already queued on the context's stream
+  CK(cudaEventRecord(ctx->ev_done[0], ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->s_in, ctx->ev_done[0], 0));
+  CK(cudaStreamWaitEvent(ctx->s_out, ctx->ev_done[0], 0));
+  if (u_host) CK(cudaMemcpyAsync(du, u_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  for (int i = 0; i < count; ++i) {
+    const int s = i & 1;
+    // slot s: its v is free once the J.v of direction i - 2 has run, its J.v once that
+    // result has been copied out
+    if (i >= 2) CK(cudaStreamWaitEvent(ctx->s_in, ctx->ev_done[s], 0));
+    CK(cudaMemcpyAsync(dv[s], v_host[i], bytes, cudaMemcpyHostToDevice, ctx->s_in));
+    CK(cudaEventRecord(ctx->ev_in[s], ctx->s_in));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_in[s], 0));
+    if (i >= 2) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_out[s], 0));
+    int rc = jvp_args(ctx, base_args(ctx), u_host ? du : dv[s], dv[s], djv[s], precision);
+    if (rc) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaStreamSynchronize(ctx->s_in);
+      cudaStreamSynchronize(ctx->s_out);
+      return rc;
+    }
+    CK(cudaEventRecord(ctx->ev_done[s], ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->s_out, ctx->ev_done[s], 0));
+    CK(cudaMemcpyAsync(jv_host[i], djv[s], bytes, cudaMemcpyDeviceToHost, ctx->s_out));
+    CK(cudaEventRecord(ctx->ev_out[s], ctx->s_out));
+  }
+  CK(cudaStreamSynchronize(ctx->s_out));
+  CK(cudaStreamSynchronize(ctx->s_in));
   CK(cudaStreamSynchronize(ctx->stream));
   return LDG_OK;
 }

@@ -72,6 +72,11 @@ struct ldg_ctx {
   double *d_shq = nullptr, *d_shpart = nullptr, *d_shdot = nullptr;
   std::vector<double> h_shdot;
   double* d_stage = nullptr;   // ldg_jvp_host: device copies of u, v and J.v (3 n_dof, first use)
+  // ldg_jvp_host_many: u, two (v, J.v) slots (5 n_dof), the copy-in and copy-out streams and
+  // per-slot events (copied in, J.v done, copied out); created on first use
+  double* d_stage_many = nullptr;
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   // L2 projection / error rule (built on first use): points, weights, basis values,
   // projection operator, and per-element error partials [E][4]
   int er_nqp = 0;

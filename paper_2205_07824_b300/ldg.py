@@ -161,6 +161,8 @@ def lib():
         L.ldg_interpolate.argtypes = [vp, ctypes.c_double, dp]
         L.ldg_project.argtypes = [vp, ctypes.c_double, dp]
         L.ldg_jvp_host.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+        L.ldg_jvp_host_many.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p)]
         L.ldg_jv_describe.restype = ctypes.c_char_p
         L.ldg_jv_describe.argtypes = [vp, ctypes.c_int]
         L.ldg_l2_error.argtypes = [vp, dp, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
@@ -512,19 +514,34 @@ class LDG:
         """The kernels that form this operator's J.v in `precision` (``ldg_jv_describe``)."""
         return lib().ldg_jv_describe(self._h, int(precision)).decode()
 
+    def _host_ptr(self, a, name):
+        if a is None:
+            return None
+        ok = a.dtype == np.float64 and a.size == self.n_dof if isinstance(a, np.ndarray) else \
+            (not a.is_cuda and str(a.dtype) == "torch.float64" and a.numel() == self.n_dof and a.is_contiguous())
+        if not ok or (isinstance(a, np.ndarray) and not a.flags.c_contiguous):
+            raise TypeError(f"{name}: expected a contiguous float64 host array of n_dof elements")
+        return ctypes.c_void_p(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
+
     def jvp_host(self, precision, u, v, out):
         """J(u) v with HOST buffers (``ldg_jvp_host``): u (or None for linear models), v and
         out are contiguous float64 numpy arrays or CPU tensors of n_dof entries."""
-        def hp(a, name):
-            if a is None:
-                return None
-            ok = a.dtype == np.float64 and a.size == self.n_dof if isinstance(a, np.ndarray) else \
-                (not a.is_cuda and str(a.dtype) == "torch.float64" and a.numel() == self.n_dof and a.is_contiguous())
-            if not ok or (isinstance(a, np.ndarray) and not a.flags.c_contiguous):
-                raise TypeError(f"{name}: expected a contiguous float64 host array of n_dof elements")
-            return ctypes.c_void_p(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
+        hp = self._host_ptr
         self._check(lib().ldg_jvp_host(self._h, int(precision), hp(u, "u"), hp(v, "v"), hp(out, "out")))
         return out
+
+    def jvp_host_many(self, precision, u, vs, outs):
+        """J(u) v_i for a sequence of directions in HOST memory (``ldg_jvp_host_many``): the
+        copies of each direction run beside the J.v of its neighbours. vs and outs are
+        equal-length sequences of contiguous float64 host arrays (numpy or CPU tensors,
+        pinned for the overlap); an output must not be the input of a later direction."""
+        if len(vs) != len(outs) or not vs:
+            raise ValueError("vs and outs: equal, non-zero lengths")
+        k = len(vs)
+        pv = (ctypes.c_void_p * k)(*[self._host_ptr(v, "v") for v in vs])
+        po = (ctypes.c_void_p * k)(*[self._host_ptr(o, "out") for o in outs])
+        self._check(lib().ldg_jvp_host_many(self._h, int(precision), self._host_ptr(u, "u"), k, pv, po))
+        return outs
 
     def project(self, t: float = 0.0, out=None):
         """L2 projection of the analytic case at time t (``ldg_project``)."""

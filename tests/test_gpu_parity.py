@@ -325,6 +325,36 @@ def test_host_buffer_solve_equals_device_solve():
     assert (rh["newton_iters"], rh["gmres_iters"], rh["status"]) == (rd["newton_iters"], rd["gmres_iters"], 0)
 
 
+@pytest.mark.parametrize("model,prec", [(oracle.EULER, 0), (oracle.NS, 1), (oracle.CONVDIFF, 0), (oracle.CONVDIFF, 2)])
+def test_host_many_jvp_equals_device_jvp(model, prec):
+    """ldg_jvp_host_many (directions in pinned host memory, copies overlapped with the J.v
+    of the neighbouring directions through two device slots) gives, for each of five
+    directions, the bits of ldg_jvp_prec on device buffers; outputs that share one host
+    buffer keep the last direction's result; the FP64 result meets the oracle."""
+    import torch
+    if model == oracle.CONVDIFF:
+        mesh, p, case = synth.hex_box((3, 4, 3)), 3, oracle.CASE_EXPSIN
+    else:
+        mesh, p, case = synth.quad_box((6, 5), hi=(10.0, 10.0), periodic=(True, True)), 3, oracle.CASE_VORTEX
+    o, g = pair(mesh, p, model, case, gmres_m=2)
+    u = synth.random_euler_state(mesh.n_elem, o.npe, 21) if model in (oracle.EULER, oracle.NS) else \
+        synth.random_vector(o.ndof, 21)
+    vs = [torch.from_numpy(synth.random_vector(o.ndof, 30 + i)).pin_memory() for i in range(5)]
+    outs = [torch.full((o.ndof,), float("nan"), dtype=torch.float64).pin_memory() for _ in range(4)]
+    uh = None if model == oracle.CONVDIFF else torch.from_numpy(u).pin_memory()
+    g.jvp_host_many(prec, uh, vs, outs + [outs[0]])    # the fifth result overwrites the first
+    for i, v in enumerate(vs):
+        ref = host(g.jvp_prec(prec, cuda(u), cuda(v.numpy())))
+        got = outs[0].numpy() if i in (0, 4) else outs[i].numpy()
+        if i == 0:
+            continue
+        assert np.array_equal(got, ref), (i, np.abs(got - ref).max())
+        if prec == 0:
+            assert_parity(got, o.jvp(u, v.numpy()), what=f"host-many J.v direction {i}")
+    with pytest.raises(RuntimeError):
+        g.jvp_host_many(prec, uh, vs[:0] + [vs[0]], [None])
+
+
 @pytest.mark.parametrize("model", [oracle.EULER, oracle.NS, oracle.CONVDIFF])
 def test_finite_difference_jvp(model):
     """The FD variant against the exact J.v: the forward difference is off by O(eps),
