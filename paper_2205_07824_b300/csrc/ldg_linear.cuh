@@ -34,7 +34,7 @@ namespace ldg {
 // the products C Dn, C L0 and C L1 (for the residual of axis-aligned boxes).
 template <int N1> struct LinOff {
   static constexpr int DN = 0, M1 = N1 * N1, C = 2 * N1 * N1, L = 3 * N1 * N1, SIZE = 3 * N1 * N1 + 2 * N1;
-  static constexpr int CD = SIZE, CL = CD + N1 * N1, SIZE_T = CL + 2 * N1;
+  static constexpr int CD = SIZE, CL = CD + N1 * N1;
 };
 
 // Elements per CTA (one thread per node, elements packed back to back) and threads.
