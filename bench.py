@@ -469,8 +469,28 @@ def run_jv(args):
             g.jvp_host(0, None, hv[0], ho[0])
         t1 = time.perf_counter() - t0
         tmax1, e2e1 = aggregate([t1 * 1e3], n * k1, world, rank)
+        # the host link's own time for one step's copies: 8 n bytes in and 8 n out, on two
+        # streams at once (what bounds the overlapped calls)
+        sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+        da = torch.empty(n, dtype=torch.float64, device="cuda")
+        link = []
+        for rep in range(6):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(sa):
+                da.copy_(hv[0], non_blocking=True)
+            with torch.cuda.stream(sb):
+                ho[1].copy_(v, non_blocking=True)
+            torch.cuda.synchronize()
+            if rep >= 2:
+                link.append((time.perf_counter() - t0) * 1e3)
+        del da
+        link_ms = statistics.median(link)
         e2e = {"value": e2e_gdofs, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                "steps": k2, "ms_per_step": tmax / k2,
+               "host_link": {"copies_ms": link_ms, "frac": link_ms / (tmax / k2),
+                             "what": "one step's copies alone (8 n bytes in, 8 n out, two streams at once), "
+                                     "median of 4; frac = that time / ms_per_step"},
                "call": "ldg_jvp_host_many (FP64): one call over the K step directions, each copied in from "
                        "pinned host memory and its J.v copied back, the copies of a step overlapped with the J.v "
                        "of its neighbours (two device slots, copy-in and copy-out streams); host wall clock "

@@ -115,7 +115,7 @@ CART_MESHES = [
     # p = 1: every node lies on a face of every axis
     ("quad_turned_p1", lambda: _turn_some(synth.quad_box((5, 4), periodic=(True, False))), 1, oracle.CONVDIFF),
     ("hex_turned_p1", lambda: _turn_some(synth.hex_box((3, 3, 2), periodic=(False, True, False))), 1, oracle.CONVDIFF),
-    ("hex_box_p5", lambda: synth.hex_box((2, 3, 2), hi=(1.0, 1.5, 0.5)), 5, oracle.POISSON),
+    ("hex_box_p5", lambda: synth.hex_box((2, 3, 2), hi=(1.0, 1.5, 0.5)), 5, oracle.CONVDIFF),
 ]
 
 
