@@ -532,6 +532,36 @@ def run_jv(args):
         dist.destroy_process_group()
 
 
+def run_mlp_probe(args):
+    """The learned preconditioner's tensor-core inference for profilers and timing: the
+    network of a 256 x 256 quadrilateral Euler mesh at p = 3 (65,536 element rows, n = 64,
+    hidden width 128; three tcgen05 GEMMs per apply), `warmup` untimed and `steps` timed
+    applications (CUDA events on the launching stream); prints the time per apply."""
+    import torch
+    from paper_2205_07824_b300 import synth
+    from paper_2205_07824_b300.ldg import LDG, EULER, CASE_VORTEX
+    mesh = synth.quad_box(256, hi=(10.0, 10.0), periodic=(True, True))
+    g = LDG(mesh, 3, EULER, CASE_VORTEX, (1.4,), gmres_m=1)
+    g.mlp_init(seed=1)
+    u = g.interpolate(0.0)
+    x = torch.randn(g.n_dof, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(2))
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 1)):
+        g.mlp_apply(u, x, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.mlp_apply(u, x, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": "learned preconditioner inference, 65,536 element rows (256 x 256 quadrilaterals, "
+                               "Euler p = 3), three tcgen05 GEMMs per apply",
+                      "ms_per_apply": e0.elapsed_time(e1) / max(args.steps, 1), "applies": args.steps,
+                      "finite": bool(torch.isfinite(out).all().item())}))
+
+
 def run_jv_probe(args):
     """The default workload's J.v for profilers: the same context with a one-column Krylov
     space (about 1.5 GB on the device), no autotuning, `warmup + steps` FP64 J.v applications
@@ -1501,7 +1531,8 @@ def main():
                          "graph's WHILE nodes (same kernels; for profilers that do not follow graph nodes)")
     ap.add_argument("--no-solve", action="store_true", help="jv: skip the vortex time-to-1e-8 comparison")
     ap.add_argument("--workload", default="jv",
-                    choices=["jv", "jvprobe", "vortex", "batch", "hex", "tri", "cylinder", "tet", "wave", "tcprobe"],
+                    choices=["jv", "jvprobe", "vortex", "batch", "hex", "tri", "cylinder", "tet", "wave", "tcprobe",
+                             "mlpprobe"],
                     help="jv (default): the FP64 J.v of 48^3 p=4 convection-diffusion; jvprobe: its J.v "
                          "applications alone, for profilers; "
                          "vortex: the 64x64 p=3 Euler BDF2 step; batch: 256 parametrised convection-diffusion "
@@ -1509,6 +1540,7 @@ def main():
                          "tri: the same sweep on 131,072 triangles; "
                          "cylinder: Navier-Stokes past a cylinder on 40,000 curved quads, learned + mixed vs "
                          "plain FP64 block-Jacobi; tet: Table 3's Poisson problem on tetrahedra, 1/n = 32, p = 3; "
+                         "mlpprobe: the learned preconditioner's tensor-core inference on 65,536 rows; "
                          "wave: DIRK34 steps of the wave model on 48^3 hexahedra, p = 4; tcprobe: the Euler J.v "
                          "in FP64, FP32 and with tensor-core contractions on square vortex meshes")
     ap.add_argument("--tc-sides", default="64,128,256,512", help="tcprobe: square mesh sides")
@@ -1556,6 +1588,9 @@ def main():
         return
     if args.workload == "tcprobe":
         run_tc_probe(args)
+        return
+    if args.workload == "mlpprobe":
+        run_mlp_probe(args)
         return
 
     import numpy as np

@@ -891,7 +891,7 @@ int tc_gemm(ldg_ctx* ctx, int a1, int b1, int a2, int b2, int N, int K1, int K2,
   TcGemmArgs g;
   g.M = (int)ctx->E; g.N = N; g.K1 = K1; g.K2 = K2; g.bias = bias; g.relu = relu; g.C = C; g.ldc = ldc;
   g.out_bf16 = out_bf16; g.err = M.d_err; g.skip = skip;
-  const size_t smem = tc_gemm_smem(N, K1, K2);
+  const size_t smem = tc_gemm_smem(N, K1, K2, out_bf16);
   static int smem_set = 0;
   if (smem_set < (int)smem) {
     CK(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));

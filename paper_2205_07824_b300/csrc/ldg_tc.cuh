@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   __shared__ __align__(8) uint64_t bar_tma, bar_mma;
   __shared__ uint32_t tmem_base;
   __shared__ int ok_s;
+  __shared__ float bias_s[256];   // the bias, read once per CTA (the epilogue reads it per column)
   const int nk1 = g.K1 / TC_BK, nk2 = g.K2 / TC_BK, nk = nk1 + nk2;
   const int N = g.N;
   const int slab_b = N * TC_BK * 2;
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ok_s = 1;
   }
+  for (int c = threadIdx.x; c < N; c += blockDim.x) bias_s[c] = g.bias ? g.bias[c] : 0.f;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -112,37 +114,50 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
       (void)mbar_wait(&bar_mma, 0);
     } else {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row = m0 + warp * 32 + lane;
+      // the warp's 32 rows go through shared memory (the operand slabs, idle once the MMAs
+      // are done): each lane writes its row there, then the warp stores whole rows, so that
+      // every 32-byte sector of the output is written once and in full
+      const int esz = g.out_bf16 ? 2 : 4;
+      const int rowb = N * esz + 16;   // 16 bytes of padding staggers the rows over the banks
+      unsigned char* stage = smem + (size_t)warp * 32 * rowb;
       const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
       for (int c0 = 0; c0 < N; c0 += 16) {
         float v[16];
         tc_ld16(lane_addr + (uint32_t)c0, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          float x = v[i];
-          if (g.bias) x += g.bias[c0 + i];
+          float x = v[i] + bias_s[c0 + i];
           if (g.relu) x = fmaxf(x, 0.f);
           v[i] = x;
         }
-        // 16-byte vector stores of the thread's 16 consecutive outputs (row strides and c0
-        // are multiples of 16 bytes)
-        if (row < g.M) {
-          if (g.out_bf16) {
-            uint32_t pk[8];
+        unsigned char* dst = stage + (size_t)lane * rowb + (size_t)c0 * esz;
+        if (g.out_bf16) {
+          uint32_t pk[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-              pk[i] = *reinterpret_cast<uint32_t*>(&b2);
-            }
-            uint4* out = reinterpret_cast<uint4*>((__nv_bfloat16*)g.C + (size_t)row * g.ldc + c0);
-            out[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            out[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-          } else {
-            float4* out = reinterpret_cast<float4*>((float*)g.C + (size_t)row * g.ldc + c0);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) out[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          for (int i = 0; i < 8; ++i) {
+            __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+            pk[i] = *reinterpret_cast<uint32_t*>(&b2);
           }
+          reinterpret_cast<uint4*>(dst)[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          reinterpret_cast<uint4*>(dst)[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            reinterpret_cast<float4*>(dst)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         }
+      }
+      __syncwarp();
+      // rows of N * esz bytes (a multiple of 32) as 16-byte pieces, consecutive lanes on
+      // consecutive pieces of a row
+      const int pieces = N * esz / 16, total = 32 * pieces;
+      unsigned char* gout = (unsigned char*)g.C;
+      const size_t ldcb = (size_t)g.ldc * esz;
+      for (int q = lane; q < total; q += 32) {
+        const int r = q / pieces, pc = q - r * pieces;
+        const int grow = m0 + warp * 32 + r;
+        if (grow < g.M)
+          *reinterpret_cast<uint4*>(gout + (size_t)grow * ldcb + (size_t)pc * 16) =
+              *reinterpret_cast<const uint4*>(stage + (size_t)r * rowb + (size_t)pc * 16);
       }
     }
   }
@@ -152,10 +167,13 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-// dynamic shared memory of k_tc_gemm (+1 KB for the 1024-byte alignment)
-inline size_t tc_gemm_smem(int N, int K1, int K2) {
+// dynamic shared memory of k_tc_gemm: the operand slabs, or the output staging of the
+// epilogue if that is larger (+1 KB for the 1024-byte alignment)
+inline size_t tc_gemm_smem(int N, int K1, int K2, int out_bf16) {
   const int nk = (K1 + K2) / TC_BK;
-  return (size_t)nk * (TC_SLAB_A + (size_t)N * TC_BK * 2) + 1024;
+  const size_t slabs = (size_t)nk * (TC_SLAB_A + (size_t)N * TC_BK * 2);
+  const size_t stage = (size_t)TC_BM * ((size_t)N * (out_bf16 ? 2 : 4) + 16);
+  return (slabs > stage ? slabs : stage) + 1024;
 }
 
 // FP32 -> BF16, row-major with independent strides (rows x cols)
