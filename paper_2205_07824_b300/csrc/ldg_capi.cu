@@ -786,9 +786,10 @@ int mlp_backward(ldg_ctx* ctx, int64_t rows) {
   return LDG_OK;
 }
 
-// prepare rows idx (or 0..rows-1) of the pair set X / T into the work buffers
+// prepare rows idx (or 0..rows-1) of the pair set X / T into the work buffers (the
+// input rows in FP32, or in BF16 into xbf for the tensor-core path)
 int mlp_prep(ldg_ctx* ctx, const double* X, const double* T, const double* U, const int* idx, int64_t rows,
-             const int* skip) {
+             const int* skip, __nv_bfloat16* xbf) {
   auto& M = ctx->mlp;
   int rc;
   if ((rc = mlp_reserve(ctx, rows))) return rc;
@@ -796,7 +797,8 @@ int mlp_prep(ldg_ctx* ctx, const double* X, const double* T, const double* U, co
     CK(cudaMemsetAsync(M.count, 0, sizeof(int), ctx->stream));
     CK(cudaMemsetAsync(M.loss, 0, sizeof(double), ctx->stream));
   }
-  k_mlp_prep<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, ctx->stream>>>(X, T, U, idx, rows, M.n, M.X, T ? M.T : nullptr,
+  k_mlp_prep<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, ctx->stream>>>(X, T, U, idx, rows, M.n, M.X, xbf,
+                                                                          T ? M.T : nullptr,
                                                                           M.mask, M.norms, skip ? nullptr : M.count,
                                                                           skip);
   count_launch();
@@ -912,20 +914,18 @@ int tc_gemm(ldg_ctx* ctx, int a1, int b1, int a2, int b2, int N, int K1, int K2,
 int mlp_apply(ldg_ctx* ctx, const double* u, const double* x, double* y, const int* skip) {
   auto& M = ctx->mlp;
   int rc;
-  if ((rc = mlp_prep(ctx, x, nullptr, u, nullptr, ctx->E, skip))) return rc;
   MlpOff o(M.n, M.h);
-  if (M.tc && M.tc_rows == ctx->E) {
+  const bool tc = M.tc && M.tc_rows == ctx->E;
+  if ((rc = mlp_prep(ctx, x, nullptr, u, nullptr, ctx->E, skip, tc ? M.Xbf : nullptr))) return rc;
+  if (tc) {
     const int n = M.n, h = M.h;
-    k_to_bf16_2d<<<std::min<int64_t>(grid_for(ctx->E * 2 * n), 148 * 8), 256, 0, ctx->stream>>>(
-        M.X, 2 * n, M.Xbf, 2 * n, ctx->E, 2 * n, skip);
-    count_launch();
     if ((rc = tc_gemm(ctx, 0, 4, -1, -1, h, 2 * n, 0, M.theta + o.b1, 1, M.H1bf, h, 1, skip))) return rc;
     if ((rc = tc_gemm(ctx, 2, 5, -1, -1, h, h, 0, M.theta + o.b2, 1, M.H2bf, h, 1, skip))) return rc;
     if ((rc = tc_gemm(ctx, 3, 6, 1, 7, n, h, n, M.theta + o.b3, 0, M.Y, n, 0, skip))) return rc;
   } else {
     mlp_forward<__nv_bfloat16>(ctx, ctx->E, M.theta_bf, M.theta, skip);
   }
-  k_mlp_unprep<<<std::min<int64_t>(grid_for(ctx->ndof), 148 * 8), 256, 0, ctx->stream>>>(M.Y, M.norms, ctx->E, M.n, y,
+  k_mlp_unprep<<<(unsigned)((ctx->E * 32 + 255) / 256), 256, 0, ctx->stream>>>(M.Y, M.norms, ctx->E, M.n, y,
                                                                                        skip);
   count_launch();
   CK(cudaGetLastError());
@@ -2288,7 +2288,7 @@ int ldg_mlp_loss_grad(ldg_ctx* ctx, const double* X, const double* T, const doub
   auto& M = ctx->mlp;
   if (!M.theta) return fail(ctx, LDG_ERR_ARG, "ldg_mlp_loss_grad: call ldg_mlp_init first");
   int rc;
-  if ((rc = mlp_prep(ctx, X, T, U, nullptr, n_pairs, nullptr))) return rc;
+  if ((rc = mlp_prep(ctx, X, T, U, nullptr, n_pairs, nullptr, nullptr))) return rc;
   mlp_forward<float>(ctx, n_pairs, M.theta, M.theta, nullptr);
   if ((rc = mlp_backward(ctx, n_pairs))) return rc;
   CK(cudaMemcpyAsync(loss, M.loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -2335,7 +2335,7 @@ int ldg_mlp_train(ldg_ctx* ctx, const double* X, const double* T, const double* 
     CK(cudaMalloc(&Gi64, (size_t)n * n * sizeof(double)));
     for (int64_t b0 = 0; b0 < n_pairs; b0 += B) {
       const int64_t rows = std::min<int64_t>(B, n_pairs - b0);
-      if ((rc = mlp_prep(ctx, X + b0 * n, T + b0 * n, U + b0 * n, nullptr, rows, nullptr))) return rc;
+      if ((rc = mlp_prep(ctx, X + b0 * n, T + b0 * n, U + b0 * n, nullptr, rows, nullptr, nullptr))) return rc;
       const int acc = b0 > 0;
       gemm<true, false, float>(ctx, n, n, (int)rows, M.X, 2 * n, M.X, 2 * n, Gm, n, nullptr, 0, nullptr, acc);
       gemm<true, false, float>(ctx, n, n, (int)rows, M.X, 2 * n, M.T, n, Cm, n, nullptr, 0, nullptr, acc);
@@ -2368,7 +2368,7 @@ int ldg_mlp_train(ldg_ctx* ctx, const double* X, const double* T, const double* 
     double acc = 0.0;
     int nb = 0;
     for (int64_t b0 = 0; b0 + B <= n_pairs; b0 += B) {
-      if ((rc = mlp_prep(ctx, X, T, U, M.idx + b0, B, nullptr))) return rc;
+      if ((rc = mlp_prep(ctx, X, T, U, M.idx + b0, B, nullptr, nullptr))) return rc;
       mlp_forward<float>(ctx, B, M.theta, M.theta, nullptr);
       if ((rc = mlp_backward(ctx, B))) return rc;
       ++M.t;

@@ -85,30 +85,43 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* 
 // Rows r < rows: Xn[r] = [X[src] / ||X[src]||, S[src]] (width 2n), Tn[r] = T[src]
 // scaled by the same norm (if T), mask[r] = (norm > tiny), norms[r] = norm;
 // *count += number of valid rows. One warp per row; src = idx[r] (idx == null: r).
+// With Xbf the row goes out in BF16 (the tensor-core operand) instead of FP32 Xn.
+// The norm is formed in FP32: the network's inputs are FP32 or BF16 anyway, and FP64
+// square roots and divisions would occupy this part's FP64 pipe for most of the kernel
+// (a row whose entries are all below about 1e-19 in magnitude reads as zero).
 __global__ void k_mlp_prep(const double* __restrict__ X, const double* __restrict__ T, const double* __restrict__ S,
                            const int* __restrict__ idx, int64_t rows, int n, float* __restrict__ Xn,
-                           float* __restrict__ Tn, float* __restrict__ mask, double* __restrict__ norms, int* count,
-                           const int* skip) {
+                           __nv_bfloat16* __restrict__ Xbf, float* __restrict__ Tn, float* __restrict__ mask,
+                           double* __restrict__ norms, int* count, const int* skip) {
   if (skip && *skip) return;
   const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
   const int64_t src = idx ? (int64_t)idx[r] : r;
   const double* x = X + src * n;
-  double s = 0.0;
-  for (int i = lane; i < n; i += 32) s += x[i] * x[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  const double nrm = sqrt(s);
-  const bool ok = nrm > 1e-30;
-  const double inv = ok ? 1.0 / nrm : 0.0;
+  float s = 0.f;
   for (int i = lane; i < n; i += 32) {
-    Xn[r * 2 * n + i] = (float)(x[i] * inv);
-    Xn[r * 2 * n + n + i] = (float)S[src * n + i];
-    if (T) Tn[r * n + i] = (float)(T[src * n + i] * inv);
+    const float xi = (float)x[i];
+    s = fmaf(xi, xi, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const float nrm = sqrtf(s);
+  const bool ok = nrm > 1e-30f;
+  const float inv = ok ? 1.f / nrm : 0.f;
+  for (int i = lane; i < n; i += 32) {
+    const float a = (float)x[i] * inv, b = (float)S[src * n + i];
+    if (Xbf) {
+      Xbf[r * 2 * n + i] = __float2bfloat16(a);
+      Xbf[r * 2 * n + n + i] = __float2bfloat16(b);
+    } else {
+      Xn[r * 2 * n + i] = a;
+      Xn[r * 2 * n + n + i] = b;
+    }
+    if (T) Tn[r * n + i] = (float)T[src * n + i] * inv;
   }
   if (lane == 0) {
     if (mask) mask[r] = ok ? 1.f : 0.f;
-    if (norms) norms[r] = nrm;
+    if (norms) norms[r] = (double)nrm;
     if (count && ok) atomicAdd(count, 1);
   }
 }
@@ -188,12 +201,15 @@ __global__ void k_f64_to_f32(const double* __restrict__ src, float* __restrict__
 }
 
 // z[r][i] = norms[r] * Y[r][i]
+// z[r] = norms[r] Y[r], one warp per row (the product in FP32, the precision of Y)
 __global__ void k_mlp_unprep(const float* __restrict__ Y, const double* __restrict__ norms, int64_t rows, int n,
                              double* __restrict__ z, const int* skip) {
   if (skip && *skip) return;
-  const int64_t total = rows * n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
-    z[i] = norms[i / n] * (double)Y[i];
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  const float nr = (float)norms[r];
+  for (int i = lane; i < n; i += 32) z[r * n + i] = (double)(nr * Y[r * n + i]);
 }
 
 }  // namespace ldg
