@@ -242,11 +242,17 @@ __global__ void __launch_bounds__(KRY_T) k_orth_update(const double* __restrict_
   }
 }
 
-// out = in / sqrt(sc[0])
+// out = in / sqrt(sc[0]) (the factor formed once per CTA: FP64 square roots and divisions
+// in every thread would cost the FP64 pipe more than the scaling)
 static __global__ void k_scale_by_norm(const double* in, const double* small_sc, double* out, int64_t n, const int* flags) {
   if (flags && flags[0]) return;
-  const double s = sqrt(small_sc[0]);
-  const double f = s > 0.0 ? 1.0 / s : 0.0;
+  __shared__ double f_s;
+  if (threadIdx.x == 0) {
+    const double s = sqrt(small_sc[0]);
+    f_s = s > 0.0 ? 1.0 / s : 0.0;
+  }
+  __syncthreads();
+  const double f = f_s;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = in[i] * f;
 }
@@ -255,8 +261,13 @@ static __global__ void k_scale_by_norm(const double* in, const double* small_sc,
 static __global__ void k_cycle_start(const double* r, double* V0, int64_t n, double* small, int m, int* flags) {
   KrySmall S{m};
   const double* sc = small + S.sc();
-  const double s = sqrt(sc[4]);
-  const double f = s > 0.0 ? 1.0 / s : 0.0;
+  __shared__ double s_s, f_s;
+  if (threadIdx.x == 0) {
+    s_s = sqrt(sc[4]);
+    f_s = s_s > 0.0 ? 1.0 / s_s : 0.0;
+  }
+  __syncthreads();
+  const double s = s_s, f = f_s;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     V0[i] = r[i] * f;
   if (blockIdx.x == 0) {
