@@ -1052,7 +1052,6 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
     k_cycle_start<<<g1, 256, 0, ctx->stream>>>(ctx->d_r, V, n, sm, m, flags);
     count_launch();
     CK(cudaGetLastError());
-    int queued = 0;
     bool stop = false;
     for (int j = 0; j < m && !stop; ++j) {
       if (j >= LAG) {
@@ -1087,9 +1086,7 @@ int do_gmres(ldg_ctx* ctx, const double* u, const double* b, double* x, double r
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(ctx->h_flags + j * 4, flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaEventRecord(ctx->ev[j], ctx->stream));
-      queued = j + 1;
     }
-    (void)queued;
     k_backsolve<<<1, 32, 0, ctx->stream>>>(sm, m, flags);
     count_launch();
     k_solution_update<<<g1, 256, 0, ctx->stream>>>(pc ? ctx->d_Z : V, n, sm, m, flags, x, n);

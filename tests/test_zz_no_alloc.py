@@ -2,7 +2,8 @@
 cannot allocate device memory at the point of the call (an application whose own
 pool or caching allocator holds all device memory, or a host loop that cannot wait
 on an allocation). Checked through the C-ABI against ldg_jvp, on two calls in a
-row, and with two contexts sharing the array. This file is collected last so that
+row, with two contexts sharing the array, and inside a global-mode stream
+capture replayed as a CUDA graph. This file is collected last so that
 a failure here cannot hide an earlier one."""
 import ctypes
 
@@ -74,3 +75,37 @@ def test_noalloc_rejects_operators_beyond_the_static_maximum():
     assert rc == -1
     msg = lib().ldg_last_error(g._h).decode()
     assert "4194304" in msg and str(g.n_dof * 3) in msg
+
+
+@pytest.mark.parametrize("which", ["convdiff_hex", "ns_quad"])
+def test_noalloc_jvp_inside_global_stream_capture(which):
+    """The entry point allocates nothing once the device's array address is known:
+    after one call outside a capture, a call inside a global-mode stream capture
+    (where an allocation anywhere in the process invalidates the capture) records,
+    the graph replays, and its J.v equals the context's own ldg_jvp."""
+    import torch
+    if which == "convdiff_hex":
+        o, g = pair(synth.hex_box((3, 4, 3), affine=SHEAR3), 3, oracle.CONVDIFF, oracle.CASE_EXPSIN, gmres_m=2)
+        u = cuda(synth.random_vector(o.ndof, 21))
+    else:
+        m = synth.quad_box((5, 4), hi=(2.0, 2.0), periodic=(True, True))
+        o, g = pair(m, 3, oracle.NS, oracle.CASE_ROTATION, gmres_m=2)
+        u = cuda(synth.random_euler_state(m.n_elem, o.npe, 22))
+    v = cuda(synth.random_vector(o.ndof, 23))
+    ref = host(g.jvp(u, v))
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g.set_stream(s)
+    out = torch.full_like(u, float("nan"))
+    with torch.cuda.stream(s):
+        assert _call(g, u, v, out) == 0
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s, capture_error_mode="global"):
+        rc = _call(g, u, v, out)
+    assert rc == 0
+    with torch.cuda.stream(s):
+        out.fill_(float("nan"))
+        graph.replay()
+    s.synchronize()
+    assert_parity(host(out), ref, what=f"jvp_noalloc replayed from a global-mode capture ({which})")
