@@ -199,3 +199,23 @@ def test_newton_step_halving_keeps_the_impulsive_start_finite():
     assert rep["newton_backtracks"] >= 1, rep
     assert rep["status"] in (0, -5), rep
     assert np.all(np.isfinite(host(u)))
+
+
+def test_full_navier_stokes_cylinder_40000_p3_sampled():
+    """Navier-Stokes past the cylinder on the full mesh of the time-to-1e-8 workload
+    (40,000 curved quadrilaterals, 100 layers x 400 around, p = 3, Re = 673, Mach 0.2
+    far field, no-slip wall): the kernels run on the whole state, and the oracle
+    evaluates R and J.v on a sample of elements (wall layer, outer layer, interior),
+    each with the q-stage of its face neighbours."""
+    mesh = synth.cylinder_mesh(100, 400, 3, seed=7)
+    o, g = _pair(mesh, 3, oracle.NS, oracle.CASE_CYLINDER, (1.4, 673.0, 0.72))
+    u = _gas_state(mesh, o.npe, 5, dp=15.0)
+    v = synth.random_vector(o.ndof, 6)
+    rng = np.random.default_rng(1)
+    el = np.unique(np.concatenate([[0, 399, 200, mesh.n_elem - 1, mesh.n_elem - 400, mesh.n_elem // 2],
+                                   rng.integers(0, mesh.n_elem, 30)]))
+    shape = (-1, 4, o.npe)
+    r = host(g.residual(cuda(u))).reshape(shape)[el]
+    assert_parity(r, o.residual_some(u, el), what="R cylinder 40,000 p=3")
+    jv = host(g.jvp(cuda(u), cuda(v))).reshape(shape)[el]
+    assert_parity(jv, o.jvp_some(u, v, el), what="J.v cylinder 40,000 p=3")
